@@ -1,0 +1,431 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks it against a
+printed worked example (Figs. 1, 2a, 2b), a closed form, a library routine, an
+independent brute force, or an invariant stated in the paper.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_00665_gb300 import inputs
+from tests import alg4_model, tree_checks as tc
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fig_karras_8_keys.json")
+
+
+def golden():
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    keys = np.array([int(b, 2) for b in g["keys_bits"]], np.uint64)
+    return g, keys
+
+
+# ---------------------------------------------------------------- Figs. 1, 2
+
+
+def test_golden_karras_topology_fig2a():
+    g, keys = golden()
+    n = len(keys)
+    t = oracle.tree_from_sorted(keys)
+    for name, node in g["karras_internal"].items():
+        k = tc.parse_node(name, n)
+        assert [t["range_l"][k], t["range_r"][k]] == node["range"], name
+        assert t["split"][k] == node["split"], name
+        assert t["left"][k] == tc.parse_node(node["left"], n), name
+        assert t["right"][k] == tc.parse_node(node["right"], n), name
+
+
+def test_golden_skips_fig1():
+    g, keys = golden()
+    n = len(keys)
+    t = oracle.tree_from_sorted(keys)
+    for name, target in g["skips"].items():
+        k = tc.parse_node(name, n)
+        got = t["skip_leaf"][k - (n - 1)] if name[0] == "L" else t["skip_internal"][k]
+        assert got == tc.parse_node(target, n), name
+
+
+def test_golden_apetrei_splits_fig2b():
+    """In Apetrei's ordering a node's index is its split (Sec. 3.2, Fig. 2b)."""
+    g, keys = golden()
+    n = len(keys)
+    t = oracle.tree_from_sorted(keys)
+
+    def apetrei_name(c):
+        if c >= n - 1:
+            return f"L{c - (n - 1)}"
+        return f"A{t['split'][c]}"
+
+    for k in range(n - 1):
+        children = [apetrei_name(t["left"][k]), apetrei_name(t["right"][k])]
+        assert g["apetrei_children"][f"A{t['split'][k]}"] == children
+    assert f"A{t['split'][0]}" == g["apetrei_root"]
+
+
+def test_golden_tree_invariants():
+    _, keys = golden()
+    t = oracle.tree_from_sorted(keys)
+    tc.check_karras_tree(keys, t["left"], t["right"], t["range_l"], t["range_r"], t["split"])
+    tc.check_skips(keys, t["left"], t["right"], t["skip_internal"], t["skip_leaf"])
+
+
+# ---------------------------------------------------------------- Algorithm 4
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_algorithm4_model_matches_oracle_any_interleaving(seed):
+    """Algorithm 4 (as read) builds the oracle's tree under any arrival order."""
+    rng = np.random.default_rng(seed)
+    for n in (1, 2, 3, 5, 8, 33, 200):
+        codes = np.sort(rng.integers(0, 1 << int(rng.integers(2, 12)), size=n).astype(np.uint64))
+        t = oracle.tree_from_sorted(codes)
+        for sched_seed in range(3):
+            m = alg4_model.run(codes, seed=sched_seed + 100 * seed)
+            assert m["left"] == t["left"].tolist()
+            assert m["skip_internal"] == t["skip_internal"].tolist()
+            assert m["skip_leaf"] == t["skip_leaf"].tolist()
+
+
+def test_algorithm4_golden_and_literal_left_child_line():
+    """The printed left-child line of Algorithm 4 does not give Fig. 1's tree;
+    the split reading (children of split p are p and p+1, Sec. 4) does."""
+    g, keys = golden()
+    n = len(keys)
+    want = [tc.parse_node(g["karras_internal"][f"I{k}"]["left"], n) for k in range(n - 1)]
+    for sched in ("random", "reverse", "forward"):
+        m = alg4_model.run(keys, seed=3, schedule=sched)
+        assert m["left"] == want
+    lit = alg4_model.run(keys, seed=3, left_child_rule="literal")
+    assert lit["left"] != want
+
+
+# ---------------------------------------------------------------- Morton codes
+
+
+def test_interleave_unit_bits():
+    # x is the most significant bit of each triple
+    assert oracle.interleave(1, 0, 0, 1) == 0b100
+    assert oracle.interleave(0, 1, 0, 1) == 0b010
+    assert oracle.interleave(0, 0, 1, 1) == 0b001
+    assert oracle.interleave(2, 0, 0, 2) == 0b100000
+    assert oracle.interleave(0, 0, 2, 2) == 0b001000
+    top = (1 << 21) - 1
+    assert oracle.interleave(top, top, top, 21) == (1 << 63) - 1
+
+
+def test_interleave_is_z_order():
+    """Z-order: comparing codes = comparing the tuples
+    (x_{b-1}, y_{b-1}, z_{b-1}, x_{b-2}, ...) lexicographically; and the map is
+    a bijection onto [0, 8^b)."""
+    b = 3
+    side = 1 << b
+    cells = [(x, y, z) for x in range(side) for y in range(side) for z in range(side)]
+    codes = [oracle.interleave(x, y, z, b) for x, y, z in cells]
+    assert sorted(codes) == list(range(side ** 3))
+
+    def bits(c):
+        x, y, z = c
+        return tuple(v for k in reversed(range(b)) for v in ((x >> k) & 1, (y >> k) & 1, (z >> k) & 1))
+
+    by_code = [c for _, c in sorted(zip(codes, cells))]
+    assert by_code == sorted(cells, key=bits)
+
+
+def test_quantize_special_cases():
+    for b in (1, 10, 21):
+        top = (1 << b) - 1
+        assert oracle.quantize(0.0, 0.0, 1.0, b) == 0
+        assert oracle.quantize(1.0, 0.0, 1.0, b) == top  # the maximum lands in the last cell
+        assert oracle.quantize(0.5, 0.0, 1.0, b) == 1 << (b - 1)
+        assert oracle.quantize(3.0, 3.0, 3.0, b) == 0  # zero extent
+        assert oracle.quantize(-2.0, -2.0, 6.0, b) == 0
+        assert oracle.quantize(6.0, -2.0, 6.0, b) == top
+
+
+def test_quantize_matches_exact_floor():
+    """Cell index vs floor(2^b (c-lo)/(hi-lo)) in exact rational arithmetic:
+    the FP32 steps may move a value across a cell boundary by rounding only."""
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    lo, hi = np.float32(-1.25), np.float32(3.5)
+    for b in (10, 21):
+        mismatches = 0
+        for c in rng.uniform(lo, hi, 2000).astype(np.float32):
+            exact = Fraction(float(c) - float(lo)) / Fraction(float(hi) - float(lo)) * (1 << b)
+            want = min(math.floor(exact), (1 << b) - 1)
+            got = oracle.quantize(float(c), float(lo), float(hi), b)
+            assert abs(got - want) <= 1
+            if got != want:
+                # three FP32 roundings (two subtractions, one division) move
+                # t by at most 3 ulp(1) = 3 * 2^-24, i.e. 3 * 2^(b-24) cells
+                assert abs(exact - round(exact)) <= Fraction(3, 1 << 24) * (1 << b)
+                mismatches += 1
+        assert mismatches <= 2 + 2000 * 3 * 2.0 ** (b - 24)
+
+
+def test_morton_codes_and_bounds():
+    pts = inputs.uniform_points(1000, seed=3)
+    codes, bounds = oracle.morton_codes(pts, oracle.POINTS, 30)
+    assert np.array_equal(bounds[:3], pts.min(axis=0)) and np.array_equal(bounds[3:], pts.max(axis=0))
+    # the points that reach each axis minimum / maximum land in cell 0 / 1023
+    for a, shift in ((0, 2), (1, 1), (2, 0)):
+        q = np.array([sum(((int(c) >> (3 * k + shift)) & 1) << k for k in range(10)) for c in codes])
+        assert q[np.argmin(pts[:, a])] == 0 and q[np.argmax(pts[:, a])] == 1023
+        # monotone: a larger coordinate never gets a smaller cell
+        o = np.argsort(pts[:, a], kind="stable")
+        assert np.all(np.diff(q[o]) >= 0)
+    assert codes.max() < (1 << 30)
+
+
+def test_box_centroids():
+    boxes = inputs.gaussian_mixture_boxes(500, seed=4)
+    c = np.zeros((500, 3), np.float32)
+    lib = oracle._load()
+    assert lib.oracle_centroids(boxes.ctypes.data, 500, oracle.BOXES, c.ctypes.data) == 0
+    want = (boxes[:, :3] + boxes[:, 3:]) * np.float32(0.5)
+    assert np.array_equal(c, want)
+
+
+def test_nonfinite_rejected():
+    pts = inputs.uniform_points(50, seed=1)
+    for bad in (np.nan, np.inf, -np.inf):
+        p = pts.copy()
+        p[17, 1] = bad
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.build(p, oracle.POINTS, 30)
+        assert e.value.status == oracle.NONFINITE
+
+
+def test_invalid_bits_rejected():
+    pts = inputs.uniform_points(10)
+    for bits in (0, 2, 31, 64, 66):
+        with pytest.raises(oracle.OracleError):
+            oracle.build(pts, oracle.POINTS, bits)
+
+
+# ---------------------------------------------------------------- sort, delta
+
+
+def test_sort_matches_stable_argsort():
+    rng = np.random.default_rng(7)
+    for distinct in (3, 100, 1 << 40):
+        codes = rng.integers(0, distinct, size=5000).astype(np.uint64)
+        perm, s = oracle.sort_codes(codes)
+        want = np.argsort(codes, kind="stable")
+        assert np.array_equal(perm, want.astype(np.uint32))
+        assert np.array_equal(s, codes[want])
+
+
+def test_delta_against_python_integers():
+    rng = np.random.default_rng(8)
+    codes = np.sort(rng.integers(0, 64, size=300).astype(np.uint64))
+    aug = tc.aug_keys(codes)
+    n = len(codes)
+    for _ in range(500):
+        i, j = sorted(rng.integers(0, n, size=2).tolist())
+        if i == j:
+            continue
+        want = (aug[i] ^ aug[j]).bit_length() - 1
+        assert oracle.delta(codes, i, j) == want
+        # delta over a range is the largest delta* inside it (sorted keys)
+        assert want == max(oracle.delta(codes, g, g + 1) for g in range(i, j))
+    INF = 2 ** 31 - 1
+    assert oracle.delta(codes, -1, 0) == INF and oracle.delta(codes, n - 1, n) == INF
+
+
+# ---------------------------------------------------------------- trees
+
+
+def _random_codes(rng, n, bits):
+    return rng.integers(0, 1 << bits, size=n).astype(np.uint64)
+
+
+@pytest.mark.parametrize("n,bits", [(2, 3), (3, 3), (17, 6), (64, 3), (257, 9), (1000, 30), (3000, 63)])
+def test_tree_invariants_random(n, bits):
+    rng = np.random.default_rng(n * 1000 + bits)
+    codes = np.sort(_random_codes(rng, n, min(bits, 62)))
+    t = oracle.tree_from_sorted(codes)
+    tc.check_karras_tree(codes, t["left"], t["right"], t["range_l"], t["range_r"], t["split"])
+    tc.check_skips(codes, t["left"], t["right"], t["skip_internal"], t["skip_leaf"])
+
+
+def test_tree_all_codes_equal():
+    """Equal codes: the position bits alone shape a balanced tree (Sec. 3.2)."""
+    n = 1000
+    codes = np.zeros(n, np.uint64)
+    t = oracle.tree_from_sorted(codes)
+    tc.check_karras_tree(codes, t["left"], t["right"], t["range_l"], t["range_r"], t["split"])
+    tc.check_skips(codes, t["left"], t["right"], t["skip_internal"], t["skip_leaf"])
+    depth = {0: 0}
+    for k in tc.preorder(n, t["left"], t["right"]):
+        if k < n - 1:
+            for c in (t["left"][k], t["right"][k]):
+                depth[int(c)] = depth[k] + 1
+    assert max(depth.values()) <= math.ceil(math.log2(n)) + 1
+
+
+def test_build_points_full():
+    pts = inputs.uniform_points(2000, seed=11)
+    t = oracle.build(pts, oracle.POINTS, 30)
+    want = np.argsort(t["codes"], kind="stable").astype(np.uint32)
+    assert np.array_equal(t["perm"], want)
+    tc.check_karras_tree(t["sorted"], t["left"], t["right"], t["range_l"], t["range_r"], t["split"])
+    tc.check_skips(t["sorted"], t["left"], t["right"], t["skip_internal"], t["skip_leaf"])
+    lb = np.concatenate([pts[t["perm"]], pts[t["perm"]]], axis=1)
+    assert np.array_equal(t["leaf_box"], lb)
+    tc.check_boxes(2000, t["range_l"], t["range_r"], t["leaf_box"], t["internal_box"])
+
+
+def test_build_boxes_duplicates_30bit():
+    boxes = inputs.gaussian_mixture_boxes(3000, seed=12, components=4)
+    t = oracle.build(boxes, oracle.BOXES, 30)
+    assert len(np.unique(t["codes"])) < 3000  # duplicate codes present
+    tc.check_karras_tree(t["sorted"], t["left"], t["right"], t["range_l"], t["range_r"], t["split"])
+    tc.check_skips(t["sorted"], t["left"], t["right"], t["skip_internal"], t["skip_leaf"])
+    assert np.array_equal(t["leaf_box"], boxes[t["perm"]])
+    tc.check_boxes(3000, t["range_l"], t["range_r"], t["leaf_box"], t["internal_box"])
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3])
+def test_tiny_builds(n):
+    pts = inputs.uniform_points(n, seed=2)
+    t = oracle.build(pts, oracle.POINTS, 63)
+    assert t["left"].shape == (max(n - 1, 0),)
+    if n == 1:
+        assert t["skip_leaf"].tolist() == [-1] and t["codes"].tolist() == [0]
+    if n >= 2:
+        tc.check_karras_tree(t["sorted"], t["left"], t["right"], t["range_l"], t["range_r"], t["split"])
+        tc.check_skips(t["sorted"], t["left"], t["right"], t["skip_internal"], t["skip_leaf"])
+    off, hits = oracle.query(t, pts, oracle.SPHERE, radius=10.0)
+    assert off.tolist() == [k * n for k in range(n + 1)]
+    for q in range(n):
+        assert hits[off[q]:off[q + 1]].tolist() == list(range(n))
+
+
+def test_degenerate_axes_and_all_equal_points():
+    p = inputs.collinear_points(500, seed=3)
+    t = oracle.build(p, oracle.POINTS, 30)
+    assert np.all(t["bounds"][[1, 2, 4, 5]] == 0)
+    tc.check_skips(t["sorted"], t["left"], t["right"], t["skip_internal"], t["skip_leaf"])
+    same = np.full((300, 3), 0.25, np.float32)
+    t = oracle.build(same, oracle.POINTS, 63)
+    assert np.all(t["codes"] == 0)
+    assert np.array_equal(t["perm"], np.arange(300, dtype=np.uint32))
+    tc.check_karras_tree(t["sorted"], t["left"], t["right"], t["range_l"], t["range_r"], t["split"])
+
+
+# ---------------------------------------------------------------- predicates, queries
+
+
+def test_sphere_predicate_against_fp64():
+    """Away from the boundary the FP32 test agrees with the exact distance."""
+    rng = np.random.default_rng(13)
+    agree = 0
+    for _ in range(3000):
+        c = rng.random(3).astype(np.float32)
+        lo = rng.random(3).astype(np.float32)
+        hi = (lo + rng.random(3).astype(np.float32) * np.float32(0.2)).astype(np.float32)
+        r = np.float32(rng.random() * 0.5)
+        e = np.maximum(np.maximum(lo.astype(np.float64) - c, c - hi.astype(np.float64)), 0.0)
+        d = math.sqrt(float((e * e).sum()))
+        if abs(d - float(r)) < 1e-5:
+            continue
+        assert oracle.sphere_box(c, r, np.concatenate([lo, hi])) == (d <= float(r))
+        agree += 1
+    assert agree > 2900
+
+
+def test_predicate_closed_boundaries():
+    box = np.array([0, 0, 0, 1, 1, 1], np.float32)
+    assert oracle.sphere_box([2.0, 0.5, 0.5], 1.0, box)  # touching: closed ball
+    assert not oracle.sphere_box([2.0, 0.5, 0.5], np.nextafter(np.float32(1), np.float32(0)), box)
+    assert oracle.sphere_box([0.5, 0.5, 0.5], 0.0, box)  # centre inside: d = 0
+    assert oracle.box_box(box, np.array([1, 1, 1, 2, 2, 2], np.float32))  # shared corner
+    assert not oracle.box_box(box, np.array([1.0000001, 0, 0, 2, 1, 1], np.float32))
+
+
+@pytest.mark.parametrize("case", ["uniform", "duplicates", "collinear", "all_equal", "boxes", "box_queries"])
+def test_traversal_equals_bruteforce(case):
+    rng = np.random.default_rng(21)
+    kind, qkind = oracle.POINTS, oracle.SPHERE
+    if case == "uniform":
+        prims = inputs.uniform_points(4096, seed=1)
+    elif case == "duplicates":
+        prims = inputs.duplicated_points(3000, 200, seed=2)
+    elif case == "collinear":
+        prims = inputs.collinear_points(2000, seed=3)
+    elif case == "all_equal":
+        prims = np.full((500, 3), 0.5, np.float32)
+    else:
+        prims = inputs.gaussian_mixture_boxes(3000, seed=4, components=8)
+        kind = oracle.BOXES
+    n = prims.shape[0]
+    if case == "box_queries":
+        queries = inputs.gaussian_mixture_boxes(700, seed=5, components=8, component_seed=4)
+        qkind = oracle.BOX
+        radii = None
+    else:
+        queries = rng.random((700, 3)).astype(np.float32)
+        # some queries sit on primitives (box primitives: at their low corner)
+        queries[:100] = prims[rng.integers(0, n, size=100), :3]
+        radii = (rng.random(700) * 0.08).astype(np.float32)
+    for bits in (30, 63):
+        t = oracle.build(prims, kind, bits)
+        off, hits = oracle.query(t, queries, qkind, radii=radii)
+        boff, bhits = oracle.bruteforce(prims, kind, queries, qkind, radii=radii)
+        assert np.array_equal(off, boff) and np.array_equal(hits, bhits)
+    assert off[-1] > 0
+
+
+def test_query_radius_scalar_and_self_hits():
+    pts = inputs.uniform_points(16384, seed=0)
+    r = inputs.radius_for_neighbours(16384)
+    assert r == np.float32(0.061546564)
+    t = oracle.build(pts, oracle.POINTS, 30)
+    off, hits = oracle.query(t, pts[:500], oracle.SPHERE, radius=r)
+    counts = np.diff(off)
+    # every query centred at a primitive reports that primitive
+    for q in range(500):
+        assert q in hits[off[q]:off[q + 1]]
+        seg = hits[off[q]:off[q + 1]]
+        assert np.all(np.diff(seg.astype(np.int64)) > 0)
+    assert 10 < counts.mean() < 20  # about 16 expected, fewer at the faces
+
+
+# ---------------------------------------------------------------- the checks catch planted mistakes
+
+
+def test_checks_catch_planted_mistakes():
+    """A mistake planted in the oracle's output (wrong index, off by one,
+    swapped operands) must fail one of the independent checks."""
+    pts = inputs.uniform_points(300, seed=9)
+    t = oracle.build(pts, oracle.POINTS, 30)
+    s = t["sorted"]
+
+    def fails(fn):
+        try:
+            fn()
+        except AssertionError:
+            return True
+        return False
+
+    left = t["left"].copy(); left[[5, 9]] = left[[9, 5]]
+    assert fails(lambda: tc.check_karras_tree(s, left, t["right"]))
+    right = t["right"].copy(); right[0] = t["left"][0]
+    assert fails(lambda: tc.check_karras_tree(s, t["left"], right))
+    si = t["skip_internal"].copy(); si[3] = si[3] + 1 if si[3] >= 0 else 0
+    assert fails(lambda: tc.check_skips(s, t["left"], t["right"], si, t["skip_leaf"]))
+    sl = t["skip_leaf"].copy(); sl[10] = 299 + 11
+    assert fails(lambda: tc.check_skips(s, t["left"], t["right"], t["skip_internal"], sl))
+    ib = t["internal_box"].copy(); ib[7, [0, 3]] = ib[7, [3, 0]]
+    assert fails(lambda: tc.check_boxes(300, t["range_l"], t["range_r"], t["leaf_box"], ib))
+    swapped = s.copy(); swapped[[40, 41]] = swapped[[41, 40]]
+    if swapped[40] != swapped[41]:
+        assert fails(lambda: tc.check_karras_tree(swapped, t["left"], t["right"]))
