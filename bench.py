@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Benchmark of the LBVH hot path: one step = one full build plus one full
+range query of the same size, on synthetic inputs already resident in HBM.
+
+Workload (default): 2^25 points uniform in [0,1)^3 (FP32), 63-bit Morton codes;
+a build (bounds, Morton codes, 8 radix-sort passes, Algorithm 4 construct) and
+2^25 sphere queries centred at the points with the radius that holds 16
+expected neighbours (Algorithm 1, CSR output with sorted hit lists).
+
+Prints ONE JSON line (rank 0). ``value`` is primitives per second through the
+whole step (build + query), whole job, device-timed with CUDA events on the
+stream the kernels run on. ``e2e`` is the same metric through the C-ABI call
+from host buffers: each step copies the points from pinned host memory,
+builds, queries, and copies the CSR result back. ``roofline`` reports the
+dominant kernel's algorithmic bytes over its event-timed duration against the
+measured HBM copy bandwidth. ``cpu_baseline`` times the CPU oracle on a
+bounded sample of the same workload (rank 0, N=1 only).
+
+``--impl reference`` times the CPU oracle itself, as the reference arm.
+
+Multi-GPU: every rank builds and queries its own independent instance (no
+data-path collective; replicas only); ``value`` = all ranks' primitives over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_00665_gb300 import inputs  # noqa: E402
+
+METRIC = "build+query Mprims/s (one LBVH build and n radius queries per step)"
+UNIT = "Mprims/s"
+
+# Algorithmic bytes per primitive (or per query) of each stage: the data the
+# method itself must move, independent of how a kernel moves it.
+#   bounds      read the points                              12
+#   encode      read the points, write the 64-bit codes      12 + 8
+#   sort pass   read key + payload, write key + payload      12 + 12 (pass 0: no payload read)
+#   construct   key 8 + perm 4 + point 12 read, leaf 16 and internal node 32
+#               written, store word 8, sibling box 24 re-read
+#   query count query 12 read, count 4 written, tree read once (48 B per leaf)
+#   query fill  query 12 + offset 8 read, 4 per hit written, tree once
+ALG_BYTES = {
+    "bounds": lambda n, nq, hits: 12 * n,
+    "encode": lambda n, nq, hits: 20 * n,
+    "sort_pass0": lambda n, nq, hits: 20 * n,
+    **{f"sort_pass{k}": (lambda n, nq, hits: 24 * n) for k in range(1, 8)},
+    "construct": lambda n, nq, hits: 104 * n,
+    "query_count": lambda n, nq, hits: 16 * nq + 48 * n,
+    "query_scan": lambda n, nq, hits: 4 * nq + 8 * (nq + 1),
+    "query_fill": lambda n, nq, hits: 20 * nq + 4 * hits + 48 * n,
+    "query_fixup": lambda n, nq, hits: 0,
+}
+
+WORKLOADS = {
+    # name: (description, n, bits, kind, generator)
+    "uniform_2^25_63bit": ("2^25 FP32 points uniform in [0,1)^3, 63-bit Morton codes; build + 2^25 sphere "
+                           "queries at the points, radius for 16 expected neighbours", 1 << 25, 63),
+    "uniform_16384_30bit": ("16,384 FP32 points uniform in [0,1)^3 (seed 0), 30-bit codes; build + 16,384 "
+                            "sphere queries at the points, radius for 16 expected neighbours", 16384, 30),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lbvh", "reference"], default="lbvh")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform_2^25_63bit")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+
+
+def dist_setup(use_cuda: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.uuid and parts[0] != self.uuid and len({r[0] for r in rows} | {parts[0]}) > 1:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- workload
+
+
+def make_inputs(workload: str, seed: int):
+    desc, n, bits = WORKLOADS[workload]
+    pts = inputs.uniform_points(n, seed=seed)
+    r = inputs.radius_for_neighbours(n)
+    return desc, n, bits, pts, r
+
+
+def measured_hbm_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(stage: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since the capture; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        table = json.load(f)
+    e = table.get(stage)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2402_00665_gb300", "csrc", e["source"])
+    if not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if sha != e.get("source_sha"):
+        return None
+    return e.get("bytes_per_launch_full")
+
+
+# ---------------------------------------------------------------- oracle timing
+
+
+def oracle_sample(seed: int, n_sample: int = 1 << 20, q_sample: int = 1 << 14, bits: int = 63):
+    """The CPU oracle on a bounded sample of the same workload: a full build of
+    n_sample uniform points and q_sample of its radius queries (radius for 16
+    neighbours at that size). Returns (prims/s, description)."""
+    import oracle
+    pts = inputs.uniform_points(n_sample, seed=seed + 101)
+    r = inputs.radius_for_neighbours(n_sample)
+    t0 = time.perf_counter()
+    tree = oracle.build(pts, oracle.POINTS, bits)
+    t1 = time.perf_counter()
+    oracle.query(tree, pts[:q_sample], oracle.SPHERE, radius=r)
+    t2 = time.perf_counter()
+    per_prim = (t1 - t0) / n_sample + (t2 - t1) / q_sample
+    desc = (f"oracle (C, 1 thread) build of {n_sample} uniform points at {bits} bits "
+            f"({t1 - t0:.2f} s) + {q_sample} of its 16-neighbour sphere queries ({t2 - t1:.2f} s); "
+            f"throughput = 1 / (build s/prim + query s/query)")
+    return 1.0 / per_prim, desc, t2 - t0
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    desc, n, bits = WORKLOADS[args.workload][:3]
+    samples = []
+    for step in range(args.warmup + args.steps):
+        v, sdesc, _ = oracle_sample(args.seed + step, n_sample=1 << 19, q_sample=1 << 13, bits=bits)
+        if step >= args.warmup:
+            samples.append(v)
+    value = statistics.median(samples) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": n / (value * 1e6) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": n, "morton_bits": bits},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args, world, rank, local):
+    import torch
+    from paper_2402_00665_gb300 import lbvh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, n, bits, pts_host, radius = make_inputs(args.workload, args.seed + rank)
+    nq = n
+    pts = torch.from_numpy(pts_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    tree = lbvh.Tree()
+    tree.set_profiling(True)
+    offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
+    # size the hit buffer once (a production caller does the same)
+    tree.build(pts, lbvh.POINTS, bits)
+    st, total = tree.query_into(pts, lbvh.SPHERE, offsets, None, radius=float(radius))
+    assert st in (lbvh.OK, lbvh.ERR_CAPACITY), st
+    hits = torch.empty(max(int(total * 1.05) + 1024, 1), dtype=torch.int32, device=dev)
+
+    def step():
+        tree.build(pts, lbvh.POINTS, bits)
+        s, tot = tree.query_into(pts, lbvh.SPHERE, offsets, hits, radius=float(radius))
+        if s != lbvh.OK:
+            raise lbvh.LbvhError(s, "lbvh_query_into")
+        return tot
+
+    for _ in range(args.warmup):
+        step()
+    tree.check()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(props.uuid) if not str(props.uuid).startswith("GPU-") else str(props.uuid)
+    except Exception:
+        pass
+
+    stage_sum: dict[str, float] = {}
+    stage_cnt: dict[str, int] = {}
+    launches0 = lbvh.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        total_hits = 0
+        for _ in range(args.steps):
+            total_hits = step()
+            for k, v in tree.stage_times().items():
+                stage_sum[k] = stage_sum.get(k, 0.0) + v
+                stage_cnt[k] = stage_cnt.get(k, 0) + 1
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    launches = lbvh.kernel_launches() - launches0
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world, dev)
+    ms_step = ms_total / args.steps
+    value = n * world / (ms_step * 1e-3) / 1e6
+    clock = clocks.summary()
+
+    stage_ms = {k: stage_sum[k] / stage_cnt[k] for k in stage_sum}
+    build_ms = sum(v for k, v in stage_ms.items() if not k.startswith("query"))
+    query_ms = sum(v for k, v in stage_ms.items() if k.startswith("query"))
+    dominant = max(stage_ms, key=lambda k: stage_ms[k])
+    peak, peak_kind = measured_hbm_gbs()
+    alg = {k: ALG_BYTES[k](n, nq, total_hits) for k in stage_ms if k in ALG_BYTES}
+    achieved = alg[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+    build_bytes = sum(v for k, v in alg.items() if not k.startswith("query"))
+
+    # ---- end to end through the C ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_pts = torch.from_numpy(pts_host).pin_memory()
+        host_off = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
+        host_hits = torch.empty(hits.numel(), dtype=torch.int32).pin_memory()
+        dpts = torch.empty_like(pts)
+
+        def e2e_step():
+            dpts.copy_(host_pts, non_blocking=True)
+            tree.build(dpts, lbvh.POINTS, bits)
+            s, tot = tree.query_into(dpts, lbvh.SPHERE, offsets, hits, radius=float(radius))
+            if s != lbvh.OK:
+                raise lbvh.LbvhError(s, "lbvh_query_into")
+            host_off.copy_(offsets, non_blocking=True)
+            host_hits[:tot].copy_(hits[:tot], non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+            return tot
+
+        for _ in range(2):
+            e2e_step()
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot = 0
+        for _ in range(args.steps):
+            tot = e2e_step()
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev) / args.steps
+        e2e = {"value": n * world / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": int(pts.numel() * 4),
+               "d2h_bytes_per_step": int((nq + 1) * 8 + tot * 4),
+               "note": "pinned host points -> device, build, query, CSR offsets + hits -> pinned host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, sdesc, _ = oracle_sample(args.seed)
+        cpu = {"value": v / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": n, "nq": nq,
+                       "morton_bits": bits, "radius": float(radius), "mean_hits": total_hits / nq,
+                       "l2": "inputs larger than L2 (points 402 MB; step touches ~5 GB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "build_mprims_s": n / (build_ms * 1e-3) / 1e6,
+            "query_mqueries_s": nq / (query_ms * 1e-3) / 1e6,
+            "build_hbm_frac": build_bytes / (build_ms * 1e-3) / 1e9 / peak,
+            "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda kv: -kv[1])},
+            "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic_for(dominant),
+                         "algorithmic_bytes": alg[dominant]},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clock,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    tree.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        world, rank, _ = dist_setup(False)
+        run_reference(args, world, rank)
+        return
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for the lbvh arm")
+    world, rank, local = dist_setup(True)
+    run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

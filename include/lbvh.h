@@ -1,0 +1,223 @@
+/*
+ * lbvh.h -- C ABI of the GB300 (sm_103a) linear BVH with skip connections.
+ *
+ * Method: Prokopenko & Lebrun-Grandie, "Revising Apetrei's bounding volume
+ * hierarchy construction algorithm to allow stackless traversal",
+ * arXiv 2402.00665. The build computes Morton codes (Sec. 3.1 step 1), sorts
+ * them (step 2), and runs the modified Apetrei bottom-up pass (Sec. 4,
+ * Algorithm 4) that writes every internal node in Karras' ordering with its
+ * left child, its skip connection (Sec. 2, Algorithm 2) and its box (step 4),
+ * in one pass. Queries walk the tree without a stack (Algorithm 1).
+ *
+ * Conventions for every function below
+ *   - Pointers named d_* are device pointers (cudaMalloc, cudaMallocAsync or
+ *     a PyTorch CUDA tensor), h_* are host pointers. The library never frees
+ *     memory the caller passed in.
+ *   - `stream` is a cudaStream_t (CUstream) handle passed as void*; NULL is
+ *     the legacy default stream. Work is enqueued on it and ordered with the
+ *     caller's other work on that stream. Calls that must know a size on the
+ *     host (a query's hit count, an export) synchronise that stream and say so.
+ *   - Every function returns an lbvh_status and never throws. A device-side
+ *     error found during a build (non-finite input, a sort wait that ran out)
+ *     is latched in the tree and reported by the next call that synchronises:
+ *     lbvh_tree_status, lbvh_query*, lbvh_tree_export.
+ *   - Floating-point layouts: points float[n][3] (x, y, z); boxes float[n][6]
+ *     (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z); sphere queries float[nq][3]
+ *     centres; box queries float[nq][6]. Arrays are contiguous, row-major.
+ *   - Canonical node ids (export): internal node k -> k, leaf k -> (n-1)+k,
+ *     sentinel -> -1. Leaf k is the k-th primitive in sorted Morton order and
+ *     perm[k] is its primitive index. The root is id 0 (I_0; L_0 when n == 1).
+ *   - Results are exact (bit-identical to the CPU oracle): codes, topology,
+ *     skips and FP32 boxes (min/max only), and the CSR hit lists, whose
+ *     entries are primitive indices in ascending order within each query.
+ */
+#ifndef LBVH_H
+#define LBVH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbvh_tree_s *lbvh_tree_t; /* opaque; device storage owned by the library */
+typedef void *lbvh_stream_t;             /* cudaStream_t */
+
+typedef enum {
+    LBVH_OK = 0,
+    LBVH_ERR_INVALID = 1,   /* bad argument: null pointer, size out of range, bad kind/bits */
+    LBVH_ERR_NONFINITE = 2, /* a primitive centroid is NaN or infinite */
+    LBVH_ERR_OOM = 3,       /* device allocation failed */
+    LBVH_ERR_CUDA = 4,      /* a CUDA runtime call failed (see lbvh_last_cuda_error) */
+    LBVH_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out; results are invalid */
+    LBVH_ERR_CORRUPT = 6,   /* a traversal exceeded 2(2n-1) steps; the tree is not valid */
+    LBVH_ERR_CAPACITY = 7   /* the caller's hit buffer is too small; *total holds the need */
+} lbvh_status;
+
+typedef enum { LBVH_PRIM_POINTS = 0, LBVH_PRIM_BOXES = 1 } lbvh_prim_kind;
+typedef enum { LBVH_Q_SPHERE = 0, LBVH_Q_BOX = 1 } lbvh_query_kind;
+
+/* Largest primitive count of one tree: the sort's look-back words carry a
+ * 30-bit count and node ids are int32 over 2n-1 nodes. */
+#define LBVH_MAX_PRIMS ((int64_t)((1 << 30) - 1))
+
+/* ---------------------------------------------------------------- tree */
+
+/* Create an empty tree handle (no device memory yet). *out receives it. */
+lbvh_status lbvh_tree_create(lbvh_tree_t *out);
+
+/* Release the tree and all device memory it owns. Waits for the tree's last
+ * stream first. Accepts NULL. */
+void lbvh_tree_destroy(lbvh_tree_t tree);
+
+/* Build (or rebuild in place) the whole hierarchy: scene bounds, Morton codes
+ * (Sec. 3.1 step 1), stable radix sort of the codes with the primitive index
+ * as payload (step 2), and the single bottom-up pass of Algorithm 4 that
+ * writes internal nodes in Karras' ordering with left child, skip and box, and
+ * every leaf's skip and box (Sec. 4).
+ *   d_prims      device float[n][3] (points) or float[n][6] (boxes); read only
+ *                during the call's stream work; the tree keeps its own copy of
+ *                the geometry in its leaves.
+ *   n            0 <= n <= LBVH_MAX_PRIMS (n == 0 gives an empty tree).
+ *   kind         lbvh_prim_kind.
+ *   morton_bits  total code bits, a multiple of 3 in [3, 63] (30 and 63 are
+ *                the usual choices: 10 or 21 bits per axis).
+ * Asynchronous on `stream`; device storage grows (cudaMallocAsync) only when n
+ * exceeds what the tree already holds. Errors found on the device are latched
+ * (see lbvh_tree_status). Returns LBVH_ERR_INVALID for bad arguments. */
+lbvh_status lbvh_build(lbvh_tree_t tree, const float *d_prims, int64_t n, int kind,
+                       int morton_bits, lbvh_stream_t stream);
+
+/* Build from codes that are already sorted (Sec. 3.1 steps 3-4 and Sec. 4
+ * only): d_sorted_codes uint64[n] ascending, d_perm uint32[n] the primitive
+ * index of each sorted position, d_prims the geometry as for lbvh_build.
+ * Used to test the bottom-up pass on the paper's worked example. */
+lbvh_status lbvh_build_from_sorted(lbvh_tree_t tree, const uint64_t *d_sorted_codes,
+                                   const uint32_t *d_perm, const float *d_prims, int64_t n,
+                                   int kind, lbvh_stream_t stream);
+
+/* Synchronise the tree's stream and return the first error latched by its
+ * last build (LBVH_OK if none). */
+lbvh_status lbvh_tree_status(lbvh_tree_t tree);
+
+/* Number of primitives of the last build. */
+lbvh_status lbvh_tree_size(lbvh_tree_t tree, int64_t *n);
+
+/* Device bytes the tree currently holds (nodes, leaves, sort and query
+ * scratch). */
+lbvh_status lbvh_tree_bytes(lbvh_tree_t tree, uint64_t *bytes);
+
+/* Copy the canonical arrays of the last build to host memory. Synchronises
+ * the tree's stream. Any pointer may be NULL to skip that array.
+ *   h_perm          uint32[n]   primitive index of sorted position k
+ *   h_sorted_codes  uint64[n]   Morton code of sorted position k
+ *   h_left          int32[n-1]  left child id of internal node k
+ *   h_skip_internal int32[n-1]  skip id of internal node k
+ *   h_skip_leaf     int32[n]    skip id of leaf k
+ *   h_internal_box  float[n-1][6] box of internal node k (lo.xyz, hi.xyz)
+ *   h_leaf_box      float[n][6]   box of leaf k (points: lo == hi)
+ *   h_bounds        float[6]      scene bounds of the centroids (min, max) */
+lbvh_status lbvh_tree_export(lbvh_tree_t tree, uint32_t *h_perm, uint64_t *h_sorted_codes,
+                             int32_t *h_left, int32_t *h_skip_internal, int32_t *h_skip_leaf,
+                             float *h_internal_box, float *h_leaf_box, float *h_bounds);
+
+/* ---------------------------------------------------------------- queries */
+
+/* Stackless range query (Algorithm 1) of every query against the tree, with
+ * results in caller-owned CSR buffers.
+ *   d_queries  sphere centres float[nq][3] or boxes float[nq][6].
+ *   qkind      lbvh_query_kind. Sphere: closed ball, hit iff the squared
+ *              distance from the centre to the primitive's box, summed over
+ *              x, y, z in that order in FP32 without fused multiply-add, is
+ *              <= r*r. Box: closed overlap on all three axes.
+ *   d_radii    float[nq] per-query radius, or NULL to use `radius` for all
+ *              (`radius` must then be finite and >= 0).
+ *   d_offsets  int64[nq+1]: hits of query q are d_hits[d_offsets[q] ..
+ *              d_offsets[q+1]), primitive indices in ascending order.
+ *   d_hits     uint32[capacity].
+ *   total      out: the total number of hits.
+ * Synchronises `stream` once (to learn the total). If total > capacity the
+ * call returns LBVH_ERR_CAPACITY with *total set and d_offsets valid, and
+ * leaves d_hits unspecified; call again with a larger buffer. */
+lbvh_status lbvh_query_into(lbvh_tree_t tree, const float *d_queries, int64_t nq, int qkind,
+                            const float *d_radii, float radius, int64_t *d_offsets,
+                            uint32_t *d_hits, uint64_t capacity, uint64_t *total,
+                            lbvh_stream_t stream);
+
+/* As lbvh_query_into, but the library allocates the CSR arrays
+ * (*d_offsets int64[nq+1], *d_hits uint32[*total]); free them with lbvh_free. */
+lbvh_status lbvh_query(lbvh_tree_t tree, const float *d_queries, int64_t nq, int qkind,
+                       const float *d_radii, float radius, int64_t **d_offsets,
+                       uint32_t **d_hits, uint64_t *total, lbvh_stream_t stream);
+
+/* Free device memory returned by lbvh_query. Accepts NULL. */
+void lbvh_free(void *d_ptr);
+
+/* ---------------------------------------------------------------- stages */
+
+/* Scene bounds and Morton code of every primitive (Sec. 3.1 step 1): the
+ * centroid (a box's is (lo + hi) * 0.5) is quantised per axis to b =
+ * morton_bits/3 bits inside the bounds, t = (c - min)/(max - min) in FP32,
+ * cell = clamp(trunc(t * 2^b), 0, 2^b - 1), 0 on an axis of zero extent; the
+ * bits are interleaved with x the most significant of each triple.
+ *   d_codes   uint64[n] out.   d_bounds  float[6] out (min.xyz, max.xyz).
+ * Returns LBVH_ERR_NONFINITE (after synchronising `stream`) if any centroid
+ * is not finite. */
+lbvh_status lbvh_morton_codes(const float *d_prims, int64_t n, int kind, int morton_bits,
+                              uint64_t *d_codes, float *d_bounds, lbvh_stream_t stream);
+
+/* Stable LSD radix sort of 64-bit keys with 32-bit payloads (Sec. 3.1 step
+ * 2). Only the low `key_bits` bits (1..64) of each key are sorted on. d_vals
+ * may be NULL for the payload 0, 1, ..., n-1 (the primitive index). Inputs are
+ * not modified; outputs must not alias inputs. Synchronises `stream` and
+ * returns LBVH_ERR_TIMEOUT if a bounded device wait ran out. */
+lbvh_status lbvh_sort_pairs(const uint64_t *d_keys, const uint32_t *d_vals, int64_t n,
+                            int key_bits, uint64_t *d_keys_out, uint32_t *d_vals_out,
+                            lbvh_stream_t stream);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Stage ids of lbvh_tree_stage_times (device time of one kernel launch, or of
+ * one sort pass). */
+enum {
+    LBVH_STAGE_BOUNDS = 0,     /* scene bounds reduction */
+    LBVH_STAGE_ENCODE = 1,     /* Morton codes + sort digit histograms */
+    LBVH_STAGE_SORT0 = 2,      /* radix-sort pass k is LBVH_STAGE_SORT0 + k, k < 8 */
+    LBVH_STAGE_CONSTRUCT = 10, /* Algorithm 4: nodes, boxes, skips */
+    LBVH_STAGE_QCOUNT = 11,    /* Algorithm 1, counting walk */
+    LBVH_STAGE_QSCAN = 12,     /* exclusive scan of the counts */
+    LBVH_STAGE_QFILL = 13,     /* Algorithm 1, filling walk + per-query sort */
+    LBVH_STAGE_QFIXUP = 14,    /* sort of hit lists longer than a thread buffers */
+    LBVH_STAGE_COUNT = 16
+};
+
+/* Turn per-stage timing of this tree's builds and queries on or off (off by
+ * default). When on, a CUDA event pair is recorded around each stage on the
+ * stream the stage runs on. */
+lbvh_status lbvh_tree_set_profiling(lbvh_tree_t tree, int on);
+
+/* Device milliseconds of each stage of the tree's last build and last query
+ * (ms: float[LBVH_STAGE_COUNT]; NaN for a stage that did not run or was not
+ * timed). Synchronises the streams involved. */
+lbvh_status lbvh_tree_stage_times(lbvh_tree_t tree, float *ms);
+
+/* Name of a stage id ("" if unknown). */
+const char *lbvh_stage_name(int stage);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t lbvh_kernel_launches(void);
+
+/* ---------------------------------------------------------------- misc */
+
+/* Human-readable name of a status. */
+const char *lbvh_status_str(lbvh_status status);
+
+/* Text of the last CUDA runtime error seen by this thread ("" if none). */
+const char *lbvh_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBVH_H */

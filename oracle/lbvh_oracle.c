@@ -37,7 +37,8 @@
  *                 get ids g and g+1 (leaf when the range is one key). Root I_0.
  *   Skips         Sec. 2 and Fig. 1: the node that follows the subtree in
  *                 pre-order, the sentinel on the right-most path.
- *   Boxes         Sec. 3.1 step 4: union of the children's boxes.
+ *   Boxes         Sec. 3.1 step 4: union of the children's boxes. Min and
+ *                 max (here and in the bounds) order -0.0 below +0.0.
  *   Queries       Algorithm 1. Sphere: closed ball; squared distance from the
  *                 centre to the box, axes x, y, z summed in that order with
  *                 separate multiply and add. Box: closed overlap test.
@@ -72,6 +73,11 @@ int oracle_centroids(const float *prims, int64_t n, int kind, float *out) {
     return ORACLE_OK;
 }
 
+/* a < b in the total order of finite floats that puts -0.0 below +0.0
+ * (the paper is silent; this makes min and max independent of the order in
+ * which values are combined) */
+static int is_below(float a, float b) { return a < b || (a == b && signbit(a) && !signbit(b)); }
+
 int oracle_scene_bounds(const float *c, int64_t n, float *out) {
     if (n <= 0) return ORACLE_INVALID;
     for (int a = 0; a < 3; ++a) {
@@ -82,8 +88,8 @@ int oracle_scene_bounds(const float *c, int64_t n, float *out) {
         for (int a = 0; a < 3; ++a) {
             float v = c[3 * i + a];
             if (!isfinite(v)) return ORACLE_NONFINITE;
-            if (v < out[a]) out[a] = v;
-            if (v > out[3 + a]) out[3 + a] = v;
+            if (is_below(v, out[a])) out[a] = v;
+            if (is_below(out[3 + a], v)) out[3 + a] = v;
         }
     }
     return ORACLE_OK;
@@ -318,8 +324,8 @@ int oracle_boxes(const float *prims, int64_t n, int kind, const uint32_t *perm,
                                          : leaf_box + 6 * (int64_t)(right[id] - ni);
         float *out = internal_box + 6 * (int64_t)id;
         for (int a = 0; a < 3; ++a) {
-            out[a] = bl[a] < br[a] ? bl[a] : br[a];
-            out[3 + a] = bl[3 + a] > br[3 + a] ? bl[3 + a] : br[3 + a];
+            out[a] = is_below(br[a], bl[a]) ? br[a] : bl[a];
+            out[3 + a] = is_below(bl[3 + a], br[3 + a]) ? br[3 + a] : bl[3 + a];
         }
     }
     free(order);

@@ -1,0 +1,184 @@
+// construct.cu -- the single bottom-up pass of Algorithm 4 (Sec. 4): modified
+// Apetrei merge that writes every internal node in Karras' ordering (Sec. 3.1)
+// with its left child, its skip connection (Algorithm 2) and its box (Karras
+// step 4, which Algorithm 4 leaves out; here the second thread up writes the
+// union of its own box, held in registers, and its sibling's).
+//
+// One thread per leaf i:
+//   1. delta*(i-1), delta*(i), delta*(i+1) from the sorted codes. delta is the
+//      XOR reading of Sec. 3.2 with keys augmented by their sorted position:
+//      64 + highest differing code bit, else the highest differing bit of the
+//      positions; +inf (255) at -1 and n-1. Only comparisons are made and no
+//      two compared gaps can share a highest bit, so this order is exact.
+//   2. The leaf's skip (Algorithm 4's leaf lines) and box are written.
+//   3. Climb: the parent's split p is range_right (left child: delta_right <
+//      delta_left) or range_left - 1 (right child). The thread swaps its half
+//      of the parent's description into store[p]. The first arrival reads
+//      "empty" and exits; the second receives the other half, so it now knows
+//      the parent's full range [l, r] and delta*(l-1), delta*(r), delta*(r+1).
+//      It computes the Karras index q = r if delta*(r) < delta*(l-1) else l,
+//      the left child (L_p if l == p else I_p: the children of split p are p
+//      and p+1), the skip (sentinel if r == n-1, else L_{r+1} if delta*(r) <
+//      delta*(r+1), else I_{r+1}), and the box, writes node q, and continues
+//      with i = q until q == 0 (I_0 is the root in Karras' ordering).
+//
+// Differences from the listing, with the same result:
+//   - store[p] carries, besides the range end, the delta* values the other
+//     thread needs (packed into 64 bits), so no thread re-reads codes while
+//     it climbs; only the leaf step reads codes, coalesced.
+//   - an atomic exchange replaces compare-and-swap: exactly two threads
+//     ever touch store[p], so the one that reads "empty" is the first. The
+//     second writes "empty" back, leaving the scratch clean for the next build
+//     (it is zeroed once, when allocated).
+//   - release/acquire: each thread fences after writing its node and before
+//     the exchange; the second fences after the exchange and reads the
+//     sibling's box through L2 (ld.global.cg).
+#include "lbvh_internal.cuh"
+
+namespace lbvh {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr uint32_t kInf = 255;  // above every finite delta* (<= 127)
+
+__device__ __forceinline__ uint32_t delta_star(uint64_t a, uint64_t b, uint32_t pos) {
+    const uint64_t x = a ^ b;
+    if (x) return 127u - (uint32_t)__clzll((long long)x);  // 64 + highest differing bit
+    return 31u - (uint32_t)__clz((int)(pos ^ (pos + 1u)));
+}
+
+// store word: bit 63 set = occupied.
+//   left child's half (its range start l and delta*(l-1)):   l | d << 32
+//   right child's half (range end r, delta*(r), delta*(r+1)): r | d << 32 | dn << 40
+__device__ __forceinline__ unsigned long long pack(uint32_t end, uint32_t d, uint32_t dn) {
+    return (1ull << 63) | ((unsigned long long)dn << 40) | ((unsigned long long)d << 32) | end;
+}
+
+template <int kKind>
+__device__ __forceinline__ void load_node_box(const float4 *inodes, const float4 *leaves, int ni,
+                                              int id, float3 &lo, float3 &hi) {
+    if (id < ni) {
+        const float4 a = __ldcg(inodes + 2 * (int64_t)id);
+        const float4 b = __ldcg(inodes + 2 * (int64_t)id + 1);
+        lo = make_float3(a.x, a.y, a.z);
+        hi = make_float3(b.x, b.y, b.z);
+    } else if (kKind == LBVH_PRIM_POINTS) {
+        const float4 a = __ldcg(leaves + (id - ni));
+        lo = make_float3(a.x, a.y, a.z);
+        hi = lo;
+    } else {
+        const float4 a = __ldcg(leaves + 2 * (int64_t)(id - ni));
+        const float4 b = __ldcg(leaves + 2 * (int64_t)(id - ni) + 1);
+        lo = make_float3(a.x, a.y, a.z);
+        hi = make_float3(b.x, b.y, b.z);
+    }
+}
+
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
+                     const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
+                     unsigned long long *store, uint32_t *flags) {
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const int ni = n - 1;
+
+    // ---- delta* around the leaf
+    const uint64_t c0 = codes[i];
+    const uint32_t dl = i > 0 ? delta_star(codes[i - 1], c0, (uint32_t)(i - 1)) : kInf;
+    uint32_t dr = kInf, drn = kInf;
+    if (i + 1 < n) {
+        const uint64_t c1 = codes[i + 1];
+        dr = delta_star(c0, c1, (uint32_t)i);
+        if (i + 2 < n) drn = delta_star(c1, codes[i + 2], (uint32_t)(i + 1));
+    }
+
+    // ---- leaf: skip (Algorithm 4, leaf part) and box
+    const int leaf_skip = i == n - 1 ? kSentinel : (dr < drn ? ni + i + 1 : i + 1);
+    const uint32_t p_id = perm[i];
+    if (p_id >= (uint32_t)n) {  // not a permutation: the sort failed
+        atomicOr(flags, kFlagCorrupt);
+        return;
+    }
+    float3 lo, hi;
+    if (kKind == LBVH_PRIM_POINTS) {
+        lo = make_float3(prims[3 * (int64_t)p_id], prims[3 * (int64_t)p_id + 1],
+                         prims[3 * (int64_t)p_id + 2]);
+        hi = lo;
+        leaves[i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
+    } else {
+        const float *b = prims + 6 * (int64_t)p_id;
+        lo = make_float3(b[0], b[1], b[2]);
+        hi = make_float3(b[3], b[4], b[5]);
+        leaves[2 * (int64_t)i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
+        leaves[2 * (int64_t)i + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+    }
+    if (n == 1) return;
+
+    // ---- climb
+    uint32_t l = i, r = i;
+    uint32_t d_left = dl, d_right = dr, d_next = drn;  // delta*(l-1), delta*(r), delta*(r+1)
+    // The augmented keys have at most 64 + 32 bits, so no leaf is deeper than
+    // 96 levels; the bound only guards against a corrupt input order.
+    for (int level = 0; level < 128; ++level) {
+        __threadfence();  // release this thread's node (or leaf) before publishing
+        const bool is_left = d_right < d_left;
+        const uint32_t p = is_left ? r : l - 1;
+        const unsigned long long mine = is_left ? pack(l, d_left, 0) : pack(r, d_right, d_next);
+        if (p >= (uint32_t)ni) {
+            atomicOr(flags, kFlagCorrupt);
+            return;
+        }
+        const unsigned long long other = atomicExch(store + p, mine);
+        if (other == 0ull) return;  // first thread up
+        store[p] = 0ull;            // second thread up: leave the slot empty again
+        __threadfence();            // acquire the sibling's node
+        int sibling;
+        if ((uint32_t)other >= (uint32_t)n) {
+            atomicOr(flags, kFlagCorrupt);
+            return;
+        }
+        if (is_left) {
+            r = (uint32_t)other;
+            d_right = (uint32_t)(other >> 32) & 0xffu;
+            d_next = (uint32_t)(other >> 40) & 0xffu;
+            sibling = (p + 1 == r) ? ni + (int)p + 1 : (int)p + 1;
+        } else {
+            l = (uint32_t)other;
+            d_left = (uint32_t)(other >> 32) & 0xffu;
+            sibling = (l == p) ? ni + (int)p : (int)p;
+        }
+        float3 slo, shi;
+        load_node_box<kKind>(inodes, leaves, ni, sibling, slo, shi);
+        lo = make_float3(min_ordered(lo.x, slo.x), min_ordered(lo.y, slo.y), min_ordered(lo.z, slo.z));
+        hi = make_float3(max_ordered(hi.x, shi.x), max_ordered(hi.y, shi.y), max_ordered(hi.z, shi.z));
+
+        const int q = d_right < d_left ? (int)r : (int)l;  // Karras index of the parent
+        const int left_child = (l == p) ? ni + (int)p : (int)p;
+        const int skip = (r == (uint32_t)(n - 1)) ? kSentinel
+                                                 : (d_right < d_next ? ni + (int)r + 1 : (int)r + 1);
+        inodes[2 * (int64_t)q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
+        inodes[2 * (int64_t)q + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
+        if (q == 0) return;  // the root
+    }
+    atomicOr(flags, kFlagCorrupt);
+}
+
+}  // namespace
+
+void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
+                      int64_t n, int kind, float4 *inodes, float4 *leaves,
+                      unsigned long long *store, uint32_t *flags, cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+    if (kind == LBVH_PRIM_POINTS)
+        construct_kernel<LBVH_PRIM_POINTS><<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims,
+                                                                       (int)n, inodes, leaves, store, flags);
+    else
+        construct_kernel<LBVH_PRIM_BOXES><<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims,
+                                                                      (int)n, inodes, leaves, store, flags);
+    count_launches(1);
+}
+
+}  // namespace lbvh

@@ -1,0 +1,144 @@
+// lbvh_internal.cuh -- declarations shared by the CUDA translation units of
+// the library (kernels + C ABI). Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lbvh.h"
+
+namespace lbvh {
+
+// ---------------------------------------------------------------- status bits
+// Latched on the device during a build or query; read back with the control
+// block and mapped to an lbvh_status on the host.
+enum : uint32_t {
+    kFlagNonfinite = 1u << 0,
+    kFlagTimeout = 1u << 1,
+    kFlagCorrupt = 1u << 2,
+};
+
+// One small device-resident block per tree: status flags, the query's hit
+// total, and the ticket counters of the sort passes and the bounds reduction.
+// Ticket counters are reset by the block that takes the last ticket, so they
+// only need zeroing once, when the block is allocated. build_flags is cleared
+// at the start of every build, the query fields at the start of every query.
+struct Control {
+    uint32_t build_flags;          // kFlag* latched by the last build
+    uint32_t bounds_ticket;        // last-block detection of the bounds reduction
+    uint32_t sort_ticket[16];      // tile tickets of each sort pass
+    uint32_t query_flags;          // kFlag* latched by the last query
+    uint32_t overflow_expected;    // queries with more hits than a thread buffers
+    unsigned long long total;      // total hits of the last query
+    uint32_t overflow_filled;      // slots of the overflow list used by the fill pass
+    uint32_t pad[7];
+};
+constexpr int kQueryBufferHits = 32;  // hits a query thread sorts in registers
+
+// ---------------------------------------------------------------- min / max
+// FP32 min / max that order -0.0 below +0.0, so the scene bounds and the
+// boxes do not depend on the order in which values are combined. Inputs are
+// finite (a build with a NaN or infinity is rejected).
+__device__ __forceinline__ float min_ordered(float a, float b) {
+    return (a < b || (a == b && __float_as_int(a) < 0)) ? a : b;
+}
+__device__ __forceinline__ float max_ordered(float a, float b) {
+    return (a > b || (a == b && __float_as_int(a) >= 0)) ? a : b;
+}
+
+// ---------------------------------------------------------------- node layout
+// Internal node k: two float4 = {lo.x, lo.y, lo.z, left}, {hi.x, hi.y, hi.z,
+// skip}; left/skip are canonical ids stored as int bits.
+// Leaf k (points): one float4 = {x, y, z, skip}.
+// Leaf k (boxes):  two float4 = {lo.xyz, skip}, {hi.xyz, 0}.
+// Canonical ids: internal k -> k, leaf k -> (n-1)+k, sentinel -> -1.
+constexpr int kSentinel = -1;
+
+// ---------------------------------------------------------------- radix sort
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kMaxPasses = 8;
+
+inline int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+inline int sort_passes(int key_bits) { return (key_bits + kRadixBits - 1) / kRadixBits; }
+
+struct SortScratch {
+    uint32_t *hist;          // kMaxPasses * kRadix global digit counts
+    uint32_t *lookback;      // 2 regions of tiles * kRadix words
+    int64_t lookback_words;  // words per region
+};
+
+// Global digit histograms of all passes (used by the stand-alone sort; the
+// build computes them inside the Morton encoder). `hist` must be zero.
+void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_t *hist,
+                            cudaStream_t s);
+
+// Sorts (keys, vals) by the low `passes * 8` bits. keys_a/vals_a hold the
+// input (with `iota` the payload is the index and vals_a's contents are
+// ignored; it is still used as a ping-pong buffer); keys_b/vals_b are the
+// second buffers. Returns true if the result ended in the *_b buffers. hist
+// must already hold the global digit counts. Region 0 of the look-back is
+// cleared here with a memset.
+// pass_events (nullable): an event pair per pass, recorded around its kernel.
+bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
+                  uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
+                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr);
+
+// ---------------------------------------------------------------- Morton
+// bounds: float[6] out; partials: float[blocks * 8]; codes: uint64[n];
+// hist: kMaxPasses * kRadix (accumulated; must be zero beforehand).
+int bounds_blocks(int64_t n);
+void launch_bounds(const float *prims, int64_t n, int kind, float *partials, float *bounds,
+                   Control *ctl, cudaStream_t s);
+void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
+                   uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
+
+// ---------------------------------------------------------------- construct
+// Algorithm 4 with boxes: writes inodes (2(n-1) float4), leaves, and uses
+// `store` (n-1 words, all zero on entry; left all zero on exit).
+// flags: kFlagCorrupt is latched if the input is not a sorted permutation.
+void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
+                      int64_t n, int kind, float4 *inodes, float4 *leaves,
+                      unsigned long long *store, uint32_t *flags, cudaStream_t s);
+
+// ---------------------------------------------------------------- query
+struct TreeView {
+    const float4 *inodes;
+    const float4 *leaves;
+    const uint32_t *perm;
+    int64_t n;
+    int kind;
+};
+struct QueryArgs {
+    const float *queries;
+    int64_t nq;
+    int qkind;
+    const float *radii;  // null: `radius` for every query
+    float radius;
+};
+// counts[q] = number of hits of query q (Algorithm 1 walk).
+void launch_query_count(const TreeView &t, const QueryArgs &q, uint32_t *counts, Control *ctl,
+                        cudaStream_t s);
+// offsets[0..nq] = exclusive scan of counts (offsets[nq] = total); also sets
+// ctl->total and ctl->overflow_expected (queries with > kQueryBufferHits).
+int64_t scan_tile_count(int64_t nq);
+void launch_exclusive_scan(const uint32_t *counts, int64_t nq, int64_t *offsets,
+                           int64_t *tile_sums, Control *ctl, cudaStream_t s);
+// Writes each query's hits (primitive ids) at offsets[q]; lists sorted in
+// registers when they fit, else appended to overflow_list for the fix-up sort.
+void launch_query_fill(const TreeView &t, const QueryArgs &q, const int64_t *offsets,
+                       uint32_t *hits, uint32_t *overflow_list, Control *ctl, cudaStream_t s);
+// Sorts the hit lists of the `count` queries in overflow_list, one CTA each.
+void launch_sort_overflow(const int64_t *offsets, uint32_t *hits, const uint32_t *overflow_list,
+                          uint32_t count, cudaStream_t s);
+
+int device_sm_count();
+
+// Adds k to the process-wide count of kernels launched by this library.
+void count_launches(int k);
+
+}  // namespace lbvh

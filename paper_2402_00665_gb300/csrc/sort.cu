@@ -1,0 +1,270 @@
+// sort.cu -- stable LSD radix sort of 64-bit keys with 32-bit payloads
+// (Sec. 3.1, Karras step 2: sort the Morton codes; the payload is the
+// primitive index, so equal codes keep index order).
+//
+// One kernel launch per 8-bit digit ("onesweep"): the global digit counts of
+// every pass are known up front (from the Morton encoder, or from
+// digit_histogram_kernel), so each pass reads and writes the data once.
+// Per pass, each CTA takes a tile of 4096 keys by ticket (so every tile it may
+// wait on is already running), ranks the keys by digit inside the tile with
+// warp match/ballot counting, publishes its per-digit counts, resolves the
+// exclusive prefix of its digits over all earlier tiles by decoupled look-back
+// with a bounded spin, stages the tile in shared memory in digit order and
+// writes it out so that consecutive threads write consecutive addresses.
+//
+// Look-back words: bits 31:30 = state (0 none, 1 aggregate, 2 inclusive
+// prefix), bits 29:0 = count. Two regions alternate between passes; every
+// tile clears its word block in the other region for the next pass.
+#include "lbvh_internal.cuh"
+
+namespace lbvh {
+
+namespace {
+
+constexpr int kWarps = kSortThreads / 32;
+constexpr uint32_t kStateAgg = 1u << 30;
+constexpr uint32_t kStatePrefix = 2u << 30;
+constexpr uint32_t kStateMask = 3u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1u;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over the 256 threads of the block.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    __syncthreads();
+    return before + x - v;
+}
+
+struct SortSmem {
+    uint32_t warp_hist[kWarps][kRadix];  // per-warp digit counts, then per-warp offsets
+    int32_t out_base[kRadix];            // global position of the digit's first staged key, minus its tile start
+    uint32_t tile_start[kRadix];         // first staged slot of each digit
+    uint32_t scan[kWarps];
+    uint32_t tile;
+    uint64_t keys[kSortTile];
+    uint32_t vals[kSortTile];
+};
+
+template <bool kIota>
+__global__ void __launch_bounds__(kSortThreads)
+    onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
+                    int shift, const uint32_t *__restrict__ pass_hist, uint32_t *lookback,
+                    uint32_t *lookback_next, uint32_t *ticket, int64_t tiles,
+                    uint32_t *flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    if (threadIdx.x == 0) {
+        const uint32_t t = atomicAdd(ticket, 1u);
+        if (t == tiles - 1) *ticket = 0;  // last ticket handed out: reset for the next pass
+        sm.tile = t;
+    }
+    for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) (&sm.warp_hist[0][0])[k] = 0;
+    __syncthreads();
+    const int64_t tile = sm.tile;
+    const int64_t tile_base = tile * kSortTile;
+    const int64_t valid = min((int64_t)kSortTile, n - tile_base);
+
+    // ---- load: warp w owns keys [w*512, w*512+512) of the tile, round j lane l
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
+    uint32_t rank[kSortItems];
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int local = warp * (kSortItems * 32) + j * 32 + lane;
+        const int64_t g = tile_base + local;
+        if (local < valid) {
+            key[j] = keys_in[g];
+            val[j] = kIota ? (uint32_t)g : vals_in[g];
+        } else {
+            key[j] = ~0ull;  // ranks after every real key of digit 0xff
+            val[j] = 0;
+        }
+    }
+
+    // ---- rank inside the warp: peers with the same digit, in (round, lane) order
+    const uint32_t below = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t d = (uint32_t)(key[j] >> shift) & (kRadix - 1);
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = __popc(peers & below);
+        const uint32_t base = sm.warp_hist[warp][d];
+        __syncwarp();
+        if (before == 0) sm.warp_hist[warp][d] = base + __popc(peers);
+        __syncwarp();
+        rank[j] = base + before;
+    }
+    __syncthreads();
+
+    // ---- per digit: counts over warps, per-warp offsets, tile count
+    const int d = threadIdx.x;  // kSortThreads == kRadix
+    uint32_t count = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = sm.warp_hist[w][d];
+        sm.warp_hist[w][d] = count;
+        count += c;
+    }
+    uint32_t *my_word = lookback + tile * kRadix + d;
+    st_relaxed(my_word, (tile == 0 ? kStatePrefix : kStateAgg) | count);
+
+    const uint32_t global_base = block_exclusive_scan(pass_hist[d], sm.scan);
+    const uint32_t start = block_exclusive_scan(count, sm.scan);
+    sm.tile_start[d] = start;
+
+    // ---- decoupled look-back over earlier tiles for digit d
+    uint32_t exclusive = 0;
+    if (tile > 0) {
+        int64_t t = tile - 1;
+        while (true) {
+            const uint32_t *w = lookback + t * kRadix + d;
+            uint32_t v = ld_relaxed(w);
+            uint32_t spins = 0;
+            while ((v & kStateMask) == 0) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(flags, kFlagTimeout);
+                    v = kStatePrefix;  // give up: results are flagged invalid
+                    break;
+                }
+                v = ld_relaxed(w);
+            }
+            exclusive += v & kCountMask;
+            if ((v & kStateMask) == kStatePrefix || t == 0) break;
+            --t;
+        }
+        st_relaxed(my_word, kStatePrefix | (exclusive + count));
+    }
+    lookback_next[tile * kRadix + d] = 0;  // the next pass's region
+    sm.out_base[d] = (int32_t)(global_base + exclusive) - (int32_t)start;
+    __syncthreads();
+
+    // ---- stage in digit order
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const uint32_t dj = (uint32_t)(key[j] >> shift) & (kRadix - 1);
+        const uint32_t slot = sm.tile_start[dj] + sm.warp_hist[warp][dj] + rank[j];
+        sm.keys[slot] = key[j];
+        sm.vals[slot] = val[j];
+    }
+    __syncthreads();
+
+    // ---- write out: slot s goes to out_base[digit] + s
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const int s = j * kSortThreads + threadIdx.x;
+        if (s < valid) {
+            const uint64_t k = sm.keys[s];
+            const uint32_t dj = (uint32_t)(k >> shift) & (kRadix - 1);
+            const int64_t pos = (int64_t)sm.out_base[dj] + s;
+            if (pos < 0 || pos >= n) {  // only after a timed-out look-back
+                atomicOr(flags, kFlagCorrupt);
+                continue;
+            }
+            keys_out[pos] = k;
+            vals_out[pos] = sm.vals[s];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    digit_histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes,
+                           uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_hist[kMaxPasses * kRadix];
+    for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) s_hist[k] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint64_t c = keys[i];
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&s_hist[p * kRadix + (uint32_t)((c >> (kRadixBits * p)) & (kRadix - 1))], 1u);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) {
+        const uint32_t v = s_hist[k];
+        if (v) atomicAdd(&hist[k], v);
+    }
+}
+
+}  // namespace
+
+void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_t *hist,
+                            cudaStream_t s) {
+    if (n <= 0) return;
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    digit_histogram_kernel<<<(int)blocks, 256, 0, s>>>(keys, n, passes, hist);
+    count_launches(1);
+}
+
+bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
+                  uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
+                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2]) {
+    if (n <= 0 || passes <= 0) return false;
+    const int64_t tiles = sort_tiles(n);
+    const size_t smem = sizeof(SortSmem);
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        configured = true;
+    }
+    cudaMemsetAsync(scratch.lookback, 0, (size_t)tiles * kRadix * sizeof(uint32_t), s);
+    uint64_t *kin = keys_a, *kout = keys_b;
+    uint32_t *vin = vals_a, *vout = vals_b;
+    for (int p = 0; p < passes; ++p) {
+        uint32_t *cur = scratch.lookback + (p & 1) * scratch.lookback_words;
+        uint32_t *nxt = scratch.lookback + ((p + 1) & 1) * scratch.lookback_words;
+        const uint32_t *hist = scratch.hist + p * kRadix;
+        if (pass_events) cudaEventRecord(pass_events[p][0], s);
+        if (p == 0 && iota)
+            onesweep_kernel<true><<<(unsigned)tiles, kSortThreads, smem, s>>>(
+                kin, nullptr, kout, vout, n, kRadixBits * p, hist, cur, nxt, &ctl->sort_ticket[p],
+                tiles, &ctl->build_flags);
+        else
+            onesweep_kernel<false><<<(unsigned)tiles, kSortThreads, smem, s>>>(
+                kin, vin, kout, vout, n, kRadixBits * p, hist, cur, nxt, &ctl->sort_ticket[p],
+                tiles, &ctl->build_flags);
+        if (pass_events) cudaEventRecord(pass_events[p][1], s);
+        count_launches(1);
+        uint64_t *tk = kin;
+        kin = kout;
+        kout = tk;
+        uint32_t *tv = vin;
+        vin = vout;
+        vout = tv;
+    }
+    return (passes & 1) != 0;
+}
+
+}  // namespace lbvh

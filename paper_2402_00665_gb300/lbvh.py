@@ -1,0 +1,285 @@
+"""Python binding of the C ABI in ``include/lbvh.h`` (ctypes).
+
+Argument marshalling only: every step of the build and the query runs in the
+CUDA kernels of ``liblbvh_gb300.so``. PyTorch supplies device memory and the
+current stream. There is no CPU fallback: if the library has not been built
+(``__graft_entry__.build()`` or ``python -m paper_2402_00665_gb300._build``)
+or no GPU is present, the calls raise.
+
+The names follow the C functions: ``Tree.build`` = ``lbvh_build``,
+``Tree.query`` = ``lbvh_query_into`` and so on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+POINTS, BOXES = 0, 1
+SPHERE, BOX = 0, 1
+MAX_PRIMS = (1 << 30) - 1
+STAGE_COUNT = 16
+
+STATUS = {0: "LBVH_OK", 1: "LBVH_ERR_INVALID", 2: "LBVH_ERR_NONFINITE", 3: "LBVH_ERR_OOM",
+          4: "LBVH_ERR_CUDA", 5: "LBVH_ERR_TIMEOUT", 6: "LBVH_ERR_CORRUPT", 7: "LBVH_ERR_CAPACITY"}
+OK, ERR_INVALID, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CORRUPT, ERR_CAPACITY = range(8)
+
+# every function declared in include/lbvh.h, with its ctypes signature
+_P = ctypes.c_void_p
+_I64, _U64, _I32, _F32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_float
+SIGNATURES = {
+    "lbvh_tree_create": (_I32, [_P]),
+    "lbvh_tree_destroy": (None, [_P]),
+    "lbvh_build": (_I32, [_P, _P, _I64, _I32, _I32, _P]),
+    "lbvh_build_from_sorted": (_I32, [_P, _P, _P, _P, _I64, _I32, _P]),
+    "lbvh_tree_status": (_I32, [_P]),
+    "lbvh_tree_size": (_I32, [_P, _P]),
+    "lbvh_tree_bytes": (_I32, [_P, _P]),
+    "lbvh_tree_export": (_I32, [_P] * 9),
+    "lbvh_query_into": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _U64, _P, _P]),
+    "lbvh_query": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _P, _P]),
+    "lbvh_free": (None, [_P]),
+    "lbvh_morton_codes": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
+    "lbvh_sort_pairs": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
+    "lbvh_tree_stage_times": (_I32, [_P, _P]),
+    "lbvh_stage_name": (ctypes.c_char_p, [_I32]),
+    "lbvh_kernel_launches": (_U64, []),
+    "lbvh_status_str": (ctypes.c_char_p, [_I32]),
+    "lbvh_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbvhError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if status == ERR_CUDA and _lib is not None:
+            msg += f" ({_lib.lbvh_last_cuda_error().decode()})"
+        super().__init__(msg)
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (it must have been built); raises if missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"CUDA library not built ({path} missing); run __graft_entry__.build() first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise LbvhError(status, where)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the LBVH library runs on the GPU only")
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, width=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.ascontiguousarray(t))
+    t = t.to(device="cuda", dtype=dtype).contiguous()
+    if width is not None:
+        t = t.reshape(-1, width)
+    return t
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else ctypes.c_void_p(0)
+
+
+class Tree:
+    """A device-resident LBVH (handle of ``lbvh_tree_t``)."""
+
+    def __init__(self):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.lbvh_tree_create(ctypes.byref(h)), "lbvh_tree_create")
+        self._h = h
+        self._keep = None
+        self.kind = POINTS
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lbvh_tree_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def build(self, prims, kind: int = POINTS, morton_bits: int = 30, stream=None) -> "Tree":
+        torch = _torch()
+        p = _dev(prims, torch.float32, 3 if kind == POINTS else 6)
+        _check(self._lib.lbvh_build(self._h, _ptr(p), p.shape[0], kind, morton_bits, _stream(stream)),
+               "lbvh_build")
+        self._keep = p  # the kernels read it asynchronously
+        self.kind = kind
+        return self
+
+    def build_from_sorted(self, sorted_codes, perm, prims, kind: int = POINTS, stream=None) -> "Tree":
+        torch = _torch()
+        c = _dev(np.asarray(sorted_codes, np.uint64).view(np.int64), torch.int64)
+        pm = _dev(np.asarray(perm, np.uint32).view(np.int32), torch.int32)
+        p = _dev(prims, torch.float32, 3 if kind == POINTS else 6)
+        _check(self._lib.lbvh_build_from_sorted(self._h, _ptr(c), _ptr(pm), _ptr(p), c.shape[0], kind,
+                                                _stream(stream)), "lbvh_build_from_sorted")
+        self._keep = (c, pm, p)
+        self.kind = kind
+        return self
+
+    def status(self) -> int:
+        return self._lib.lbvh_tree_status(self._h)
+
+    def check(self):
+        _check(self.status(), "lbvh_tree_status")
+
+    def size(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.lbvh_tree_size(self._h, ctypes.byref(n)), "lbvh_tree_size")
+        return n.value
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_uint64()
+        _check(self._lib.lbvh_tree_bytes(self._h, ctypes.byref(b)), "lbvh_tree_bytes")
+        return b.value
+
+    def set_profiling(self, on: bool = True):
+        _check(self._lib.lbvh_tree_set_profiling(self._h, int(bool(on))), "lbvh_tree_set_profiling")
+
+    def stage_times(self) -> dict:
+        """{stage name: device ms} of the last build and query (timed stages only)."""
+        ms = (ctypes.c_float * STAGE_COUNT)()
+        _check(self._lib.lbvh_tree_stage_times(self._h, ms), "lbvh_tree_stage_times")
+        out = {}
+        for k in range(STAGE_COUNT):
+            if ms[k] == ms[k]:  # not NaN
+                out[self._lib.lbvh_stage_name(k).decode()] = float(ms[k])
+        return out
+
+    def export(self) -> dict:
+        """Canonical arrays of the last build, copied to host numpy arrays."""
+        n = self.size()
+        ni = max(n - 1, 0)
+        out = {
+            "n": n,
+            "perm": np.zeros(n, np.uint32), "sorted": np.zeros(n, np.uint64),
+            "left": np.zeros(ni, np.int32), "skip_internal": np.zeros(ni, np.int32),
+            "skip_leaf": np.zeros(n, np.int32), "internal_box": np.zeros((ni, 6), np.float32),
+            "leaf_box": np.zeros((n, 6), np.float32), "bounds": np.zeros(6, np.float32),
+        }
+        a = [ctypes.c_void_p(out[k].ctypes.data) for k in
+             ("perm", "sorted", "left", "skip_internal", "skip_leaf", "internal_box", "leaf_box", "bounds")]
+        _check(self._lib.lbvh_tree_export(self._h, *a), "lbvh_tree_export")
+        return out
+
+    def query_into(self, queries, qkind, offsets, hits, radius: float = 0.0, radii=None, stream=None):
+        """lbvh_query_into with caller tensors; returns (status, total)."""
+        torch = _torch()
+        q = _dev(queries, torch.float32, 3 if qkind == SPHERE else 6)
+        r = None if radii is None else _dev(radii, torch.float32).reshape(-1)
+        total = ctypes.c_uint64()
+        cap = 0 if hits is None else hits.numel()
+        st = self._lib.lbvh_query_into(self._h, _ptr(q), q.shape[0], qkind, _ptr(r), float(radius),
+                                       _ptr(offsets), _ptr(hits), cap, ctypes.byref(total),
+                                       _stream(stream))
+        return st, total.value
+
+    def query(self, queries, qkind: int = SPHERE, radius: float = 0.0, radii=None, capacity=None,
+              stream=None):
+        """Stackless range query (Algorithm 1): returns CSR (offsets int64[nq+1], hits int32 view of uint32)."""
+        torch = _torch()
+        q = _dev(queries, torch.float32, 3 if qkind == SPHERE else 6)
+        nq = q.shape[0]
+        offsets = torch.empty(nq + 1, dtype=torch.int64, device="cuda")
+        cap = int(capacity) if capacity is not None else max(16 * nq, 1)
+        hits = torch.empty(cap, dtype=torch.int32, device="cuda")
+        st, total = self.query_into(q, qkind, offsets, hits, radius, radii, stream)
+        if st == ERR_CAPACITY:
+            hits = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+            st, total = self.query_into(q, qkind, offsets, hits, radius, radii, stream)
+        _check(st, "lbvh_query_into")
+        return offsets, hits[:total]
+
+
+def morton_codes(prims, kind: int = POINTS, morton_bits: int = 30, stream=None):
+    """lbvh_morton_codes: (codes as int64 tensor holding the uint64 bits, bounds float[6])."""
+    lib = load()
+    torch = _torch()
+    p = _dev(prims, torch.float32, 3 if kind == POINTS else 6)
+    n = p.shape[0]
+    codes = torch.empty(n, dtype=torch.int64, device="cuda")
+    bounds = torch.empty(6, dtype=torch.float32, device="cuda")
+    _check(lib.lbvh_morton_codes(_ptr(p), n, kind, morton_bits, _ptr(codes), _ptr(bounds), _stream(stream)),
+           "lbvh_morton_codes")
+    return codes, bounds
+
+
+def sort_pairs(keys, vals=None, key_bits: int = 64, stream=None):
+    """lbvh_sort_pairs on int64-held uint64 keys; vals None = primitive index."""
+    lib = load()
+    torch = _torch()
+    k = keys if isinstance(keys, torch.Tensor) else torch.as_tensor(np.asarray(keys, np.uint64).view(np.int64))
+    k = k.to(device="cuda", dtype=torch.int64).contiguous()
+    v = None
+    if vals is not None:
+        v = vals if isinstance(vals, torch.Tensor) else torch.as_tensor(np.asarray(vals, np.uint32).view(np.int32))
+        v = v.to(device="cuda", dtype=torch.int32).contiguous()
+    n = k.numel()
+    ko = torch.empty_like(k)
+    vo = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(lib.lbvh_sort_pairs(_ptr(k), _ptr(v), n, key_bits, _ptr(ko), _ptr(vo), _stream(stream)),
+           "lbvh_sort_pairs")
+    return ko, vo
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().lbvh_kernel_launches())
+
+
+def to_u64(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def to_u32(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint32)

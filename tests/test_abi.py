@@ -1,0 +1,90 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+function that ``include/lbvh.h`` declares; the binding refuses to run without a
+GPU (no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2402_00665_gb300 import _build, lbvh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(lbvh_\w+)\s*\(", text, flags=re.M):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbvh_build", "lbvh_query", "lbvh_query_into", "lbvh_tree_export",
+                     "lbvh_tree_bytes", "lbvh_free", "lbvh_tree_destroy", "lbvh_status_str"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    assert sorted(lbvh.SIGNATURES) == declared_functions()
+
+
+def test_library_is_built_for_sm_103a_only():
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings_without_gpu(lib_path):
+    lib = lbvh.load()
+    assert lib.lbvh_status_str(0) == b"LBVH_OK"
+    assert lib.lbvh_status_str(7) == b"LBVH_ERR_CAPACITY"
+    assert lib.lbvh_status_str(99) == b"LBVH_ERR_UNKNOWN"
+
+
+def test_invalid_arguments_rejected_before_any_device_work(lib_path):
+    lib = lbvh.load()
+    assert lib.lbvh_tree_create(None) == lbvh.ERR_INVALID
+    h = ctypes.c_void_p()
+    assert lib.lbvh_tree_create(ctypes.byref(h)) == lbvh.OK
+    try:
+        assert lib.lbvh_build(h, None, 10, 0, 30, None) == lbvh.ERR_INVALID  # null prims
+        assert lib.lbvh_build(h, None, -1, 0, 30, None) == lbvh.ERR_INVALID
+        assert lib.lbvh_build(h, None, lbvh.MAX_PRIMS + 1, 0, 30, None) == lbvh.ERR_INVALID
+        dummy = ctypes.c_void_p(16)
+        for bits in (0, 2, 31, 64):
+            assert lib.lbvh_build(h, dummy, 10, 0, bits, None) == lbvh.ERR_INVALID
+        assert lib.lbvh_build(h, dummy, 10, 7, 30, None) == lbvh.ERR_INVALID  # kind
+        # querying a tree that was never built
+        off = ctypes.c_void_p(16)
+        total = ctypes.c_uint64()
+        assert lib.lbvh_query_into(h, dummy, 1, 0, None, 1.0, off, None, 0, ctypes.byref(total),
+                                   None) == lbvh.ERR_INVALID
+        assert lib.lbvh_tree_status(h) == lbvh.ERR_INVALID
+    finally:
+        lib.lbvh_tree_destroy(h)
+
+
+def test_binding_fails_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError, match="no CUDA device"):
+        lbvh.Tree().build([[0.0, 0.0, 0.0]])
