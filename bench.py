@@ -52,18 +52,19 @@ UNIT = "Mprims/s"
 #   sort pass   read key + payload, write key + payload      12 + 12 (pass 0: no payload read)
 #   construct   key 8 + perm 4 + point 12 read, leaf 16 and internal node 32
 #               written, store word 8, sibling box 24 re-read
-#   query count query 12 read, count 4 written, tree read once (48 B per leaf)
-#   query fill  query 12 + offset 8 read, 4 per hit written, tree once
+#   query walk  query 12 read, count 4 written, 4 per hit kept, tree read once (48 B/leaf)
+#   query copy  count/start/offset read per query, 4 per hit read and 4 written
 ALG_BYTES = {
     "bounds": lambda n, nq, hits: 12 * n,
     "encode": lambda n, nq, hits: 20 * n,
     "sort_pass0": lambda n, nq, hits: 20 * n,
     **{f"sort_pass{k}": (lambda n, nq, hits: 24 * n) for k in range(1, 8)},
     "construct": lambda n, nq, hits: 104 * n,
-    "query_count": lambda n, nq, hits: 16 * nq + 48 * n,
+    "query_walk": lambda n, nq, hits: 16 * nq + 4 * hits + 48 * n,
+    "query_order": lambda n, nq, hits: 12 * nq + 8 * nq + 4 * 24 * nq,
     "query_scan": lambda n, nq, hits: 4 * nq + 8 * (nq + 1),
-    "query_fill": lambda n, nq, hits: 20 * nq + 4 * hits + 48 * n,
-    "query_fixup": lambda n, nq, hits: 0,
+    "query_copy": lambda n, nq, hits: 16 * nq + 8 * hits,
+    "query_overflow": lambda n, nq, hits: 0,
 }
 
 WORKLOADS = {
@@ -271,6 +272,10 @@ def run_gpu(args, world, rank, local):
     desc, n, bits, pts_host, radius = make_inputs(args.workload, args.seed + rank)
     nq = n
     pts = torch.from_numpy(pts_host).to(dev)
+    # the queries are the points, held in their own buffer: the general query
+    # path (query centres Morton-encoded and sorted) runs, not the shortcut for
+    # a tree queried with its own primitive buffer
+    qpts = pts.clone()
     stream = torch.cuda.current_stream(dev)
 
     tree = lbvh.Tree()
@@ -278,13 +283,13 @@ def run_gpu(args, world, rank, local):
     offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     # size the hit buffer once (a production caller does the same)
     tree.build(pts, lbvh.POINTS, bits)
-    st, total = tree.query_into(pts, lbvh.SPHERE, offsets, None, radius=float(radius))
+    st, total = tree.query_into(qpts, lbvh.SPHERE, offsets, None, radius=float(radius))
     assert st in (lbvh.OK, lbvh.ERR_CAPACITY), st
     hits = torch.empty(max(int(total * 1.05) + 1024, 1), dtype=torch.int32, device=dev)
 
     def step():
         tree.build(pts, lbvh.POINTS, bits)
-        s, tot = tree.query_into(pts, lbvh.SPHERE, offsets, hits, radius=float(radius))
+        s, tot = tree.query_into(qpts, lbvh.SPHERE, offsets, hits, radius=float(radius))
         if s != lbvh.OK:
             raise lbvh.LbvhError(s, "lbvh_query_into")
         return tot
@@ -342,11 +347,13 @@ def run_gpu(args, world, rank, local):
         host_off = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
         host_hits = torch.empty(hits.numel(), dtype=torch.int32).pin_memory()
         dpts = torch.empty_like(pts)
+        dq = torch.empty_like(pts)
 
         def e2e_step():
             dpts.copy_(host_pts, non_blocking=True)
+            dq.copy_(host_pts, non_blocking=True)
             tree.build(dpts, lbvh.POINTS, bits)
-            s, tot = tree.query_into(dpts, lbvh.SPHERE, offsets, hits, radius=float(radius))
+            s, tot = tree.query_into(dq, lbvh.SPHERE, offsets, hits, radius=float(radius))
             if s != lbvh.OK:
                 raise lbvh.LbvhError(s, "lbvh_query_into")
             host_off.copy_(offsets, non_blocking=True)
@@ -365,9 +372,10 @@ def run_gpu(args, world, rank, local):
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world, dev) / args.steps
         e2e = {"value": n * world / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
-               "h2d_bytes_per_step": int(pts.numel() * 4),
+               "h2d_bytes_per_step": int(2 * pts.numel() * 4),
                "d2h_bytes_per_step": int((nq + 1) * 8 + tot * 4),
-               "note": "pinned host points -> device, build, query, CSR offsets + hits -> pinned host"}
+               "note": "pinned host points and query centres -> device, build, query, "
+                       "CSR offsets + hits -> pinned host"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -185,10 +185,11 @@ enum {
     LBVH_STAGE_ENCODE = 1,     /* Morton codes + sort digit histograms */
     LBVH_STAGE_SORT0 = 2,      /* radix-sort pass k is LBVH_STAGE_SORT0 + k, k < 8 */
     LBVH_STAGE_CONSTRUCT = 10, /* Algorithm 4: nodes, boxes, skips */
-    LBVH_STAGE_QCOUNT = 11,    /* Algorithm 1, counting walk */
+    LBVH_STAGE_QCOUNT = 11,    /* Algorithm 1 walk: counts, short sorted hit lists */
     LBVH_STAGE_QSCAN = 12,     /* exclusive scan of the counts */
-    LBVH_STAGE_QFILL = 13,     /* Algorithm 1, filling walk + per-query sort */
-    LBVH_STAGE_QFIXUP = 14,    /* sort of hit lists longer than a thread buffers */
+    LBVH_STAGE_QFILL = 13,     /* short lists copied to their CSR positions */
+    LBVH_STAGE_QFIXUP = 14,    /* second walk + sort for lists longer than 32 */
+    LBVH_STAGE_QORDER = 15,    /* Morton order of the query centres (encode + sort) */
     LBVH_STAGE_COUNT = 16
 };
 

@@ -120,8 +120,10 @@ struct lbvh_tree_s {
     bool sorted_in_b = false;
     bool store_dirty = false;  // a failed build may have left store words set
     DevBuf keys[2], vals[2];
-    DevBuf inodes, leaves, store, lookback, hist, partials, bounds, ctl;
-    DevBuf counts, tile_sums, overflow;
+    DevBuf node_a, node_b, store, lookback, hist, partials, bounds, ctl;
+    DevBuf counts, tile_sums, overflow, count_sorted, slots;
+    DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
+    const float *prims_ptr = nullptr;      // the last build's input (self-queries)
     lbvh::Control *h_ctl = nullptr;  // pinned mirror of the control block
     Profiler prof;
 
@@ -129,7 +131,7 @@ struct lbvh_tree_s {
     const uint32_t *perm() const { return vals[sorted_in_b ? 1 : 0].as<uint32_t>(); }
     lbvh::Control *dctl() const { return ctl.as<lbvh::Control>(); }
     lbvh::TreeView view() const {
-        return lbvh::TreeView{inodes.as<float4>(), leaves.as<float4>(), perm(), n, kind};
+        return lbvh::TreeView{node_a.as<float4>(), node_b.as<float4>(), perm(), n, kind};
     }
 };
 
@@ -165,8 +167,8 @@ lbvh_status reserve_tree(lbvh_tree_s *t, int64_t n, int kind, cudaStream_t s) {
         LBVH_CUDA(t->keys[k].ensure(un * 8, s));
         LBVH_CUDA(t->vals[k].ensure(un * 4, s));
     }
-    LBVH_CUDA(t->inodes.ensure(ui * 32, s));
-    LBVH_CUDA(t->leaves.ensure(un * (kind == LBVH_PRIM_POINTS ? 16 : 32), s));
+    LBVH_CUDA(t->node_a.ensure((ui + un) * 16, s));
+    LBVH_CUDA(t->node_b.ensure(node_b_count(n, kind) * 16, s));
     LBVH_CUDA(t->store.ensure(ui * 8, s, true));
     LBVH_CUDA(t->lookback.ensure((size_t)tiles * kRadix * 4 * 2, s));
     LBVH_CUDA(t->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
@@ -198,24 +200,75 @@ lbvh_status read_control(lbvh_tree_t t, cudaStream_t s) {
     return LBVH_OK;
 }
 
-// The query up to the hit count: count walk + scan; synchronises `s`.
-lbvh_status query_count(lbvh_tree_t t, const lbvh::QueryArgs &qa, int64_t *d_offsets,
+constexpr int64_t kOrderMinQueries = 2048;  // below this, walk in input order
+constexpr int kOrderBits = 30;              // Morton bits of the query order
+
+// The order in which threads take the queries: the Morton order of the query
+// centres inside the tree's bounds (encode + radix sort, the build's own
+// kernels). Queries that are the primitives of the last build (same pointer
+// and count) reuse the build's permutation. Order only changes speed, never
+// results.
+lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
+    using namespace lbvh;
+    qa.order = nullptr;
+    if (qa.nq < kOrderMinQueries || t->n == 0) return LBVH_OK;
+    const bool same_points = qa.qkind == LBVH_Q_SPHERE && t->kind == LBVH_PRIM_POINTS;
+    const bool same_boxes = qa.qkind == LBVH_Q_BOX && t->kind == LBVH_PRIM_BOXES;
+    if (qa.queries == t->prims_ptr && qa.nq == t->n && (same_points || same_boxes)) {
+        qa.order = t->perm();
+        return LBVH_OK;
+    }
+    const size_t unq = (size_t)qa.nq;
+    const int passes = sort_passes(kOrderBits);
+    for (int k = 0; k < 2; ++k) {
+        LBVH_CUDA(t->qkeys[k].ensure(unq * 8, s));
+        LBVH_CUDA(t->qvals[k].ensure(unq * 4, s));
+    }
+    LBVH_CUDA(t->qlookback.ensure((size_t)sort_tiles(qa.nq) * kRadix * 4 * 2, s));
+    LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)passes * kRadix * 4, s));
+    const int as_prims = qa.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
+    launch_encode(qa.queries, qa.nq, as_prims, kOrderBits, t->bounds.as<float>(),
+                  t->qkeys[0].as<uint64_t>(), t->hist.as<uint32_t>(), 1, s);
+    LBVH_LAUNCHED();
+    SortScratch scratch{t->hist.as<uint32_t>(), t->qlookback.as<uint32_t>(), sort_tiles(qa.nq) * kRadix};
+    const bool in_b = run_onesweep(t->qkeys[0].as<uint64_t>(), t->qvals[0].as<uint32_t>(), true,
+                                   t->qkeys[1].as<uint64_t>(), t->qvals[1].as<uint32_t>(), qa.nq, passes,
+                                   scratch, t->dctl(), s);
+    LBVH_LAUNCHED();
+    qa.order = t->qvals[in_b ? 1 : 0].as<uint32_t>();
+    return LBVH_OK;
+}
+
+lbvh::QueryScratch query_scratch(lbvh_tree_t t) {
+    return lbvh::QueryScratch{t->counts.as<uint32_t>(), t->count_sorted.as<uint32_t>(),
+                              t->slots.as<uint32_t>(), t->overflow.as<uint32_t>()};
+}
+
+// The query up to the hit count: order, collecting walk, scan; synchronises `s`.
+lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
                         cudaStream_t s, uint64_t *total) {
     using namespace lbvh;
     LBVH_CUDA(cudaStreamWaitEvent(s, t->built, 0));
     const size_t unq = (size_t)qa.nq;
     LBVH_CUDA(t->counts.ensure(unq * 4 + 4, s));
-    LBVH_CUDA(t->tile_sums.ensure((size_t)scan_tile_count(qa.nq) * 8 + 8, s));
+    LBVH_CUDA(t->count_sorted.ensure(unq * 4 + 4, s));
     LBVH_CUDA(t->overflow.ensure(unq * 4 + 4, s));
+    LBVH_CUDA(t->tile_sums.ensure((size_t)scan_tile_count(qa.nq) * 8 + 8, s));
+    LBVH_CUDA(t->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
     Control *c = t->dctl();
     LBVH_CUDA(cudaMemsetAsync(&c->query_flags, 0, offsetof(Control, pad) - offsetof(Control, query_flags), s));
     t->prof.clear(LBVH_STAGE_QCOUNT, LBVH_STAGE_COUNT);
+    t->prof.begin(LBVH_STAGE_QORDER, s);
+    lbvh_status ost = query_order(t, qa, s);
+    if (ost != LBVH_OK) return ost;
+    t->prof.end(LBVH_STAGE_QORDER, s);
+    const QueryScratch qs = query_scratch(t);
     t->prof.begin(LBVH_STAGE_QCOUNT, s);
-    launch_query_count(t->view(), qa, t->counts.as<uint32_t>(), c, s);
+    launch_query_collect(t->view(), qa, qs, c, s);
     t->prof.end(LBVH_STAGE_QCOUNT, s);
     LBVH_LAUNCHED();
     t->prof.begin(LBVH_STAGE_QSCAN, s);
-    launch_exclusive_scan(t->counts.as<uint32_t>(), qa.nq, d_offsets, t->tile_sums.as<int64_t>(), c, s);
+    launch_exclusive_scan(qs.counts, qa.nq, d_offsets, t->tile_sums.as<int64_t>(), c, s);
     t->prof.end(LBVH_STAGE_QSCAN, s);
     LBVH_LAUNCHED();
     lbvh_status st = read_control(t, s);
@@ -230,13 +283,14 @@ lbvh_status query_fill(lbvh_tree_t t, const lbvh::QueryArgs &qa, const int64_t *
                        uint32_t *d_hits, cudaStream_t s) {
     using namespace lbvh;
     if (t->h_ctl->total == 0) return LBVH_OK;
+    const QueryScratch qs = query_scratch(t);
     t->prof.begin(LBVH_STAGE_QFILL, s);
-    launch_query_fill(t->view(), qa, d_offsets, d_hits, t->overflow.as<uint32_t>(), t->dctl(), s);
+    launch_query_copy(qa, qs, d_offsets, d_hits, s);
     t->prof.end(LBVH_STAGE_QFILL, s);
     LBVH_LAUNCHED();
-    if (t->h_ctl->overflow_expected > 0) {
+    if (t->h_ctl->overflow_filled > 0) {
         t->prof.begin(LBVH_STAGE_QFIXUP, s);
-        launch_sort_overflow(d_offsets, d_hits, t->overflow.as<uint32_t>(), t->h_ctl->overflow_expected, s);
+        launch_query_overflow(t->view(), qa, qs, t->h_ctl->overflow_filled, d_offsets, d_hits, s);
         t->prof.end(LBVH_STAGE_QFIXUP, s);
         LBVH_LAUNCHED();
     }
@@ -267,9 +321,11 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
     if (!t) return;
     if (t->has_build) cudaStreamSynchronize(t->stream);
     cudaStream_t s = t->stream;
-    for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->inodes, &t->leaves,
+    for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->node_a, &t->node_b,
                       &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
-                      &t->counts, &t->tile_sums, &t->overflow})
+                      &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
+                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->count_sorted,
+                      &t->slots})
         b->release(s);
     cudaStreamSynchronize(s);
     if (t->h_ctl) cudaFreeHost(t->h_ctl);
@@ -290,6 +346,7 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
     t->n = n;
     t->kind = kind;
     t->bits = morton_bits;
+    t->prims_ptr = d_prims;
     Control *c = t->dctl();
     LBVH_CUDA(cudaMemsetAsync(&c->build_flags, 0, sizeof(uint32_t), s));
     if (t->store_dirty && t->store.bytes) {
@@ -306,7 +363,7 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_ENCODE, s);
         launch_encode(d_prims, n, kind, morton_bits, t->bounds.as<float>(), t->keys[0].as<uint64_t>(),
-                      t->hist.as<uint32_t>(), passes, s);
+                      t->hist.as<uint32_t>(), 1, s);
         t->prof.end(LBVH_STAGE_ENCODE, s);
         LBVH_LAUNCHED();
         SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles(n) * kRadix};
@@ -317,8 +374,8 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
             for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_CONSTRUCT, s);
-        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes.as<float4>(),
-                         t->leaves.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
+        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->node_a.as<float4>(),
+                         t->node_b.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
         t->prof.end(LBVH_STAGE_CONSTRUCT, s);
         LBVH_LAUNCHED();
     }
@@ -338,6 +395,7 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
     t->n = n;
     t->kind = kind;
     t->bits = 0;
+    t->prims_ptr = d_prims;
     t->sorted_in_b = false;
     Control *c = t->dctl();
     LBVH_CUDA(cudaMemsetAsync(&c->build_flags, 0, sizeof(uint32_t), s));
@@ -350,8 +408,8 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
         LBVH_CUDA(cudaMemcpyAsync(t->vals[0].p, d_perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
         launch_bounds(d_prims, n, kind, t->partials.as<float>(), t->bounds.as<float>(), c, s);
         LBVH_LAUNCHED();
-        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes.as<float4>(),
-                         t->leaves.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
+        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->node_a.as<float4>(),
+                         t->node_b.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
         LBVH_LAUNCHED();
     }
     return finish_build(t, s);
@@ -373,9 +431,11 @@ lbvh_status lbvh_tree_size(lbvh_tree_t t, int64_t *n) {
 lbvh_status lbvh_tree_bytes(lbvh_tree_t t, uint64_t *bytes) {
     if (!t || !bytes) return LBVH_ERR_INVALID;
     uint64_t b = 0;
-    for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->inodes, &t->leaves,
+    for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->node_a, &t->node_b,
                             &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
-                            &t->counts, &t->tile_sums, &t->overflow})
+                            &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
+                            &t->qvals[0], &t->qvals[1], &t->qlookback, &t->count_sorted,
+                            &t->slots})
         b += d->bytes;
     *bytes = b;
     return LBVH_OK;
@@ -387,43 +447,37 @@ lbvh_status lbvh_tree_export(lbvh_tree_t t, uint32_t *h_perm, uint64_t *h_sorted
     lbvh_status st = lbvh_tree_status(t);
     if (st != LBVH_OK) return st;
     const int64_t n = t->n, ni = n > 0 ? n - 1 : 0;
-    cudaStream_t s = t->stream;
     if (n == 0) return LBVH_OK;
     if (h_perm) LBVH_CUDA(cudaMemcpy(h_perm, t->perm(), n * 4, cudaMemcpyDeviceToHost));
     if (h_sorted_codes) LBVH_CUDA(cudaMemcpy(h_sorted_codes, t->sorted_codes(), n * 8, cudaMemcpyDeviceToHost));
     if (h_bounds) LBVH_CUDA(cudaMemcpy(h_bounds, t->bounds.p, 24, cudaMemcpyDeviceToHost));
-    if (ni > 0 && (h_left || h_skip_internal || h_internal_box)) {
-        std::vector<float4> nodes((size_t)ni * 2);
-        LBVH_CUDA(cudaMemcpy(nodes.data(), t->inodes.p, ni * 32, cudaMemcpyDeviceToHost));
+    if (h_left || h_skip_internal || h_internal_box || h_skip_leaf || h_leaf_box) {
+        std::vector<float4> a((size_t)(ni + n)), b(lbvh::node_b_count(n, t->kind));
+        LBVH_CUDA(cudaMemcpy(a.data(), t->node_a.p, a.size() * 16, cudaMemcpyDeviceToHost));
+        if (!b.empty()) LBVH_CUDA(cudaMemcpy(b.data(), t->node_b.p, b.size() * 16, cudaMemcpyDeviceToHost));
         for (int64_t k = 0; k < ni; ++k) {
-            const float4 a = nodes[2 * k], b = nodes[2 * k + 1];
             int32_t left, skip;
-            std::memcpy(&left, &a.w, 4);
-            std::memcpy(&skip, &b.w, 4);
+            std::memcpy(&left, &a[k].w, 4);
+            std::memcpy(&skip, &b[k].w, 4);
             if (h_left) h_left[k] = left;
             if (h_skip_internal) h_skip_internal[k] = skip;
             if (h_internal_box) {
-                const float v[6] = {a.x, a.y, a.z, b.x, b.y, b.z};
+                const float v[6] = {a[k].x, a[k].y, a[k].z, b[k].x, b[k].y, b[k].z};
                 std::memcpy(h_internal_box + 6 * k, v, sizeof v);
             }
         }
-    }
-    if (h_skip_leaf || h_leaf_box) {
-        const int per = t->kind == LBVH_PRIM_POINTS ? 1 : 2;
-        std::vector<float4> leaves((size_t)n * per);
-        LBVH_CUDA(cudaMemcpy(leaves.data(), t->leaves.p, n * 16 * per, cudaMemcpyDeviceToHost));
         for (int64_t k = 0; k < n; ++k) {
-            const float4 a = leaves[per * k], b = leaves[per * k + per - 1];
+            const float4 lo = a[ni + k];
+            const float4 hi = t->kind == LBVH_PRIM_POINTS ? lo : b[ni + k];
             int32_t skip;
-            std::memcpy(&skip, &a.w, 4);
+            std::memcpy(&skip, &lo.w, 4);
             if (h_skip_leaf) h_skip_leaf[k] = skip;
             if (h_leaf_box) {
-                const float v[6] = {a.x, a.y, a.z, b.x, b.y, b.z};
+                const float v[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
                 std::memcpy(h_leaf_box + 6 * k, v, sizeof v);
             }
         }
     }
-    (void)s;
     return LBVH_OK;
 }
 
@@ -434,7 +488,7 @@ lbvh_status lbvh_query_into(lbvh_tree_t t, const float *d_queries, int64_t nq, i
     if (st != LBVH_OK) return st;
     if (!d_offsets || !total || (capacity > 0 && !d_hits)) return LBVH_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const lbvh::QueryArgs qa{d_queries, nq, qkind, d_radii, radius};
+    lbvh::QueryArgs qa{d_queries, nq, qkind, d_radii, radius, nullptr};
     st = query_count(t, qa, d_offsets, s, total);
     if (st != LBVH_OK) return st;
     if (*total > capacity) return LBVH_ERR_CAPACITY;
@@ -451,7 +505,7 @@ lbvh_status lbvh_query(lbvh_tree_t t, const float *d_queries, int64_t nq, int qk
     *d_hits = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     LBVH_CUDA(cudaMalloc(reinterpret_cast<void **>(d_offsets), ((size_t)nq + 1) * 8));
-    const lbvh::QueryArgs qa{d_queries, nq, qkind, d_radii, radius};
+    lbvh::QueryArgs qa{d_queries, nq, qkind, d_radii, radius, nullptr};
     st = query_count(t, qa, *d_offsets, s, total);
     if (st == LBVH_OK) {
         cudaError_t e = cudaMalloc(reinterpret_cast<void **>(d_hits), (size_t)(*total > 0 ? *total : 1) * 4);
@@ -528,7 +582,7 @@ lbvh_status lbvh_sort_pairs(const uint64_t *d_keys, const uint32_t *d_vals, int6
     if (e == cudaSuccess && d_vals)
         e = cudaMemcpyAsync(d_vals_out, d_vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) {
-        launch_digit_histogram(d_keys_out, n, passes, hist.as<uint32_t>(), s);
+        launch_digit_histogram(d_keys_out, n, 1, hist.as<uint32_t>(), s);
         SortScratch scratch{hist.as<uint32_t>(), lookback.as<uint32_t>(), tiles * kRadix};
         const bool in_b = run_onesweep(d_keys_out, d_vals_out, d_vals == nullptr, tk.as<uint64_t>(),
                                        tv.as<uint32_t>(), n, passes, scratch, ctl.as<Control>(), s);
@@ -572,8 +626,8 @@ lbvh_status lbvh_tree_stage_times(lbvh_tree_t t, float *ms) {
 const char *lbvh_stage_name(int stage) {
     static const char *names[LBVH_STAGE_COUNT] = {
         "bounds", "encode", "sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3", "sort_pass4",
-        "sort_pass5", "sort_pass6", "sort_pass7", "construct", "query_count", "query_scan",
-        "query_fill", "query_fixup", ""};
+        "sort_pass5", "sort_pass6", "sort_pass7", "construct", "query_walk", "query_scan",
+        "query_copy", "query_overflow", "query_order"};
     return (stage >= 0 && stage < LBVH_STAGE_COUNT) ? names[stage] : "";
 }
 

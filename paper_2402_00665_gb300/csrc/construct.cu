@@ -30,9 +30,14 @@
 //     ever touch store[p], so the one that reads "empty" is the first. The
 //     second writes "empty" back, leaving the scratch clean for the next build
 //     (it is zeroed once, when allocated).
-//   - release/acquire: each thread fences after writing its node and before
-//     the exchange; the second fences after the exchange and reads the
-//     sibling's box through L2 (ld.global.cg).
+//   - release/acquire: the exchange is an acq_rel atomic at device scope, so
+//     a thread's node is visible before its half of the parent is, and the
+//     second thread reads the sibling's box (through L2, ld.global.cg) only
+//     after it has seen that half.
+#include <cuda/atomic>
+
+#include <cstdlib>
+
 #include "lbvh_internal.cuh"
 
 namespace lbvh {
@@ -56,29 +61,38 @@ __device__ __forceinline__ unsigned long long pack(uint32_t end, uint32_t d, uin
 }
 
 template <int kKind>
-__device__ __forceinline__ void load_node_box(const float4 *inodes, const float4 *leaves, int ni,
+__device__ __forceinline__ void load_node_box(const float4 *node_a, const float4 *node_b, int ni,
                                               int id, float3 &lo, float3 &hi) {
-    if (id < ni) {
-        const float4 a = __ldcg(inodes + 2 * (int64_t)id);
-        const float4 b = __ldcg(inodes + 2 * (int64_t)id + 1);
-        lo = make_float3(a.x, a.y, a.z);
-        hi = make_float3(b.x, b.y, b.z);
-    } else if (kKind == LBVH_PRIM_POINTS) {
-        const float4 a = __ldcg(leaves + (id - ni));
-        lo = make_float3(a.x, a.y, a.z);
+    const float4 a = __ldcg(node_a + id);
+    lo = make_float3(a.x, a.y, a.z);
+    if (kKind == LBVH_PRIM_POINTS && id >= ni) {
         hi = lo;
     } else {
-        const float4 a = __ldcg(leaves + 2 * (int64_t)(id - ni));
-        const float4 b = __ldcg(leaves + 2 * (int64_t)(id - ni) + 1);
-        lo = make_float3(a.x, a.y, a.z);
+        const float4 b = __ldcg(node_b + id);
         hi = make_float3(b.x, b.y, b.z);
     }
 }
 
-template <int kKind>
+// The exchange on store[p] publishes this thread's finished node (release)
+// and, for the second thread, makes the sibling's node visible (acquire):
+// either as one acq_rel atomic, or as a relaxed atomic between two fences.
+template <bool kAcqRel>
+__device__ __forceinline__ unsigned long long publish_exchange(unsigned long long *slot,
+                                                               unsigned long long v) {
+    if (kAcqRel) {
+        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*slot);
+        return a.exchange(v, cuda::memory_order_acq_rel);
+    }
+    __threadfence();
+    const unsigned long long old = atomicExch(slot, v);
+    __threadfence();
+    return old;
+}
+
+template <int kKind, bool kAcqRel>
 __global__ void __launch_bounds__(kThreads)
     construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
-                     const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
+                     const float *__restrict__ prims, int n, float4 *node_a, float4 *node_b,
                      unsigned long long *store, uint32_t *flags) {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
@@ -106,13 +120,13 @@ __global__ void __launch_bounds__(kThreads)
         lo = make_float3(prims[3 * (int64_t)p_id], prims[3 * (int64_t)p_id + 1],
                          prims[3 * (int64_t)p_id + 2]);
         hi = lo;
-        leaves[i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
+        node_a[ni + i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
     } else {
         const float *b = prims + 6 * (int64_t)p_id;
         lo = make_float3(b[0], b[1], b[2]);
         hi = make_float3(b[3], b[4], b[5]);
-        leaves[2 * (int64_t)i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
-        leaves[2 * (int64_t)i + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+        node_a[ni + i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
+        node_b[ni + i] = make_float4(hi.x, hi.y, hi.z, 0.0f);
     }
     if (n == 1) return;
 
@@ -122,7 +136,6 @@ __global__ void __launch_bounds__(kThreads)
     // The augmented keys have at most 64 + 32 bits, so no leaf is deeper than
     // 96 levels; the bound only guards against a corrupt input order.
     for (int level = 0; level < 128; ++level) {
-        __threadfence();  // release this thread's node (or leaf) before publishing
         const bool is_left = d_right < d_left;
         const uint32_t p = is_left ? r : l - 1;
         const unsigned long long mine = is_left ? pack(l, d_left, 0) : pack(r, d_right, d_next);
@@ -130,10 +143,9 @@ __global__ void __launch_bounds__(kThreads)
             atomicOr(flags, kFlagCorrupt);
             return;
         }
-        const unsigned long long other = atomicExch(store + p, mine);
+        const unsigned long long other = publish_exchange<kAcqRel>(store + p, mine);
         if (other == 0ull) return;  // first thread up
         store[p] = 0ull;            // second thread up: leave the slot empty again
-        __threadfence();            // acquire the sibling's node
         int sibling;
         if ((uint32_t)other >= (uint32_t)n) {
             atomicOr(flags, kFlagCorrupt);
@@ -150,7 +162,7 @@ __global__ void __launch_bounds__(kThreads)
             sibling = (l == p) ? ni + (int)p : (int)p;
         }
         float3 slo, shi;
-        load_node_box<kKind>(inodes, leaves, ni, sibling, slo, shi);
+        load_node_box<kKind>(node_a, node_b, ni, sibling, slo, shi);
         lo = make_float3(min_ordered(lo.x, slo.x), min_ordered(lo.y, slo.y), min_ordered(lo.z, slo.z));
         hi = make_float3(max_ordered(hi.x, shi.x), max_ordered(hi.y, shi.y), max_ordered(hi.z, shi.z));
 
@@ -158,8 +170,8 @@ __global__ void __launch_bounds__(kThreads)
         const int left_child = (l == p) ? ni + (int)p : (int)p;
         const int skip = (r == (uint32_t)(n - 1)) ? kSentinel
                                                  : (d_right < d_next ? ni + (int)r + 1 : (int)r + 1);
-        inodes[2 * (int64_t)q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
-        inodes[2 * (int64_t)q + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
+        node_a[q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
+        node_b[q] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
         if (q == 0) return;  // the root
     }
     atomicOr(flags, kFlagCorrupt);
@@ -168,16 +180,16 @@ __global__ void __launch_bounds__(kThreads)
 }  // namespace
 
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
-                      int64_t n, int kind, float4 *inodes, float4 *leaves,
+                      int64_t n, int kind, float4 *node_a, float4 *node_b,
                       unsigned long long *store, uint32_t *flags, cudaStream_t s) {
     if (n <= 0) return;
+    // LBVH_CONSTRUCT_FENCES=1 selects the fence form of the exchange (tuning)
+    static const bool fences = getenv("LBVH_CONSTRUCT_FENCES") && atoi(getenv("LBVH_CONSTRUCT_FENCES"));
     const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-    if (kind == LBVH_PRIM_POINTS)
-        construct_kernel<LBVH_PRIM_POINTS><<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims,
-                                                                       (int)n, inodes, leaves, store, flags);
-    else
-        construct_kernel<LBVH_PRIM_BOXES><<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims,
-                                                                      (int)n, inodes, leaves, store, flags);
+    auto k = kind == LBVH_PRIM_POINTS
+                 ? (fences ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_POINTS, true>)
+                 : (fences ? construct_kernel<LBVH_PRIM_BOXES, false> : construct_kernel<LBVH_PRIM_BOXES, true>);
+    k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, node_a, node_b, store, flags);
     count_launches(1);
 }
 

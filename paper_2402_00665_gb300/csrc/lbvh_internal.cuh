@@ -29,12 +29,11 @@ struct Control {
     uint32_t bounds_ticket;        // last-block detection of the bounds reduction
     uint32_t sort_ticket[16];      // tile tickets of each sort pass
     uint32_t query_flags;          // kFlag* latched by the last query
-    uint32_t overflow_expected;    // queries with more hits than a thread buffers
+    uint32_t overflow_filled;      // entries of the overflow list
     unsigned long long total;      // total hits of the last query
-    uint32_t overflow_filled;      // slots of the overflow list used by the fill pass
-    uint32_t pad[7];
+    uint32_t pad[8];
 };
-constexpr int kQueryBufferHits = 32;  // hits a query thread sorts in registers
+constexpr int kQueryBufferHits = 32;  // hits kept per query by the walk
 
 // ---------------------------------------------------------------- min / max
 // FP32 min / max that order -0.0 below +0.0, so the scene bounds and the
@@ -48,22 +47,29 @@ __device__ __forceinline__ float max_ordered(float a, float b) {
 }
 
 // ---------------------------------------------------------------- node layout
-// Internal node k: two float4 = {lo.x, lo.y, lo.z, left}, {hi.x, hi.y, hi.z,
-// skip}; left/skip are canonical ids stored as int bits.
-// Leaf k (points): one float4 = {x, y, z, skip}.
-// Leaf k (boxes):  two float4 = {lo.xyz, skip}, {hi.xyz, 0}.
-// Canonical ids: internal k -> k, leaf k -> (n-1)+k, sentinel -> -1.
+// Two float4 arrays indexed by canonical node id (internal k -> k, leaf k ->
+// (n-1)+k, sentinel -> -1), so that a walk step is the same code for every
+// node:
+//   a[id]  internal: {lo.x, lo.y, lo.z, left}    leaf: {lo.xyz (point: xyz), skip}
+//   b[id]  internal: {hi.x, hi.y, hi.z, skip}    box leaf: {hi.xyz, 0}
+// a has 2n-1 entries; b has n-1 (points: a leaf's box is its point) or 2n-1
+// (boxes). left/skip are stored as int bits.
 constexpr int kSentinel = -1;
+
+inline size_t node_b_count(int64_t n, int kind) {
+    const int64_t ni = n > 0 ? n - 1 : 0;
+    return (size_t)(kind == LBVH_PRIM_POINTS ? ni : ni + n);
+}
 
 // ---------------------------------------------------------------- radix sort
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
 constexpr int kMaxPasses = 8;
 
-inline int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+// Keys per tile of the sort's tile shape in use (threads * keys per thread).
+int64_t sort_tile_keys();
+inline int64_t sort_tiles(int64_t n) { return (n + sort_tile_keys() - 1) / sort_tile_keys(); }
 inline int sort_passes(int key_bits) { return (key_bits + kRadixBits - 1) / kRadixBits; }
 
 struct SortScratch {
@@ -72,17 +78,19 @@ struct SortScratch {
     int64_t lookback_words;  // words per region
 };
 
-// Global digit histograms of all passes (used by the stand-alone sort; the
-// build computes them inside the Morton encoder). `hist` must be zero.
+// Global digit histograms of the first `passes` passes (the stand-alone sort
+// asks for pass 0 only; the build's encoder counts pass 0 itself). `hist`
+// must be zero.
 void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_t *hist,
                             cudaStream_t s);
 
 // Sorts (keys, vals) by the low `passes * 8` bits. keys_a/vals_a hold the
 // input (with `iota` the payload is the index and vals_a's contents are
 // ignored; it is still used as a ping-pong buffer); keys_b/vals_b are the
-// second buffers. Returns true if the result ended in the *_b buffers. hist
-// must already hold the global digit counts. Region 0 of the look-back is
-// cleared here with a memset.
+// second buffers. Returns true if the result ended in the *_b buffers.
+// hist[0..256) must hold pass 0's global digit counts and the rest of hist
+// must be zero (pass p counts pass p+1's digits). Region 0 of the look-back
+// is cleared here with a memset.
 // pass_events (nullable): an event pair per pass, recorded around its kernel.
 bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
@@ -98,17 +106,17 @@ void launch_encode(const float *prims, int64_t n, int kind, int bits, const floa
                    uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
 
 // ---------------------------------------------------------------- construct
-// Algorithm 4 with boxes: writes inodes (2(n-1) float4), leaves, and uses
+// Algorithm 4 with boxes: writes node_a / node_b (layout above), and uses
 // `store` (n-1 words, all zero on entry; left all zero on exit).
 // flags: kFlagCorrupt is latched if the input is not a sorted permutation.
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
-                      int64_t n, int kind, float4 *inodes, float4 *leaves,
+                      int64_t n, int kind, float4 *node_a, float4 *node_b,
                       unsigned long long *store, uint32_t *flags, cudaStream_t s);
 
 // ---------------------------------------------------------------- query
 struct TreeView {
-    const float4 *inodes;
-    const float4 *leaves;
+    const float4 *a;
+    const float4 *b;
     const uint32_t *perm;
     int64_t n;
     int kind;
@@ -119,22 +127,27 @@ struct QueryArgs {
     int qkind;
     const float *radii;  // null: `radius` for every query
     float radius;
+    const uint32_t *order;  // null: thread i walks query i; else query order[i]
 };
-// counts[q] = number of hits of query q (Algorithm 1 walk).
-void launch_query_count(const TreeView &t, const QueryArgs &q, uint32_t *counts, Control *ctl,
-                        cudaStream_t s);
-// offsets[0..nq] = exclusive scan of counts (offsets[nq] = total); also sets
-// ctl->total and ctl->overflow_expected (queries with > kQueryBufferHits).
+struct QueryScratch {
+    uint32_t *counts;         // nq, hits of query q (query order)
+    uint32_t *count_sorted;   // nq, hits of the query thread i walked
+    uint32_t *slots;          // nq * kQueryBufferHits: thread i's hits, walk order
+    uint32_t *overflow_list;  // nq, queries to walk a second time
+};
+// The collecting walk (counts, short sorted lists, overflow list).
+void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
+                          cudaStream_t s);
+// offsets[0..nq] = exclusive scan of counts (offsets[nq] = total = ctl->total).
 int64_t scan_tile_count(int64_t nq);
 void launch_exclusive_scan(const uint32_t *counts, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s);
-// Writes each query's hits (primitive ids) at offsets[q]; lists sorted in
-// registers when they fit, else appended to overflow_list for the fix-up sort.
-void launch_query_fill(const TreeView &t, const QueryArgs &q, const int64_t *offsets,
-                       uint32_t *hits, uint32_t *overflow_list, Control *ctl, cudaStream_t s);
-// Sorts the hit lists of the `count` queries in overflow_list, one CTA each.
-void launch_sort_overflow(const int64_t *offsets, uint32_t *hits, const uint32_t *overflow_list,
-                          uint32_t count, cudaStream_t s);
+// Short lists from the scratch buffer to their CSR positions.
+void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
+                       uint32_t *hits, cudaStream_t s);
+// Second walk + sort for the `count` queries of the overflow list.
+void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScratch &qs,
+                           uint32_t count, const int64_t *offsets, uint32_t *hits, cudaStream_t s);
 
 int device_sm_count();
 

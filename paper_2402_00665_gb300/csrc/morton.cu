@@ -182,22 +182,49 @@ __global__ void __launch_bounds__(kThreads)
     }
     __syncthreads();
     if (!s_last) return;
-    // the last block folds the per-block partials
+    // the last block folds the per-block partials, all threads in parallel
     __threadfence();
+    MinMax f;
+    f.init();
+    int all = 1;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) {
+        const float *p = partials + 8 * (int64_t)b;
+        for (int a = 0; a < 3; ++a) {
+            f.lo[a] = min_ordered(f.lo[a], __ldcg(p + a));
+            f.hi[a] = max_ordered(f.hi[a], __ldcg(p + 3 + a));
+        }
+        all &= __ldcg(p + 6) != 0.0f;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        for (int a = 0; a < 3; ++a) {
+            f.lo[a] = min_ordered(f.lo[a], __shfl_xor_sync(0xffffffffu, f.lo[a], off));
+            f.hi[a] = max_ordered(f.hi[a], __shfl_xor_sync(0xffffffffu, f.hi[a], off));
+        }
+        all &= __shfl_xor_sync(0xffffffffu, all, off);
+    }
+    __syncthreads();  // s_v / s_ok are reused
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) {
+            s_v[warp][a] = f.lo[a];
+            s_v[warp][3 + a] = f.hi[a];
+        }
+        s_ok[warp] = all;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         float v[6];
-        int all = 1;
-        for (int k = 0; k < 6; ++k) v[k] = __ldcg(partials + k);
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            const float *p = partials + 8 * (int64_t)b;
+        int ok_all = 1;
+        for (int k = 0; k < 6; ++k) v[k] = s_v[0][k];
+        for (int w = 1; w < kThreads / 32; ++w) {
             for (int a = 0; a < 3; ++a) {
-                v[a] = min_ordered(v[a], __ldcg(p + a));
-                v[3 + a] = max_ordered(v[3 + a], __ldcg(p + 3 + a));
+                v[a] = min_ordered(v[a], s_v[w][a]);
+                v[3 + a] = max_ordered(v[3 + a], s_v[w][3 + a]);
             }
-            all &= __ldcg(p + 6) != 0.0f;
+            ok_all &= s_ok[w];
         }
+        ok_all &= s_ok[0];
         for (int k = 0; k < 6; ++k) bounds[k] = v[k];
-        if (!all) atomicOr(&ctl->build_flags, kFlagNonfinite);
+        if (!ok_all) atomicOr(&ctl->build_flags, kFlagNonfinite);
         ctl->bounds_ticket = 0;  // ready for the next reduction
     }
 }

@@ -3,21 +3,35 @@
 // Each thread walks the tree for one query: start at the root (id 0); when
 // the predicate holds on an internal node go to its left child, on a leaf
 // report it and go to its skip; when it fails go to the skip; stop at the
-// sentinel. Internal nodes are two float4 (box + left, box + skip), point
-// leaves one float4 (xyz + skip), so every step is one or two 16-byte loads
-// through the read-only path and a few FP32 operations.
+// sentinel. Every step runs the same code for internal nodes and leaves: one
+// 16-byte load of a[id] (lo + left, or a leaf's lo + skip), one of b[id]
+// (hi + skip) unless the node is a point leaf, the box test, and a select.
 //
 // Predicates (closed, FP32, fixed operation order, no fused multiply-add):
 //   sphere  e_a = max(lo_a - c_a, c_a - hi_a, 0); d2 = (ex*ex + ey*ey) + ez*ez;
 //           hit iff d2 <= r*r. Rounding is monotone, so a node's d2 never
 //           exceeds the d2 of a primitive inside it: the walk prunes nothing
-//           a brute-force scan would report.
+//           a brute-force scan would report. For a point leaf (lo == hi == p)
+//           e_a = |p_a - c_a| exactly, because fl(c - p) = -fl(p - c).
 //   box     lo_q <= hi_b and lo_b <= hi_q on every axis.
 //
-// CSR in three steps: a counting walk, an exclusive scan of the counts, and a
-// filling walk that sorts each query's primitive ids in registers (lists of up
-// to kQueryBufferHits; longer lists are written in walk order and sorted by a
-// fix-up kernel, one CTA per list, with a bitonic network).
+// Threads take the queries in the order given by QueryArgs::order (the
+// queries sorted by the Morton code of their centre, so that a warp's walks
+// visit the same nodes), and write results at the query's own index.
+//
+// CSR in one walk:
+//   collect   thread i walks query order[i] and writes up to kQueryBufferHits
+//             primitive ids, in walk order, into its own slot of a scratch
+//             array (no shared memory: L1 stays with the tree); it writes the
+//             hit count at the query's index.
+//   scan      exclusive scan of the counts -> offsets, total (host reads it).
+//   copy      each thread loads one slot into registers, sorts it with a
+//             bitonic network, and the warp writes its 32 lists to their CSR
+//             positions through shared memory, one coalesced list per step.
+//   overflow  queries with more hits walk again and write straight into the
+//             CSR; a fix-up kernel sorts those lists, one CTA per list.
+#include <type_traits>
+
 #include "lbvh_internal.cuh"
 
 namespace lbvh {
@@ -85,81 +99,127 @@ __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf)
     uint32_t steps = 0;
     while (node != kSentinel) {
         if ((uint32_t)node >= nodes || ++steps > max_steps) return false;
-        if (node < ni) {
-            const float4 a = __ldg(t.inodes + 2 * node);
-            const float4 b = __ldg(t.inodes + 2 * node + 1);
-            node = hits(q, xyz(a), xyz(b)) ? __float_as_int(a.w) : __float_as_int(b.w);
-        } else {
-            const int k = node - ni;
-            float4 a, b;
-            if (kP == LBVH_PRIM_POINTS) {
-                a = __ldg(t.leaves + k);
-                b = a;
-            } else {
-                a = __ldg(t.leaves + 2 * k);
-                b = __ldg(t.leaves + 2 * k + 1);
-            }
-            if (hits(q, xyz(a), xyz(b))) on_leaf(k);
-            node = __float_as_int(a.w);
-        }
+        const bool leaf = node >= ni;
+        const float4 a = __ldg(t.a + node);
+        float4 b = a;  // a point leaf's box is its point
+        if (kP == LBVH_PRIM_BOXES || !leaf) b = __ldg(t.b + node);
+        const bool hit = hits(q, xyz(a), xyz(b));
+        if (hit && leaf) on_leaf(node - ni);
+        // internal: left child on a hit, else skip; leaf: its skip (in a.w)
+        node = __float_as_int((hit || leaf) ? a.w : b.w);
     }
     return true;
 }
 
+constexpr int kSlot = kQueryBufferHits;
+
+__device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) {
+    return qa.order ? (int64_t)__ldg(qa.order + i) : i;
+}
+
+// One walk per query: hit count at the query's index, up to kSlot primitive
+// ids (walk order) in the thread's slot. See the file comment.
 template <int kQ, int kP>
 __global__ void __launch_bounds__(kThreads)
-    count_kernel(TreeView t, QueryArgs qa, uint32_t *__restrict__ counts, Control *ctl) {
-    const int64_t qi = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (qi >= qa.nq) return;
+    collect_kernel(TreeView t, QueryArgs qa, uint32_t *__restrict__ counts,
+                   uint32_t *__restrict__ count_sorted, uint32_t *__restrict__ slots,
+                   uint32_t *__restrict__ overflow_list, Control *ctl) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= qa.nq) return;
+    const int64_t qi = thread_query(qa, i);
+    uint32_t *slot = slots + i * kSlot;
     uint32_t c = 0;
     if (t.n > 0 && ctl->build_flags == 0) {
         const auto q = QueryOf<kQ>::load(qa, qi);
-        if (!walk<kP>(t, q, [&](int) { ++c; })) atomicOr(&ctl->query_flags, kFlagCorrupt);
-    }
-    counts[qi] = c;
-}
-
-// Keeps buf[0..K) ascending: x moves in from the front, the largest value
-// falls off the end (a padding value while fewer than K hits were inserted).
-template <int K>
-__device__ __forceinline__ void insert_sorted(uint32_t (&buf)[K], uint32_t x) {
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const uint32_t lo = min(buf[j], x);
-        x = max(buf[j], x);
-        buf[j] = lo;
-    }
-}
-
-template <int kQ, int kP>
-__global__ void __launch_bounds__(kThreads)
-    fill_kernel(TreeView t, QueryArgs qa, const int64_t *__restrict__ offsets,
-                uint32_t *__restrict__ hits_out, uint32_t *__restrict__ overflow_list,
-                Control *ctl) {
-    const int64_t qi = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (qi >= qa.nq) return;
-    const int64_t base = offsets[qi];
-    const int64_t count = offsets[qi + 1] - base;
-    if (count == 0) return;
-    const auto q = QueryOf<kQ>::load(qa, qi);
-    uint32_t *out = hits_out + base;
-    if (count <= kQueryBufferHits) {
-        uint32_t buf[kQueryBufferHits];
-#pragma unroll
-        for (int j = 0; j < kQueryBufferHits; ++j) buf[j] = 0xffffffffu;
-        walk<kP>(t, q, [&](int k) { insert_sorted(buf, __ldg(t.perm + k)); });
-#pragma unroll
-        for (int j = 0; j < kQueryBufferHits; ++j)
-            if (j < count) out[j] = buf[j];
-    } else {
-        int64_t c = 0;
-        walk<kP>(t, q, [&](int k) {
-            if (c < count) out[c] = __ldg(t.perm + k);
+        const bool ok = walk<kP>(t, q, [&](int k) {
+            if (c < (uint32_t)kSlot) slot[c] = __ldg(t.perm + k);
             ++c;
         });
-        const uint32_t slot = atomicAdd(&ctl->overflow_filled, 1u);
-        overflow_list[slot] = (uint32_t)qi;
+        if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
     }
+    counts[qi] = c;
+    count_sorted[i] = c;
+    if (c > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi;
+}
+
+// Ascending bitonic sorting network over 32 registers (indices are compile
+// time constants after unrolling).
+__device__ __forceinline__ void sort32(uint32_t (&v)[32]) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int x = 0; x < 32; ++x) {
+                const int y = x ^ j;
+                if (y > x) {
+                    const uint32_t lo = min(v[x], v[y]), hi = max(v[x], v[y]);
+                    const bool up = (x & k) == 0;
+                    v[x] = up ? lo : hi;
+                    v[y] = up ? hi : lo;
+                }
+            }
+        }
+    }
+}
+
+// Thread i sorts slot i in registers; the warp then writes its 32 lists to
+// their CSR positions, one list per step, lanes on consecutive hits.
+__global__ void __launch_bounds__(kThreads)
+    copy_kernel(int64_t nq, const uint32_t *__restrict__ order,
+                const uint32_t *__restrict__ count_sorted, const int64_t *__restrict__ offsets,
+                const uint32_t *__restrict__ slots, uint32_t *__restrict__ hits) {
+    __shared__ uint32_t s_lists[kThreads / 32][32][kSlot + 1];
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t c = 0;
+    int64_t dst = 0;
+    if (i < nq) {
+        c = count_sorted[i];
+        if (c > (uint32_t)kSlot) c = 0;  // written by the overflow walk
+        if (c) dst = offsets[order ? (int64_t)__ldg(order + i) : i];
+    }
+    if (__any_sync(0xffffffffu, c != 0)) {
+        uint32_t v[kSlot];
+        const uint4 *src = reinterpret_cast<const uint4 *>(slots + i * kSlot);
+#pragma unroll
+        for (int j4 = 0; j4 < kSlot / 4; ++j4) {
+            uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
+            if (4 * j4 < (int)c) w = src[j4];
+            v[4 * j4] = 4 * j4 < (int)c ? w.x : ~0u;
+            v[4 * j4 + 1] = 4 * j4 + 1 < (int)c ? w.y : ~0u;
+            v[4 * j4 + 2] = 4 * j4 + 2 < (int)c ? w.z : ~0u;
+            v[4 * j4 + 3] = 4 * j4 + 3 < (int)c ? w.w : ~0u;
+        }
+        if (c > 1) sort32(v);
+#pragma unroll
+        for (int j = 0; j < kSlot; ++j) s_lists[warp][lane][j] = v[j];
+        __syncwarp();
+        for (int s = 0; s < 32; ++s) {
+            const uint32_t cs = __shfl_sync(0xffffffffu, c, s);
+            const int64_t ds = __shfl_sync(0xffffffffu, dst, s);
+            if ((uint32_t)lane < cs) hits[ds + lane] = s_lists[warp][s][lane];
+        }
+    }
+}
+
+// Second walk for the overflow list: hits go straight to the CSR in walk
+// order (sorted afterwards by sort_lists_kernel).
+template <int kQ, int kP>
+__global__ void __launch_bounds__(kThreads)
+    overflow_walk_kernel(TreeView t, QueryArgs qa, const uint32_t *__restrict__ list, uint32_t count,
+                         const int64_t *__restrict__ offsets, uint32_t *__restrict__ hits) {
+    const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (j >= count) return;
+    const int64_t qi = list[j];
+    const int64_t base = offsets[qi];
+    const int64_t total = offsets[qi + 1] - base;
+    const auto q = QueryOf<kQ>::load(qa, qi);
+    int64_t c = 0;
+    walk<kP>(t, q, [&](int k) {
+        if (c < total) hits[base + c] = __ldg(t.perm + k);
+        ++c;
+    });
 }
 
 // ---------------------------------------------------------------- scan
@@ -187,24 +247,16 @@ __device__ __forceinline__ int64_t block_scan_exclusive(int64_t v, int64_t *s_wa
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-    scan_reduce_kernel(const uint32_t *__restrict__ counts, int64_t nq, int64_t *tile_sums,
-                       uint32_t *overflow_expected) {
+    scan_reduce_kernel(const uint32_t *__restrict__ counts, int64_t nq, int64_t *tile_sums) {
     __shared__ int64_t s_warp[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t sum = 0;
-    uint32_t big = 0;
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = base + j * kScanThreads + threadIdx.x;
-        if (i < nq) {
-            const uint32_t c = counts[i];
-            sum += c;
-            big += c > (uint32_t)kQueryBufferHits;
-        }
+        if (i < nq) sum += counts[i];
     }
     int64_t total;
     block_scan_exclusive(sum, s_warp, total);
-    for (int off = 16; off > 0; off >>= 1) big += __shfl_xor_sync(0xffffffffu, big, off);
-    if ((threadIdx.x & 31) == 0 && big) atomicAdd(overflow_expected, big);
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
@@ -309,54 +361,52 @@ __global__ void __launch_bounds__(kFixThreads)
     }
 }
 
-template <int kQ, int kP>
-void launch_count_t(const TreeView &t, const QueryArgs &q, uint32_t *counts, Control *ctl,
-                    cudaStream_t s) {
-    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
-    count_kernel<kQ, kP><<<blocks, kThreads, 0, s>>>(t, q, counts, ctl);
-    count_launches(1);
-}
-
-template <int kQ, int kP>
-void launch_fill_t(const TreeView &t, const QueryArgs &q, const int64_t *offsets,
-                   uint32_t *hits, uint32_t *overflow_list, Control *ctl, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
-    fill_kernel<kQ, kP><<<blocks, kThreads, 0, s>>>(t, q, offsets, hits, overflow_list, ctl);
-    count_launches(1);
-}
-
 }  // namespace
 
-void launch_query_count(const TreeView &t, const QueryArgs &q, uint32_t *counts, Control *ctl,
-                        cudaStream_t s) {
-    if (q.nq <= 0) return;
-    if (q.qkind == LBVH_Q_SPHERE) {
-        if (t.kind == LBVH_PRIM_POINTS)
-            launch_count_t<LBVH_Q_SPHERE, LBVH_PRIM_POINTS>(t, q, counts, ctl, s);
+template <typename F>
+void dispatch_kinds(int qkind, int pkind, F &&f) {
+    if (qkind == LBVH_Q_SPHERE) {
+        if (pkind == LBVH_PRIM_POINTS)
+            f(std::integral_constant<int, LBVH_Q_SPHERE>{}, std::integral_constant<int, LBVH_PRIM_POINTS>{});
         else
-            launch_count_t<LBVH_Q_SPHERE, LBVH_PRIM_BOXES>(t, q, counts, ctl, s);
+            f(std::integral_constant<int, LBVH_Q_SPHERE>{}, std::integral_constant<int, LBVH_PRIM_BOXES>{});
     } else {
-        if (t.kind == LBVH_PRIM_POINTS)
-            launch_count_t<LBVH_Q_BOX, LBVH_PRIM_POINTS>(t, q, counts, ctl, s);
+        if (pkind == LBVH_PRIM_POINTS)
+            f(std::integral_constant<int, LBVH_Q_BOX>{}, std::integral_constant<int, LBVH_PRIM_POINTS>{});
         else
-            launch_count_t<LBVH_Q_BOX, LBVH_PRIM_BOXES>(t, q, counts, ctl, s);
+            f(std::integral_constant<int, LBVH_Q_BOX>{}, std::integral_constant<int, LBVH_PRIM_BOXES>{});
     }
 }
 
-void launch_query_fill(const TreeView &t, const QueryArgs &q, const int64_t *offsets,
-                       uint32_t *hits, uint32_t *overflow_list, Control *ctl, cudaStream_t s) {
+void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
+                          cudaStream_t s) {
     if (q.nq <= 0) return;
-    if (q.qkind == LBVH_Q_SPHERE) {
-        if (t.kind == LBVH_PRIM_POINTS)
-            launch_fill_t<LBVH_Q_SPHERE, LBVH_PRIM_POINTS>(t, q, offsets, hits, overflow_list, ctl, s);
-        else
-            launch_fill_t<LBVH_Q_SPHERE, LBVH_PRIM_BOXES>(t, q, offsets, hits, overflow_list, ctl, s);
-    } else {
-        if (t.kind == LBVH_PRIM_POINTS)
-            launch_fill_t<LBVH_Q_BOX, LBVH_PRIM_POINTS>(t, q, offsets, hits, overflow_list, ctl, s);
-        else
-            launch_fill_t<LBVH_Q_BOX, LBVH_PRIM_BOXES>(t, q, offsets, hits, overflow_list, ctl, s);
-    }
+    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
+    dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
+        collect_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
+            t, q, qs.counts, qs.count_sorted, qs.slots, qs.overflow_list, ctl);
+    });
+    count_launches(1);
+}
+
+void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
+                       uint32_t *hits, cudaStream_t s) {
+    if (q.nq <= 0) return;
+    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
+    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, q.order, qs.count_sorted, offsets, qs.slots, hits);
+    count_launches(1);
+}
+
+void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScratch &qs,
+                           uint32_t count, const int64_t *offsets, uint32_t *hits, cudaStream_t s) {
+    if (count == 0) return;
+    const unsigned blocks = (unsigned)((count + kThreads - 1) / kThreads);
+    dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
+        overflow_walk_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
+            t, q, qs.overflow_list, count, offsets, hits);
+    });
+    sort_lists_kernel<<<count, kFixThreads, 0, s>>>(offsets, hits, qs.overflow_list);
+    count_launches(2);
 }
 
 int64_t scan_tile_count(int64_t nq) { return (nq + kScanTile - 1) / kScanTile; }
@@ -365,19 +415,11 @@ void launch_exclusive_scan(const uint32_t *counts, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s) {
     const int64_t tiles = scan_tile_count(nq);
     if (tiles > 0)
-        scan_reduce_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(counts, nq, tile_sums,
-                                                                  &ctl->overflow_expected);
+        scan_reduce_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(counts, nq, tile_sums);
     scan_tiles_kernel<<<1, kScanThreads, 0, s>>>(tile_sums, tiles, offsets, nq, &ctl->total);
     if (tiles > 0)
         scan_apply_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(counts, nq, tile_sums, offsets);
     count_launches(tiles > 0 ? 3 : 1);
-}
-
-void launch_sort_overflow(const int64_t *offsets, uint32_t *hits, const uint32_t *overflow_list,
-                          uint32_t count, cudaStream_t s) {
-    if (count == 0) return;
-    sort_lists_kernel<<<count, kFixThreads, 0, s>>>(offsets, hits, overflow_list);
-    count_launches(1);
 }
 
 }  // namespace lbvh

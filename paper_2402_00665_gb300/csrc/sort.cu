@@ -3,8 +3,9 @@
 // primitive index, so equal codes keep index order).
 //
 // One kernel launch per 8-bit digit ("onesweep"): the global digit counts of
-// every pass are known up front (from the Morton encoder, or from
-// digit_histogram_kernel), so each pass reads and writes the data once.
+// a pass are known when it starts (pass 0's from the Morton encoder or from
+// digit_histogram_kernel; pass p+1's counted by pass p as it reads the keys),
+// so each pass reads and writes the data once.
 // Per pass, each CTA takes a tile of 4096 keys by ticket (so every tile it may
 // wait on is already running), ranks the keys by digit inside the tile with
 // warp match/ballot counting, publishes its per-digit counts, resolves the
@@ -15,6 +16,8 @@
 // Look-back words: bits 31:30 = state (0 none, 1 aggregate, 2 inclusive
 // prefix), bits 29:0 = count. Two regions alternate between passes; every
 // tile clears its word block in the other region for the next pass.
+#include <cstdlib>
+
 #include "lbvh_internal.cuh"
 
 namespace lbvh {
@@ -60,25 +63,45 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return before + x - v;
 }
 
+template <int kItems>
 struct SortSmem {
+    static constexpr int kTile = kSortThreads * kItems;
     uint32_t warp_hist[kWarps][kRadix];  // per-warp digit counts, then per-warp offsets
     int32_t out_base[kRadix];            // global position of the digit's first staged key, minus its tile start
     uint32_t tile_start[kRadix];         // first staged slot of each digit
     uint32_t scan[kWarps];
     uint32_t tile;
-    uint64_t keys[kSortTile];
-    uint32_t vals[kSortTile];
+    uint32_t next_hist[kRadix];          // digit counts of the next pass
+    uint64_t keys[kTile];
+    uint32_t vals[kTile];
 };
 
-template <bool kIota>
-__global__ void __launch_bounds__(kSortThreads)
+// Lanes of the warp whose digit equals d: match.any, or eight ballots (one
+// per digit bit).
+template <bool kBallot>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
+    if (!kBallot) return __match_any_sync(0xffffffffu, d);
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t vote = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? vote : ~vote;
+    }
+    return peers;
+}
+
+template <bool kIota, int kItems, int kMinBlocks, bool kBallot>
+__global__ void __launch_bounds__(kSortThreads, kMinBlocks)
     onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
                     int shift, const uint32_t *__restrict__ pass_hist, uint32_t *lookback,
                     uint32_t *lookback_next, uint32_t *ticket, int64_t tiles,
-                    uint32_t *flags) {
+                    uint32_t *flags, uint32_t *next_hist) {
+    using Smem = SortSmem<kItems>;
+    constexpr int kTile = Smem::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem &sm = *reinterpret_cast<SortSmem *>(smem_raw);
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     if (threadIdx.x == 0) {
@@ -87,18 +110,20 @@ __global__ void __launch_bounds__(kSortThreads)
         sm.tile = t;
     }
     for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) (&sm.warp_hist[0][0])[k] = 0;
+    sm.next_hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t tile = sm.tile;
-    const int64_t tile_base = tile * kSortTile;
-    const int64_t valid = min((int64_t)kSortTile, n - tile_base);
+    const int64_t tile_base = tile * kTile;
+    const int64_t valid = min((int64_t)kTile, n - tile_base);
 
-    // ---- load: warp w owns keys [w*512, w*512+512) of the tile, round j lane l
-    uint64_t key[kSortItems];
-    uint32_t val[kSortItems];
-    uint32_t rank[kSortItems];
+    // ---- load: warp w owns keys [w*32*kItems, (w+1)*32*kItems) of the tile,
+    // round j lane l holds key w*32*kItems + 32*j + l
+    uint64_t key[kItems];
+    uint32_t val[kItems];
+    uint32_t rank[kItems];
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const int local = warp * (kSortItems * 32) + j * 32 + lane;
+    for (int j = 0; j < kItems; ++j) {
+        const int local = warp * (kItems * 32) + j * 32 + lane;
         const int64_t g = tile_base + local;
         if (local < valid) {
             key[j] = keys_in[g];
@@ -109,12 +134,22 @@ __global__ void __launch_bounds__(kSortThreads)
         }
     }
 
+    // ---- digit counts for the next pass (its global histogram)
+    if (next_hist) {
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int local = warp * (kItems * 32) + j * 32 + lane;
+            if (local < valid)
+                atomicAdd(&sm.next_hist[(uint32_t)(key[j] >> (shift + kRadixBits)) & (kRadix - 1)], 1u);
+        }
+    }
+
     // ---- rank inside the warp: peers with the same digit, in (round, lane) order
     const uint32_t below = lanemask_lt();
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < kItems; ++j) {
         const uint32_t d = (uint32_t)(key[j] >> shift) & (kRadix - 1);
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = digit_peers<kBallot>(d);
         const uint32_t before = __popc(peers & below);
         const uint32_t base = sm.warp_hist[warp][d];
         __syncwarp();
@@ -166,9 +201,14 @@ __global__ void __launch_bounds__(kSortThreads)
     sm.out_base[d] = (int32_t)(global_base + exclusive) - (int32_t)start;
     __syncthreads();
 
+    if (next_hist) {
+        const uint32_t c = sm.next_hist[threadIdx.x];
+        if (c) atomicAdd(next_hist + threadIdx.x, c);
+    }
+
     // ---- stage in digit order
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < kItems; ++j) {
         const uint32_t dj = (uint32_t)(key[j] >> shift) & (kRadix - 1);
         const uint32_t slot = sm.tile_start[dj] + sm.warp_hist[warp][dj] + rank[j];
         sm.keys[slot] = key[j];
@@ -178,7 +218,7 @@ __global__ void __launch_bounds__(kSortThreads)
 
     // ---- write out: slot s goes to out_base[digit] + s
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
+    for (int j = 0; j < kItems; ++j) {
         const int s = j * kSortThreads + threadIdx.x;
         if (s < valid) {
             const uint64_t k = sm.keys[s];
@@ -192,6 +232,46 @@ __global__ void __launch_bounds__(kSortThreads)
             vals_out[pos] = sm.vals[s];
         }
     }
+}
+
+using PassKernel = void (*)(const uint64_t *, const uint32_t *, uint64_t *, uint32_t *, int64_t, int,
+                            const uint32_t *, uint32_t *, uint32_t *, uint32_t *, int64_t, uint32_t *,
+                            uint32_t *);
+
+struct Variant {
+    int items, min_blocks;
+    bool ballot;
+    PassKernel first, rest;  // payload = index / payload read
+    size_t smem;
+};
+
+template <int kItems, int kMinBlocks, bool kBallot>
+Variant make_variant() {
+    return Variant{kItems, kMinBlocks, kBallot, onesweep_kernel<true, kItems, kMinBlocks, kBallot>,
+                   onesweep_kernel<false, kItems, kMinBlocks, kBallot>, sizeof(SortSmem<kItems>)};
+}
+
+// Tile shapes the library is compiled with. The first entry is the default;
+// LBVH_SORT_VARIANT=<index> selects another (used by the tuning sweep).
+const Variant &variant() {
+    static const Variant table[] = {
+        make_variant<12, 4, true>(), make_variant<16, 3, true>(),  make_variant<8, 4, true>(),
+        make_variant<16, 2, true>(), make_variant<12, 3, true>(),  make_variant<8, 6, true>(),
+        make_variant<16, 2, false>(),
+    };
+    static int pick = -1;
+    if (pick < 0) {
+        const char *env = getenv("LBVH_SORT_VARIANT");
+        const int want = env ? atoi(env) : 0;
+        pick = (want >= 0 && want < (int)(sizeof table / sizeof table[0])) ? want : 0;
+        for (const Variant &v : table) {
+            for (PassKernel k : {v.first, v.rest}) {
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+                cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            }
+        }
+    }
+    return table[pick];
 }
 
 __global__ void __launch_bounds__(256)
@@ -225,20 +305,14 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
     count_launches(1);
 }
 
+int64_t sort_tile_keys() { return (int64_t)kSortThreads * variant().items; }
+
 bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2]) {
     if (n <= 0 || passes <= 0) return false;
+    const Variant &v = variant();
     const int64_t tiles = sort_tiles(n);
-    const size_t smem = sizeof(SortSmem);
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(onesweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        cudaFuncSetAttribute(onesweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        configured = true;
-    }
     cudaMemsetAsync(scratch.lookback, 0, (size_t)tiles * kRadix * sizeof(uint32_t), s);
     uint64_t *kin = keys_a, *kout = keys_b;
     uint32_t *vin = vals_a, *vout = vals_b;
@@ -247,14 +321,11 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
         uint32_t *nxt = scratch.lookback + ((p + 1) & 1) * scratch.lookback_words;
         const uint32_t *hist = scratch.hist + p * kRadix;
         if (pass_events) cudaEventRecord(pass_events[p][0], s);
-        if (p == 0 && iota)
-            onesweep_kernel<true><<<(unsigned)tiles, kSortThreads, smem, s>>>(
-                kin, nullptr, kout, vout, n, kRadixBits * p, hist, cur, nxt, &ctl->sort_ticket[p],
-                tiles, &ctl->build_flags);
-        else
-            onesweep_kernel<false><<<(unsigned)tiles, kSortThreads, smem, s>>>(
-                kin, vin, kout, vout, n, kRadixBits * p, hist, cur, nxt, &ctl->sort_ticket[p],
-                tiles, &ctl->build_flags);
+        PassKernel k = (p == 0 && iota) ? v.first : v.rest;
+        uint32_t *next_hist = p + 1 < passes ? scratch.hist + (p + 1) * kRadix : nullptr;
+        k<<<(unsigned)tiles, kSortThreads, v.smem, s>>>(kin, vin, kout, vout, n, kRadixBits * p, hist, cur,
+                                                         nxt, &ctl->sort_ticket[p], tiles, &ctl->build_flags,
+                                                         next_hist);
         if (pass_events) cudaEventRecord(pass_events[p][1], s);
         count_launches(1);
         uint64_t *tk = kin;

@@ -344,3 +344,22 @@ def test_library_allocated_query_matches_caller_buffers():
     assert torch.equal(off, ref_off) and torch.equal(hits, ref_hits)
     lib.lbvh_free(d_off)
     lib.lbvh_free(d_hits)
+
+
+def test_self_query_reuses_build_order_same_result():
+    """Queries that are the build's own primitives (same buffer) are walked in
+    the build's Morton order; results equal those from a separate buffer."""
+    lbvh = L()
+    pts = torch.as_tensor(inputs.uniform_points(50000, seed=20)).cuda()
+    r = float(inputs.radius_for_neighbours(50000))
+    t = lbvh.Tree().build(pts, lbvh.POINTS, 63)
+    off_a, hits_a = t.query(pts, lbvh.SPHERE, radius=r)           # aliased: build order
+    off_b, hits_b = t.query(pts.clone(), lbvh.SPHERE, radius=r)   # encoded + sorted order
+    assert torch.equal(off_a, off_b) and torch.equal(hits_a, hits_b)
+    o = oracle.build(pts.cpu().numpy(), oracle.POINTS, 63)
+    assert_csr_equal(off_a, hits_a, *oracle.query(o, pts.cpu().numpy(), oracle.SPHERE, radius=np.float32(r)))
+    boxes = torch.as_tensor(inputs.gaussian_mixture_boxes(40000, seed=21)).cuda()
+    t = lbvh.Tree().build(boxes, lbvh.BOXES, 30)
+    off_a, hits_a = t.query(boxes, lbvh.BOX)
+    off_b, hits_b = t.query(boxes.clone(), lbvh.BOX)
+    assert torch.equal(off_a, off_b) and torch.equal(hits_a, hits_b)
