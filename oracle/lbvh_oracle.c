@@ -41,7 +41,8 @@
  *                 max (here and in the bounds) order -0.0 below +0.0.
  *   Queries       Algorithm 1. Sphere: closed ball; squared distance from the
  *                 centre to the box, axes x, y, z summed in that order with
- *                 separate multiply and add. Box: closed overlap test.
+ *                 separate multiply and add; a NaN centre coordinate or radius
+ *                 hits nothing. Box: closed overlap test.
  */
 #include "lbvh_oracle.h"
 
@@ -391,6 +392,7 @@ int oracle_build(const float *prims, int64_t n, int kind, int bits, uint64_t *co
 static int sphere_box_r2(const float *c, float r2, const float *box) {
     float e[3];
     for (int a = 0; a < 3; ++a) {
+        if (isnan(c[a])) return 0; /* a centre with a NaN coordinate hits nothing */
         float below = box[a] - c[a];
         float above = c[a] - box[3 + a];
         e[a] = fmaxf(fmaxf(below, above), 0.0f);

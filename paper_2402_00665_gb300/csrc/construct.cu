@@ -60,17 +60,11 @@ __device__ __forceinline__ unsigned long long pack(uint32_t end, uint32_t d, uin
     return (1ull << 63) | ((unsigned long long)dn << 40) | ((unsigned long long)d << 32) | end;
 }
 
-template <int kKind>
-__device__ __forceinline__ void load_node_box(const float4 *node_a, const float4 *node_b, int ni,
-                                              int id, float3 &lo, float3 &hi) {
-    const float4 a = __ldcg(node_a + id);
+__device__ __forceinline__ void load_node_box(const float4 *nodes, int id, float3 &lo, float3 &hi) {
+    const float4 a = __ldcg(nodes + 2 * (int64_t)id);
+    const float4 b = __ldcg(nodes + 2 * (int64_t)id + 1);
     lo = make_float3(a.x, a.y, a.z);
-    if (kKind == LBVH_PRIM_POINTS && id >= ni) {
-        hi = lo;
-    } else {
-        const float4 b = __ldcg(node_b + id);
-        hi = make_float3(b.x, b.y, b.z);
-    }
+    hi = make_float3(b.x, b.y, b.z);
 }
 
 // The exchange on store[p] publishes this thread's finished node (release)
@@ -92,7 +86,7 @@ __device__ __forceinline__ unsigned long long publish_exchange(unsigned long lon
 template <int kKind, bool kAcqRel>
 __global__ void __launch_bounds__(kThreads)
     construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
-                     const float *__restrict__ prims, int n, float4 *node_a, float4 *node_b,
+                     const float *__restrict__ prims, int n, float4 *nodes,
                      unsigned long long *store, uint32_t *flags) {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
@@ -120,14 +114,14 @@ __global__ void __launch_bounds__(kThreads)
         lo = make_float3(prims[3 * (int64_t)p_id], prims[3 * (int64_t)p_id + 1],
                          prims[3 * (int64_t)p_id + 2]);
         hi = lo;
-        node_a[ni + i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
     } else {
         const float *b = prims + 6 * (int64_t)p_id;
         lo = make_float3(b[0], b[1], b[2]);
         hi = make_float3(b[3], b[4], b[5]);
-        node_a[ni + i] = make_float4(lo.x, lo.y, lo.z, __int_as_float(leaf_skip));
-        node_b[ni + i] = make_float4(hi.x, hi.y, hi.z, 0.0f);
     }
+    const int64_t leaf_id = ni + i;
+    nodes[2 * leaf_id] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(p_id));
+    nodes[2 * leaf_id + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(leaf_skip));
     if (n == 1) return;
 
     // ---- climb
@@ -162,7 +156,7 @@ __global__ void __launch_bounds__(kThreads)
             sibling = (l == p) ? ni + (int)p : (int)p;
         }
         float3 slo, shi;
-        load_node_box<kKind>(node_a, node_b, ni, sibling, slo, shi);
+        load_node_box(nodes, sibling, slo, shi);
         lo = make_float3(min_ordered(lo.x, slo.x), min_ordered(lo.y, slo.y), min_ordered(lo.z, slo.z));
         hi = make_float3(max_ordered(hi.x, shi.x), max_ordered(hi.y, shi.y), max_ordered(hi.z, shi.z));
 
@@ -170,8 +164,8 @@ __global__ void __launch_bounds__(kThreads)
         const int left_child = (l == p) ? ni + (int)p : (int)p;
         const int skip = (r == (uint32_t)(n - 1)) ? kSentinel
                                                  : (d_right < d_next ? ni + (int)r + 1 : (int)r + 1);
-        node_a[q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
-        node_b[q] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
+        nodes[2 * (int64_t)q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
+        nodes[2 * (int64_t)q + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
         if (q == 0) return;  // the root
     }
     atomicOr(flags, kFlagCorrupt);
@@ -180,8 +174,8 @@ __global__ void __launch_bounds__(kThreads)
 }  // namespace
 
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
-                      int64_t n, int kind, float4 *node_a, float4 *node_b,
-                      unsigned long long *store, uint32_t *flags, cudaStream_t s) {
+                      int64_t n, int kind, float4 *nodes, unsigned long long *store,
+                      uint32_t *flags, cudaStream_t s) {
     if (n <= 0) return;
     // LBVH_CONSTRUCT_FENCES=1 selects the fence form of the exchange (tuning)
     static const bool fences = getenv("LBVH_CONSTRUCT_FENCES") && atoi(getenv("LBVH_CONSTRUCT_FENCES"));
@@ -189,7 +183,7 @@ void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const 
     auto k = kind == LBVH_PRIM_POINTS
                  ? (fences ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_POINTS, true>)
                  : (fences ? construct_kernel<LBVH_PRIM_BOXES, false> : construct_kernel<LBVH_PRIM_BOXES, true>);
-    k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, node_a, node_b, store, flags);
+    k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, nodes, store, flags);
     count_launches(1);
 }
 

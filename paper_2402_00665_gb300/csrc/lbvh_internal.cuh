@@ -47,19 +47,15 @@ __device__ __forceinline__ float max_ordered(float a, float b) {
 }
 
 // ---------------------------------------------------------------- node layout
-// Two float4 arrays indexed by canonical node id (internal k -> k, leaf k ->
-// (n-1)+k, sentinel -> -1), so that a walk step is the same code for every
-// node:
-//   a[id]  internal: {lo.x, lo.y, lo.z, left}    leaf: {lo.xyz (point: xyz), skip}
-//   b[id]  internal: {hi.x, hi.y, hi.z, skip}    box leaf: {hi.xyz, 0}
-// a has 2n-1 entries; b has n-1 (points: a leaf's box is its point) or 2n-1
-// (boxes). left/skip are stored as int bits.
+// One 32-byte record (two float4) per node, indexed by canonical id
+// (internal k -> k, leaf k -> (n-1)+k, sentinel -> -1), so that a walk step
+// touches one sector and runs the same code for every node:
+//   nodes[2 id]      {lo.x, lo.y, lo.z, left}   leaf: {lo.xyz, primitive index}
+//   nodes[2 id + 1]  {hi.x, hi.y, hi.z, skip}   leaf: {hi.xyz, skip}
+// A point leaf has lo == hi. left/skip/index are stored as int bits.
 constexpr int kSentinel = -1;
 
-inline size_t node_b_count(int64_t n, int kind) {
-    const int64_t ni = n > 0 ? n - 1 : 0;
-    return (size_t)(kind == LBVH_PRIM_POINTS ? ni : ni + n);
-}
+inline size_t node_count(int64_t n) { return (size_t)(n > 0 ? 2 * n - 1 : 0); }
 
 // ---------------------------------------------------------------- radix sort
 constexpr int kRadixBits = 8;
@@ -106,18 +102,16 @@ void launch_encode(const float *prims, int64_t n, int kind, int bits, const floa
                    uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
 
 // ---------------------------------------------------------------- construct
-// Algorithm 4 with boxes: writes node_a / node_b (layout above), and uses
+// Algorithm 4 with boxes: writes `nodes` (layout above), and uses
 // `store` (n-1 words, all zero on entry; left all zero on exit).
 // flags: kFlagCorrupt is latched if the input is not a sorted permutation.
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
-                      int64_t n, int kind, float4 *node_a, float4 *node_b,
-                      unsigned long long *store, uint32_t *flags, cudaStream_t s);
+                      int64_t n, int kind, float4 *nodes, unsigned long long *store,
+                      uint32_t *flags, cudaStream_t s);
 
 // ---------------------------------------------------------------- query
 struct TreeView {
-    const float4 *a;
-    const float4 *b;
-    const uint32_t *perm;
+    const float4 *nodes;
     int64_t n;
     int kind;
 };
@@ -130,9 +124,8 @@ struct QueryArgs {
     const uint32_t *order;  // null: thread i walks query i; else query order[i]
 };
 struct QueryScratch {
-    uint32_t *counts;         // nq, hits of query q (query order)
-    uint32_t *count_sorted;   // nq, hits of the query thread i walked
-    uint32_t *slots;          // nq * kQueryBufferHits: thread i's hits, walk order
+    uint32_t *counts;         // nq, hits of query q
+    uint32_t *slots;          // nq * kQueryBufferHits: query q's first hits, walk order
     uint32_t *overflow_list;  // nq, queries to walk a second time
 };
 // The collecting walk (counts, short sorted lists, overflow list).

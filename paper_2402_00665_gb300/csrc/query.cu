@@ -3,16 +3,17 @@
 // Each thread walks the tree for one query: start at the root (id 0); when
 // the predicate holds on an internal node go to its left child, on a leaf
 // report it and go to its skip; when it fails go to the skip; stop at the
-// sentinel. Every step runs the same code for internal nodes and leaves: one
-// 16-byte load of a[id] (lo + left, or a leaf's lo + skip), one of b[id]
-// (hi + skip) unless the node is a point leaf, the box test, and a select.
+// sentinel. Every step runs the same code for internal nodes and leaves: the
+// node's 32-byte record (one sector: lo + left or primitive index, hi + skip),
+// the box test, and a select.
 //
 // Predicates (closed, FP32, fixed operation order, no fused multiply-add):
 //   sphere  e_a = max(lo_a - c_a, c_a - hi_a, 0); d2 = (ex*ex + ey*ey) + ez*ez;
 //           hit iff d2 <= r*r. Rounding is monotone, so a node's d2 never
 //           exceeds the d2 of a primitive inside it: the walk prunes nothing
-//           a brute-force scan would report. For a point leaf (lo == hi == p)
-//           e_a = |p_a - c_a| exactly, because fl(c - p) = -fl(p - c).
+//           a brute-force scan would report. Computed as e_a = c_a -
+//           clamp(c_a, lo_a, hi_a), which has the same magnitude as
+//           max(lo_a - c_a, c_a - hi_a, 0) because fl(x - y) = -fl(y - x).
 //   box     lo_q <= hi_b and lo_b <= hi_q on every axis.
 //
 // Threads take the queries in the order given by QueryArgs::order (the
@@ -20,14 +21,15 @@
 // visit the same nodes), and write results at the query's own index.
 //
 // CSR in one walk:
-//   collect   thread i walks query order[i] and writes up to kQueryBufferHits
-//             primitive ids, in walk order, into its own slot of a scratch
-//             array (no shared memory: L1 stays with the tree); it writes the
-//             hit count at the query's index.
+//   collect   thread i walks query q = order[i] and writes up to
+//             kQueryBufferHits primitive ids, in walk order, into q's slot of
+//             a scratch array (no shared memory: L1 stays with the tree), and
+//             q's hit count.
 //   scan      exclusive scan of the counts -> offsets, total (host reads it).
-//   copy      each thread loads one slot into registers, sorts it with a
-//             bitonic network, and the warp writes its 32 lists to their CSR
-//             positions through shared memory, one coalesced list per step.
+//   copy      in query order: each thread loads one slot into registers and
+//             sorts it with a bitonic network; the warp writes its 32 lists,
+//             adjacent in the CSR, through shared memory, one coalesced list
+//             per step.
 //   overflow  queries with more hits walk again and write straight into the
 //             CSR; a fix-up kernel sorts those lists, one CTA per list.
 #include <type_traits>
@@ -48,8 +50,9 @@ struct Box {
     float3 lo, hi;
 };
 
+// |gap| between c and [lo, hi]: c - clamp(c, lo, hi) (sign irrelevant: squared)
 __device__ __forceinline__ float gap(float lo, float c, float hi) {
-    return fmaxf(fmaxf(__fsub_rn(lo, c), __fsub_rn(c, hi)), 0.0f);
+    return __fsub_rn(c, fminf(fmaxf(c, lo), hi));
 }
 
 __device__ __forceinline__ bool hits(const Sphere &s, float3 lo, float3 hi) {
@@ -87,28 +90,29 @@ struct QueryOf<LBVH_Q_BOX> {
 
 __device__ __forceinline__ float3 xyz(float4 v) { return make_float3(v.x, v.y, v.z); }
 
-// Algorithm 1. on_leaf(k) is called for every leaf k that satisfies the
-// predicate, in increasing k. Returns false if the walk ran past 2(2n-1)
-// steps or met an id outside the tree (a corrupt tree).
-template <int kP, typename Q, typename F>
+// Algorithm 1. on_leaf(id) is called with the primitive index of every leaf
+// that satisfies the predicate, leaves in increasing sorted position. Returns
+// false if the walk ran past 2(2n-1) steps or met an id outside the tree (a
+// corrupt tree).
+template <typename Q, typename F>
 __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf) {
     const int ni = (int)t.n - 1;
     const uint32_t nodes = 2u * (uint32_t)t.n - 1u;
     const uint32_t max_steps = 2u * nodes;
     int node = 0;
     uint32_t steps = 0;
-    while (node != kSentinel) {
-        if ((uint32_t)node >= nodes || ++steps > max_steps) return false;
-        const bool leaf = node >= ni;
-        const float4 a = __ldg(t.a + node);
-        float4 b = a;  // a point leaf's box is its point
-        if (kP == LBVH_PRIM_BOXES || !leaf) b = __ldg(t.b + node);
+    // the sentinel (-1) and any id outside the tree end the loop
+    while ((uint32_t)node < nodes) {
+        if (++steps > max_steps) return false;
+        const float4 a = __ldg(t.nodes + 2 * node);
+        const float4 b = __ldg(t.nodes + 2 * node + 1);
         const bool hit = hits(q, xyz(a), xyz(b));
-        if (hit && leaf) on_leaf(node - ni);
-        // internal: left child on a hit, else skip; leaf: its skip (in a.w)
-        node = __float_as_int((hit || leaf) ? a.w : b.w);
+        const bool leaf = node >= ni;
+        if (hit && leaf) on_leaf(__float_as_uint(a.w));
+        // internal hit: left child (a.w); miss or leaf: skip (b.w)
+        node = __float_as_int((hit && !leaf) ? a.w : b.w);
     }
-    return true;
+    return node == kSentinel;
 }
 
 constexpr int kSlot = kQueryBufferHits;
@@ -117,28 +121,26 @@ __device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) 
     return qa.order ? (int64_t)__ldg(qa.order + i) : i;
 }
 
-// One walk per query: hit count at the query's index, up to kSlot primitive
-// ids (walk order) in the thread's slot. See the file comment.
+// One walk per query: hit count and up to kSlot primitive ids (walk order) in
+// the query's own slot. See the file comment.
 template <int kQ, int kP>
 __global__ void __launch_bounds__(kThreads)
     collect_kernel(TreeView t, QueryArgs qa, uint32_t *__restrict__ counts,
-                   uint32_t *__restrict__ count_sorted, uint32_t *__restrict__ slots,
-                   uint32_t *__restrict__ overflow_list, Control *ctl) {
+                   uint32_t *__restrict__ slots, uint32_t *__restrict__ overflow_list, Control *ctl) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= qa.nq) return;
     const int64_t qi = thread_query(qa, i);
-    uint32_t *slot = slots + i * kSlot;
+    uint32_t *slot = slots + qi * kSlot;
     uint32_t c = 0;
     if (t.n > 0 && ctl->build_flags == 0) {
         const auto q = QueryOf<kQ>::load(qa, qi);
-        const bool ok = walk<kP>(t, q, [&](int k) {
-            if (c < (uint32_t)kSlot) slot[c] = __ldg(t.perm + k);
+        const bool ok = walk(t, q, [&](uint32_t id) {
+            if (c < (uint32_t)kSlot) slot[c] = id;
             ++c;
         });
         if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
     }
     counts[qi] = c;
-    count_sorted[i] = c;
     if (c > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi;
 }
 
@@ -163,43 +165,42 @@ __device__ __forceinline__ void sort32(uint32_t (&v)[32]) {
     }
 }
 
-// Thread i sorts slot i in registers; the warp then writes its 32 lists to
-// their CSR positions, one list per step, lanes on consecutive hits.
+// Thread q sorts query q's slot in registers; the warp then writes its 32
+// lists, which are adjacent in the CSR, one list per step with lanes on
+// consecutive hits.
 __global__ void __launch_bounds__(kThreads)
-    copy_kernel(int64_t nq, const uint32_t *__restrict__ order,
-                const uint32_t *__restrict__ count_sorted, const int64_t *__restrict__ offsets,
+    copy_kernel(int64_t nq, const uint32_t *__restrict__ counts, const int64_t *__restrict__ offsets,
                 const uint32_t *__restrict__ slots, uint32_t *__restrict__ hits) {
     __shared__ uint32_t s_lists[kThreads / 32][32][kSlot + 1];
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t c = 0;
     int64_t dst = 0;
-    if (i < nq) {
-        c = count_sorted[i];
+    if (q < nq) {
+        c = counts[q];
         if (c > (uint32_t)kSlot) c = 0;  // written by the overflow walk
-        if (c) dst = offsets[order ? (int64_t)__ldg(order + i) : i];
+        dst = offsets[q];
     }
-    if (__any_sync(0xffffffffu, c != 0)) {
-        uint32_t v[kSlot];
-        const uint4 *src = reinterpret_cast<const uint4 *>(slots + i * kSlot);
+    if (!__any_sync(0xffffffffu, c != 0)) return;
+    uint32_t v[kSlot];
+    const uint4 *src = reinterpret_cast<const uint4 *>(slots + q * kSlot);
 #pragma unroll
-        for (int j4 = 0; j4 < kSlot / 4; ++j4) {
-            uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
-            if (4 * j4 < (int)c) w = src[j4];
-            v[4 * j4] = 4 * j4 < (int)c ? w.x : ~0u;
-            v[4 * j4 + 1] = 4 * j4 + 1 < (int)c ? w.y : ~0u;
-            v[4 * j4 + 2] = 4 * j4 + 2 < (int)c ? w.z : ~0u;
-            v[4 * j4 + 3] = 4 * j4 + 3 < (int)c ? w.w : ~0u;
-        }
-        if (c > 1) sort32(v);
+    for (int j4 = 0; j4 < kSlot / 4; ++j4) {
+        uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
+        if (4 * j4 < (int)c) w = src[j4];
+        v[4 * j4] = 4 * j4 < (int)c ? w.x : ~0u;
+        v[4 * j4 + 1] = 4 * j4 + 1 < (int)c ? w.y : ~0u;
+        v[4 * j4 + 2] = 4 * j4 + 2 < (int)c ? w.z : ~0u;
+        v[4 * j4 + 3] = 4 * j4 + 3 < (int)c ? w.w : ~0u;
+    }
+    if (__any_sync(0xffffffffu, c > 1)) sort32(v);
 #pragma unroll
-        for (int j = 0; j < kSlot; ++j) s_lists[warp][lane][j] = v[j];
-        __syncwarp();
-        for (int s = 0; s < 32; ++s) {
-            const uint32_t cs = __shfl_sync(0xffffffffu, c, s);
-            const int64_t ds = __shfl_sync(0xffffffffu, dst, s);
-            if ((uint32_t)lane < cs) hits[ds + lane] = s_lists[warp][s][lane];
-        }
+    for (int j = 0; j < kSlot; ++j) s_lists[warp][lane][j] = v[j];
+    __syncwarp();
+    for (int s = 0; s < 32; ++s) {
+        const uint32_t cs = __shfl_sync(0xffffffffu, c, s);
+        const int64_t ds = __shfl_sync(0xffffffffu, dst, s);
+        if ((uint32_t)lane < cs) hits[ds + lane] = s_lists[warp][s][lane];
     }
 }
 
@@ -216,8 +217,8 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t total = offsets[qi + 1] - base;
     const auto q = QueryOf<kQ>::load(qa, qi);
     int64_t c = 0;
-    walk<kP>(t, q, [&](int k) {
-        if (c < total) hits[base + c] = __ldg(t.perm + k);
+    walk(t, q, [&](uint32_t id) {
+        if (c < total) hits[base + c] = id;
         ++c;
     });
 }
@@ -384,7 +385,7 @@ void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScra
     const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
     dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
         collect_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
-            t, q, qs.counts, qs.count_sorted, qs.slots, qs.overflow_list, ctl);
+            t, q, qs.counts, qs.slots, qs.overflow_list, ctl);
     });
     count_launches(1);
 }
@@ -393,7 +394,7 @@ void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t
                        uint32_t *hits, cudaStream_t s) {
     if (q.nq <= 0) return;
     const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
-    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, q.order, qs.count_sorted, offsets, qs.slots, hits);
+    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, qs.counts, offsets, qs.slots, hits);
     count_launches(1);
 }
 

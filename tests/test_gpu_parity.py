@@ -363,3 +363,16 @@ def test_self_query_reuses_build_order_same_result():
     off_a, hits_a = t.query(boxes, lbvh.BOX)
     off_b, hits_b = t.query(boxes.clone(), lbvh.BOX)
     assert torch.equal(off_a, off_b) and torch.equal(hits_a, hits_b)
+
+
+def test_nan_and_infinite_query_centres():
+    lbvh = L()
+    pts = inputs.uniform_points(5000, seed=32)
+    q = inputs.uniform_points(4000, seed=33)
+    q[::7, 0] = np.nan
+    q[3::11, 2] = np.inf
+    q[5::13, 1] = -np.inf
+    t = gpu_build(pts, lbvh.POINTS, 63)
+    off, hits = t.query(q, lbvh.SPHERE, radius=0.2)
+    o = oracle.build(pts, oracle.POINTS, 63)
+    assert_csr_equal(off, hits, *oracle.query(o, q, oracle.SPHERE, radius=np.float32(0.2)))

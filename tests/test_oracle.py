@@ -429,3 +429,18 @@ def test_checks_catch_planted_mistakes():
     swapped = s.copy(); swapped[[40, 41]] = swapped[[41, 40]]
     if swapped[40] != swapped[41]:
         assert fails(lambda: tc.check_karras_tree(swapped, t["left"], t["right"]))
+
+
+def test_nan_queries_hit_nothing_and_signed_zero_bounds():
+    pts = inputs.uniform_points(300, seed=31)
+    t = oracle.build(pts, oracle.POINTS, 30)
+    q = np.array([[np.nan, 0.5, 0.5], [0.5, 0.5, 0.5], [np.inf, 0.5, 0.5]], np.float32)
+    off, hits = oracle.query(t, q, oracle.SPHERE, radius=10.0)
+    assert np.diff(off).tolist() == [0, 300, 0]
+    off, _ = oracle.query(t, q[1:2], oracle.SPHERE, radius=np.nan)
+    assert off.tolist() == [0, 0]
+    # -0.0 orders below +0.0 in the bounds, whatever the input order
+    for order in ([0.0, -0.0], [-0.0, 0.0]):
+        p = np.array([[v, 1.0, 2.0] for v in order], np.float32)
+        _, b = oracle.morton_codes(p, oracle.POINTS, 30)
+        assert np.signbit(b[0]) and not np.signbit(b[3])
