@@ -120,7 +120,7 @@ struct lbvh_tree_s {
     bool sorted_in_b = false;
     bool store_dirty = false;  // a failed build may have left store words set
     DevBuf keys[2], vals[2];
-    DevBuf nodes, store, lookback, hist, partials, bounds, ctl;
+    DevBuf inodes, leaves, store, lookback, hist, partials, bounds, ctl;
     DevBuf counts, tile_sums, overflow, slots;
     DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
     const float *prims_ptr = nullptr;      // the last build's input (self-queries)
@@ -131,7 +131,7 @@ struct lbvh_tree_s {
     const uint32_t *perm() const { return vals[sorted_in_b ? 1 : 0].as<uint32_t>(); }
     lbvh::Control *dctl() const { return ctl.as<lbvh::Control>(); }
     lbvh::TreeView view() const {
-        return lbvh::TreeView{nodes.as<float4>(), n, kind};
+        return lbvh::TreeView{inodes.as<float4>(), leaves.as<float4>(), n, kind};
     }
 };
 
@@ -167,7 +167,8 @@ lbvh_status reserve_tree(lbvh_tree_s *t, int64_t n, int kind, cudaStream_t s) {
         LBVH_CUDA(t->keys[k].ensure(un * 8, s));
         LBVH_CUDA(t->vals[k].ensure(un * 4, s));
     }
-    LBVH_CUDA(t->nodes.ensure(node_count(n) * 32, s));
+    LBVH_CUDA(t->inodes.ensure(ui * 32, s));
+    LBVH_CUDA(t->leaves.ensure(leaf_float4s(n, kind) * 16, s));
     LBVH_CUDA(t->store.ensure(ui * 8, s, true));
     LBVH_CUDA(t->lookback.ensure((size_t)tiles * kRadix * 4 * 2, s));
     LBVH_CUDA(t->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
@@ -239,7 +240,7 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
 }
 
 lbvh::QueryScratch query_scratch(lbvh_tree_t t) {
-    return lbvh::QueryScratch{t->counts.as<uint32_t>(), t->slots.as<uint32_t>(),
+    return lbvh::QueryScratch{t->counts.as<uint2>(), t->slots.as<uint32_t>(),
                               t->overflow.as<uint32_t>()};
 }
 
@@ -249,7 +250,7 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     using namespace lbvh;
     LBVH_CUDA(cudaStreamWaitEvent(s, t->built, 0));
     const size_t unq = (size_t)qa.nq;
-    LBVH_CUDA(t->counts.ensure(unq * 4 + 4, s));
+    LBVH_CUDA(t->counts.ensure(unq * 8 + 8, s));
     LBVH_CUDA(t->overflow.ensure(unq * 4 + 4, s));
     LBVH_CUDA(t->tile_sums.ensure((size_t)scan_tile_count(qa.nq) * 8 + 8, s));
     LBVH_CUDA(t->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
@@ -266,7 +267,7 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     t->prof.end(LBVH_STAGE_QCOUNT, s);
     LBVH_LAUNCHED();
     t->prof.begin(LBVH_STAGE_QSCAN, s);
-    launch_exclusive_scan(qs.counts, qa.nq, d_offsets, t->tile_sums.as<int64_t>(), c, s);
+    launch_exclusive_scan(qs.count_pos, qa.nq, d_offsets, t->tile_sums.as<int64_t>(), c, s);
     t->prof.end(LBVH_STAGE_QSCAN, s);
     LBVH_LAUNCHED();
     lbvh_status st = read_control(t, s);
@@ -319,7 +320,7 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
     if (!t) return;
     if (t->has_build) cudaStreamSynchronize(t->stream);
     cudaStream_t s = t->stream;
-    for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
+    for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->inodes, &t->leaves,
                       &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                       &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                       &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots})
@@ -371,7 +372,8 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
             for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_CONSTRUCT, s);
-        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->nodes.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
+        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes.as<float4>(),
+                         t->leaves.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
         t->prof.end(LBVH_STAGE_CONSTRUCT, s);
         LBVH_LAUNCHED();
     }
@@ -404,7 +406,8 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
         LBVH_CUDA(cudaMemcpyAsync(t->vals[0].p, d_perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
         launch_bounds(d_prims, n, kind, t->partials.as<float>(), t->bounds.as<float>(), c, s);
         LBVH_LAUNCHED();
-        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->nodes.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
+        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes.as<float4>(),
+                         t->leaves.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
         LBVH_LAUNCHED();
     }
     return finish_build(t, s);
@@ -426,7 +429,7 @@ lbvh_status lbvh_tree_size(lbvh_tree_t t, int64_t *n) {
 lbvh_status lbvh_tree_bytes(lbvh_tree_t t, uint64_t *bytes) {
     if (!t || !bytes) return LBVH_ERR_INVALID;
     uint64_t b = 0;
-    for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
+    for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->inodes, &t->leaves,
                             &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                             &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                             &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots})
@@ -445,22 +448,34 @@ lbvh_status lbvh_tree_export(lbvh_tree_t t, uint32_t *h_perm, uint64_t *h_sorted
     if (h_perm) LBVH_CUDA(cudaMemcpy(h_perm, t->perm(), n * 4, cudaMemcpyDeviceToHost));
     if (h_sorted_codes) LBVH_CUDA(cudaMemcpy(h_sorted_codes, t->sorted_codes(), n * 8, cudaMemcpyDeviceToHost));
     if (h_bounds) LBVH_CUDA(cudaMemcpy(h_bounds, t->bounds.p, 24, cudaMemcpyDeviceToHost));
-    if (h_left || h_skip_internal || h_internal_box || h_skip_leaf || h_leaf_box) {
-        std::vector<float4> nd(lbvh::node_count(n) * 2);
-        LBVH_CUDA(cudaMemcpy(nd.data(), t->nodes.p, nd.size() * 16, cudaMemcpyDeviceToHost));
-        for (int64_t id = 0; id < ni + n; ++id) {
-            const float4 a = nd[2 * id], b = nd[2 * id + 1];
-            int32_t aw, skip;
-            std::memcpy(&aw, &a.w, 4);
+    if (ni > 0 && (h_left || h_skip_internal || h_internal_box)) {
+        std::vector<float4> nodes((size_t)ni * 2);
+        LBVH_CUDA(cudaMemcpy(nodes.data(), t->inodes.p, ni * 32, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < ni; ++k) {
+            const float4 a = nodes[2 * k], b = nodes[2 * k + 1];
+            int32_t left, skip;
+            std::memcpy(&left, &a.w, 4);
             std::memcpy(&skip, &b.w, 4);
-            const float v[6] = {a.x, a.y, a.z, b.x, b.y, b.z};
-            if (id < ni) {
-                if (h_left) h_left[id] = aw;
-                if (h_skip_internal) h_skip_internal[id] = skip;
-                if (h_internal_box) std::memcpy(h_internal_box + 6 * id, v, sizeof v);
-            } else {
-                if (h_skip_leaf) h_skip_leaf[id - ni] = skip;
-                if (h_leaf_box) std::memcpy(h_leaf_box + 6 * (id - ni), v, sizeof v);
+            if (h_left) h_left[k] = left;
+            if (h_skip_internal) h_skip_internal[k] = skip;
+            if (h_internal_box) {
+                const float v[6] = {a.x, a.y, a.z, b.x, b.y, b.z};
+                std::memcpy(h_internal_box + 6 * k, v, sizeof v);
+            }
+        }
+    }
+    if (h_skip_leaf || h_leaf_box) {
+        const int per = t->kind == LBVH_PRIM_POINTS ? 1 : 2;
+        std::vector<float4> leaves((size_t)n * per);
+        LBVH_CUDA(cudaMemcpy(leaves.data(), t->leaves.p, n * 16 * per, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < n; ++k) {
+            const float4 a = leaves[per * k], b = leaves[per * k + per - 1];
+            uint32_t word;
+            std::memcpy(&word, &a.w, 4);
+            if (h_skip_leaf) h_skip_leaf[k] = lbvh::leaf_skip_id(word, (int)k, (int)n);
+            if (h_leaf_box) {
+                const float v[6] = {a.x, a.y, a.z, b.x, b.y, b.z};
+                std::memcpy(h_leaf_box + 6 * k, v, sizeof v);
             }
         }
     }

@@ -60,11 +60,24 @@ __device__ __forceinline__ unsigned long long pack(uint32_t end, uint32_t d, uin
     return (1ull << 63) | ((unsigned long long)dn << 40) | ((unsigned long long)d << 32) | end;
 }
 
-__device__ __forceinline__ void load_node_box(const float4 *nodes, int id, float3 &lo, float3 &hi) {
-    const float4 a = __ldcg(nodes + 2 * (int64_t)id);
-    const float4 b = __ldcg(nodes + 2 * (int64_t)id + 1);
-    lo = make_float3(a.x, a.y, a.z);
-    hi = make_float3(b.x, b.y, b.z);
+template <int kKind>
+__device__ __forceinline__ void load_node_box(const float4 *inodes, const float4 *leaves, int ni,
+                                              int id, float3 &lo, float3 &hi) {
+    if (id < ni) {
+        const float4 a = __ldcg(inodes + 2 * (int64_t)id);
+        const float4 b = __ldcg(inodes + 2 * (int64_t)id + 1);
+        lo = make_float3(a.x, a.y, a.z);
+        hi = make_float3(b.x, b.y, b.z);
+    } else if (kKind == LBVH_PRIM_POINTS) {
+        const float4 a = __ldcg(leaves + (id - ni));
+        lo = make_float3(a.x, a.y, a.z);
+        hi = lo;
+    } else {
+        const float4 a = __ldcg(leaves + 2 * (int64_t)(id - ni));
+        const float4 b = __ldcg(leaves + 2 * (int64_t)(id - ni) + 1);
+        lo = make_float3(a.x, a.y, a.z);
+        hi = make_float3(b.x, b.y, b.z);
+    }
 }
 
 // The exchange on store[p] publishes this thread's finished node (release)
@@ -86,7 +99,7 @@ __device__ __forceinline__ unsigned long long publish_exchange(unsigned long lon
 template <int kKind, bool kAcqRel>
 __global__ void __launch_bounds__(kThreads)
     construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
-                     const float *__restrict__ prims, int n, float4 *nodes,
+                     const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
                      unsigned long long *store, uint32_t *flags) {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
@@ -119,9 +132,14 @@ __global__ void __launch_bounds__(kThreads)
         lo = make_float3(b[0], b[1], b[2]);
         hi = make_float3(b[3], b[4], b[5]);
     }
-    const int64_t leaf_id = ni + i;
-    nodes[2 * leaf_id] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(p_id));
-    nodes[2 * leaf_id + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(leaf_skip));
+    // the leaf's skip is position i+1: one bit says I_{i+1} rather than L_{i+1}
+    const uint32_t word = p_id | (leaf_skip >= 0 && leaf_skip < ni ? kLeafSkipInternal : 0u);
+    if (kKind == LBVH_PRIM_POINTS) {
+        leaves[i] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
+    } else {
+        leaves[2 * (int64_t)i] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
+        leaves[2 * (int64_t)i + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
+    }
     if (n == 1) return;
 
     // ---- climb
@@ -156,7 +174,7 @@ __global__ void __launch_bounds__(kThreads)
             sibling = (l == p) ? ni + (int)p : (int)p;
         }
         float3 slo, shi;
-        load_node_box(nodes, sibling, slo, shi);
+        load_node_box<kKind>(inodes, leaves, ni, sibling, slo, shi);
         lo = make_float3(min_ordered(lo.x, slo.x), min_ordered(lo.y, slo.y), min_ordered(lo.z, slo.z));
         hi = make_float3(max_ordered(hi.x, shi.x), max_ordered(hi.y, shi.y), max_ordered(hi.z, shi.z));
 
@@ -164,8 +182,8 @@ __global__ void __launch_bounds__(kThreads)
         const int left_child = (l == p) ? ni + (int)p : (int)p;
         const int skip = (r == (uint32_t)(n - 1)) ? kSentinel
                                                  : (d_right < d_next ? ni + (int)r + 1 : (int)r + 1);
-        nodes[2 * (int64_t)q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
-        nodes[2 * (int64_t)q + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
+        inodes[2 * (int64_t)q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
+        inodes[2 * (int64_t)q + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
         if (q == 0) return;  // the root
     }
     atomicOr(flags, kFlagCorrupt);
@@ -174,8 +192,8 @@ __global__ void __launch_bounds__(kThreads)
 }  // namespace
 
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
-                      int64_t n, int kind, float4 *nodes, unsigned long long *store,
-                      uint32_t *flags, cudaStream_t s) {
+                      int64_t n, int kind, float4 *inodes, float4 *leaves,
+                      unsigned long long *store, uint32_t *flags, cudaStream_t s) {
     if (n <= 0) return;
     // LBVH_CONSTRUCT_FENCES=1 selects the fence form of the exchange (tuning)
     static const bool fences = getenv("LBVH_CONSTRUCT_FENCES") && atoi(getenv("LBVH_CONSTRUCT_FENCES"));
@@ -183,7 +201,7 @@ void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const 
     auto k = kind == LBVH_PRIM_POINTS
                  ? (fences ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_POINTS, true>)
                  : (fences ? construct_kernel<LBVH_PRIM_BOXES, false> : construct_kernel<LBVH_PRIM_BOXES, true>);
-    k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, nodes, store, flags);
+    k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags);
     count_launches(1);
 }
 

@@ -47,15 +47,28 @@ __device__ __forceinline__ float max_ordered(float a, float b) {
 }
 
 // ---------------------------------------------------------------- node layout
-// One 32-byte record (two float4) per node, indexed by canonical id
-// (internal k -> k, leaf k -> (n-1)+k, sentinel -> -1), so that a walk step
-// touches one sector and runs the same code for every node:
-//   nodes[2 id]      {lo.x, lo.y, lo.z, left}   leaf: {lo.xyz, primitive index}
-//   nodes[2 id + 1]  {hi.x, hi.y, hi.z, skip}   leaf: {hi.xyz, skip}
-// A point leaf has lo == hi. left/skip/index are stored as int bits.
+// Canonical ids: internal k -> k, leaf k -> (n-1)+k, sentinel -> -1.
+// Internal node k: one 32-byte record (two float4) in `inodes`:
+//   inodes[2k]      {lo.x, lo.y, lo.z, left}
+//   inodes[2k + 1]  {hi.x, hi.y, hi.z, skip}
+// Leaf k: the skip of a leaf is always position k+1 (Algorithm 2): L_{k+1}
+// or I_{k+1}, or the sentinel for k = n-1, so it needs one bit. One word
+// carries the primitive index and that bit:
+//   word = perm[k] | (skip is I_{k+1} ? kLeafSkipInternal : 0)
+//   points: leaves[k]      {x, y, z, word}                 (16 bytes)
+//   boxes:  leaves[2k]     {lo.xyz, word}, leaves[2k+1] {hi.xyz, 0}
+// left/skip/word are stored as int bits.
 constexpr int kSentinel = -1;
+constexpr uint32_t kLeafSkipInternal = 1u << 31;
+constexpr uint32_t kLeafIndexMask = kLeafSkipInternal - 1u;
 
-inline size_t node_count(int64_t n) { return (size_t)(n > 0 ? 2 * n - 1 : 0); }
+inline size_t leaf_float4s(int64_t n, int kind) { return (size_t)n * (kind == LBVH_PRIM_POINTS ? 1 : 2); }
+
+// Skip id of leaf k from its word.
+__host__ __device__ __forceinline__ int leaf_skip_id(uint32_t word, int k, int n) {
+    if (k == n - 1) return kSentinel;
+    return (word & kLeafSkipInternal) ? k + 1 : (n - 1) + k + 1;
+}
 
 // ---------------------------------------------------------------- radix sort
 constexpr int kRadixBits = 8;
@@ -102,16 +115,17 @@ void launch_encode(const float *prims, int64_t n, int kind, int bits, const floa
                    uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
 
 // ---------------------------------------------------------------- construct
-// Algorithm 4 with boxes: writes `nodes` (layout above), and uses
+// Algorithm 4 with boxes: writes inodes and leaves (layout above), and uses
 // `store` (n-1 words, all zero on entry; left all zero on exit).
 // flags: kFlagCorrupt is latched if the input is not a sorted permutation.
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
-                      int64_t n, int kind, float4 *nodes, unsigned long long *store,
-                      uint32_t *flags, cudaStream_t s);
+                      int64_t n, int kind, float4 *inodes, float4 *leaves,
+                      unsigned long long *store, uint32_t *flags, cudaStream_t s);
 
 // ---------------------------------------------------------------- query
 struct TreeView {
-    const float4 *nodes;
+    const float4 *inodes;
+    const float4 *leaves;
     int64_t n;
     int kind;
 };
@@ -124,16 +138,17 @@ struct QueryArgs {
     const uint32_t *order;  // null: thread i walks query i; else query order[i]
 };
 struct QueryScratch {
-    uint32_t *counts;         // nq, hits of query q
-    uint32_t *slots;          // nq * kQueryBufferHits: query q's first hits, walk order
+    uint2 *count_pos;         // nq: (hits of query q, walk position i of q)
+    uint32_t *slots;          // nq * kQueryBufferHits: first hits of walk position i, walk order
     uint32_t *overflow_list;  // nq, queries to walk a second time
 };
 // The collecting walk (counts, short sorted lists, overflow list).
 void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
                           cudaStream_t s);
-// offsets[0..nq] = exclusive scan of counts (offsets[nq] = total = ctl->total).
+// offsets[0..nq] = exclusive scan of count_pos[.].x (offsets[nq] = total =
+// ctl->total).
 int64_t scan_tile_count(int64_t nq);
-void launch_exclusive_scan(const uint32_t *counts, int64_t nq, int64_t *offsets,
+void launch_exclusive_scan(const uint2 *count_pos, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s);
 // Short lists from the scratch buffer to their CSR positions.
 void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,

@@ -3,9 +3,10 @@
 // Each thread walks the tree for one query: start at the root (id 0); when
 // the predicate holds on an internal node go to its left child, on a leaf
 // report it and go to its skip; when it fails go to the skip; stop at the
-// sentinel. Every step runs the same code for internal nodes and leaves: the
-// node's 32-byte record (one sector: lo + left or primitive index, hi + skip),
-// the box test, and a select.
+// sentinel. Every step runs the same code for internal nodes and leaves: a
+// 16-byte load (internal: lo + left; point leaf: xyz + index word), a second
+// one for internal nodes and box leaves (hi + skip), the box test, and a
+// select. A leaf's skip is position k+1, leaf or internal by one bit.
 //
 // Predicates (closed, FP32, fixed operation order, no fused multiply-add):
 //   sphere  e_a = max(lo_a - c_a, c_a - hi_a, 0); d2 = (ex*ex + ey*ey) + ez*ez;
@@ -22,9 +23,9 @@
 //
 // CSR in one walk:
 //   collect   thread i walks query q = order[i] and writes up to
-//             kQueryBufferHits primitive ids, in walk order, into q's slot of
-//             a scratch array (no shared memory: L1 stays with the tree), and
-//             q's hit count.
+//             kQueryBufferHits primitive ids, in walk order, into slot i of a
+//             scratch array (no shared memory: L1 stays with the tree), and
+//             (hit count, i) at q.
 //   scan      exclusive scan of the counts -> offsets, total (host reads it).
 //   copy      in query order: each thread loads one slot into registers and
 //             sorts it with a bitonic network; the warp writes its 32 lists,
@@ -94,23 +95,28 @@ __device__ __forceinline__ float3 xyz(float4 v) { return make_float3(v.x, v.y, v
 // that satisfies the predicate, leaves in increasing sorted position. Returns
 // false if the walk ran past 2(2n-1) steps or met an id outside the tree (a
 // corrupt tree).
-template <typename Q, typename F>
+template <int kP, typename Q, typename F>
 __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf) {
-    const int ni = (int)t.n - 1;
-    const uint32_t nodes = 2u * (uint32_t)t.n - 1u;
+    const int n = (int)t.n;
+    const int ni = n - 1;
+    const uint32_t nodes = 2u * (uint32_t)n - 1u;
     const uint32_t max_steps = 2u * nodes;
     int node = 0;
     uint32_t steps = 0;
     // the sentinel (-1) and any id outside the tree end the loop
     while ((uint32_t)node < nodes) {
         if (++steps > max_steps) return false;
-        const float4 a = __ldg(t.nodes + 2 * node);
-        const float4 b = __ldg(t.nodes + 2 * node + 1);
-        const bool hit = hits(q, xyz(a), xyz(b));
         const bool leaf = node >= ni;
-        if (hit && leaf) on_leaf(__float_as_uint(a.w));
-        // internal hit: left child (a.w); miss or leaf: skip (b.w)
-        node = __float_as_int((hit && !leaf) ? a.w : b.w);
+        const int k = node - ni;
+        const float4 *rec = leaf ? t.leaves + (kP == LBVH_PRIM_POINTS ? k : 2 * k) : t.inodes + 2 * node;
+        const float4 a = __ldg(rec);
+        float4 b = a;  // a point leaf's box is its point
+        if (kP == LBVH_PRIM_BOXES || !leaf) b = __ldg(rec + 1);
+        const bool hit = hits(q, xyz(a), xyz(b));
+        const uint32_t word = __float_as_uint(a.w);
+        if (hit && leaf) on_leaf(word & kLeafIndexMask);
+        // internal: left child on a hit, else skip; leaf: position k+1
+        node = leaf ? leaf_skip_id(word, k, n) : __float_as_int(hit ? a.w : b.w);
     }
     return node == kSentinel;
 }
@@ -122,25 +128,25 @@ __device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) 
 }
 
 // One walk per query: hit count and up to kSlot primitive ids (walk order) in
-// the query's own slot. See the file comment.
+// the slot of the walk position. See the file comment.
 template <int kQ, int kP>
 __global__ void __launch_bounds__(kThreads)
-    collect_kernel(TreeView t, QueryArgs qa, uint32_t *__restrict__ counts,
+    collect_kernel(TreeView t, QueryArgs qa, uint2 *__restrict__ count_pos,
                    uint32_t *__restrict__ slots, uint32_t *__restrict__ overflow_list, Control *ctl) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= qa.nq) return;
     const int64_t qi = thread_query(qa, i);
-    uint32_t *slot = slots + qi * kSlot;
+    uint32_t *slot = slots + i * kSlot;
     uint32_t c = 0;
     if (t.n > 0 && ctl->build_flags == 0) {
         const auto q = QueryOf<kQ>::load(qa, qi);
-        const bool ok = walk(t, q, [&](uint32_t id) {
+        const bool ok = walk<kP>(t, q, [&](uint32_t id) {
             if (c < (uint32_t)kSlot) slot[c] = id;
             ++c;
         });
         if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
     }
-    counts[qi] = c;
+    count_pos[qi] = make_uint2(c, (uint32_t)i);
     if (c > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi;
 }
 
@@ -169,21 +175,22 @@ __device__ __forceinline__ void sort32(uint32_t (&v)[32]) {
 // lists, which are adjacent in the CSR, one list per step with lanes on
 // consecutive hits.
 __global__ void __launch_bounds__(kThreads)
-    copy_kernel(int64_t nq, const uint32_t *__restrict__ counts, const int64_t *__restrict__ offsets,
+    copy_kernel(int64_t nq, const uint2 *__restrict__ count_pos, const int64_t *__restrict__ offsets,
                 const uint32_t *__restrict__ slots, uint32_t *__restrict__ hits) {
     __shared__ uint32_t s_lists[kThreads / 32][32][kSlot + 1];
     const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t c = 0;
-    int64_t dst = 0;
+    int64_t dst = 0, pos = 0;
     if (q < nq) {
-        c = counts[q];
-        if (c > (uint32_t)kSlot) c = 0;  // written by the overflow walk
+        const uint2 cp = count_pos[q];
+        c = cp.x > (uint32_t)kSlot ? 0u : cp.x;  // longer lists: the overflow walk
+        pos = cp.y;
         dst = offsets[q];
     }
     if (!__any_sync(0xffffffffu, c != 0)) return;
     uint32_t v[kSlot];
-    const uint4 *src = reinterpret_cast<const uint4 *>(slots + q * kSlot);
+    const uint4 *src = reinterpret_cast<const uint4 *>(slots + pos * kSlot);
 #pragma unroll
     for (int j4 = 0; j4 < kSlot / 4; ++j4) {
         uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
@@ -217,7 +224,7 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t total = offsets[qi + 1] - base;
     const auto q = QueryOf<kQ>::load(qa, qi);
     int64_t c = 0;
-    walk(t, q, [&](uint32_t id) {
+    walk<kP>(t, q, [&](uint32_t id) {
         if (c < total) hits[base + c] = id;
         ++c;
     });
@@ -248,13 +255,13 @@ __device__ __forceinline__ int64_t block_scan_exclusive(int64_t v, int64_t *s_wa
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-    scan_reduce_kernel(const uint32_t *__restrict__ counts, int64_t nq, int64_t *tile_sums) {
+    scan_reduce_kernel(const uint2 *__restrict__ counts, int64_t nq, int64_t *tile_sums) {
     __shared__ int64_t s_warp[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t sum = 0;
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = base + j * kScanThreads + threadIdx.x;
-        if (i < nq) sum += counts[i];
+        if (i < nq) sum += counts[i].x;
     }
     int64_t total;
     block_scan_exclusive(sum, s_warp, total);
@@ -281,7 +288,7 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-    scan_apply_kernel(const uint32_t *__restrict__ counts, int64_t nq,
+    scan_apply_kernel(const uint2 *__restrict__ counts, int64_t nq,
                       const int64_t *__restrict__ tile_sums, int64_t *__restrict__ offsets) {
     __shared__ int64_t s_warp[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(kScanThreads)
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = first + j;
-        c[j] = i < nq ? counts[i] : 0u;
+        c[j] = i < nq ? counts[i].x : 0u;
         sum += c[j];
     }
     int64_t total;
@@ -385,7 +392,7 @@ void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScra
     const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
     dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
         collect_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
-            t, q, qs.counts, qs.slots, qs.overflow_list, ctl);
+            t, q, qs.count_pos, qs.slots, qs.overflow_list, ctl);
     });
     count_launches(1);
 }
@@ -394,7 +401,7 @@ void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t
                        uint32_t *hits, cudaStream_t s) {
     if (q.nq <= 0) return;
     const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
-    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, qs.counts, offsets, qs.slots, hits);
+    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, qs.count_pos, offsets, qs.slots, hits);
     count_launches(1);
 }
 
@@ -412,7 +419,7 @@ void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScr
 
 int64_t scan_tile_count(int64_t nq) { return (nq + kScanTile - 1) / kScanTile; }
 
-void launch_exclusive_scan(const uint32_t *counts, int64_t nq, int64_t *offsets,
+void launch_exclusive_scan(const uint2 *counts, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s) {
     const int64_t tiles = scan_tile_count(nq);
     if (tiles > 0)
