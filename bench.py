@@ -71,6 +71,8 @@ WORKLOADS = {
     # name: (description, n, bits, kind, generator)
     "uniform_2^25_63bit": ("2^25 FP32 points uniform in [0,1)^3, 63-bit Morton codes; build + 2^25 sphere "
                            "queries at the points, radius for 16 expected neighbours", 1 << 25, 63),
+    "uniform_2^24_63bit": ("2^24 FP32 points uniform in [0,1)^3, 63-bit Morton codes; build + 2^24 sphere "
+                           "queries at the points, radius for 16 expected neighbours (profiling case)", 1 << 24, 63),
     "uniform_16384_30bit": ("16,384 FP32 points uniform in [0,1)^3 (seed 0), 30-bit codes; build + 16,384 "
                             "sphere queries at the points, radius for 16 expected neighbours", 16384, 30),
 }

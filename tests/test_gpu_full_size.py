@@ -1,0 +1,88 @@
+"""Parity at the full benchmark sizes, in the launch configuration bench.py
+times (default sort tile shape, Morton-ordered queries in their own buffer).
+
+The whole tree is compared with the oracle's, element by element; queries are
+checked on a seeded sample against the oracle, and every query's CSR list is
+checked for properties that hold at any size (ascending ids, the query's own
+primitive present for queries centred at the points).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_00665_gb300 import _build, inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+N = 1 << 25
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    _build.build()
+    from paper_2402_00665_gb300 import lbvh
+    return lbvh.load()
+
+
+def assert_tree_equal(g, o):
+    for k in ("perm", "sorted", "left", "skip_internal", "skip_leaf"):
+        assert np.array_equal(g[k], o[k]), k
+    for k in ("internal_box", "leaf_box", "bounds"):
+        assert np.array_equal(np.asarray(g[k]).view(np.uint32), np.asarray(o[k]).view(np.uint32)), k
+
+
+def sampled_csr_check(off, hits, o, queries, qkind, radius, sample):
+    off = off.cpu().numpy()
+    hits = hits.cpu().numpy().view(np.uint32)
+    assert off[0] == 0 and np.all(np.diff(off) >= 0) and off[-1] == hits.size
+    qs = queries[sample]
+    ooff, ohits = oracle.query(o, qs, qkind, radius=radius)
+    for j, q in enumerate(sample):
+        got = hits[off[q]:off[q + 1]]
+        want = ohits[ooff[j]:ooff[j + 1]]
+        assert np.array_equal(got, want), f"query {q}"
+    return off, hits
+
+
+def test_full_uniform_points_2pow25_63bit():
+    from paper_2402_00665_gb300 import lbvh
+    pts = inputs.uniform_points(N, seed=0)
+    r = inputs.radius_for_neighbours(N)
+    dpts = torch.from_numpy(pts).cuda()
+    dq = dpts.clone()
+    t = lbvh.Tree().build(dpts, lbvh.POINTS, 63)
+    t.check()
+    o = oracle.build(pts, oracle.POINTS, 63)
+    assert_tree_equal(t.export(), o)
+    off, hits = t.query(dq, lbvh.SPHERE, radius=float(r), capacity=20 * N)
+    sample = np.random.default_rng(7).choice(N, size=4096, replace=False)
+    off, hits = sampled_csr_check(off, hits, o, pts, oracle.SPHERE, r, sample)
+    # every list ascending, and each query (centred at point q) contains q
+    seg = np.repeat(np.arange(N), np.diff(off))
+    assert np.all((np.diff(hits.astype(np.int64)) > 0) | (np.diff(seg) != 0))
+    has_self = np.zeros(N, bool)
+    has_self[seg[hits == seg]] = True
+    assert has_self.all()
+    assert 15.0 < hits.size / N < 18.0
+
+
+@pytest.mark.parametrize("bits", [30, 63])
+def test_full_mixture_boxes_2pow25(bits):
+    from paper_2402_00665_gb300 import lbvh
+    boxes = inputs.gaussian_mixture_boxes(N, seed=0)
+    queries = inputs.gaussian_mixture_boxes(N // 2, seed=1, component_seed=0)
+    t = lbvh.Tree().build(boxes, lbvh.BOXES, bits)
+    t.check()
+    o = oracle.build(boxes, oracle.BOXES, bits)
+    if bits == 30:
+        assert len(np.unique(o["sorted"])) < N // 2  # many duplicate codes: tie-break stress
+    assert_tree_equal(t.export(), o)
+    off, hits = t.query(torch.from_numpy(queries).cuda(), lbvh.BOX, capacity=16 * N)
+    sample = np.random.default_rng(8).choice(N // 2, size=2048, replace=False)
+    sampled_csr_check(off, hits, o, queries, oracle.BOX, 0.0, sample)
