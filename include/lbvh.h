@@ -176,6 +176,43 @@ lbvh_status lbvh_sort_pairs(const uint64_t *d_keys, const uint32_t *d_vals, int6
                             int key_bits, uint64_t *d_keys_out, uint32_t *d_vals_out,
                             lbvh_stream_t stream);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* Largest n accepted by lbvh_construct_static. */
+#define LBVH_STATIC_MAX_PRIMS ((int64_t)((1 << 20) + 1))
+
+/* The bottom-up pass of lbvh_build_from_sorted (nodes, boxes, skip
+ * connections from sorted codes) without any device allocation. The paper has
+ * no counterpart: this entry point exists for callers that may not allocate
+ * device memory through this library -- for example a host application whose
+ * own pool allocator owns the whole device heap and forbids other
+ * allocations, or a code path that must not call cudaMalloc / cudaFree
+ * because those synchronise the device. The caller passes every input and
+ * output buffer; the scratch words of the merge live in a file-scope device
+ * array of LBVH_STATIC_MAX_PRIMS - 1 64-bit words (8 MiB) that every GPU which
+ * loads this library keeps until the process exits.
+ *   d_sorted_codes uint64[n] ascending; d_perm uint32[n] primitive index of
+ *     each sorted position; d_prims float[n][3] points or float[n][6] boxes.
+ *   1 <= n <= LBVH_STATIC_MAX_PRIMS, else LBVH_ERR_INVALID (nothing runs).
+ *   d_inodes float4[2(n-1)] out (may be NULL when n == 1): internal node k =
+ *     {lo.x, lo.y, lo.z, left}, {hi.x, hi.y, hi.z, skip}, ids as int bits.
+ *   d_leaves out: points float4[n] = {x, y, z, word}; boxes float4[2n] =
+ *     {lo.xyz, word}, {hi.xyz, 0}; word (uint32 bits) = primitive index |
+ *     (1u << 31 if the leaf's skip is internal node k+1, else leaf k+1; the
+ *     last leaf's skip is the sentinel).
+ *   d_flags uint32 device word or NULL: bit 2 is set if the codes/perm are not
+ *     a sorted permutation (the outputs are then invalid). The caller clears it.
+ * Asynchronous on `stream`; allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library call). The first call on a device looks up the device
+ * address of the scratch array (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture. Each call
+ * clears the scratch words it uses; calls that overlap on the GPU (on
+ * different streams, or from different threads) share the one array and race,
+ * so serialise them. */
+lbvh_status lbvh_construct_static(const uint64_t *d_sorted_codes, const uint32_t *d_perm,
+                                  const float *d_prims, int64_t n, int kind, float *d_inodes,
+                                  float *d_leaves, uint32_t *d_flags, lbvh_stream_t stream);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Stage ids of lbvh_tree_stage_times (device time of one kernel launch, or of

@@ -37,6 +37,7 @@
 #include <cuda/atomic>
 
 #include <cstdlib>
+#include <mutex>
 
 #include "lbvh_internal.cuh"
 
@@ -206,3 +207,69 @@ void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const 
 }
 
 }  // namespace lbvh
+
+// ---------------------------------------------------------------- no-allocation variant
+//
+// lbvh_construct_static runs the same construct kernel as the tree builds,
+// with Algorithm 4's `store` words in a file-scope device array instead of
+// memory the library allocates. The array is as large as the biggest tree the
+// entry point accepts, and every GPU that loads this library holds it until
+// the process exits.
+namespace {
+
+constexpr int64_t kStaticMaxPrims = (int64_t(1) << 20) + 1;  // store words: n - 1 <= 2^20 (8 MiB)
+
+__device__ __align__(256) unsigned long long g_static_store[kStaticMaxPrims - 1];
+__device__ __align__(256) uint32_t g_static_flags[64];
+
+// Device addresses of the two arrays, looked up once per device (with that
+// device current) and kept; host code must not use the symbols themselves.
+struct StaticScratch {
+    unsigned long long *store = nullptr;
+    uint32_t *flags = nullptr;
+};
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+StaticScratch g_static[kMaxDevices];
+
+lbvh_status static_scratch(StaticScratch *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBVH_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    StaticScratch &s = g_static[dev];
+    if (!s.store) {
+        void *store = nullptr, *flags = nullptr;
+        if (cudaGetSymbolAddress(&store, g_static_store) != cudaSuccess) return LBVH_ERR_CUDA;
+        if (cudaGetSymbolAddress(&flags, g_static_flags) != cudaSuccess) return LBVH_ERR_CUDA;
+        s.store = static_cast<unsigned long long *>(store);
+        s.flags = static_cast<uint32_t *>(flags);
+    }
+    *out = s;
+    return LBVH_OK;
+}
+
+}  // namespace
+
+extern "C" lbvh_status lbvh_construct_static(const uint64_t *d_sorted_codes, const uint32_t *d_perm,
+                                             const float *d_prims, int64_t n, int kind, float *d_inodes,
+                                             float *d_leaves, uint32_t *d_flags, lbvh_stream_t stream) {
+    if (n < 1 || n > kStaticMaxPrims) return LBVH_ERR_INVALID;
+    if (kind != LBVH_PRIM_POINTS && kind != LBVH_PRIM_BOXES) return LBVH_ERR_INVALID;
+    if (!d_sorted_codes || !d_perm || !d_prims || !d_leaves || (n > 1 && !d_inodes)) return LBVH_ERR_INVALID;
+    StaticScratch scratch;
+    const lbvh_status st = static_scratch(&scratch);
+    if (st != LBVH_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // every call shares the array: the store words must start empty (zero)
+    if (n > 1 && cudaMemsetAsync(scratch.store, 0, (size_t)(n - 1) * sizeof(unsigned long long), s) != cudaSuccess)
+        return LBVH_ERR_CUDA;
+    uint32_t *flags = d_flags;
+    if (!flags) {
+        flags = scratch.flags;
+        if (cudaMemsetAsync(flags, 0, sizeof(uint32_t), s) != cudaSuccess) return LBVH_ERR_CUDA;
+    }
+    lbvh::launch_construct(d_sorted_codes, d_perm, d_prims, n, kind, reinterpret_cast<float4 *>(d_inodes),
+                           reinterpret_cast<float4 *>(d_leaves), scratch.store, flags, s);
+    return cudaGetLastError() == cudaSuccess ? LBVH_OK : LBVH_ERR_CUDA;
+}
+

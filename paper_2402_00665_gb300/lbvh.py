@@ -45,6 +45,7 @@ SIGNATURES = {
     "lbvh_free": (None, [_P]),
     "lbvh_morton_codes": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "lbvh_sort_pairs": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
     "lbvh_tree_stage_times": (_I32, [_P, _P]),
     "lbvh_stage_name": (ctypes.c_char_p, [_I32]),
