@@ -128,9 +128,11 @@ lbvh_status lbvh_tree_export(lbvh_tree_t tree, uint32_t *h_perm, uint64_t *h_sor
  * results in caller-owned CSR buffers.
  *   d_queries  sphere centres float[nq][3] or boxes float[nq][6].
  *   qkind      lbvh_query_kind. Sphere: closed ball, hit iff the squared
- *              distance from the centre to the primitive's box, summed over
- *              x, y, z in that order in FP32 without fused multiply-add, is
- *              <= r*r. Box: closed overlap on all three axes.
+ *              distance from the centre to the primitive's box is <= r*r,
+ *              in FP32: d2 = ex*ex, then + ey*ey and + ez*ez each as one
+ *              fused multiply-add (e = the centre's gap to the box on that
+ *              axis); a NaN centre coordinate or radius hits nothing. Box:
+ *              closed overlap on all three axes.
  *   d_radii    float[nq] per-query radius, or NULL to use `radius` for all
  *              (`radius` must then be finite and >= 0).
  *   d_offsets  int64[nq+1]: hits of query q are d_hits[d_offsets[q] ..

@@ -7,8 +7,8 @@
  * load it; the product path never does. It shares no code with the CUDA path.
  *
  * Build: plain C99, -O2 -ffp-contract=off, so that every float operation is
- * one IEEE-754 single-precision operation rounded to nearest (no fused
- * multiply-add), exactly as written below.
+ * one IEEE-754 single-precision operation rounded to nearest exactly as
+ * written below (fused multiply-add only where fmaf is called).
  *
  * The method's result is exact: for distinct augmented keys the binary radix
  * tree is unique (Sec. 3.1), and the stackless traversal reports exactly the
@@ -40,9 +40,10 @@
  *   Boxes         Sec. 3.1 step 4: union of the children's boxes. Min and
  *                 max (here and in the bounds) order -0.0 below +0.0.
  *   Queries       Algorithm 1. Sphere: closed ball; squared distance from the
- *                 centre to the box, axes x, y, z summed in that order with
- *                 separate multiply and add; a NaN centre coordinate or radius
- *                 hits nothing. Box: closed overlap test.
+ *                 centre to the box, axes x, y, z accumulated in that order,
+ *                 ex*ex rounded, then each further term added with one fused
+ *                 multiply-add; a NaN centre coordinate or radius hits
+ *                 nothing. Box: closed overlap test.
  */
 #include "lbvh_oracle.h"
 
@@ -388,7 +389,7 @@ int oracle_build(const float *prims, int64_t n, int kind, int bits, uint64_t *co
 /* ------------------------------------------------------------------ */
 
 /* Closed ball against a closed box. Per axis the gap is
- * e = max(lo - c, c - hi, 0); d2 = (ex*ex + ey*ey) + ez*ez. */
+ * e = max(lo - c, c - hi, 0); d2 = fma(ez, ez, fma(ey, ey, ex*ex)). */
 static int sphere_box_r2(const float *c, float r2, const float *box) {
     float e[3];
     for (int a = 0; a < 3; ++a) {
@@ -397,11 +398,11 @@ static int sphere_box_r2(const float *c, float r2, const float *box) {
         float above = c[a] - box[3 + a];
         e[a] = fmaxf(fmaxf(below, above), 0.0f);
     }
-    float sx = e[0] * e[0];
-    float sy = e[1] * e[1];
-    float sz = e[2] * e[2];
-    float d2 = sx + sy;
-    d2 = d2 + sz;
+    /* d2 = ex*ex, then + ey*ey and + ez*ez each as one fused multiply-add
+     * (a single rounding per step) */
+    float d2 = e[0] * e[0];
+    d2 = fmaf(e[1], e[1], d2);
+    d2 = fmaf(e[2], e[2], d2);
     return d2 <= r2;
 }
 

@@ -120,7 +120,7 @@ struct lbvh_tree_s {
     bool sorted_in_b = false;
     bool store_dirty = false;  // a failed build may have left store words set
     DevBuf keys[2], vals[2];
-    DevBuf inodes, leaves, store, lookback, hist, partials, bounds, ctl;
+    DevBuf nodes, store, lookback, hist, partials, bounds, ctl;
     DevBuf counts, tile_sums, overflow, slots;
     DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
     const float *prims_ptr = nullptr;      // the last build's input (self-queries)
@@ -131,7 +131,11 @@ struct lbvh_tree_s {
     const uint32_t *perm() const { return vals[sorted_in_b ? 1 : 0].as<uint32_t>(); }
     lbvh::Control *dctl() const { return ctl.as<lbvh::Control>(); }
     lbvh::TreeView view() const {
-        return lbvh::TreeView{inodes.as<float4>(), leaves.as<float4>(), n, kind};
+        return lbvh::TreeView{inodes(), leaves(), n, kind};
+    }
+    // internal records, then the leaves (one allocation)
+    float4 *inodes() const { return nodes.as<float4>(); }
+    float4 *leaves() const { return nodes.as<float4>() + 2 * (n > 0 ? n - 1 : 0);
     }
 };
 
@@ -167,8 +171,7 @@ lbvh_status reserve_tree(lbvh_tree_s *t, int64_t n, int kind, cudaStream_t s) {
         LBVH_CUDA(t->keys[k].ensure(un * 8, s));
         LBVH_CUDA(t->vals[k].ensure(un * 4, s));
     }
-    LBVH_CUDA(t->inodes.ensure(ui * 32, s));
-    LBVH_CUDA(t->leaves.ensure(leaf_float4s(n, kind) * 16, s));
+    LBVH_CUDA(t->nodes.ensure(ui * 32 + leaf_float4s(n, kind) * 16, s));
     LBVH_CUDA(t->store.ensure(ui * 8, s, true));
     LBVH_CUDA(t->lookback.ensure((size_t)tiles * kRadix * 4 * 2, s));
     LBVH_CUDA(t->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
@@ -320,7 +323,7 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
     if (!t) return;
     if (t->has_build) cudaStreamSynchronize(t->stream);
     cudaStream_t s = t->stream;
-    for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->inodes, &t->leaves,
+    for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
                       &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                       &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                       &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots})
@@ -372,8 +375,8 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
             for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_CONSTRUCT, s);
-        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes.as<float4>(),
-                         t->leaves.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
+        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(),
+                         t->leaves(), t->store.as<unsigned long long>(), &c->build_flags, s);
         t->prof.end(LBVH_STAGE_CONSTRUCT, s);
         LBVH_LAUNCHED();
     }
@@ -406,8 +409,8 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
         LBVH_CUDA(cudaMemcpyAsync(t->vals[0].p, d_perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
         launch_bounds(d_prims, n, kind, t->partials.as<float>(), t->bounds.as<float>(), c, s);
         LBVH_LAUNCHED();
-        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes.as<float4>(),
-                         t->leaves.as<float4>(), t->store.as<unsigned long long>(), &c->build_flags, s);
+        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(),
+                         t->leaves(), t->store.as<unsigned long long>(), &c->build_flags, s);
         LBVH_LAUNCHED();
     }
     return finish_build(t, s);
@@ -429,7 +432,7 @@ lbvh_status lbvh_tree_size(lbvh_tree_t t, int64_t *n) {
 lbvh_status lbvh_tree_bytes(lbvh_tree_t t, uint64_t *bytes) {
     if (!t || !bytes) return LBVH_ERR_INVALID;
     uint64_t b = 0;
-    for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->inodes, &t->leaves,
+    for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
                             &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                             &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                             &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots})
@@ -450,7 +453,7 @@ lbvh_status lbvh_tree_export(lbvh_tree_t t, uint32_t *h_perm, uint64_t *h_sorted
     if (h_bounds) LBVH_CUDA(cudaMemcpy(h_bounds, t->bounds.p, 24, cudaMemcpyDeviceToHost));
     if (ni > 0 && (h_left || h_skip_internal || h_internal_box)) {
         std::vector<float4> nodes((size_t)ni * 2);
-        LBVH_CUDA(cudaMemcpy(nodes.data(), t->inodes.p, ni * 32, cudaMemcpyDeviceToHost));
+        LBVH_CUDA(cudaMemcpy(nodes.data(), t->inodes(), ni * 32, cudaMemcpyDeviceToHost));
         for (int64_t k = 0; k < ni; ++k) {
             const float4 a = nodes[2 * k], b = nodes[2 * k + 1];
             int32_t left, skip;
@@ -467,7 +470,7 @@ lbvh_status lbvh_tree_export(lbvh_tree_t t, uint32_t *h_perm, uint64_t *h_sorted
     if (h_skip_leaf || h_leaf_box) {
         const int per = t->kind == LBVH_PRIM_POINTS ? 1 : 2;
         std::vector<float4> leaves((size_t)n * per);
-        LBVH_CUDA(cudaMemcpy(leaves.data(), t->leaves.p, n * 16 * per, cudaMemcpyDeviceToHost));
+        LBVH_CUDA(cudaMemcpy(leaves.data(), t->leaves(), n * 16 * per, cudaMemcpyDeviceToHost));
         for (int64_t k = 0; k < n; ++k) {
             const float4 a = leaves[per * k], b = leaves[per * k + per - 1];
             uint32_t word;

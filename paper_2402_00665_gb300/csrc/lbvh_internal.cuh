@@ -57,7 +57,12 @@ __device__ __forceinline__ float max_ordered(float a, float b) {
 //   word = perm[k] | (skip is I_{k+1} ? kLeafSkipInternal : 0)
 //   points: leaves[k]      {x, y, z, word}                 (16 bytes)
 //   boxes:  leaves[2k]     {lo.xyz, word}, leaves[2k+1] {hi.xyz, 0}
-// left/skip/word are stored as int bits.
+// left/skip/word are stored as int bits. The tree keeps both arrays in one
+// allocation, leaves right after the 2(n-1) float4 of the internal nodes, so
+// a node's record starts at float4 unit 2*id (internal, box leaf) or id+(n-1)
+// (point leaf) of that allocation. In ids, a leaf's skip is id + 1 (L_{k+1})
+// or id + 1 - (n-1) (I_{k+1}); for the last leaf id + 1 = 2n-1, one past the
+// last node, which ends a walk like the sentinel.
 constexpr int kSentinel = -1;
 constexpr uint32_t kLeafSkipInternal = 1u << 31;
 constexpr uint32_t kLeafIndexMask = kLeafSkipInternal - 1u;

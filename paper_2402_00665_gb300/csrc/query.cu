@@ -8,13 +8,14 @@
 // one for internal nodes and box leaves (hi + skip), the box test, and a
 // select. A leaf's skip is position k+1, leaf or internal by one bit.
 //
-// Predicates (closed, FP32, fixed operation order, no fused multiply-add):
-//   sphere  e_a = max(lo_a - c_a, c_a - hi_a, 0); d2 = (ex*ex + ey*ey) + ez*ez;
-//           hit iff d2 <= r*r. Rounding is monotone, so a node's d2 never
-//           exceeds the d2 of a primitive inside it: the walk prunes nothing
-//           a brute-force scan would report. Computed as e_a = c_a -
-//           clamp(c_a, lo_a, hi_a), which has the same magnitude as
-//           max(lo_a - c_a, c_a - hi_a, 0) because fl(x - y) = -fl(y - x).
+// Predicates (closed, FP32, fixed operation order):
+//   sphere  e_a = max(lo_a - c_a, c_a - hi_a, 0);
+//           d2 = fma(ez, ez, fma(ey, ey, ex*ex)) (each step rounded once);
+//           hit iff d2 <= r*r. Every step is monotone in e_a >= 0, so a
+//           node's d2 never exceeds the d2 of a primitive inside it: the walk
+//           prunes nothing a brute-force scan would report. e_a is computed
+//           as c_a - clamp(c_a, lo_a, hi_a), which has the same magnitude
+//           because fl(x - y) = -fl(y - x).
 //   box     lo_q <= hi_b and lo_b <= hi_q on every axis.
 //
 // Threads take the queries in the order given by QueryArgs::order (the
@@ -60,7 +61,7 @@ __device__ __forceinline__ bool hits(const Sphere &s, float3 lo, float3 hi) {
     const float ex = gap(lo.x, s.c.x, hi.x);
     const float ey = gap(lo.y, s.c.y, hi.y);
     const float ez = gap(lo.z, s.c.z, hi.z);
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+    const float d2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
     return d2 <= s.r2;
 }
 
@@ -76,8 +77,8 @@ struct QueryOf<LBVH_Q_SPHERE> {
     using type = Sphere;
     static __device__ __forceinline__ Sphere load(const QueryArgs &a, int64_t q) {
         const float *p = a.queries + 3 * q;
-        const float r = a.radii ? a.radii[q] : a.radius;
-        return Sphere{make_float3(p[0], p[1], p[2]), __fmul_rn(r, r)};
+        const float r = a.radii ? __ldcs(a.radii + q) : a.radius;
+        return Sphere{make_float3(__ldcs(p), __ldcs(p + 1), __ldcs(p + 2)), __fmul_rn(r, r)};
     }
 };
 template <>
@@ -85,7 +86,8 @@ struct QueryOf<LBVH_Q_BOX> {
     using type = Box;
     static __device__ __forceinline__ Box load(const QueryArgs &a, int64_t q) {
         const float *p = a.queries + 6 * q;
-        return Box{make_float3(p[0], p[1], p[2]), make_float3(p[3], p[4], p[5])};
+        return Box{make_float3(__ldcs(p), __ldcs(p + 1), __ldcs(p + 2)),
+                   make_float3(__ldcs(p + 3), __ldcs(p + 4), __ldcs(p + 5))};
     }
 };
 
@@ -97,34 +99,35 @@ __device__ __forceinline__ float3 xyz(float4 v) { return make_float3(v.x, v.y, v
 // corrupt tree).
 template <int kP, typename Q, typename F>
 __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf) {
-    const int n = (int)t.n;
-    const int ni = n - 1;
-    const uint32_t nodes = 2u * (uint32_t)n - 1u;
-    const uint32_t max_steps = 2u * nodes;
+    const int ni = (int)t.n - 1;
+    const int nodes = 2 * (int)t.n - 1;
+    const uint32_t max_steps = 2u * (uint32_t)nodes;
+    const float4 *base = t.inodes;  // leaves follow the internal records
     int node = 0;
     uint32_t steps = 0;
-    // the sentinel (-1) and any id outside the tree end the loop
-    while ((uint32_t)node < nodes) {
+    // ids outside [0, nodes) end the loop: the sentinel, one past the last
+    // leaf (the last leaf's skip), or a corrupt id (reported below)
+    while ((uint32_t)node < (uint32_t)nodes) {
         if (++steps > max_steps) return false;
         const bool leaf = node >= ni;
-        const int k = node - ni;
-        const float4 *rec = leaf ? t.leaves + (kP == LBVH_PRIM_POINTS ? k : 2 * k) : t.inodes + 2 * node;
-        const float4 a = __ldg(rec);
+        const int unit = kP == LBVH_PRIM_BOXES ? 2 * node : (leaf ? node + ni : 2 * node);
+        const float4 a = __ldg(base + unit);
         float4 b = a;  // a point leaf's box is its point
-        if (kP == LBVH_PRIM_BOXES || !leaf) b = __ldg(rec + 1);
+        if (kP == LBVH_PRIM_BOXES || !leaf) b = __ldg(base + unit + 1);
         const bool hit = hits(q, xyz(a), xyz(b));
         const uint32_t word = __float_as_uint(a.w);
         if (hit && leaf) on_leaf(word & kLeafIndexMask);
-        // internal: left child on a hit, else skip; leaf: position k+1
-        node = leaf ? leaf_skip_id(word, k, n) : __float_as_int(hit ? a.w : b.w);
+        // internal: left child on a hit, else skip; leaf k: position k+1
+        node = leaf ? node + 1 - ((word & kLeafSkipInternal) ? ni : 0)
+                    : __float_as_int(hit ? a.w : b.w);
     }
-    return node == kSentinel;
+    return node == kSentinel || node == nodes;
 }
 
 constexpr int kSlot = kQueryBufferHits;
 
 __device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) {
-    return qa.order ? (int64_t)__ldg(qa.order + i) : i;
+    return qa.order ? (int64_t)__ldcs(qa.order + i) : i;
 }
 
 // One walk per query: hit count and up to kSlot primitive ids (walk order) in
@@ -141,12 +144,12 @@ __global__ void __launch_bounds__(kThreads)
     if (t.n > 0 && ctl->build_flags == 0) {
         const auto q = QueryOf<kQ>::load(qa, qi);
         const bool ok = walk<kP>(t, q, [&](uint32_t id) {
-            if (c < (uint32_t)kSlot) slot[c] = id;
+            if (c < (uint32_t)kSlot) __stcs(slot + c, id);  // streamed: keep L2 for the tree
             ++c;
         });
         if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
     }
-    count_pos[qi] = make_uint2(c, (uint32_t)i);
+    __stcs(count_pos + qi, make_uint2(c, (uint32_t)i));
     if (c > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi;
 }
 
