@@ -23,7 +23,8 @@
 // visit the same nodes), and write results at the query's own index.
 //
 // CSR in one walk:
-//   collect   thread i walks query q = order[i] and writes up to
+//   collect   each thread walks K adjacent sorted positions i (query q =
+//             order[i]) in lock step (K loads in flight) and writes up to
 //             kQueryBufferHits primitive ids, in walk order, into slot i of a
 //             scratch array (no shared memory: L1 stays with the tree), and
 //             (hit count, i) at q.
@@ -34,6 +35,7 @@
 //             per step.
 //   overflow  queries with more hits walk again and write straight into the
 //             CSR; a fix-up kernel sorts those lists, one CTA per list.
+#include <cstdlib>
 #include <type_traits>
 
 #include "lbvh_internal.cuh"
@@ -130,27 +132,80 @@ __device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) 
     return qa.order ? (int64_t)__ldcs(qa.order + i) : i;
 }
 
-// One walk per query: hit count and up to kSlot primitive ids (walk order) in
-// the slot of the walk position. See the file comment.
-template <int kQ, int kP>
+// K walks per thread, advanced in lock step: each iteration first issues the
+// node loads of every live walk, then tests them, so K independent loads are
+// in flight per thread (the walk is bound by the latency of its dependent
+// loads, not by bandwidth). Thread t walks sorted positions K*t .. K*t+K-1,
+// which are neighbours in the Morton order. Each walk keeps its hit count and
+// up to kSlot primitive ids (walk order) in the slot of its walk position.
+template <int kQ, int kP, int K>
 __global__ void __launch_bounds__(kThreads)
     collect_kernel(TreeView t, QueryArgs qa, uint2 *__restrict__ count_pos,
                    uint32_t *__restrict__ slots, uint32_t *__restrict__ overflow_list, Control *ctl) {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i >= qa.nq) return;
-    const int64_t qi = thread_query(qa, i);
-    uint32_t *slot = slots + i * kSlot;
-    uint32_t c = 0;
-    if (t.n > 0 && ctl->build_flags == 0) {
-        const auto q = QueryOf<kQ>::load(qa, qi);
-        const bool ok = walk<kP>(t, q, [&](uint32_t id) {
-            if (c < (uint32_t)kSlot) __stcs(slot + c, id);  // streamed: keep L2 for the tree
-            ++c;
-        });
-        if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
+    const int64_t first = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * K;
+    if (first >= qa.nq) return;
+    const bool walk_ok = t.n > 0 && ctl->build_flags == 0;
+    const int ni = (int)t.n - 1;
+    const int nodes = 2 * (int)t.n - 1;
+    const uint32_t max_steps = 2u * (uint32_t)nodes;
+    const float4 *base = t.inodes;
+    using Q = typename QueryOf<kQ>::type;
+    Q q[K];
+    int node[K];
+    uint32_t cnt[K], steps[K];
+    int64_t qi[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int64_t i = first + j;
+        cnt[j] = 0;
+        steps[j] = 0;
+        node[j] = (i < qa.nq && walk_ok) ? 0 : kSentinel;
+        qi[j] = i < qa.nq ? thread_query(qa, i) : 0;
+        if (i < qa.nq) q[j] = QueryOf<kQ>::load(qa, qi[j]);
     }
-    __stcs(count_pos + qi, make_uint2(c, (uint32_t)i));
-    if (c > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi;
+    while (true) {
+        float4 a[K], b[K];
+        bool live[K], any = false;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            live[j] = (uint32_t)node[j] < (uint32_t)nodes;
+            any |= live[j];
+            if (live[j]) {
+                const bool leaf = node[j] >= ni;
+                const int unit = kP == LBVH_PRIM_BOXES ? 2 * node[j] : (leaf ? node[j] + ni : 2 * node[j]);
+                a[j] = __ldg(base + unit);
+                b[j] = a[j];  // a point leaf's box is its point
+                if (kP == LBVH_PRIM_BOXES || !leaf) b[j] = __ldg(base + unit + 1);
+            }
+        }
+        if (!any) break;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (!live[j]) continue;
+            if (++steps[j] > max_steps) {  // a corrupt tree: stop this walk
+                node[j] = nodes + 1;
+                continue;
+            }
+            const bool leaf = node[j] >= ni;
+            const bool hit = hits(q[j], xyz(a[j]), xyz(b[j]));
+            const uint32_t word = __float_as_uint(a[j].w);
+            if (hit && leaf) {
+                if (cnt[j] < (uint32_t)kSlot) __stcs(slots + (first + j) * kSlot + cnt[j], word & kLeafIndexMask);
+                ++cnt[j];
+            }
+            // internal: left child on a hit, else skip; leaf k: position k+1
+            node[j] = leaf ? node[j] + 1 - ((word & kLeafSkipInternal) ? ni : 0)
+                           : __float_as_int(hit ? a[j].w : b[j].w);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int64_t i = first + j;
+        if (i >= qa.nq) continue;
+        if (walk_ok && !(node[j] == kSentinel || node[j] == nodes)) atomicOr(&ctl->query_flags, kFlagCorrupt);
+        __stcs(count_pos + qi[j], make_uint2(cnt[j], (uint32_t)i));  // streamed: keep L2 for the tree
+        if (cnt[j] > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi[j];
+    }
 }
 
 // Ascending bitonic sorting network over 32 registers (indices are compile
@@ -389,14 +444,40 @@ void dispatch_kinds(int qkind, int pkind, F &&f) {
     }
 }
 
+// Walks per thread in the collecting kernel: LBVH_WALKS_PER_THREAD=1..4
+// overrides the default (tuning sweeps). One is fastest on GB300: the walk is
+// bound by L1 wavefronts (distinct sectors per load), which more walks per
+// thread only increase.
+static int walks_per_thread() {
+    static int k = 0;
+    if (k == 0) {
+        const char *env = getenv("LBVH_WALKS_PER_THREAD");
+        const int want = env ? atoi(env) : 1;
+        k = want >= 1 && want <= 4 ? want : 1;
+    }
+    return k;
+}
+
+template <int K>
+void launch_collect_k(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
+                      cudaStream_t s) {
+    const int64_t threads = (q.nq + K - 1) / K;
+    const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
+    dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
+        collect_kernel<decltype(qk)::value, decltype(pk)::value, K><<<blocks, kThreads, 0, s>>>(
+            t, q, qs.count_pos, qs.slots, qs.overflow_list, ctl);
+    });
+}
+
 void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
                           cudaStream_t s) {
     if (q.nq <= 0) return;
-    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
-    dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
-        collect_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
-            t, q, qs.count_pos, qs.slots, qs.overflow_list, ctl);
-    });
+    switch (walks_per_thread()) {
+    case 3: launch_collect_k<3>(t, q, qs, ctl, s); break;
+    case 4: launch_collect_k<4>(t, q, qs, ctl, s); break;
+    case 2: launch_collect_k<2>(t, q, qs, ctl, s); break;
+    default: launch_collect_k<1>(t, q, qs, ctl, s); break;
+    }
     count_launches(1);
 }
 
