@@ -178,6 +178,59 @@ lbvh_status lbvh_sort_pairs(const uint64_t *d_keys, const uint32_t *d_vals, int6
                             int key_bits, uint64_t *d_keys_out, uint32_t *d_vals_out,
                             lbvh_stream_t stream);
 
+/* ---------------------------------------------------------------- batches */
+
+typedef struct lbvh_batch_s *lbvh_batch_t; /* opaque; device storage owned by the library */
+
+/* Create an empty batch handle. */
+lbvh_status lbvh_batch_create(lbvh_batch_t *out);
+
+/* Release the batch and its device memory (waits for its stream). Accepts NULL. */
+void lbvh_batch_destroy(lbvh_batch_t batch);
+
+/* Build `count` independent trees and answer each tree's own queries in one
+ * pass over all of them: the same method as lbvh_build + lbvh_query_into per
+ * instance (Sec. 3.1 steps 1-4, Algorithm 4, Algorithm 1), with every step
+ * run once for the whole batch (per-instance scene bounds; one radix sort of
+ * keys that carry the instance index above the Morton code; the bottom-up
+ * pass of all trees at once; one walk kernel for all queries). Each
+ * instance's tree and hit lists are identical to what a single build of that
+ * instance produces.
+ *   d_prims          concatenated primitives (layout of lbvh_build), device.
+ *   h_prim_offsets   host int64[count+1], h_prim_offsets[0] == 0: instance b
+ *                    owns primitives [off[b], off[b+1]) (may be empty).
+ *   morton_bits      as lbvh_build; morton_bits + ceil(log2(count)) <= 64.
+ *   d_queries        concatenated queries (layout of lbvh_query_into).
+ *   h_query_offsets  host int64[count+1]: queries of instance b.
+ *   d_radii/radius   as lbvh_query_into (per query, or one for all).
+ *   d_offsets        int64[total queries + 1]; d_hits uint32[capacity]: one
+ *                    CSR over all queries in their concatenated order; hit
+ *                    ids are primitive indices local to the query's instance.
+ *   total            out: total hits. If total > capacity, returns
+ *                    LBVH_ERR_CAPACITY (d_offsets valid, d_hits unspecified).
+ * The first call with a given set of arguments (pointers, offsets, kinds,
+ * bits, radius, capacity) sets up buffers, tunes the sort's tile shape on the
+ * batch (CUDA-event timing) and records the whole pipeline as one CUDA graph;
+ * later calls with the same arguments launch that graph once. Every call
+ * synchronises `stream` once at the end (to report total and status). Totals
+ * of primitives and of queries are each below 2^32. */
+lbvh_status lbvh_batch_build_query(lbvh_batch_t batch, const float *d_prims,
+                                   const int64_t *h_prim_offsets, int64_t count, int kind,
+                                   int morton_bits, const float *d_queries,
+                                   const int64_t *h_query_offsets, int qkind, const float *d_radii,
+                                   float radius, int64_t *d_offsets, uint32_t *d_hits,
+                                   uint64_t capacity, uint64_t *total, lbvh_stream_t stream);
+
+/* Canonical arrays of one instance of the last batch run (as
+ * lbvh_tree_export; perm holds indices local to the instance). */
+lbvh_status lbvh_batch_export(lbvh_batch_t batch, int64_t instance, uint32_t *h_perm,
+                              uint64_t *h_sorted_codes, int32_t *h_left, int32_t *h_skip_internal,
+                              int32_t *h_skip_leaf, float *h_internal_box, float *h_leaf_box,
+                              float *h_bounds);
+
+/* The sort tile shape the batch's autotuner chose (-1: default, not tuned). */
+lbvh_status lbvh_batch_sort_variant(lbvh_batch_t batch, int *variant);
+
 /* ---------------------------------------------------------------- no allocation */
 
 /* Largest n accepted by lbvh_construct_static. */

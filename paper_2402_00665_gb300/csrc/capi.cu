@@ -6,6 +6,8 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "lbvh_internal.cuh"
@@ -165,7 +167,7 @@ namespace {
 lbvh_status reserve_tree(lbvh_tree_s *t, int64_t n, int kind, cudaStream_t s) {
     using namespace lbvh;
     const size_t un = (size_t)n, ui = (size_t)(n > 0 ? n - 1 : 0);
-    const int64_t tiles = sort_tiles(n);
+    const int64_t tiles = sort_tiles_max(n);
     LBVH_CUDA(t->ctl.ensure(sizeof(Control), s, true));
     for (int k = 0; k < 2; ++k) {
         LBVH_CUDA(t->keys[k].ensure(un * 8, s));
@@ -227,13 +229,13 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
         LBVH_CUDA(t->qkeys[k].ensure(unq * 8, s));
         LBVH_CUDA(t->qvals[k].ensure(unq * 4, s));
     }
-    LBVH_CUDA(t->qlookback.ensure((size_t)sort_tiles(qa.nq) * kRadix * 4 * 2, s));
+    LBVH_CUDA(t->qlookback.ensure((size_t)sort_tiles_max(qa.nq) * kRadix * 4 * 2, s));
     LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)passes * kRadix * 4, s));
     const int as_prims = qa.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
     launch_encode(qa.queries, qa.nq, as_prims, kOrderBits, t->bounds.as<float>(),
                   t->qkeys[0].as<uint64_t>(), t->hist.as<uint32_t>(), 1, s);
     LBVH_LAUNCHED();
-    SortScratch scratch{t->hist.as<uint32_t>(), t->qlookback.as<uint32_t>(), sort_tiles(qa.nq) * kRadix};
+    SortScratch scratch{t->hist.as<uint32_t>(), t->qlookback.as<uint32_t>(), sort_tiles_max(qa.nq) * kRadix};
     const bool in_b = run_onesweep(t->qkeys[0].as<uint64_t>(), t->qvals[0].as<uint32_t>(), true,
                                    t->qkeys[1].as<uint64_t>(), t->qvals[1].as<uint32_t>(), qa.nq, passes,
                                    scratch, t->dctl(), s);
@@ -287,7 +289,7 @@ lbvh_status query_fill(lbvh_tree_t t, const lbvh::QueryArgs &qa, const int64_t *
     if (t->h_ctl->total == 0) return LBVH_OK;
     const QueryScratch qs = query_scratch(t);
     t->prof.begin(LBVH_STAGE_QFILL, s);
-    launch_query_copy(qa, qs, d_offsets, d_hits, s);
+    launch_query_copy(qa, qs, d_offsets, d_hits, t->dctl(), s);
     t->prof.end(LBVH_STAGE_QFILL, s);
     LBVH_LAUNCHED();
     if (t->h_ctl->overflow_filled > 0) {
@@ -306,6 +308,251 @@ lbvh_status check_query_args(lbvh_tree_t t, const float *q, int64_t nq, int qkin
     if (nq > 0 && !q) return LBVH_ERR_INVALID;
     if (qkind == LBVH_Q_SPHERE && !radii && !(std::isfinite(radius) && radius >= 0.0f))
         return LBVH_ERR_INVALID;
+    return LBVH_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+struct BatchSignature {
+    const float *prims = nullptr, *queries = nullptr, *radii = nullptr;
+    int kind = 0, qkind = 0, bits = 0;
+    float radius = 0.0f;
+    std::vector<int64_t> prim_off, query_off;
+    int64_t *offsets = nullptr;
+    uint32_t *hits = nullptr;
+    unsigned long long capacity = 0;
+    bool operator==(const BatchSignature &o) const {
+        return prims == o.prims && queries == o.queries && radii == o.radii && kind == o.kind &&
+               qkind == o.qkind && bits == o.bits && radius == o.radius && prim_off == o.prim_off &&
+               query_off == o.query_off && offsets == o.offsets && hits == o.hits && capacity == o.capacity;
+    }
+};
+
+// Process-wide autotuning results: sort tile shape per (keys, passes) bucket.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned_variant;
+
+int ceil_log2(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+}  // namespace
+
+struct lbvh_batch_s {
+    BatchSignature sig;
+    bool ready = false;   // buffers and tables match `sig`
+    int64_t count = 0, N = 0, NQ = 0, nchunks = 0, nqchunks = 0;
+    int ibits = 0, passes = 0, qpasses = 0, sort_variant = -1;
+    bool self_query = false, sorted_in_b = false;
+    DevBuf prim_off, query_off, node_start, store_start, chunks, chunk_first, qchunks;
+    DevBuf keys[2], vals[2], nodes, store, lookback, hist, partials, bounds, ctl;
+    DevBuf count_pos, slots, overflow, tile_sums, qkeys[2], qvals[2], qlookback;
+    std::vector<int64_t> h_node_start;
+    lbvh::Control *h_ctl = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_kernels = 0;
+    cudaStream_t stream = nullptr;  // the batch's own stream (capturable), ordered after the caller's
+    cudaEvent_t ordered = nullptr;
+
+    lbvh::BatchTables tables() const {
+        return lbvh::BatchTables{prim_off.as<int64_t>(), query_off.as<int64_t>(), node_start.as<int64_t>(),
+                                 store_start.as<int64_t>(), chunks.as<lbvh::BatchChunk>(),
+                                 chunk_first.as<int64_t>(), qchunks.as<lbvh::BatchChunk>(), (int)count,
+                                 N, NQ, nchunks, nqchunks};
+    }
+    const uint64_t *sorted_codes() const { return keys[sorted_in_b ? 1 : 0].as<uint64_t>(); }
+    const uint32_t *perm() const { return vals[sorted_in_b ? 1 : 0].as<uint32_t>(); }
+    lbvh::Control *dctl() const { return ctl.as<lbvh::Control>(); }
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+};
+
+namespace {
+
+std::vector<lbvh::BatchChunk> make_chunks(const std::vector<int64_t> &off, std::vector<int64_t> *first) {
+    std::vector<lbvh::BatchChunk> out;
+    if (first) first->assign(off.size(), 0);
+    for (size_t b = 0; b + 1 < off.size(); ++b) {
+        if (first) (*first)[b] = (int64_t)out.size();
+        for (int64_t c = off[b]; c < off[b + 1]; c += lbvh::kBatchChunk)
+            out.push_back(lbvh::BatchChunk{c, std::min(off[b + 1], c + (int64_t)lbvh::kBatchChunk), (int)b, 0});
+    }
+    if (first) first->back() = (int64_t)out.size();
+    return out;
+}
+
+lbvh_status upload(DevBuf &dst, const void *src, size_t bytes, cudaStream_t s) {
+    LBVH_CUDA(dst.ensure(bytes + 8, s));
+    if (bytes) LBVH_CUDA(cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyHostToDevice, s));
+    return LBVH_OK;
+}
+
+// Buffers and tables for the signature in b->sig (one synchronising set-up).
+lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
+    using namespace lbvh;
+    const BatchSignature &g = b->sig;
+    b->count = (int64_t)g.prim_off.size() - 1;
+    b->N = g.prim_off.back();
+    b->NQ = g.query_off.back();
+    b->ibits = ceil_log2(b->count);
+    b->passes = sort_passes(g.bits + b->ibits);
+    b->qpasses = sort_passes(30 + b->ibits);
+    const bool same_points = g.qkind == LBVH_Q_SPHERE && g.kind == LBVH_PRIM_POINTS;
+    const bool same_boxes = g.qkind == LBVH_Q_BOX && g.kind == LBVH_PRIM_BOXES;
+    b->self_query = g.queries == g.prims && g.query_off == g.prim_off && (same_points || same_boxes);
+    std::vector<int64_t> first;
+    const std::vector<BatchChunk> chunks = make_chunks(g.prim_off, &first);
+    const std::vector<BatchChunk> qchunks = make_chunks(g.query_off, nullptr);
+    b->nchunks = (int64_t)chunks.size();
+    b->nqchunks = (int64_t)qchunks.size();
+    std::vector<int64_t> node_start(b->count), store_start(b->count);
+    int64_t units = 0, words = 0;
+    for (int64_t k = 0; k < b->count; ++k) {
+        const int64_t n = g.prim_off[k + 1] - g.prim_off[k];
+        node_start[k] = units;
+        store_start[k] = words;
+        if (n > 0) {
+            units += 2 * (n - 1) + (g.kind == LBVH_PRIM_POINTS ? n : 2 * n);
+            words += n - 1;
+        }
+    }
+    b->h_node_start = node_start;
+    lbvh_status st;
+    if ((st = upload(b->prim_off, g.prim_off.data(), g.prim_off.size() * 8, s)) != LBVH_OK) return st;
+    if ((st = upload(b->query_off, g.query_off.data(), g.query_off.size() * 8, s)) != LBVH_OK) return st;
+    if ((st = upload(b->node_start, node_start.data(), node_start.size() * 8, s)) != LBVH_OK) return st;
+    if ((st = upload(b->store_start, store_start.data(), store_start.size() * 8, s)) != LBVH_OK) return st;
+    if ((st = upload(b->chunks, chunks.data(), chunks.size() * sizeof(BatchChunk), s)) != LBVH_OK) return st;
+    if ((st = upload(b->chunk_first, first.data(), first.size() * 8, s)) != LBVH_OK) return st;
+    if ((st = upload(b->qchunks, qchunks.data(), qchunks.size() * sizeof(BatchChunk), s)) != LBVH_OK) return st;
+    const size_t un = (size_t)b->N, unq = (size_t)b->NQ;
+    LBVH_CUDA(b->ctl.ensure(sizeof(Control), s, true));
+    for (int k = 0; k < 2; ++k) {
+        LBVH_CUDA(b->keys[k].ensure(un * 8 + 8, s));
+        LBVH_CUDA(b->vals[k].ensure(un * 4 + 4, s));
+        LBVH_CUDA(b->qkeys[k].ensure(unq * 8 + 8, s));
+        LBVH_CUDA(b->qvals[k].ensure(unq * 4 + 4, s));
+    }
+    LBVH_CUDA(b->nodes.ensure((size_t)units * 16 + 16, s));
+    LBVH_CUDA(b->store.ensure((size_t)words * 8 + 8, s, true));
+    LBVH_CUDA(b->lookback.ensure((size_t)sort_tiles_max(b->N) * kRadix * 8 + 8, s));
+    LBVH_CUDA(b->qlookback.ensure((size_t)sort_tiles_max(b->NQ) * kRadix * 8 + 8, s));
+    LBVH_CUDA(b->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
+    LBVH_CUDA(b->partials.ensure((size_t)b->nchunks * 32 + 32, s));
+    LBVH_CUDA(b->bounds.ensure((size_t)b->count * 24 + 24, s));
+    LBVH_CUDA(b->count_pos.ensure(unq * 8 + 8, s));
+    LBVH_CUDA(b->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
+    LBVH_CUDA(b->overflow.ensure(unq * 4 + 4, s));
+    LBVH_CUDA(b->tile_sums.ensure((size_t)scan_tile_count(b->NQ) * 8 + 8, s));
+    if (!b->h_ctl) LBVH_CUDA(cudaMallocHost(&b->h_ctl, sizeof(Control)));
+    LBVH_CUDA(cudaStreamSynchronize(s));
+    b->ready = true;
+    return LBVH_OK;
+}
+
+// The whole batched pipeline on `s`, with no host synchronisation (so it can
+// be captured in a CUDA graph): bounds, composite keys, one radix sort over
+// all instances, the bottom-up pass of every tree, the queries' Morton order,
+// the collecting walk, the scan, the checked copy and the overflow lists.
+lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {
+    using namespace lbvh;
+    const BatchSignature &g = b->sig;
+    const BatchTables bt = b->tables();
+    Control *c = b->dctl();
+    LBVH_CUDA(cudaMemsetAsync(&c->build_flags, 0, sizeof(uint32_t), s));
+    LBVH_CUDA(cudaMemsetAsync(&c->query_flags, 0, offsetof(Control, pad) - offsetof(Control, query_flags), s));
+    if (b->N > 0) {
+        LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->passes * kRadix * 4, s));
+        launch_batch_bounds(g.prims, g.kind, bt, b->partials.as<float>(), b->bounds.as<float>(), c, s);
+        launch_batch_encode(g.prims, g.kind, false, bt, g.bits, b->bounds.as<float>(), b->keys[0].as<uint64_t>(),
+                            b->hist.as<uint32_t>(), s);
+        SortScratch scratch{b->hist.as<uint32_t>(), b->lookback.as<uint32_t>(), sort_tiles_max(b->N) * kRadix};
+        b->sorted_in_b = run_onesweep(b->keys[0].as<uint64_t>(), b->vals[0].as<uint32_t>(), true,
+                                      b->keys[1].as<uint64_t>(), b->vals[1].as<uint32_t>(), b->N, b->passes,
+                                      scratch, c, s, nullptr, b->sort_variant);
+        launch_batch_construct(b->sorted_codes(), b->perm(), g.prims, bt, g.kind, b->nodes.as<float4>(),
+                               b->store.as<unsigned long long>(), &c->build_flags, s);
+        LBVH_LAUNCHED();
+    }
+    if (b->NQ == 0) {
+        LBVH_CUDA(cudaMemsetAsync(g.offsets, 0, 8, s));
+        return LBVH_OK;
+    }
+    QueryArgs qa{g.queries, b->NQ, g.qkind, g.radii, g.radius, nullptr};
+    if (b->self_query) {
+        qa.order = b->perm();
+    } else {
+        LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->qpasses * kRadix * 4, s));
+        const int as_prims = g.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
+        launch_batch_encode(g.queries, as_prims, true, bt, 30, b->bounds.as<float>(), b->qkeys[0].as<uint64_t>(),
+                            b->hist.as<uint32_t>(), s);
+        SortScratch scratch{b->hist.as<uint32_t>(), b->qlookback.as<uint32_t>(), sort_tiles_max(b->NQ) * kRadix};
+        const bool in_b = run_onesweep(b->qkeys[0].as<uint64_t>(), b->qvals[0].as<uint32_t>(), true,
+                                       b->qkeys[1].as<uint64_t>(), b->qvals[1].as<uint32_t>(), b->NQ,
+                                       b->qpasses, scratch, c, s, nullptr, b->sort_variant);
+        qa.order = b->qvals[in_b ? 1 : 0].as<uint32_t>();
+    }
+    const QueryScratch qs{b->count_pos.as<uint2>(), b->slots.as<uint32_t>(), b->overflow.as<uint32_t>()};
+    launch_batch_collect(b->nodes.as<float4>(), g.kind, bt, qa, qs, c, s);
+    launch_exclusive_scan(qs.count_pos, b->NQ, g.offsets, b->tile_sums.as<int64_t>(), c, s);
+    launch_query_copy_checked(qa, qs, g.offsets, g.hits, g.capacity, c, s);
+    launch_batch_overflow(b->nodes.as<float4>(), g.kind, bt, qa, qs, c, g.offsets, g.hits, g.capacity, s);
+    LBVH_LAUNCHED();
+    return LBVH_OK;
+}
+
+// Sort tile shape for this batch: the fastest variant on the batch's own keys
+// (timed with events on `s`), remembered per (keys bucket, passes).
+lbvh_status batch_autotune(lbvh_batch_t b, cudaStream_t s) {
+    using namespace lbvh;
+    if (b->sort_variant >= 0 || b->N < (1 << 20)) return LBVH_OK;
+    const std::pair<int, int> key{ceil_log2(b->N), b->passes};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tuned_variant.find(key);
+        if (it != g_tuned_variant.end()) {
+            b->sort_variant = it->second;
+            return LBVH_OK;
+        }
+    }
+    const BatchSignature &g = b->sig;
+    const BatchTables bt = b->tables();
+    Control *c = b->dctl();
+    cudaEvent_t e0, e1;
+    LBVH_CUDA(cudaEventCreate(&e0));
+    LBVH_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int pick = 0;
+    for (int v = 0; v < sort_variant_count(); ++v) {
+        float ms_total = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {
+            LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->passes * kRadix * 4, s));
+            launch_batch_encode(g.prims, g.kind, false, bt, g.bits, b->bounds.as<float>(),
+                                b->keys[0].as<uint64_t>(), b->hist.as<uint32_t>(), s);
+            SortScratch scratch{b->hist.as<uint32_t>(), b->lookback.as<uint32_t>(), sort_tiles_max(b->N) * kRadix};
+            LBVH_CUDA(cudaEventRecord(e0, s));
+            run_onesweep(b->keys[0].as<uint64_t>(), b->vals[0].as<uint32_t>(), true, b->keys[1].as<uint64_t>(),
+                         b->vals[1].as<uint32_t>(), b->N, b->passes, scratch, c, s, nullptr, v);
+            LBVH_CUDA(cudaEventRecord(e1, s));
+            LBVH_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            LBVH_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep) ms_total += ms;  // the first repetition warms up
+        }
+        if (ms_total < best) {
+            best = ms_total;
+            pick = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->sort_variant = pick;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tuned_variant[key] = pick;
     return LBVH_OK;
 }
 
@@ -367,7 +614,7 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
                       t->hist.as<uint32_t>(), 1, s);
         t->prof.end(LBVH_STAGE_ENCODE, s);
         LBVH_LAUNCHED();
-        SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles(n) * kRadix};
+        SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles_max(n) * kRadix};
         t->sorted_in_b = run_onesweep(t->keys[0].as<uint64_t>(), t->vals[0].as<uint32_t>(), true,
                                       t->keys[1].as<uint64_t>(), t->vals[1].as<uint32_t>(), n, passes,
                                       scratch, c, s, t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr);
@@ -574,7 +821,7 @@ lbvh_status lbvh_sort_pairs(const uint64_t *d_keys, const uint32_t *d_vals, int6
     if (!d_keys || !d_keys_out || !d_vals_out) return LBVH_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int passes = sort_passes(key_bits);
-    const int64_t tiles = sort_tiles(n);
+    const int64_t tiles = sort_tiles_max(n);
     DevBuf ctl, hist, lookback, tk, tv;
     Control h{};
     cudaError_t e = ctl.ensure(sizeof(Control), s, true);
@@ -608,6 +855,178 @@ lbvh_status lbvh_sort_pairs(const uint64_t *d_keys, const uint32_t *d_vals, int6
     }
     for (DevBuf *b : {&ctl, &hist, &lookback, &tk, &tv}) b->release(s);
     return st;
+}
+
+lbvh_status lbvh_batch_create(lbvh_batch_t *out) {
+    if (!out) return LBVH_ERR_INVALID;
+    *out = new (std::nothrow) lbvh_batch_s();
+    return *out ? LBVH_OK : LBVH_ERR_OOM;
+}
+
+void lbvh_batch_destroy(lbvh_batch_t b) {
+    if (!b) return;
+    cudaStream_t s = b->stream;
+    if (s) cudaStreamSynchronize(s);
+    b->drop_graph();
+    for (DevBuf *d : {&b->prim_off, &b->query_off, &b->node_start, &b->store_start, &b->chunks, &b->chunk_first,
+                      &b->qchunks, &b->keys[0], &b->keys[1], &b->vals[0], &b->vals[1], &b->nodes, &b->store,
+                      &b->lookback, &b->hist, &b->partials, &b->bounds, &b->ctl, &b->count_pos, &b->slots,
+                      &b->overflow, &b->tile_sums, &b->qkeys[0], &b->qkeys[1], &b->qvals[0], &b->qvals[1],
+                      &b->qlookback})
+        d->release(s);
+    if (s) cudaStreamSynchronize(s);
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    if (b->ordered) cudaEventDestroy(b->ordered);
+    if (s) cudaStreamDestroy(s);
+    delete b;
+}
+
+lbvh_status lbvh_batch_build_query(lbvh_batch_t b, const float *d_prims, const int64_t *h_prim_offsets,
+                                   int64_t count, int kind, int morton_bits, const float *d_queries,
+                                   const int64_t *h_query_offsets, int qkind, const float *d_radii,
+                                   float radius, int64_t *d_offsets, uint32_t *d_hits, uint64_t capacity,
+                                   uint64_t *total, lbvh_stream_t stream) {
+    using namespace lbvh;
+    if (!b || count < 1 || !h_prim_offsets || !h_query_offsets || !d_offsets || !total) return LBVH_ERR_INVALID;
+    if (kind != LBVH_PRIM_POINTS && kind != LBVH_PRIM_BOXES) return LBVH_ERR_INVALID;
+    if (qkind != LBVH_Q_SPHERE && qkind != LBVH_Q_BOX) return LBVH_ERR_INVALID;
+    if (!valid_bits(morton_bits) || morton_bits + ceil_log2(count) > 64) return LBVH_ERR_INVALID;
+    if (qkind == LBVH_Q_SPHERE && !d_radii && !(std::isfinite(radius) && radius >= 0.0f)) return LBVH_ERR_INVALID;
+    if (h_prim_offsets[0] != 0 || h_query_offsets[0] != 0) return LBVH_ERR_INVALID;
+    for (int64_t k = 0; k < count; ++k) {
+        const int64_t n = h_prim_offsets[k + 1] - h_prim_offsets[k];
+        const int64_t m = h_query_offsets[k + 1] - h_query_offsets[k];
+        if (n < 0 || n > LBVH_MAX_PRIMS || m < 0) return LBVH_ERR_INVALID;
+    }
+    if (h_prim_offsets[count] > ((int64_t)1 << 32) - 1 || h_query_offsets[count] > ((int64_t)1 << 32) - 1)
+        return LBVH_ERR_INVALID;
+    if ((h_prim_offsets[count] > 0 && !d_prims) || (h_query_offsets[count] > 0 && !d_queries))
+        return LBVH_ERR_INVALID;
+    if (capacity > 0 && !d_hits) return LBVH_ERR_INVALID;
+    // run on the batch's own stream (the caller's may be the legacy default
+    // stream, which cannot be captured), after the caller's pending work
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    if (!b->stream) LBVH_CUDA(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+    if (!b->ordered) LBVH_CUDA(cudaEventCreateWithFlags(&b->ordered, cudaEventDisableTiming));
+    LBVH_CUDA(cudaEventRecord(b->ordered, caller));
+    LBVH_CUDA(cudaStreamWaitEvent(b->stream, b->ordered, 0));
+    cudaStream_t s = b->stream;
+    BatchSignature sig;
+    sig.prims = d_prims;
+    sig.queries = d_queries;
+    sig.radii = d_radii;
+    sig.kind = kind;
+    sig.qkind = qkind;
+    sig.bits = morton_bits;
+    sig.radius = radius;
+    sig.prim_off.assign(h_prim_offsets, h_prim_offsets + count + 1);
+    sig.query_off.assign(h_query_offsets, h_query_offsets + count + 1);
+    sig.offsets = d_offsets;
+    sig.hits = d_hits;
+    sig.capacity = capacity;
+    lbvh_status st = LBVH_OK;
+    if (!(b->ready && b->sig == sig)) {
+        // a new shape: set up, tune, run once directly, then capture a graph
+        b->drop_graph();
+        const bool same_tables = b->ready && b->sig.prim_off == sig.prim_off && b->sig.query_off == sig.query_off &&
+                                 b->sig.kind == sig.kind && b->sig.bits == sig.bits;
+        b->sig = sig;
+        if (!same_tables) {
+            b->ready = false;
+            b->sort_variant = -1;
+            if ((st = batch_setup(b, s)) != LBVH_OK) return st;
+        } else {
+            b->self_query = false;
+            const bool same_points = qkind == LBVH_Q_SPHERE && kind == LBVH_PRIM_POINTS;
+            const bool same_boxes = qkind == LBVH_Q_BOX && kind == LBVH_PRIM_BOXES;
+            b->self_query = d_queries == d_prims && sig.query_off == sig.prim_off && (same_points || same_boxes);
+        }
+        if ((st = batch_enqueue(b, s)) != LBVH_OK) return st;  // bounds for the autotuner, and a first result
+        if ((st = batch_autotune(b, s)) != LBVH_OK) return st;
+        if ((st = batch_enqueue(b, s)) != LBVH_OK) return st;
+        const unsigned long long before = lbvh_kernel_launches();
+        cudaGraph_t graph = nullptr;
+        LBVH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        st = batch_enqueue(b, s);
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (st != LBVH_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        LBVH_CUDA(ce);
+        b->graph_kernels = (int)(lbvh_kernel_launches() - before);
+        const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        LBVH_CUDA(ie);
+    } else {
+        LBVH_CUDA(cudaGraphLaunch(b->exec, s));
+        lbvh::count_launches(b->graph_kernels);
+    }
+    LBVH_CUDA(cudaMemcpyAsync(b->h_ctl, b->ctl.p, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    LBVH_CUDA(cudaStreamSynchronize(s));
+    *total = b->h_ctl->total;
+    st = flags_status(b->h_ctl->build_flags);
+    if (st == LBVH_OK) st = flags_status(b->h_ctl->query_flags);
+    if (st == LBVH_OK && (b->h_ctl->query_flags & kFlagCapacity)) st = LBVH_ERR_CAPACITY;
+    if (st == LBVH_OK && *total > capacity) st = LBVH_ERR_CAPACITY;
+    if (b->h_ctl->build_flags & (kFlagTimeout | kFlagCorrupt)) {  // re-zero the store before the next run
+        cudaMemsetAsync(b->store.p, 0, b->store.bytes, s);
+        cudaStreamSynchronize(s);
+    }
+    return st;
+}
+
+lbvh_status lbvh_batch_export(lbvh_batch_t b, int64_t instance, uint32_t *h_perm, uint64_t *h_sorted_codes,
+                              int32_t *h_left, int32_t *h_skip_internal, int32_t *h_skip_leaf,
+                              float *h_internal_box, float *h_leaf_box, float *h_bounds) {
+    if (!b || !b->ready || instance < 0 || instance >= b->count) return LBVH_ERR_INVALID;
+    LBVH_CUDA(cudaStreamSynchronize(b->stream));
+    const int64_t o = b->sig.prim_off[instance];
+    const int64_t n = b->sig.prim_off[instance + 1] - o, ni = n > 0 ? n - 1 : 0;
+    if (h_bounds) LBVH_CUDA(cudaMemcpy(h_bounds, b->bounds.as<float>() + 6 * instance, 24, cudaMemcpyDeviceToHost));
+    if (n == 0) return LBVH_OK;
+    if (h_perm) {
+        LBVH_CUDA(cudaMemcpy(h_perm, b->perm() + o, n * 4, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < n; ++k) h_perm[k] -= (uint32_t)o;
+    }
+    if (h_sorted_codes) {
+        LBVH_CUDA(cudaMemcpy(h_sorted_codes, b->sorted_codes() + o, n * 8, cudaMemcpyDeviceToHost));
+        const uint64_t mask = b->sig.bits >= 64 ? ~0ull : ((1ull << b->sig.bits) - 1ull);
+        for (int64_t k = 0; k < n; ++k) h_sorted_codes[k] &= mask;
+    }
+    const int per = b->sig.kind == LBVH_PRIM_POINTS ? 1 : 2;
+    std::vector<float4> rec((size_t)(2 * ni + per * n));
+    LBVH_CUDA(cudaMemcpy(rec.data(), b->nodes.as<float4>() + b->h_node_start[instance], rec.size() * 16,
+                         cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < ni; ++k) {
+        const float4 a = rec[2 * k], c = rec[2 * k + 1];
+        int32_t left, skip;
+        std::memcpy(&left, &a.w, 4);
+        std::memcpy(&skip, &c.w, 4);
+        if (h_left) h_left[k] = left;
+        if (h_skip_internal) h_skip_internal[k] = skip;
+        if (h_internal_box) {
+            const float v[6] = {a.x, a.y, a.z, c.x, c.y, c.z};
+            std::memcpy(h_internal_box + 6 * k, v, sizeof v);
+        }
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        const float4 a = rec[2 * ni + per * k], c = rec[2 * ni + per * k + per - 1];
+        uint32_t word;
+        std::memcpy(&word, &a.w, 4);
+        if (h_skip_leaf) h_skip_leaf[k] = lbvh::leaf_skip_id(word, (int)k, (int)n);
+        if (h_leaf_box) {
+            const float v[6] = {a.x, a.y, a.z, c.x, c.y, c.z};
+            std::memcpy(h_leaf_box + 6 * k, v, sizeof v);
+        }
+    }
+    return LBVH_OK;
+}
+
+lbvh_status lbvh_batch_sort_variant(lbvh_batch_t b, int *variant) {
+    if (!b || !variant) return LBVH_ERR_INVALID;
+    *variant = b->sort_variant;
+    return LBVH_OK;
 }
 
 lbvh_status lbvh_tree_set_profiling(lbvh_tree_t t, int on) {

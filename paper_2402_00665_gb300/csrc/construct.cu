@@ -97,13 +97,16 @@ __device__ __forceinline__ unsigned long long publish_exchange(unsigned long lon
     return old;
 }
 
+// Algorithm 4 for leaf i of one tree of n leaves. codes/perm point at the
+// tree's first sorted position; perm holds primitive indices into `prims`,
+// the tree's own indices being perm - perm_base. inodes/leaves/store are the
+// tree's own arrays (layout in lbvh_internal.cuh).
 template <int kKind, bool kAcqRel>
-__global__ void __launch_bounds__(kThreads)
-    construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
-                     const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
-                     unsigned long long *store, uint32_t *flags) {
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
+__device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__restrict__ codes,
+                                               const uint32_t *__restrict__ perm, uint32_t perm_base,
+                                               const float *__restrict__ prims, float4 *inodes,
+                                               float4 *leaves, unsigned long long *store,
+                                               uint32_t *flags) {
     const int ni = n - 1;
 
     // ---- delta* around the leaf
@@ -119,7 +122,8 @@ __global__ void __launch_bounds__(kThreads)
     // ---- leaf: skip (Algorithm 4, leaf part) and box
     const int leaf_skip = i == n - 1 ? kSentinel : (dr < drn ? ni + i + 1 : i + 1);
     const uint32_t p_id = perm[i];
-    if (p_id >= (uint32_t)n) {  // not a permutation: the sort failed
+    const uint32_t p_own = p_id - perm_base;
+    if (p_own >= (uint32_t)n) {  // not a permutation of this tree: the sort failed
         atomicOr(flags, kFlagCorrupt);
         return;
     }
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(kThreads)
         hi = make_float3(b[3], b[4], b[5]);
     }
     // the leaf's skip is position i+1: one bit says I_{i+1} rather than L_{i+1}
-    const uint32_t word = p_id | (leaf_skip >= 0 && leaf_skip < ni ? kLeafSkipInternal : 0u);
+    const uint32_t word = p_own | (leaf_skip >= 0 && leaf_skip < ni ? kLeafSkipInternal : 0u);
     if (kKind == LBVH_PRIM_POINTS) {
         leaves[i] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
     } else {
@@ -142,7 +146,6 @@ __global__ void __launch_bounds__(kThreads)
         leaves[2 * (int64_t)i + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
     }
     if (n == 1) return;
-
     // ---- climb
     uint32_t l = i, r = i;
     uint32_t d_left = dl, d_right = dr, d_next = drn;  // delta*(l-1), delta*(r), delta*(r+1)
@@ -190,7 +193,54 @@ __global__ void __launch_bounds__(kThreads)
     atomicOr(flags, kFlagCorrupt);
 }
 
+template <int kKind, bool kAcqRel>
+__global__ void __launch_bounds__(kThreads)
+    construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
+                     const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
+                     unsigned long long *store, uint32_t *flags) {
+    const int i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    construct_leaf<kKind, kAcqRel>(i, n, codes, perm, 0u, prims, inodes, leaves, store, flags);
+}
+
+// Many trees at once: global sorted position g belongs to the instance b with
+// off[b] <= g < off[b+1]; its tree's records start at node_start[b] (float4
+// units) and its store words at store_start[b].
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    batch_construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
+                           const float *__restrict__ prims, const int64_t *__restrict__ off,
+                           const int64_t *__restrict__ node_start, const int64_t *__restrict__ store_start,
+                           int count, int64_t total, float4 *nodes, unsigned long long *store,
+                           uint32_t *flags) {
+    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (g >= total) return;
+    const int b = instance_of(off, count, g);
+    const int64_t o = off[b];
+    const int n = (int)(off[b + 1] - o);
+    float4 *inodes = nodes + node_start[b];
+    float4 *leaves = inodes + 2 * (int64_t)(n - 1);
+    construct_leaf<kKind, true>((int)(g - o), n, codes + o, perm + o, (uint32_t)o, prims, inodes, leaves,
+                                store + store_start[b], flags);
+}
+
 }  // namespace
+
+void launch_batch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
+                            const BatchTables &bt, int kind, float4 *nodes, unsigned long long *store,
+                            uint32_t *flags, cudaStream_t s) {
+    if (bt.total_prims <= 0) return;
+    const unsigned blocks = (unsigned)((bt.total_prims + kThreads - 1) / kThreads);
+    if (kind == LBVH_PRIM_POINTS)
+        batch_construct_kernel<LBVH_PRIM_POINTS><<<blocks, kThreads, 0, s>>>(
+            sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count, bt.total_prims,
+            nodes, store, flags);
+    else
+        batch_construct_kernel<LBVH_PRIM_BOXES><<<blocks, kThreads, 0, s>>>(
+            sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count, bt.total_prims,
+            nodes, store, flags);
+    count_launches(1);
+}
 
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
                       int64_t n, int kind, float4 *inodes, float4 *leaves,

@@ -17,6 +17,7 @@ enum : uint32_t {
     kFlagNonfinite = 1u << 0,
     kFlagTimeout = 1u << 1,
     kFlagCorrupt = 1u << 2,
+    kFlagCapacity = 1u << 3,
 };
 
 // One small device-resident block per tree: status flags, the query's hit
@@ -106,9 +107,15 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
 // must be zero (pass p counts pass p+1's digits). Region 0 of the look-back
 // is cleared here with a memset.
 // pass_events (nullable): an event pair per pass, recorded around its kernel.
+// variant_idx: tile shape (< sort_variant_count()), or -1 for the default.
+// The look-back regions must hold sort_tiles_max(n) * kRadix words each.
 bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
-                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr);
+                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
+                  int variant_idx = -1);
+int sort_variant_count();
+int64_t sort_tile_keys_min();
+inline int64_t sort_tiles_max(int64_t n) { return (n + sort_tile_keys_min() - 1) / sort_tile_keys_min(); }
 
 // ---------------------------------------------------------------- Morton
 // bounds: float[6] out; partials: float[blocks * 8]; codes: uint64[n];
@@ -157,10 +164,68 @@ void launch_exclusive_scan(const uint2 *count_pos, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s);
 // Short lists from the scratch buffer to their CSR positions.
 void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
-                       uint32_t *hits, cudaStream_t s);
+                       uint32_t *hits, Control *ctl, cudaStream_t s);
 // Second walk + sort for the `count` queries of the overflow list.
 void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScratch &qs,
                            uint32_t count, const int64_t *offsets, uint32_t *hits, cudaStream_t s);
+
+// ---------------------------------------------------------------- batches
+// Many independent trees in one pass. Instance b owns primitives
+// [prim_off[b], prim_off[b+1]) of one concatenated array and queries
+// [query_off[b], query_off[b+1]); its tree's records start at node_start[b]
+// (float4 units of one shared node buffer, laid out as a single tree) and its
+// Algorithm 4 store words at store_start[b]. Chunks split every instance into
+// pieces of at most kBatchChunk primitives for the per-instance reductions.
+constexpr int kBatchChunk = 8192;
+struct BatchChunk {
+    int64_t begin, end;
+    int inst, pad;
+};
+struct BatchTables {
+    const int64_t *prim_off;     // count + 1
+    const int64_t *query_off;    // count + 1
+    const int64_t *node_start;   // count
+    const int64_t *store_start;  // count
+    const BatchChunk *chunks;    // nchunks (primitives)
+    const int64_t *chunk_first;  // count + 1: instance b's chunks are [chunk_first[b], chunk_first[b+1])
+    const BatchChunk *qchunks;   // nqchunks (queries, for their Morton order)
+    int count;
+    int64_t total_prims, total_queries, nchunks, nqchunks;
+};
+
+// Largest b in [0, count) with off[b] <= g (the instance of element g).
+__device__ __forceinline__ int instance_of(const int64_t *__restrict__ off, int count, int64_t g) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-instance bounds: partials (nchunks * 8 floats), then bounds (count * 6).
+void launch_batch_bounds(const float *prims, int kind, const BatchTables &bt, float *partials,
+                         float *bounds, Control *ctl, cudaStream_t s);
+// Composite keys (instance << bits | Morton code) of primitives (or of query
+// centres, with `queries` = true: qchunks and qkind decide the layout), plus
+// pass 0's digit histogram.
+void launch_batch_encode(const float *data, int kind, bool queries, const BatchTables &bt, int bits,
+                         const float *bounds, uint64_t *keys, uint32_t *hist, cudaStream_t s);
+void launch_batch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
+                            const BatchTables &bt, int kind, float4 *nodes, unsigned long long *store,
+                            uint32_t *flags, cudaStream_t s);
+// The collecting walk over all instances' queries (instance of a query found
+// from query_off), and the overflow walk + list sort with device-side counts.
+void launch_batch_collect(const float4 *nodes, int kind, const BatchTables &bt, const QueryArgs &q,
+                          const QueryScratch &qs, Control *ctl, cudaStream_t s);
+void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt, const QueryArgs &q,
+                           const QueryScratch &qs, Control *ctl, const int64_t *offsets, uint32_t *hits,
+                           unsigned long long capacity, cudaStream_t s);
+// Copy with the capacity check on the device (no host round trip): lists are
+// written only if ctl->total <= capacity; otherwise kFlagCapacity is latched.
+void launch_query_copy_checked(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
+                               uint32_t *hits, unsigned long long capacity, Control *ctl, cudaStream_t s);
 
 int device_sm_count();
 

@@ -258,7 +258,145 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ---- batches: one CTA per chunk of one instance
+
+template <int kKind>
+__device__ __forceinline__ void centroid_at(const float *prims, int64_t i, float &x, float &y, float &z) {
+    if (kKind == LBVH_PRIM_POINTS) {
+        x = prims[3 * i];
+        y = prims[3 * i + 1];
+        z = prims[3 * i + 2];
+    } else {
+        box_centroid(prims + 6 * i, x, y, z);
+    }
+}
+
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    batch_bounds_kernel(const float *__restrict__ prims, const BatchChunk *__restrict__ chunks,
+                        float *__restrict__ partials) {
+    const BatchChunk c = chunks[blockIdx.x];
+    MinMax m;
+    m.init();
+    for (int64_t i = c.begin + threadIdx.x; i < c.end; i += kThreads) {
+        float x, y, z;
+        centroid_at<kKind>(prims, i, x, y, z);
+        m.add(x, y, z);
+    }
+    __shared__ float s_v[kThreads / 32][6];
+    __shared__ int s_ok[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int ok = m.ok;
+    for (int off = 16; off > 0; off >>= 1) {
+        for (int a = 0; a < 3; ++a) {
+            m.lo[a] = min_ordered(m.lo[a], __shfl_xor_sync(0xffffffffu, m.lo[a], off));
+            m.hi[a] = max_ordered(m.hi[a], __shfl_xor_sync(0xffffffffu, m.hi[a], off));
+        }
+        ok &= __shfl_xor_sync(0xffffffffu, ok, off);
+    }
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) {
+            s_v[warp][a] = m.lo[a];
+            s_v[warp][3 + a] = m.hi[a];
+        }
+        s_ok[warp] = ok;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v[6];
+        int all = 1;
+        for (int k = 0; k < 6; ++k) v[k] = s_v[0][k];
+        for (int w = 0; w < kThreads / 32; ++w) {
+            for (int a = 0; a < 3; ++a) {
+                v[a] = min_ordered(v[a], s_v[w][a]);
+                v[3 + a] = max_ordered(v[3 + a], s_v[w][3 + a]);
+            }
+            all &= s_ok[w];
+        }
+        float *out = partials + 8 * (int64_t)blockIdx.x;
+        for (int k = 0; k < 6; ++k) out[k] = v[k];
+        out[6] = all ? 1.0f : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    batch_bounds_fold_kernel(const float *__restrict__ partials, const int64_t *__restrict__ chunk_first,
+                             int count, float *__restrict__ bounds, Control *ctl) {
+    const int b = blockIdx.x * kThreads + threadIdx.x;
+    if (b >= count) return;
+    float v[6] = {FLT_MAX, FLT_MAX, FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX};
+    int all = 1;
+    for (int64_t c = chunk_first[b]; c < chunk_first[b + 1]; ++c) {
+        const float *p = partials + 8 * c;
+        for (int a = 0; a < 3; ++a) {
+            v[a] = min_ordered(v[a], p[a]);
+            v[3 + a] = max_ordered(v[3 + a], p[3 + a]);
+        }
+        all &= p[6] != 0.0f;
+    }
+    for (int k = 0; k < 6; ++k) bounds[6 * (int64_t)b + k] = v[k];
+    if (!all) atomicOr(&ctl->build_flags, kFlagNonfinite);
+}
+
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    batch_encode_kernel(const float *__restrict__ data, const BatchChunk *__restrict__ chunks, int b,
+                        int bits, const float *__restrict__ bounds, uint64_t *__restrict__ keys,
+                        uint32_t *__restrict__ hist) {
+    __shared__ uint32_t s_hist[kRadix];
+    s_hist[threadIdx.x] = 0;  // kThreads == kRadix
+    const BatchChunk c = chunks[blockIdx.x];
+    Grid3 g;
+    const float *bd = bounds + 6 * (int64_t)c.inst;
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = bd[a];
+        g.extent[a] = __fsub_rn(bd[3 + a], bd[a]);
+    }
+    g.topi = (1u << b) - 1u;
+    g.cells = (float)(1u << b);
+    g.top = (float)g.topi;
+    const uint64_t inst = (uint64_t)c.inst << bits;
+    __syncthreads();
+    for (int64_t i = c.begin + threadIdx.x; i < c.end; i += kThreads) {
+        float x, y, z;
+        centroid_at<kKind>(data, i, x, y, z);
+        const uint64_t key = inst | morton(x, y, z, g);
+        keys[i] = key;
+        atomicAdd(&s_hist[(uint32_t)key & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    const uint32_t v = s_hist[threadIdx.x];
+    if (v) atomicAdd(&hist[threadIdx.x], v);
+}
+
 }  // namespace
+
+void launch_batch_bounds(const float *prims, int kind, const BatchTables &bt, float *partials,
+                         float *bounds, Control *ctl, cudaStream_t s) {
+    if (bt.nchunks <= 0) return;
+    if (kind == LBVH_PRIM_POINTS)
+        batch_bounds_kernel<LBVH_PRIM_POINTS><<<(unsigned)bt.nchunks, kThreads, 0, s>>>(prims, bt.chunks, partials);
+    else
+        batch_bounds_kernel<LBVH_PRIM_BOXES><<<(unsigned)bt.nchunks, kThreads, 0, s>>>(prims, bt.chunks, partials);
+    batch_bounds_fold_kernel<<<(unsigned)((bt.count + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+        partials, bt.chunk_first, bt.count, bounds, ctl);
+    count_launches(2);
+}
+
+void launch_batch_encode(const float *data, int kind, bool queries, const BatchTables &bt, int bits,
+                         const float *bounds, uint64_t *keys, uint32_t *hist, cudaStream_t s) {
+    const int64_t nchunks = queries ? bt.nqchunks : bt.nchunks;
+    const BatchChunk *chunks = queries ? bt.qchunks : bt.chunks;
+    if (nchunks <= 0) return;
+    const int b = bits / 3;
+    if (kind == LBVH_PRIM_POINTS)
+        batch_encode_kernel<LBVH_PRIM_POINTS><<<(unsigned)nchunks, kThreads, 0, s>>>(data, chunks, b, bits, bounds,
+                                                                                     keys, hist);
+    else
+        batch_encode_kernel<LBVH_PRIM_BOXES><<<(unsigned)nchunks, kThreads, 0, s>>>(data, chunks, b, bits, bounds,
+                                                                                    keys, hist);
+    count_launches(1);
+}
 
 int bounds_blocks(int64_t n) {
     const int64_t want = (n / 4 + kThreads - 1) / kThreads;

@@ -234,8 +234,13 @@ __device__ __forceinline__ void sort32(uint32_t (&v)[32]) {
 // consecutive hits.
 __global__ void __launch_bounds__(kThreads)
     copy_kernel(int64_t nq, const uint2 *__restrict__ count_pos, const int64_t *__restrict__ offsets,
-                const uint32_t *__restrict__ slots, uint32_t *__restrict__ hits) {
+                const uint32_t *__restrict__ slots, uint32_t *__restrict__ hits,
+                unsigned long long capacity, Control *ctl) {
     __shared__ uint32_t s_lists[kThreads / 32][32][kSlot + 1];
+    if (ctl->total > capacity) {  // the caller's buffer is too small: write nothing
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->query_flags, kFlagCapacity);
+        return;
+    }
     const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t c = 0;
@@ -427,6 +432,83 @@ __global__ void __launch_bounds__(kFixThreads)
     }
 }
 
+// ---- batches: the same walk, on the tree of the query's instance
+
+template <int kQ, int kP>
+__global__ void __launch_bounds__(kThreads)
+    batch_collect_kernel(const float4 *__restrict__ nodes, BatchTables bt, QueryArgs qa,
+                         uint2 *__restrict__ count_pos, uint32_t *__restrict__ slots,
+                         uint32_t *__restrict__ overflow_list, Control *ctl) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= qa.nq) return;
+    const int64_t qi = thread_query(qa, i);
+    const int b = instance_of(bt.query_off, bt.count, qi);
+    const int64_t n = bt.prim_off[b + 1] - bt.prim_off[b];
+    uint32_t c = 0;
+    if (n > 0 && ctl->build_flags == 0) {
+        const TreeView t{nodes + bt.node_start[b], nullptr, n, kP};
+        const auto q = QueryOf<kQ>::load(qa, qi);
+        uint32_t *slot = slots + i * kSlot;
+        const bool ok = walk<kP>(t, q, [&](uint32_t id) {
+            if (c < (uint32_t)kSlot) __stcs(slot + c, id);
+            ++c;
+        });
+        if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
+    }
+    __stcs(count_pos + qi, make_uint2(c, (uint32_t)i));
+    if (c > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi;
+}
+
+// Overflow lists whose number is known only on the device: a fixed grid
+// strides over them.
+template <int kQ, int kP>
+__global__ void __launch_bounds__(kThreads)
+    batch_overflow_kernel(const float4 *__restrict__ nodes, BatchTables bt, QueryArgs qa,
+                          const uint32_t *__restrict__ list, const Control *ctl,
+                          const int64_t *__restrict__ offsets, uint32_t *__restrict__ hits,
+                          unsigned long long capacity) {
+    if (ctl->total > capacity) return;  // nothing is written into a buffer that is too small
+    const uint32_t count = ctl->overflow_filled;
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < count; j += (int64_t)gridDim.x * kThreads) {
+        const int64_t qi = list[j];
+        const int b = instance_of(bt.query_off, bt.count, qi);
+        const int64_t n = bt.prim_off[b + 1] - bt.prim_off[b];
+        const TreeView t{nodes + bt.node_start[b], nullptr, n, kP};
+        const int64_t base = offsets[qi];
+        const int64_t total = offsets[qi + 1] - base;
+        const auto q = QueryOf<kQ>::load(qa, qi);
+        int64_t c = 0;
+        walk<kP>(t, q, [&](uint32_t id) {
+            if (c < total) hits[base + c] = id;
+            ++c;
+        });
+    }
+}
+
+__global__ void __launch_bounds__(kFixThreads)
+    batch_sort_lists_kernel(const int64_t *__restrict__ offsets, uint32_t *hits,
+                            const uint32_t *__restrict__ list, const Control *ctl,
+                            unsigned long long capacity) {
+    __shared__ uint32_t s[kFixSmem];
+    if (ctl->total > capacity) return;
+    const uint32_t count = ctl->overflow_filled;
+    for (uint32_t j = blockIdx.x; j < count; j += gridDim.x) {
+        const uint32_t q = list[j];
+        const int64_t base = offsets[q];
+        const int64_t m = offsets[q + 1] - base;
+        uint32_t *seg = hits + base;
+        if (m <= kFixSmem) {
+            for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s[i] = seg[i];
+            __syncthreads();
+            bitonic_sort(s, m);
+            for (int64_t i = threadIdx.x; i < m; i += blockDim.x) seg[i] = s[i];
+        } else {
+            bitonic_sort(seg, m);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 template <typename F>
@@ -481,12 +563,17 @@ void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScra
     count_launches(1);
 }
 
-void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
-                       uint32_t *hits, cudaStream_t s) {
+void launch_query_copy_checked(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
+                               uint32_t *hits, unsigned long long capacity, Control *ctl, cudaStream_t s) {
     if (q.nq <= 0) return;
     const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
-    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, qs.count_pos, offsets, qs.slots, hits);
+    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, qs.count_pos, offsets, qs.slots, hits, capacity, ctl);
     count_launches(1);
+}
+
+void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
+                       uint32_t *hits, Control *ctl, cudaStream_t s) {
+    launch_query_copy_checked(q, qs, offsets, hits, ~0ull, ctl, s);
 }
 
 void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScratch &qs,
@@ -498,6 +585,31 @@ void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScr
             t, q, qs.overflow_list, count, offsets, hits);
     });
     sort_lists_kernel<<<count, kFixThreads, 0, s>>>(offsets, hits, qs.overflow_list);
+    count_launches(2);
+}
+
+void launch_batch_collect(const float4 *nodes, int kind, const BatchTables &bt, const QueryArgs &q,
+                          const QueryScratch &qs, Control *ctl, cudaStream_t s) {
+    if (q.nq <= 0) return;
+    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
+    dispatch_kinds(q.qkind, kind, [&](auto qk, auto pk) {
+        batch_collect_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
+            nodes, bt, q, qs.count_pos, qs.slots, qs.overflow_list, ctl);
+    });
+    count_launches(1);
+}
+
+void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt, const QueryArgs &q,
+                           const QueryScratch &qs, Control *ctl, const int64_t *offsets, uint32_t *hits,
+                           unsigned long long capacity, cudaStream_t s) {
+    if (q.nq <= 0) return;
+    const unsigned blocks = (unsigned)device_sm_count() * 2;
+    dispatch_kinds(q.qkind, kind, [&](auto qk, auto pk) {
+        batch_overflow_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
+            nodes, bt, q, qs.overflow_list, ctl, offsets, hits, capacity);
+    });
+    batch_sort_lists_kernel<<<(unsigned)device_sm_count() * 2, kFixThreads, 0, s>>>(
+        offsets, hits, qs.overflow_list, ctl, capacity);
     count_launches(2);
 }
 

@@ -252,26 +252,38 @@ Variant make_variant() {
 }
 
 // Tile shapes the library is compiled with. The first entry is the default;
-// LBVH_SORT_VARIANT=<index> selects another (used by the tuning sweep).
-const Variant &variant() {
+// LBVH_SORT_VARIANT=<index> selects another process-wide (tuning sweeps), and
+// run_onesweep can be given one explicitly (the batch autotuner).
+const Variant *variant_table(int *count) {
     static const Variant table[] = {
         make_variant<12, 4, true>(), make_variant<16, 3, true>(),  make_variant<8, 4, true>(),
         make_variant<16, 2, true>(), make_variant<12, 3, true>(),  make_variant<8, 6, true>(),
         make_variant<16, 2, false>(),
     };
-    static int pick = -1;
-    if (pick < 0) {
-        const char *env = getenv("LBVH_SORT_VARIANT");
-        const int want = env ? atoi(env) : 0;
-        pick = (want >= 0 && want < (int)(sizeof table / sizeof table[0])) ? want : 0;
+    static bool configured = false;
+    if (!configured) {
         for (const Variant &v : table) {
             for (PassKernel k : {v.first, v.rest}) {
                 cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
                 cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             }
         }
+        configured = true;
     }
-    return table[pick];
+    *count = (int)(sizeof table / sizeof table[0]);
+    return table;
+}
+
+const Variant &variant(int idx = -1) {
+    int count = 0;
+    const Variant *table = variant_table(&count);
+    static int pick = -1;
+    if (pick < 0) {
+        const char *env = getenv("LBVH_SORT_VARIANT");
+        const int want = env ? atoi(env) : 0;
+        pick = (want >= 0 && want < count) ? want : 0;
+    }
+    return table[(idx >= 0 && idx < count) ? idx : pick];
 }
 
 __global__ void __launch_bounds__(256)
@@ -307,12 +319,26 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
 
 int64_t sort_tile_keys() { return (int64_t)kSortThreads * variant().items; }
 
+int sort_variant_count() {
+    int count = 0;
+    variant_table(&count);
+    return count;
+}
+
+int64_t sort_tile_keys_min() {
+    int count = 0;
+    const Variant *t = variant_table(&count);
+    int items = t[0].items;
+    for (int k = 1; k < count; ++k) items = t[k].items < items ? t[k].items : items;
+    return (int64_t)kSortThreads * items;
+}
+
 bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
-                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2]) {
+                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx) {
     if (n <= 0 || passes <= 0) return false;
-    const Variant &v = variant();
-    const int64_t tiles = sort_tiles(n);
+    const Variant &v = variant(variant_idx);
+    const int64_t tiles = (n + (int64_t)kSortThreads * v.items - 1) / ((int64_t)kSortThreads * v.items);
     cudaMemsetAsync(scratch.lookback, 0, (size_t)tiles * kRadix * sizeof(uint32_t), s);
     uint64_t *kin = keys_a, *kout = keys_b;
     uint32_t *vin = vals_a, *vout = vals_b;

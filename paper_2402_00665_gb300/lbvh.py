@@ -45,6 +45,11 @@ SIGNATURES = {
     "lbvh_free": (None, [_P]),
     "lbvh_morton_codes": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "lbvh_sort_pairs": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "lbvh_batch_create": (_I32, [_P]),
+    "lbvh_batch_destroy": (None, [_P]),
+    "lbvh_batch_build_query": (_I32, [_P, _P, _P, _I64, _I32, _I32, _P, _P, _I32, _P, _F32, _P, _P, _U64, _P, _P]),
+    "lbvh_batch_export": (_I32, [_P, _I64] + [_P] * 8),
+    "lbvh_batch_sort_variant": (_I32, [_P, _P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
     "lbvh_tree_stage_times": (_I32, [_P, _P]),
@@ -240,6 +245,87 @@ class Tree:
             st, total = self.query_into(q, qkind, offsets, hits, radius, radii, stream)
         _check(st, "lbvh_query_into")
         return offsets, hits[:total]
+
+
+class Batch:
+    """Many independent trees built and queried in one pass (``lbvh_batch_*``).
+
+    Pass the same tensors on every call to replay the recorded CUDA graph.
+    """
+
+    def __init__(self):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.lbvh_batch_create(ctypes.byref(h)), "lbvh_batch_create")
+        self._h = h
+        self._keep = None
+        self._out = None
+        self.kind = POINTS
+        self.count = 0
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lbvh_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_query(self, prims, prim_offsets, kind: int = POINTS, morton_bits: int = 30, queries=None,
+                    query_offsets=None, qkind: int = SPHERE, radius: float = 0.0, radii=None,
+                    offsets=None, hits=None, capacity=None, stream=None):
+        """Returns (offsets int64[nq+1], hits int32 view of uint32 local ids, total, status)."""
+        torch = _torch()
+        p = prims if isinstance(prims, torch.Tensor) and prims.is_cuda else _dev(prims, torch.float32)
+        q = p if queries is None else (queries if isinstance(queries, torch.Tensor) and queries.is_cuda
+                                       else _dev(queries, torch.float32))
+        po = np.ascontiguousarray(prim_offsets, dtype=np.int64)
+        qo = po if query_offsets is None else np.ascontiguousarray(query_offsets, dtype=np.int64)
+        count = po.size - 1
+        nq = int(qo[-1])
+        r = None
+        if radii is not None:
+            r = radii if isinstance(radii, torch.Tensor) and radii.is_cuda else _dev(radii, torch.float32).reshape(-1)
+        if offsets is None:
+            if self._out is None or self._out[0].numel() != nq + 1:
+                self._out = (torch.empty(nq + 1, dtype=torch.int64, device="cuda"), None)
+            offsets = self._out[0]
+        if hits is None:
+            cap = int(capacity) if capacity is not None else max(20 * nq, 1)
+            if self._out[1] is None or self._out[1].numel() != cap:
+                self._out = (offsets, torch.empty(cap, dtype=torch.int32, device="cuda"))
+            hits = self._out[1]
+        total = ctypes.c_uint64()
+        st = self._lib.lbvh_batch_build_query(
+            self._h, _ptr(p), ctypes.c_void_p(po.ctypes.data), count, kind, morton_bits, _ptr(q),
+            ctypes.c_void_p(qo.ctypes.data), qkind, _ptr(r), float(radius), _ptr(offsets), _ptr(hits),
+            hits.numel(), ctypes.byref(total), _stream(stream))
+        self._keep = (p, q, r)
+        self.kind, self.count, self._po = kind, count, po
+        return offsets, hits, total.value, st
+
+    def export(self, instance: int) -> dict:
+        n = int(self._po[instance + 1] - self._po[instance])
+        ni = max(n - 1, 0)
+        out = {
+            "n": n,
+            "perm": np.zeros(n, np.uint32), "sorted": np.zeros(n, np.uint64),
+            "left": np.zeros(ni, np.int32), "skip_internal": np.zeros(ni, np.int32),
+            "skip_leaf": np.zeros(n, np.int32), "internal_box": np.zeros((ni, 6), np.float32),
+            "leaf_box": np.zeros((n, 6), np.float32), "bounds": np.zeros(6, np.float32),
+        }
+        a = [ctypes.c_void_p(out[k].ctypes.data) for k in
+             ("perm", "sorted", "left", "skip_internal", "skip_leaf", "internal_box", "leaf_box", "bounds")]
+        _check(self._lib.lbvh_batch_export(self._h, instance, *a), "lbvh_batch_export")
+        return out
+
+    def sort_variant(self) -> int:
+        v = ctypes.c_int()
+        _check(self._lib.lbvh_batch_sort_variant(self._h, ctypes.byref(v)), "lbvh_batch_sort_variant")
+        return v.value
 
 
 def morton_codes(prims, kind: int = POINTS, morton_bits: int = 30, stream=None):
