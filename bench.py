@@ -67,6 +67,16 @@ ALG_BYTES = {
     "query_overflow": lambda n, nq, hits: 0,
 }
 
+BATCH_WORKLOADS = {
+    # name: (description, clouds, min size, max size, seed, Morton bits)
+    "batched_4096_clouds": ("4,096 independent FP32 point clouds, sizes floor(exp(U(ln 256, ln 262144))) "
+                            "(seed 1), uniform in [0,1)^3; each built (30-bit codes) and queried with its own "
+                            "points at the radius for 16 expected neighbours of its size; all in one CUDA-graph "
+                            "launch vs a loop of single builds", 4096, 256, 262144, 1, 30),
+    "batched_256_clouds": ("256 clouds, sizes log-uniform in [256, 262144] (seed 1), as batched_4096_clouds "
+                           "(short case)", 256, 256, 262144, 1, 30),
+}
+
 WORKLOADS = {
     # name: (description, n, bits, kind, generator)
     "uniform_2^25_63bit": ("2^25 FP32 points uniform in [0,1)^3, 63-bit Morton codes; build + 2^25 sphere "
@@ -84,7 +94,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lbvh", "reference"], default="lbvh")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="uniform_2^25_63bit")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS),
+                    default="uniform_2^25_63bit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -243,7 +254,11 @@ def oracle_sample(seed: int, n_sample: int = 1 << 20, q_sample: int = 1 << 14, b
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    desc, n, bits = WORKLOADS[args.workload][:3]
+    if args.workload in BATCH_WORKLOADS:
+        d = BATCH_WORKLOADS[args.workload]
+        desc, n, bits = d[0], int(inputs.cloud_sizes(d[1], d[2], d[3], d[4]).sum()), d[5]
+    else:
+        desc, n, bits = WORKLOADS[args.workload][:3]
     samples = []
     for step in range(args.warmup + args.steps):
         v, sdesc, _ = oracle_sample(args.seed + step, n_sample=1 << 19, q_sample=1 << 13, bits=bits)
@@ -410,8 +425,104 @@ def run_gpu(args, world, rank, local):
     tree.close()
 
 
+def run_batch(args, world, rank, local):
+    """Batched configuration: all clouds in one graph launch per step, and the
+    same work as a loop of one lbvh_build + lbvh_query_into per cloud."""
+    import torch
+    from paper_2402_00665_gb300 import lbvh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, count, lo, hi, seed, bits = BATCH_WORKLOADS[args.workload]
+    sizes, pts_host = inputs.batched_clouds(count, lo, hi, seed + rank)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    radii_inst = np.array([inputs.radius_for_neighbours(int(k)) for k in sizes], np.float32)
+    radii = torch.from_numpy(np.repeat(radii_inst, sizes).astype(np.float32)).to(dev)
+    pts = torch.from_numpy(pts_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    batch = lbvh.Batch()
+    cap = int(20 * n)
+    offsets = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    hits = torch.empty(cap, dtype=torch.int32, device=dev)
+
+    def batch_step():
+        _, _, tot, st = batch.build_query(pts, off, lbvh.POINTS, bits, radii=radii, offsets=offsets, hits=hits)
+        if st != lbvh.OK:
+            raise lbvh.LbvhError(st, "lbvh_batch_build_query")
+        return tot
+
+    for _ in range(args.warmup):
+        total = batch_step()
+    torch.cuda.synchronize()
+    launches0 = lbvh.kernel_launches()
+    barrier(world)
+    with ClockSampler(None) as clocks:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            total = batch_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    launches = lbvh.kernel_launches() - launches0
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
+    value = n * world / (ms_step * 1e-3) / 1e6
+
+    # the loop of single builds: same clouds, same queries, one call pair each
+    tree = lbvh.Tree()
+    loff = torch.empty(int(sizes.max()) + 1, dtype=torch.int64, device=dev)
+    lhits = torch.empty(int(40 * sizes.max()) + 1024, dtype=torch.int32, device=dev)
+
+    def loop_pass():
+        tot = 0
+        for k in range(count):
+            a, e = int(off[k]), int(off[k + 1])
+            tree.build(pts[a:e], lbvh.POINTS, bits)
+            st, t = tree.query_into(pts[a:e], lbvh.SPHERE, loff[:e - a + 1], lhits, radius=float(radii_inst[k]))
+            if st != lbvh.OK:
+                raise lbvh.LbvhError(st, "lbvh_query_into")
+            tot += t
+        return tot
+
+    loop_pass()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    loop_total = loop_pass()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = ev0.elapsed_time(ev1)
+    assert loop_total == total, (loop_total, total)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "clouds": count, "n": n,
+                       "morton_bits": bits, "mean_hits": total / n,
+                       "l2": "inputs larger than L2 (points 1.9 GB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "loop_of_single_builds": {"value": n / (loop_ms * 1e-3) / 1e6, "unit": UNIT, "ms": loop_ms},
+            "speedup_vs_loop": loop_ms / ms_step,
+            "sort_variant": batch.sort_variant(),
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    batch.close()
+    tree.close()
+
+
 def main():
     args = parse()
+    if args.workload in BATCH_WORKLOADS and args.impl == "lbvh":
+        import torch
+        if not torch.cuda.is_available():
+            raise SystemExit("bench.py needs a CUDA GPU for the lbvh arm")
+        world, rank, local = dist_setup(True)
+        run_batch(args, world, rank, local)
+        return
     if args.impl == "reference":
         world, rank, _ = dist_setup(False)
         run_reference(args, world, rank)
