@@ -231,6 +231,68 @@ lbvh_status lbvh_batch_export(lbvh_batch_t batch, int64_t instance, uint32_t *h_
 /* The sort tile shape the batch's autotuner chose (-1: default, not tuned). */
 lbvh_status lbvh_batch_sort_variant(lbvh_batch_t batch, int *variant);
 
+/* ---------------------------------------------------------------- serving */
+
+typedef struct lbvh_server_s *lbvh_server_t; /* opaque */
+
+/* One request. A build request (n > 0) builds a tree of its primitives and
+ * answers its queries; a query-only request (n == 0) queries the resident
+ * tree stored under `key`. Every pointer is device memory that the caller
+ * keeps valid (inputs) or reserved (outputs) until lbvh_server_wait returns
+ * for the request. */
+typedef struct {
+    const float *d_prims;  /* build: float[n][3] or float[n][6] */
+    int64_t n;             /* primitives; 0 = query the resident tree `key` */
+    int kind;              /* lbvh_prim_kind */
+    int morton_bits;       /* as lbvh_build */
+    const float *d_queries;
+    int64_t nq;
+    int qkind;             /* lbvh_query_kind */
+    float radius;
+    const float *d_radii;  /* nullable: per-query radii */
+    int64_t *d_offsets;    /* out: int64[nq+1], the request's own CSR */
+    uint32_t *d_hits;      /* out: uint32[capacity] */
+    uint64_t capacity;
+    uint64_t key;          /* build: nonzero keeps the tree resident under this key
+                              (replacing an older one); query-only: the tree to use */
+} lbvh_request;
+
+typedef struct {
+    lbvh_status status;   /* LBVH_ERR_CAPACITY: `total` is the need; LBVH_ERR_INVALID for a
+                             query on a key that is not resident (never built, or evicted) */
+    uint64_t total;       /* hits of the request */
+    double queued_s;      /* submission -> start of the batch that ran it */
+    double service_s;     /* start of that batch -> results in the request's buffers */
+    double latency_s;     /* submission -> results in the request's buffers */
+    int batch_size;       /* requests that ran in the same batch */
+} lbvh_result;
+
+/* Start a request server: `slots` worker streams (1..16), each running one
+ * batch at a time, so up to `slots` batches overlap on the device; at most
+ * `max_batch` requests per batch. The scheduler admits queued requests in
+ * arrival order while their estimated working bytes plus the bytes of the
+ * resident trees fit `hbm_budget_bytes`, evicting the least recently used
+ * resident trees (not in use) to make room; requests that arrive while others
+ * run join the next batch as soon as a slot and memory are free (continuous
+ * batching). Build requests in one batch share primitive kind, Morton bits
+ * and query kind (a request of another kind starts the next batch). Each
+ * request's results equal those of lbvh_build + lbvh_query_into on it alone. */
+lbvh_status lbvh_server_create(uint64_t hbm_budget_bytes, int slots, int max_batch,
+                               lbvh_server_t *out);
+
+/* Queue a request (copied; returns at once). *ticket identifies it. */
+lbvh_status lbvh_server_submit(lbvh_server_t server, const lbvh_request *request, uint64_t *ticket);
+
+/* Block until the request has finished; fills *result and forgets the ticket. */
+lbvh_status lbvh_server_wait(lbvh_server_t server, uint64_t ticket, lbvh_result *result);
+
+/* Resident-tree bytes and count, evictions and batches so far (any pointer may be NULL). */
+lbvh_status lbvh_server_stats(lbvh_server_t server, uint64_t *resident_bytes, uint64_t *resident_trees,
+                              uint64_t *evictions, uint64_t *batches);
+
+/* Finish all queued work, then stop the threads and free everything. */
+void lbvh_server_destroy(lbvh_server_t server);
+
 /* ---------------------------------------------------------------- no allocation */
 
 /* Largest n accepted by lbvh_construct_static. */

@@ -353,6 +353,7 @@ struct lbvh_batch_s {
     lbvh::Control *h_ctl = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_kernels = 0;
+    bool graphs = true;             // record and replay CUDA graphs (off: run directly every call)
     cudaStream_t stream = nullptr;  // the batch's own stream (capturable), ordered after the caller's
     cudaEvent_t ordered = nullptr;
 
@@ -925,7 +926,25 @@ lbvh_status lbvh_batch_build_query(lbvh_batch_t b, const float *d_prims, const i
     sig.hits = d_hits;
     sig.capacity = capacity;
     lbvh_status st = LBVH_OK;
-    if (!(b->ready && b->sig == sig)) {
+    if (!b->graphs) {
+        // run directly: set up when the instance tables change, use a tuned
+        // tile shape if one is known for this size, never capture
+        const bool same_tables = b->ready && b->sig.prim_off == sig.prim_off && b->sig.query_off == sig.query_off &&
+                                 b->sig.kind == sig.kind && b->sig.bits == sig.bits;
+        b->sig = sig;
+        if (!same_tables) {
+            b->ready = false;
+            if ((st = batch_setup(b, s)) != LBVH_OK) return st;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            auto it = g_tuned_variant.find({ceil_log2(b->N), b->passes});
+            b->sort_variant = it != g_tuned_variant.end() ? it->second : -1;
+        } else {
+            const bool same_points = qkind == LBVH_Q_SPHERE && kind == LBVH_PRIM_POINTS;
+            const bool same_boxes = qkind == LBVH_Q_BOX && kind == LBVH_PRIM_BOXES;
+            b->self_query = d_queries == d_prims && sig.query_off == sig.prim_off && (same_points || same_boxes);
+        }
+        if ((st = batch_enqueue(b, s)) != LBVH_OK) return st;
+    } else if (!(b->ready && b->sig == sig)) {
         // a new shape: set up, tune, run once directly, then capture a graph
         b->drop_graph();
         const bool same_tables = b->ready && b->sig.prim_off == sig.prim_off && b->sig.query_off == sig.query_off &&
@@ -1028,6 +1047,58 @@ lbvh_status lbvh_batch_sort_variant(lbvh_batch_t b, int *variant) {
     *variant = b->sort_variant;
     return LBVH_OK;
 }
+
+}  // extern "C"
+
+namespace lbvh {
+
+void batch_set_graphs(lbvh_batch_t b, bool on) {
+    if (b->graphs != on) b->drop_graph();
+    b->graphs = on;
+}
+
+namespace {
+__global__ void rebase_u32_kernel(uint32_t *dst, const uint32_t *src, int64_t n, uint32_t sub) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] - sub;
+}
+__global__ void mask_u64_kernel(uint64_t *dst, const uint64_t *src, int64_t n, uint64_t mask) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i] & mask;
+}
+}  // namespace
+
+lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cudaStream_t s) {
+    if (!b || !b->ready || !t || instance < 0 || instance >= b->count) return LBVH_ERR_INVALID;
+    const int64_t o = b->sig.prim_off[instance];
+    const int64_t n = b->sig.prim_off[instance + 1] - o;
+    const int kind = b->sig.kind;
+    lbvh_status st = reserve_tree(t, n, kind, s);
+    if (st != LBVH_OK) return st;
+    t->n = n;
+    t->kind = kind;
+    t->bits = b->sig.bits;
+    t->sorted_in_b = false;
+    t->prims_ptr = nullptr;
+    LBVH_CUDA(cudaMemsetAsync(&t->dctl()->build_flags, 0, sizeof(uint32_t), s));
+    LBVH_CUDA(cudaMemcpyAsync(t->bounds.p, b->bounds.as<float>() + 6 * instance, 24, cudaMemcpyDeviceToDevice, s));
+    if (n > 0) {
+        const int64_t units = 2 * (n - 1) + (kind == LBVH_PRIM_POINTS ? n : 2 * n);
+        LBVH_CUDA(cudaMemcpyAsync(t->nodes.p, b->nodes.as<float4>() + b->h_node_start[instance], units * 16,
+                                  cudaMemcpyDeviceToDevice, s));
+        const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
+        rebase_u32_kernel<<<blocks, 256, 0, s>>>(t->vals[0].as<uint32_t>(), b->perm() + o, n, (uint32_t)o);
+        const uint64_t mask = b->sig.bits >= 64 ? ~0ull : ((1ull << b->sig.bits) - 1ull);
+        mask_u64_kernel<<<blocks, 256, 0, s>>>(t->keys[0].as<uint64_t>(), b->sorted_codes() + o, n, mask);
+        count_launches(2);
+        LBVH_LAUNCHED();
+    }
+    return finish_build(t, s);
+}
+
+}  // namespace lbvh
+
+extern "C" {
 
 lbvh_status lbvh_tree_set_profiling(lbvh_tree_t t, int on) {
     if (!t) return LBVH_ERR_INVALID;

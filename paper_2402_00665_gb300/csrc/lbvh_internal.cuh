@@ -227,6 +227,11 @@ void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt,
 void launch_query_copy_checked(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
                                uint32_t *hits, unsigned long long capacity, Control *ctl, cudaStream_t s);
 
+// Used by the request server (server.cu): run a batch without graph capture,
+// and copy one instance of a finished batch into a tree of its own.
+void batch_set_graphs(lbvh_batch_t b, bool on);
+lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cudaStream_t s);
+
 int device_sm_count();
 
 // Adds k to the process-wide count of kernels launched by this library.

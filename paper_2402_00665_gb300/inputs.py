@@ -12,6 +12,7 @@ Workloads (the paper's own experiments use synthetic clouds as well, Sec. 5):
   (component centres uniform in [0, 1]^3, equal weights), half-extents
   lognormal per axis. At 30-bit codes most centres of a component share a
   Morton code, which stresses the index tie-break.
+* ``gaussian_mixture_points`` - points from the same kind of mixture.
 * ``batched_clouds`` - many independent uniform clouds with log-uniform sizes.
 * ``poisson_requests`` - arrival times and sizes of a served request stream.
 * ``filled_cube`` / ``hollow_cube`` - the two point clouds of the paper's
@@ -55,6 +56,16 @@ def gaussian_mixture_boxes(n: int, seed: int = 0, components: int = 64, sigma: f
     out[:, :3] = (c - h).astype(np.float32)
     out[:, 3:] = (c + h).astype(np.float32)
     return out
+
+
+def gaussian_mixture_points(n: int, seed: int = 0, components: int = 64, sigma: float = 0.005) -> np.ndarray:
+    """float32[n, 3] points from a mixture of isotropic Gaussians (component
+    centres uniform in [0, 1]^3, equal weights)."""
+    crng = np.random.default_rng(seed)
+    centres = crng.random((components, 3))
+    rng = np.random.default_rng([seed, 3])
+    which = rng.integers(0, components, size=n)
+    return (centres[which] + rng.normal(0.0, sigma, size=(n, 3))).astype(np.float32)
 
 
 def cloud_sizes(count: int, lo: int, hi: int, seed: int = 1) -> np.ndarray:

@@ -50,6 +50,11 @@ SIGNATURES = {
     "lbvh_batch_build_query": (_I32, [_P, _P, _P, _I64, _I32, _I32, _P, _P, _I32, _P, _F32, _P, _P, _U64, _P, _P]),
     "lbvh_batch_export": (_I32, [_P, _I64] + [_P] * 8),
     "lbvh_batch_sort_variant": (_I32, [_P, _P]),
+    "lbvh_server_create": (_I32, [_U64, _I32, _I32, _P]),
+    "lbvh_server_submit": (_I32, [_P, _P, _P]),
+    "lbvh_server_wait": (_I32, [_P, _U64, _P]),
+    "lbvh_server_stats": (_I32, [_P, _P, _P, _P, _P]),
+    "lbvh_server_destroy": (None, [_P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
     "lbvh_tree_stage_times": (_I32, [_P, _P]),
@@ -326,6 +331,85 @@ class Batch:
         v = ctypes.c_int()
         _check(self._lib.lbvh_batch_sort_variant(self._h, ctypes.byref(v)), "lbvh_batch_sort_variant")
         return v.value
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("d_prims", ctypes.c_void_p), ("n", ctypes.c_int64), ("kind", ctypes.c_int),
+                ("morton_bits", ctypes.c_int), ("d_queries", ctypes.c_void_p), ("nq", ctypes.c_int64),
+                ("qkind", ctypes.c_int), ("radius", ctypes.c_float), ("d_radii", ctypes.c_void_p),
+                ("d_offsets", ctypes.c_void_p), ("d_hits", ctypes.c_void_p), ("capacity", ctypes.c_uint64),
+                ("key", ctypes.c_uint64)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("total", ctypes.c_uint64), ("queued_s", ctypes.c_double),
+                ("service_s", ctypes.c_double), ("latency_s", ctypes.c_double), ("batch_size", ctypes.c_int)]
+
+
+class Server:
+    """Request server (``lbvh_server_*``): build + query requests batched as
+    they arrive, trees kept resident under an HBM byte budget."""
+
+    def __init__(self, budget_bytes: int, slots: int = 2, max_batch: int = 64):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.lbvh_server_create(int(budget_bytes), slots, max_batch, ctypes.byref(h)),
+               "lbvh_server_create")
+        self._h = h
+        self._live = {}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lbvh_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, prims=None, kind: int = POINTS, morton_bits: int = 30, queries=None, qkind: int = SPHERE,
+               radius: float = 0.0, radii=None, capacity: int | None = None, key: int = 0) -> int:
+        """Queue a request; ``prims=None`` queries the resident tree ``key``.
+        ``queries=None`` queries the primitives themselves."""
+        torch = _torch()
+        p = None if prims is None else (prims if isinstance(prims, torch.Tensor) and prims.is_cuda
+                                        else _dev(prims, torch.float32))
+        q = p if queries is None else (queries if isinstance(queries, torch.Tensor) and queries.is_cuda
+                                       else _dev(queries, torch.float32))
+        if q is None:
+            raise ValueError("a query-only request needs queries")
+        n = 0 if p is None else p.numel() // (3 if kind == POINTS else 6)
+        nq = q.numel() // (3 if qkind == SPHERE else 6)
+        r = None
+        if radii is not None:
+            r = radii if isinstance(radii, torch.Tensor) and radii.is_cuda else _dev(radii, torch.float32).reshape(-1)
+        cap = int(capacity) if capacity is not None else max(32 * nq, 64)
+        offsets = torch.empty(nq + 1, dtype=torch.int64, device="cuda")
+        hits = torch.empty(max(cap, 1), dtype=torch.int32, device="cuda")
+        req = _Request(_ptr(p), n, kind, morton_bits, _ptr(q), nq, qkind, float(radius), _ptr(r),
+                       _ptr(offsets), _ptr(hits), cap, int(key))
+        ticket = ctypes.c_uint64()
+        torch.cuda.current_stream().synchronize()  # inputs written on the caller's stream are complete
+        _check(self._lib.lbvh_server_submit(self._h, ctypes.byref(req), ctypes.byref(ticket)), "lbvh_server_submit")
+        self._live[ticket.value] = (p, q, r, offsets, hits)
+        return ticket.value
+
+    def wait(self, ticket: int):
+        """Block until done: (offsets, hits[:total], result dict)."""
+        res = _Result()
+        _check(self._lib.lbvh_server_wait(self._h, ticket, ctypes.byref(res)), "lbvh_server_wait")
+        _, _, _, offsets, hits = self._live.pop(ticket)
+        info = {"status": res.status, "total": res.total, "queued_s": res.queued_s,
+                "service_s": res.service_s, "latency_s": res.latency_s, "batch_size": res.batch_size}
+        return offsets, hits[:res.total] if res.status == OK else hits[:0], info
+
+    def stats(self) -> dict:
+        v = [ctypes.c_uint64() for _ in range(4)]
+        _check(self._lib.lbvh_server_stats(self._h, *[ctypes.byref(x) for x in v]), "lbvh_server_stats")
+        return dict(zip(("resident_bytes", "resident_trees", "evictions", "batches"), (x.value for x in v)))
 
 
 def morton_codes(prims, kind: int = POINTS, morton_bits: int = 30, stream=None):
