@@ -77,6 +77,19 @@ BATCH_WORKLOADS = {
                            "(short case)", 256, 256, 262144, 1, 30),
 }
 
+SERVED_WORKLOADS = {
+    # name: (description, requests, rate per s, min size, max size, seed, Morton bits, budget bytes)
+    "served_poisson_2000": ("Poisson stream at 2,000 requests/s; each request builds a tree of its own "
+                            "FP32 point cloud (sizes log-uniform in [1,024, 4,194,304]; uniform or "
+                            "64-component Gaussian mixture, alternating at random) with 63-bit codes and "
+                            "answers one ~16-neighbour sphere query per point; trees stay resident under a "
+                            "60 GB HBM budget with LRU eviction; served with continuous batching vs "
+                            "one-at-a-time processing of the same arrivals", 400, 2000.0, 1024, 4194304, 2, 63,
+                            60 << 30),
+    "served_poisson_short": ("as served_poisson_2000 with 60 requests (short case)", 60, 2000.0, 1024, 4194304,
+                             2, 63, 60 << 30),
+}
+
 WORKLOADS = {
     # name: (description, n, bits, kind, generator)
     "uniform_2^25_63bit": ("2^25 FP32 points uniform in [0,1)^3, 63-bit Morton codes; build + 2^25 sphere "
@@ -94,7 +107,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lbvh", "reference"], default="lbvh")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS),
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVED_WORKLOADS),
                     default="uniform_2^25_63bit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -257,6 +270,9 @@ def run_reference(args, world, rank):
     if args.workload in BATCH_WORKLOADS:
         d = BATCH_WORKLOADS[args.workload]
         desc, n, bits = d[0], int(inputs.cloud_sizes(d[1], d[2], d[3], d[4]).sum()), d[5]
+    elif args.workload in SERVED_WORKLOADS:
+        d = SERVED_WORKLOADS[args.workload]
+        desc, n, bits = d[0], int(inputs.poisson_requests(d[1], d[2], d[3], d[4], d[5])[1].sum()), d[6]
     else:
         desc, n, bits = WORKLOADS[args.workload][:3]
     samples = []
@@ -514,8 +530,141 @@ def run_batch(args, world, rank, local):
     tree.close()
 
 
+def mixture_radius(n: int, k: float = 16.0, components: int = 64, sigma: float = 0.005) -> float:
+    """Radius holding ~k neighbours of a point of an equal-weight Gaussian
+    mixture: the expected density at a sample of one component is
+    (n / components) / ((4 pi)^(3/2) sigma^3)."""
+    density = (n / components) / ((4.0 * math.pi) ** 1.5 * sigma ** 3)
+    return float(np.float32((3.0 * k / (4.0 * math.pi * density)) ** (1.0 / 3.0)))
+
+
+def run_served(args, world, rank, local):
+    """Served configuration: requests arrive on a Poisson schedule; the request
+    server batches them continuously; the same arrivals are then processed one
+    at a time (lbvh_build + lbvh_query_into per request, in arrival order)."""
+    import threading
+
+    import torch
+    from paper_2402_00665_gb300 import lbvh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, count, rate, lo, hi, seed, bits, budget = SERVED_WORKLOADS[args.workload]
+    arrivals, sizes, kinds = inputs.poisson_requests(count, rate, lo, hi, seed + rank)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    host = np.empty((int(off[-1]), 3), np.float32)
+    radii = np.empty(count, np.float32)
+    for k in range(count):
+        n = int(sizes[k])
+        if kinds[k] == 0:
+            host[off[k]:off[k + 1]] = inputs.uniform_points(n, seed=1000 + k)
+            radii[k] = inputs.radius_for_neighbours(n)
+        else:
+            host[off[k]:off[k + 1]] = inputs.gaussian_mixture_points(n, seed=1000 + k)
+            radii[k] = mixture_radius(n)
+    pts = torch.from_numpy(host).to(dev)
+    views = [pts[off[k]:off[k + 1]] for k in range(count)]
+    caps = [int(40 * sizes[k]) + 1024 for k in range(count)]
+    torch.cuda.synchronize()
+
+    def percentiles(lat):
+        lat = np.sort(np.asarray(lat))
+        return float(np.percentile(lat, 50) * 1e3), float(np.percentile(lat, 99) * 1e3)
+
+    # ---- served: a submitter follows the arrival schedule
+    srv = lbvh.Server(budget, slots=3, max_batch=64)
+    warm = srv.submit(views[0], lbvh.POINTS, bits, radius=float(radii[0]), capacity=caps[0])
+    srv.wait(warm)
+    tickets = [None] * count
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k in range(count):
+            delay = t0 + arrivals[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(views[k], lbvh.POINTS, bits, radius=float(radii[k]), capacity=caps[k],
+                                    key=k + 1)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, batch_sizes, totals = [], [], 0
+    launches0 = lbvh.kernel_launches()
+    with ClockSampler(None) as clocks:
+        for k in range(count):
+            while tickets[k] is None:
+                time.sleep(0.0001)
+            _, _, info = srv.wait(tickets[k])
+            if info["status"] != lbvh.OK:
+                raise lbvh.LbvhError(info["status"], "served request")
+            lat.append(info["latency_s"])
+            batch_sizes.append(info["batch_size"])
+            totals += info["total"]
+        t_end = time.perf_counter()
+    th.join()
+    launches = lbvh.kernel_launches() - launches0
+    stats = srv.stats()
+    srv.close()
+    served_s = t_end - t0
+    served_p50, served_p99 = percentiles(lat)
+
+    # ---- one at a time, same arrivals
+    tree = lbvh.Tree()
+    fo = torch.empty(int(sizes.max()) + 1, dtype=torch.int64, device=dev)
+    fh = torch.empty(max(caps), dtype=torch.int32, device=dev)
+    tree.build(views[0], lbvh.POINTS, bits)
+    tree.query_into(views[0], lbvh.SPHERE, fo[:int(sizes[0]) + 1], fh, radius=float(radii[0]))
+    torch.cuda.synchronize()
+    flat, ftotal = [], 0
+    t0 = time.perf_counter()
+    for k in range(count):
+        wait = t0 + arrivals[k] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        tree.build(views[k], lbvh.POINTS, bits)
+        st, tot = tree.query_into(views[k], lbvh.SPHERE, fo[:int(sizes[k]) + 1], fh, radius=float(radii[k]))
+        if st != lbvh.OK:
+            raise lbvh.LbvhError(st, "lbvh_query_into")
+        ftotal += tot
+        flat.append(time.perf_counter() - (t0 + arrivals[k]))
+    fifo_s = time.perf_counter() - t0
+    tree.close()
+    assert ftotal == totals, (ftotal, totals)
+    fifo_p50, fifo_p99 = percentiles(flat)
+    n = int(off[-1])
+    value = n * world / served_s / 1e6
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": served_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "requests": count, "rate_per_s": rate,
+                       "n_total": n, "morton_bits": bits, "budget_bytes": budget,
+                       "offered_mprims_s": n / float(arrivals[-1]) / 1e6,
+                       "mean_hits": totals / n, "parallelism": "replicas" if world > 1 else "single"},
+            "served": {"throughput_mprims_s": value, "p50_ms": served_p50, "p99_ms": served_p99,
+                       "wall_s": served_s, "mean_batch": float(np.mean(batch_sizes)),
+                       "batches": stats["batches"], "resident_trees": stats["resident_trees"],
+                       "resident_bytes": stats["resident_bytes"], "evictions": stats["evictions"]},
+            "one_at_a_time": {"throughput_mprims_s": n / fifo_s / 1e6, "p50_ms": fifo_p50, "p99_ms": fifo_p99,
+                              "wall_s": fifo_s},
+            "speedup_vs_one_at_a_time": fifo_s / served_s,
+            "timing": "wall clock from the first arrival to the last completion; latency = arrival to results",
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload in SERVED_WORKLOADS and args.impl == "lbvh":
+        import torch
+        if not torch.cuda.is_available():
+            raise SystemExit("bench.py needs a CUDA GPU for the lbvh arm")
+        world, rank, local = dist_setup(True)
+        run_served(args, world, rank, local)
+        return
     if args.workload in BATCH_WORKLOADS and args.impl == "lbvh":
         import torch
         if not torch.cuda.is_available():
