@@ -156,6 +156,13 @@ lbvh_status lbvh_query(lbvh_tree_t tree, const float *d_queries, int64_t nq, int
 /* Free device memory returned by lbvh_query. Accepts NULL. */
 void lbvh_free(void *d_ptr);
 
+/* Device memory that trees, batches and servers allocate comes from one
+ * stream-ordered pool per device that the library owns and that keeps freed
+ * blocks for reuse (so repeated builds do not map and unmap memory). This
+ * returns the pool's unused blocks to the device; blocks held by live trees,
+ * batches and servers stay. */
+lbvh_status lbvh_release_cached_memory(void);
+
 /* ---------------------------------------------------------------- stages */
 
 /* Scene bounds and Morton code of every primitive (Sec. 3.1 step 1): the
@@ -182,6 +189,10 @@ lbvh_status lbvh_sort_pairs(const uint64_t *d_keys, const uint32_t *d_vals, int6
 
 typedef struct lbvh_batch_s *lbvh_batch_t; /* opaque; device storage owned by the library */
 
+/* Most instances in one batch call (the sort keeps 1 KiB of digit counts per
+ * instance and pass). */
+#define LBVH_MAX_BATCH (1 << 20)
+
 /* Create an empty batch handle. */
 lbvh_status lbvh_batch_create(lbvh_batch_t *out);
 
@@ -191,15 +202,16 @@ void lbvh_batch_destroy(lbvh_batch_t batch);
 /* Build `count` independent trees and answer each tree's own queries in one
  * pass over all of them: the same method as lbvh_build + lbvh_query_into per
  * instance (Sec. 3.1 steps 1-4, Algorithm 4, Algorithm 1), with every step
- * run once for the whole batch (per-instance scene bounds; one radix sort of
- * keys that carry the instance index above the Morton code; the bottom-up
- * pass of all trees at once; one walk kernel for all queries). Each
+ * run once for the whole batch (per-instance scene bounds; one segmented
+ * radix sort in which every instance's codes are sorted on their own; the
+ * bottom-up pass of all trees at once; one walk kernel for all queries). Each
  * instance's tree and hit lists are identical to what a single build of that
  * instance produces.
  *   d_prims          concatenated primitives (layout of lbvh_build), device.
+ *   count            number of instances, 1 <= count <= LBVH_MAX_BATCH.
  *   h_prim_offsets   host int64[count+1], h_prim_offsets[0] == 0: instance b
  *                    owns primitives [off[b], off[b+1]) (may be empty).
- *   morton_bits      as lbvh_build; morton_bits + ceil(log2(count)) <= 64.
+ *   morton_bits      as lbvh_build (any width; instances are sorted apart).
  *   d_queries        concatenated queries (layout of lbvh_query_into).
  *   h_query_offsets  host int64[count+1]: queries of instance b.
  *   d_radii/radius   as lbvh_query_into (per query, or one for all).
@@ -213,7 +225,7 @@ void lbvh_batch_destroy(lbvh_batch_t batch);
  * batch (CUDA-event timing) and records the whole pipeline as one CUDA graph;
  * later calls with the same arguments launch that graph once. Every call
  * synchronises `stream` once at the end (to report total and status). Totals
- * of primitives and of queries are each below 2^32. */
+ * of primitives and of queries are each below 2^31. */
 lbvh_status lbvh_batch_build_query(lbvh_batch_t batch, const float *d_prims,
                                    const int64_t *h_prim_offsets, int64_t count, int kind,
                                    int morton_bits, const float *d_queries,
@@ -289,6 +301,18 @@ lbvh_status lbvh_server_wait(lbvh_server_t server, uint64_t ticket, lbvh_result 
 /* Resident-tree bytes and count, evictions and batches so far (any pointer may be NULL). */
 lbvh_status lbvh_server_stats(lbvh_server_t server, uint64_t *resident_bytes, uint64_t *resident_trees,
                               uint64_t *evictions, uint64_t *batches);
+
+/* Where the workers' time went, summed over all batches so far (host wall
+ * clock, so with several slots the sums can exceed the elapsed time):
+ *   seconds[0]  staging a batch's inputs (copies into one concatenated batch),
+ *   seconds[1]  the batched build + query (lbvh_batch_build_query, which
+ *               waits for its own results),
+ *   seconds[2]  handing the results to each request and copying the trees
+ *               that stay resident, up to the wait for those copies,
+ *   seconds[3]  query-only requests.
+ * `seconds` holds LBVH_SERVER_PHASES doubles. */
+#define LBVH_SERVER_PHASES 4
+lbvh_status lbvh_server_phase_seconds(lbvh_server_t server, double *seconds);
 
 /* Finish all queued work, then stop the threads and free everything. */
 void lbvh_server_destroy(lbvh_server_t server);

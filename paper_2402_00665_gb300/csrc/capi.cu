@@ -2,6 +2,7 @@
 // a tree, and the order of kernel launches for a build and a query. No
 // arithmetic of the method happens here; every step runs in the kernels.
 #include <atomic>
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -41,10 +42,10 @@ struct DevBuf {
 
     cudaError_t ensure(size_t want, cudaStream_t s, bool zero = false) {
         if (want <= bytes) return cudaSuccess;
-        if (p) cudaFreeAsync(p, s);
+        if (p) lbvh::pool_free(p, s);
         p = nullptr;
         bytes = 0;
-        cudaError_t e = cudaMallocAsync(&p, want, s);
+        cudaError_t e = lbvh::pool_alloc(&p, want, s);
         if (e != cudaSuccess) {
             p = nullptr;
             return e;
@@ -54,7 +55,7 @@ struct DevBuf {
         return e;
     }
     void release(cudaStream_t s) {
-        if (p) cudaFreeAsync(p, s);
+        if (p) lbvh::pool_free(p, s);
         p = nullptr;
         bytes = 0;
     }
@@ -63,6 +64,40 @@ struct DevBuf {
         return static_cast<T *>(p);
     }
 };
+
+// Pinned host mirrors of the control block. They are carved from 64 KiB
+// pinned pages that live until the process exits and are recycled, never
+// freed: cudaFreeHost would wait for the whole device, which a request server
+// evicting trees while other batches run cannot afford.
+struct PinnedControls {
+    std::mutex mu;
+    std::vector<lbvh::Control *> free_list;
+
+    cudaError_t get(lbvh::Control **out) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (free_list.empty()) {
+            constexpr size_t kPage = 64 << 10, kEach = (sizeof(lbvh::Control) + 127) & ~size_t(127);
+            void *page = nullptr;
+            const cudaError_t e = cudaHostAlloc(&page, kPage, cudaHostAllocPortable);
+            if (e != cudaSuccess) return e;
+            for (size_t off = 0; off + kEach <= kPage; off += kEach)
+                free_list.push_back(reinterpret_cast<lbvh::Control *>(static_cast<char *>(page) + off));
+        }
+        *out = free_list.back();
+        free_list.pop_back();
+        return cudaSuccess;
+    }
+    void put(lbvh::Control *c) {
+        if (!c) return;
+        std::lock_guard<std::mutex> lock(mu);
+        free_list.push_back(c);
+    }
+};
+
+PinnedControls &pinned_controls() {
+    static PinnedControls *pool = new PinnedControls();  // never destroyed (used until exit)
+    return *pool;
+}
 
 bool valid_bits(int bits) { return bits >= 3 && bits <= 63 && bits % 3 == 0; }
 
@@ -115,6 +150,9 @@ struct Profiler {
 struct lbvh_tree_s {
     cudaStream_t stream = nullptr;  // stream of the last build
     cudaEvent_t built = nullptr;    // recorded after the last build
+    cudaEvent_t used = nullptr;     // recorded after the last query's last kernel
+    bool queried = false;           // `used` has been recorded
+    bool lean = false;              // nodes and bounds only (no perm / codes): queries, no export
     int64_t n = 0;
     int kind = LBVH_PRIM_POINTS;
     int bits = 0;
@@ -126,7 +164,7 @@ struct lbvh_tree_s {
     DevBuf counts, tile_sums, overflow, slots;
     DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
     const float *prims_ptr = nullptr;      // the last build's input (self-queries)
-    lbvh::Control *h_ctl = nullptr;  // pinned mirror of the control block
+    lbvh::Control *h_ctl = nullptr;  // pinned mirror of the control block (from pinned_controls())
     Profiler prof;
 
     const uint64_t *sorted_codes() const { return keys[sorted_in_b ? 1 : 0].as<uint64_t>(); }
@@ -146,6 +184,53 @@ namespace lbvh {
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+namespace {
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;  // per device, kept until the process exits
+
+cudaError_t device_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    g_pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+}  // namespace
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = device_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void pool_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+cudaError_t pool_reserve(size_t bytes, cudaStream_t s) {
+    void *p = nullptr;
+    cudaError_t e = pool_alloc(&p, bytes, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaFreeAsync(p, s)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
 
 int device_sm_count() {
     static int sms = 0;
@@ -179,7 +264,8 @@ lbvh_status reserve_tree(lbvh_tree_s *t, int64_t n, int kind, cudaStream_t s) {
     LBVH_CUDA(t->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
     LBVH_CUDA(t->partials.ensure((size_t)bounds_blocks(n) * 8 * 4, s));
     LBVH_CUDA(t->bounds.ensure(6 * 4, s));
-    if (!t->h_ctl) LBVH_CUDA(cudaMallocHost(&t->h_ctl, sizeof(Control)));
+    if (!t->h_ctl) LBVH_CUDA(pinned_controls().get(&t->h_ctl));
+    t->lean = false;
     return LBVH_OK;
 }
 
@@ -199,6 +285,7 @@ lbvh_status finish_build(lbvh_tree_t t, cudaStream_t s) {
 }
 
 lbvh_status read_control(lbvh_tree_t t, cudaStream_t s) {
+    if (!t->h_ctl) LBVH_CUDA(pinned_controls().get(&t->h_ctl));
     LBVH_CUDA(cudaMemcpyAsync(t->h_ctl, t->ctl.p, sizeof(lbvh::Control), cudaMemcpyDeviceToHost, s));
     LBVH_CUDA(cudaStreamSynchronize(s));
     if (t->h_ctl->build_flags & (lbvh::kFlagTimeout | lbvh::kFlagCorrupt)) t->store_dirty = true;
@@ -294,10 +381,14 @@ lbvh_status query_fill(lbvh_tree_t t, const lbvh::QueryArgs &qa, const int64_t *
     LBVH_LAUNCHED();
     if (t->h_ctl->overflow_filled > 0) {
         t->prof.begin(LBVH_STAGE_QFIXUP, s);
-        launch_query_overflow(t->view(), qa, qs, t->h_ctl->overflow_filled, d_offsets, d_hits, s);
+        launch_query_overflow(t->view(), qa, qs, t->h_ctl->overflow_filled, d_offsets, d_hits, t->dctl(), s);
         t->prof.end(LBVH_STAGE_QFIXUP, s);
         LBVH_LAUNCHED();
     }
+    // the last kernels that read this tree's buffers: destroy waits for them
+    if (!t->used) LBVH_CUDA(cudaEventCreateWithFlags(&t->used, cudaEventDisableTiming));
+    LBVH_CUDA(cudaEventRecord(t->used, s));
+    t->queried = true;
     return LBVH_OK;
 }
 
@@ -344,11 +435,16 @@ struct lbvh_batch_s {
     BatchSignature sig;
     bool ready = false;   // buffers and tables match `sig`
     int64_t count = 0, N = 0, NQ = 0, nchunks = 0, nqchunks = 0;
-    int ibits = 0, passes = 0, qpasses = 0, sort_variant = -1;
+    int passes = 0, qpasses = 0, sort_variant = -1;
     bool self_query = false, sorted_in_b = false;
     DevBuf prim_off, query_off, node_start, store_start, chunks, chunk_first, qchunks;
     DevBuf keys[2], vals[2], nodes, store, lookback, hist, partials, bounds, ctl;
     DevBuf count_pos, slots, overflow, tile_sums, qkeys[2], qvals[2], qlookback;
+    // Segmented-sort tile tables: row r (r < sort_variant_count(): that
+    // variant; the last row: the default variant) holds count + 1 entries.
+    DevBuf tile_first, qtile_first;
+    std::vector<int64_t> h_tiles, h_qtiles;  // tiles per row
+    int64_t max_tiles = 0, max_qtiles = 0;
     std::vector<int64_t> h_node_start;
     lbvh::Control *h_ctl = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -366,6 +462,14 @@ struct lbvh_batch_s {
     const uint64_t *sorted_codes() const { return keys[sorted_in_b ? 1 : 0].as<uint64_t>(); }
     const uint32_t *perm() const { return vals[sorted_in_b ? 1 : 0].as<uint32_t>(); }
     lbvh::Control *dctl() const { return ctl.as<lbvh::Control>(); }
+    // Segments of the primitive (or query) sort for tile shape `variant`.
+    lbvh::SortSegments segments(bool queries, int variant) const {
+        const int rows = (int)h_tiles.size();
+        const int r = (variant >= 0 && variant < rows - 1) ? variant : rows - 1;
+        const int64_t *tf = (queries ? qtile_first : tile_first).as<int64_t>() + (int64_t)r * (count + 1);
+        return lbvh::SortSegments{(queries ? query_off : prim_off).as<int64_t>(), tf, (int)count,
+                                  (queries ? h_qtiles : h_tiles)[r]};
+    }
     void drop_graph() {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
@@ -399,9 +503,8 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
     b->count = (int64_t)g.prim_off.size() - 1;
     b->N = g.prim_off.back();
     b->NQ = g.query_off.back();
-    b->ibits = ceil_log2(b->count);
-    b->passes = sort_passes(g.bits + b->ibits);
-    b->qpasses = sort_passes(30 + b->ibits);
+    b->passes = sort_passes(g.bits);
+    b->qpasses = sort_passes(30);
     const bool same_points = g.qkind == LBVH_Q_SPHERE && g.kind == LBVH_PRIM_POINTS;
     const bool same_boxes = g.qkind == LBVH_Q_BOX && g.kind == LBVH_PRIM_BOXES;
     b->self_query = g.queries == g.prims && g.query_off == g.prim_off && (same_points || same_boxes);
@@ -422,7 +525,30 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
         }
     }
     b->h_node_start = node_start;
+    // Tile tables of the segmented sorts, one row per tile shape.
+    const int rows = sort_variant_count() + 1;
+    std::vector<int64_t> tf((size_t)rows * (b->count + 1)), qtf((size_t)rows * (b->count + 1));
+    b->h_tiles.assign(rows, 0);
+    b->h_qtiles.assign(rows, 0);
+    for (int r = 0; r < rows; ++r) {
+        const int64_t tk = sort_variant_tile_keys(r < rows - 1 ? r : -1);
+        int64_t t = 0, qt = 0;
+        for (int64_t k = 0; k <= b->count; ++k) {
+            tf[(size_t)r * (b->count + 1) + k] = t;
+            qtf[(size_t)r * (b->count + 1) + k] = qt;
+            if (k < b->count) {
+                t += (g.prim_off[k + 1] - g.prim_off[k] + tk - 1) / tk;
+                qt += (g.query_off[k + 1] - g.query_off[k] + tk - 1) / tk;
+            }
+        }
+        b->h_tiles[r] = t;
+        b->h_qtiles[r] = qt;
+    }
+    b->max_tiles = *std::max_element(b->h_tiles.begin(), b->h_tiles.end());
+    b->max_qtiles = *std::max_element(b->h_qtiles.begin(), b->h_qtiles.end());
     lbvh_status st;
+    if ((st = upload(b->tile_first, tf.data(), tf.size() * 8, s)) != LBVH_OK) return st;
+    if ((st = upload(b->qtile_first, qtf.data(), qtf.size() * 8, s)) != LBVH_OK) return st;
     if ((st = upload(b->prim_off, g.prim_off.data(), g.prim_off.size() * 8, s)) != LBVH_OK) return st;
     if ((st = upload(b->query_off, g.query_off.data(), g.query_off.size() * 8, s)) != LBVH_OK) return st;
     if ((st = upload(b->node_start, node_start.data(), node_start.size() * 8, s)) != LBVH_OK) return st;
@@ -440,16 +566,16 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
     }
     LBVH_CUDA(b->nodes.ensure((size_t)units * 16 + 16, s));
     LBVH_CUDA(b->store.ensure((size_t)words * 8 + 8, s, true));
-    LBVH_CUDA(b->lookback.ensure((size_t)sort_tiles_max(b->N) * kRadix * 8 + 8, s));
-    LBVH_CUDA(b->qlookback.ensure((size_t)sort_tiles_max(b->NQ) * kRadix * 8 + 8, s));
-    LBVH_CUDA(b->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
+    LBVH_CUDA(b->lookback.ensure((size_t)b->max_tiles * kRadix * 8 + 8, s));
+    LBVH_CUDA(b->qlookback.ensure((size_t)b->max_qtiles * kRadix * 8 + 8, s));
+    LBVH_CUDA(b->hist.ensure((size_t)kMaxPasses * b->count * kRadix * 4 + 4, s));
     LBVH_CUDA(b->partials.ensure((size_t)b->nchunks * 32 + 32, s));
     LBVH_CUDA(b->bounds.ensure((size_t)b->count * 24 + 24, s));
     LBVH_CUDA(b->count_pos.ensure(unq * 8 + 8, s));
     LBVH_CUDA(b->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
     LBVH_CUDA(b->overflow.ensure(unq * 4 + 4, s));
     LBVH_CUDA(b->tile_sums.ensure((size_t)scan_tile_count(b->NQ) * 8 + 8, s));
-    if (!b->h_ctl) LBVH_CUDA(cudaMallocHost(&b->h_ctl, sizeof(Control)));
+    if (!b->h_ctl) LBVH_CUDA(pinned_controls().get(&b->h_ctl));
     LBVH_CUDA(cudaStreamSynchronize(s));
     b->ready = true;
     return LBVH_OK;
@@ -467,14 +593,15 @@ lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {
     LBVH_CUDA(cudaMemsetAsync(&c->build_flags, 0, sizeof(uint32_t), s));
     LBVH_CUDA(cudaMemsetAsync(&c->query_flags, 0, offsetof(Control, pad) - offsetof(Control, query_flags), s));
     if (b->N > 0) {
-        LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->passes * kRadix * 4, s));
+        LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->passes * b->count * kRadix * 4, s));
         launch_batch_bounds(g.prims, g.kind, bt, b->partials.as<float>(), b->bounds.as<float>(), c, s);
         launch_batch_encode(g.prims, g.kind, false, bt, g.bits, b->bounds.as<float>(), b->keys[0].as<uint64_t>(),
                             b->hist.as<uint32_t>(), s);
-        SortScratch scratch{b->hist.as<uint32_t>(), b->lookback.as<uint32_t>(), sort_tiles_max(b->N) * kRadix};
+        SortScratch scratch{b->hist.as<uint32_t>(), b->lookback.as<uint32_t>(), b->max_tiles * kRadix};
+        const SortSegments seg = b->segments(false, b->sort_variant);
         b->sorted_in_b = run_onesweep(b->keys[0].as<uint64_t>(), b->vals[0].as<uint32_t>(), true,
                                       b->keys[1].as<uint64_t>(), b->vals[1].as<uint32_t>(), b->N, b->passes,
-                                      scratch, c, s, nullptr, b->sort_variant);
+                                      scratch, c, s, nullptr, b->sort_variant, &seg);
         launch_batch_construct(b->sorted_codes(), b->perm(), g.prims, bt, g.kind, b->nodes.as<float4>(),
                                b->store.as<unsigned long long>(), &c->build_flags, s);
         LBVH_LAUNCHED();
@@ -487,14 +614,15 @@ lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {
     if (b->self_query) {
         qa.order = b->perm();
     } else {
-        LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->qpasses * kRadix * 4, s));
+        LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->qpasses * b->count * kRadix * 4, s));
         const int as_prims = g.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
         launch_batch_encode(g.queries, as_prims, true, bt, 30, b->bounds.as<float>(), b->qkeys[0].as<uint64_t>(),
                             b->hist.as<uint32_t>(), s);
-        SortScratch scratch{b->hist.as<uint32_t>(), b->qlookback.as<uint32_t>(), sort_tiles_max(b->NQ) * kRadix};
+        SortScratch scratch{b->hist.as<uint32_t>(), b->qlookback.as<uint32_t>(), b->max_qtiles * kRadix};
+        const SortSegments seg = b->segments(true, b->sort_variant);
         const bool in_b = run_onesweep(b->qkeys[0].as<uint64_t>(), b->qvals[0].as<uint32_t>(), true,
                                        b->qkeys[1].as<uint64_t>(), b->qvals[1].as<uint32_t>(), b->NQ,
-                                       b->qpasses, scratch, c, s, nullptr, b->sort_variant);
+                                       b->qpasses, scratch, c, s, nullptr, b->sort_variant, &seg);
         qa.order = b->qvals[in_b ? 1 : 0].as<uint32_t>();
     }
     const QueryScratch qs{b->count_pos.as<uint2>(), b->slots.as<uint32_t>(), b->overflow.as<uint32_t>()};
@@ -531,13 +659,14 @@ lbvh_status batch_autotune(lbvh_batch_t b, cudaStream_t s) {
     for (int v = 0; v < sort_variant_count(); ++v) {
         float ms_total = 0.0f;
         for (int rep = 0; rep < 2; ++rep) {
-            LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->passes * kRadix * 4, s));
+            LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->passes * b->count * kRadix * 4, s));
             launch_batch_encode(g.prims, g.kind, false, bt, g.bits, b->bounds.as<float>(),
                                 b->keys[0].as<uint64_t>(), b->hist.as<uint32_t>(), s);
-            SortScratch scratch{b->hist.as<uint32_t>(), b->lookback.as<uint32_t>(), sort_tiles_max(b->N) * kRadix};
+            SortScratch scratch{b->hist.as<uint32_t>(), b->lookback.as<uint32_t>(), b->max_tiles * kRadix};
+            const SortSegments seg = b->segments(false, v);
             LBVH_CUDA(cudaEventRecord(e0, s));
             run_onesweep(b->keys[0].as<uint64_t>(), b->vals[0].as<uint32_t>(), true, b->keys[1].as<uint64_t>(),
-                         b->vals[1].as<uint32_t>(), b->N, b->passes, scratch, c, s, nullptr, v);
+                         b->vals[1].as<uint32_t>(), b->N, b->passes, scratch, c, s, nullptr, v, &seg);
             LBVH_CUDA(cudaEventRecord(e1, s));
             LBVH_CUDA(cudaEventSynchronize(e1));
             float ms = 0.0f;
@@ -569,16 +698,20 @@ lbvh_status lbvh_tree_create(lbvh_tree_t *out) {
 
 void lbvh_tree_destroy(lbvh_tree_t t) {
     if (!t) return;
-    if (t->has_build) cudaStreamSynchronize(t->stream);
-    cudaStream_t s = t->stream;
+    // Wait for this tree's own work only (its last build and its last
+    // query), not for whole streams or the device; then the buffers go back
+    // to the stream-ordered pool and the pinned mirror to its free list.
+    if (t->has_build && t->built) cudaEventSynchronize(t->built);
+    else if (t->nodes.p) cudaDeviceSynchronize();  // a build that failed part-way may still run
+    if (t->queried) cudaEventSynchronize(t->used);
     for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
                       &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                       &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                       &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots})
-        b->release(s);
-    cudaStreamSynchronize(s);
-    if (t->h_ctl) cudaFreeHost(t->h_ctl);
+        b->release(cudaStreamPerThread);
+    pinned_controls().put(t->h_ctl);
     if (t->built) cudaEventDestroy(t->built);
+    if (t->used) cudaEventDestroy(t->used);
     t->prof.release();
     delete t;
 }
@@ -692,6 +825,7 @@ lbvh_status lbvh_tree_bytes(lbvh_tree_t t, uint64_t *bytes) {
 lbvh_status lbvh_tree_export(lbvh_tree_t t, uint32_t *h_perm, uint64_t *h_sorted_codes,
                              int32_t *h_left, int32_t *h_skip_internal, int32_t *h_skip_leaf,
                              float *h_internal_box, float *h_leaf_box, float *h_bounds) {
+    if (t && t->lean) return LBVH_ERR_INVALID;  // resident copy without perm and codes
     lbvh_status st = lbvh_tree_status(t);
     if (st != LBVH_OK) return st;
     const int64_t n = t->n, ni = n > 0 ? n - 1 : 0;
@@ -779,6 +913,12 @@ lbvh_status lbvh_query(lbvh_tree_t t, const float *d_queries, int64_t nq, int qk
 
 void lbvh_free(void *d_ptr) {
     if (d_ptr) cudaFree(d_ptr);
+}
+
+lbvh_status lbvh_release_cached_memory(void) {
+    std::lock_guard<std::mutex> lock(lbvh::g_pool_mu);
+    for (auto &kv : lbvh::g_pools) LBVH_CUDA(cudaMemPoolTrimTo(kv.second, 0));
+    return LBVH_OK;
 }
 
 lbvh_status lbvh_morton_codes(const float *d_prims, int64_t n, int kind, int morton_bits,
@@ -873,10 +1013,10 @@ void lbvh_batch_destroy(lbvh_batch_t b) {
                       &b->qchunks, &b->keys[0], &b->keys[1], &b->vals[0], &b->vals[1], &b->nodes, &b->store,
                       &b->lookback, &b->hist, &b->partials, &b->bounds, &b->ctl, &b->count_pos, &b->slots,
                       &b->overflow, &b->tile_sums, &b->qkeys[0], &b->qkeys[1], &b->qvals[0], &b->qvals[1],
-                      &b->qlookback})
+                      &b->qlookback, &b->tile_first, &b->qtile_first})
         d->release(s);
     if (s) cudaStreamSynchronize(s);
-    if (b->h_ctl) cudaFreeHost(b->h_ctl);
+    pinned_controls().put(b->h_ctl);
     if (b->ordered) cudaEventDestroy(b->ordered);
     if (s) cudaStreamDestroy(s);
     delete b;
@@ -888,10 +1028,11 @@ lbvh_status lbvh_batch_build_query(lbvh_batch_t b, const float *d_prims, const i
                                    float radius, int64_t *d_offsets, uint32_t *d_hits, uint64_t capacity,
                                    uint64_t *total, lbvh_stream_t stream) {
     using namespace lbvh;
-    if (!b || count < 1 || !h_prim_offsets || !h_query_offsets || !d_offsets || !total) return LBVH_ERR_INVALID;
+    if (!b || count < 1 || count > LBVH_MAX_BATCH || !h_prim_offsets || !h_query_offsets || !d_offsets || !total)
+        return LBVH_ERR_INVALID;
     if (kind != LBVH_PRIM_POINTS && kind != LBVH_PRIM_BOXES) return LBVH_ERR_INVALID;
     if (qkind != LBVH_Q_SPHERE && qkind != LBVH_Q_BOX) return LBVH_ERR_INVALID;
-    if (!valid_bits(morton_bits) || morton_bits + ceil_log2(count) > 64) return LBVH_ERR_INVALID;
+    if (!valid_bits(morton_bits)) return LBVH_ERR_INVALID;
     if (qkind == LBVH_Q_SPHERE && !d_radii && !(std::isfinite(radius) && radius >= 0.0f)) return LBVH_ERR_INVALID;
     if (h_prim_offsets[0] != 0 || h_query_offsets[0] != 0) return LBVH_ERR_INVALID;
     for (int64_t k = 0; k < count; ++k) {
@@ -899,7 +1040,7 @@ lbvh_status lbvh_batch_build_query(lbvh_batch_t b, const float *d_prims, const i
         const int64_t m = h_query_offsets[k + 1] - h_query_offsets[k];
         if (n < 0 || n > LBVH_MAX_PRIMS || m < 0) return LBVH_ERR_INVALID;
     }
-    if (h_prim_offsets[count] > ((int64_t)1 << 32) - 1 || h_query_offsets[count] > ((int64_t)1 << 32) - 1)
+    if (h_prim_offsets[count] > ((int64_t)1 << 31) - 1 || h_query_offsets[count] > ((int64_t)1 << 31) - 1)
         return LBVH_ERR_INVALID;
     if ((h_prim_offsets[count] > 0 && !d_prims) || (h_query_offsets[count] > 0 && !d_queries))
         return LBVH_ERR_INVALID;
@@ -1010,8 +1151,6 @@ lbvh_status lbvh_batch_export(lbvh_batch_t b, int64_t instance, uint32_t *h_perm
     }
     if (h_sorted_codes) {
         LBVH_CUDA(cudaMemcpy(h_sorted_codes, b->sorted_codes() + o, n * 8, cudaMemcpyDeviceToHost));
-        const uint64_t mask = b->sig.bits >= 64 ? ~0ull : ((1ull << b->sig.bits) - 1ull);
-        for (int64_t k = 0; k < n; ++k) h_sorted_codes[k] &= mask;
     }
     const int per = b->sig.kind == LBVH_PRIM_POINTS ? 1 : 2;
     std::vector<float4> rec((size_t)(2 * ni + per * n));
@@ -1057,24 +1196,19 @@ void batch_set_graphs(lbvh_batch_t b, bool on) {
     b->graphs = on;
 }
 
-namespace {
-__global__ void rebase_u32_kernel(uint32_t *dst, const uint32_t *src, int64_t n, uint32_t sub) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[i] - sub;
-}
-__global__ void mask_u64_kernel(uint64_t *dst, const uint64_t *src, int64_t n, uint64_t mask) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = src[i] & mask;
-}
-}  // namespace
-
 lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cudaStream_t s) {
+    // A lean copy: what queries read (nodes, scene bounds, control block, the
+    // query-order histogram) and nothing that only exports or rebuilds need.
     if (!b || !b->ready || !t || instance < 0 || instance >= b->count) return LBVH_ERR_INVALID;
     const int64_t o = b->sig.prim_off[instance];
     const int64_t n = b->sig.prim_off[instance + 1] - o;
     const int kind = b->sig.kind;
-    lbvh_status st = reserve_tree(t, n, kind, s);
-    if (st != LBVH_OK) return st;
+    const int64_t units = n > 0 ? 2 * (n - 1) + (kind == LBVH_PRIM_POINTS ? n : 2 * n) : 0;
+    LBVH_CUDA(t->ctl.ensure(sizeof(Control), s, true));
+    LBVH_CUDA(t->nodes.ensure((size_t)units * 16 + 16, s));
+    LBVH_CUDA(t->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
+    LBVH_CUDA(t->bounds.ensure(6 * 4, s));
+    t->lean = true;
     t->n = n;
     t->kind = kind;
     t->bits = b->sig.bits;
@@ -1082,18 +1216,16 @@ lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cud
     t->prims_ptr = nullptr;
     LBVH_CUDA(cudaMemsetAsync(&t->dctl()->build_flags, 0, sizeof(uint32_t), s));
     LBVH_CUDA(cudaMemcpyAsync(t->bounds.p, b->bounds.as<float>() + 6 * instance, 24, cudaMemcpyDeviceToDevice, s));
-    if (n > 0) {
-        const int64_t units = 2 * (n - 1) + (kind == LBVH_PRIM_POINTS ? n : 2 * n);
+    if (units > 0)
         LBVH_CUDA(cudaMemcpyAsync(t->nodes.p, b->nodes.as<float4>() + b->h_node_start[instance], units * 16,
                                   cudaMemcpyDeviceToDevice, s));
-        const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 4096);
-        rebase_u32_kernel<<<blocks, 256, 0, s>>>(t->vals[0].as<uint32_t>(), b->perm() + o, n, (uint32_t)o);
-        const uint64_t mask = b->sig.bits >= 64 ? ~0ull : ((1ull << b->sig.bits) - 1ull);
-        mask_u64_kernel<<<blocks, 256, 0, s>>>(t->keys[0].as<uint64_t>(), b->sorted_codes() + o, n, mask);
-        count_launches(2);
-        LBVH_LAUNCHED();
-    }
     return finish_build(t, s);
+}
+
+void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s) {
+    for (DevBuf *b : {&t->counts, &t->tile_sums, &t->overflow, &t->slots, &t->qkeys[0], &t->qkeys[1],
+                      &t->qvals[0], &t->qvals[1], &t->qlookback})
+        b->release(s);
 }
 
 }  // namespace lbvh

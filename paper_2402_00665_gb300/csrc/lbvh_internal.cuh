@@ -32,7 +32,8 @@ struct Control {
     uint32_t query_flags;          // kFlag* latched by the last query
     uint32_t overflow_filled;      // entries of the overflow list
     unsigned long long total;      // total hits of the last query
-    uint32_t pad[8];
+    uint32_t overflow_big;         // overflow lists too long for one warp's sort
+    uint32_t pad[7];
 };
 constexpr int kQueryBufferHits = 32;  // hits kept per query by the walk
 
@@ -99,6 +100,19 @@ struct SortScratch {
 void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_t *hist,
                             cudaStream_t s);
 
+// Independent segments sorted in one pass sequence: segment b is keys
+// [off[b], off[b+1]) and is sorted on its own (tiles never straddle two
+// segments, digit counts and look-back chains are per segment), so the keys
+// need no segment bits. Segment b's tiles are [tile_first[b], tile_first[b+1])
+// for the tile shape the sort runs with (see sort_variant_tile_keys).
+// hist then holds, per pass, `count` rows of kRadix counts.
+struct SortSegments {
+    const int64_t *off;         // count + 1, device
+    const int64_t *tile_first;  // count + 1, device
+    int count;
+    int64_t tiles;              // tile_first[count]
+};
+
 // Sorts (keys, vals) by the low `passes * 8` bits. keys_a/vals_a hold the
 // input (with `iota` the payload is the index and vals_a's contents are
 // ignored; it is still used as a ping-pong buffer); keys_b/vals_b are the
@@ -108,12 +122,17 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
 // is cleared here with a memset.
 // pass_events (nullable): an event pair per pass, recorded around its kernel.
 // variant_idx: tile shape (< sort_variant_count()), or -1 for the default.
-// The look-back regions must hold sort_tiles_max(n) * kRadix words each.
+// The look-back regions must hold sort_tiles_max(n) * kRadix words each
+// (seg->tiles * kRadix with segments).
+// seg (nullable): sort each segment on its own; its tile table must be the
+// one for variant_idx's tile shape.
 bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
-                  int variant_idx = -1);
+                  int variant_idx = -1, const SortSegments *seg = nullptr);
 int sort_variant_count();
+// Keys per tile of variant idx (-1: the default variant).
+int64_t sort_variant_tile_keys(int idx);
 int64_t sort_tile_keys_min();
 inline int64_t sort_tiles_max(int64_t n) { return (n + sort_tile_keys_min() - 1) / sort_tile_keys_min(); }
 
@@ -166,8 +185,10 @@ void launch_exclusive_scan(const uint2 *count_pos, int64_t nq, int64_t *offsets,
 void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
                        uint32_t *hits, Control *ctl, cudaStream_t s);
 // Second walk + sort for the `count` queries of the overflow list.
+// ctl: the query's control block (overflow counts on the device).
 void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScratch &qs,
-                           uint32_t count, const int64_t *offsets, uint32_t *hits, cudaStream_t s);
+                           uint32_t count, const int64_t *offsets, uint32_t *hits, Control *ctl,
+                           cudaStream_t s);
 
 // ---------------------------------------------------------------- batches
 // Many independent trees in one pass. Instance b owns primitives
@@ -207,9 +228,9 @@ __device__ __forceinline__ int instance_of(const int64_t *__restrict__ off, int 
 // Per-instance bounds: partials (nchunks * 8 floats), then bounds (count * 6).
 void launch_batch_bounds(const float *prims, int kind, const BatchTables &bt, float *partials,
                          float *bounds, Control *ctl, cudaStream_t s);
-// Composite keys (instance << bits | Morton code) of primitives (or of query
-// centres, with `queries` = true: qchunks and qkind decide the layout), plus
-// pass 0's digit histogram.
+// Morton codes of primitives (or of query centres, with `queries` = true:
+// qchunks and qkind decide the layout), each in its own instance's grid, plus
+// pass 0's digit histogram of every instance (hist row inst * kRadix).
 void launch_batch_encode(const float *data, int kind, bool queries, const BatchTables &bt, int bits,
                          const float *bounds, uint64_t *keys, uint32_t *hist, cudaStream_t s);
 void launch_batch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
@@ -227,12 +248,26 @@ void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt,
 void launch_query_copy_checked(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,
                                uint32_t *hits, unsigned long long capacity, Control *ctl, cudaStream_t s);
 
-// Used by the request server (server.cu): run a batch without graph capture,
-// and copy one instance of a finished batch into a tree of its own.
+// Used by the request server (server.cu): run a batch without graph capture;
+// copy one instance of a finished batch into a tree of its own (nodes and
+// bounds only: it can be queried, not exported); free a tree's query scratch
+// (stream-ordered on s, after the queries that used it).
 void batch_set_graphs(lbvh_batch_t b, bool on);
 lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cudaStream_t s);
+void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s);
 
 int device_sm_count();
+
+// Device memory of the library: one stream-ordered pool per device, owned by
+// the library, that keeps freed blocks for reuse (its release threshold is
+// never reached), so buffers that are freed and allocated again do not map
+// and unmap memory at every synchronisation. lbvh_release_cached_memory
+// hands the unused part back.
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+// Grows the current device's pool by `bytes` of reusable memory now (one
+// allocation, freed again at once and kept by the pool).
+cudaError_t pool_reserve(size_t bytes, cudaStream_t s);
 
 // Adds k to the process-wide count of kernels launched by this library.
 void count_launches(int k);

@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kThreads)
 template <int kKind>
 __global__ void __launch_bounds__(kThreads)
     batch_encode_kernel(const float *__restrict__ data, const BatchChunk *__restrict__ chunks, int b,
-                        int bits, const float *__restrict__ bounds, uint64_t *__restrict__ keys,
+                        const float *__restrict__ bounds, uint64_t *__restrict__ keys,
                         uint32_t *__restrict__ hist) {
     __shared__ uint32_t s_hist[kRadix];
     s_hist[threadIdx.x] = 0;  // kThreads == kRadix
@@ -355,18 +355,17 @@ __global__ void __launch_bounds__(kThreads)
     g.topi = (1u << b) - 1u;
     g.cells = (float)(1u << b);
     g.top = (float)g.topi;
-    const uint64_t inst = (uint64_t)c.inst << bits;
     __syncthreads();
     for (int64_t i = c.begin + threadIdx.x; i < c.end; i += kThreads) {
         float x, y, z;
         centroid_at<kKind>(data, i, x, y, z);
-        const uint64_t key = inst | morton(x, y, z, g);
+        const uint64_t key = morton(x, y, z, g);
         keys[i] = key;
         atomicAdd(&s_hist[(uint32_t)key & (kRadix - 1)], 1u);
     }
     __syncthreads();
     const uint32_t v = s_hist[threadIdx.x];
-    if (v) atomicAdd(&hist[threadIdx.x], v);
+    if (v) atomicAdd(&hist[(int64_t)c.inst * kRadix + threadIdx.x], v);
 }
 
 }  // namespace
@@ -390,10 +389,10 @@ void launch_batch_encode(const float *data, int kind, bool queries, const BatchT
     if (nchunks <= 0) return;
     const int b = bits / 3;
     if (kind == LBVH_PRIM_POINTS)
-        batch_encode_kernel<LBVH_PRIM_POINTS><<<(unsigned)nchunks, kThreads, 0, s>>>(data, chunks, b, bits, bounds,
+        batch_encode_kernel<LBVH_PRIM_POINTS><<<(unsigned)nchunks, kThreads, 0, s>>>(data, chunks, b, bounds,
                                                                                      keys, hist);
     else
-        batch_encode_kernel<LBVH_PRIM_BOXES><<<(unsigned)nchunks, kThreads, 0, s>>>(data, chunks, b, bits, bounds,
+        batch_encode_kernel<LBVH_PRIM_BOXES><<<(unsigned)nchunks, kThreads, 0, s>>>(data, chunks, b, bounds,
                                                                                     keys, hist);
     count_launches(1);
 }

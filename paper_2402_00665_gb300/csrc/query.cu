@@ -34,7 +34,9 @@
 //             adjacent in the CSR, through shared memory, one coalesced list
 //             per step.
 //   overflow  queries with more hits walk again and write straight into the
-//             CSR; a fix-up kernel sorts those lists, one CTA per list.
+//             CSR; a fix-up kernel sorts those lists, one warp per list (one
+//             CTA per list above 1024 hits).
+#include <algorithm>
 #include <cstdlib>
 #include <type_traits>
 
@@ -414,21 +416,87 @@ __device__ void bitonic_sort(uint32_t *a, int64_t m) {
     }
 }
 
+// One warp per overflow list (the common case: a few dozen to a few hundred
+// hits): the warp loads the list into its own shared-memory region, runs the
+// network with __syncwarp between steps and writes it back. Lists longer than
+// kWarpSortMax go to a second list (kept in the then unused slot buffer) for
+// sort_big_lists_kernel. Both kernels stride over counts held on the device
+// and write nothing when the hits did not fit the caller's buffer.
+constexpr int kWarpSortMax = 1024;
+constexpr int kSortWarps = kThreads / 32;
+
+__device__ void warp_bitonic_sort(uint32_t *a, int m) {
+    const int lane = threadIdx.x & 31;
+    int lg = 0;
+    while ((1 << lg) < m) ++lg;
+    const int pairs = (1 << lg) >> 1;
+    for (int lk = 1; lk <= lg; ++lk) {
+        // first step of the merge of blocks of 2^lk: i pairs with its mirror
+        const int lh = lk - 1;
+        for (int i = lane; i < pairs; i += 32) {
+            const int blk = i >> lh, off = i & ((1 << lh) - 1);
+            const int lo = (blk << lk) + off, hi = (blk << lk) + (1 << lk) - 1 - off;
+            if (hi < m) order_pair(a, lo, hi);
+        }
+        __syncwarp();
+        for (int lj = lk - 2; lj >= 0; --lj) {
+            for (int i = lane; i < pairs; i += 32) {
+                const int blk = i >> lj, off = i & ((1 << lj) - 1);
+                const int lo = (blk << (lj + 1)) + off, hi = lo + (1 << lj);
+                if (hi < m) order_pair(a, lo, hi);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+    warp_sort_lists_kernel(const int64_t *__restrict__ offsets, uint32_t *hits,
+                           const uint32_t *__restrict__ list, uint32_t *__restrict__ big_list, Control *ctl,
+                           unsigned long long capacity) {
+    __shared__ uint32_t s[kSortWarps][kWarpSortMax];
+    if (ctl->total > capacity) return;
+    const uint32_t count = ctl->overflow_filled;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *a = s[warp];
+    for (int64_t j = (int64_t)blockIdx.x * kSortWarps + warp; j < count; j += (int64_t)gridDim.x * kSortWarps) {
+        const uint32_t q = list[j];
+        const int64_t base = offsets[q];
+        const int64_t m = offsets[q + 1] - base;
+        if (m > kWarpSortMax) {
+            if (lane == 0) big_list[atomicAdd(&ctl->overflow_big, 1u)] = q;
+            continue;
+        }
+        uint32_t *seg = hits + base;
+        for (int i = lane; i < m; i += 32) a[i] = seg[i];
+        __syncwarp();
+        warp_bitonic_sort(a, (int)m);
+        for (int i = lane; i < m; i += 32) seg[i] = a[i];
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(kFixThreads)
-    sort_lists_kernel(const int64_t *__restrict__ offsets, uint32_t *hits,
-                      const uint32_t *__restrict__ list) {
+    sort_big_lists_kernel(const int64_t *__restrict__ offsets, uint32_t *hits,
+                          const uint32_t *__restrict__ big_list, const Control *ctl,
+                          unsigned long long capacity) {
     __shared__ uint32_t s[kFixSmem];
-    const uint32_t q = list[blockIdx.x];
-    const int64_t base = offsets[q];
-    const int64_t m = offsets[q + 1] - base;
-    uint32_t *seg = hits + base;
-    if (m <= kFixSmem) {
-        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s[i] = seg[i];
+    if (ctl->total > capacity) return;
+    const uint32_t count = ctl->overflow_big;
+    for (uint32_t j = blockIdx.x; j < count; j += gridDim.x) {
+        const uint32_t q = big_list[j];
+        const int64_t base = offsets[q];
+        const int64_t m = offsets[q + 1] - base;
+        uint32_t *seg = hits + base;
+        if (m <= kFixSmem) {
+            for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s[i] = seg[i];
+            __syncthreads();
+            bitonic_sort(s, m);
+            for (int64_t i = threadIdx.x; i < m; i += blockDim.x) seg[i] = s[i];
+        } else {
+            bitonic_sort(seg, m);  // in global memory; one CTA owns the list
+        }
         __syncthreads();
-        bitonic_sort(s, m);
-        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) seg[i] = s[i];
-    } else {
-        bitonic_sort(seg, m);  // in global memory; one CTA owns the list
     }
 }
 
@@ -482,30 +550,6 @@ __global__ void __launch_bounds__(kThreads)
             if (c < total) hits[base + c] = id;
             ++c;
         });
-    }
-}
-
-__global__ void __launch_bounds__(kFixThreads)
-    batch_sort_lists_kernel(const int64_t *__restrict__ offsets, uint32_t *hits,
-                            const uint32_t *__restrict__ list, const Control *ctl,
-                            unsigned long long capacity) {
-    __shared__ uint32_t s[kFixSmem];
-    if (ctl->total > capacity) return;
-    const uint32_t count = ctl->overflow_filled;
-    for (uint32_t j = blockIdx.x; j < count; j += gridDim.x) {
-        const uint32_t q = list[j];
-        const int64_t base = offsets[q];
-        const int64_t m = offsets[q + 1] - base;
-        uint32_t *seg = hits + base;
-        if (m <= kFixSmem) {
-            for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s[i] = seg[i];
-            __syncthreads();
-            bitonic_sort(s, m);
-            for (int64_t i = threadIdx.x; i < m; i += blockDim.x) seg[i] = s[i];
-        } else {
-            bitonic_sort(seg, m);
-        }
-        __syncthreads();
     }
 }
 
@@ -576,16 +620,30 @@ void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t
     launch_query_copy_checked(q, qs, offsets, hits, ~0ull, ctl, s);
 }
 
+// Sorts the overflow lists: warps for the lists, CTAs for the long ones.
+// `bound`: an upper bound of the overflow count (sizes the warp kernel's grid).
+static void launch_sort_lists(const QueryScratch &qs, uint64_t bound, const int64_t *offsets, uint32_t *hits,
+                              unsigned long long capacity, Control *ctl, cudaStream_t s) {
+    const uint64_t want = (bound + kSortWarps - 1) / kSortWarps;
+    const uint64_t cap = (uint64_t)device_sm_count() * 8;
+    const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+    warp_sort_lists_kernel<<<blocks, kThreads, 0, s>>>(offsets, hits, qs.overflow_list, qs.slots, ctl, capacity);
+    sort_big_lists_kernel<<<(unsigned)device_sm_count(), kFixThreads, 0, s>>>(offsets, hits, qs.slots, ctl,
+                                                                              capacity);
+    count_launches(2);
+}
+
 void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScratch &qs,
-                           uint32_t count, const int64_t *offsets, uint32_t *hits, cudaStream_t s) {
+                           uint32_t count, const int64_t *offsets, uint32_t *hits, Control *ctl,
+                           cudaStream_t s) {
     if (count == 0) return;
     const unsigned blocks = (unsigned)((count + kThreads - 1) / kThreads);
     dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
         overflow_walk_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
             t, q, qs.overflow_list, count, offsets, hits);
     });
-    sort_lists_kernel<<<count, kFixThreads, 0, s>>>(offsets, hits, qs.overflow_list);
-    count_launches(2);
+    launch_sort_lists(qs, count, offsets, hits, ~0ull, ctl, s);
+    count_launches(1);
 }
 
 void launch_batch_collect(const float4 *nodes, int kind, const BatchTables &bt, const QueryArgs &q,
@@ -603,14 +661,13 @@ void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt,
                            const QueryScratch &qs, Control *ctl, const int64_t *offsets, uint32_t *hits,
                            unsigned long long capacity, cudaStream_t s) {
     if (q.nq <= 0) return;
-    const unsigned blocks = (unsigned)device_sm_count() * 2;
+    const unsigned blocks = (unsigned)device_sm_count() * 8;
     dispatch_kinds(q.qkind, kind, [&](auto qk, auto pk) {
         batch_overflow_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
             nodes, bt, q, qs.overflow_list, ctl, offsets, hits, capacity);
     });
-    batch_sort_lists_kernel<<<(unsigned)device_sm_count() * 2, kFixThreads, 0, s>>>(
-        offsets, hits, qs.overflow_list, ctl, capacity);
-    count_launches(2);
+    count_launches(1);
+    launch_sort_lists(qs, (uint64_t)q.nq, offsets, hits, capacity, ctl, s);
 }
 
 int64_t scan_tile_count(int64_t nq) { return (nq + kScanTile - 1) / kScanTile; }

@@ -73,16 +73,16 @@ struct Buf {
     size_t bytes = 0;
     lbvh_status ensure(size_t want, cudaStream_t s) {
         if (want <= bytes) return LBVH_OK;
-        if (p) cudaFreeAsync(p, s);
+        if (p) lbvh::pool_free(p, s);
         p = nullptr;
         bytes = 0;
         want = std::max<size_t>(want, 256);
-        if (cudaMallocAsync(&p, want, s) != cudaSuccess) return LBVH_ERR_OOM;
+        if (lbvh::pool_alloc(&p, want, s) != cudaSuccess) return LBVH_ERR_OOM;
         bytes = want;
         return LBVH_OK;
     }
     void release(cudaStream_t s) {
-        if (p) cudaFreeAsync(p, s);
+        if (p) lbvh::pool_free(p, s);
         p = nullptr;
         bytes = 0;
     }
@@ -138,9 +138,12 @@ uint64_t estimate_bytes(const lbvh_request &r) {
     return build + query;
 }
 
+// Device bytes of a resident tree: its nodes (2(n-1) internal records of
+// 32 bytes, leaves of 16 or 32 bytes) plus the control block, bounds and the
+// query-order histogram.
 uint64_t resident_bytes_of(int64_t n, int kind) {
     const uint64_t un = (uint64_t)std::max<int64_t>(n, 1);
-    return un * ((kind == LBVH_PRIM_POINTS ? 48 : 64) + 12 + 24 + 16) + 4096;
+    return (2 * (un - 1) + (kind == LBVH_PRIM_POINTS ? un : 2 * un)) * 16 + 16 + 8192 + 512;
 }
 
 bool same_batch_kind(const lbvh_request &a, const lbvh_request &b) {
@@ -161,6 +164,7 @@ struct lbvh_server_s {
     std::list<uint64_t> lru;
     uint64_t resident_total = 0, inflight = 0, next_ticket = 1;
     uint64_t evictions = 0, batches = 0, requests_done = 0, jobs_finished = 0;
+    double phase_s[LBVH_SERVER_PHASES] = {};  // see lbvh_server_phase_seconds
     bool stop = false;
     Clock::time_point t0 = Clock::now();
     std::vector<std::unique_ptr<Slot>> slots;
@@ -313,11 +317,13 @@ void lbvh_server_s::run_query_job(Slot *slot, Job &job) {
     const lbvh_status st = lbvh_query_into(tree, r.req.d_queries, r.req.nq, r.req.qkind, r.req.d_radii,
                                            r.req.radius, r.req.d_offsets, r.req.d_hits, r.req.capacity, &total,
                                            slot->stream);
+    lbvh::tree_release_query_scratch(tree, slot->stream);  // resident bytes stay those of the tree
     cudaStreamSynchronize(slot->stream);
     std::lock_guard<std::mutex> lk(mu);
     auto it = resident.find(r.req.key);
     if (it != resident.end()) it->second.in_use--;
     complete(r, st, total, start, 1);
+    phase_s[3] += seconds_since(start, Clock::now());
 }
 
 void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
@@ -369,6 +375,7 @@ void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
         }
     }
     cudaMemcpyAsync(slot->qbase.p, qo.data(), (size_t)(count + 1) * 8, cudaMemcpyHostToDevice, s);
+    const Clock::time_point staged = Clock::now();
     const float *queries = self_query ? slot->prims.as<float>() : slot->queries.as<float>();
     const float *radii = k0.qkind == LBVH_Q_SPHERE ? slot->radii.as<float>() : nullptr;
     uint64_t total = 0;
@@ -382,6 +389,7 @@ void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
                                     slot->offsets.as<int64_t>(), slot->hits.as<uint32_t>(), total + 1, &total, s);
     }
     if (st != LBVH_OK) return fail_all(st);
+    const Clock::time_point batched = Clock::now();
     request_totals_kernel<<<(count + 255) / 256, 256, 0, s>>>(slot->offsets.as<int64_t>(), slot->qbase.as<int64_t>(),
                                                               count, slot->totals.as<unsigned long long>());
     slot->h_totals.resize(count);
@@ -409,6 +417,9 @@ void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
     }
     cudaStreamSynchronize(s);
     std::lock_guard<std::mutex> lk(mu);
+    phase_s[0] += seconds_since(start, staged);
+    phase_s[1] += seconds_since(staged, batched);
+    phase_s[2] += seconds_since(batched, Clock::now());
     for (auto &kt : keep) {
         const uint64_t key = kt.first;
         auto old = resident.find(key);
@@ -511,6 +522,13 @@ lbvh_status lbvh_server_stats(lbvh_server_t srv, uint64_t *resident_bytes, uint6
     if (resident_trees) *resident_trees = srv->resident.size();
     if (evictions) *evictions = srv->evictions;
     if (batches) *batches = srv->batches;
+    return LBVH_OK;
+}
+
+lbvh_status lbvh_server_phase_seconds(lbvh_server_t srv, double *seconds) {
+    if (!srv || !seconds) return LBVH_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    for (int k = 0; k < LBVH_SERVER_PHASES; ++k) seconds[k] = srv->phase_s[k];
     return LBVH_OK;
 }
 

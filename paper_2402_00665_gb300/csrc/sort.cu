@@ -6,12 +6,16 @@
 // a pass are known when it starts (pass 0's from the Morton encoder or from
 // digit_histogram_kernel; pass p+1's counted by pass p as it reads the keys),
 // so each pass reads and writes the data once.
-// Per pass, each CTA takes a tile of 4096 keys by ticket (so every tile it may
+// Per pass, each CTA takes a tile (256 threads x 8-16 keys) by ticket (so every tile it may
 // wait on is already running), ranks the keys by digit inside the tile with
 // warp match/ballot counting, publishes its per-digit counts, resolves the
 // exclusive prefix of its digits over all earlier tiles by decoupled look-back
 // with a bounded spin, stages the tile in shared memory in digit order and
 // writes it out so that consecutive threads write consecutive addresses.
+//
+// The same kernel also sorts many independent segments at once (batches of
+// trees): tiles then never straddle two segments, and each segment has its own
+// digit counts and look-back chain, so keys carry no segment bits.
 //
 // Look-back words: bits 31:30 = state (0 none, 1 aggregate, 2 inclusive
 // prefix), bits 29:0 = count. Two regions alternate between passes; every
@@ -71,6 +75,7 @@ struct SortSmem {
     uint32_t tile_start[kRadix];         // first staged slot of each digit
     uint32_t scan[kWarps];
     uint32_t tile;
+    int32_t seg;                         // segment of the tile (segmented sorts)
     uint32_t next_hist[kRadix];          // digit counts of the next pass
     uint64_t keys[kTile];
     uint32_t vals[kTile];
@@ -91,13 +96,22 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
     return peers;
 }
 
-template <bool kIota, int kItems, int kMinBlocks, bool kBallot>
+struct SegArgs {
+    const int64_t *off, *tile_first;
+    int count;
+};
+
+// kSeg: segments are sorted independently. A tile then lies inside one
+// segment; its keys start at off[seg] + (tile - tile_first[seg]) * kTile, its
+// digit counts come from and go to the segment's rows of the histograms, and
+// its look-back chain ends at the segment's first tile.
+template <bool kIota, int kItems, int kMinBlocks, bool kBallot, bool kSeg>
 __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
     onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
                     int shift, const uint32_t *__restrict__ pass_hist, uint32_t *lookback,
                     uint32_t *lookback_next, uint32_t *ticket, int64_t tiles,
-                    uint32_t *flags, uint32_t *next_hist) {
+                    uint32_t *flags, uint32_t *next_hist, SegArgs seg) {
     using Smem = SortSmem<kItems>;
     constexpr int kTile = Smem::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -108,13 +122,23 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
         const uint32_t t = atomicAdd(ticket, 1u);
         if (t == tiles - 1) *ticket = 0;  // last ticket handed out: reset for the next pass
         sm.tile = t;
+        if (kSeg) sm.seg = instance_of(seg.tile_first, seg.count, t);
     }
     for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) (&sm.warp_hist[0][0])[k] = 0;
     sm.next_hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t tile = sm.tile;
-    const int64_t tile_base = tile * kTile;
-    const int64_t valid = min((int64_t)kTile, n - tile_base);
+    int64_t first_tile = 0, seg_begin = 0, seg_end = n, tile_base = tile * kTile;
+    if (kSeg) {
+        const int sg = sm.seg;
+        first_tile = seg.tile_first[sg];
+        seg_begin = seg.off[sg];
+        seg_end = seg.off[sg + 1];
+        tile_base = seg_begin + (tile - first_tile) * kTile;
+        pass_hist += (int64_t)sg * kRadix;
+        if (next_hist) next_hist += (int64_t)sg * kRadix;
+    }
+    const int64_t valid = min((int64_t)kTile, seg_end - tile_base);
 
     // ---- load: warp w owns keys [w*32*kItems, (w+1)*32*kItems) of the tile,
     // round j lane l holds key w*32*kItems + 32*j + l
@@ -169,15 +193,15 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
         count += c;
     }
     uint32_t *my_word = lookback + tile * kRadix + d;
-    st_relaxed(my_word, (tile == 0 ? kStatePrefix : kStateAgg) | count);
+    st_relaxed(my_word, (tile == first_tile ? kStatePrefix : kStateAgg) | count);
 
-    const uint32_t global_base = block_exclusive_scan(pass_hist[d], sm.scan);
+    const uint32_t global_base = (uint32_t)seg_begin + block_exclusive_scan(pass_hist[d], sm.scan);
     const uint32_t start = block_exclusive_scan(count, sm.scan);
     sm.tile_start[d] = start;
 
     // ---- decoupled look-back over earlier tiles for digit d
     uint32_t exclusive = 0;
-    if (tile > 0) {
+    if (tile > first_tile) {
         int64_t t = tile - 1;
         while (true) {
             const uint32_t *w = lookback + t * kRadix + d;
@@ -192,7 +216,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
                 v = ld_relaxed(w);
             }
             exclusive += v & kCountMask;
-            if ((v & kStateMask) == kStatePrefix || t == 0) break;
+            if ((v & kStateMask) == kStatePrefix || t == first_tile) break;
             --t;
         }
         st_relaxed(my_word, kStatePrefix | (exclusive + count));
@@ -224,7 +248,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
             const uint64_t k = sm.keys[s];
             const uint32_t dj = (uint32_t)(k >> shift) & (kRadix - 1);
             const int64_t pos = (int64_t)sm.out_base[dj] + s;
-            if (pos < 0 || pos >= n) {  // only after a timed-out look-back
+            if (pos < seg_begin || pos >= seg_end) {  // only after a timed-out look-back
                 atomicOr(flags, kFlagCorrupt);
                 continue;
             }
@@ -236,19 +260,26 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
 
 using PassKernel = void (*)(const uint64_t *, const uint32_t *, uint64_t *, uint32_t *, int64_t, int,
                             const uint32_t *, uint32_t *, uint32_t *, uint32_t *, int64_t, uint32_t *,
-                            uint32_t *);
+                            uint32_t *, SegArgs);
 
 struct Variant {
     int items, min_blocks;
     bool ballot;
-    PassKernel first, rest;  // payload = index / payload read
+    PassKernel first, rest;          // payload = index / payload read
+    PassKernel seg_first, seg_rest;  // the same, segmented
     size_t smem;
 };
 
 template <int kItems, int kMinBlocks, bool kBallot>
 Variant make_variant() {
-    return Variant{kItems, kMinBlocks, kBallot, onesweep_kernel<true, kItems, kMinBlocks, kBallot>,
-                   onesweep_kernel<false, kItems, kMinBlocks, kBallot>, sizeof(SortSmem<kItems>)};
+    return Variant{kItems,
+                   kMinBlocks,
+                   kBallot,
+                   onesweep_kernel<true, kItems, kMinBlocks, kBallot, false>,
+                   onesweep_kernel<false, kItems, kMinBlocks, kBallot, false>,
+                   onesweep_kernel<true, kItems, kMinBlocks, kBallot, true>,
+                   onesweep_kernel<false, kItems, kMinBlocks, kBallot, true>,
+                   sizeof(SortSmem<kItems>)};
 }
 
 // Tile shapes the library is compiled with. The first entry is the default;
@@ -263,7 +294,7 @@ const Variant *variant_table(int *count) {
     static bool configured = false;
     if (!configured) {
         for (const Variant &v : table) {
-            for (PassKernel k : {v.first, v.rest}) {
+            for (PassKernel k : {v.first, v.rest, v.seg_first, v.seg_rest}) {
                 cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
                 cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             }
@@ -319,6 +350,8 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
 
 int64_t sort_tile_keys() { return (int64_t)kSortThreads * variant().items; }
 
+int64_t sort_variant_tile_keys(int idx) { return (int64_t)kSortThreads * variant(idx).items; }
+
 int sort_variant_count() {
     int count = 0;
     variant_table(&count);
@@ -335,23 +368,28 @@ int64_t sort_tile_keys_min() {
 
 bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
-                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx) {
+                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx,
+                  const SortSegments *seg) {
     if (n <= 0 || passes <= 0) return false;
     const Variant &v = variant(variant_idx);
-    const int64_t tiles = (n + (int64_t)kSortThreads * v.items - 1) / ((int64_t)kSortThreads * v.items);
+    const int64_t tiles = seg ? seg->tiles
+                              : (n + (int64_t)kSortThreads * v.items - 1) / ((int64_t)kSortThreads * v.items);
+    if (tiles <= 0) return false;
+    const SegArgs sa{seg ? seg->off : nullptr, seg ? seg->tile_first : nullptr, seg ? seg->count : 0};
+    const int64_t hist_stride = (int64_t)kRadix * (seg ? seg->count : 1);
     cudaMemsetAsync(scratch.lookback, 0, (size_t)tiles * kRadix * sizeof(uint32_t), s);
     uint64_t *kin = keys_a, *kout = keys_b;
     uint32_t *vin = vals_a, *vout = vals_b;
     for (int p = 0; p < passes; ++p) {
         uint32_t *cur = scratch.lookback + (p & 1) * scratch.lookback_words;
         uint32_t *nxt = scratch.lookback + ((p + 1) & 1) * scratch.lookback_words;
-        const uint32_t *hist = scratch.hist + p * kRadix;
+        const uint32_t *hist = scratch.hist + p * hist_stride;
         if (pass_events) cudaEventRecord(pass_events[p][0], s);
-        PassKernel k = (p == 0 && iota) ? v.first : v.rest;
-        uint32_t *next_hist = p + 1 < passes ? scratch.hist + (p + 1) * kRadix : nullptr;
+        PassKernel k = seg ? ((p == 0 && iota) ? v.seg_first : v.seg_rest) : ((p == 0 && iota) ? v.first : v.rest);
+        uint32_t *next_hist = p + 1 < passes ? scratch.hist + (p + 1) * hist_stride : nullptr;
         k<<<(unsigned)tiles, kSortThreads, v.smem, s>>>(kin, vin, kout, vout, n, kRadixBits * p, hist, cur,
                                                          nxt, &ctl->sort_ticket[p], tiles, &ctl->build_flags,
-                                                         next_hist);
+                                                         next_hist, sa);
         if (pass_events) cudaEventRecord(pass_events[p][1], s);
         count_launches(1);
         uint64_t *tk = kin;

@@ -22,6 +22,8 @@ from . import _build
 POINTS, BOXES = 0, 1
 SPHERE, BOX = 0, 1
 MAX_PRIMS = (1 << 30) - 1
+MAX_BATCH = 1 << 20
+SERVER_PHASES = 4
 STAGE_COUNT = 16
 
 STATUS = {0: "LBVH_OK", 1: "LBVH_ERR_INVALID", 2: "LBVH_ERR_NONFINITE", 3: "LBVH_ERR_OOM",
@@ -54,6 +56,8 @@ SIGNATURES = {
     "lbvh_server_submit": (_I32, [_P, _P, _P]),
     "lbvh_server_wait": (_I32, [_P, _U64, _P]),
     "lbvh_server_stats": (_I32, [_P, _P, _P, _P, _P]),
+    "lbvh_server_phase_seconds": (_I32, [_P, _P]),
+    "lbvh_release_cached_memory": (_I32, []),
     "lbvh_server_destroy": (None, [_P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
@@ -411,6 +415,12 @@ class Server:
         _check(self._lib.lbvh_server_stats(self._h, *[ctypes.byref(x) for x in v]), "lbvh_server_stats")
         return dict(zip(("resident_bytes", "resident_trees", "evictions", "batches"), (x.value for x in v)))
 
+    def phase_seconds(self) -> dict:
+        """lbvh_server_phase_seconds: worker time per phase, summed over batches."""
+        v = (ctypes.c_double * SERVER_PHASES)()
+        _check(self._lib.lbvh_server_phase_seconds(self._h, v), "lbvh_server_phase_seconds")
+        return dict(zip(("stage", "batch", "deliver", "query_only"), list(v)))
+
 
 def morton_codes(prims, kind: int = POINTS, morton_bits: int = 30, stream=None):
     """lbvh_morton_codes: (codes as int64 tensor holding the uint64 bits, bounds float[6])."""
@@ -441,6 +451,11 @@ def sort_pairs(keys, vals=None, key_bits: int = 64, stream=None):
     _check(lib.lbvh_sort_pairs(_ptr(k), _ptr(v), n, key_bits, _ptr(ko), _ptr(vo), _stream(stream)),
            "lbvh_sort_pairs")
     return ko, vo
+
+
+def release_cached_memory() -> None:
+    """lbvh_release_cached_memory: hand the library pool's unused blocks back."""
+    _check(load().lbvh_release_cached_memory(), "lbvh_release_cached_memory")
 
 
 def kernel_launches() -> int:

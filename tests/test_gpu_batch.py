@@ -108,6 +108,23 @@ def test_batch_points_separate_queries_63bit():
     run_and_compare(sizes, 0, 51, 0, False, seed=2, qsizes=[10, 5000, 3, 0, 7000])
 
 
+# Instances whose sizes sit on and around the sort's tile sizes (2048, 3072
+# and 4096 keys), so tiles of one instance end exactly at, or one key past, a
+# tile boundary; 63-bit codes with many instances (each instance's codes are
+# sorted apart, so the code width does not limit the instance count).
+TILE_EDGE_SIZES = [3071, 3072, 3073, 6144, 6145, 2047, 2048, 2049, 4095, 4096, 4097, 1, 0, 2, 12289]
+
+
+def test_batch_63bit_many_instances_tile_edges():
+    rng = np.random.default_rng(8)
+    sizes = TILE_EDGE_SIZES + [int(x) for x in rng.integers(1, 900, size=40)]
+    run_and_compare(sizes, 0, 63, 0, True, seed=8)
+
+
+def test_batch_boxes_63bit_tile_edges():
+    run_and_compare(TILE_EDGE_SIZES, 1, 63, 1, False, seed=9, qsizes=[s // 2 for s in TILE_EDGE_SIZES])
+
+
 def test_batch_boxes_box_queries():
     sizes = [2000, 1, 5000, 3, 10000]
     run_and_compare(sizes, 1, 30, 1, False, seed=3, qsizes=[700, 2, 1500, 0, 3000])
@@ -139,6 +156,35 @@ def test_batch_large_triggers_autotune_and_graph_picks_up_new_data():
     got = csr_segments(off, hits[:total], int(po[1]), int(po[2]))
     want = csr_segments(toff, thits, 0, sizes[1])
     assert all(np.array_equal(x, y) for x, y in zip(got, want))
+
+
+def test_batch_long_hit_lists():
+    # per-instance radii that give lists of ~40-400 hits (warp sort), a few
+    # thousand (CTA sort in shared memory) and all 12,000 points (CTA sort in
+    # global memory)
+    lbvh = L()
+    sizes = [3000, 12000, 500, 6000]
+    rads = [0.12, 2.0, 0.45, 0.5]
+    po = offsets_of(sizes)
+    pts = inputs.uniform_points(int(po[-1]), seed=21)
+    qsizes = [300, 40, 50, 200]
+    qo = offsets_of(qsizes)
+    q = np.concatenate([pts[po[k]:po[k] + qsizes[k]] for k in range(len(sizes))])
+    radii = np.repeat(np.array(rads, np.float32), qsizes)
+    b = lbvh.Batch()
+    cap = int(sum(qs * n for qs, n in zip(qsizes, sizes)))
+    off, hits, total, st = b.build_query(torch.from_numpy(pts).cuda(), po, lbvh.POINTS, 30,
+                                         torch.from_numpy(q).cuda(), qo, lbvh.SPHERE,
+                                         radii=torch.from_numpy(radii).cuda(), capacity=cap)
+    assert st == lbvh.OK
+    hits = hits[:total]
+    for k in range(len(sizes)):
+        o = oracle.build(pts[po[k]:po[k + 1]], oracle.POINTS, 30)
+        ooff, ohits = oracle.query(o, q[qo[k]:qo[k + 1]], oracle.SPHERE, radius=np.float32(rads[k]))
+        got = csr_segments(off, hits, int(qo[k]), int(qo[k + 1]))
+        want = [ohits[ooff[j]:ooff[j + 1]] for j in range(qsizes[k])]
+        assert all(np.array_equal(x, y) for x, y in zip(got, want)), k
+        assert max(len(x) for x in want) > 32
 
 
 def test_batch_capacity_error():

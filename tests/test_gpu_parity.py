@@ -280,10 +280,11 @@ def test_box_queries_on_points():
     assert_csr_equal(off, hits, *oracle.query(o, q, oracle.BOX))
 
 
-@pytest.mark.parametrize("radius", [0.0, 0.05, 0.2, 2.0])
+@pytest.mark.parametrize("radius", [0.0, 0.05, 0.2, 0.5, 2.0])
 def test_long_hit_lists_use_the_fixup_sort(radius):
-    """Lists longer than the register buffer (32) and than shared memory
-    (8192) are sorted by the fix-up kernel."""
+    """Lists longer than the walk's buffer (32) are sorted by the fix-up
+    kernels: by one warp up to 1024 hits, by one CTA in shared memory up to
+    8192, by one CTA in global memory above."""
     lbvh = L()
     pts = inputs.uniform_points(12000, seed=17)
     q = pts[::40]

@@ -78,12 +78,34 @@ def test_mixed_requests_equal_their_results_alone():
     srv.close()
 
 
+def test_wide_codes_share_batches():
+    # a burst of 63-bit requests: they queue up and run in shared batches
+    lbvh = L()
+    srv = lbvh.Server(budget_bytes=8 << 30, slots=1, max_batch=32)
+    reqs = []
+    for k in range(24):
+        n = 3000 + 997 * k
+        prims = torch.from_numpy(inputs.gaussian_mixture_points(n, seed=300 + k, components=4)).cuda()
+        r = float(inputs.radius_for_neighbours(n))
+        want = alone(prims, lbvh.POINTS, 63, prims, lbvh.SPHERE, r)
+        reqs.append((prims, r, want))
+    tickets = [srv.submit(p, lbvh.POINTS, 63, radius=r, capacity=len(w[1]) + 16) for p, r, w in reqs]
+    sizes = []
+    for t, (p, r, (ooff, ohits)) in zip(tickets, reqs):
+        off, hits, info = srv.wait(t)
+        assert info["status"] == lbvh.OK, info
+        sizes.append(info["batch_size"])
+        assert np.array_equal(off.cpu().numpy(), ooff) and np.array_equal(hits.cpu().numpy(), ohits)
+    assert max(sizes) > 2
+    srv.close()
+
+
 def test_budget_evicts_least_recently_used_and_refuses_what_never_fits():
     lbvh = L()
-    pts = [torch.from_numpy(inputs.uniform_points(20000, seed=k)).cuda() for k in range(6)]
+    pts = [torch.from_numpy(inputs.uniform_points(20000, seed=k)).cuda() for k in range(10)]
     r = float(inputs.radius_for_neighbours(20000))
-    # each request needs ~9.1 MB while it runs and leaves a ~2 MB tree: with
-    # 14 MB, the fourth request has to evict the oldest tree
+    # each request needs ~7-10 MB while it runs and leaves a ~1 MB tree (nodes
+    # only): with 14 MB, ten requests cannot all stay resident
     srv = lbvh.Server(budget_bytes=14 << 20, slots=1, max_batch=1)
     for k, p in enumerate(pts):
         off, hits, info = srv.wait(srv.submit(p, lbvh.POINTS, 30, radius=r, key=k + 1))
@@ -93,9 +115,9 @@ def test_budget_evicts_least_recently_used_and_refuses_what_never_fits():
     # the oldest tree was evicted: a query on it is refused; the newest answers
     _, _, info = srv.wait(srv.submit(None, lbvh.POINTS, 30, pts[0][:100], radius=r, key=1))
     assert info["status"] == lbvh.ERR_INVALID
-    off, hits, info = srv.wait(srv.submit(None, lbvh.POINTS, 30, pts[5][:100], radius=r, key=6))
+    off, hits, info = srv.wait(srv.submit(None, lbvh.POINTS, 30, pts[9][:100], radius=r, key=10))
     assert info["status"] == lbvh.OK
-    ooff, ohits = alone(pts[5], lbvh.POINTS, 30, pts[5][:100], lbvh.SPHERE, r)
+    ooff, ohits = alone(pts[9], lbvh.POINTS, 30, pts[9][:100], lbvh.SPHERE, r)
     assert np.array_equal(off.cpu().numpy(), ooff) and np.array_equal(hits.cpu().numpy(), ohits)
     # a request larger than the whole budget is refused
     big = torch.from_numpy(inputs.uniform_points(400000, seed=9)).cuda()
