@@ -54,18 +54,25 @@ UNIT = "Mprims/s"
 #               written, store word 8, sibling box 24 re-read
 #   query walk  query 12 read, count 4 written, 4 per hit kept, tree read once (48 B/leaf)
 #   query copy  count/start/offset read per query, 4 per hit read and 4 written
-ALG_BYTES = {
-    "bounds": lambda n, nq, hits: 12 * n,
-    "encode": lambda n, nq, hits: 20 * n,
-    "sort_pass0": lambda n, nq, hits: 20 * n,
-    **{f"sort_pass{k}": (lambda n, nq, hits: 24 * n) for k in range(1, 8)},
-    "construct": lambda n, nq, hits: 104 * n,
-    "query_walk": lambda n, nq, hits: 16 * nq + 4 * hits + 48 * n,
-    "query_order": lambda n, nq, hits: 12 * nq + 8 * nq + 4 * 24 * nq,
-    "query_scan": lambda n, nq, hits: 4 * nq + 8 * (nq + 1),
-    "query_copy": lambda n, nq, hits: 16 * nq + 8 * hits,
-    "query_overflow": lambda n, nq, hits: 0,
-}
+def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_queries: bool = False):
+    """Algorithmic bytes of one launch of a stage (the data the method must
+    move): pb = bytes of a primitive, lb = of a leaf record, qb = of a query."""
+    pb, lb, qb = (24, 32, 24 if box_queries else 12) if boxes else (12, 16, 24 if box_queries else 12)
+    table = {
+        "bounds": pb * n,
+        "encode": (pb + 8) * n,
+        "sort_pass0": 20 * n,
+        **{f"sort_pass{k}": 24 * n for k in range(1, 8)},
+        # codes, perm, primitive read; leaf + internal node write; store word; sibling box re-read
+        "construct": (8 + 4 + pb + lb + 32 + 8 + 24) * n,
+        # query + count/position per query, each kept hit, the tree once
+        "query_walk": (qb + 8) * nq + 4 * hits + (32 + lb) * n,
+        "query_order": (qb + 8 + 4 * 24) * nq,
+        "query_scan": 4 * nq + 8 * (nq + 1),
+        "query_copy": 16 * nq + 8 * hits,
+        "query_overflow": 0,
+    }
+    return table.get(stage)
 
 BATCH_WORKLOADS = {
     # name: (description, clouds, min size, max size, seed, Morton bits)
@@ -98,6 +105,10 @@ WORKLOADS = {
                            "queries at the points, radius for 16 expected neighbours (profiling case)", 1 << 24, 63),
     "uniform_16384_30bit": ("16,384 FP32 points uniform in [0,1)^3 (seed 0), 30-bit codes; build + 16,384 "
                             "sphere queries at the points, radius for 16 expected neighbours", 16384, 30),
+    "mixture_boxes_2^25_63bit": ("2^25 FP32 boxes, centres from a 64-component Gaussian mixture (sigma 0.005, "
+                                 "component centres uniform in [0,1)^3), half-extents lognormal(ln 1e-4, 0.5); "
+                                 "63-bit codes; build + 2^24 box-overlap queries from the same mixture",
+                                 1 << 25, 63, "mixture_boxes"),
 }
 
 
@@ -207,11 +218,21 @@ class ClockSampler:
 # ---------------------------------------------------------------- workload
 
 
+def workload_family(workload: str) -> str:
+    w = WORKLOADS[workload]
+    return w[3] if len(w) > 3 else "uniform"
+
+
 def make_inputs(workload: str, seed: int):
-    desc, n, bits = WORKLOADS[workload]
+    """(description, n, bits, prims, queries or None (= the prims), boxes?, box queries?, radius)."""
+    desc, n, bits = WORKLOADS[workload][:3]
+    if workload_family(workload) == "mixture_boxes":
+        prims = inputs.gaussian_mixture_boxes(n, seed=seed)
+        queries = inputs.gaussian_mixture_boxes(n // 2, seed=seed + 1, component_seed=seed)
+        return desc, n, bits, prims, queries, True, True, 0.0
     pts = inputs.uniform_points(n, seed=seed)
     r = inputs.radius_for_neighbours(n)
-    return desc, n, bits, pts, r
+    return desc, n, bits, pts, None, False, False, r
 
 
 def measured_hbm_gbs():
@@ -245,21 +266,31 @@ def traffic_for(stage: str):
 # ---------------------------------------------------------------- oracle timing
 
 
-def oracle_sample(seed: int, n_sample: int = 1 << 20, q_sample: int = 1 << 14, bits: int = 63):
+def oracle_sample(seed: int, n_sample: int = 1 << 23, q_sample: int = 1 << 18, bits: int = 63,
+                  family: str = "uniform"):
     """The CPU oracle on a bounded sample of the same workload: a full build of
-    n_sample uniform points and q_sample of its radius queries (radius for 16
-    neighbours at that size). Returns (prims/s, description)."""
+    n_sample primitives and q_sample of its queries (uniform points with radius
+    queries for 16 neighbours at that size, or mixture boxes with box queries
+    from the same mixture). Returns (prims/s, description)."""
     import oracle
-    pts = inputs.uniform_points(n_sample, seed=seed + 101)
-    r = inputs.radius_for_neighbours(n_sample)
+    if family == "mixture_boxes":
+        prims = inputs.gaussian_mixture_boxes(n_sample, seed=seed + 101)
+        q = inputs.gaussian_mixture_boxes(q_sample, seed=seed + 102, component_seed=seed + 101)
+        kind, qkind, r, what = oracle.BOXES, oracle.BOX, 0.0, "Gaussian-mixture boxes", 
+        qwhat = "box-overlap queries from the same mixture"
+    else:
+        prims = inputs.uniform_points(n_sample, seed=seed + 101)
+        q = prims[:q_sample]
+        kind, qkind, r, what = oracle.POINTS, oracle.SPHERE, inputs.radius_for_neighbours(n_sample), "uniform points"
+        qwhat = "16-neighbour sphere queries at its points"
     t0 = time.perf_counter()
-    tree = oracle.build(pts, oracle.POINTS, bits)
+    tree = oracle.build(prims, kind, bits)
     t1 = time.perf_counter()
-    oracle.query(tree, pts[:q_sample], oracle.SPHERE, radius=r)
+    oracle.query(tree, q, qkind, radius=r)
     t2 = time.perf_counter()
     per_prim = (t1 - t0) / n_sample + (t2 - t1) / q_sample
-    desc = (f"oracle (C, 1 thread) build of {n_sample} uniform points at {bits} bits "
-            f"({t1 - t0:.2f} s) + {q_sample} of its 16-neighbour sphere queries ({t2 - t1:.2f} s); "
+    desc = (f"oracle (C, 1 thread) build of {n_sample} {what} at {bits} bits "
+            f"({t1 - t0:.2f} s) + {q_sample} {qwhat} ({t2 - t1:.2f} s); "
             f"throughput = 1 / (build s/prim + query s/query)")
     return 1.0 / per_prim, desc, t2 - t0
 
@@ -275,9 +306,11 @@ def run_reference(args, world, rank):
         desc, n, bits = d[0], int(inputs.poisson_requests(d[1], d[2], d[3], d[4], d[5])[1].sum()), d[6]
     else:
         desc, n, bits = WORKLOADS[args.workload][:3]
+    family = workload_family(args.workload) if args.workload in WORKLOADS else "uniform"
     samples = []
     for step in range(args.warmup + args.steps):
-        v, sdesc, _ = oracle_sample(args.seed + step, n_sample=1 << 19, q_sample=1 << 13, bits=bits)
+        v, sdesc, _ = oracle_sample(args.seed + step, n_sample=1 << 19, q_sample=1 << 13, bits=bits,
+                                    family=family)
         if step >= args.warmup:
             samples.append(v)
     value = statistics.median(samples) / 1e6
@@ -302,27 +335,32 @@ def run_gpu(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    desc, n, bits, pts_host, radius = make_inputs(args.workload, args.seed + rank)
-    nq = n
-    pts = torch.from_numpy(pts_host).to(dev)
-    # the queries are the points, held in their own buffer: the general query
-    # path (query centres Morton-encoded and sorted) runs, not the shortcut for
-    # a tree queried with its own primitive buffer
-    qpts = pts.clone()
+    desc, n, bits, prims_host, queries_host, boxes, box_queries, radius = make_inputs(args.workload,
+                                                                                       args.seed + rank)
+    kind = lbvh.BOXES if boxes else lbvh.POINTS
+    qkind = lbvh.BOX if box_queries else lbvh.SPHERE
+    pts = torch.from_numpy(prims_host).to(dev)
+    # queries in their own buffer (the points themselves for the uniform
+    # workloads): the general query path (query centres Morton-encoded and
+    # sorted) runs, not the shortcut for a tree queried with its own primitives
+    if queries_host is None:
+        queries_host = prims_host
+    qpts = torch.from_numpy(queries_host).to(dev)
+    nq = qpts.shape[0]
     stream = torch.cuda.current_stream(dev)
 
     tree = lbvh.Tree()
     tree.set_profiling(True)
     offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     # size the hit buffer once (a production caller does the same)
-    tree.build(pts, lbvh.POINTS, bits)
-    st, total = tree.query_into(qpts, lbvh.SPHERE, offsets, None, radius=float(radius))
+    tree.build(pts, kind, bits)
+    st, total = tree.query_into(qpts, qkind, offsets, None, radius=float(radius))
     assert st in (lbvh.OK, lbvh.ERR_CAPACITY), st
     hits = torch.empty(max(int(total * 1.05) + 1024, 1), dtype=torch.int32, device=dev)
 
     def step():
-        tree.build(pts, lbvh.POINTS, bits)
-        s, tot = tree.query_into(qpts, lbvh.SPHERE, offsets, hits, radius=float(radius))
+        tree.build(pts, kind, bits)
+        s, tot = tree.query_into(qpts, qkind, offsets, hits, radius=float(radius))
         if s != lbvh.OK:
             raise lbvh.LbvhError(s, "lbvh_query_into")
         return tot
@@ -369,24 +407,26 @@ def run_gpu(args, world, rank, local):
     query_ms = sum(v for k, v in stage_ms.items() if k.startswith("query"))
     dominant = max(stage_ms, key=lambda k: stage_ms[k])
     peak, peak_kind = measured_hbm_gbs()
-    alg = {k: ALG_BYTES[k](n, nq, total_hits) for k in stage_ms if k in ALG_BYTES}
+    alg = {k: alg_bytes(k, n, nq, total_hits, boxes, box_queries) for k in stage_ms
+           if alg_bytes(k, n, nq, total_hits) is not None}
     achieved = alg[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
     build_bytes = sum(v for k, v in alg.items() if not k.startswith("query"))
 
     # ---- end to end through the C ABI from host buffers
     e2e = None
     if not args.no_e2e:
-        host_pts = torch.from_numpy(pts_host).pin_memory()
+        host_pts = torch.from_numpy(prims_host).pin_memory()
+        host_q = torch.from_numpy(queries_host).pin_memory()
         host_off = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
         host_hits = torch.empty(hits.numel(), dtype=torch.int32).pin_memory()
         dpts = torch.empty_like(pts)
-        dq = torch.empty_like(pts)
+        dq = torch.empty_like(qpts)
 
         def e2e_step():
             dpts.copy_(host_pts, non_blocking=True)
-            dq.copy_(host_pts, non_blocking=True)
-            tree.build(dpts, lbvh.POINTS, bits)
-            s, tot = tree.query_into(dq, lbvh.SPHERE, offsets, hits, radius=float(radius))
+            dq.copy_(host_q, non_blocking=True)
+            tree.build(dpts, kind, bits)
+            s, tot = tree.query_into(dq, qkind, offsets, hits, radius=float(radius))
             if s != lbvh.OK:
                 raise lbvh.LbvhError(s, "lbvh_query_into")
             host_off.copy_(offsets, non_blocking=True)
@@ -405,14 +445,14 @@ def run_gpu(args, world, rank, local):
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world, dev) / args.steps
         e2e = {"value": n * world / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
-               "h2d_bytes_per_step": int(2 * pts.numel() * 4),
+               "h2d_bytes_per_step": int((pts.numel() + qpts.numel()) * 4),
                "d2h_bytes_per_step": int((nq + 1) * 8 + tot * 4),
-               "note": "pinned host points and query centres -> device, build, query, "
+               "note": "pinned host primitives and queries -> device, build, query, "
                        "CSR offsets + hits -> pinned host"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sdesc, _ = oracle_sample(args.seed)
+        v, sdesc, _ = oracle_sample(args.seed, bits=bits, family=workload_family(args.workload))
         cpu = {"value": v / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc}
 
     if rank == 0:
@@ -422,7 +462,7 @@ def run_gpu(args, world, rank, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "n": n, "nq": nq,
                        "morton_bits": bits, "radius": float(radius), "mean_hits": total_hits / nq,
-                       "l2": "inputs larger than L2 (points 402 MB; step touches ~5 GB)",
+                       "l2": f"inputs larger than L2 (primitives {pts.numel() * 4 / 1e6:.0f} MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "build_mprims_s": n / (build_ms * 1e-3) / 1e6,
             "query_mqueries_s": nq / (query_ms * 1e-3) / 1e6,
@@ -538,7 +578,11 @@ def mixture_radius(n: int, k: float = 16.0, components: int = 64, sigma: float =
     return float(np.float32((3.0 * k / (4.0 * math.pi * density)) ** (1.0 / 3.0)))
 
 
-WARM_REQUESTS = 64
+# One worker slot with batches of up to 256 requests measured best on this
+# workload (throughput at the offered load, lowest p99); two slots of 64 were
+# within noise on throughput with a wider p99.
+SERVER_SLOTS = 1
+SERVER_MAX_BATCH = 256
 
 
 def run_served(args, world, rank, local):
@@ -575,30 +619,25 @@ def run_served(args, world, rank, local):
         return float(np.percentile(lat, 50) * 1e3), float(np.percentile(lat, 99) * 1e3)
 
     # ---- served: a submitter follows the arrival schedule
-    srv = lbvh.Server(budget, slots=3, max_batch=64)
-    # warm-up: one burst of the first requests (not kept resident), so the
-    # slots' staging buffers have grown as they would in steady serving
-    warm = [srv.submit(views[k], lbvh.POINTS, bits, radius=float(radii[k]), capacity=caps[k])
-            for k in range(min(WARM_REQUESTS, count))]
-    for w in warm:
-        srv.wait(w)
-    phases0 = srv.phase_seconds()
-    tickets = [None] * count
-    t0 = time.perf_counter()
+    srv = lbvh.Server(budget, slots=SERVER_SLOTS, max_batch=SERVER_MAX_BATCH)
 
-    def submitter():
-        for k in range(count):
-            delay = t0 + arrivals[k] - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            tickets[k] = srv.submit(views[k], lbvh.POINTS, bits, radius=float(radii[k]), capacity=caps[k],
-                                    key=k + 1)
+    def replay(keep: bool):
+        """Submit the requests on their arrival schedule (a submitter thread)
+        and wait for each in turn; returns (wall s, latencies, batch sizes, hits)."""
+        tickets = [None] * count
+        t0 = time.perf_counter()
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    lat, batch_sizes, totals = [], [], 0
-    launches0 = lbvh.kernel_launches()
-    with ClockSampler(None) as clocks:
+        def submitter():
+            for k in range(count):
+                delay = t0 + arrivals[k] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[k] = srv.submit(views[k], lbvh.POINTS, bits, radius=float(radii[k]), capacity=caps[k],
+                                        key=k + 1 if keep else 0)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, sizes_seen, hits = [], [], 0
         for k in range(count):
             while tickets[k] is None:
                 time.sleep(0.0001)
@@ -606,37 +645,50 @@ def run_served(args, world, rank, local):
             if info["status"] != lbvh.OK:
                 raise lbvh.LbvhError(info["status"], "served request")
             lat.append(info["latency_s"])
-            batch_sizes.append(info["batch_size"])
-            totals += info["total"]
-        t_end = time.perf_counter()
-    th.join()
+            sizes_seen.append(info["batch_size"])
+            hits += info["total"]
+        wall = time.perf_counter() - t0
+        th.join()
+        return wall, lat, sizes_seen, hits
+
+    # warm-up: one untimed replay of the same schedule whose trees are not
+    # kept, so the server's buffers have the sizes of steady serving
+    replay(keep=False)
+    torch.cuda.synchronize()
+    phases0 = srv.phase_seconds()
+    batches0 = srv.stats()["batches"]
+    launches0 = lbvh.kernel_launches()
+    with ClockSampler(None) as clocks:
+        served_s, lat, batch_sizes, totals = replay(keep=True)
     launches = lbvh.kernel_launches() - launches0
     stats = srv.stats()
     phases = {k: v - phases0[k] for k, v in srv.phase_seconds().items()}
     srv.close()
-    served_s = t_end - t0
     served_p50, served_p99 = percentiles(lat)
 
     # ---- one at a time, same arrivals
     tree = lbvh.Tree()
     fo = torch.empty(int(sizes.max()) + 1, dtype=torch.int64, device=dev)
     fh = torch.empty(max(caps), dtype=torch.int32, device=dev)
-    tree.build(views[0], lbvh.POINTS, bits)
-    tree.query_into(views[0], lbvh.SPHERE, fo[:int(sizes[0]) + 1], fh, radius=float(radii[0]))
+
+    def fifo_replay():
+        lat, hits = [], 0
+        t0 = time.perf_counter()
+        for k in range(count):
+            wait = t0 + arrivals[k] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            tree.build(views[k], lbvh.POINTS, bits)
+            st, tot = tree.query_into(views[k], lbvh.SPHERE, fo[:int(sizes[k]) + 1], fh, radius=float(radii[k]))
+            if st != lbvh.OK:
+                raise lbvh.LbvhError(st, "lbvh_query_into")
+            hits += tot
+            lat.append(time.perf_counter() - (t0 + arrivals[k]))
+        return time.perf_counter() - t0, lat, hits
+
+    fifo_replay()  # warm-up, untimed
     torch.cuda.synchronize()
-    flat, ftotal = [], 0
-    t0 = time.perf_counter()
-    for k in range(count):
-        wait = t0 + arrivals[k] - time.perf_counter()
-        if wait > 0:
-            time.sleep(wait)
-        tree.build(views[k], lbvh.POINTS, bits)
-        st, tot = tree.query_into(views[k], lbvh.SPHERE, fo[:int(sizes[k]) + 1], fh, radius=float(radii[k]))
-        if st != lbvh.OK:
-            raise lbvh.LbvhError(st, "lbvh_query_into")
-        ftotal += tot
-        flat.append(time.perf_counter() - (t0 + arrivals[k]))
-    fifo_s = time.perf_counter() - t0
+    fifo_s, flat, ftotal = fifo_replay()
     tree.close()
     assert ftotal == totals, (ftotal, totals)
     fifo_p50, fifo_p99 = percentiles(flat)
@@ -653,14 +705,15 @@ def run_served(args, world, rank, local):
                        "mean_hits": totals / n, "parallelism": "replicas" if world > 1 else "single"},
             "served": {"throughput_mprims_s": value, "p50_ms": served_p50, "p99_ms": served_p99,
                        "wall_s": served_s, "mean_batch": float(np.mean(batch_sizes)),
-                       "batches": stats["batches"], "resident_trees": stats["resident_trees"],
+                       "batches": stats["batches"] - batches0, "slots": SERVER_SLOTS,
+                       "max_batch": SERVER_MAX_BATCH, "resident_trees": stats["resident_trees"],
                        "resident_bytes": stats["resident_bytes"], "evictions": stats["evictions"],
                        "worker_phase_s": phases},
             "one_at_a_time": {"throughput_mprims_s": n / fifo_s / 1e6, "p50_ms": fifo_p50, "p99_ms": fifo_p99,
                               "wall_s": fifo_s},
             "speedup_vs_one_at_a_time": fifo_s / served_s,
             "timing": "wall clock from the first arrival to the last completion; latency = arrival to results; "
-                      f"server warmed by a burst of the first {min(WARM_REQUESTS, count)} requests",
+                      "server warmed by one untimed replay of the same schedule (trees not kept)",
             "gpu_launches": launches,
             "clocks": clocks.summary(),
         }

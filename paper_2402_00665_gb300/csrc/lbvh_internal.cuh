@@ -35,7 +35,7 @@ struct Control {
     uint32_t overflow_big;         // overflow lists too long for one warp's sort
     uint32_t pad[7];
 };
-constexpr int kQueryBufferHits = 32;  // hits kept per query by the walk
+constexpr int kQueryBufferHits = 64;  // hits kept per query by the walk
 
 // ---------------------------------------------------------------- min / max
 // FP32 min / max that order -0.0 below +0.0, so the scene bounds and the

@@ -29,10 +29,11 @@
 //             scratch array (no shared memory: L1 stays with the tree), and
 //             (hit count, i) at q.
 //   scan      exclusive scan of the counts -> offsets, total (host reads it).
-//   copy      in query order: each thread loads one slot into registers and
-//             sorts it with a bitonic network; the warp writes its 32 lists,
-//             adjacent in the CSR, through shared memory, one coalesced list
-//             per step.
+//   copy      in query order: each thread loads one slot of up to 32 hits
+//             into registers and sorts it with a bitonic network; the warp
+//             writes its 32 lists, adjacent in the CSR, through shared
+//             memory, one coalesced list per step; lists of 33..64 hits are
+//             sorted by the whole warp (two values per lane, shuffles).
 //   overflow  queries with more hits walk again and write straight into the
 //             CSR; a fix-up kernel sorts those lists, one warp per list (one
 //             CTA per list above 1024 hits).
@@ -128,7 +129,8 @@ __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf)
     return node == kSentinel || node == nodes;
 }
 
-constexpr int kSlot = kQueryBufferHits;
+constexpr int kSlot = kQueryBufferHits;  // ids kept per walk (slot size)
+constexpr int kRegSort = 32;             // lists up to this long are sorted in one thread's registers
 
 __device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) {
     return qa.order ? (int64_t)__ldcs(qa.order + i) : i;
@@ -231,33 +233,61 @@ __device__ __forceinline__ void sort32(uint32_t (&v)[32]) {
     }
 }
 
-// Thread q sorts query q's slot in registers; the warp then writes its 32
-// lists, which are adjacent in the CSR, one list per step with lanes on
-// consecutive hits.
+// Ascending bitonic sort of 64 values held by a warp, value e in lane e % 32
+// (v0: e < 32, v1: e >= 32). Steps with partner distance 32 compare a lane's
+// two values; the others exchange with lane ^ j by shuffle.
+__device__ __forceinline__ void warp_sort64(uint32_t &v0, uint32_t &v1) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {  // k == 64: one ascending merge
+                const uint32_t lo = min(v0, v1), hi = max(v0, v1);
+                v0 = lo;
+                v1 = hi;
+            } else {
+                const bool lower = (lane & j) == 0;
+                const uint32_t p0 = __shfl_xor_sync(0xffffffffu, v0, j);
+                const uint32_t p1 = __shfl_xor_sync(0xffffffffu, v1, j);
+                const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+                v0 = lower == up0 ? min(v0, p0) : max(v0, p0);
+                v1 = lower == up1 ? min(v1, p1) : max(v1, p1);
+            }
+        }
+    }
+}
+
+// Thread q sorts query q's list in registers if it has at most 32 hits; the
+// warp then writes its 32 lists, which are adjacent in the CSR, one list per
+// step with lanes on consecutive hits. Lists of 33..64 hits are then sorted
+// and written by the whole warp, one after the other.
 __global__ void __launch_bounds__(kThreads)
     copy_kernel(int64_t nq, const uint2 *__restrict__ count_pos, const int64_t *__restrict__ offsets,
                 const uint32_t *__restrict__ slots, uint32_t *__restrict__ hits,
                 unsigned long long capacity, Control *ctl) {
-    __shared__ uint32_t s_lists[kThreads / 32][32][kSlot + 1];
+    __shared__ uint32_t s_lists[kThreads / 32][32][kRegSort + 1];
     if (ctl->total > capacity) {  // the caller's buffer is too small: write nothing
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctl->query_flags, kFlagCapacity);
         return;
     }
     const int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t c = 0;
+    uint32_t c = 0, mid = 0;
     int64_t dst = 0, pos = 0;
     if (q < nq) {
         const uint2 cp = count_pos[q];
-        c = cp.x > (uint32_t)kSlot ? 0u : cp.x;  // longer lists: the overflow walk
+        c = cp.x > (uint32_t)kRegSort ? 0u : cp.x;
+        mid = cp.x > (uint32_t)kRegSort && cp.x <= (uint32_t)kSlot ? cp.x : 0u;  // longer: the overflow walk
         pos = cp.y;
         dst = offsets[q];
     }
-    if (!__any_sync(0xffffffffu, c != 0)) return;
-    uint32_t v[kSlot];
+    uint32_t mids = __ballot_sync(0xffffffffu, mid != 0);
+    if (!__any_sync(0xffffffffu, c != 0) && mids == 0) return;
+    uint32_t v[kRegSort];
     const uint4 *src = reinterpret_cast<const uint4 *>(slots + pos * kSlot);
 #pragma unroll
-    for (int j4 = 0; j4 < kSlot / 4; ++j4) {
+    for (int j4 = 0; j4 < kRegSort / 4; ++j4) {
         uint4 w = make_uint4(~0u, ~0u, ~0u, ~0u);
         if (4 * j4 < (int)c) w = src[j4];
         v[4 * j4] = 4 * j4 < (int)c ? w.x : ~0u;
@@ -267,12 +297,25 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (__any_sync(0xffffffffu, c > 1)) sort32(v);
 #pragma unroll
-    for (int j = 0; j < kSlot; ++j) s_lists[warp][lane][j] = v[j];
+    for (int j = 0; j < kRegSort; ++j) s_lists[warp][lane][j] = v[j];
     __syncwarp();
     for (int s = 0; s < 32; ++s) {
         const uint32_t cs = __shfl_sync(0xffffffffu, c, s);
         const int64_t ds = __shfl_sync(0xffffffffu, dst, s);
         if ((uint32_t)lane < cs) hits[ds + lane] = s_lists[warp][s][lane];
+    }
+    while (mids) {
+        const int s = __ffs(mids) - 1;
+        mids &= mids - 1;
+        const uint32_t m = __shfl_sync(0xffffffffu, mid, s);
+        const int64_t ps = __shfl_sync(0xffffffffu, pos, s);
+        const int64_t ds = __shfl_sync(0xffffffffu, dst, s);
+        const uint32_t *slot = slots + ps * kSlot;
+        uint32_t v0 = (uint32_t)lane < m ? slot[lane] : ~0u;
+        uint32_t v1 = (uint32_t)lane + 32 < m ? slot[lane + 32] : ~0u;
+        warp_sort64(v0, v1);
+        if ((uint32_t)lane < m) hits[ds + lane] = v0;
+        if ((uint32_t)lane + 32 < m) hits[ds + lane + 32] = v1;
     }
 }
 

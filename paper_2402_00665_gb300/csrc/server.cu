@@ -134,7 +134,7 @@ uint64_t estimate_bytes(const lbvh_request &r) {
     const uint64_t prim = r.kind == LBVH_PRIM_POINTS ? 12 : 24;
     const uint64_t qsz = r.qkind == LBVH_Q_SPHERE ? 12 : 24;
     const uint64_t build = n * (prim + 24 + 24 + 48 + 8 + 16);
-    const uint64_t query = nq * (qsz + 4 + 8 + 128 + 4 + 8 + 24 + 8) + r.capacity * 4;
+    const uint64_t query = nq * (qsz + 4 + 8 + lbvh::kQueryBufferHits * 4 + 4 + 8 + 24 + 8) + r.capacity * 4;
     return build + query;
 }
 

@@ -159,12 +159,13 @@ def test_batch_large_triggers_autotune_and_graph_picks_up_new_data():
 
 
 def test_batch_long_hit_lists():
-    # per-instance radii that give lists of ~40-400 hits (warp sort), a few
-    # thousand (CTA sort in shared memory) and all 12,000 points (CTA sort in
-    # global memory)
+    # per-instance radii that give lists of ~30-90 hits (register and warp
+    # sorts, and the second walk), ~190 (warp sort after the second walk), a
+    # few thousand (CTA sort in shared memory) and all 12,000 points (CTA sort
+    # in global memory)
     lbvh = L()
     sizes = [3000, 12000, 500, 6000]
-    rads = [0.12, 2.0, 0.45, 0.5]
+    rads = [0.17, 2.0, 0.45, 0.5]
     po = offsets_of(sizes)
     pts = inputs.uniform_points(int(po[-1]), seed=21)
     qsizes = [300, 40, 50, 200]

@@ -280,11 +280,12 @@ def test_box_queries_on_points():
     assert_csr_equal(off, hits, *oracle.query(o, q, oracle.BOX))
 
 
-@pytest.mark.parametrize("radius", [0.0, 0.05, 0.2, 0.5, 2.0])
+@pytest.mark.parametrize("radius", [0.0, 0.05, 0.1, 0.2, 0.5, 2.0])
 def test_long_hit_lists_use_the_fixup_sort(radius):
-    """Lists longer than the walk's buffer (32) are sorted by the fix-up
-    kernels: by one warp up to 1024 hits, by one CTA in shared memory up to
-    8192, by one CTA in global memory above."""
+    """Lists of up to 32 hits are sorted in one thread's registers, 33..64 by
+    a warp in registers; longer ones (past the walk's 64-hit buffer) walk again
+    and are sorted by one warp up to 1024 hits, by one CTA in shared memory up
+    to 8192, by one CTA in global memory above."""
     lbvh = L()
     pts = inputs.uniform_points(12000, seed=17)
     q = pts[::40]
