@@ -43,6 +43,7 @@ sys.path.insert(0, ROOT)
 from paper_2402_00665_gb300 import inputs  # noqa: E402
 
 METRIC = "build+query Mprims/s (one LBVH build and n radius queries per step)"
+REFIT_METRIC = "refit Mprims/s (new boxes for moved primitives on a kept topology)"
 UNIT = "Mprims/s"
 
 # Algorithmic bytes per primitive (or per query) of each stage: the data the
@@ -105,6 +106,10 @@ WORKLOADS = {
                            "queries at the points, radius for 16 expected neighbours (profiling case)", 1 << 24, 63),
     "uniform_16384_30bit": ("16,384 FP32 points uniform in [0,1)^3 (seed 0), 30-bit codes; build + 16,384 "
                             "sphere queries at the points, radius for 16 expected neighbours", 16384, 30),
+    "refit_uniform_2^25_63bit": ("refit of a 2^25-point tree (63-bit codes, built once from uniform points in "
+                                 "[0,1)^3) to moved points: every step gives the tree new coordinates (the points "
+                                 "plus N(0, 0.001) jitter, two alternating sets) and recomputes all boxes on the "
+                                 "kept topology", 1 << 25, 63, "refit"),
     "mixture_boxes_2^25_63bit": ("2^25 FP32 boxes, centres from a 64-component Gaussian mixture (sigma 0.005, "
                                  "component centres uniform in [0,1)^3), half-extents lognormal(ln 1e-4, 0.5); "
                                  "63-bit codes; build + 2^24 box-overlap queries from the same mixture",
@@ -307,15 +312,32 @@ def run_reference(args, world, rank):
     else:
         desc, n, bits = WORKLOADS[args.workload][:3]
     family = workload_family(args.workload) if args.workload in WORKLOADS else "uniform"
+    metric = METRIC
     samples = []
-    for step in range(args.warmup + args.steps):
-        v, sdesc, _ = oracle_sample(args.seed + step, n_sample=1 << 19, q_sample=1 << 13, bits=bits,
-                                    family=family)
-        if step >= args.warmup:
-            samples.append(v)
+    if family == "refit":
+        import oracle
+        metric = REFIT_METRIC
+        m = 1 << 20
+        pts = inputs.uniform_points(m, seed=args.seed)
+        ot = oracle.build(pts, oracle.POINTS, bits)
+        rng = np.random.default_rng(args.seed + 1)
+        for step in range(args.warmup + args.steps):
+            mv = (pts + rng.normal(0.0, 0.001, size=pts.shape)).astype(np.float32)
+            t0 = time.perf_counter()
+            oracle.refit(ot, mv)
+            dt = time.perf_counter() - t0
+            if step >= args.warmup:
+                samples.append(m / dt)
+        sdesc = f"oracle refit (C boxes in post-order, 1 thread) of a {m}-point tree, per step"
+    else:
+        for step in range(args.warmup + args.steps):
+            v, sdesc, _ = oracle_sample(args.seed + step, n_sample=1 << 19, q_sample=1 << 13, bits=bits,
+                                        family=family)
+            if step >= args.warmup:
+                samples.append(v)
     value = statistics.median(samples) / 1e6
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": n / (value * 1e6) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -476,6 +498,101 @@ def run_gpu(args, world, rank, local):
             "gpu_launches": launches,
             "clocks": clock,
             "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    tree.close()
+
+
+def run_refit(args, world, rank, local):
+    """Refit configuration: a tree built once, then refitted every step."""
+    import torch
+    from paper_2402_00665_gb300 import lbvh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, n, bits = WORKLOADS[args.workload][:3]
+    base = inputs.uniform_points(n, seed=args.seed + rank)
+    rng = np.random.default_rng(args.seed + rank + 1)
+    moved_host = [(base + rng.normal(0.0, 0.001, size=base.shape)).astype(np.float32) for _ in range(2)]
+    moved = [torch.from_numpy(m).to(dev) for m in moved_host]
+    stream = torch.cuda.current_stream(dev)
+    tree = lbvh.Tree()
+    tree.set_profiling(True)
+    tree.build(torch.from_numpy(base).to(dev), lbvh.POINTS, bits)
+    for k in range(args.warmup):
+        tree.refit(moved[k % 2])
+    tree.check()
+    torch.cuda.synchronize()
+    stage_sum: dict[str, float] = {}
+    launches0 = lbvh.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(None) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for k in range(args.steps):
+            tree.refit(moved[k % 2])
+            for name, v in tree.stage_times().items():
+                stage_sum[name] = stage_sum.get(name, 0.0) + v
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    tree.check()
+    launches = lbvh.kernel_launches() - launches0
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    value = n * world / (ms_step * 1e-3) / 1e6
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+    peak, peak_kind = measured_hbm_gbs()
+    alg = {k: alg_bytes(k, n, 0, 0) for k in stage_ms if alg_bytes(k, n, 0, 0) is not None}
+    achieved = alg["construct"] / (stage_ms["construct"] * 1e-3) / 1e9
+    refit_frac = sum(alg.values()) / (sum(stage_ms.values()) * 1e-3) / 1e9 / peak
+
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(m).pin_memory() for m in moved_host]
+        dpts = torch.empty_like(moved[0])
+        for k in range(2):
+            dpts.copy_(host[k], non_blocking=True)
+            tree.refit(dpts)
+            tree.check()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            dpts.copy_(host[k % 2], non_blocking=True)
+            tree.refit(dpts)
+            tree.check()  # reads the control block back: the step's result status
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev) / args.steps
+        e2e = {"value": n * world / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": int(dpts.numel() * 4), "d2h_bytes_per_step": 128,
+               "note": "pinned host points -> device, refit, control block (status) -> host"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        m = 1 << 22
+        pts = inputs.uniform_points(m, seed=args.seed + 7)
+        ot = oracle.build(pts, oracle.POINTS, bits)
+        mv = (pts + np.random.default_rng(8).normal(0.0, 0.001, size=pts.shape)).astype(np.float32)
+        t0 = time.perf_counter()
+        oracle.refit(ot, mv)
+        dt = time.perf_counter() - t0
+        cpu = {"value": m / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle refit (C boxes in post-order, 1 thread) of a {m}-point tree: {dt:.2f} s"}
+    if rank == 0:
+        line = {
+            "metric": REFIT_METRIC, "value": value,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": n, "morton_bits": bits,
+                       "l2": f"inputs larger than L2 (points {n * 12 / 1e6:.0f} MB, two alternating sets)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "refit_hbm_frac": refit_frac,
+            "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda kv: -kv[1])},
+            "roofline": {"bound": "hbm", "kernel": "construct", "achieved": achieved, "peak": peak,
+                         "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic_for("construct"), "algorithmic_bytes": alg["construct"]},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks.summary(), "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     tree.close()
@@ -744,7 +861,10 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU for the lbvh arm")
     world, rank, local = dist_setup(True)
-    run_gpu(args, world, rank, local)
+    if workload_family(args.workload) == "refit":
+        run_refit(args, world, rank, local)
+    else:
+        run_gpu(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

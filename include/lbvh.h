@@ -67,8 +67,9 @@ typedef enum { LBVH_Q_SPHERE = 0, LBVH_Q_BOX = 1 } lbvh_query_kind;
 /* Create an empty tree handle (no device memory yet). *out receives it. */
 lbvh_status lbvh_tree_create(lbvh_tree_t *out);
 
-/* Release the tree and all device memory it owns. Waits for the tree's last
- * stream first. Accepts NULL. */
+/* Release the tree and all device memory it owns. Waits for the tree's own
+ * last build and last query to finish first (not for whole streams). Accepts
+ * NULL. */
 void lbvh_tree_destroy(lbvh_tree_t tree);
 
 /* Build (or rebuild in place) the whole hierarchy: scene bounds, Morton codes
@@ -83,11 +84,26 @@ void lbvh_tree_destroy(lbvh_tree_t tree);
  *   kind         lbvh_prim_kind.
  *   morton_bits  total code bits, a multiple of 3 in [3, 63] (30 and 63 are
  *                the usual choices: 10 or 21 bits per axis).
- * Asynchronous on `stream`; device storage grows (cudaMallocAsync) only when n
- * exceeds what the tree already holds. Errors found on the device are latched
+ * Asynchronous on `stream`; device storage grows (from the library's
+ * stream-ordered pool) only when n exceeds what the tree already holds. Errors found on the device are latched
  * (see lbvh_tree_status). Returns LBVH_ERR_INVALID for bad arguments. */
 lbvh_status lbvh_build(lbvh_tree_t tree, const float *d_prims, int64_t n, int kind,
                        int morton_bits, lbvh_stream_t stream);
+
+/* Refit: new boxes for moved primitives on the tree's existing topology.
+ * Every leaf box is re-read from d_prims (leaf k holds primitive perm[k] as
+ * before) and the bottom-up pass of Algorithm 4 runs again over the stored
+ * sorted codes, so every node keeps its children and skip connection and gets
+ * the union of its new child boxes; the scene bounds are recomputed (they
+ * only steer the query order). Codes are not recomputed: queries stay exact
+ * however far the primitives move, but the tree's quality decays with the
+ * motion, and a rebuild restores it.
+ *   d_prims  device float[n][3] or float[n][6], the same n, kind and index
+ *            order as the tree's last build.
+ * Asynchronous on `stream`. Returns LBVH_ERR_INVALID for a tree without a
+ * build or without stored codes (trees kept by the request server); device
+ * errors (non-finite input) are latched as in lbvh_build. */
+lbvh_status lbvh_refit(lbvh_tree_t tree, const float *d_prims, lbvh_stream_t stream);
 
 /* Build from codes that are already sorted (Sec. 3.1 steps 3-4 and Sec. 4
  * only): d_sorted_codes uint64[n] ascending, d_perm uint32[n] the primitive

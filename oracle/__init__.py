@@ -185,6 +185,35 @@ def build(prims, kind=POINTS, bits=30):
     return t
 
 
+def refit(tree, prims):
+    """Refit (box update on a fixed topology): a copy of `tree` whose leaf and
+    internal boxes and scene bounds come from `prims` (the same n and kind, the
+    same index order), with codes, permutation, children and skips unchanged.
+    The boxes are Karras step 4 over the kept topology, by the same post-order
+    routine as a build."""
+    p = _prims(prims, tree["kind"])
+    n = tree["n"]
+    if p.shape[0] != n:
+        raise OracleError(INVALID)
+    t = dict(tree)
+    t["leaf_box"] = np.zeros((n, 6), np.float32)
+    t["internal_box"] = np.zeros((max(n - 1, 0), 6), np.float32)
+    t["bounds"] = np.zeros(6, np.float32)
+    lib = _load()
+    st = OK
+    if n > 0:
+        c = np.zeros((n, 3), np.float32)
+        st = lib.oracle_centroids(_ptr(p), n, tree["kind"], _ptr(c))
+        if st == OK:
+            st = lib.oracle_scene_bounds(_ptr(c), n, _ptr(t["bounds"]))
+    if st == OK:
+        st = lib.oracle_boxes(_ptr(p), n, tree["kind"], _ptr(tree["perm"]), _ptr(tree["left"]),
+                              _ptr(tree["right"]), _ptr(t["leaf_box"]), _ptr(t["internal_box"]))
+    if st != OK:
+        raise OracleError(st)
+    return t
+
+
 def _queries(queries, qkind):
     q = np.ascontiguousarray(queries, dtype=np.float32)
     return q.reshape(-1, 3 if qkind == SPHERE else 6)

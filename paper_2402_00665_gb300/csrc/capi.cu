@@ -797,6 +797,36 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
     return finish_build(t, s);
 }
 
+lbvh_status lbvh_refit(lbvh_tree_t t, const float *d_prims, lbvh_stream_t stream) {
+    using namespace lbvh;
+    if (!t || !t->has_build || t->lean) return LBVH_ERR_INVALID;
+    const int64_t n = t->n;
+    if (n > 0 && !d_prims) return LBVH_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LBVH_CUDA(cudaStreamWaitEvent(s, t->built, 0));
+    if (t->queried) LBVH_CUDA(cudaStreamWaitEvent(s, t->used, 0));
+    t->prims_ptr = d_prims;
+    Control *c = t->dctl();
+    LBVH_CUDA(cudaMemsetAsync(&c->build_flags, 0, sizeof(uint32_t), s));
+    if (t->store_dirty && t->store.bytes) {
+        LBVH_CUDA(cudaMemsetAsync(t->store.p, 0, t->store.bytes, s));
+        t->store_dirty = false;
+    }
+    t->prof.clear(0, LBVH_STAGE_QCOUNT);
+    if (n > 0) {
+        t->prof.begin(LBVH_STAGE_BOUNDS, s);
+        launch_bounds(d_prims, n, t->kind, t->partials.as<float>(), t->bounds.as<float>(), c, s);
+        t->prof.end(LBVH_STAGE_BOUNDS, s);
+        LBVH_LAUNCHED();
+        t->prof.begin(LBVH_STAGE_CONSTRUCT, s);
+        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, t->kind, t->inodes(), t->leaves(),
+                         t->store.as<unsigned long long>(), &c->build_flags, s);
+        t->prof.end(LBVH_STAGE_CONSTRUCT, s);
+        LBVH_LAUNCHED();
+    }
+    return finish_build(t, s);
+}
+
 lbvh_status lbvh_tree_status(lbvh_tree_t t) {
     if (!t || !t->has_build) return LBVH_ERR_INVALID;
     lbvh_status st = read_control(t, t->stream);

@@ -58,6 +58,7 @@ SIGNATURES = {
     "lbvh_server_stats": (_I32, [_P, _P, _P, _P, _P]),
     "lbvh_server_phase_seconds": (_I32, [_P, _P]),
     "lbvh_release_cached_memory": (_I32, []),
+    "lbvh_refit": (_I32, [_P, _P, _P]),
     "lbvh_server_destroy": (None, [_P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
@@ -169,6 +170,14 @@ class Tree:
                "lbvh_build")
         self._keep = p  # the kernels read it asynchronously
         self.kind = kind
+        return self
+
+    def refit(self, prims, stream=None) -> "Tree":
+        """lbvh_refit: new boxes from moved primitives, same topology."""
+        torch = _torch()
+        p = _dev(prims, torch.float32, 3 if self.kind == POINTS else 6)
+        _check(self._lib.lbvh_refit(self._h, _ptr(p), _stream(stream)), "lbvh_refit")
+        self._keep = p
         return self
 
     def build_from_sorted(self, sorted_codes, perm, prims, kind: int = POINTS, stream=None) -> "Tree":

@@ -444,3 +444,49 @@ def test_nan_queries_hit_nothing_and_signed_zero_bounds():
         p = np.array([[v, 1.0, 2.0] for v in order], np.float32)
         _, b = oracle.morton_codes(p, oracle.POINTS, 30)
         assert np.signbit(b[0]) and not np.signbit(b[3])
+
+
+# ---------------------------------------------------------------- refit
+
+
+@pytest.mark.parametrize("kind", [oracle.POINTS, oracle.BOXES])
+def test_refit_keeps_topology_and_boxes_are_leaf_range_unions(kind):
+    rng = np.random.default_rng(41)
+    n = 700
+    if kind == oracle.POINTS:
+        a = inputs.uniform_points(n, seed=41)
+        b = (a + rng.normal(0, 0.05, size=a.shape)).astype(np.float32)
+    else:
+        a = inputs.gaussian_mixture_boxes(n, seed=41, components=6)
+        b = (a + np.repeat(rng.normal(0, 0.02, size=(n, 3)), 2, axis=0).reshape(n, 6)).astype(np.float32)
+    t = oracle.build(a, kind, 30)
+    r = oracle.refit(t, b)
+    for k in ("perm", "sorted", "left", "right", "skip_internal", "skip_leaf", "range_l", "range_r"):
+        assert np.array_equal(r[k], t[k]), k
+    # leaf k holds primitive perm[k] of the new coordinates
+    lb = b[t["perm"]] if kind == oracle.BOXES else np.concatenate([b[t["perm"]], b[t["perm"]]], axis=1)
+    assert np.array_equal(r["leaf_box"].view(np.uint32), lb.view(np.uint32))
+    # every internal box is the min/max over its leaf range (brute force)
+    tc.check_boxes(n, t["range_l"], t["range_r"], r["leaf_box"], r["internal_box"])
+    # the scene bounds are the new centroids' min/max
+    c = b if kind == oracle.POINTS else (b[:, :3] + b[:, 3:]) * np.float32(0.5)
+    assert np.array_equal(r["bounds"], np.concatenate([c.min(axis=0), c.max(axis=0)]).astype(np.float32))
+    # refitting with the original coordinates gives the original tree back
+    r0 = oracle.refit(t, a)
+    for k in ("leaf_box", "internal_box", "bounds"):
+        assert np.array_equal(r0[k].view(np.uint32), t[k].view(np.uint32)), k
+    # a stale box is caught by the same check (the refit really changed boxes)
+    with pytest.raises(AssertionError):
+        tc.check_boxes(n, t["range_l"], t["range_r"], r["leaf_box"], t["internal_box"])
+
+
+def test_refit_tree_queries_equal_bruteforce_on_moved_points():
+    rng = np.random.default_rng(42)
+    a = inputs.uniform_points(1500, seed=42)
+    b = (a + rng.normal(0, 0.1, size=a.shape)).astype(np.float32)  # far moves: a poor but valid tree
+    r = oracle.refit(oracle.build(a, oracle.POINTS, 63), b)
+    q = inputs.uniform_points(300, seed=43)
+    rad = np.float32(0.07)
+    off, hits = oracle.query(r, q, oracle.SPHERE, radius=rad)
+    boff, bhits = oracle.bruteforce(b, oracle.POINTS, q, oracle.SPHERE, radius=rad)
+    assert np.array_equal(off, boff) and np.array_equal(hits, bhits)
