@@ -110,6 +110,11 @@ WORKLOADS = {
                                  "[0,1)^3) to moved points: every step gives the tree new coordinates (the points "
                                  "plus N(0, 0.001) jitter, two alternating sets) and recomputes all boxes on the "
                                  "kept topology", 1 << 25, 63, "refit"),
+    "construction_rates": ("construction rate vs n of the three hierarchy algorithms the paper compares "
+                           "(Algorithm 4, Karras, Algorithm 3 + a skip pass) on its two synthetic clouds: filled "
+                           "cube (uniform in [-a,a]^3) and hollow cube (uniform on the six faces in turn), "
+                           "a = n^(1/3), 63-bit codes, n = 2^12 .. 2^25; median device time of 10 builds each",
+                           1 << 25, 63, "curves"),
     "mixture_boxes_2^25_63bit": ("2^25 FP32 boxes, centres from a 64-component Gaussian mixture (sigma 0.005, "
                                  "component centres uniform in [0,1)^3), half-extents lognormal(ln 1e-4, 0.5); "
                                  "63-bit codes; build + 2^24 box-overlap queries from the same mixture",
@@ -314,7 +319,19 @@ def run_reference(args, world, rank):
     family = workload_family(args.workload) if args.workload in WORKLOADS else "uniform"
     metric = METRIC
     samples = []
-    if family == "refit":
+    if family == "curves":
+        import oracle
+        metric = "construction rate Mprims/s (Algorithm 4, filled cube, largest n)"
+        m = 1 << 19
+        pts = inputs.filled_cube(m, seed=args.seed)
+        for step in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            oracle.build(pts, oracle.POINTS, bits)
+            dt = time.perf_counter() - t0
+            if step >= args.warmup:
+                samples.append(m / dt)
+        sdesc = f"oracle build (C, 1 thread) of a {m}-point filled cube, per step"
+    elif family == "refit":
         import oracle
         metric = REFIT_METRIC
         m = 1 << 20
@@ -598,6 +615,73 @@ def run_refit(args, world, rank, local):
     tree.close()
 
 
+CURVE_SIZES = [1 << k for k in range(12, 26)]
+ALGORITHM_NAMES = {0: "modified_apetrei_alg4", 1: "karras", 2: "apetrei_alg3"}
+
+
+def run_curves(args, world, rank, local):
+    """Build rate vs n for the three algorithms on the filled and hollow cubes."""
+    import torch
+    from paper_2402_00665_gb300 import lbvh
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, _, bits = WORKLOADS[args.workload][:3]
+    stream = torch.cuda.current_stream(dev)
+    reps = max(args.steps, 1)
+    table: dict = {}
+    launches0 = lbvh.kernel_launches()
+    with ClockSampler(None) as clocks:
+        for geometry, gen in (("filled_cube", inputs.filled_cube), ("hollow_cube", inputs.hollow_cube)):
+            table[geometry] = {}
+            for n in CURVE_SIZES:
+                pts = torch.from_numpy(gen(n, seed=args.seed + rank)).to(dev)
+                row = {}
+                for alg, name in ALGORITHM_NAMES.items():
+                    tree = lbvh.Tree()
+                    tree.set_profiling(True)
+                    for _ in range(max(args.warmup, 1)):
+                        tree.build(pts, lbvh.POINTS, bits, algorithm=alg)
+                    tree.check()
+                    times, hier, second = [], [], []
+                    for _ in range(reps):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        tree.build(pts, lbvh.POINTS, bits, algorithm=alg)
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        times.append(e0.elapsed_time(e1))
+                        st = tree.stage_times()
+                        hier.append(st.get("construct", 0.0))
+                        second.append(st.get("build_second_pass", 0.0))
+                    tree.check()
+                    tree.close()
+                    ms = statistics.median(times)
+                    row[name] = {"build_ms": round(ms, 4), "mprims_s": round(n / (ms * 1e-3) / 1e6, 1),
+                                 "hierarchy_ms": round(statistics.median(hier), 4),
+                                 "second_pass_ms": round(statistics.median(second), 4)}
+                table[geometry][str(n)] = row
+                del pts
+    launches = lbvh.kernel_launches() - launches0
+    top = table["filled_cube"][str(CURVE_SIZES[-1])]
+    if rank == 0:
+        line = {
+            "metric": "construction rate Mprims/s (Algorithm 4, filled cube, largest n)",
+            "value": top[ALGORITHM_NAMES[0]]["mprims_s"], "unit": UNIT, "n_gpus": world, "steps": reps,
+            "warmup": max(args.warmup, 1), "ms_per_step": top[ALGORITHM_NAMES[0]]["build_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "morton_bits": bits,
+                       "sizes": CURVE_SIZES, "timing": "CUDA events around each whole build (bounds, codes, "
+                       "sort, hierarchy, second pass), median of the steps; hierarchy_ms / second_pass_ms "
+                       "from the library's stage events",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "rates": table, "gpu_launches": launches, "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_batch(args, world, rank, local):
     """Batched configuration: all clouds in one graph launch per step, and the
     same work as a loop of one lbvh_build + lbvh_query_into per cloud."""
@@ -863,6 +947,8 @@ def main():
     world, rank, local = dist_setup(True)
     if workload_family(args.workload) == "refit":
         run_refit(args, world, rank, local)
+    elif workload_family(args.workload) == "curves":
+        run_curves(args, world, rank, local)
     else:
         run_gpu(args, world, rank, local)
     if world > 1:

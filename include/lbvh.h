@@ -90,6 +90,29 @@ void lbvh_tree_destroy(lbvh_tree_t tree);
 lbvh_status lbvh_build(lbvh_tree_t tree, const float *d_prims, int64_t n, int kind,
                        int morton_bits, lbvh_stream_t stream);
 
+/* The hierarchy algorithms the paper compares (Sec. 3-5). */
+typedef enum {
+    LBVH_BUILD_MODIFIED_APETREI = 0, /* Algorithm 4: one bottom-up pass, Karras ordering, skips, boxes */
+    LBVH_BUILD_KARRAS = 1,           /* Karras (Sec. 3.1): a thread per internal node finds its range
+                                        and split by binary search; a bottom-up pass writes boxes */
+    LBVH_BUILD_APETREI = 2           /* Algorithm 3: bottom-up with compare-and-swap, nodes in
+                                        Apetrei's ordering (index = split); a second pass converts to
+                                        Karras' ordering and installs skips (Algorithm 2) */
+} lbvh_build_algorithm;
+
+/* lbvh_build with the hierarchy step of the chosen algorithm. Scene bounds,
+ * codes and the sort are the same; every algorithm ends in the same tree
+ * (Karras' ordering, left children, skips, boxes: the radix tree of the
+ * augmented keys is unique), so the result equals lbvh_build's bit for bit
+ * and is queried and exported the same way. For timing the three against
+ * each other: stage LBVH_STAGE_CONSTRUCT is the hierarchy kernel (Algorithm 4,
+ * Karras' per-node search, Algorithm 3) and LBVH_STAGE_SECOND the extra pass
+ * the other two need (Karras: boxes; Apetrei: ordering and skips). The Karras
+ * and Apetrei builds use scratch of 20 and 48 bytes per primitive. Returns
+ * LBVH_ERR_INVALID for an unknown algorithm, else as lbvh_build. */
+lbvh_status lbvh_build_variant(lbvh_tree_t tree, const float *d_prims, int64_t n, int kind,
+                               int morton_bits, int algorithm, lbvh_stream_t stream);
+
 /* Refit: new boxes for moved primitives on the tree's existing topology.
  * Every leaf box is re-read from d_prims (leaf k holds primitive perm[k] as
  * before) and the bottom-up pass of Algorithm 4 runs again over the stored
@@ -384,7 +407,8 @@ enum {
     LBVH_STAGE_QFILL = 13,     /* short lists copied to their CSR positions */
     LBVH_STAGE_QFIXUP = 14,    /* second walk + sort for lists longer than 32 */
     LBVH_STAGE_QORDER = 15,    /* Morton order of the query centres (encode + sort) */
-    LBVH_STAGE_COUNT = 16
+    LBVH_STAGE_SECOND = 16,    /* second pass of lbvh_build_variant's Karras / Apetrei builds */
+    LBVH_STAGE_COUNT = 17
 };
 
 /* Turn per-stage timing of this tree's builds and queries on or off (off by

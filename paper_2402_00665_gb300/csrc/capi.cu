@@ -163,6 +163,7 @@ struct lbvh_tree_s {
     DevBuf nodes, store, lookback, hist, partials, bounds, ctl;
     DevBuf counts, tile_sums, overflow, slots;
     DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
+    DevBuf vscratch;                       // scratch of the Karras / Apetrei builds
     const float *prims_ptr = nullptr;      // the last build's input (self-queries)
     lbvh::Control *h_ctl = nullptr;  // pinned mirror of the control block (from pinned_controls())
     Profiler prof;
@@ -348,7 +349,7 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     LBVH_CUDA(t->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
     Control *c = t->dctl();
     LBVH_CUDA(cudaMemsetAsync(&c->query_flags, 0, offsetof(Control, pad) - offsetof(Control, query_flags), s));
-    t->prof.clear(LBVH_STAGE_QCOUNT, LBVH_STAGE_COUNT);
+    t->prof.clear(LBVH_STAGE_QCOUNT, LBVH_STAGE_QORDER + 1);
     t->prof.begin(LBVH_STAGE_QORDER, s);
     lbvh_status ost = query_order(t, qa, s);
     if (ost != LBVH_OK) return ost;
@@ -707,7 +708,7 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
     for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
                       &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                       &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
-                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots})
+                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots, &t->vscratch})
         b->release(cudaStreamPerThread);
     pinned_controls().put(t->h_ctl);
     if (t->built) cudaEventDestroy(t->built);
@@ -716,15 +717,22 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
     delete t;
 }
 
-lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind, int morton_bits,
-                       lbvh_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind, int morton_bits,
+                       int algorithm, lbvh_stream_t stream) {
     using namespace lbvh;
     lbvh_status st = check_build_args(t, d_prims, n, kind);
     if (st != LBVH_OK) return st;
     if (!valid_bits(morton_bits)) return LBVH_ERR_INVALID;
+    if (algorithm < LBVH_BUILD_MODIFIED_APETREI || algorithm > LBVH_BUILD_APETREI) return LBVH_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     st = reserve_tree(t, n, kind, s);
     if (st != LBVH_OK) return st;
+    if (algorithm != LBVH_BUILD_MODIFIED_APETREI)
+        LBVH_CUDA(t->vscratch.ensure(variant_scratch_bytes(n, algorithm), s));
     t->n = n;
     t->kind = kind;
     t->bits = morton_bits;
@@ -736,6 +744,7 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
         t->store_dirty = false;
     }
     t->prof.clear(0, LBVH_STAGE_QCOUNT);
+    t->prof.clear(LBVH_STAGE_SECOND, LBVH_STAGE_SECOND + 1);
     if (n > 0) {
         const int passes = sort_passes(morton_bits);
         LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)passes * kRadix * 4, s));
@@ -756,12 +765,39 @@ lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
             for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_CONSTRUCT, s);
-        launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(),
-                         t->leaves(), t->store.as<unsigned long long>(), &c->build_flags, s);
+        if (algorithm == LBVH_BUILD_MODIFIED_APETREI)
+            launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(), t->leaves(),
+                             t->store.as<unsigned long long>(), &c->build_flags, s);
+        else
+            launch_variant_hierarchy(algorithm, t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(),
+                                     t->leaves(), t->vscratch.p, t->store.as<unsigned long long>(),
+                                     &c->build_flags, s);
         t->prof.end(LBVH_STAGE_CONSTRUCT, s);
         LBVH_LAUNCHED();
+        if (algorithm != LBVH_BUILD_MODIFIED_APETREI) {
+            t->prof.begin(LBVH_STAGE_SECOND, s);
+            launch_variant_second(algorithm, t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(),
+                                  t->leaves(), t->vscratch.p, t->store.as<unsigned long long>(),
+                                  &c->build_flags, s);
+            t->prof.end(LBVH_STAGE_SECOND, s);
+            LBVH_LAUNCHED();
+        }
     }
     return finish_build(t, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbvh_status lbvh_build(lbvh_tree_t t, const float *d_prims, int64_t n, int kind, int morton_bits,
+                       lbvh_stream_t stream) {
+    return build_impl(t, d_prims, n, kind, morton_bits, LBVH_BUILD_MODIFIED_APETREI, stream);
+}
+
+lbvh_status lbvh_build_variant(lbvh_tree_t t, const float *d_prims, int64_t n, int kind, int morton_bits,
+                               int algorithm, lbvh_stream_t stream) {
+    return build_impl(t, d_prims, n, kind, morton_bits, algorithm, stream);
 }
 
 lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes,
@@ -1283,7 +1319,7 @@ const char *lbvh_stage_name(int stage) {
     static const char *names[LBVH_STAGE_COUNT] = {
         "bounds", "encode", "sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3", "sort_pass4",
         "sort_pass5", "sort_pass6", "sort_pass7", "construct", "query_walk", "query_scan",
-        "query_copy", "query_overflow", "query_order"};
+        "query_copy", "query_overflow", "query_order", "build_second_pass"};
     return (stage >= 0 && stage < LBVH_STAGE_COUNT) ? names[stage] : "";
 }
 

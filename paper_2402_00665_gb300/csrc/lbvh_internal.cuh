@@ -149,6 +149,16 @@ void launch_encode(const float *prims, int64_t n, int kind, int bits, const floa
 // Algorithm 4 with boxes: writes inodes and leaves (layout above), and uses
 // `store` (n-1 words, all zero on entry; left all zero on exit).
 // flags: kFlagCorrupt is latched if the input is not a sorted permutation.
+// The Karras and Apetrei hierarchy builds (variants.cu): scratch bytes, the
+// hierarchy kernel, and the second pass (Karras: boxes; Apetrei: ordering and
+// skips). `store` is the tree's zeroed Algorithm 4 scratch (left zeroed).
+size_t variant_scratch_bytes(int64_t n, int algorithm);
+void launch_variant_hierarchy(int algorithm, const uint64_t *codes, const uint32_t *perm, const float *prims,
+                              int64_t n, int kind, float4 *inodes, float4 *leaves, void *scratch,
+                              unsigned long long *store, uint32_t *flags, cudaStream_t s);
+void launch_variant_second(int algorithm, const uint64_t *codes, const uint32_t *perm, const float *prims,
+                           int64_t n, int kind, float4 *inodes, float4 *leaves, void *scratch,
+                           unsigned long long *store, uint32_t *flags, cudaStream_t s);
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
                       int64_t n, int kind, float4 *inodes, float4 *leaves,
                       unsigned long long *store, uint32_t *flags, cudaStream_t s);

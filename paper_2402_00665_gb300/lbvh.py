@@ -24,7 +24,8 @@ SPHERE, BOX = 0, 1
 MAX_PRIMS = (1 << 30) - 1
 MAX_BATCH = 1 << 20
 SERVER_PHASES = 4
-STAGE_COUNT = 16
+BUILD_MODIFIED_APETREI, BUILD_KARRAS, BUILD_APETREI = 0, 1, 2
+STAGE_COUNT = 17
 
 STATUS = {0: "LBVH_OK", 1: "LBVH_ERR_INVALID", 2: "LBVH_ERR_NONFINITE", 3: "LBVH_ERR_OOM",
           4: "LBVH_ERR_CUDA", 5: "LBVH_ERR_TIMEOUT", 6: "LBVH_ERR_CORRUPT", 7: "LBVH_ERR_CAPACITY"}
@@ -59,6 +60,7 @@ SIGNATURES = {
     "lbvh_server_phase_seconds": (_I32, [_P, _P]),
     "lbvh_release_cached_memory": (_I32, []),
     "lbvh_refit": (_I32, [_P, _P, _P]),
+    "lbvh_build_variant": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P]),
     "lbvh_server_destroy": (None, [_P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
@@ -163,11 +165,17 @@ class Tree:
     def handle(self):
         return self._h
 
-    def build(self, prims, kind: int = POINTS, morton_bits: int = 30, stream=None) -> "Tree":
+    def build(self, prims, kind: int = POINTS, morton_bits: int = 30, stream=None,
+              algorithm: int | None = None) -> "Tree":
+        """lbvh_build, or lbvh_build_variant when `algorithm` is given."""
         torch = _torch()
         p = _dev(prims, torch.float32, 3 if kind == POINTS else 6)
-        _check(self._lib.lbvh_build(self._h, _ptr(p), p.shape[0], kind, morton_bits, _stream(stream)),
-               "lbvh_build")
+        if algorithm is None:
+            _check(self._lib.lbvh_build(self._h, _ptr(p), p.shape[0], kind, morton_bits, _stream(stream)),
+                   "lbvh_build")
+        else:
+            _check(self._lib.lbvh_build_variant(self._h, _ptr(p), p.shape[0], kind, morton_bits, algorithm,
+                                                _stream(stream)), "lbvh_build_variant")
         self._keep = p  # the kernels read it asynchronously
         self.kind = kind
         return self
