@@ -16,7 +16,10 @@ and at the top of ``lbvh_oracle.c``:
 * delta, topology - Sec. 3.1 and Sec. 3.2 (XOR, index-augmented keys)
 * skips - Sec. 2 and Fig. 1 (pre-order successor past the subtree)
 * boxes - Sec. 3.1 step 4
-* queries - Algorithm 1, plus all-pairs brute force
+* queries - Algorithm 1, plus all-pairs brute force; predicates: closed ball,
+  box overlap, and ray segment (slab test: Sec. 1 names both distance and
+  ray range searches)
+* refit - boxes (Sec. 3.1 step 4) recomputed on a kept topology
 """
 from __future__ import annotations
 
@@ -34,7 +37,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liblbvh_oracle.so")
 
 POINTS, BOXES = 0, 1
-SPHERE, BOX = 0, 1
+SPHERE, BOX, RAY = 0, 1, 2
 OK, INVALID, NONFINITE = 0, 1, 2
 
 _lock = threading.Lock()
@@ -79,6 +82,7 @@ def _load():
             "oracle_query_bruteforce": (i64, [P, i64, i32, P, i64, i32, P, f32, P, P, i64]),
             "oracle_sphere_box": (i32, [P, f32, P]),
             "oracle_box_box": (i32, [P, P]),
+            "oracle_ray_box": (i32, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -216,7 +220,7 @@ def refit(tree, prims):
 
 def _queries(queries, qkind):
     q = np.ascontiguousarray(queries, dtype=np.float32)
-    return q.reshape(-1, 3 if qkind == SPHERE else 6)
+    return q.reshape(-1, {SPHERE: 3, BOX: 6, RAY: 8}[qkind])
 
 
 def _radii(radii, nq):
@@ -267,6 +271,12 @@ def sphere_box(centre, radius, box6) -> bool:
     c = np.ascontiguousarray(centre, dtype=np.float32)
     b = np.ascontiguousarray(box6, dtype=np.float32)
     return bool(_load().oracle_sphere_box(_ptr(c), np.float32(radius), _ptr(b)))
+
+
+def ray_box(ray8, box6) -> bool:
+    r = np.ascontiguousarray(ray8, np.float32)
+    b = np.ascontiguousarray(box6, np.float32)
+    return bool(_load().oracle_ray_box(_ptr(r), _ptr(b)))
 
 
 def box_box(a6, b6) -> bool:

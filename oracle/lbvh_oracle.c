@@ -418,14 +418,49 @@ int oracle_box_box(const float *a, const float *b) {
     return 1;
 }
 
+/* A ray segment {origin.xyz, tmin, direction.xyz, tmax} against a closed box
+ * (the slab test; range search for rays is Sec. 1's second example). Per axis:
+ * inv = 1/d (IEEE division); when d == 0 or inv is infinite the ray is
+ * parallel to the slab and stays in it only if lo <= o <= hi; otherwise
+ * t1 = (lo - o) * inv and t2 = (hi - o) * inv, each operation rounded once.
+ * tnear = max(tmin, min(t1, t2)) and tfar = min(tmax, max(t1, t2)) over the
+ * axes; hit iff tnear <= tfar. A ray whose origin or direction is not finite,
+ * or whose tmin or tmax is NaN, hits nothing. Every step is monotone in the
+ * box, so a node's test passes whenever a box inside it passes. */
+static int ray_box(const float *ray, const float *box) {
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(ray[a]) || !isfinite(ray[4 + a])) return 0;
+    if (isnan(ray[3]) || isnan(ray[7])) return 0;
+    float tnear = ray[3], tfar = ray[7];
+    for (int a = 0; a < 3; ++a) {
+        const float o = ray[a], d = ray[4 + a];
+        const float inv = 1.0f / d;
+        if (d == 0.0f || isinf(inv)) {
+            if (!(box[a] <= o && o <= box[3 + a])) return 0;
+            continue;
+        }
+        const float t1 = (box[a] - o) * inv;
+        const float t2 = (box[3 + a] - o) * inv;
+        const float tlo = t1 < t2 ? t1 : t2, thi = t1 < t2 ? t2 : t1;
+        if (tlo > tnear) tnear = tlo;
+        if (thi < tfar) tfar = thi;
+    }
+    return tnear <= tfar;
+}
+
+int oracle_ray_box(const float *ray8, const float *box6) { return ray_box(ray8, box6); }
+
 static int cmp_u32(const void *pa, const void *pb) {
     uint32_t a = *(const uint32_t *)pa, b = *(const uint32_t *)pb;
     return a < b ? -1 : (a > b ? 1 : 0);
 }
 
 static int query_hits(int qkind, const float *q, float r2, const float *box) {
+    if (qkind == ORACLE_RAY) return ray_box(q, box);
     return qkind == ORACLE_SPHERE ? sphere_box_r2(q, r2, box) : oracle_box_box(q, box);
 }
+
+static int query_dim(int qkind) { return qkind == ORACLE_SPHERE ? 3 : (qkind == ORACLE_BOX ? 6 : 8); }
 
 int64_t oracle_query_traverse(int64_t n, const int32_t *left, const int32_t *skip_internal,
                               const int32_t *skip_leaf, const float *leaf_box,
@@ -433,9 +468,9 @@ int64_t oracle_query_traverse(int64_t n, const int32_t *left, const int32_t *ski
                               const float *queries, int64_t nq, int qkind,
                               const float *radii, float radius, int64_t *offsets,
                               uint32_t *hits, int64_t cap) {
-    if (n < 0 || nq < 0 || (qkind != ORACLE_SPHERE && qkind != ORACLE_BOX)) return -1;
+    if (n < 0 || nq < 0 || (qkind != ORACLE_SPHERE && qkind != ORACLE_BOX && qkind != ORACLE_RAY)) return -1;
     const int64_t ni = n - 1;
-    const int qdim = qkind == ORACLE_SPHERE ? 3 : 6;
+    const int qdim = query_dim(qkind);
     const int64_t max_steps = 2 * (2 * n - 1) + 1;
     int64_t total = 0;
     for (int64_t qi = 0; qi < nq; ++qi) {
@@ -473,9 +508,9 @@ int64_t oracle_query_traverse(int64_t n, const int32_t *left, const int32_t *ski
 int64_t oracle_query_bruteforce(const float *prims, int64_t n, int kind, const float *queries,
                                 int64_t nq, int qkind, const float *radii, float radius,
                                 int64_t *offsets, uint32_t *hits, int64_t cap) {
-    if (n < 0 || nq < 0 || (qkind != ORACLE_SPHERE && qkind != ORACLE_BOX)) return -1;
+    if (n < 0 || nq < 0 || (qkind != ORACLE_SPHERE && qkind != ORACLE_BOX && qkind != ORACLE_RAY)) return -1;
     if (kind != ORACLE_POINTS && kind != ORACLE_BOXES) return -1;
-    const int qdim = qkind == ORACLE_SPHERE ? 3 : 6;
+    const int qdim = query_dim(qkind);
     int64_t total = 0;
     for (int64_t qi = 0; qi < nq; ++qi) {
         const float *q = queries + qdim * qi;

@@ -39,7 +39,7 @@ extern "C" {
 
 enum { ORACLE_OK = 0, ORACLE_INVALID = 1, ORACLE_NONFINITE = 2 };
 enum { ORACLE_POINTS = 0, ORACLE_BOXES = 1 };
-enum { ORACLE_SPHERE = 0, ORACLE_BOX = 1 };
+enum { ORACLE_SPHERE = 0, ORACLE_BOX = 1, ORACLE_RAY = 2 };
 
 /* Centroid of each primitive. points: float[n][3]; boxes: float[n][6] as
  * (lo.x, lo.y, lo.z, hi.x, hi.y, hi.z). out: float[n][3]. */
@@ -122,6 +122,8 @@ int64_t oracle_query_bruteforce(const float *prims, int64_t n, int kind,
 /* The predicates themselves, exported for tests. */
 int oracle_sphere_box(const float *centre, float radius, const float *box6);
 int oracle_box_box(const float *a6, const float *b6);
+/* Ray segment {origin.xyz, tmin, direction.xyz, tmax} against a closed box (slab test). */
+int oracle_ray_box(const float *ray8, const float *box6);
 
 #ifdef __cplusplus
 }

@@ -490,3 +490,97 @@ def test_refit_tree_queries_equal_bruteforce_on_moved_points():
     off, hits = oracle.query(r, q, oracle.SPHERE, radius=rad)
     boff, bhits = oracle.bruteforce(b, oracle.POINTS, q, oracle.SPHERE, radius=rad)
     assert np.array_equal(off, boff) and np.array_equal(hits, bhits)
+
+
+# ---------------------------------------------------------------- ray queries
+
+
+def _ray(o, d, tmin=0.0, tmax=np.inf):
+    return np.array([o[0], o[1], o[2], tmin, d[0], d[1], d[2], tmax], np.float32)
+
+
+def _slab_exact(ray, box):
+    """The slab test in exact rational arithmetic (fractions): hit iff the
+    closed segment meets the closed box. Infinite tmax is handled as
+    unbounded."""
+    from fractions import Fraction as F
+    o = [F(float(v)) for v in ray[:3]]
+    d = [F(float(v)) for v in ray[4:7]]
+    tn = F(float(ray[3])) if np.isfinite(ray[3]) else None
+    tf = F(float(ray[7])) if np.isfinite(ray[7]) else None
+    for a in range(3):
+        lo, hi = F(float(box[a])), F(float(box[3 + a]))
+        if d[a] == 0:
+            if not (lo <= o[a] <= hi):
+                return False
+            continue
+        t1, t2 = (lo - o[a]) / d[a], (hi - o[a]) / d[a]
+        t1, t2 = min(t1, t2), max(t1, t2)
+        tn = t1 if tn is None or t1 > tn else tn
+        tf = t2 if tf is None or t2 < tf else tf
+    return tn is None or tf is None or tn <= tf
+
+
+def test_ray_box_special_cases():
+    box = np.array([0, 0, 0, 1, 1, 1], np.float32)
+    assert oracle.ray_box(_ray([-1, 0.5, 0.5], [1, 0, 0]), box)            # through the middle
+    assert not oracle.ray_box(_ray([-1, 0.5, 0.5], [-1, 0, 0]), box)       # pointing away
+    assert not oracle.ray_box(_ray([-1, 0.5, 0.5], [1, 0, 0], tmax=0.5), box)  # stops short
+    assert oracle.ray_box(_ray([-1, 0.5, 0.5], [1, 0, 0], tmax=1.0), box)      # reaches the face (closed)
+    assert oracle.ray_box(_ray([0.5, 0.5, 0.5], [0, 0, 1], tmax=0.0), box)     # starts inside
+    assert oracle.ray_box(_ray([-1, 1, 0.5], [1, 0, 0]), box)              # grazes an edge (closed)
+    assert not oracle.ray_box(_ray([-1, 1.0000001, 0.5], [1, 0, 0]), box)  # parallel, just outside
+    assert not oracle.ray_box(_ray([-1, 0.5, 0.5], [1, 0, 0], tmin=2.5), box)  # starts past it
+    assert not oracle.ray_box(_ray([np.nan, 0.5, 0.5], [1, 0, 0]), box)
+    assert not oracle.ray_box(_ray([-1, 0.5, 0.5], [1, 0, 0], tmax=np.nan), box)
+    assert not oracle.ray_box(_ray([-1, 0.5, 0.5], [np.inf, 0, 0]), box)
+    # a degenerate box (a point leaf) is hit by a ray through it
+    pt = np.array([0.25, 0.5, 0.75, 0.25, 0.5, 0.75], np.float32)
+    assert oracle.ray_box(_ray([0.25, 0.5, -3], [0, 0, 1]), pt)
+    assert not oracle.ray_box(_ray([0.25, 0.5000001, -3], [0, 0, 1]), pt)
+
+
+def test_ray_box_matches_exact_slab_test_away_from_the_boundary():
+    rng = np.random.default_rng(51)
+    agree = 0
+    for _ in range(3000):
+        lo = rng.random(3)
+        box = np.concatenate([lo, lo + rng.random(3) * 0.3]).astype(np.float32)
+        o = (rng.random(3) * 2 - 0.5).astype(np.float32)
+        d = rng.normal(size=3).astype(np.float32)
+        ray = _ray(o, d, 0.0, float(rng.choice([np.inf, 0.5, 2.0])))
+        want = _slab_exact(ray, box)
+        # skip rays within a relative 1e-5 of touching (rounding may decide those)
+        eps = 1e-5
+        grown = box.astype(np.float64) + np.array([-eps] * 3 + [eps] * 3)
+        shrunk = box.astype(np.float64) + np.array([eps] * 3 + [-eps] * 3)
+        if _slab_exact(ray, grown.astype(np.float32)) != _slab_exact(ray, shrunk.astype(np.float32)):
+            continue
+        assert oracle.ray_box(ray, box) == want
+        agree += 1
+    assert agree > 2500
+
+
+@pytest.mark.parametrize("kind", [oracle.POINTS, oracle.BOXES])
+def test_ray_traversal_equals_bruteforce(kind):
+    rng = np.random.default_rng(52)
+    n = 3000
+    if kind == oracle.BOXES:
+        prims = inputs.gaussian_mixture_boxes(n, seed=52, components=8, log_half_mu=math.log(0.01))
+    else:
+        prims = inputs.uniform_points(n, seed=52)
+    t = oracle.build(prims, kind, 30)
+    nr = 400
+    o = rng.random((nr, 3)).astype(np.float32)
+    d = rng.normal(size=(nr, 3)).astype(np.float32)
+    rays = np.concatenate([o, np.zeros((nr, 1)), d, np.full((nr, 1), 0.3)], axis=1).astype(np.float32)
+    if kind == oracle.POINTS:
+        # axis-parallel rays through existing points: exact hits on degenerate boxes
+        k = rng.integers(0, n, size=nr // 2)
+        rays[: nr // 2, :3] = prims[k]
+        rays[: nr // 2, 2] -= 0.1
+        rays[: nr // 2, 4:7] = [0, 0, 1]
+    off, hits = oracle.query(t, rays, oracle.RAY)
+    boff, bhits = oracle.bruteforce(prims, kind, rays, oracle.RAY)
+    assert np.array_equal(off, boff) and np.array_equal(hits, bhits)
+    assert len(hits) >= nr // 2
