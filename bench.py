@@ -55,10 +55,13 @@ UNIT = "Mprims/s"
 #               written, store word 8, sibling box 24 re-read
 #   query walk  query 12 read, count 4 written, 4 per hit kept, tree read once (48 B/leaf)
 #   query copy  count/start/offset read per query, 4 per hit read and 4 written
-def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_queries: bool = False):
+def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_queries: bool = False,
+              long_lists: tuple = (0, 0)):
     """Algorithmic bytes of one launch of a stage (the data the method must
-    move): pb = bytes of a primitive, lb = of a leaf record, qb = of a query."""
-    pb, lb, qb = (24, 32, 24 if box_queries else 12) if boxes else (12, 16, 24 if box_queries else 12)
+    move): pb = bytes of a primitive, lb = of a leaf record, qb = of a query;
+    long_lists = (queries with more hits than the walk keeps, their hits)."""
+    qb = 32 if box_queries == "ray" else (24 if box_queries else 12)
+    pb, lb = (24, 32) if boxes else (12, 16)
     table = {
         "bounds": pb * n,
         "encode": (pb + 8) * n,
@@ -71,7 +74,8 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
         "query_order": (qb + 8 + 4 * 24) * nq,
         "query_scan": 4 * nq + 8 * (nq + 1),
         "query_copy": 16 * nq + 8 * hits,
-        "query_overflow": 0,
+        # the second walk of the long lists: query + offsets, hits written, then sorted in place
+        "query_overflow": (qb + 16) * long_lists[0] + 12 * long_lists[1],
     }
     return table.get(stage)
 
@@ -115,6 +119,10 @@ WORKLOADS = {
                            "cube (uniform in [-a,a]^3) and hollow cube (uniform on the six faces in turn), "
                            "a = n^(1/3), 63-bit codes, n = 2^12 .. 2^25; median device time of 10 builds each",
                            1 << 25, 63, "curves"),
+    "rays_mixture_boxes_2^25_63bit": ("2^25 FP32 boxes from the 64-component Gaussian mixture of "
+                                      "mixture_boxes_2^25_63bit (63-bit codes); build + 2^22 ray-segment queries "
+                                      "(origins uniform in [0,1)^3, directions uniform on the sphere, t in "
+                                      "[0, 0.05]), walked in input order", 1 << 25, 63, "rays"),
     "mixture_boxes_2^25_63bit": ("2^25 FP32 boxes, centres from a 64-component Gaussian mixture (sigma 0.005, "
                                  "component centres uniform in [0,1)^3), half-extents lognormal(ln 1e-4, 0.5); "
                                  "63-bit codes; build + 2^24 box-overlap queries from the same mixture",
@@ -236,6 +244,9 @@ def workload_family(workload: str) -> str:
 def make_inputs(workload: str, seed: int):
     """(description, n, bits, prims, queries or None (= the prims), boxes?, box queries?, radius)."""
     desc, n, bits = WORKLOADS[workload][:3]
+    if workload_family(workload) == "rays":
+        prims = inputs.gaussian_mixture_boxes(n, seed=seed)
+        return desc, n, bits, prims, inputs.random_rays(n // 8, seed=seed + 1, tmax=0.05), True, "ray", 0.0
     if workload_family(workload) == "mixture_boxes":
         prims = inputs.gaussian_mixture_boxes(n, seed=seed)
         queries = inputs.gaussian_mixture_boxes(n // 2, seed=seed + 1, component_seed=seed)
@@ -283,7 +294,12 @@ def oracle_sample(seed: int, n_sample: int = 1 << 23, q_sample: int = 1 << 18, b
     queries for 16 neighbours at that size, or mixture boxes with box queries
     from the same mixture). Returns (prims/s, description)."""
     import oracle
-    if family == "mixture_boxes":
+    if family == "rays":
+        prims = inputs.gaussian_mixture_boxes(n_sample, seed=seed + 101)
+        q = inputs.random_rays(q_sample, seed=seed + 102, tmax=0.05)
+        kind, qkind, r, what = oracle.BOXES, oracle.RAY, 0.0, "Gaussian-mixture boxes"
+        qwhat = "ray-segment queries (t in [0, 0.05])"
+    elif family == "mixture_boxes":
         prims = inputs.gaussian_mixture_boxes(n_sample, seed=seed + 101)
         q = inputs.gaussian_mixture_boxes(q_sample, seed=seed + 102, component_seed=seed + 101)
         kind, qkind, r, what = oracle.BOXES, oracle.BOX, 0.0, "Gaussian-mixture boxes", 
@@ -377,7 +393,7 @@ def run_gpu(args, world, rank, local):
     desc, n, bits, prims_host, queries_host, boxes, box_queries, radius = make_inputs(args.workload,
                                                                                        args.seed + rank)
     kind = lbvh.BOXES if boxes else lbvh.POINTS
-    qkind = lbvh.BOX if box_queries else lbvh.SPHERE
+    qkind = lbvh.RAY if box_queries == "ray" else (lbvh.BOX if box_queries else lbvh.SPHERE)
     pts = torch.from_numpy(prims_host).to(dev)
     # queries in their own buffer (the points themselves for the uniform
     # workloads): the general query path (query centres Morton-encoded and
@@ -446,7 +462,10 @@ def run_gpu(args, world, rank, local):
     query_ms = sum(v for k, v in stage_ms.items() if k.startswith("query"))
     dominant = max(stage_ms, key=lambda k: stage_ms[k])
     peak, peak_kind = measured_hbm_gbs()
-    alg = {k: alg_bytes(k, n, nq, total_hits, boxes, box_queries) for k in stage_ms
+    lens = offsets[1:] - offsets[:-1]
+    long_mask = lens > 64  # the walk keeps 64 hits per query; longer lists walk again
+    long_lists = (int(long_mask.sum().item()), int(lens[long_mask].sum().item()))
+    alg = {k: alg_bytes(k, n, nq, total_hits, boxes, box_queries, long_lists) for k in stage_ms
            if alg_bytes(k, n, nq, total_hits) is not None}
     achieved = alg[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
     build_bytes = sum(v for k, v in alg.items() if not k.startswith("query"))
@@ -503,6 +522,7 @@ def run_gpu(args, world, rank, local):
                        "morton_bits": bits, "radius": float(radius), "mean_hits": total_hits / nq,
                        "l2": f"inputs larger than L2 (primitives {pts.numel() * 4 / 1e6:.0f} MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
+            "long_lists": {"queries": long_lists[0], "hits": long_lists[1]},
             "build_mprims_s": n / (build_ms * 1e-3) / 1e6,
             "query_mqueries_s": nq / (query_ms * 1e-3) / 1e6,
             "build_hbm_frac": build_bytes / (build_ms * 1e-3) / 1e9 / peak,

@@ -56,7 +56,7 @@ typedef enum {
 } lbvh_status;
 
 typedef enum { LBVH_PRIM_POINTS = 0, LBVH_PRIM_BOXES = 1 } lbvh_prim_kind;
-typedef enum { LBVH_Q_SPHERE = 0, LBVH_Q_BOX = 1 } lbvh_query_kind;
+typedef enum { LBVH_Q_SPHERE = 0, LBVH_Q_BOX = 1, LBVH_Q_RAY = 2 } lbvh_query_kind;
 
 /* Largest primitive count of one tree: the sort's look-back words carry a
  * 30-bit count and node ids are int32 over 2n-1 nodes. */
@@ -164,14 +164,24 @@ lbvh_status lbvh_tree_export(lbvh_tree_t tree, uint32_t *h_perm, uint64_t *h_sor
 /* ---------------------------------------------------------------- queries */
 
 /* Stackless range query (Algorithm 1) of every query against the tree, with
- * results in caller-owned CSR buffers.
- *   d_queries  sphere centres float[nq][3] or boxes float[nq][6].
+ * results in caller-owned CSR buffers. Sec. 1 gives the two kinds of range
+ * search: objects within a distance, and objects a ray meets.
+ *   d_queries  sphere centres float[nq][3], boxes float[nq][6], or ray
+ *              segments float[nq][8] = {origin.xyz, tmin, direction.xyz,
+ *              tmax} (16-byte aligned).
  *   qkind      lbvh_query_kind. Sphere: closed ball, hit iff the squared
  *              distance from the centre to the primitive's box is <= r*r,
  *              in FP32: d2 = ex*ex, then + ey*ey and + ez*ez each as one
  *              fused multiply-add (e = the centre's gap to the box on that
  *              axis); a NaN centre coordinate or radius hits nothing. Box:
- *              closed overlap on all three axes.
+ *              closed overlap on all three axes. Ray: the slab test, each
+ *              operation rounded once: per axis inv = 1/d; an axis with d == 0
+ *              (or an infinite inv) needs lo <= o <= hi; else t1 = (lo-o)*inv,
+ *              t2 = (hi-o)*inv, tnear = max(tmin, min(t1,t2)), tfar =
+ *              min(tmax, max(t1,t2)); hit iff tnear <= tfar. A ray with a
+ *              non-finite origin or direction, or a NaN tmin/tmax, hits
+ *              nothing. Rays are walked in the order given; spheres and boxes
+ *              in the Morton order of their centres.
  *   d_radii    float[nq] per-query radius, or NULL to use `radius` for all
  *              (`radius` must then be finite and >= 0).
  *   d_offsets  int64[nq+1]: hits of query q are d_hits[d_offsets[q] ..
@@ -238,7 +248,8 @@ lbvh_status lbvh_batch_create(lbvh_batch_t *out);
 /* Release the batch and its device memory (waits for its stream). Accepts NULL. */
 void lbvh_batch_destroy(lbvh_batch_t batch);
 
-/* Build `count` independent trees and answer each tree's own queries in one
+/* Build `count` independent trees and answer each tree's own queries (spheres
+ * or boxes; rays: LBVH_ERR_INVALID) in one
  * pass over all of them: the same method as lbvh_build + lbvh_query_into per
  * instance (Sec. 3.1 steps 1-4, Algorithm 4, Algorithm 1), with every step
  * run once for the whole batch (per-instance scene bounds; one segmented
@@ -287,8 +298,8 @@ lbvh_status lbvh_batch_sort_variant(lbvh_batch_t batch, int *variant);
 typedef struct lbvh_server_s *lbvh_server_t; /* opaque */
 
 /* One request. A build request (n > 0) builds a tree of its primitives and
- * answers its queries; a query-only request (n == 0) queries the resident
- * tree stored under `key`. Every pointer is device memory that the caller
+ * answers its queries (spheres or boxes); a query-only request (n == 0)
+ * queries the resident tree stored under `key` (spheres, boxes or rays). Every pointer is device memory that the caller
  * keeps valid (inputs) or reserved (outputs) until lbvh_server_wait returns
  * for the request. */
 typedef struct {

@@ -304,7 +304,8 @@ constexpr int kOrderBits = 30;              // Morton bits of the query order
 lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
     using namespace lbvh;
     qa.order = nullptr;
-    if (qa.nq < kOrderMinQueries || t->n == 0) return LBVH_OK;
+    // rays are walked in the caller's order (a camera's rays are coherent as given)
+    if (qa.nq < kOrderMinQueries || t->n == 0 || qa.qkind == LBVH_Q_RAY) return LBVH_OK;
     const bool same_points = qa.qkind == LBVH_Q_SPHERE && t->kind == LBVH_PRIM_POINTS;
     const bool same_boxes = qa.qkind == LBVH_Q_BOX && t->kind == LBVH_PRIM_BOXES;
     if (qa.queries == t->prims_ptr && qa.nq == t->n && (same_points || same_boxes)) {
@@ -396,8 +397,9 @@ lbvh_status query_fill(lbvh_tree_t t, const lbvh::QueryArgs &qa, const int64_t *
 lbvh_status check_query_args(lbvh_tree_t t, const float *q, int64_t nq, int qkind,
                              const float *radii, float radius) {
     if (!t || !t->has_build || nq < 0 || nq > LBVH_MAX_PRIMS) return LBVH_ERR_INVALID;
-    if (qkind != LBVH_Q_SPHERE && qkind != LBVH_Q_BOX) return LBVH_ERR_INVALID;
+    if (qkind != LBVH_Q_SPHERE && qkind != LBVH_Q_BOX && qkind != LBVH_Q_RAY) return LBVH_ERR_INVALID;
     if (nq > 0 && !q) return LBVH_ERR_INVALID;
+    if (qkind == LBVH_Q_RAY && (reinterpret_cast<uintptr_t>(q) & 15u)) return LBVH_ERR_INVALID;  // float4 loads
     if (qkind == LBVH_Q_SPHERE && !radii && !(std::isfinite(radius) && radius >= 0.0f))
         return LBVH_ERR_INVALID;
     return LBVH_OK;

@@ -17,6 +17,8 @@
 //           as c_a - clamp(c_a, lo_a, hi_a), which has the same magnitude
 //           because fl(x - y) = -fl(y - x).
 //   box     lo_q <= hi_b and lo_b <= hi_q on every axis.
+//   ray     the slab test of a segment {origin, tmin, direction, tmax}
+//           (see hits(const Ray &...)); rays are walked in input order.
 //
 // Threads take the queries in the order given by QueryArgs::order (the
 // queries sorted by the Morton code of their centre, so that a warp's walks
@@ -56,6 +58,13 @@ struct Sphere {
 struct Box {
     float3 lo, hi;
 };
+// A ray segment: origin, 1/direction per axis (IEEE division), which axes
+// are parallel (direction 0, or a reciprocal that overflows), and [tmin, tmax].
+struct Ray {
+    float3 o, inv;
+    float tmin, tmax;
+    uint32_t parallel;  // bit a: axis a
+};
 
 // |gap| between c and [lo, hi]: c - clamp(c, lo, hi) (sign irrelevant: squared)
 __device__ __forceinline__ float gap(float lo, float c, float hi) {
@@ -68,6 +77,27 @@ __device__ __forceinline__ bool hits(const Sphere &s, float3 lo, float3 hi) {
     const float ez = gap(lo.z, s.c.z, hi.z);
     const float d2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
     return d2 <= s.r2;
+}
+
+// Slab test, each operation rounded once: per axis t1 = (lo - o) * inv and
+// t2 = (hi - o) * inv; tnear = max(tmin, min(t1, t2)), tfar = min(tmax,
+// max(t1, t2)); a parallel axis instead requires lo <= o <= hi. Hit iff
+// tnear <= tfar. Monotone in the box, like the other predicates.
+__device__ __forceinline__ bool slab(float lo, float hi, float o, float inv, bool parallel, float &tn,
+                                     float &tf) {
+    if (parallel) return lo <= o && o <= hi;
+    const float t1 = __fmul_rn(__fsub_rn(lo, o), inv), t2 = __fmul_rn(__fsub_rn(hi, o), inv);
+    tn = fmaxf(tn, fminf(t1, t2));
+    tf = fminf(tf, fmaxf(t1, t2));
+    return true;
+}
+
+__device__ __forceinline__ bool hits(const Ray &r, float3 lo, float3 hi) {
+    float tn = r.tmin, tf = r.tmax;
+    if (!slab(lo.x, hi.x, r.o.x, r.inv.x, r.parallel & 1u, tn, tf)) return false;
+    if (!slab(lo.y, hi.y, r.o.y, r.inv.y, r.parallel & 2u, tn, tf)) return false;
+    if (!slab(lo.z, hi.z, r.o.z, r.inv.z, r.parallel & 4u, tn, tf)) return false;
+    return tn <= tf;
 }
 
 __device__ __forceinline__ bool hits(const Box &q, float3 lo, float3 hi) {
@@ -84,6 +114,36 @@ struct QueryOf<LBVH_Q_SPHERE> {
         const float *p = a.queries + 3 * q;
         const float r = a.radii ? __ldcs(a.radii + q) : a.radius;
         return Sphere{make_float3(__ldcs(p), __ldcs(p + 1), __ldcs(p + 2)), __fmul_rn(r, r)};
+    }
+};
+template <>
+struct QueryOf<LBVH_Q_RAY> {
+    using type = Ray;
+    static __device__ __forceinline__ float axis_inv(float d, uint32_t bit, uint32_t &parallel) {
+        const float inv = __fdiv_rn(1.0f, d);
+        if (d == 0.0f || isinf(inv)) parallel |= bit;
+        return inv;
+    }
+    static __device__ __forceinline__ Ray load(const QueryArgs &a, int64_t q) {
+        const float4 *p = reinterpret_cast<const float4 *>(a.queries) + 2 * q;
+        const float4 u = __ldcs(p), v = __ldcs(p + 1);
+        Ray r;
+        r.parallel = 0;
+        r.o = make_float3(u.x, u.y, u.z);
+        r.inv = make_float3(axis_inv(v.x, 1u, r.parallel), axis_inv(v.y, 2u, r.parallel),
+                            axis_inv(v.z, 4u, r.parallel));
+        r.tmin = u.w;
+        r.tmax = v.w;
+        const bool finite = isfinite(u.x) && isfinite(u.y) && isfinite(u.z) && isfinite(v.x) && isfinite(v.y) &&
+                            isfinite(v.z) && !isnan(u.w) && !isnan(v.w);
+        if (!finite) {  // hits nothing: an empty parameter interval on every axis
+            r.tmin = 1.0f;
+            r.tmax = 0.0f;
+            r.parallel = 0;
+            r.o = make_float3(0.0f, 0.0f, 0.0f);
+            r.inv = make_float3(1.0f, 1.0f, 1.0f);
+        }
+        return r;
     }
 };
 template <>
@@ -600,7 +660,12 @@ __global__ void __launch_bounds__(kThreads)
 
 template <typename F>
 void dispatch_kinds(int qkind, int pkind, F &&f) {
-    if (qkind == LBVH_Q_SPHERE) {
+    if (qkind == LBVH_Q_RAY) {
+        if (pkind == LBVH_PRIM_POINTS)
+            f(std::integral_constant<int, LBVH_Q_RAY>{}, std::integral_constant<int, LBVH_PRIM_POINTS>{});
+        else
+            f(std::integral_constant<int, LBVH_Q_RAY>{}, std::integral_constant<int, LBVH_PRIM_BOXES>{});
+    } else if (qkind == LBVH_Q_SPHERE) {
         if (pkind == LBVH_PRIM_POINTS)
             f(std::integral_constant<int, LBVH_Q_SPHERE>{}, std::integral_constant<int, LBVH_PRIM_POINTS>{});
         else

@@ -132,7 +132,7 @@ struct Slot {
 uint64_t estimate_bytes(const lbvh_request &r) {
     const uint64_t n = (uint64_t)r.n, nq = (uint64_t)r.nq;
     const uint64_t prim = r.kind == LBVH_PRIM_POINTS ? 12 : 24;
-    const uint64_t qsz = r.qkind == LBVH_Q_SPHERE ? 12 : 24;
+    const uint64_t qsz = r.qkind == LBVH_Q_SPHERE ? 12 : (r.qkind == LBVH_Q_BOX ? 24 : 32);
     const uint64_t build = n * (prim + 24 + 24 + 48 + 8 + 16);
     const uint64_t query = nq * (qsz + 4 + 8 + lbvh::kQueryBufferHits * 4 + 4 + 8 + 24 + 8) + r.capacity * 4;
     return build + query;
@@ -484,7 +484,8 @@ lbvh_status lbvh_server_submit(lbvh_server_t srv, const lbvh_request *req, uint6
     const lbvh_request &r = *req;
     if (r.n < 0 || r.n > LBVH_MAX_PRIMS || r.nq < 0 || r.nq > LBVH_MAX_PRIMS) return LBVH_ERR_INVALID;
     if (r.kind != LBVH_PRIM_POINTS && r.kind != LBVH_PRIM_BOXES) return LBVH_ERR_INVALID;
-    if (r.qkind != LBVH_Q_SPHERE && r.qkind != LBVH_Q_BOX) return LBVH_ERR_INVALID;
+    if (r.qkind != LBVH_Q_SPHERE && r.qkind != LBVH_Q_BOX && r.qkind != LBVH_Q_RAY) return LBVH_ERR_INVALID;
+    if (r.qkind == LBVH_Q_RAY && r.n > 0) return LBVH_ERR_INVALID;  // rays: query-only requests
     if (r.n > 0 && (!r.d_prims || r.morton_bits < 3 || r.morton_bits > 63 || r.morton_bits % 3)) return LBVH_ERR_INVALID;
     if (r.n == 0 && r.key == 0) return LBVH_ERR_INVALID;  // query-only needs a resident tree
     if (r.nq > 0 && !r.d_queries) return LBVH_ERR_INVALID;

@@ -14,6 +14,7 @@ Workloads (the paper's own experiments use synthetic clouds as well, Sec. 5):
   Morton code, which stresses the index tie-break.
 * ``gaussian_mixture_points`` - points from the same kind of mixture.
 * ``batched_clouds`` - many independent uniform clouds with log-uniform sizes.
+* ``random_rays`` - ray segments with uniform origins and directions.
 * ``poisson_requests`` - arrival times and sizes of a served request stream.
 * ``filled_cube`` / ``hollow_cube`` - the two point clouds of the paper's
   construction-rate experiment: uniform inside [-a, a]^3, and uniform on the
@@ -66,6 +67,20 @@ def gaussian_mixture_points(n: int, seed: int = 0, components: int = 64, sigma: 
     rng = np.random.default_rng([seed, 3])
     which = rng.integers(0, components, size=n)
     return (centres[which] + rng.normal(0.0, sigma, size=(n, 3))).astype(np.float32)
+
+
+def random_rays(count: int, seed: int = 0, tmax: float = np.inf) -> np.ndarray:
+    """float32[count, 8] ray segments {origin.xyz, tmin = 0, direction.xyz,
+    tmax}: origins uniform in [0, 1)^3, directions uniform on the unit sphere
+    (normalised Gaussian triples)."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros((count, 8), np.float32)
+    out[:, :3] = rng.random((count, 3))
+    d = rng.normal(size=(count, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    out[:, 4:7] = d
+    out[:, 7] = tmax
+    return out
 
 
 def cloud_sizes(count: int, lo: int, hi: int, seed: int = 1) -> np.ndarray:

@@ -20,11 +20,12 @@ import numpy as np
 from . import _build
 
 POINTS, BOXES = 0, 1
-SPHERE, BOX = 0, 1
+SPHERE, BOX, RAY = 0, 1, 2
 MAX_PRIMS = (1 << 30) - 1
 MAX_BATCH = 1 << 20
 SERVER_PHASES = 4
 BUILD_MODIFIED_APETREI, BUILD_KARRAS, BUILD_APETREI = 0, 1, 2
+_QDIM = {SPHERE: 3, BOX: 6, RAY: 8}
 STAGE_COUNT = 17
 
 STATUS = {0: "LBVH_OK", 1: "LBVH_ERR_INVALID", 2: "LBVH_ERR_NONFINITE", 3: "LBVH_ERR_OOM",
@@ -247,7 +248,7 @@ class Tree:
     def query_into(self, queries, qkind, offsets, hits, radius: float = 0.0, radii=None, stream=None):
         """lbvh_query_into with caller tensors; returns (status, total)."""
         torch = _torch()
-        q = _dev(queries, torch.float32, 3 if qkind == SPHERE else 6)
+        q = _dev(queries, torch.float32, _QDIM[qkind])
         r = None if radii is None else _dev(radii, torch.float32).reshape(-1)
         total = ctypes.c_uint64()
         cap = 0 if hits is None else hits.numel()
@@ -260,7 +261,7 @@ class Tree:
               stream=None):
         """Stackless range query (Algorithm 1): returns CSR (offsets int64[nq+1], hits int32 view of uint32)."""
         torch = _torch()
-        q = _dev(queries, torch.float32, 3 if qkind == SPHERE else 6)
+        q = _dev(queries, torch.float32, _QDIM[qkind])
         nq = q.shape[0]
         offsets = torch.empty(nq + 1, dtype=torch.int64, device="cuda")
         cap = int(capacity) if capacity is not None else max(16 * nq, 1)
@@ -403,7 +404,7 @@ class Server:
         if q is None:
             raise ValueError("a query-only request needs queries")
         n = 0 if p is None else p.numel() // (3 if kind == POINTS else 6)
-        nq = q.numel() // (3 if qkind == SPHERE else 6)
+        nq = q.numel() // _QDIM[qkind]
         r = None
         if radii is not None:
             r = radii if isinstance(radii, torch.Tensor) and radii.is_cuda else _dev(radii, torch.float32).reshape(-1)
