@@ -71,7 +71,7 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
         "construct": (8 + 4 + pb + lb + 32 + 8 + 24) * n,
         # query + count/position per query, each kept hit, the tree once
         "query_walk": (qb + 8) * nq + 4 * hits + (32 + lb) * n,
-        "query_order": (qb + 8 + 4 * 24) * nq,
+        "query_order": (qb + 8 + 3 * 24) * nq,  # 24-bit order codes: 3 sort passes
         "query_scan": 4 * nq + 8 * (nq + 1),
         "query_copy": 16 * nq + 8 * hits,
         # the second walk of the long lists: query + offsets, hits written, then sorted in place
@@ -479,8 +479,10 @@ def run_gpu(args, world, rank, local):
         host_hits = torch.empty(hits.numel(), dtype=torch.int32).pin_memory()
         dpts = torch.empty_like(pts)
         dq = torch.empty_like(qpts)
-
         def e2e_step():
+            # (copying the queries on a second stream during the build, and the
+            # offsets during the hit copy, measured slower: the host links are
+            # shared and the build's sort competes for HBM)
             dpts.copy_(host_pts, non_blocking=True)
             dq.copy_(host_q, non_blocking=True)
             tree.build(dpts, kind, bits)

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -294,7 +295,19 @@ lbvh_status read_control(lbvh_tree_t t, cudaStream_t s) {
 }
 
 constexpr int64_t kOrderMinQueries = 2048;  // below this, walk in input order
-constexpr int kOrderBits = 30;              // Morton bits of the query order
+// Morton bits of the query order: 24 (3 sort passes) walked as fast as 30 on
+// 2^25 uniform queries and saved a pass (measured sweep 15..30 bits); order
+// changes speed only. LBVH_QUERY_ORDER_BITS=<multiple of 3 in [3, 63]>
+// overrides it process-wide (tuning sweeps).
+int order_bits() {
+    static int bits = 0;
+    if (bits == 0) {
+        const char *env = getenv("LBVH_QUERY_ORDER_BITS");
+        const int want = env ? atoi(env) : 24;
+        bits = (want >= 3 && want <= 63 && want % 3 == 0) ? want : 24;
+    }
+    return bits;
+}
 
 // The order in which threads take the queries: the Morton order of the query
 // centres inside the tree's bounds (encode + radix sort, the build's own
@@ -313,7 +326,7 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
         return LBVH_OK;
     }
     const size_t unq = (size_t)qa.nq;
-    const int passes = sort_passes(kOrderBits);
+    const int passes = sort_passes(order_bits());
     for (int k = 0; k < 2; ++k) {
         LBVH_CUDA(t->qkeys[k].ensure(unq * 8, s));
         LBVH_CUDA(t->qvals[k].ensure(unq * 4, s));
@@ -321,7 +334,7 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
     LBVH_CUDA(t->qlookback.ensure((size_t)sort_tiles_max(qa.nq) * kRadix * 4 * 2, s));
     LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)passes * kRadix * 4, s));
     const int as_prims = qa.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
-    launch_encode(qa.queries, qa.nq, as_prims, kOrderBits, t->bounds.as<float>(),
+    launch_encode(qa.queries, qa.nq, as_prims, order_bits(), t->bounds.as<float>(),
                   t->qkeys[0].as<uint64_t>(), t->hist.as<uint32_t>(), 1, s);
     LBVH_LAUNCHED();
     SortScratch scratch{t->hist.as<uint32_t>(), t->qlookback.as<uint32_t>(), sort_tiles_max(qa.nq) * kRadix};
@@ -507,7 +520,7 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
     b->N = g.prim_off.back();
     b->NQ = g.query_off.back();
     b->passes = sort_passes(g.bits);
-    b->qpasses = sort_passes(30);
+    b->qpasses = sort_passes(order_bits());
     const bool same_points = g.qkind == LBVH_Q_SPHERE && g.kind == LBVH_PRIM_POINTS;
     const bool same_boxes = g.qkind == LBVH_Q_BOX && g.kind == LBVH_PRIM_BOXES;
     b->self_query = g.queries == g.prims && g.query_off == g.prim_off && (same_points || same_boxes);
@@ -619,7 +632,7 @@ lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {
     } else {
         LBVH_CUDA(cudaMemsetAsync(b->hist.p, 0, (size_t)b->qpasses * b->count * kRadix * 4, s));
         const int as_prims = g.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
-        launch_batch_encode(g.queries, as_prims, true, bt, 30, b->bounds.as<float>(), b->qkeys[0].as<uint64_t>(),
+        launch_batch_encode(g.queries, as_prims, true, bt, order_bits(), b->bounds.as<float>(), b->qkeys[0].as<uint64_t>(),
                             b->hist.as<uint32_t>(), s);
         SortScratch scratch{b->hist.as<uint32_t>(), b->qlookback.as<uint32_t>(), b->max_qtiles * kRadix};
         const SortSegments seg = b->segments(true, b->sort_variant);
