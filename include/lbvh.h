@@ -404,6 +404,16 @@ lbvh_status lbvh_construct_static(const uint64_t *d_sorted_codes, const uint32_t
                                   const float *d_prims, int64_t n, int kind, float *d_inodes,
                                   float *d_leaves, uint32_t *d_flags, lbvh_stream_t stream);
 
+/* ---------------------------------------------------------------- failure tests */
+
+/* Test hook for failure detection, off by default (-1). While set, tile
+ * `tile` of the first pass of every radix sort publishes nothing to the
+ * decoupled look-back, so the later tiles' waits on it run out (each wait is
+ * bounded to about one second): the build then reports LBVH_ERR_TIMEOUT, its
+ * output is invalid and nothing is written out of bounds; the next build
+ * after the hook is cleared is correct again. Nothing faults, traps or hangs. */
+lbvh_status lbvh_test_hold_sort_tile(int64_t tile);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Stage ids of lbvh_tree_stage_times (device time of one kernel launch, or of

@@ -996,6 +996,12 @@ void lbvh_free(void *d_ptr) {
     if (d_ptr) cudaFree(d_ptr);
 }
 
+lbvh_status lbvh_test_hold_sort_tile(int64_t tile) {
+    if (tile < -1) return LBVH_ERR_INVALID;
+    lbvh::sort_set_hold_tile(tile);
+    return LBVH_OK;
+}
+
 lbvh_status lbvh_release_cached_memory(void) {
     std::lock_guard<std::mutex> lock(lbvh::g_pool_mu);
     for (auto &kv : lbvh::g_pools) LBVH_CUDA(cudaMemPoolTrimTo(kv.second, 0));

@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(kThreads)
                      unsigned long long *store, uint32_t *flags) {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
+    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;  // the sort failed: leave store untouched
     construct_leaf<kKind, kAcqRel>(i, n, codes, perm, 0u, prims, inodes, leaves, store, flags);
 }
 
@@ -215,6 +216,7 @@ __global__ void __launch_bounds__(kThreads)
                            uint32_t *flags) {
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (g >= total) return;
+    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;  // the sort failed: leave store untouched
     const int b = instance_of(off, count, g);
     const int64_t o = off[b];
     const int n = (int)(off[b + 1] - o);

@@ -131,6 +131,9 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
                   int variant_idx = -1, const SortSegments *seg = nullptr);
 int sort_variant_count();
+// Test hook (lbvh_test_hold_sort_tile): tile `tile` of every sort's first pass
+// publishes nothing, so later tiles' bounded look-back waits run out; -1: off.
+void sort_set_hold_tile(int64_t tile);
 // Keys per tile of variant idx (-1: the default variant).
 int64_t sort_variant_tile_keys(int idx);
 int64_t sort_tile_keys_min();

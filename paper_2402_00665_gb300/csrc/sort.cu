@@ -20,6 +20,7 @@
 // Look-back words: bits 31:30 = state (0 none, 1 aggregate, 2 inclusive
 // prefix), bits 29:0 = count. Two regions alternate between passes; every
 // tile clears its word block in the other region for the next pass.
+#include <atomic>
 #include <cstdlib>
 
 #include "lbvh_internal.cuh"
@@ -33,7 +34,16 @@ constexpr uint32_t kStateAgg = 1u << 30;
 constexpr uint32_t kStatePrefix = 2u << 30;
 constexpr uint32_t kStateMask = 3u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
-constexpr uint32_t kSpinLimit = 1u << 22;
+// A look-back wait gives up after about one second (%globaltimer), or after
+// 2^26 polls whatever the clock says.
+constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr uint32_t kSpinLimit = 1u << 26;
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
     uint32_t v;
@@ -111,7 +121,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
                     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
                     int shift, const uint32_t *__restrict__ pass_hist, uint32_t *lookback,
                     uint32_t *lookback_next, uint32_t *ticket, int64_t tiles,
-                    uint32_t *flags, uint32_t *next_hist, SegArgs seg) {
+                    uint32_t *flags, uint32_t *next_hist, SegArgs seg, int64_t hold_tile) {
     using Smem = SortSmem<kItems>;
     constexpr int kTile = Smem::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -193,7 +203,8 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
         count += c;
     }
     uint32_t *my_word = lookback + tile * kRadix + d;
-    st_relaxed(my_word, (tile == first_tile ? kStatePrefix : kStateAgg) | count);
+    const bool publish = tile != hold_tile;  // a test hook: this tile's successors must time out
+    if (publish) st_relaxed(my_word, (tile == first_tile ? kStatePrefix : kStateAgg) | count);
 
     const uint32_t global_base = (uint32_t)seg_begin + block_exclusive_scan(pass_hist[d], sm.scan);
     const uint32_t start = block_exclusive_scan(count, sm.scan);
@@ -206,20 +217,24 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
         while (true) {
             const uint32_t *w = lookback + t * kRadix + d;
             uint32_t v = ld_relaxed(w);
-            uint32_t spins = 0;
-            while ((v & kStateMask) == 0) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(flags, kFlagTimeout);
-                    v = kStatePrefix;  // give up: results are flagged invalid
-                    break;
+            if ((v & kStateMask) == 0) {
+                const uint64_t t0 = global_ns();
+                uint32_t spins = 0;
+                while ((v & kStateMask) == 0) {
+                    ++spins;
+                    if (spins > kSpinLimit || ((spins & 1023u) == 0 && global_ns() - t0 > kWaitNs)) {
+                        atomicOr(flags, kFlagTimeout);
+                        v = kStatePrefix;  // give up: results are flagged invalid
+                        break;
+                    }
+                    v = ld_relaxed(w);
                 }
-                v = ld_relaxed(w);
             }
             exclusive += v & kCountMask;
             if ((v & kStateMask) == kStatePrefix || t == first_tile) break;
             --t;
         }
-        st_relaxed(my_word, kStatePrefix | (exclusive + count));
+        if (publish) st_relaxed(my_word, kStatePrefix | (exclusive + count));
     }
     lookback_next[tile * kRadix + d] = 0;  // the next pass's region
     sm.out_base[d] = (int32_t)(global_base + exclusive) - (int32_t)start;
@@ -260,7 +275,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
 
 using PassKernel = void (*)(const uint64_t *, const uint32_t *, uint64_t *, uint32_t *, int64_t, int,
                             const uint32_t *, uint32_t *, uint32_t *, uint32_t *, int64_t, uint32_t *,
-                            uint32_t *, SegArgs);
+                            uint32_t *, SegArgs, int64_t);
 
 struct Variant {
     int items, min_blocks;
@@ -350,6 +365,10 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
 
 int64_t sort_tile_keys() { return (int64_t)kSortThreads * variant().items; }
 
+std::atomic<int64_t> g_hold_tile{-1};
+
+void sort_set_hold_tile(int64_t tile) { g_hold_tile.store(tile, std::memory_order_relaxed); }
+
 int64_t sort_variant_tile_keys(int idx) { return (int64_t)kSortThreads * variant(idx).items; }
 
 int sort_variant_count() {
@@ -387,9 +406,10 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
         if (pass_events) cudaEventRecord(pass_events[p][0], s);
         PassKernel k = seg ? ((p == 0 && iota) ? v.seg_first : v.seg_rest) : ((p == 0 && iota) ? v.first : v.rest);
         uint32_t *next_hist = p + 1 < passes ? scratch.hist + (p + 1) * hist_stride : nullptr;
+        const int64_t hold = p == 0 ? g_hold_tile.load(std::memory_order_relaxed) : -1;
         k<<<(unsigned)tiles, kSortThreads, v.smem, s>>>(kin, vin, kout, vout, n, kRadixBits * p, hist, cur,
                                                          nxt, &ctl->sort_ticket[p], tiles, &ctl->build_flags,
-                                                         next_hist, sa);
+                                                         next_hist, sa, hold);
         if (pass_events) cudaEventRecord(pass_events[p][1], s);
         count_launches(1);
         uint64_t *tk = kin;

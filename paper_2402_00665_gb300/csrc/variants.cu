@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(kThreads)
     const int i = blockIdx.x * kThreads + threadIdx.x;
     const int ni = n - 1;
     if (i >= ni) return;
+    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;  // the sort failed
     const uint64_t ci = codes[i];
     const uint32_t dl = delta_to(codes, n, i, ci, i - 1);
     const uint32_t dr = delta_to(codes, n, i, ci, i + 1);
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(kThreads)
                         unsigned int *counters, uint32_t *flags) {
     const int k = blockIdx.x * kThreads + threadIdx.x;
     if (k >= n) return;
+    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;  // an earlier step failed: counters untouched
     const int ni = n - 1;
     const uint32_t p_id = perm[k];
     if (p_id >= (uint32_t)n) {
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(kThreads)
                    unsigned long long *store, uint32_t *flags) {
     const int i = blockIdx.x * kThreads + threadIdx.x;
     if (i >= n) return;
+    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;  // the sort failed: store untouched
     const int ni = n - 1;
     const uint32_t p_id = perm[i];
     if (p_id >= (uint32_t)n) {

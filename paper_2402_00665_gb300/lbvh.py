@@ -61,6 +61,7 @@ SIGNATURES = {
     "lbvh_server_phase_seconds": (_I32, [_P, _P]),
     "lbvh_release_cached_memory": (_I32, []),
     "lbvh_refit": (_I32, [_P, _P, _P]),
+    "lbvh_test_hold_sort_tile": (_I32, [_I64]),
     "lbvh_build_variant": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P]),
     "lbvh_server_destroy": (None, [_P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
