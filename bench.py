@@ -886,6 +886,7 @@ def run_served(args, world, rank, local):
     launches = lbvh.kernel_launches() - launches0
     stats = srv.stats()
     phases = {k: v - phases0[k] for k, v in srv.phase_seconds().items()}
+    server_latency = srv.latency()  # the server's own record (includes the warm-up replay)
     srv.close()
     served_p50, served_p99 = percentiles(lat)
 
@@ -931,7 +932,8 @@ def run_served(args, world, rank, local):
                        "batches": stats["batches"] - batches0, "slots": SERVER_SLOTS,
                        "max_batch": SERVER_MAX_BATCH, "resident_trees": stats["resident_trees"],
                        "resident_bytes": stats["resident_bytes"], "evictions": stats["evictions"],
-                       "worker_phase_s": phases},
+                       "worker_phase_s": phases,
+                       "server_reported_latency_all_requests": server_latency},
             "one_at_a_time": {"throughput_mprims_s": n / fifo_s / 1e6, "p50_ms": fifo_p50, "p99_ms": fifo_p99,
                               "wall_s": fifo_s},
             "speedup_vs_one_at_a_time": fifo_s / served_s,

@@ -113,6 +113,25 @@ typedef enum {
 lbvh_status lbvh_build_variant(lbvh_tree_t tree, const float *d_prims, int64_t n, int kind,
                                int morton_bits, int algorithm, lbvh_stream_t stream);
 
+/* Checkpoint: the whole tree as one flat host byte image, and back.
+ * Image (version 1, little-endian): "LBVHTREE" (8 bytes), uint32 version,
+ * kind, morton_bits, 0; uint64 n; float bounds[6] (scene bounds of the
+ * centroids), 8 bytes of padding; uint64 sorted codes[n]; uint32 perm[n];
+ * then the device node records as they are (internal node k: float4 {lo.xyz,
+ * left}, float4 {hi.xyz, skip}; leaves: float4 {x, y, z, word} for points or
+ * {lo.xyz, word}, {hi.xyz, 0} for boxes, as described at lbvh_build).
+ * lbvh_tree_save: with h_buf == NULL (or capacity too small: then
+ * LBVH_ERR_CAPACITY) only *bytes is set to the image size; otherwise the
+ * image is written to h_buf (host memory; synchronises the tree's stream).
+ * Trees kept by the request server hold no codes and return
+ * LBVH_ERR_INVALID. lbvh_tree_load: replaces the tree with the image (the
+ * copies run on `stream`, which is synchronised before the call returns); a
+ * bad magic, version, kind, bit count, size or n returns LBVH_ERR_INVALID
+ * before anything is copied. A loaded tree is
+ * queried, exported, refitted and saved like a built one. */
+lbvh_status lbvh_tree_save(lbvh_tree_t tree, void *h_buf, uint64_t capacity, uint64_t *bytes);
+lbvh_status lbvh_tree_load(lbvh_tree_t tree, const void *h_buf, uint64_t bytes, lbvh_stream_t stream);
+
 /* Refit: new boxes for moved primitives on the tree's existing topology.
  * Every leaf box is re-read from d_prims (leaf k holds primitive perm[k] as
  * before) and the bottom-up pass of Algorithm 4 runs again over the stored
@@ -351,6 +370,10 @@ lbvh_status lbvh_server_wait(lbvh_server_t server, uint64_t ticket, lbvh_result 
 /* Resident-tree bytes and count, evictions and batches so far (any pointer may be NULL). */
 lbvh_status lbvh_server_stats(lbvh_server_t server, uint64_t *resident_bytes, uint64_t *resident_trees,
                               uint64_t *evictions, uint64_t *batches);
+
+/* Latency (submission to results, seconds) of every request answered so far:
+ * nearest-rank p50 and p99 and the count (any pointer may be NULL). */
+lbvh_status lbvh_server_latency(lbvh_server_t server, double *p50_s, double *p99_s, uint64_t *count);
 
 /* Where the workers' time went, summed over all batches so far (host wall
  * clock, so with several slots the sums can exceed the elapsed time):

@@ -12,6 +12,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbvh_internal.cuh"
 
 namespace {
@@ -109,6 +111,14 @@ lbvh_status flags_status(uint32_t flags) {
     return LBVH_OK;
 }
 
+// Host-side scoped NVTX range (API calls and the sort).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Event pairs around each stage (see LBVH_STAGE_*), recorded only when on.
 struct Profiler {
     bool on = false;
@@ -130,10 +140,14 @@ struct Profiler {
     void clear(int lo, int hi) {
         for (int k = lo; k < hi; ++k) recorded[k] = false;
     }
+    // Each stage is also an NVTX range on the host thread (no-ops unless a
+    // profiler is attached), so tools see where launches come from.
     void begin(int st, cudaStream_t s) {
+        nvtxRangePushA(lbvh_stage_name(st));
         if (on) cudaEventRecord(ev[st][0], s);
     }
     void end(int st, cudaStream_t s) {
+        nvtxRangePop();
         if (!on) return;
         cudaEventRecord(ev[st][1], s);
         recorded[st] = true;
@@ -366,8 +380,8 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     t->prof.clear(LBVH_STAGE_QCOUNT, LBVH_STAGE_QORDER + 1);
     t->prof.begin(LBVH_STAGE_QORDER, s);
     lbvh_status ost = query_order(t, qa, s);
-    if (ost != LBVH_OK) return ost;
     t->prof.end(LBVH_STAGE_QORDER, s);
+    if (ost != LBVH_OK) return ost;
     const QueryScratch qs = query_scratch(t);
     t->prof.begin(LBVH_STAGE_QCOUNT, s);
     launch_query_collect(t->view(), qa, qs, c, s);
@@ -738,6 +752,7 @@ namespace {
 
 lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind, int morton_bits,
                        int algorithm, lbvh_stream_t stream) {
+    NvtxRange nvtx_range("lbvh_build");
     using namespace lbvh;
     lbvh_status st = check_build_args(t, d_prims, n, kind);
     if (st != LBVH_OK) return st;
@@ -773,9 +788,11 @@ lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
         t->prof.end(LBVH_STAGE_ENCODE, s);
         LBVH_LAUNCHED();
         SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles_max(n) * kRadix};
+        nvtxRangePushA("sort");
         t->sorted_in_b = run_onesweep(t->keys[0].as<uint64_t>(), t->vals[0].as<uint32_t>(), true,
                                       t->keys[1].as<uint64_t>(), t->vals[1].as<uint32_t>(), n, passes,
                                       scratch, c, s, t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr);
+        nvtxRangePop();
         if (t->prof.on)
             for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
         LBVH_LAUNCHED();
@@ -849,6 +866,7 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
 }
 
 lbvh_status lbvh_refit(lbvh_tree_t t, const float *d_prims, lbvh_stream_t stream) {
+    NvtxRange nvtx_range("lbvh_refit");
     using namespace lbvh;
     if (!t || !t->has_build || t->lean) return LBVH_ERR_INVALID;
     const int64_t n = t->n;
@@ -875,6 +893,96 @@ lbvh_status lbvh_refit(lbvh_tree_t t, const float *d_prims, lbvh_stream_t stream
         t->prof.end(LBVH_STAGE_CONSTRUCT, s);
         LBVH_LAUNCHED();
     }
+    return finish_build(t, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr char kImageMagic[8] = {'L', 'B', 'V', 'H', 'T', 'R', 'E', 'E'};
+constexpr uint32_t kImageVersion = 1;
+
+struct ImageHeader {
+    char magic[8];
+    uint32_t version, kind, bits, zero;
+    uint64_t n;
+    float bounds[6];
+    uint32_t pad[2];
+};
+static_assert(sizeof(ImageHeader) == 64, "image header layout");
+
+uint64_t image_node_bytes(int64_t n, int kind) {
+    if (n <= 0) return 0;
+    return (uint64_t)(2 * (n - 1)) * 16 + (uint64_t)lbvh::leaf_float4s(n, kind) * 16;
+}
+
+uint64_t image_bytes(int64_t n, int kind) {
+    return sizeof(ImageHeader) + (uint64_t)n * 12 + image_node_bytes(n, kind);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbvh_status lbvh_tree_save(lbvh_tree_t t, void *h_buf, uint64_t capacity, uint64_t *bytes) {
+    if (!t || !bytes || !t->has_build || t->lean) return LBVH_ERR_INVALID;
+    const int64_t n = t->n;
+    *bytes = image_bytes(n, t->kind);
+    if (!h_buf) return LBVH_OK;
+    if (capacity < *bytes) return LBVH_ERR_CAPACITY;
+    lbvh_status st = lbvh_tree_status(t);  // synchronises; a failed build is not saved
+    if (st != LBVH_OK) return st;
+    ImageHeader h{};
+    std::memcpy(h.magic, kImageMagic, 8);
+    h.version = kImageVersion;
+    h.kind = (uint32_t)t->kind;
+    h.bits = (uint32_t)t->bits;
+    h.n = (uint64_t)n;
+    LBVH_CUDA(cudaMemcpy(h.bounds, t->bounds.p, 24, cudaMemcpyDeviceToHost));
+    char *out = static_cast<char *>(h_buf);
+    std::memcpy(out, &h, sizeof h);
+    out += sizeof h;
+    if (n > 0) {
+        LBVH_CUDA(cudaMemcpy(out, t->sorted_codes(), (size_t)n * 8, cudaMemcpyDeviceToHost));
+        out += (size_t)n * 8;
+        LBVH_CUDA(cudaMemcpy(out, t->perm(), (size_t)n * 4, cudaMemcpyDeviceToHost));
+        out += (size_t)n * 4;
+        LBVH_CUDA(cudaMemcpy(out, t->nodes.p, image_node_bytes(n, t->kind), cudaMemcpyDeviceToHost));
+    }
+    return LBVH_OK;
+}
+
+lbvh_status lbvh_tree_load(lbvh_tree_t t, const void *h_buf, uint64_t bytes, lbvh_stream_t stream) {
+    if (!t || !h_buf || bytes < sizeof(ImageHeader)) return LBVH_ERR_INVALID;
+    ImageHeader h;
+    std::memcpy(&h, h_buf, sizeof h);
+    if (std::memcmp(h.magic, kImageMagic, 8) != 0 || h.version != kImageVersion) return LBVH_ERR_INVALID;
+    if (h.kind != LBVH_PRIM_POINTS && h.kind != LBVH_PRIM_BOXES) return LBVH_ERR_INVALID;
+    if (h.n > (uint64_t)LBVH_MAX_PRIMS || (h.bits != 0 && !valid_bits((int)h.bits))) return LBVH_ERR_INVALID;
+    const int64_t n = (int64_t)h.n;
+    const int kind = (int)h.kind;
+    if (bytes != image_bytes(n, kind)) return LBVH_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    lbvh_status st = reserve_tree(t, n, kind, s);
+    if (st != LBVH_OK) return st;
+    t->n = n;
+    t->kind = kind;
+    t->bits = (int)h.bits;
+    t->sorted_in_b = false;
+    t->prims_ptr = nullptr;
+    LBVH_CUDA(cudaMemsetAsync(&t->dctl()->build_flags, 0, sizeof(uint32_t), s));
+    LBVH_CUDA(cudaMemcpyAsync(t->bounds.p, h.bounds, 24, cudaMemcpyHostToDevice, s));
+    const char *in = static_cast<const char *>(h_buf) + sizeof h;
+    if (n > 0) {
+        LBVH_CUDA(cudaMemcpyAsync(t->keys[0].p, in, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+        in += (size_t)n * 8;
+        LBVH_CUDA(cudaMemcpyAsync(t->vals[0].p, in, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        in += (size_t)n * 4;
+        LBVH_CUDA(cudaMemcpyAsync(t->nodes.p, in, image_node_bytes(n, kind), cudaMemcpyHostToDevice, s));
+    }
+    // the bounds copy above reads a stack value: make sure it has been taken
+    LBVH_CUDA(cudaStreamSynchronize(s));
     return finish_build(t, s);
 }
 
@@ -951,6 +1059,7 @@ lbvh_status lbvh_tree_export(lbvh_tree_t t, uint32_t *h_perm, uint64_t *h_sorted
 lbvh_status lbvh_query_into(lbvh_tree_t t, const float *d_queries, int64_t nq, int qkind,
                             const float *d_radii, float radius, int64_t *d_offsets, uint32_t *d_hits,
                             uint64_t capacity, uint64_t *total, lbvh_stream_t stream) {
+    NvtxRange nvtx_range("lbvh_query_into");
     lbvh_status st = check_query_args(t, d_queries, nq, qkind, d_radii, radius);
     if (st != LBVH_OK) return st;
     if (!d_offsets || !total || (capacity > 0 && !d_hits)) return LBVH_ERR_INVALID;
@@ -965,6 +1074,7 @@ lbvh_status lbvh_query_into(lbvh_tree_t t, const float *d_queries, int64_t nq, i
 lbvh_status lbvh_query(lbvh_tree_t t, const float *d_queries, int64_t nq, int qkind,
                        const float *d_radii, float radius, int64_t **d_offsets, uint32_t **d_hits,
                        uint64_t *total, lbvh_stream_t stream) {
+    NvtxRange nvtx_range("lbvh_query");
     lbvh_status st = check_query_args(t, d_queries, nq, qkind, d_radii, radius);
     if (st != LBVH_OK) return st;
     if (!d_offsets || !d_hits || !total) return LBVH_ERR_INVALID;
@@ -1114,6 +1224,7 @@ lbvh_status lbvh_batch_build_query(lbvh_batch_t b, const float *d_prims, const i
                                    const int64_t *h_query_offsets, int qkind, const float *d_radii,
                                    float radius, int64_t *d_offsets, uint32_t *d_hits, uint64_t capacity,
                                    uint64_t *total, lbvh_stream_t stream) {
+    NvtxRange nvtx_range("lbvh_batch_build_query");
     using namespace lbvh;
     if (!b || count < 1 || count > LBVH_MAX_BATCH || !h_prim_offsets || !h_query_offsets || !d_offsets || !total)
         return LBVH_ERR_INVALID;

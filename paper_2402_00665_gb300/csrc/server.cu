@@ -11,6 +11,7 @@
 // kernels (lbvh_batch_build_query, lbvh_query_into); this file moves request
 // data in and out of batches (copy, rebase of offsets) and keeps the books.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -21,6 +22,8 @@
 #include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "lbvh_internal.cuh"
 
@@ -165,6 +168,7 @@ struct lbvh_server_s {
     uint64_t resident_total = 0, inflight = 0, next_ticket = 1;
     uint64_t evictions = 0, batches = 0, requests_done = 0, jobs_finished = 0;
     double phase_s[LBVH_SERVER_PHASES] = {};  // see lbvh_server_phase_seconds
+    std::vector<double> latencies;            // of every answered request, seconds
     bool stop = false;
     Clock::time_point t0 = Clock::now();
     std::vector<std::unique_ptr<Slot>> slots;
@@ -181,6 +185,7 @@ struct lbvh_server_s {
         o.result.service_s = seconds_since(start, now);
         o.result.latency_s = seconds_since(r.submitted, now);
         o.result.batch_size = batch_size;
+        latencies.push_back(o.result.latency_s);
         ++requests_done;
     }
 
@@ -306,6 +311,10 @@ void lbvh_server_s::worker_loop(Slot *slot) {
 }
 
 void lbvh_server_s::run_query_job(Slot *slot, Job &job) {
+    nvtxRangePushA("lbvh_server query");
+    struct PopAtExit {
+        ~PopAtExit() { nvtxRangePop(); }
+    } pop_at_exit;
     Request &r = job.reqs[0];
     const Clock::time_point start = Clock::now();
     lbvh_tree_t tree;
@@ -327,6 +336,10 @@ void lbvh_server_s::run_query_job(Slot *slot, Job &job) {
 }
 
 void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
+    nvtxRangePushA("lbvh_server batch");
+    struct PopAtExit {
+        ~PopAtExit() { nvtxRangePop(); }
+    } pop_at_exit;
     const Clock::time_point start = Clock::now();
     const int count = (int)job.reqs.size();
     const lbvh_request &k0 = job.reqs[0].req;
@@ -523,6 +536,27 @@ lbvh_status lbvh_server_stats(lbvh_server_t srv, uint64_t *resident_bytes, uint6
     if (resident_trees) *resident_trees = srv->resident.size();
     if (evictions) *evictions = srv->evictions;
     if (batches) *batches = srv->batches;
+    return LBVH_OK;
+}
+
+lbvh_status lbvh_server_latency(lbvh_server_t srv, double *p50_s, double *p99_s, uint64_t *count) {
+    if (!srv) return LBVH_ERR_INVALID;
+    std::vector<double> v;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        v = srv->latencies;
+    }
+    if (count) *count = v.size();
+    // nearest-rank percentiles
+    auto pct = [&](double p) {
+        if (v.empty()) return 0.0;
+        size_t k = (size_t)std::ceil(p / 100.0 * (double)v.size());
+        k = k == 0 ? 0 : k - 1;
+        std::nth_element(v.begin(), v.begin() + k, v.end());
+        return v[k];
+    };
+    if (p50_s) *p50_s = pct(50.0);
+    if (p99_s) *p99_s = pct(99.0);
     return LBVH_OK;
 }
 

@@ -59,9 +59,12 @@ SIGNATURES = {
     "lbvh_server_wait": (_I32, [_P, _U64, _P]),
     "lbvh_server_stats": (_I32, [_P, _P, _P, _P, _P]),
     "lbvh_server_phase_seconds": (_I32, [_P, _P]),
+    "lbvh_server_latency": (_I32, [_P, _P, _P, _P]),
     "lbvh_release_cached_memory": (_I32, []),
     "lbvh_refit": (_I32, [_P, _P, _P]),
     "lbvh_test_hold_sort_tile": (_I32, [_I64]),
+    "lbvh_tree_save": (_I32, [_P, _P, _U64, _P]),
+    "lbvh_tree_load": (_I32, [_P, _P, _U64, _P]),
     "lbvh_build_variant": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P]),
     "lbvh_server_destroy": (None, [_P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
@@ -180,6 +183,20 @@ class Tree:
                                                 _stream(stream)), "lbvh_build_variant")
         self._keep = p  # the kernels read it asynchronously
         self.kind = kind
+        return self
+
+    def save(self) -> bytes:
+        """lbvh_tree_save: the tree as one flat byte image."""
+        size = ctypes.c_uint64()
+        _check(self._lib.lbvh_tree_save(self._h, None, 0, ctypes.byref(size)), "lbvh_tree_save")
+        buf = ctypes.create_string_buffer(size.value)
+        _check(self._lib.lbvh_tree_save(self._h, buf, size.value, ctypes.byref(size)), "lbvh_tree_save")
+        return buf.raw
+
+    def load(self, image: bytes, stream=None) -> "Tree":
+        """lbvh_tree_load: replace this tree with a saved image."""
+        _check(self._lib.lbvh_tree_load(self._h, image, len(image), _stream(stream)), "lbvh_tree_load")
+        self.kind = int.from_bytes(image[12:16], "little")
         return self
 
     def refit(self, prims, stream=None) -> "Tree":
@@ -433,6 +450,13 @@ class Server:
         v = [ctypes.c_uint64() for _ in range(4)]
         _check(self._lib.lbvh_server_stats(self._h, *[ctypes.byref(x) for x in v]), "lbvh_server_stats")
         return dict(zip(("resident_bytes", "resident_trees", "evictions", "batches"), (x.value for x in v)))
+
+    def latency(self) -> dict:
+        """lbvh_server_latency: p50 / p99 (seconds) and count of answered requests."""
+        p50, p99, cnt = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+        _check(self._lib.lbvh_server_latency(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(cnt)),
+               "lbvh_server_latency")
+        return {"p50_s": p50.value, "p99_s": p99.value, "count": cnt.value}
 
     def phase_seconds(self) -> dict:
         """lbvh_server_phase_seconds: worker time per phase, summed over batches."""

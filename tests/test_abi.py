@@ -78,6 +78,17 @@ def test_invalid_arguments_rejected_before_any_device_work(lib_path):
         assert lib.lbvh_query_into(h, dummy, 1, 0, None, 1.0, off, None, 0, ctypes.byref(total),
                                    None) == lbvh.ERR_INVALID
         assert lib.lbvh_tree_status(h) == lbvh.ERR_INVALID
+        # checkpoint images are validated before any device work
+        size = ctypes.c_uint64()
+        assert lib.lbvh_tree_save(h, None, 0, ctypes.byref(size)) == lbvh.ERR_INVALID  # never built
+        good_header = b"LBVHTREE" + (1).to_bytes(4, "little") + bytes(52)  # n = 0, points
+        assert lib.lbvh_tree_load(h, b"NOTATREE" + bytes(56), 64, None) == lbvh.ERR_INVALID
+        assert lib.lbvh_tree_load(h, b"LBVHTREE" + (2).to_bytes(4, "little") + bytes(52), 64,
+                                  None) == lbvh.ERR_INVALID  # version
+        assert lib.lbvh_tree_load(h, good_header, 63, None) == lbvh.ERR_INVALID  # truncated
+        assert lib.lbvh_tree_load(h, good_header + bytes(8), 72, None) == lbvh.ERR_INVALID  # size vs n
+        bad_kind = b"LBVHTREE" + (1).to_bytes(4, "little") + (5).to_bytes(4, "little") + bytes(48)
+        assert lib.lbvh_tree_load(h, bad_kind, 64, None) == lbvh.ERR_INVALID
     finally:
         lib.lbvh_tree_destroy(h)
 

@@ -97,6 +97,8 @@ def test_wide_codes_share_batches():
         sizes.append(info["batch_size"])
         assert np.array_equal(off.cpu().numpy(), ooff) and np.array_equal(hits.cpu().numpy(), ohits)
     assert max(sizes) > 2
+    lat = srv.latency()
+    assert lat["count"] == 24 and 0.0 < lat["p50_s"] <= lat["p99_s"]
     srv.close()
 
 
