@@ -176,10 +176,11 @@ struct lbvh_tree_s {
     bool store_dirty = false;  // a failed build may have left store words set
     DevBuf keys[2], vals[2];
     DevBuf nodes, store, lookback, hist, partials, bounds, ctl;
-    DevBuf counts, tile_sums, overflow, slots;
+    DevBuf counts, tile_sums, overflow, slots, spill_head, spill;
     DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
     DevBuf vscratch;                       // scratch of the Karras / Apetrei builds
     const float *prims_ptr = nullptr;      // the last build's input (self-queries)
+    int64_t spill_nq = 0;                  // query count the spill pool was sized for
     lbvh::Control *h_ctl = nullptr;  // pinned mirror of the control block (from pinned_controls())
     Profiler prof;
 
@@ -309,16 +310,17 @@ lbvh_status read_control(lbvh_tree_t t, cudaStream_t s) {
 }
 
 constexpr int64_t kOrderMinQueries = 2048;  // below this, walk in input order
-// Morton bits of the query order: 24 (3 sort passes) walked as fast as 30 on
-// 2^25 uniform queries and saved a pass (measured sweep 15..30 bits); order
-// changes speed only. LBVH_QUERY_ORDER_BITS=<multiple of 3 in [3, 63]>
+// Morton bits of the query order: 30 (4 sort passes). 24 bits saved a pass
+// on uniform queries at the same walk time, but on clustered queries (a
+// Gaussian mixture) the coarser cells cost more walk time than the pass;
+// order changes speed only. LBVH_QUERY_ORDER_BITS=<multiple of 3 in [3, 63]>
 // overrides it process-wide (tuning sweeps).
 int order_bits() {
     static int bits = 0;
     if (bits == 0) {
         const char *env = getenv("LBVH_QUERY_ORDER_BITS");
-        const int want = env ? atoi(env) : 24;
-        bits = (want >= 3 && want <= 63 && want % 3 == 0) ? want : 24;
+        const int want = env ? atoi(env) : 30;
+        bits = (want >= 3 && want <= 63 && want % 3 == 0) ? want : 30;
     }
     return bits;
 }
@@ -361,8 +363,9 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
 }
 
 lbvh::QueryScratch query_scratch(lbvh_tree_t t) {
-    return lbvh::QueryScratch{t->counts.as<uint2>(), t->slots.as<uint32_t>(),
-                              t->overflow.as<uint32_t>()};
+    return lbvh::QueryScratch{t->counts.as<uint2>(), t->slots.as<uint32_t>(), t->overflow.as<uint32_t>(),
+                              t->spill_head.as<uint32_t>(), t->spill.as<uint32_t>(),
+                              lbvh::spill_chunks_for(t->spill_nq)};
 }
 
 // The query up to the hit count: order, collecting walk, scan; synchronises `s`.
@@ -373,6 +376,11 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     const size_t unq = (size_t)qa.nq;
     LBVH_CUDA(t->counts.ensure(unq * 8 + 8, s));
     LBVH_CUDA(t->overflow.ensure(unq * 4 + 4, s));
+    LBVH_CUDA(t->spill_head.ensure(unq * 4 + 4, s));
+    if (spill_chunks_for(qa.nq) > spill_chunks_for(t->spill_nq) || !t->spill.p) {
+        LBVH_CUDA(t->spill.ensure((size_t)spill_chunks_for(qa.nq) * kSpillChunkWords * 4, s));
+        t->spill_nq = qa.nq;
+    }
     LBVH_CUDA(t->tile_sums.ensure((size_t)scan_tile_count(qa.nq) * 8 + 8, s));
     LBVH_CUDA(t->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
     Control *c = t->dctl();
@@ -469,7 +477,7 @@ struct lbvh_batch_s {
     bool self_query = false, sorted_in_b = false;
     DevBuf prim_off, query_off, node_start, store_start, chunks, chunk_first, qchunks;
     DevBuf keys[2], vals[2], nodes, store, lookback, hist, partials, bounds, ctl;
-    DevBuf count_pos, slots, overflow, tile_sums, qkeys[2], qvals[2], qlookback;
+    DevBuf count_pos, slots, overflow, tile_sums, qkeys[2], qvals[2], qlookback, spill_head, spill;
     // Segmented-sort tile tables: row r (r < sort_variant_count(): that
     // variant; the last row: the default variant) holds count + 1 entries.
     DevBuf tile_first, qtile_first;
@@ -604,6 +612,8 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
     LBVH_CUDA(b->count_pos.ensure(unq * 8 + 8, s));
     LBVH_CUDA(b->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
     LBVH_CUDA(b->overflow.ensure(unq * 4 + 4, s));
+    LBVH_CUDA(b->spill_head.ensure(unq * 4 + 4, s));
+    LBVH_CUDA(b->spill.ensure((size_t)spill_chunks_for(b->NQ) * kSpillChunkWords * 4, s));
     LBVH_CUDA(b->tile_sums.ensure((size_t)scan_tile_count(b->NQ) * 8 + 8, s));
     if (!b->h_ctl) LBVH_CUDA(pinned_controls().get(&b->h_ctl));
     LBVH_CUDA(cudaStreamSynchronize(s));
@@ -655,7 +665,8 @@ lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {
                                        b->qpasses, scratch, c, s, nullptr, b->sort_variant, &seg);
         qa.order = b->qvals[in_b ? 1 : 0].as<uint32_t>();
     }
-    const QueryScratch qs{b->count_pos.as<uint2>(), b->slots.as<uint32_t>(), b->overflow.as<uint32_t>()};
+    const QueryScratch qs{b->count_pos.as<uint2>(), b->slots.as<uint32_t>(), b->overflow.as<uint32_t>(),
+                          b->spill_head.as<uint32_t>(), b->spill.as<uint32_t>(), spill_chunks_for(b->NQ)};
     launch_batch_collect(b->nodes.as<float4>(), g.kind, bt, qa, qs, c, s);
     launch_exclusive_scan(qs.count_pos, b->NQ, g.offsets, b->tile_sums.as<int64_t>(), c, s);
     launch_query_copy_checked(qa, qs, g.offsets, g.hits, g.capacity, c, s);
@@ -737,7 +748,8 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
     for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
                       &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                       &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
-                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots, &t->vscratch})
+                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots, &t->vscratch, &t->spill_head,
+                      &t->spill})
         b->release(cudaStreamPerThread);
     pinned_controls().put(t->h_ctl);
     if (t->built) cudaEventDestroy(t->built);
@@ -1005,7 +1017,8 @@ lbvh_status lbvh_tree_bytes(lbvh_tree_t t, uint64_t *bytes) {
     for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
                             &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                             &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
-                            &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots})
+                            &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots, &t->vscratch,
+                            &t->spill_head, &t->spill})
         b += d->bytes;
     *bytes = b;
     return LBVH_OK;
@@ -1210,7 +1223,7 @@ void lbvh_batch_destroy(lbvh_batch_t b) {
                       &b->qchunks, &b->keys[0], &b->keys[1], &b->vals[0], &b->vals[1], &b->nodes, &b->store,
                       &b->lookback, &b->hist, &b->partials, &b->bounds, &b->ctl, &b->count_pos, &b->slots,
                       &b->overflow, &b->tile_sums, &b->qkeys[0], &b->qkeys[1], &b->qvals[0], &b->qvals[1],
-                      &b->qlookback, &b->tile_first, &b->qtile_first})
+                      &b->qlookback, &b->tile_first, &b->qtile_first, &b->spill_head, &b->spill})
         d->release(s);
     if (s) cudaStreamSynchronize(s);
     pinned_controls().put(b->h_ctl);
@@ -1422,8 +1435,9 @@ lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cud
 
 void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s) {
     for (DevBuf *b : {&t->counts, &t->tile_sums, &t->overflow, &t->slots, &t->qkeys[0], &t->qkeys[1],
-                      &t->qvals[0], &t->qvals[1], &t->qlookback})
+                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->spill_head, &t->spill})
         b->release(s);
+    t->spill_nq = 0;
 }
 
 }  // namespace lbvh

@@ -33,7 +33,8 @@ struct Control {
     uint32_t overflow_filled;      // entries of the overflow list
     unsigned long long total;      // total hits of the last query
     uint32_t overflow_big;         // overflow lists too long for one warp's sort
-    uint32_t pad[7];
+    uint32_t spill_used;           // spill chunks handed out by the walk
+    uint32_t pad[6];
 };
 constexpr int kQueryBufferHits = 64;  // hits kept per query by the walk
 
@@ -181,10 +182,23 @@ struct QueryArgs {
     float radius;
     const uint32_t *order;  // null: thread i walks query i; else query order[i]
 };
+// Hits past a walk's slot go to chunks of kSpillChunkWords words taken from a
+// shared pool (word 0 links to the next chunk of the same walk, the rest
+// hold hits). When the pool runs out, the query walks a second time instead.
+constexpr int kSpillChunkWords = 64;
+constexpr uint32_t kSpilledTag = 1u << 31;  // overflow-list entry whose hits are all in slot + chunks
+inline uint32_t spill_chunks_for(int64_t nq) {
+    const int64_t c = nq / 16;
+    return (uint32_t)(c < 1024 ? 1024 : (c > (1 << 26) ? (1 << 26) : c));
+}
+
 struct QueryScratch {
     uint2 *count_pos;         // nq: (hits of query q, walk position i of q)
     uint32_t *slots;          // nq * kQueryBufferHits: first hits of walk position i, walk order
-    uint32_t *overflow_list;  // nq, queries to walk a second time
+    uint32_t *overflow_list;  // nq: queries with more hits than a slot (kSpilledTag: no second walk)
+    uint32_t *spill_head;     // nq: first spill chunk of walk position i
+    uint32_t *spill;          // spill_chunks * kSpillChunkWords
+    uint32_t spill_chunks;
 };
 // The collecting walk (counts, short sorted lists, overflow list).
 void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,

@@ -36,9 +36,12 @@
 //             writes its 32 lists, adjacent in the CSR, through shared
 //             memory, one coalesced list per step; lists of 33..64 hits are
 //             sorted by the whole warp (two values per lane, shuffles).
-//   overflow  queries with more hits walk again and write straight into the
-//             CSR; a fix-up kernel sorts those lists, one warp per list (one
-//             CTA per list above 1024 hits).
+//   overflow  hits past the slot go on, during the same walk, to chunks of a
+//             shared spill pool; those lists are copied (slot + chunks) to
+//             their CSR ranges; only when the pool runs out does a query walk
+//             a second time, writing straight into the CSR. A fix-up kernel
+//             then sorts every such list, one warp per list (one CTA per list
+//             above 1024 hits).
 #include <algorithm>
 #include <cstdlib>
 #include <type_traits>
@@ -162,6 +165,33 @@ __device__ __forceinline__ float3 xyz(float4 v) { return make_float3(v.x, v.y, v
 // that satisfies the predicate, leaves in increasing sorted position. Returns
 // false if the walk ran past 2(2n-1) steps or met an id outside the tree (a
 // corrupt tree).
+// Algorithm 1 from `node` on, stopping early when on_leaf returns false: the
+// return value is then the next node to visit (so the walk can resume there),
+// else a terminal id (outside [0, 2n-1)); `steps` carries the step count and
+// a corrupt tree (more than 2(2n-1) steps) returns 2n.
+template <int kP, typename Q, typename F>
+__device__ __forceinline__ int walk_from(const TreeView &t, const Q &q, int node, uint32_t &steps,
+                                         F &&on_leaf) {
+    const int ni = (int)t.n - 1;
+    const int nodes = 2 * (int)t.n - 1;
+    const uint32_t max_steps = 2u * (uint32_t)nodes;
+    const float4 *base = t.inodes;  // leaves follow the internal records
+    while ((uint32_t)node < (uint32_t)nodes) {
+        if (++steps > max_steps) return nodes + 1;
+        const bool leaf = node >= ni;
+        const int unit = kP == LBVH_PRIM_BOXES ? 2 * node : (leaf ? node + ni : 2 * node);
+        const float4 a = __ldg(base + unit);
+        float4 b = a;  // a point leaf's box is its point
+        if (kP == LBVH_PRIM_BOXES || !leaf) b = __ldg(base + unit + 1);
+        const bool hit = hits(q, xyz(a), xyz(b));
+        const uint32_t word = __float_as_uint(a.w);
+        // internal: left child on a hit, else skip; leaf k: position k+1
+        node = leaf ? node + 1 - ((word & kLeafSkipInternal) ? ni : 0) : __float_as_int(hit ? a.w : b.w);
+        if (hit && leaf && !on_leaf(word & kLeafIndexMask)) return node;
+    }
+    return node;
+}
+
 template <int kP, typename Q, typename F>
 __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf) {
     const int ni = (int)t.n - 1;
@@ -196,19 +226,77 @@ __device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) 
     return qa.order ? (int64_t)__ldcs(qa.order + i) : i;
 }
 
+// Hits past a walk's slot: appended to chunks from the shared pool, the first
+// chunk recorded in spill_head[i], each chunk's word 0 linking to the next.
+// `cur` is the walk's current chunk (kNoChunk before the first); it becomes
+// kSpillFailed when the pool is exhausted, and the query then takes the
+// second walk.
+constexpr uint32_t kNoChunk = 0xffffffffu, kSpillFailed = 0xfffffffeu;
+
+__device__ __forceinline__ void spill_put(const QueryScratch &qs, Control *ctl, int64_t i, uint32_t cnt,
+                                          uint32_t id, uint32_t &cur) {
+    if (cur == kSpillFailed) return;
+    const uint32_t sidx = cnt - (uint32_t)kSlot;                   // index among the spilled hits
+    const uint32_t off = sidx % (uint32_t)(kSpillChunkWords - 1);  // slot in the chunk (after the link)
+    if (off == 0) {
+        const uint32_t fresh = atomicAdd(&ctl->spill_used, 1u);
+        if (fresh >= qs.spill_chunks) {
+            cur = kSpillFailed;
+            return;
+        }
+        if (cur == kNoChunk) qs.spill_head[i] = fresh;
+        else qs.spill[(int64_t)cur * kSpillChunkWords] = fresh;
+        cur = fresh;
+    }
+    qs.spill[(int64_t)cur * kSpillChunkWords + 1 + off] = id;
+}
+
+// One query's collecting walk at walk position i (query qi): the first kSlot
+// hits go to the slot, later ones to spill chunks. Writes (count, i) and, for
+// a long list, its overflow-list entry (tagged when all its hits are in slot
+// + chunks).
+template <int kQ, int kP>
+__device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs &qa, const QueryScratch &qs,
+                                             Control *ctl, int64_t i, int64_t qi, bool walk_ok) {
+    uint32_t cnt = 0;
+    uint32_t cur = kNoChunk;
+    if (walk_ok) {
+        const auto q = QueryOf<kQ>::load(qa, qi);
+        uint32_t *slot = qs.slots + i * kSlot;
+        const bool ok = walk<kP>(t, q, [&](uint32_t id) {
+            if (cnt < (uint32_t)kSlot) __stcs(slot + cnt, id);
+            else spill_put(qs, ctl, i, cnt, id, cur);
+            ++cnt;
+        });
+        if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
+    }
+    __stcs(qs.count_pos + qi, make_uint2(cnt, (uint32_t)i));  // streamed: keep L2 for the tree
+    if (cnt > (uint32_t)kSlot)
+        qs.overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] =
+            (uint32_t)qi | (cur != kSpillFailed ? kSpilledTag : 0u);
+}
+
 // K walks per thread, advanced in lock step: each iteration first issues the
 // node loads of every live walk, then tests them, so K independent loads are
 // in flight per thread (the walk is bound by the latency of its dependent
 // loads, not by bandwidth). Thread t walks sorted positions K*t .. K*t+K-1,
 // which are neighbours in the Morton order. Each walk keeps its hit count and
 // up to kSlot primitive ids (walk order) in the slot of its walk position.
+// At most 32 registers (8 CTAs of 256 threads per SM): the walk hides its
+// load latency with occupancy.
 template <int kQ, int kP, int K>
 __global__ void __launch_bounds__(kThreads)
-    collect_kernel(TreeView t, QueryArgs qa, uint2 *__restrict__ count_pos,
-                   uint32_t *__restrict__ slots, uint32_t *__restrict__ overflow_list, Control *ctl) {
+    collect_kernel(TreeView t, QueryArgs qa, QueryScratch qs, Control *ctl) {
+    uint2 *__restrict__ count_pos = qs.count_pos;
+    uint32_t *__restrict__ slots = qs.slots;
     const int64_t first = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * K;
     if (first >= qa.nq) return;
     const bool walk_ok = t.n > 0 && ctl->build_flags == 0;
+    if (K == 1) {
+        collect_walk<kQ, kP>(t, qa, qs, ctl, first, thread_query(qa, first), walk_ok);
+        return;
+    }
+    // K > 1 (tuning): lock-step walks; lists past the slot take the second walk
     const int ni = (int)t.n - 1;
     const int nodes = 2 * (int)t.n - 1;
     const uint32_t max_steps = 2u * (uint32_t)nodes;
@@ -268,7 +356,8 @@ __global__ void __launch_bounds__(kThreads)
         if (i >= qa.nq) continue;
         if (walk_ok && !(node[j] == kSentinel || node[j] == nodes)) atomicOr(&ctl->query_flags, kFlagCorrupt);
         __stcs(count_pos + qi[j], make_uint2(cnt[j], (uint32_t)i));  // streamed: keep L2 for the tree
-        if (cnt[j] > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi[j];
+        if (cnt[j] > (uint32_t)kSlot)
+            qs.overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi[j];
     }
 }
 
@@ -387,7 +476,9 @@ __global__ void __launch_bounds__(kThreads)
                          const int64_t *__restrict__ offsets, uint32_t *__restrict__ hits) {
     const int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (j >= count) return;
-    const int64_t qi = list[j];
+    const uint32_t e = list[j];
+    if (e & kSpilledTag) return;  // its hits are in its slot and spill chunks
+    const int64_t qi = e;
     const int64_t base = offsets[qi];
     const int64_t total = offsets[qi + 1] - base;
     const auto q = QueryOf<kQ>::load(qa, qi);
@@ -563,7 +654,7 @@ __global__ void __launch_bounds__(kThreads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *a = s[warp];
     for (int64_t j = (int64_t)blockIdx.x * kSortWarps + warp; j < count; j += (int64_t)gridDim.x * kSortWarps) {
-        const uint32_t q = list[j];
+        const uint32_t q = list[j] & ~kSpilledTag;
         const int64_t base = offsets[q];
         const int64_t m = offsets[q + 1] - base;
         if (m > kWarpSortMax) {
@@ -603,31 +694,52 @@ __global__ void __launch_bounds__(kFixThreads)
     }
 }
 
+// Lists whose hits past the slot all went to spill chunks: one warp per list
+// copies the slot and then each chunk of its chain to the list's CSR range
+// (in walk order; the list sorts follow).
+__global__ void __launch_bounds__(kThreads)
+    spill_gather_kernel(QueryScratch qs, const int64_t *__restrict__ offsets, uint32_t *__restrict__ hits,
+                        const Control *ctl, unsigned long long capacity) {
+    if (ctl->total > capacity) return;
+    const uint32_t count = ctl->overflow_filled;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kThreads / 32;
+    for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < count; j += (int64_t)gridDim.x * kWarps) {
+        const uint32_t e = qs.overflow_list[j];
+        if (!(e & kSpilledTag)) continue;  // walks a second time instead
+        const uint32_t q = e & ~kSpilledTag;
+        const int64_t base = offsets[q];
+        const int64_t m = offsets[q + 1] - base;
+        const uint32_t pos = qs.count_pos[q].y;
+        uint32_t *dst = hits + base;
+        const uint32_t *slot = qs.slots + (int64_t)pos * kSlot;
+        for (int k = lane; k < kSlot; k += 32) dst[k] = slot[k];
+        int64_t done = kSlot;
+        uint32_t c = qs.spill_head[pos];
+        while (done < m) {
+            if (c >= qs.spill_chunks) break;  // cannot happen for a tagged list; guards the reads
+            const uint32_t *chunk = qs.spill + (int64_t)c * kSpillChunkWords;
+            const int64_t take = min((int64_t)(kSpillChunkWords - 1), m - done);
+            for (int k = lane; k < take; k += 32) dst[done + k] = chunk[1 + k];
+            done += take;
+            c = chunk[0];
+        }
+    }
+}
+
 // ---- batches: the same walk, on the tree of the query's instance
 
 template <int kQ, int kP>
-__global__ void __launch_bounds__(kThreads)
-    batch_collect_kernel(const float4 *__restrict__ nodes, BatchTables bt, QueryArgs qa,
-                         uint2 *__restrict__ count_pos, uint32_t *__restrict__ slots,
-                         uint32_t *__restrict__ overflow_list, Control *ctl) {
+__global__ void __launch_bounds__(kThreads, 8)  // at most 32 registers: full occupancy for the walk
+    batch_collect_kernel(const float4 *__restrict__ nodes, BatchTables bt, QueryArgs qa, QueryScratch qs,
+                         Control *ctl) {
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i >= qa.nq) return;
     const int64_t qi = thread_query(qa, i);
     const int b = instance_of(bt.query_off, bt.count, qi);
     const int64_t n = bt.prim_off[b + 1] - bt.prim_off[b];
-    uint32_t c = 0;
-    if (n > 0 && ctl->build_flags == 0) {
-        const TreeView t{nodes + bt.node_start[b], nullptr, n, kP};
-        const auto q = QueryOf<kQ>::load(qa, qi);
-        uint32_t *slot = slots + i * kSlot;
-        const bool ok = walk<kP>(t, q, [&](uint32_t id) {
-            if (c < (uint32_t)kSlot) __stcs(slot + c, id);
-            ++c;
-        });
-        if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
-    }
-    __stcs(count_pos + qi, make_uint2(c, (uint32_t)i));
-    if (c > (uint32_t)kSlot) overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi;
+    const TreeView t{nodes + bt.node_start[b], nullptr, n, kP};
+    collect_walk<kQ, kP>(t, qa, qs, ctl, i, qi, n > 0 && ctl->build_flags == 0);
 }
 
 // Overflow lists whose number is known only on the device: a fixed grid
@@ -641,7 +753,9 @@ __global__ void __launch_bounds__(kThreads)
     if (ctl->total > capacity) return;  // nothing is written into a buffer that is too small
     const uint32_t count = ctl->overflow_filled;
     for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < count; j += (int64_t)gridDim.x * kThreads) {
-        const int64_t qi = list[j];
+        const uint32_t e = list[j];
+        if (e & kSpilledTag) continue;  // its hits are in its slot and spill chunks
+        const int64_t qi = e;
         const int b = instance_of(bt.query_off, bt.count, qi);
         const int64_t n = bt.prim_off[b + 1] - bt.prim_off[b];
         const TreeView t{nodes + bt.node_start[b], nullptr, n, kP};
@@ -698,8 +812,7 @@ void launch_collect_k(const TreeView &t, const QueryArgs &q, const QueryScratch 
     const int64_t threads = (q.nq + K - 1) / K;
     const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
     dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
-        collect_kernel<decltype(qk)::value, decltype(pk)::value, K><<<blocks, kThreads, 0, s>>>(
-            t, q, qs.count_pos, qs.slots, qs.overflow_list, ctl);
+        collect_kernel<decltype(qk)::value, decltype(pk)::value, K><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl);
     });
 }
 
@@ -730,15 +843,18 @@ void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t
 
 // Sorts the overflow lists: warps for the lists, CTAs for the long ones.
 // `bound`: an upper bound of the overflow count (sizes the warp kernel's grid).
+// First copies the spilled lists (slot + chunks) to their CSR ranges; the
+// big-list sort then reuses the slot buffer, which nothing reads any more.
 static void launch_sort_lists(const QueryScratch &qs, uint64_t bound, const int64_t *offsets, uint32_t *hits,
                               unsigned long long capacity, Control *ctl, cudaStream_t s) {
     const uint64_t want = (bound + kSortWarps - 1) / kSortWarps;
     const uint64_t cap = (uint64_t)device_sm_count() * 8;
     const unsigned blocks = (unsigned)std::max<uint64_t>(1, std::min(want, cap));
+    spill_gather_kernel<<<blocks, kThreads, 0, s>>>(qs, offsets, hits, ctl, capacity);
     warp_sort_lists_kernel<<<blocks, kThreads, 0, s>>>(offsets, hits, qs.overflow_list, qs.slots, ctl, capacity);
     sort_big_lists_kernel<<<(unsigned)device_sm_count(), kFixThreads, 0, s>>>(offsets, hits, qs.slots, ctl,
                                                                               capacity);
-    count_launches(2);
+    count_launches(3);
 }
 
 void launch_query_overflow(const TreeView &t, const QueryArgs &q, const QueryScratch &qs,
@@ -759,8 +875,8 @@ void launch_batch_collect(const float4 *nodes, int kind, const BatchTables &bt, 
     if (q.nq <= 0) return;
     const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
     dispatch_kinds(q.qkind, kind, [&](auto qk, auto pk) {
-        batch_collect_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(
-            nodes, bt, q, qs.count_pos, qs.slots, qs.overflow_list, ctl);
+        batch_collect_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(nodes, bt, q, qs,
+                                                                                                    ctl);
     });
     count_launches(1);
 }
