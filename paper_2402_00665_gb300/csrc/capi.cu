@@ -559,6 +559,7 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
         store_start[k] = words;
         if (n > 0) {
             units += 2 * (n - 1) + (g.kind == LBVH_PRIM_POINTS ? n : 2 * n);
+            units += units & 1;  // every tree starts on a 32-byte boundary (the walk loads 32-byte records)
             words += n - 1;
         }
     }
