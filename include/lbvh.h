@@ -64,6 +64,10 @@ typedef enum { LBVH_Q_SPHERE = 0, LBVH_Q_BOX = 1, LBVH_Q_RAY = 2 } lbvh_query_ki
 
 /* ---------------------------------------------------------------- tree */
 
+/* A tree handle may be used by one call at a time (builds, queries, refits,
+ * exports and saves share its scratch buffers); different trees may be used
+ * from different threads at once. */
+
 /* Create an empty tree handle (no device memory yet). *out receives it. */
 lbvh_status lbvh_tree_create(lbvh_tree_t *out);
 

@@ -250,13 +250,13 @@ cudaError_t pool_reserve(size_t bytes, cudaStream_t s) {
 }
 
 int device_sm_count() {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
+    // read once, thread-safely (function-local static initialisation)
+    static const int sms = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return sms;
 }
 
@@ -316,12 +316,11 @@ constexpr int64_t kOrderMinQueries = 2048;  // below this, walk in input order
 // order changes speed only. LBVH_QUERY_ORDER_BITS=<multiple of 3 in [3, 63]>
 // overrides it process-wide (tuning sweeps).
 int order_bits() {
-    static int bits = 0;
-    if (bits == 0) {
+    static const int bits = [] {
         const char *env = getenv("LBVH_QUERY_ORDER_BITS");
         const int want = env ? atoi(env) : 30;
-        bits = (want >= 3 && want <= 63 && want % 3 == 0) ? want : 30;
-    }
+        return (want >= 3 && want <= 63 && want % 3 == 0) ? want : 30;
+    }();
     return bits;
 }
 

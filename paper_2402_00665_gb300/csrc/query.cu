@@ -818,12 +818,11 @@ void dispatch_kinds(int qkind, int pkind, F &&f) {
 // bound by L1 wavefronts (distinct sectors per load), which more walks per
 // thread only increase.
 static int walks_per_thread() {
-    static int k = 0;
-    if (k == 0) {
+    static const int k = [] {
         const char *env = getenv("LBVH_WALKS_PER_THREAD");
         const int want = env ? atoi(env) : 1;
-        k = want >= 1 && want <= 4 ? want : 1;
-    }
+        return want >= 1 && want <= 4 ? want : 1;
+    }();
     return k;
 }
 

@@ -138,7 +138,7 @@ uint64_t estimate_bytes(const lbvh_request &r) {
     const uint64_t qsz = r.qkind == LBVH_Q_SPHERE ? 12 : (r.qkind == LBVH_Q_BOX ? 24 : 32);
     const uint64_t build = n * (prim + 24 + 24 + 48 + 8 + 16);
     const uint64_t query = nq * (qsz + 4 + 8 + lbvh::kQueryBufferHits * 4 + 4 + 8 + 24 + 8) + r.capacity * 4;
-    return build + query;
+    return std::max<uint64_t>(build + query, 1);  // a running job always counts as in flight
 }
 
 // Device bytes of a resident tree: its nodes (2(n-1) internal records of
@@ -235,6 +235,7 @@ void lbvh_server_s::schedule_loop() {
                     cv_done.notify_all();
                     continue;
                 }
+                if (it->second.in_use > 0) break;  // another query is using this tree: one at a time
                 it->second.in_use++;  // pinned: make_room must not evict the tree this request needs
                 if (!make_room(r.est_bytes)) {
                     it->second.in_use--;

@@ -306,16 +306,17 @@ const Variant *variant_table(int *count) {
         make_variant<16, 2, true>(), make_variant<12, 3, true>(),  make_variant<8, 6, true>(),
         make_variant<16, 2, false>(),
     };
-    static bool configured = false;
-    if (!configured) {
+    // kernel attributes set once, thread-safely (function-local static initialisation)
+    static const bool configured = [] {
         for (const Variant &v : table) {
             for (PassKernel k : {v.first, v.rest, v.seg_first, v.seg_rest}) {
                 cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
                 cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             }
         }
-        configured = true;
-    }
+        return true;
+    }();
+    (void)configured;
     *count = (int)(sizeof table / sizeof table[0]);
     return table;
 }
@@ -323,12 +324,11 @@ const Variant *variant_table(int *count) {
 const Variant &variant(int idx = -1) {
     int count = 0;
     const Variant *table = variant_table(&count);
-    static int pick = -1;
-    if (pick < 0) {
+    static const int pick = [&] {
         const char *env = getenv("LBVH_SORT_VARIANT");
         const int want = env ? atoi(env) : 0;
-        pick = (want >= 0 && want < count) ? want : 0;
-    }
+        return (want >= 0 && want < count) ? want : 0;
+    }();
     return table[(idx >= 0 && idx < count) ? idx : pick];
 }
 

@@ -102,6 +102,25 @@ def test_wide_codes_share_batches():
     srv.close()
 
 
+def test_queries_on_one_resident_tree_from_several_slots():
+    # query-only requests on the same key queue behind each other (a tree is
+    # used by one call at a time) while other slots stay free
+    lbvh = L()
+    pts = torch.from_numpy(inputs.uniform_points(50000, seed=21)).cuda()
+    r = float(inputs.radius_for_neighbours(50000))
+    srv = lbvh.Server(budget_bytes=1 << 30, slots=4, max_batch=8)
+    _, _, info = srv.wait(srv.submit(pts, lbvh.POINTS, 30, radius=r, key=9, capacity=1 << 22))
+    assert info["status"] == lbvh.OK
+    qs = [pts[k * 5000:(k + 1) * 5000] for k in range(8)]
+    tickets = [srv.submit(None, lbvh.POINTS, 30, q, radius=r, key=9, capacity=1 << 20) for q in qs]
+    for q, t in zip(qs, tickets):
+        off, hits, info = srv.wait(t)
+        assert info["status"] == lbvh.OK
+        ooff, ohits = alone(pts, lbvh.POINTS, 30, q, lbvh.SPHERE, r)
+        assert np.array_equal(off.cpu().numpy(), ooff) and np.array_equal(hits.cpu().numpy(), ohits)
+    srv.close()
+
+
 def test_budget_evicts_least_recently_used_and_refuses_what_never_fits():
     lbvh = L()
     pts = [torch.from_numpy(inputs.uniform_points(20000, seed=k)).cuda() for k in range(10)]
