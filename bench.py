@@ -100,6 +100,9 @@ SERVED_WORKLOADS = {
                             60 << 30),
     "served_poisson_short": ("as served_poisson_2000 with 60 requests (short case)", 60, 2000.0, 1024, 4194304,
                              2, 63, 60 << 30),
+    "served_poisson_2000_budget4gb": ("as served_poisson_2000 under a 4 GB HBM budget: the resident trees do not "
+                                      "all fit, so admission evicts the least recently used ones while requests "
+                                      "arrive", 400, 2000.0, 1024, 4194304, 2, 63, 4 << 30),
 }
 
 WORKLOADS = {
@@ -127,6 +130,11 @@ WORKLOADS = {
                                  "component centres uniform in [0,1)^3), half-extents lognormal(ln 1e-4, 0.5); "
                                  "63-bit codes; build + 2^24 box-overlap queries from the same mixture",
                                  1 << 25, 63, "mixture_boxes"),
+    "mixture_boxes_2^25_30bit": ("as mixture_boxes_2^25_63bit with 30-bit codes: most centres of a component "
+                                 "share a code, so the index tie-break decides much of the tree",
+                                 1 << 25, 30, "mixture_boxes"),
+    "mixture_boxes_2^23_63bit": ("as mixture_boxes_2^25_63bit with 2^23 boxes and 2^22 queries (profiling case)",
+                                 1 << 23, 63, "mixture_boxes"),
 }
 
 
