@@ -622,7 +622,7 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
 }
 
 // The whole batched pipeline on `s`, with no host synchronisation (so it can
-// be captured in a CUDA graph): bounds, composite keys, one radix sort over
+// be captured in a CUDA graph): bounds, Morton codes, one segmented radix sort over
 // all instances, the bottom-up pass of every tree, the queries' Morton order,
 // the collecting walk, the scan, the checked copy and the overflow lists.
 lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {

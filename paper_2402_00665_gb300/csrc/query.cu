@@ -25,11 +25,11 @@
 // visit the same nodes), and write results at the query's own index.
 //
 // CSR in one walk:
-//   collect   each thread walks K adjacent sorted positions i (query q =
-//             order[i]) in lock step (K loads in flight) and writes up to
-//             kQueryBufferHits primitive ids, in walk order, into slot i of a
-//             scratch array (no shared memory: L1 stays with the tree), and
-//             (hit count, i) at q.
+//   collect   each thread walks sorted position i (query q = order[i]; K > 1
+//             adjacent positions in lock step is a tuning option) and writes
+//             up to kQueryBufferHits primitive ids, in walk order, into slot i
+//             of a scratch array (no shared memory: L1 stays with the tree),
+//             and (hit count, i) at q.
 //   scan      exclusive scan of the counts -> offsets, total (host reads it).
 //   copy      in query order: each thread loads one slot of up to 32 hits
 //             into registers and sorts it with a bitonic network; the warp
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // Second walk for the overflow list: hits go straight to the CSR in walk
-// order (sorted afterwards by sort_lists_kernel).
+// order (sorted afterwards by the list sorts).
 template <int kQ, int kP>
 __global__ void __launch_bounds__(kThreads)
     overflow_walk_kernel(TreeView t, QueryArgs qa, const uint32_t *__restrict__ list, uint32_t count,
