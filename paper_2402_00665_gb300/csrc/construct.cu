@@ -30,10 +30,15 @@
 //     ever touch store[p], so the one that reads "empty" is the first. The
 //     second writes "empty" back, leaving the scratch clean for the next build
 //     (it is zeroed once, when allocated).
-//   - release/acquire: the exchange is an acq_rel atomic at device scope, so
-//     a thread's node is visible before its half of the parent is, and the
-//     second thread reads the sibling's box (through L2, ld.global.cg) only
-//     after it has seen that half.
+//   - release/acquire: the exchange is an acq_rel atomic, so a thread's node
+//     is visible before its half of the parent is, and the second thread
+//     reads the sibling's box only after it has seen that half.
+//   - two phases (construct_block_kernel): splits whose two children both
+//     lie inside one CTA's 256 leaves meet in shared memory (block-scope
+//     exchange, sibling box from shared memory); only the nodes spanning a
+//     CTA edge, a few percent of them, meet in the device-scope `store`
+//     words (sibling box through L2, ld.global.cg). The batched kernel keeps
+//     one phase, every exchange at device scope.
 #include <cuda/atomic>
 
 #include <cstdlib>
@@ -97,19 +102,24 @@ __device__ __forceinline__ unsigned long long publish_exchange(unsigned long lon
     return old;
 }
 
-// Algorithm 4 for leaf i of one tree of n leaves. codes/perm point at the
-// tree's first sorted position; perm holds primitive indices into `prims`,
-// the tree's own indices being perm - perm_base. inodes/leaves/store are the
-// tree's own arrays (layout in lbvh_internal.cuh).
-template <int kKind, bool kAcqRel>
-__device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__restrict__ codes,
-                                               const uint32_t *__restrict__ perm, uint32_t perm_base,
-                                               const float *__restrict__ prims, float4 *inodes,
-                                               float4 *leaves, unsigned long long *store,
-                                               uint32_t *flags) {
-    const int ni = n - 1;
+// A thread's finished node while it climbs: leaf range [l, r], delta*(l-1),
+// delta*(r), delta*(r+1), and its box.
+struct Climb {
+    uint32_t l, r, d_left, d_right, d_next;
+    float3 lo, hi;
+};
 
-    // ---- delta* around the leaf
+// Algorithm 4's leaf step for leaf i of one tree of n leaves: delta* around
+// the leaf, the leaf's skip and box (written out), and the climb state.
+// codes/perm point at the tree's first sorted position; perm holds primitive
+// indices into `prims`, the tree's own indices being perm - perm_base. False
+// (and kFlagCorrupt) if perm is not a permutation of this tree.
+template <int kKind>
+__device__ __forceinline__ bool leaf_step(int i, int n, const uint64_t *__restrict__ codes,
+                                          const uint32_t *__restrict__ perm, uint32_t perm_base,
+                                          const float *__restrict__ prims, float4 *leaves, uint32_t *flags,
+                                          Climb &c) {
+    const int ni = n - 1;
     const uint64_t c0 = codes[i];
     const uint32_t dl = i > 0 ? delta_star(codes[i - 1], c0, (uint32_t)(i - 1)) : kInf;
     uint32_t dr = kInf, drn = kInf;
@@ -118,14 +128,12 @@ __device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__r
         dr = delta_star(c0, c1, (uint32_t)i);
         if (i + 2 < n) drn = delta_star(c1, codes[i + 2], (uint32_t)(i + 1));
     }
-
-    // ---- leaf: skip (Algorithm 4, leaf part) and box
     const int leaf_skip = i == n - 1 ? kSentinel : (dr < drn ? ni + i + 1 : i + 1);
     const uint32_t p_id = perm[i];
     const uint32_t p_own = p_id - perm_base;
     if (p_own >= (uint32_t)n) {  // not a permutation of this tree: the sort failed
         atomicOr(flags, kFlagCorrupt);
-        return;
+        return false;
     }
     float3 lo, hi;
     if (kKind == LBVH_PRIM_POINTS) {
@@ -145,16 +153,64 @@ __device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__r
         leaves[2 * (int64_t)i] = make_float4(lo.x, lo.y, lo.z, __uint_as_float(word));
         leaves[2 * (int64_t)i + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
     }
-    if (n == 1) return;
-    // ---- climb
-    uint32_t l = i, r = i;
-    uint32_t d_left = dl, d_right = dr, d_next = drn;  // delta*(l-1), delta*(r), delta*(r+1)
+    c = Climb{(uint32_t)i, (uint32_t)i, dl, dr, drn, lo, hi};
+    return true;
+}
+
+// The parent's split p of c's node (range_right for a left child, range_left
+// - 1 for a right child) and the half of the parent's description c gives.
+__device__ __forceinline__ bool parent_split(const Climb &c, uint32_t &p, unsigned long long &mine) {
+    const bool is_left = c.d_right < c.d_left;
+    p = is_left ? c.r : c.l - 1;
+    mine = is_left ? pack(c.l, c.d_left, 0) : pack(c.r, c.d_right, c.d_next);
+    return is_left;
+}
+
+// The second thread up at split p takes the sibling's half: c becomes the
+// parent's range; returns the sibling's node id (leaves from ni up).
+__device__ __forceinline__ int take_half(Climb &c, bool is_left, uint32_t p, unsigned long long other,
+                                         int ni) {
+    if (is_left) {
+        c.r = (uint32_t)other;
+        c.d_right = (uint32_t)(other >> 32) & 0xffu;
+        c.d_next = (uint32_t)(other >> 40) & 0xffu;
+        return (p + 1 == c.r) ? ni + (int)p + 1 : (int)p + 1;
+    }
+    c.l = (uint32_t)other;
+    c.d_left = (uint32_t)(other >> 32) & 0xffu;
+    return (c.l == p) ? ni + (int)p : (int)p;
+}
+
+// The parent of split p: box = union with the sibling's, Karras index q = r
+// if delta*(r) < delta*(l-1) else l, left child (L_p if l == p else I_p),
+// skip (sentinel if r == n-1, else L_{r+1} if delta*(r) < delta*(r+1), else
+// I_{r+1}). Writes node q and returns q.
+__device__ __forceinline__ int write_parent(Climb &c, uint32_t p, int n, float3 slo, float3 shi,
+                                            float4 *inodes) {
+    const int ni = n - 1;
+    c.lo = make_float3(min_ordered(c.lo.x, slo.x), min_ordered(c.lo.y, slo.y), min_ordered(c.lo.z, slo.z));
+    c.hi = make_float3(max_ordered(c.hi.x, shi.x), max_ordered(c.hi.y, shi.y), max_ordered(c.hi.z, shi.z));
+    const int q = c.d_right < c.d_left ? (int)c.r : (int)c.l;
+    const int left_child = (c.l == p) ? ni + (int)p : (int)p;
+    const int skip = (c.r == (uint32_t)(n - 1)) ? kSentinel
+                                                : (c.d_right < c.d_next ? ni + (int)c.r + 1 : (int)c.r + 1);
+    inodes[2 * (int64_t)q] = make_float4(c.lo.x, c.lo.y, c.lo.z, __int_as_float(left_child));
+    inodes[2 * (int64_t)q + 1] = make_float4(c.hi.x, c.hi.y, c.hi.z, __int_as_float(skip));
+    return q;
+}
+
+// Climb from c's node with device-scope exchanges on store[p] until this
+// thread is the first up at a split, or has written the root I_0.
+template <int kKind, bool kAcqRel>
+__device__ __forceinline__ void climb_global(Climb c, int n, float4 *inodes, const float4 *leaves,
+                                             unsigned long long *store, uint32_t *flags) {
+    const int ni = n - 1;
     // The augmented keys have at most 64 + 32 bits, so no leaf is deeper than
     // 96 levels; the bound only guards against a corrupt input order.
     for (int level = 0; level < 128; ++level) {
-        const bool is_left = d_right < d_left;
-        const uint32_t p = is_left ? r : l - 1;
-        const unsigned long long mine = is_left ? pack(l, d_left, 0) : pack(r, d_right, d_next);
+        uint32_t p;
+        unsigned long long mine;
+        const bool is_left = parent_split(c, p, mine);
         if (p >= (uint32_t)ni) {
             atomicOr(flags, kFlagCorrupt);
             return;
@@ -162,35 +218,102 @@ __device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__r
         const unsigned long long other = publish_exchange<kAcqRel>(store + p, mine);
         if (other == 0ull) return;  // first thread up
         store[p] = 0ull;            // second thread up: leave the slot empty again
-        int sibling;
         if ((uint32_t)other >= (uint32_t)n) {
             atomicOr(flags, kFlagCorrupt);
             return;
         }
-        if (is_left) {
-            r = (uint32_t)other;
-            d_right = (uint32_t)(other >> 32) & 0xffu;
-            d_next = (uint32_t)(other >> 40) & 0xffu;
-            sibling = (p + 1 == r) ? ni + (int)p + 1 : (int)p + 1;
-        } else {
-            l = (uint32_t)other;
-            d_left = (uint32_t)(other >> 32) & 0xffu;
-            sibling = (l == p) ? ni + (int)p : (int)p;
-        }
+        const int sibling = take_half(c, is_left, p, other, ni);
         float3 slo, shi;
         load_node_box<kKind>(inodes, leaves, ni, sibling, slo, shi);
-        lo = make_float3(min_ordered(lo.x, slo.x), min_ordered(lo.y, slo.y), min_ordered(lo.z, slo.z));
-        hi = make_float3(max_ordered(hi.x, shi.x), max_ordered(hi.y, shi.y), max_ordered(hi.z, shi.z));
-
-        const int q = d_right < d_left ? (int)r : (int)l;  // Karras index of the parent
-        const int left_child = (l == p) ? ni + (int)p : (int)p;
-        const int skip = (r == (uint32_t)(n - 1)) ? kSentinel
-                                                 : (d_right < d_next ? ni + (int)r + 1 : (int)r + 1);
-        inodes[2 * (int64_t)q] = make_float4(lo.x, lo.y, lo.z, __int_as_float(left_child));
-        inodes[2 * (int64_t)q + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip));
-        if (q == 0) return;  // the root
+        if (write_parent(c, p, n, slo, shi, inodes) == 0) return;  // the root
     }
     atomicOr(flags, kFlagCorrupt);
+}
+
+// Algorithm 4 for leaf i, every exchange at device scope (batched trees).
+template <int kKind, bool kAcqRel>
+__device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__restrict__ codes,
+                                               const uint32_t *__restrict__ perm, uint32_t perm_base,
+                                               const float *__restrict__ prims, float4 *inodes,
+                                               float4 *leaves, unsigned long long *store,
+                                               uint32_t *flags) {
+    Climb c;
+    if (!leaf_step<kKind>(i, n, codes, perm, perm_base, prims, leaves, flags, c)) return;
+    if (n == 1) return;
+    climb_global<kKind, kAcqRel>(c, n, inodes, leaves, store, flags);
+}
+
+// Algorithm 4 with the climb split in two phases. CTA b owns leaves [a, a +
+// kThreads), a = b * kThreads. A node whose leaf range lies inside [a, a +
+// kThreads) has both children there, so its split p has a <= p and p + 1 <
+// a + kThreads; such splits meet in a shared-memory word with a block-scope
+// exchange, and the sibling's box is read from shared memory. A thread stops
+// phase 1 at a split on the block's edge, or as the first up at a word. After
+// the barrier every node inside the block is finished; a word still holding
+// its first thread's half has a sibling that spans the block's edge, and that
+// thread, like the one stopped at the edge, continues with the device-scope
+// exchanges of climb_global. Each node is still written once, by the second
+// thread up at its split, with the same fields: only where the two halves
+// meet changes.
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
+                           const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
+                           unsigned long long *store, uint32_t *flags) {
+    __shared__ unsigned long long s_word[kThreads];  // split p at p - a
+    __shared__ float3 s_lo[2][kThreads], s_hi[2][kThreads];  // boxes: [0] leaf, [1] internal node, at id - a
+    __shared__ int s_failed;
+    const int a = blockIdx.x * kThreads;
+    const int i = a + threadIdx.x;
+    const int ni = n - 1;
+    s_word[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) s_failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
+    __syncthreads();
+    if (s_failed) return;  // the sort failed: leave store untouched (the whole block returns)
+    Climb c;
+    bool pending = false, in_word = false;
+    uint32_t word_p = 0;
+    if (i < n && leaf_step<kKind>(i, n, codes, perm, 0u, prims, leaves, flags, c) && n > 1) {
+        s_lo[0][threadIdx.x] = c.lo;
+        s_hi[0][threadIdx.x] = c.hi;
+        for (int level = 0; level < 128; ++level) {
+            uint32_t p;
+            unsigned long long mine;
+            const bool is_left = parent_split(c, p, mine);
+            if (p >= (uint32_t)ni) {
+                atomicOr(flags, kFlagCorrupt);
+                break;
+            }
+            if (p < (uint32_t)a || p + 1 >= (uint32_t)(a + kThreads)) {  // on the block's edge
+                pending = true;
+                break;
+            }
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(s_word[p - a]);
+            const unsigned long long other = w.exchange(mine, cuda::memory_order_acq_rel);
+            if (other == 0ull) {  // first up: the sibling may come in this phase, or never
+                pending = in_word = true;
+                word_p = p;
+                break;
+            }
+            w.store(0ull, cuda::memory_order_relaxed);  // taken
+            if ((uint32_t)other >= (uint32_t)n) {
+                atomicOr(flags, kFlagCorrupt);
+                break;
+            }
+            const int sibling = take_half(c, is_left, p, other, ni);
+            const int k = sibling < ni ? 1 : 0;
+            const int at = (sibling < ni ? sibling : sibling - ni) - a;
+            const int q = write_parent(c, p, n, s_lo[k][at], s_hi[k][at], inodes);
+            if (q == 0) break;  // the root: the whole tree lies in this block
+            s_lo[1][q - a] = c.lo;
+            s_hi[1][q - a] = c.hi;
+        }
+    }
+    __syncthreads();
+    if (!pending) return;
+    if (in_word && s_word[word_p - a] == 0ull) return;  // the sibling came and carried on
+    // this thread wrote its own node, so its device-scope release covers it
+    climb_global<kKind, true>(c, n, inodes, leaves, store, flags);
 }
 
 template <int kKind, bool kAcqRel>
@@ -248,12 +371,16 @@ void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const 
                       int64_t n, int kind, float4 *inodes, float4 *leaves,
                       unsigned long long *store, uint32_t *flags, cudaStream_t s) {
     if (n <= 0) return;
-    // LBVH_CONSTRUCT_FENCES=1 selects the fence form of the exchange (tuning)
+    // tuning: LBVH_CONSTRUCT_GLOBAL=1 runs every exchange at device scope (one
+    // phase), LBVH_CONSTRUCT_FENCES=1 that with the fence form of the exchange
+    static const bool one_phase = getenv("LBVH_CONSTRUCT_GLOBAL") && atoi(getenv("LBVH_CONSTRUCT_GLOBAL"));
     static const bool fences = getenv("LBVH_CONSTRUCT_FENCES") && atoi(getenv("LBVH_CONSTRUCT_FENCES"));
     const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-    auto k = kind == LBVH_PRIM_POINTS
-                 ? (fences ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_POINTS, true>)
-                 : (fences ? construct_kernel<LBVH_PRIM_BOXES, false> : construct_kernel<LBVH_PRIM_BOXES, true>);
+    const bool pts = kind == LBVH_PRIM_POINTS;
+    auto k = !(one_phase || fences)
+                 ? (pts ? construct_block_kernel<LBVH_PRIM_POINTS> : construct_block_kernel<LBVH_PRIM_BOXES>)
+             : fences ? (pts ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_BOXES, false>)
+                      : (pts ? construct_kernel<LBVH_PRIM_POINTS, true> : construct_kernel<LBVH_PRIM_BOXES, true>);
     k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags);
     count_launches(1);
 }
