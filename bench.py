@@ -52,7 +52,8 @@ UNIT = "Mprims/s"
 #   encode      read the points, write the 64-bit codes      12 + 8
 #   sort pass   read key + payload, write key + payload      12 + 12 (pass 0: no payload read)
 #   construct   key 8 + perm 4 + point 12 read, leaf 16 and internal node 32
-#               written, store word 8, sibling box 24 re-read
+#               written (the store words and sibling boxes of the nodes inside
+#               a CTA's leaves stay in shared memory)
 #   query walk  query 12 read, count 4 written, 4 per hit kept, tree read once (48 B/leaf)
 #   query copy  count/start/offset read per query, 4 per hit read and 4 written
 def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_queries: bool = False,
@@ -67,8 +68,8 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
         "encode": (pb + 8) * n,
         "sort_pass0": 20 * n,
         **{f"sort_pass{k}": 24 * n for k in range(1, 8)},
-        # codes, perm, primitive read; leaf + internal node write; store word; sibling box re-read
-        "construct": (8 + 4 + pb + lb + 32 + 8 + 24) * n,
+        # codes, perm, primitive read; leaf + internal node write
+        "construct": (8 + 4 + pb + lb + 32) * n,
         # query + count/position per query, each kept hit, the tree once
         "query_walk": (qb + 8) * nq + 4 * hits + (32 + lb) * n,
         "query_order": (qb + 8 + 4 * 24) * nq,  # 30-bit order codes: 4 sort passes
