@@ -34,11 +34,11 @@
 //     is visible before its half of the parent is, and the second thread
 //     reads the sibling's box only after it has seen that half.
 //   - two phases (construct_block_kernel): splits whose two children both
-//     lie inside one CTA's 256 leaves meet in shared memory (block-scope
-//     exchange, sibling box from shared memory); only the nodes spanning a
-//     CTA edge, a few percent of them, meet in the device-scope `store`
-//     words (sibling box through L2, ld.global.cg). The batched kernel keeps
-//     one phase, every exchange at device scope.
+//     lie inside one group of consecutive leaves (128 by default) meet in
+//     shared memory (block-scope exchange, sibling box from shared memory);
+//     only the nodes spanning a group's edge meet in the device-scope
+//     `store` words (sibling box through L2, ld.global.cg). The batched
+//     kernel keeps every exchange at device scope.
 #include <cuda/atomic>
 
 #include <cstdlib>
@@ -109,25 +109,30 @@ struct Climb {
     float3 lo, hi;
 };
 
-// Algorithm 4's leaf step for leaf i of one tree of n leaves: delta* around
-// the leaf, the leaf's skip and box (written out), and the climb state.
-// codes/perm point at the tree's first sorted position; perm holds primitive
-// indices into `prims`, the tree's own indices being perm - perm_base. False
-// (and kFlagCorrupt) if perm is not a permutation of this tree.
-template <int kKind>
-__device__ __forceinline__ bool leaf_step(int i, int n, const uint64_t *__restrict__ codes,
-                                          const uint32_t *__restrict__ perm, uint32_t perm_base,
-                                          const float *__restrict__ prims, float4 *leaves, uint32_t *flags,
-                                          Climb &c) {
-    const int ni = n - 1;
+// delta*(i-1), delta*(i), delta*(i+1) around leaf i (255 = +inf at -1 and n-1).
+__device__ __forceinline__ void leaf_deltas(int i, int n, const uint64_t *__restrict__ codes, uint32_t &dl,
+                                            uint32_t &dr, uint32_t &drn) {
     const uint64_t c0 = codes[i];
-    const uint32_t dl = i > 0 ? delta_star(codes[i - 1], c0, (uint32_t)(i - 1)) : kInf;
-    uint32_t dr = kInf, drn = kInf;
+    dl = i > 0 ? delta_star(codes[i - 1], c0, (uint32_t)(i - 1)) : kInf;
+    dr = kInf;
+    drn = kInf;
     if (i + 1 < n) {
         const uint64_t c1 = codes[i + 1];
         dr = delta_star(c0, c1, (uint32_t)i);
         if (i + 2 < n) drn = delta_star(c1, codes[i + 2], (uint32_t)(i + 1));
     }
+}
+
+// Algorithm 4's leaf step for leaf i of one tree of n leaves, given its
+// delta* values: the leaf's skip and box (written out) and the climb state.
+// perm holds primitive indices into `prims`, the tree's own indices being
+// perm - perm_base. False (and kFlagCorrupt) if perm is not a permutation of
+// this tree.
+template <int kKind>
+__device__ __forceinline__ bool leaf_write(int i, int n, const uint32_t *__restrict__ perm, uint32_t perm_base,
+                                           const float *__restrict__ prims, float4 *leaves, uint32_t *flags,
+                                           uint32_t dl, uint32_t dr, uint32_t drn, Climb &c) {
+    const int ni = n - 1;
     const int leaf_skip = i == n - 1 ? kSentinel : (dr < drn ? ni + i + 1 : i + 1);
     const uint32_t p_id = perm[i];
     const uint32_t p_own = p_id - perm_base;
@@ -155,6 +160,16 @@ __device__ __forceinline__ bool leaf_step(int i, int n, const uint64_t *__restri
     }
     c = Climb{(uint32_t)i, (uint32_t)i, dl, dr, drn, lo, hi};
     return true;
+}
+
+template <int kKind>
+__device__ __forceinline__ bool leaf_step(int i, int n, const uint64_t *__restrict__ codes,
+                                          const uint32_t *__restrict__ perm, uint32_t perm_base,
+                                          const float *__restrict__ prims, float4 *leaves, uint32_t *flags,
+                                          Climb &c) {
+    uint32_t dl, dr, drn;
+    leaf_deltas(i, n, codes, dl, dr, drn);
+    return leaf_write<kKind>(i, n, perm, perm_base, prims, leaves, flags, dl, dr, drn, c);
 }
 
 // The parent's split p of c's node (range_right for a left child, range_left
@@ -243,39 +258,47 @@ __device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__r
     climb_global<kKind, kAcqRel>(c, n, inodes, leaves, store, flags);
 }
 
-// Algorithm 4 with the climb split in two phases. CTA b owns leaves [a, a +
-// kThreads), a = b * kThreads. A node whose leaf range lies inside [a, a +
-// kThreads) has both children there, so its split p has a <= p and p + 1 <
-// a + kThreads; such splits meet in a shared-memory word with a block-scope
-// exchange, and the sibling's box is read from shared memory. A thread stops
-// phase 1 at a split on the block's edge, or as the first up at a word. After
-// the barrier every node inside the block is finished; a word still holding
-// its first thread's half has a sibling that spans the block's edge, and that
-// thread, like the one stopped at the edge, continues with the device-scope
-// exchanges of climb_global. Each node is still written once, by the second
-// thread up at its split, with the same fields: only where the two halves
-// meet changes.
-template <int kKind>
-__global__ void __launch_bounds__(kThreads)
+// Algorithm 4 with the climb split in two phases. The leaves are cut into
+// groups of kGroup consecutive leaves [a, a + kGroup) (a warp, or a whole
+// CTA). A node whose leaf range lies inside a group has both children there,
+// so its split p has a <= p and p + 1 < a + kGroup; such splits meet in a
+// shared-memory word with a block-scope exchange, and the sibling's box is
+// read from shared memory. A thread stops phase 1 at a split on the group's
+// edge, or as the first up at a word. After the group's barrier every node
+// inside the group is finished; a word still holding its first thread's half
+// has a sibling that spans the group's edge, and that thread, like one stopped
+// at the edge, continues with the device-scope exchanges of climb_global.
+// Each node is still written once, by the second thread up at its split, with
+// the same fields: only where the two halves meet changes.
+template <int kGroup>
+struct GroupShape {
+    static constexpr int kCta = kGroup == 32 ? 256 : kGroup;  // warp groups: eight per CTA
+};
+
+template <int kKind, int kGroup>
+__global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kGroup>::kCta)
     construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
                            const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
                            unsigned long long *store, uint32_t *flags) {
-    __shared__ unsigned long long s_word[kThreads];  // split p at p - a
-    __shared__ float3 s_lo[2][kThreads], s_hi[2][kThreads];  // boxes: [0] leaf, [1] internal node, at id - a
+    constexpr int kCta = GroupShape<kGroup>::kCta;
+    __shared__ unsigned long long s_word[kCta];  // split p at g0 + p - a
+    __shared__ float3 s_lo[2][kCta], s_hi[2][kCta];  // boxes: [0] leaf, [1] internal node, at g0 + id - a
     __shared__ int s_failed;
-    const int a = blockIdx.x * kThreads;
-    const int i = a + threadIdx.x;
+    const int t = threadIdx.x;
+    const int g0 = t / kGroup * kGroup;    // the group's first thread
+    const int a = blockIdx.x * kCta + g0;  // the group's first leaf
+    const int i = blockIdx.x * kCta + t;
     const int ni = n - 1;
-    s_word[threadIdx.x] = 0ull;
-    if (threadIdx.x == 0) s_failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
+    s_word[t] = 0ull;
+    if (t == 0) s_failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
     __syncthreads();
-    if (s_failed) return;  // the sort failed: leave store untouched (the whole block returns)
+    if (s_failed) return;  // the sort failed: leave store untouched (the whole CTA returns)
     Climb c;
     bool pending = false, in_word = false;
-    uint32_t word_p = 0;
+    uint32_t word_at = 0;
     if (i < n && leaf_step<kKind>(i, n, codes, perm, 0u, prims, leaves, flags, c) && n > 1) {
-        s_lo[0][threadIdx.x] = c.lo;
-        s_hi[0][threadIdx.x] = c.hi;
+        s_lo[0][t] = c.lo;
+        s_hi[0][t] = c.hi;
         for (int level = 0; level < 128; ++level) {
             uint32_t p;
             unsigned long long mine;
@@ -284,15 +307,16 @@ __global__ void __launch_bounds__(kThreads)
                 atomicOr(flags, kFlagCorrupt);
                 break;
             }
-            if (p < (uint32_t)a || p + 1 >= (uint32_t)(a + kThreads)) {  // on the block's edge
+            const uint32_t at = p - (uint32_t)a;  // huge when p < a
+            if (at >= (uint32_t)(kGroup - 1)) {  // on the group's edge
                 pending = true;
                 break;
             }
-            cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(s_word[p - a]);
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(s_word[g0 + at]);
             const unsigned long long other = w.exchange(mine, cuda::memory_order_acq_rel);
             if (other == 0ull) {  // first up: the sibling may come in this phase, or never
                 pending = in_word = true;
-                word_p = p;
+                word_at = at;
                 break;
             }
             w.store(0ull, cuda::memory_order_relaxed);  // taken
@@ -302,16 +326,19 @@ __global__ void __launch_bounds__(kThreads)
             }
             const int sibling = take_half(c, is_left, p, other, ni);
             const int k = sibling < ni ? 1 : 0;
-            const int at = (sibling < ni ? sibling : sibling - ni) - a;
-            const int q = write_parent(c, p, n, s_lo[k][at], s_hi[k][at], inodes);
-            if (q == 0) break;  // the root: the whole tree lies in this block
-            s_lo[1][q - a] = c.lo;
-            s_hi[1][q - a] = c.hi;
+            const int sat = g0 + (sibling < ni ? sibling : sibling - ni) - a;  // g0 + at or g0 + at + 1
+            const int q = write_parent(c, p, n, s_lo[k][sat], s_hi[k][sat], inodes);
+            if (q == 0) break;  // the root: the whole tree lies in this group
+            s_lo[1][g0 + q - a] = c.lo;  // q is l or r, inside the group
+            s_hi[1][g0 + q - a] = c.hi;
         }
     }
-    __syncthreads();
+    if (kGroup == 32)
+        __syncwarp();
+    else
+        __syncthreads();
     if (!pending) return;
-    if (in_word && s_word[word_p - a] == 0ull) return;  // the sibling came and carried on
+    if (in_word && s_word[g0 + word_at] == 0ull) return;  // the sibling came and carried on
     // this thread wrote its own node, so its device-scope release covers it
     climb_global<kKind, true>(c, n, inodes, leaves, store, flags);
 }
@@ -367,21 +394,51 @@ void launch_batch_construct(const uint64_t *sorted_codes, const uint32_t *perm, 
     count_launches(1);
 }
 
+namespace {
+
+template <int kGroup>
+void launch_construct_block(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims, int64_t n,
+                            int kind, float4 *inodes, float4 *leaves, unsigned long long *store, uint32_t *flags,
+                            cudaStream_t s) {
+    constexpr int kCta = GroupShape<kGroup>::kCta;
+    const unsigned blocks = (unsigned)((n + kCta - 1) / kCta);
+    auto k = kind == LBVH_PRIM_POINTS ? construct_block_kernel<LBVH_PRIM_POINTS, kGroup>
+                                      : construct_block_kernel<LBVH_PRIM_BOXES, kGroup>;
+    k<<<blocks, kCta, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags);
+}
+
+}  // namespace
+
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
                       int64_t n, int kind, float4 *inodes, float4 *leaves,
                       unsigned long long *store, uint32_t *flags, cudaStream_t s) {
     if (n <= 0) return;
-    // tuning: LBVH_CONSTRUCT_GLOBAL=1 runs every exchange at device scope (one
-    // phase), LBVH_CONSTRUCT_FENCES=1 that with the fence form of the exchange
+    // tuning: LBVH_CONSTRUCT_GROUP = leaves per phase-1 group of
+    // construct_block_kernel (32, 64, 128 or 256); LBVH_CONSTRUCT_GLOBAL=1 runs
+    // every exchange at device scope (construct_kernel), LBVH_CONSTRUCT_FENCES=1
+    // that with the fence form
+    static const int group = [] {
+        const char *e = getenv("LBVH_CONSTRUCT_GROUP");
+        const int g = e ? atoi(e) : 128;
+        return (g == 32 || g == 64 || g == 256) ? g : 128;
+    }();
     static const bool one_phase = getenv("LBVH_CONSTRUCT_GLOBAL") && atoi(getenv("LBVH_CONSTRUCT_GLOBAL"));
     static const bool fences = getenv("LBVH_CONSTRUCT_FENCES") && atoi(getenv("LBVH_CONSTRUCT_FENCES"));
-    const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
     const bool pts = kind == LBVH_PRIM_POINTS;
-    auto k = !(one_phase || fences)
-                 ? (pts ? construct_block_kernel<LBVH_PRIM_POINTS> : construct_block_kernel<LBVH_PRIM_BOXES>)
-             : fences ? (pts ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_BOXES, false>)
-                      : (pts ? construct_kernel<LBVH_PRIM_POINTS, true> : construct_kernel<LBVH_PRIM_BOXES, true>);
-    k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags);
+    if (one_phase || fences) {
+        const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
+        auto k = fences ? (pts ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_BOXES, false>)
+                        : (pts ? construct_kernel<LBVH_PRIM_POINTS, true> : construct_kernel<LBVH_PRIM_BOXES, true>);
+        k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags);
+    } else if (group == 32) {
+        launch_construct_block<32>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
+    } else if (group == 64) {
+        launch_construct_block<64>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
+    } else if (group == 256) {
+        launch_construct_block<256>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
+    } else {
+        launch_construct_block<128>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
+    }
     count_launches(1);
 }
 
