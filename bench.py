@@ -72,7 +72,7 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
         "construct": (8 + 4 + pb + lb + 32) * n,
         # query + count/position per query, each kept hit, the tree once
         "query_walk": (qb + 8) * nq + 4 * hits + (32 + lb) * n,
-        "query_order": (qb + 8 + 4 * 24) * nq,  # 30-bit order codes: 4 sort passes
+        "query_order": (qb + 4 + 4 * 16) * nq,  # 30-bit order codes as 32-bit keys: 4 sort passes
         "query_scan": 4 * nq + 8 * (nq + 1),
         "query_copy": 16 * nq + 8 * hits,
         # the second walk of the long lists: query + offsets, hits written, then sorted in place

@@ -131,6 +131,11 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
                   int variant_idx = -1, const SortSegments *seg = nullptr);
+// The same sort for 32-bit keys (the default tile shape; segment tables made
+// for tile variant 0 fit it). At most 4 passes.
+bool run_onesweep32(uint32_t *keys_a, uint32_t *vals_a, bool iota, uint32_t *keys_b, uint32_t *vals_b,
+                    int64_t n, int passes, const SortScratch &scratch, Control *ctl, cudaStream_t s,
+                    const SortSegments *seg = nullptr);
 int sort_variant_count();
 // Test hook (lbvh_test_hold_sort_tile): tile `tile` of every sort's first pass
 // publishes nothing, so later tiles' bounded look-back waits run out; -1: off.
@@ -148,6 +153,9 @@ void launch_bounds(const float *prims, int64_t n, int kind, float *partials, flo
                    Control *ctl, cudaStream_t s);
 void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
                    uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
+// The same codes as 32-bit keys (bits <= 30).
+void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
+                   uint32_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
 
 // ---------------------------------------------------------------- construct
 // Algorithm 4 with boxes: writes inodes and leaves (layout above), and uses

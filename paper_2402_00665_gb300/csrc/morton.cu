@@ -229,10 +229,10 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-template <int kKind>
+template <int kKind, typename K>
 __global__ void __launch_bounds__(kThreads)
     encode_kernel(const float *__restrict__ prims, int64_t n, int b,
-                  const float *__restrict__ bounds, uint64_t *__restrict__ codes,
+                  const float *__restrict__ bounds, K *__restrict__ codes,
                   uint32_t *__restrict__ hist, int passes) {
     __shared__ uint32_t s_hist[kMaxPasses * kRadix];
     for (int k = threadIdx.x; k < passes * kRadix; k += kThreads) s_hist[k] = 0;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
     for_each_centroid<kKind>(prims, n, [&](int64_t i, float x, float y, float z) {
         const uint64_t c = morton(x, y, z, g);
-        codes[i] = c;
+        codes[i] = (K)c;
         for (int p = 0; p < passes; ++p)
             atomicAdd(&s_hist[p * kRadix + (uint32_t)((c >> (kRadixBits * p)) & (kRadix - 1))], 1u);
     });
@@ -413,17 +413,28 @@ void launch_bounds(const float *prims, int64_t n, int kind, float *partials, flo
     count_launches(1);
 }
 
-void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s) {
+template <typename K>
+static void encode_as(const float *prims, int64_t n, int kind, int bits, const float *bounds, K *codes,
+                      uint32_t *hist, int hist_passes, cudaStream_t s) {
     const int blocks = bounds_blocks(n);
     const int b = bits / 3;
     if (kind == LBVH_PRIM_POINTS)
-        encode_kernel<LBVH_PRIM_POINTS><<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
-                                                                    hist_passes);
+        encode_kernel<LBVH_PRIM_POINTS, K><<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
+                                                                       hist_passes);
     else
-        encode_kernel<LBVH_PRIM_BOXES><<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
-                                                                   hist_passes);
+        encode_kernel<LBVH_PRIM_BOXES, K><<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
+                                                                      hist_passes);
     count_launches(1);
+}
+
+void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
+                   uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s) {
+    encode_as(prims, n, kind, bits, bounds, codes, hist, hist_passes, s);
+}
+
+void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
+                   uint32_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s) {
+    encode_as(prims, n, kind, bits, bounds, codes, hist, hist_passes, s);
 }
 
 }  // namespace lbvh

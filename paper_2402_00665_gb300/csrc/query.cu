@@ -190,32 +190,6 @@ __device__ __forceinline__ void load_node(const float4 *base, int unit, bool lea
 // that satisfies the predicate, leaves in increasing sorted position. Returns
 // false if the walk ran past 2(2n-1) steps or met an id outside the tree (a
 // corrupt tree).
-// Algorithm 1 from `node` on, stopping early when on_leaf returns false: the
-// return value is then the next node to visit (so the walk can resume there),
-// else a terminal id (outside [0, 2n-1)); `steps` carries the step count and
-// a corrupt tree (more than 2(2n-1) steps) returns 2n.
-template <int kP, typename Q, typename F>
-__device__ __forceinline__ int walk_from(const TreeView &t, const Q &q, int node, uint32_t &steps,
-                                         F &&on_leaf) {
-    const int ni = (int)t.n - 1;
-    const int nodes = 2 * (int)t.n - 1;
-    const uint32_t max_steps = 2u * (uint32_t)nodes;
-    const float4 *base = t.inodes;  // leaves follow the internal records
-    while ((uint32_t)node < (uint32_t)nodes) {
-        if (++steps > max_steps) return nodes + 1;
-        const bool leaf = node >= ni;
-        const int unit = kP == LBVH_PRIM_BOXES ? 2 * node : (leaf ? node + ni : 2 * node);
-        float4 a, b;
-        load_node<kP>(base, unit, leaf, a, b);
-        const bool hit = hits(q, xyz(a), xyz(b));
-        const uint32_t word = __float_as_uint(a.w);
-        // internal: left child on a hit, else skip; leaf k: position k+1
-        node = leaf ? node + 1 - ((word & kLeafSkipInternal) ? ni : 0) : __float_as_int(hit ? a.w : b.w);
-        if (hit && leaf && !on_leaf(word & kLeafIndexMask)) return node;
-    }
-    return node;
-}
-
 template <int kP, typename Q, typename F>
 __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf) {
     const int ni = (int)t.n - 1;

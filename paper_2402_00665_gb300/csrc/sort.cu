@@ -77,7 +77,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return before + x - v;
 }
 
-template <int kItems>
+template <int kItems, typename K = uint64_t>
 struct SortSmem {
     static constexpr int kTile = kSortThreads * kItems;
     uint32_t warp_hist[kWarps][kRadix];  // per-warp digit counts, then per-warp offsets
@@ -87,7 +87,7 @@ struct SortSmem {
     uint32_t tile;
     int32_t seg;                         // segment of the tile (segmented sorts)
     uint32_t next_hist[kRadix];          // digit counts of the next pass
-    uint64_t keys[kTile];
+    K keys[kTile];
     uint32_t vals[kTile];
 };
 
@@ -115,15 +115,15 @@ struct SegArgs {
 // segment; its keys start at off[seg] + (tile - tile_first[seg]) * kTile, its
 // digit counts come from and go to the segment's rows of the histograms, and
 // its look-back chain ends at the segment's first tile.
-template <bool kIota, int kItems, int kMinBlocks, bool kBallot, bool kSeg>
+template <bool kIota, int kItems, int kMinBlocks, bool kBallot, bool kSeg, typename K = uint64_t>
 __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
-    onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                    uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
+    onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                    K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
                     int shift, const uint32_t *__restrict__ pass_hist, uint32_t *lookback,
                     uint32_t *lookback_next, uint32_t *ticket, int64_t tiles,
                     uint32_t *flags, uint32_t *next_hist, SegArgs seg, int64_t hold_tile,
                     int64_t prefetch_ahead) {
-    using Smem = SortSmem<kItems>;
+    using Smem = SortSmem<kItems, K>;
     constexpr int kTile = Smem::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
         if (ft < tiles) {
             const int64_t fb = ft * kTile;
             const int64_t fcnt = min((int64_t)kTile, n - fb);
-            const uint32_t kbytes = (uint32_t)((fcnt * 8) & ~15ll);  // rounded down: stays inside the array
+            const uint32_t kbytes = (uint32_t)((fcnt * (int64_t)sizeof(K)) & ~15ll);  // rounded down: stays inside
             if (kbytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(keys_in + fb), "r"(kbytes) : "memory");
             if (!kIota) {
                 const uint32_t vbytes = (uint32_t)((fcnt * 4) & ~15ll);
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
 
     // ---- load: warp w owns keys [w*32*kItems, (w+1)*32*kItems) of the tile,
     // round j lane l holds key w*32*kItems + 32*j + l
-    uint64_t key[kItems];
+    K key[kItems];
     uint32_t val[kItems];
     uint32_t rank[kItems];
 #pragma unroll
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
             key[j] = keys_in[g];
             val[j] = kIota ? (uint32_t)g : vals_in[g];
         } else {
-            key[j] = ~0ull;  // ranks after every real key of digit 0xff
+            key[j] = ~K(0);  // ranks after every real key of digit 0xff
             val[j] = 0;
         }
     }
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
     for (int j = 0; j < kItems; ++j) {
         const int s = j * kSortThreads + threadIdx.x;
         if (s < valid) {
-            const uint64_t k = sm.keys[s];
+            const K k = sm.keys[s];
             const uint32_t dj = (uint32_t)(k >> shift) & (kRadix - 1);
             const int64_t pos = (int64_t)sm.out_base[dj] + s;
             if (pos < seg_begin || pos >= seg_end) {  // only after a timed-out look-back
@@ -290,28 +290,32 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
     }
 }
 
-using PassKernel = void (*)(const uint64_t *, const uint32_t *, uint64_t *, uint32_t *, int64_t, int,
-                            const uint32_t *, uint32_t *, uint32_t *, uint32_t *, int64_t, uint32_t *,
-                            uint32_t *, SegArgs, int64_t, int64_t);
+template <typename K>
+using PassKernelT = void (*)(const K *, const uint32_t *, K *, uint32_t *, int64_t, int, const uint32_t *,
+                             uint32_t *, uint32_t *, uint32_t *, int64_t, uint32_t *, uint32_t *, SegArgs,
+                             int64_t, int64_t);
+using PassKernel = PassKernelT<uint64_t>;
 
-struct Variant {
+template <typename K = uint64_t>
+struct VariantT {
     int items, min_blocks;
     bool ballot;
-    PassKernel first, rest;          // payload = index / payload read
-    PassKernel seg_first, seg_rest;  // the same, segmented
+    PassKernelT<K> first, rest;          // payload = index / payload read
+    PassKernelT<K> seg_first, seg_rest;  // the same, segmented
     size_t smem;
 };
+using Variant = VariantT<uint64_t>;
 
-template <int kItems, int kMinBlocks, bool kBallot>
-Variant make_variant() {
-    return Variant{kItems,
-                   kMinBlocks,
-                   kBallot,
-                   onesweep_kernel<true, kItems, kMinBlocks, kBallot, false>,
-                   onesweep_kernel<false, kItems, kMinBlocks, kBallot, false>,
-                   onesweep_kernel<true, kItems, kMinBlocks, kBallot, true>,
-                   onesweep_kernel<false, kItems, kMinBlocks, kBallot, true>,
-                   sizeof(SortSmem<kItems>)};
+template <int kItems, int kMinBlocks, bool kBallot, typename K = uint64_t>
+VariantT<K> make_variant() {
+    return VariantT<K>{kItems,
+                       kMinBlocks,
+                       kBallot,
+                       onesweep_kernel<true, kItems, kMinBlocks, kBallot, false, K>,
+                       onesweep_kernel<false, kItems, kMinBlocks, kBallot, false, K>,
+                       onesweep_kernel<true, kItems, kMinBlocks, kBallot, true, K>,
+                       onesweep_kernel<false, kItems, kMinBlocks, kBallot, true, K>,
+                       sizeof(SortSmem<kItems, K>)};
 }
 
 // Tile shapes the library is compiled with. The first entry is the default;
@@ -336,6 +340,21 @@ const Variant *variant_table(int *count) {
     (void)configured;
     *count = (int)(sizeof table / sizeof table[0]);
     return table;
+}
+
+// 32-bit keys (query orders of up to 30 bits): the default tile shape only;
+// its tiles hold as many keys as variant 0's, so segment tables made for
+// variant 0 serve it.
+const VariantT<uint32_t> &variant32() {
+    static const VariantT<uint32_t> v = [] {
+        const VariantT<uint32_t> w = make_variant<12, 4, true, uint32_t>();
+        for (PassKernelT<uint32_t> k : {w.first, w.rest, w.seg_first, w.seg_rest}) {
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem);
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
+        return w;
+    }();
+    return v;
 }
 
 const Variant &variant(int idx = -1) {
@@ -406,7 +425,7 @@ int64_t sort_tile_keys_min() {
 // (a sweep of 76..1216 at 2^25 keys: 0.313 ms per pass from 152 to 456,
 // 0.327 ms without prefetch). LBVH_SORT_PREFETCH=0 turns it off, any other
 // value sets the distance (tuning sweeps).
-static int64_t prefetch_tiles(const Variant &) {
+static int64_t prefetch_tiles() {
     static const int64_t env = [] {
         const char *e = getenv("LBVH_SORT_PREFETCH");
         return e ? (int64_t)atoll(e) : -1;
@@ -415,34 +434,34 @@ static int64_t prefetch_tiles(const Variant &) {
     return (int64_t)device_sm_count() * 2;
 }
 
-bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
-                  uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
-                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx,
-                  const SortSegments *seg) {
+template <typename K>
+static bool run_passes(const VariantT<K> &v, K *keys_a, uint32_t *vals_a, bool iota, K *keys_b, uint32_t *vals_b,
+                       int64_t n, int passes, const SortScratch &scratch, Control *ctl, cudaStream_t s,
+                       cudaEvent_t (*pass_events)[2], const SortSegments *seg) {
     if (n <= 0 || passes <= 0) return false;
-    const Variant &v = variant(variant_idx);
     const int64_t tiles = seg ? seg->tiles
                               : (n + (int64_t)kSortThreads * v.items - 1) / ((int64_t)kSortThreads * v.items);
     if (tiles <= 0) return false;
     const SegArgs sa{seg ? seg->off : nullptr, seg ? seg->tile_first : nullptr, seg ? seg->count : 0};
     const int64_t hist_stride = (int64_t)kRadix * (seg ? seg->count : 1);
     cudaMemsetAsync(scratch.lookback, 0, (size_t)tiles * kRadix * sizeof(uint32_t), s);
-    uint64_t *kin = keys_a, *kout = keys_b;
+    K *kin = keys_a, *kout = keys_b;
     uint32_t *vin = vals_a, *vout = vals_b;
     for (int p = 0; p < passes; ++p) {
         uint32_t *cur = scratch.lookback + (p & 1) * scratch.lookback_words;
         uint32_t *nxt = scratch.lookback + ((p + 1) & 1) * scratch.lookback_words;
         const uint32_t *hist = scratch.hist + p * hist_stride;
         if (pass_events) cudaEventRecord(pass_events[p][0], s);
-        PassKernel k = seg ? ((p == 0 && iota) ? v.seg_first : v.seg_rest) : ((p == 0 && iota) ? v.first : v.rest);
+        PassKernelT<K> k =
+            seg ? ((p == 0 && iota) ? v.seg_first : v.seg_rest) : ((p == 0 && iota) ? v.first : v.rest);
         uint32_t *next_hist = p + 1 < passes ? scratch.hist + (p + 1) * hist_stride : nullptr;
         const int64_t hold = p == 0 ? g_hold_tile.load(std::memory_order_relaxed) : -1;
         k<<<(unsigned)tiles, kSortThreads, v.smem, s>>>(kin, vin, kout, vout, n, kRadixBits * p, hist, cur,
                                                          nxt, &ctl->sort_ticket[p], tiles, &ctl->build_flags,
-                                                         next_hist, sa, hold, prefetch_tiles(v));
+                                                         next_hist, sa, hold, prefetch_tiles());
         if (pass_events) cudaEventRecord(pass_events[p][1], s);
         count_launches(1);
-        uint64_t *tk = kin;
+        K *tk = kin;
         kin = kout;
         kout = tk;
         uint32_t *tv = vin;
@@ -450,6 +469,22 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
         vout = tv;
     }
     return (passes & 1) != 0;
+}
+
+bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
+                  uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
+                  Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx,
+                  const SortSegments *seg) {
+    return run_passes(variant(variant_idx), keys_a, vals_a, iota, keys_b, vals_b, n, passes, scratch, ctl, s,
+                      pass_events, seg);
+}
+
+bool run_onesweep32(uint32_t *keys_a, uint32_t *vals_a, bool iota, uint32_t *keys_b, uint32_t *vals_b,
+                    int64_t n, int passes, const SortScratch &scratch, Control *ctl, cudaStream_t s,
+                    const SortSegments *seg) {
+    if (passes > 4) passes = 4;  // four 8-bit digits cover a 32-bit key
+    return run_passes(variant32(), keys_a, vals_a, iota, keys_b, vals_b, n, passes, scratch, ctl, s, nullptr,
+                      seg);
 }
 
 }  // namespace lbvh
