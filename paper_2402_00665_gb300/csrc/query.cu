@@ -356,25 +356,52 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// Ascending bitonic sorting network over 32 registers (indices are compile
-// time constants after unrolling).
-__device__ __forceinline__ void sort32(uint32_t (&v)[32]) {
+// Batcher's odd-even merge sort of v[0..kN) (kN a power of two), keeping only
+// the comparators inside v[0..kAct). Every comparator puts the smaller value
+// at the lower index, so padding values ~0u at the top never move and the
+// comparators that reach them do nothing: the pruned network sorts kAct
+// values (8: 19 comparators, 16: 63, 24: 132, 32: 191; a bitonic network
+// over 32 takes 240). Written as templates so that every index is a
+// compile-time constant and v stays in registers.
+template <int kAct>
+__device__ __forceinline__ void compare_swap(uint32_t (&v)[32], int x, int y) {
+    if (y < kAct) {
+        const uint32_t a = v[x], b = v[y];
+        v[x] = min(a, b);
+        v[y] = max(a, b);
+    }
+}
+
+// merges the two sorted halves of the elements lo, lo + r, lo + 2r, ... of v[lo, lo + n)
+template <int kLo, int kN, int kR, int kAct>
+struct OddEvenMerge {
+    static __device__ __forceinline__ void run(uint32_t (&v)[32]) {
+        constexpr int m = 2 * kR;
+        if constexpr (m < kN) {
+            OddEvenMerge<kLo, kN, m, kAct>::run(v);
+            OddEvenMerge<kLo + kR, kN, m, kAct>::run(v);
 #pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-            for (int x = 0; x < 32; ++x) {
-                const int y = x ^ j;
-                if (y > x) {
-                    const uint32_t lo = min(v[x], v[y]), hi = max(v[x], v[y]);
-                    const bool up = (x & k) == 0;
-                    v[x] = up ? lo : hi;
-                    v[y] = up ? hi : lo;
-                }
-            }
+            for (int i = kLo + kR; i + kR < kLo + kN; i += m) compare_swap<kAct>(v, i, i + kR);
+        } else {
+            compare_swap<kAct>(v, kLo, kLo + kR);
         }
     }
+};
+
+template <int kLo, int kN, int kAct>
+struct OddEvenSort {
+    static __device__ __forceinline__ void run(uint32_t (&v)[32]) {
+        if constexpr (kN > 1) {
+            OddEvenSort<kLo, kN / 2, kAct>::run(v);
+            OddEvenSort<kLo + kN / 2, kN / 2, kAct>::run(v);
+            OddEvenMerge<kLo, kN, 1, kAct>::run(v);
+        }
+    }
+};
+
+template <int kN, int kAct>
+__device__ __forceinline__ void merge_sort_net(uint32_t (&v)[32]) {
+    OddEvenSort<0, kN, kAct>::run(v);
 }
 
 // Ascending bitonic sort of 64 values held by a warp, value e in lane e % 32
@@ -439,9 +466,19 @@ __global__ void __launch_bounds__(kThreads)
         v[4 * j4 + 2] = 4 * j4 + 2 < (int)c ? w.z : ~0u;
         v[4 * j4 + 3] = 4 * j4 + 3 < (int)c ? w.w : ~0u;
     }
-    if (__any_sync(0xffffffffu, c > 1)) sort32(v);
+    // the network for the warp's longest list (lists are padded with ~0u)
+    const uint32_t cmax = __reduce_max_sync(0xffffffffu, c);
+    if (cmax > 24)
+        merge_sort_net<32, 32>(v);
+    else if (cmax > 16)
+        merge_sort_net<32, 24>(v);
+    else if (cmax > 8)
+        merge_sort_net<16, 16>(v);
+    else if (cmax > 1)
+        merge_sort_net<8, 8>(v);
 #pragma unroll
-    for (int j = 0; j < kRegSort; ++j) s_lists[warp][lane][j] = v[j];
+    for (int j = 0; j < kRegSort; ++j)
+        if (j < (int)cmax) s_lists[warp][lane][j] = v[j];
     __syncwarp();
     for (int s = 0; s < 32; ++s) {
         const uint32_t cs = __shfl_sync(0xffffffffu, c, s);

@@ -295,6 +295,33 @@ def test_long_hit_lists_use_the_fixup_sort(radius):
     assert_csr_equal(off, hits, *oracle.query(o, q, oracle.SPHERE, radius=np.float32(radius)))
 
 
+def test_hit_lists_of_every_length_and_warp_maximum():
+    """Lists of 0..~36 hits with the longest list of each group of 32
+    consecutive queries in every range of the copy's pruned sorting networks
+    (<= 8, 16, 24, 32, and past the register sort), primitive ids in random
+    order along the line."""
+    lbvh = L()
+    rng = np.random.default_rng(21)
+    n = 2000
+    pts = np.zeros((n, 3), np.float32)
+    pts[:, 0] = rng.permutation(n).astype(np.float32)
+    scales = [0.3, 2.6, 3.9, 4.4, 7.9, 8.4, 11.9, 12.4, 15.9, 17.6]
+    nq = 32 * len(scales) * 4
+    q = np.zeros((nq, 3), np.float32)
+    q[:, 0] = rng.integers(20, n - 20, nq).astype(np.float32)
+    q[:, 1] = np.float32(0.1)
+    radii = np.concatenate([rng.random(32).astype(np.float32) * np.float32(scales[g % len(scales)])
+                            for g in range(nq // 32)]).astype(np.float32)
+    t = gpu_build(pts, lbvh.POINTS, 30)
+    off, hits = t.query(q, lbvh.SPHERE, radii=radii)
+    o = oracle.build(pts, oracle.POINTS, 30)
+    ooff, ohits = oracle.query(o, q, oracle.SPHERE, radii=radii)
+    assert_csr_equal(off, hits, ooff, ohits)
+    lens = np.diff(ooff).reshape(-1, 32).max(axis=1)
+    for lo, hi in ((0, 1), (2, 8), (9, 16), (17, 24), (25, 32), (33, 64)):
+        assert ((lens >= lo) & (lens <= hi)).any(), (lo, hi, lens)
+
+
 def test_all_equal_points_every_query_hits_everything():
     lbvh = L()
     pts = np.full((9000, 3), 0.5, np.float32)
