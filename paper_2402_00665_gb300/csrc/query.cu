@@ -252,7 +252,7 @@ __device__ __forceinline__ void spill_put(const QueryScratch &qs, Control *ctl, 
 // hits go to the slot, later ones to spill chunks. Writes (count, i) and, for
 // a long list, its overflow-list entry (tagged when all its hits are in slot
 // + chunks).
-template <int kQ, int kP>
+template <int kQ, int kP, bool kPairs>
 __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs &qa, const QueryScratch &qs,
                                              Control *ctl, int64_t i, int64_t qi, bool walk_ok) {
     uint32_t cnt = 0;
@@ -260,11 +260,28 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
     if (walk_ok) {
         const auto q = QueryOf<kQ>::load(qa, qi);
         uint32_t *slot = qs.slots + i * kSlot;
+        // kPairs: hits go to the slot two at a time (one 8-byte store; words
+        // past the count are never read). Point trees, one tree: walk 16.19
+        // -> 16.00 ms on 2^25 uniform points at 40 registers instead of 32;
+        // on box trees the extra registers cost more (D3 walk 8.39 -> 8.49
+        // ms), and the batched kernel, held to 32, would spill.
+        uint2 buf = make_uint2(0u, 0u);
         const bool ok = walk<kP>(t, q, [&](uint32_t id) {
-            if (cnt < (uint32_t)kSlot) __stcs(slot + cnt, id);
-            else spill_put(qs, ctl, i, cnt, id, cur);
+            if (cnt < (uint32_t)kSlot) {
+                if (!kPairs) {
+                    __stcs(slot + cnt, id);
+                } else if (cnt & 1u) {
+                    buf.y = id;
+                    __stcs(reinterpret_cast<uint2 *>(slot + cnt - 1), buf);
+                } else {
+                    buf.x = id;
+                }
+            } else {
+                spill_put(qs, ctl, i, cnt, id, cur);
+            }
             ++cnt;
         });
+        if (kPairs && cnt < (uint32_t)kSlot && (cnt & 1u)) __stcs(reinterpret_cast<uint2 *>(slot + cnt - 1), buf);
         if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
     }
     __stcs(qs.count_pos + qi, make_uint2(cnt, (uint32_t)i));  // streamed: keep L2 for the tree
@@ -290,7 +307,7 @@ __global__ void __launch_bounds__(kThreads)
     if (first >= qa.nq) return;
     const bool walk_ok = t.n > 0 && ctl->build_flags == 0;
     if (K == 1) {
-        collect_walk<kQ, kP>(t, qa, qs, ctl, first, thread_query(qa, first), walk_ok);
+        collect_walk<kQ, kP, kP == LBVH_PRIM_POINTS>(t, qa, qs, ctl, first, thread_query(qa, first), walk_ok);
         return;
     }
     // K > 1 (tuning): lock-step walks; lists past the slot take the second walk
@@ -771,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 8)  // at most 32 registers: full oc
     const int b = instance_of(bt.query_off, bt.count, qi);
     const int64_t n = bt.prim_off[b + 1] - bt.prim_off[b];
     const TreeView t{nodes + bt.node_start[b], nullptr, n, kP};
-    collect_walk<kQ, kP>(t, qa, qs, ctl, i, qi, n > 0 && ctl->build_flags == 0);
+    collect_walk<kQ, kP, false>(t, qa, qs, ctl, i, qi, n > 0 && ctl->build_flags == 0);
 }
 
 // Overflow lists whose number is known only on the device: a fixed grid
