@@ -148,6 +148,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVED_WORKLOADS),
                     default="uniform_2^25_63bit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-staged", action="store_true",
+                    help="e2e results into device arrays, then copied to host (instead of written to host directly)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
@@ -489,17 +491,26 @@ def run_gpu(args, world, rank, local):
         dpts = torch.empty_like(pts)
         dq = torch.empty_like(qpts)
         def e2e_step():
-            # (copying the queries on a second stream during the build, and the
-            # offsets during the hit copy, measured slower: the host links are
-            # shared and the build's sort competes for HBM)
+            # inputs in by copy; results through lbvh_query_into_host, which
+            # stages the CSR on the device chunk by chunk and copies each chunk
+            # to the page-locked host arrays while the next one runs, or with
+            # --e2e-staged into device arrays and then copied (copying the
+            # queries on a second stream during the build, and the offsets
+            # during the hit copy, measured slower: the host links are shared
+            # and the build's sort competes for HBM)
             dpts.copy_(host_pts, non_blocking=True)
             dq.copy_(host_q, non_blocking=True)
             tree.build(dpts, kind, bits)
-            s, tot = tree.query_into(dq, qkind, offsets, hits, radius=float(radius))
-            if s != lbvh.OK:
-                raise lbvh.LbvhError(s, "lbvh_query_into")
-            host_off.copy_(offsets, non_blocking=True)
-            host_hits[:tot].copy_(hits[:tot], non_blocking=True)
+            if args.e2e_staged:
+                s, tot = tree.query_into(dq, qkind, offsets, hits, radius=float(radius))
+                if s != lbvh.OK:
+                    raise lbvh.LbvhError(s, "lbvh_query_into")
+                host_off.copy_(offsets, non_blocking=True)
+                host_hits[:tot].copy_(hits[:tot], non_blocking=True)
+            else:
+                s, tot = tree.query_into_host(dq, qkind, host_off, host_hits, radius=float(radius))
+                if s != lbvh.OK:
+                    raise lbvh.LbvhError(s, "lbvh_query_into_host")
             torch.cuda.current_stream(dev).synchronize()
             return tot
 
@@ -516,8 +527,10 @@ def run_gpu(args, world, rank, local):
         e2e = {"value": n * world / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int((pts.numel() + qpts.numel()) * 4),
                "d2h_bytes_per_step": int((nq + 1) * 8 + tot * 4),
-               "note": "pinned host primitives and queries -> device, build, query, "
-                       "CSR offsets + hits -> pinned host"}
+               "note": "pinned host primitives and queries -> device, build, query, CSR offsets + hits "
+                       + ("-> device, then copied to pinned host" if args.e2e_staged
+                          else "-> pinned host by lbvh_query_into_host (chunks staged on the device, "
+                               "each copied while the next runs)")}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

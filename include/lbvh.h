@@ -219,6 +219,23 @@ lbvh_status lbvh_query_into(lbvh_tree_t tree, const float *d_queries, int64_t nq
                             uint32_t *d_hits, uint64_t capacity, uint64_t *total,
                             lbvh_stream_t stream);
 
+/* As lbvh_query_into, but the CSR arrays are in page-locked host memory
+ * (cudaMallocHost, cudaHostAlloc or cudaHostRegister): h_offsets int64[nq+1],
+ * h_hits uint32[capacity], owned by the caller. The queries go through the
+ * device path in chunks (in index order; at least 2^23 queries each, at most
+ * 4 chunks), each into one of two device staging areas that the tree owns; a
+ * chunk's offsets and hits are copied to the host on the tree's own copy
+ * stream while the GPU works on the next chunk. Like every call here it
+ * returns once the last chunk is counted; the host arrays are complete once
+ * `stream` has been synchronised (it waits for the copies). Over capacity:
+ * the offsets are still written, no hit is, LBVH_ERR_CAPACITY with the full
+ * *total. Host memory that is not page-locked (pageable or device memory)
+ * -> LBVH_ERR_INVALID, nothing is launched. Other errors as lbvh_query_into. */
+lbvh_status lbvh_query_into_host(lbvh_tree_t tree, const float *d_queries, int64_t nq, int qkind,
+                                 const float *d_radii, float radius, int64_t *h_offsets,
+                                 uint32_t *h_hits, uint64_t capacity, uint64_t *total,
+                                 lbvh_stream_t stream);
+
 /* As lbvh_query_into, but the library allocates the CSR arrays
  * (*d_offsets int64[nq+1], *d_hits uint32[*total]); free them with lbvh_free. */
 lbvh_status lbvh_query(lbvh_tree_t tree, const float *d_queries, int64_t nq, int qkind,

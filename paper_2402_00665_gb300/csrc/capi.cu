@@ -179,6 +179,11 @@ struct lbvh_tree_s {
     DevBuf counts, tile_sums, overflow, slots, spill_head, spill;
     DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
     DevBuf vscratch;                       // scratch of the Karras / Apetrei builds
+    // lbvh_query_into_host: device staging of two chunks' CSR, the stream
+    // that copies them to the host, and its events
+    DevBuf stage_off[2], stage_hits[2];
+    cudaStream_t xfer = nullptr;
+    cudaEvent_t staged[2] = {nullptr, nullptr}, drained[2] = {nullptr, nullptr}, xfer_done = nullptr;
     const float *prims_ptr = nullptr;      // the last build's input (self-queries)
     int64_t spill_nq = 0;                  // query count the spill pool was sized for
     lbvh::Control *h_ctl = nullptr;  // pinned mirror of the control block (from pinned_controls())
@@ -758,11 +763,14 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
                       &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                       &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                       &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots, &t->vscratch, &t->spill_head,
-                      &t->spill})
+                      &t->spill, &t->stage_off[0], &t->stage_off[1], &t->stage_hits[0], &t->stage_hits[1]})
         b->release(cudaStreamPerThread);
     pinned_controls().put(t->h_ctl);
     if (t->built) cudaEventDestroy(t->built);
     if (t->used) cudaEventDestroy(t->used);
+    for (cudaEvent_t e : {t->staged[0], t->staged[1], t->drained[0], t->drained[1], t->xfer_done})
+        if (e) cudaEventDestroy(e);
+    if (t->xfer) cudaStreamDestroy(t->xfer);
     t->prof.release();
     delete t;
 }
@@ -1091,6 +1099,113 @@ lbvh_status lbvh_query_into(lbvh_tree_t t, const float *d_queries, int64_t nq, i
     if (st != LBVH_OK) return st;
     if (*total > capacity) return LBVH_ERR_CAPACITY;
     return query_fill(t, qa, d_offsets, d_hits, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+bool page_locked(const void *h) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        (void)cudaGetLastError();  // not a pointer CUDA knows: leave no sticky error
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// Queries per chunk of lbvh_query_into_host: at least 2^23, at most 4
+// chunks. 2^25 sphere queries (17 hits each): 27.0 ms with 3 or 4 chunks,
+// 27.8 with 2, 29.2 with 8, 35.5 with 16, against 32.6 ms for the query and
+// the copies one after the other (each chunk adds a host round trip, and
+// its copy shares the link and L2 with the next chunk's walk).
+// LBVH_HOST_CHUNK=<queries> and LBVH_HOST_CHUNKS=<count> override both
+// (tuning sweeps).
+int64_t host_chunk_min() {
+    static const int64_t v = [] {
+        const char *e = getenv("LBVH_HOST_CHUNK");
+        const long long x = e ? atoll(e) : 0;
+        return x > 0 ? (int64_t)x : (int64_t(1) << 23);
+    }();
+    return v;
+}
+int64_t host_chunks_max() {
+    static const int64_t v = [] {
+        const char *e = getenv("LBVH_HOST_CHUNKS");
+        const long long x = e ? atoll(e) : 0;
+        return x > 0 ? (int64_t)x : 4;
+    }();
+    return v;
+}
+
+lbvh_status host_stream(lbvh_tree_t t) {
+    if (t->xfer) return LBVH_OK;
+    LBVH_CUDA(cudaStreamCreateWithFlags(&t->xfer, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&t->staged[0], &t->staged[1], &t->drained[0], &t->drained[1], &t->xfer_done})
+        LBVH_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return LBVH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Chunks of queries in index order, each through the device path into one of
+// two staging areas; the copy of chunk k to the host runs on the tree's copy
+// stream while the GPU works on chunk k+1 (chunk k+2 reuses the area once that
+// copy is done). The caller's stream waits for the last copy.
+lbvh_status lbvh_query_into_host(lbvh_tree_t t, const float *d_queries, int64_t nq, int qkind,
+                                 const float *d_radii, float radius, int64_t *h_offsets, uint32_t *h_hits,
+                                 uint64_t capacity, uint64_t *total, lbvh_stream_t stream) {
+    NvtxRange nvtx_range("lbvh_query_into_host");
+    using namespace lbvh;
+    lbvh_status st = check_query_args(t, d_queries, nq, qkind, d_radii, radius);
+    if (st != LBVH_OK) return st;
+    if (!h_offsets || !total || (capacity > 0 && !h_hits)) return LBVH_ERR_INVALID;
+    if (!page_locked(h_offsets) || (capacity > 0 && !page_locked(h_hits))) return LBVH_ERR_INVALID;
+    if ((st = host_stream(t)) != LBVH_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int dim = qkind == LBVH_Q_SPHERE ? 3 : (qkind == LBVH_Q_BOX ? 6 : 8);
+    const int64_t cmin = host_chunk_min();
+    const int64_t chunks = nq <= cmin ? 1 : std::min<int64_t>(host_chunks_max(), (nq + cmin - 1) / cmin);
+    const int64_t per = (nq + chunks - 1) / chunks;
+    uint64_t base = 0;
+    bool over = false;
+    for (int64_t k = 0; k < chunks; ++k) {
+        const int64_t q0 = k * per, m = std::min(per, nq - q0);
+        if (m < 0 || (m == 0 && k > 0)) break;
+        const int b = (int)(k & 1);
+        if (k >= 2) LBVH_CUDA(cudaStreamWaitEvent(s, t->drained[b], 0));  // its staging area is free again
+        LBVH_CUDA(t->stage_off[b].ensure((size_t)(m + 1) * 8, s));
+        int64_t *soff = t->stage_off[b].as<int64_t>();
+        QueryArgs qa{d_queries + q0 * dim, m, qkind, d_radii ? d_radii + q0 : nullptr, radius, nullptr};
+        uint64_t tot = 0;
+        if ((st = query_count(t, qa, soff, s, &tot)) != LBVH_OK) break;
+        const bool fits = !over && base + tot <= capacity;
+        over = !fits;
+        if (fits && tot > 0) {
+            LBVH_CUDA(t->stage_hits[b].ensure((size_t)tot * 4, s));
+            if ((st = query_fill(t, qa, soff, t->stage_hits[b].as<uint32_t>(), s)) != LBVH_OK) break;
+        }
+        if (base > 0) launch_offsets_add(soff, m + 1, (int64_t)base, s);
+        LBVH_CUDA(cudaEventRecord(t->staged[b], s));
+        LBVH_CUDA(cudaStreamWaitEvent(t->xfer, t->staged[b], 0));
+        LBVH_CUDA(cudaMemcpyAsync(h_offsets + q0, soff, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, t->xfer));
+        if (fits && tot > 0)
+            LBVH_CUDA(cudaMemcpyAsync(h_hits + base, t->stage_hits[b].p, (size_t)tot * 4, cudaMemcpyDeviceToHost,
+                                      t->xfer));
+        LBVH_CUDA(cudaEventRecord(t->drained[b], t->xfer));
+        base += tot;
+    }
+    // the caller's stream (and the tree's `used` event) cover the copies
+    LBVH_CUDA(cudaEventRecord(t->xfer_done, t->xfer));
+    LBVH_CUDA(cudaStreamWaitEvent(s, t->xfer_done, 0));
+    if (!t->used) LBVH_CUDA(cudaEventCreateWithFlags(&t->used, cudaEventDisableTiming));
+    LBVH_CUDA(cudaEventRecord(t->used, s));
+    t->queried = true;
+    *total = base;
+    if (st != LBVH_OK) return st;
+    return over ? LBVH_ERR_CAPACITY : LBVH_OK;
 }
 
 lbvh_status lbvh_query(lbvh_tree_t t, const float *d_queries, int64_t nq, int qkind,
@@ -1444,7 +1559,8 @@ lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cud
 
 void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s) {
     for (DevBuf *b : {&t->counts, &t->tile_sums, &t->overflow, &t->slots, &t->qkeys[0], &t->qkeys[1],
-                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->spill_head, &t->spill})
+                      &t->qvals[0], &t->qvals[1], &t->qlookback, &t->spill_head, &t->spill,
+                      &t->stage_off[0], &t->stage_off[1], &t->stage_hits[0], &t->stage_hits[1]})
         b->release(s);
     t->spill_nq = 0;
 }

@@ -214,6 +214,8 @@ void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScra
 // offsets[0..nq] = exclusive scan of count_pos[.].x (offsets[nq] = total =
 // ctl->total).
 int64_t scan_tile_count(int64_t nq);
+// offsets[0..n) += base (a chunk's CSR offsets moved to its place in the whole)
+void launch_offsets_add(int64_t *offsets, int64_t n, int64_t base, cudaStream_t s);
 void launch_exclusive_scan(const uint2 *count_pos, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s);
 // Short lists from the scratch buffer to their CSR positions.

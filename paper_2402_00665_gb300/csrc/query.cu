@@ -944,6 +944,19 @@ void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt,
 
 int64_t scan_tile_count(int64_t nq) { return (nq + kScanTile - 1) / kScanTile; }
 
+namespace {
+__global__ void __launch_bounds__(kThreads) offsets_add_kernel(int64_t *off, int64_t n, int64_t base) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < n) off[i] += base;
+}
+}  // namespace
+
+void launch_offsets_add(int64_t *offsets, int64_t n, int64_t base, cudaStream_t s) {
+    if (n <= 0) return;
+    offsets_add_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(offsets, n, base);
+    count_launches(1);
+}
+
 void launch_exclusive_scan(const uint2 *counts, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s) {
     const int64_t tiles = scan_tile_count(nq);

@@ -45,6 +45,7 @@ SIGNATURES = {
     "lbvh_tree_bytes": (_I32, [_P, _P]),
     "lbvh_tree_export": (_I32, [_P] * 9),
     "lbvh_query_into": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _U64, _P, _P]),
+    "lbvh_query_into_host": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _U64, _P, _P]),
     "lbvh_query": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _P, _P]),
     "lbvh_free": (None, [_P]),
     "lbvh_morton_codes": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
@@ -273,6 +274,19 @@ class Tree:
         st = self._lib.lbvh_query_into(self._h, _ptr(q), q.shape[0], qkind, _ptr(r), float(radius),
                                        _ptr(offsets), _ptr(hits), cap, ctypes.byref(total),
                                        _stream(stream))
+        return st, total.value
+
+    def query_into_host(self, queries, qkind, offsets, hits, radius: float = 0.0, radii=None, stream=None):
+        """lbvh_query_into_host: the CSR written by the kernels straight into
+        page-locked host tensors (``pin_memory()``); returns (status, total)."""
+        torch = _torch()
+        q = _dev(queries, torch.float32, _QDIM[qkind])
+        r = None if radii is None else _dev(radii, torch.float32).reshape(-1)
+        total = ctypes.c_uint64()
+        cap = 0 if hits is None else hits.numel()
+        st = self._lib.lbvh_query_into_host(self._h, _ptr(q), q.shape[0], qkind, _ptr(r), float(radius),
+                                            _ptr(offsets), _ptr(hits), cap, ctypes.byref(total),
+                                            _stream(stream))
         return st, total.value
 
     def query(self, queries, qkind: int = SPHERE, radius: float = 0.0, radii=None, capacity=None,

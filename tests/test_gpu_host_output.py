@@ -1,0 +1,103 @@
+"""lbvh_query_into_host: the CSR in page-locked host memory (chunks staged on
+the device, copied while the next chunk runs) equals the device-buffer query,
+with one chunk and with several; memory that is not page-locked is refused
+before anything is launched."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2402_00665_gb300 import _build, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    _build.build()
+    from paper_2402_00665_gb300 import lbvh
+    return lbvh.load()
+
+
+def L():
+    from paper_2402_00665_gb300 import lbvh
+    return lbvh
+
+
+@pytest.mark.parametrize("radius", [None, 0.2])
+def test_host_csr_equals_device_csr(radius):
+    lbvh = L()
+    n = 16384
+    pts = inputs.uniform_points(n, seed=0)
+    r = float(inputs.radius_for_neighbours(n)) if radius is None else radius  # 0.2: lists past the slot
+    t = lbvh.Tree().build(pts, lbvh.POINTS, 63)
+    q = torch.from_numpy(pts[::3].copy()).cuda()
+    doff, dhits = t.query(q, lbvh.SPHERE, radius=r)
+    total = int(doff[-1].item())
+    hoff = torch.empty(q.shape[0] + 1, dtype=torch.int64).pin_memory()
+    hhits = torch.empty(total + 5, dtype=torch.int32).pin_memory()
+    st, tot = t.query_into_host(q, lbvh.SPHERE, hoff, hhits, radius=r)
+    torch.cuda.synchronize()
+    assert st == lbvh.OK and tot == total
+    assert np.array_equal(hoff.numpy(), doff.cpu().numpy())
+    assert np.array_equal(hhits[:tot].numpy(), dhits.cpu().numpy())
+    o = oracle.build(pts, oracle.POINTS, 63)
+    ooff, ohits = oracle.query(o, pts[::3], oracle.SPHERE, radius=np.float32(r))
+    assert np.array_equal(hoff.numpy(), ooff) and np.array_equal(hhits[:tot].numpy().view(np.uint32), ohits)
+
+
+def test_several_chunks():
+    # 9e6 queries: two chunks (at least 2^23 queries each), two staging areas
+    lbvh = L()
+    pts = torch.from_numpy(inputs.uniform_points(1 << 20, seed=5)).cuda()
+    q = torch.rand((9_000_000, 3), generator=torch.Generator().manual_seed(6)).cuda()
+    r = float(inputs.radius_for_neighbours(1 << 20)) * 0.6
+    t = lbvh.Tree().build(pts, lbvh.POINTS, 63)
+    doff, dhits = t.query(q, lbvh.SPHERE, radius=r)
+    total = int(doff[-1].item())
+    hoff = torch.empty(q.shape[0] + 1, dtype=torch.int64).pin_memory()
+    hhits = torch.empty(total, dtype=torch.int32).pin_memory()
+    st, tot = t.query_into_host(q, lbvh.SPHERE, hoff, hhits, radius=r)
+    torch.cuda.synchronize()
+    assert st == lbvh.OK and tot == total
+    assert torch.equal(hoff, doff.cpu()) and torch.equal(hhits, dhits.cpu())
+    # capacity running out in the second chunk: offsets all written, the total reported
+    half = int(doff[q.shape[0] // 2].item())
+    hoff2 = torch.full((q.shape[0] + 1,), -1, dtype=torch.int64).pin_memory()
+    st, tot = t.query_into_host(q, lbvh.SPHERE, hoff2, torch.empty(half + 7, dtype=torch.int32).pin_memory(),
+                                radius=r)
+    torch.cuda.synchronize()
+    assert st == lbvh.ERR_CAPACITY and tot == total and torch.equal(hoff2, doff.cpu())
+
+
+def test_capacity_too_small_reports_the_need():
+    lbvh = L()
+    pts = inputs.uniform_points(4000, seed=3)
+    t = lbvh.Tree().build(pts, lbvh.POINTS, 30)
+    hoff = torch.empty(4001, dtype=torch.int64).pin_memory()
+    hhits = torch.empty(10, dtype=torch.int32).pin_memory()
+    st, tot = t.query_into_host(pts, lbvh.SPHERE, hoff, hhits, radius=0.05)
+    torch.cuda.synchronize()
+    assert st == lbvh.ERR_CAPACITY and tot > 10
+
+
+def test_memory_that_is_not_page_locked_is_refused():
+    lbvh = L()
+    pts = inputs.uniform_points(3000, seed=4)
+    t = lbvh.Tree().build(pts, lbvh.POINTS, 30)
+    good_off = torch.empty(3001, dtype=torch.int64).pin_memory()
+    good_hits = torch.empty(1 << 16, dtype=torch.int32).pin_memory()
+    pageable_off = torch.empty(3001, dtype=torch.int64)
+    pageable_hits = torch.empty(1 << 16, dtype=torch.int32)
+    device_off = torch.empty(3001, dtype=torch.int64, device="cuda")
+    for off, hits in ((pageable_off, good_hits), (good_off, pageable_hits), (device_off, good_hits)):
+        st, _ = t.query_into_host(pts, lbvh.SPHERE, off, hits, radius=0.01)
+        assert st == lbvh.ERR_INVALID
+    st, tot = t.query_into_host(pts, lbvh.SPHERE, good_off, good_hits, radius=0.01)
+    torch.cuda.synchronize()
+    assert st == lbvh.OK and good_off[-1].item() == tot
