@@ -277,8 +277,9 @@ class Tree:
         return st, total.value
 
     def query_into_host(self, queries, qkind, offsets, hits, radius: float = 0.0, radii=None, stream=None):
-        """lbvh_query_into_host: the CSR written by the kernels straight into
-        page-locked host tensors (``pin_memory()``); returns (status, total)."""
+        """lbvh_query_into_host: the CSR into page-locked host tensors
+        (``pin_memory()``), chunk copies overlapped with the next chunk's walk;
+        complete once the stream is synchronised. Returns (status, total)."""
         torch = _torch()
         q = _dev(queries, torch.float32, _QDIM[qkind])
         r = None if radii is None else _dev(radii, torch.float32).reshape(-1)

@@ -101,3 +101,23 @@ def test_memory_that_is_not_page_locked_is_refused():
     st, tot = t.query_into_host(pts, lbvh.SPHERE, good_off, good_hits, radius=0.01)
     torch.cuda.synchronize()
     assert st == lbvh.OK and good_off[-1].item() == tot
+
+
+def test_no_queries_and_ray_chunks():
+    lbvh = L()
+    boxes = inputs.gaussian_mixture_boxes(1 << 16, seed=7, components=8)
+    t = lbvh.Tree().build(boxes, lbvh.BOXES, 63)
+    hoff = torch.full((1,), -1, dtype=torch.int64).pin_memory()
+    st, tot = t.query_into_host(torch.empty((0, 8), device="cuda"), lbvh.RAY, hoff, None)
+    torch.cuda.synchronize()
+    assert st == lbvh.OK and tot == 0 and hoff[0].item() == 0
+    # 9e6 ray segments (two chunks; each chunk's rays start 32-byte aligned)
+    rays = torch.from_numpy(inputs.random_rays(9_000_000, seed=8, tmax=0.05)).cuda()
+    doff, dhits = t.query(rays, lbvh.RAY)
+    total = int(doff[-1].item())
+    hoff = torch.empty(rays.shape[0] + 1, dtype=torch.int64).pin_memory()
+    hhits = torch.empty(max(total, 1), dtype=torch.int32).pin_memory()
+    st, tot = t.query_into_host(rays, lbvh.RAY, hoff, hhits)
+    torch.cuda.synchronize()
+    assert st == lbvh.OK and tot == total
+    assert torch.equal(hoff, doff.cpu()) and torch.equal(hhits[:tot], dhits.cpu())
