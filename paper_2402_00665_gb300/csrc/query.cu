@@ -262,9 +262,9 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
         uint32_t *slot = qs.slots + i * kSlot;
         // kPairs: hits go to the slot two at a time (one 8-byte store; words
         // past the count are never read). Point trees, one tree: walk 16.19
-        // -> 16.00 ms on 2^25 uniform points at 40 registers instead of 32;
-        // on box trees the extra registers cost more (D3 walk 8.39 -> 8.49
-        // ms), and the batched kernel, held to 32, would spill.
+        // -> 15.87 ms on 2^25 uniform points (held to 32 registers, with an
+        // 8-byte spill; 16.00 ms at 40 registers); on box trees it cost more
+        // (D3 walk 8.39 -> 8.49 ms at 40 registers).
         uint2 buf = make_uint2(0u, 0u);
         const bool ok = walk<kP>(t, q, [&](uint32_t id) {
             if (cnt < (uint32_t)kSlot) {
@@ -299,7 +299,7 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
 // At most 32 registers (8 CTAs of 256 threads per SM): the walk hides its
 // load latency with occupancy.
 template <int kQ, int kP, int K>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, K == 1 ? 8 : 1)
     collect_kernel(TreeView t, QueryArgs qa, QueryScratch qs, Control *ctl) {
     uint2 *__restrict__ count_pos = qs.count_pos;
     uint32_t *__restrict__ slots = qs.slots;
