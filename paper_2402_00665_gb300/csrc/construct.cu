@@ -37,8 +37,9 @@
 //     lie inside one group of consecutive leaves (128 by default) meet in
 //     shared memory (block-scope exchange, sibling box from shared memory);
 //     only the nodes spanning a group's edge meet in the device-scope
-//     `store` words (sibling box through L2, ld.global.cg). The batched
-//     kernel keeps every exchange at device scope.
+//     `store` words (sibling box through L2, ld.global.cg). Batches group
+//     their global sorted positions the same way (a group may hold several
+//     trees; a split only ever joins leaves of one).
 #include <cuda/atomic>
 
 #include <cstdlib>
@@ -275,30 +276,30 @@ struct GroupShape {
     static constexpr int kCta = kGroup == 32 ? 256 : kGroup;  // warp groups: eight per CTA
 };
 
-template <int kKind, int kGroup>
-__global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kGroup>::kCta)
-    construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
-                           const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
-                           unsigned long long *store, uint32_t *flags) {
-    constexpr int kCta = GroupShape<kGroup>::kCta;
-    __shared__ unsigned long long s_word[kCta];  // split p at g0 + p - a
-    __shared__ float3 s_lo[2][kCta], s_hi[2][kCta];  // boxes: [0] leaf, [1] internal node, at g0 + id - a
-    __shared__ int s_failed;
-    const int t = threadIdx.x;
-    const int g0 = t / kGroup * kGroup;    // the group's first thread
-    const int a = blockIdx.x * kCta + g0;  // the group's first leaf
-    const int i = blockIdx.x * kCta + t;
+template <int kCta>
+struct GroupSmem {
+    unsigned long long word[kCta];  // split at global position a + j: word[g0 + j]
+    float3 lo[2][kCta], hi[2][kCta];  // boxes: [0] leaf, [1] internal node, by global position / index
+    int failed;
+};
+
+// Both phases for the thread of leaf i of a tree of n leaves whose leaf 0 sits
+// at global position o (0 for a single tree; trees of a batch follow each
+// other), in the group whose first global position is a (shared slots from
+// g0). A split joins two leaves of one tree, so groups may hold several trees.
+template <int kKind, int kGroup, int kCta>
+__device__ __forceinline__ void two_phase(GroupSmem<kCta> &sm, bool active, int i, int n, int64_t o, int64_t a,
+                                          int g0, int t, const uint64_t *__restrict__ codes,
+                                          const uint32_t *__restrict__ perm, uint32_t perm_base,
+                                          const float *__restrict__ prims, float4 *inodes, float4 *leaves,
+                                          unsigned long long *store, uint32_t *flags) {
     const int ni = n - 1;
-    s_word[t] = 0ull;
-    if (t == 0) s_failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
-    __syncthreads();
-    if (s_failed) return;  // the sort failed: leave store untouched (the whole CTA returns)
     Climb c;
     bool pending = false, in_word = false;
-    uint32_t word_at = 0;
-    if (i < n && leaf_step<kKind>(i, n, codes, perm, 0u, prims, leaves, flags, c) && n > 1) {
-        s_lo[0][t] = c.lo;
-        s_hi[0][t] = c.hi;
+    int word_at = 0;
+    if (active && leaf_step<kKind>(i, n, codes, perm, perm_base, prims, leaves, flags, c) && n > 1) {
+        sm.lo[0][t] = c.lo;
+        sm.hi[0][t] = c.hi;
         for (int level = 0; level < 128; ++level) {
             uint32_t p;
             unsigned long long mine;
@@ -307,12 +308,13 @@ __global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kG
                 atomicOr(flags, kFlagCorrupt);
                 break;
             }
-            const uint32_t at = p - (uint32_t)a;  // huge when p < a
-            if (at >= (uint32_t)(kGroup - 1)) {  // on the group's edge
+            const int64_t rel = o + (int64_t)p - a;  // the split's place in the group
+            if (rel < 0 || rel >= kGroup - 1) {       // on the group's edge
                 pending = true;
                 break;
             }
-            cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(s_word[g0 + at]);
+            const int at = (int)rel;
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(sm.word[g0 + at]);
             const unsigned long long other = w.exchange(mine, cuda::memory_order_acq_rel);
             if (other == 0ull) {  // first up: the sibling may come in this phase, or never
                 pending = in_word = true;
@@ -326,11 +328,12 @@ __global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kG
             }
             const int sibling = take_half(c, is_left, p, other, ni);
             const int k = sibling < ni ? 1 : 0;
-            const int sat = g0 + (sibling < ni ? sibling : sibling - ni) - a;  // g0 + at or g0 + at + 1
-            const int q = write_parent(c, p, n, s_lo[k][sat], s_hi[k][sat], inodes);
+            const int sat = g0 + (int)(o + (sibling < ni ? sibling : sibling - ni) - a);  // g0 + at or + at + 1
+            const int q = write_parent(c, p, n, sm.lo[k][sat], sm.hi[k][sat], inodes);
             if (q == 0) break;  // the root: the whole tree lies in this group
-            s_lo[1][g0 + q - a] = c.lo;  // q is l or r, inside the group
-            s_hi[1][g0 + q - a] = c.hi;
+            const int qat = g0 + (int)(o + q - a);  // q is l or r, inside the group
+            sm.lo[1][qat] = c.lo;
+            sm.hi[1][qat] = c.hi;
         }
     }
     if (kGroup == 32)
@@ -338,9 +341,57 @@ __global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kG
     else
         __syncthreads();
     if (!pending) return;
-    if (in_word && s_word[g0 + word_at] == 0ull) return;  // the sibling came and carried on
+    if (in_word && sm.word[g0 + word_at] == 0ull) return;  // the sibling came and carried on
     // this thread wrote its own node, so its device-scope release covers it
     climb_global<kKind, true>(c, n, inodes, leaves, store, flags);
+}
+
+template <int kKind, int kGroup>
+__global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kGroup>::kCta)
+    construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
+                           const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
+                           unsigned long long *store, uint32_t *flags) {
+    constexpr int kCta = GroupShape<kGroup>::kCta;
+    __shared__ GroupSmem<kCta> sm;
+    const int t = threadIdx.x;
+    const int g0 = t / kGroup * kGroup;  // the group's first thread
+    const int i = blockIdx.x * kCta + t;
+    sm.word[t] = 0ull;
+    if (t == 0) sm.failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
+    __syncthreads();
+    if (sm.failed) return;  // the sort failed: leave store untouched (the whole CTA returns)
+    two_phase<kKind, kGroup, kCta>(sm, i < n, i, n, 0, (int64_t)blockIdx.x * kCta + g0, g0, t, codes, perm, 0u,
+                                   prims, inodes, leaves, store, flags);
+}
+
+// Many trees at once, grouped by global sorted position: global position g
+// belongs to the instance b with off[b] <= g < off[b+1]; its tree's records
+// start at node_start[b] (float4 units) and its store words at store_start[b].
+template <int kKind, int kGroup>
+__global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kGroup>::kCta)
+    batch_construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
+                                 const float *__restrict__ prims, const int64_t *__restrict__ off,
+                                 const int64_t *__restrict__ node_start, const int64_t *__restrict__ store_start,
+                                 int count, int64_t total, float4 *nodes, unsigned long long *store,
+                                 uint32_t *flags) {
+    constexpr int kCta = GroupShape<kGroup>::kCta;
+    __shared__ GroupSmem<kCta> sm;
+    const int t = threadIdx.x;
+    const int g0 = t / kGroup * kGroup;
+    const int64_t g = (int64_t)blockIdx.x * kCta + t;
+    sm.word[t] = 0ull;
+    if (t == 0) sm.failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
+    __syncthreads();
+    if (sm.failed) return;
+    const bool active = g < total;
+    const int b = active ? instance_of(off, count, g) : 0;
+    const int64_t o = active ? off[b] : 0;
+    const int n = active ? (int)(off[b + 1] - o) : 1;
+    float4 *inodes = nodes + (active ? node_start[b] : 0);
+    float4 *leaves = inodes + 2 * (int64_t)(n - 1);
+    two_phase<kKind, kGroup, kCta>(sm, active, (int)(g - o), n, o, (int64_t)blockIdx.x * kCta + g0, g0, t,
+                                   codes + o, perm + o, (uint32_t)o, prims, inodes, leaves,
+                                   store + (active ? store_start[b] : 0), flags);
 }
 
 template <int kKind, bool kAcqRel>
@@ -382,15 +433,22 @@ void launch_batch_construct(const uint64_t *sorted_codes, const uint32_t *perm, 
                             const BatchTables &bt, int kind, float4 *nodes, unsigned long long *store,
                             uint32_t *flags, cudaStream_t s) {
     if (bt.total_prims <= 0) return;
-    const unsigned blocks = (unsigned)((bt.total_prims + kThreads - 1) / kThreads);
-    if (kind == LBVH_PRIM_POINTS)
-        batch_construct_kernel<LBVH_PRIM_POINTS><<<blocks, kThreads, 0, s>>>(
-            sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count, bt.total_prims,
-            nodes, store, flags);
-    else
-        batch_construct_kernel<LBVH_PRIM_BOXES><<<blocks, kThreads, 0, s>>>(
-            sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count, bt.total_prims,
-            nodes, store, flags);
+    // LBVH_CONSTRUCT_GLOBAL=1: every exchange at device scope (tuning)
+    static const bool one_phase = getenv("LBVH_CONSTRUCT_GLOBAL") && atoi(getenv("LBVH_CONSTRUCT_GLOBAL"));
+    const bool pts = kind == LBVH_PRIM_POINTS;
+    if (one_phase) {
+        const unsigned blocks = (unsigned)((bt.total_prims + kThreads - 1) / kThreads);
+        auto k = pts ? batch_construct_kernel<LBVH_PRIM_POINTS> : batch_construct_kernel<LBVH_PRIM_BOXES>;
+        k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count,
+                                      bt.total_prims, nodes, store, flags);
+    } else {
+        constexpr int kGroup = 128, kCta = GroupShape<kGroup>::kCta;
+        const unsigned blocks = (unsigned)((bt.total_prims + kCta - 1) / kCta);
+        auto k = pts ? batch_construct_block_kernel<LBVH_PRIM_POINTS, kGroup>
+                     : batch_construct_block_kernel<LBVH_PRIM_BOXES, kGroup>;
+        k<<<blocks, kCta, 0, s>>>(sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count,
+                                  bt.total_prims, nodes, store, flags);
+    }
     count_launches(1);
 }
 
