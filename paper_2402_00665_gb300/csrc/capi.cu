@@ -1171,38 +1171,48 @@ lbvh_status lbvh_query_into_host(lbvh_tree_t t, const float *d_queries, int64_t 
     const int64_t per = (nq + chunks - 1) / chunks;
     uint64_t base = 0;
     bool over = false;
-    for (int64_t k = 0; k < chunks; ++k) {
-        const int64_t q0 = k * per, m = std::min(per, nq - q0);
-        if (m < 0 || (m == 0 && k > 0)) break;
-        const int b = (int)(k & 1);
-        if (k >= 2) LBVH_CUDA(cudaStreamWaitEvent(s, t->drained[b], 0));  // its staging area is free again
-        LBVH_CUDA(t->stage_off[b].ensure((size_t)(m + 1) * 8, s));
-        int64_t *soff = t->stage_off[b].as<int64_t>();
-        QueryArgs qa{d_queries + q0 * dim, m, qkind, d_radii ? d_radii + q0 : nullptr, radius, nullptr};
-        uint64_t tot = 0;
-        if ((st = query_count(t, qa, soff, s, &tot)) != LBVH_OK) break;
-        const bool fits = !over && base + tot <= capacity;
-        over = !fits;
-        if (fits && tot > 0) {
-            LBVH_CUDA(t->stage_hits[b].ensure((size_t)tot * 4, s));
-            if ((st = query_fill(t, qa, soff, t->stage_hits[b].as<uint32_t>(), s)) != LBVH_OK) break;
+    auto run = [&]() -> lbvh_status {
+        for (int64_t k = 0; k < chunks; ++k) {
+            const int64_t q0 = k * per, m = std::min(per, nq - q0);
+            if (m < 0 || (m == 0 && k > 0)) break;
+            const int b = (int)(k & 1);
+            if (k >= 2) LBVH_CUDA(cudaStreamWaitEvent(s, t->drained[b], 0));  // its staging area is free again
+            LBVH_CUDA(t->stage_off[b].ensure((size_t)(m + 1) * 8, s));
+            int64_t *soff = t->stage_off[b].as<int64_t>();
+            QueryArgs qa{d_queries + q0 * dim, m, qkind, d_radii ? d_radii + q0 : nullptr, radius, nullptr};
+            uint64_t tot = 0;
+            lbvh_status cst = query_count(t, qa, soff, s, &tot);
+            if (cst != LBVH_OK) return cst;
+            const bool fits = !over && base + tot <= capacity;
+            over = !fits;
+            if (fits && tot > 0) {
+                LBVH_CUDA(t->stage_hits[b].ensure((size_t)tot * 4, s));
+                if ((cst = query_fill(t, qa, soff, t->stage_hits[b].as<uint32_t>(), s)) != LBVH_OK) return cst;
+            }
+            if (base > 0) launch_offsets_add(soff, m + 1, (int64_t)base, s);
+            LBVH_CUDA(cudaEventRecord(t->staged[b], s));
+            LBVH_CUDA(cudaStreamWaitEvent(t->xfer, t->staged[b], 0));
+            LBVH_CUDA(cudaMemcpyAsync(h_offsets + q0, soff, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, t->xfer));
+            if (fits && tot > 0)
+                LBVH_CUDA(cudaMemcpyAsync(h_hits + base, t->stage_hits[b].p, (size_t)tot * 4,
+                                          cudaMemcpyDeviceToHost, t->xfer));
+            LBVH_CUDA(cudaEventRecord(t->drained[b], t->xfer));
+            base += tot;
         }
-        if (base > 0) launch_offsets_add(soff, m + 1, (int64_t)base, s);
-        LBVH_CUDA(cudaEventRecord(t->staged[b], s));
-        LBVH_CUDA(cudaStreamWaitEvent(t->xfer, t->staged[b], 0));
-        LBVH_CUDA(cudaMemcpyAsync(h_offsets + q0, soff, (size_t)(m + 1) * 8, cudaMemcpyDeviceToHost, t->xfer));
-        if (fits && tot > 0)
-            LBVH_CUDA(cudaMemcpyAsync(h_hits + base, t->stage_hits[b].p, (size_t)tot * 4, cudaMemcpyDeviceToHost,
-                                      t->xfer));
-        LBVH_CUDA(cudaEventRecord(t->drained[b], t->xfer));
-        base += tot;
+        return LBVH_OK;
+    };
+    st = run();
+    // on every path: the caller's stream (and the tree's `used` event) cover
+    // the copies already issued
+    const bool tail_ok = cudaEventRecord(t->xfer_done, t->xfer) == cudaSuccess &&
+                         cudaStreamWaitEvent(s, t->xfer_done, 0) == cudaSuccess &&
+                         (t->used || cudaEventCreateWithFlags(&t->used, cudaEventDisableTiming) == cudaSuccess) &&
+                         cudaEventRecord(t->used, s) == cudaSuccess;
+    if (!tail_ok) {
+        cudaStreamSynchronize(t->xfer);  // nothing may still read the staging areas
+        if (st == LBVH_OK) st = LBVH_ERR_CUDA;
     }
-    // the caller's stream (and the tree's `used` event) cover the copies
-    LBVH_CUDA(cudaEventRecord(t->xfer_done, t->xfer));
-    LBVH_CUDA(cudaStreamWaitEvent(s, t->xfer_done, 0));
-    if (!t->used) LBVH_CUDA(cudaEventCreateWithFlags(&t->used, cudaEventDisableTiming));
-    LBVH_CUDA(cudaEventRecord(t->used, s));
-    t->queried = true;
+    t->queried = t->used != nullptr;
     *total = base;
     if (st != LBVH_OK) return st;
     return over ? LBVH_ERR_CAPACITY : LBVH_OK;
