@@ -149,7 +149,7 @@ def parse():
                     default="uniform_2^25_63bit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-staged", action="store_true",
-                    help="e2e results into device arrays, then copied to host (instead of written to host directly)")
+                    help="e2e results into device arrays, then copied to host (instead of lbvh_query_into_host)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
