@@ -77,6 +77,8 @@ def test_invalid_arguments_rejected_before_any_device_work(lib_path):
         total = ctypes.c_uint64()
         assert lib.lbvh_query_into(h, dummy, 1, 0, None, 1.0, off, None, 0, ctypes.byref(total),
                                    None) == lbvh.ERR_INVALID
+        assert lib.lbvh_query_into_host(h, dummy, 1, 0, None, 1.0, off, None, 0, ctypes.byref(total),
+                                        None) == lbvh.ERR_INVALID
         assert lib.lbvh_tree_status(h) == lbvh.ERR_INVALID
         # checkpoint images are validated before any device work
         size = ctypes.c_uint64()
