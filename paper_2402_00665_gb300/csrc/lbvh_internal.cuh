@@ -84,9 +84,7 @@ constexpr int kRadix = 1 << kRadixBits;
 constexpr int kSortThreads = 256;
 constexpr int kMaxPasses = 8;
 
-// Keys per tile of the sort's tile shape in use (threads * keys per thread).
-int64_t sort_tile_keys();
-inline int64_t sort_tiles(int64_t n) { return (n + sort_tile_keys() - 1) / sort_tile_keys(); }
+// 8-bit digit passes for keys of key_bits bits.
 inline int sort_passes(int key_bits) { return (key_bits + kRadixBits - 1) / kRadixBits; }
 
 struct SortScratch {

@@ -399,8 +399,6 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
     count_launches(1);
 }
 
-int64_t sort_tile_keys() { return (int64_t)kSortThreads * variant().items; }
-
 std::atomic<int64_t> g_hold_tile{-1};
 
 void sort_set_hold_tile(int64_t tile) { g_hold_tile.store(tile, std::memory_order_relaxed); }
