@@ -9,9 +9,11 @@ expected neighbours (Algorithm 1, CSR output with sorted hit lists).
 
 Prints ONE JSON line (rank 0). ``value`` is primitives per second through the
 whole step (build + query), whole job, device-timed with CUDA events on the
-stream the kernels run on. ``e2e`` is the same metric through the C-ABI call
-from host buffers: each step copies the points from pinned host memory,
-builds, queries, and copies the CSR result back. ``roofline`` reports the
+stream the kernels run on. ``e2e`` is the same metric through the C-ABI calls
+from host buffers: each step copies the points and queries from pinned host
+memory, builds, and queries with lbvh_query_into_host, which leaves the CSR
+result in pinned host memory (chunk copies overlapped with the next chunk's
+walk; --e2e-staged: query into device arrays, then copy). ``roofline`` reports the
 dominant kernel's algorithmic bytes over its event-timed duration against the
 measured HBM copy bandwidth. ``cpu_baseline`` times the CPU oracle on a
 bounded sample of the same workload (rank 0, N=1 only).
