@@ -435,12 +435,16 @@ void lbvh_server_destroy(lbvh_server_t server);
  *     {lo.xyz, word}, {hi.xyz, 0}; word (uint32 bits) = primitive index |
  *     (1u << 31 if the leaf's skip is internal node k+1, else leaf k+1; the
  *     last leaf's skip is the sentinel).
- *   d_flags uint32 device word or NULL: bit 2 is set if the codes/perm are not
- *     a sorted permutation (the outputs are then invalid). The caller clears it.
+ *   d_flags uint32 device word or NULL: bit 2 is set if a perm entry is out
+ *     of range, two adjacent codes are out of order, or the merge leaves the
+ *     tree (the outputs are then invalid). A perm that repeats an index is
+ *     not detected. The caller clears the word.
  * Asynchronous on `stream`; allocates nothing (no cudaMalloc, cudaFree or
- * allocating library call). The first call on a device looks up the device
- * address of the scratch array (cudaGetSymbolAddress) with that device
- * current, so make that first call before any stream capture. Each call
+ * allocating library call). Every call looks up the device address of the
+ * scratch array (cudaGetSymbolAddress) with the calling thread's current
+ * device, so an address is never kept past a device reset; the first call on
+ * a device also loads the library's device code there, so make that first
+ * call before any stream capture. Each call
  * clears the scratch words it uses; calls that overlap on the GPU (on
  * different streams, or from different threads) share the one array and race,
  * so serialise them. */

@@ -172,10 +172,11 @@ struct lbvh_tree_s {
     int kind = LBVH_PRIM_POINTS;
     int bits = 0;
     bool has_build = false;
-    bool sorted_in_b = false;
+    int codes_in = 0, perm_in = 0;  // which keys[] / vals[] buffer holds the sorted codes / permutation
     bool store_dirty = false;  // a failed build may have left store words set
     DevBuf keys[2], vals[2];
     DevBuf nodes, store, lookback, hist, partials, bounds, ctl;
+    DevBuf pend;  // climbs handed from the construct to its second kernel (zeroed, kept zero)
     DevBuf counts, tile_sums, overflow, slots, spill_head, spill;
     DevBuf qkeys[2], qvals[2], qlookback;  // Morton order of the queries
     DevBuf vscratch;                       // scratch of the Karras / Apetrei builds
@@ -189,8 +190,8 @@ struct lbvh_tree_s {
     lbvh::Control *h_ctl = nullptr;  // pinned mirror of the control block (from pinned_controls())
     Profiler prof;
 
-    const uint64_t *sorted_codes() const { return keys[sorted_in_b ? 1 : 0].as<uint64_t>(); }
-    const uint32_t *perm() const { return vals[sorted_in_b ? 1 : 0].as<uint32_t>(); }
+    const uint64_t *sorted_codes() const { return keys[codes_in].as<uint64_t>(); }
+    const uint32_t *perm() const { return vals[perm_in].as<uint32_t>(); }
     lbvh::Control *dctl() const { return ctl.as<lbvh::Control>(); }
     lbvh::TreeView view() const {
         return lbvh::TreeView{inodes(), leaves(), n, kind};
@@ -282,6 +283,7 @@ lbvh_status reserve_tree(lbvh_tree_s *t, int64_t n, int kind, cudaStream_t s) {
     }
     LBVH_CUDA(t->nodes.ensure(ui * 32 + leaf_float4s(n, kind) * 16, s));
     LBVH_CUDA(t->store.ensure(ui * 8, s, true));
+    LBVH_CUDA(t->pend.ensure(construct_pend_bytes(n), s, true));
     LBVH_CUDA(t->lookback.ensure((size_t)tiles * kRadix * 4 * 2, s));
     LBVH_CUDA(t->hist.ensure((size_t)kMaxPasses * kRadix * 4, s));
     LBVH_CUDA(t->partials.ensure((size_t)bounds_blocks(n) * 8 * 4, s));
@@ -318,16 +320,8 @@ constexpr int64_t kOrderMinQueries = 2048;  // below this, walk in input order
 // Morton bits of the query order: 30 (4 sort passes). 24 bits saved a pass
 // on uniform queries at the same walk time, but on clustered queries (a
 // Gaussian mixture) the coarser cells cost more walk time than the pass;
-// order changes speed only. LBVH_QUERY_ORDER_BITS=<multiple of 3 in [3, 63]>
-// overrides it process-wide (tuning sweeps).
-int order_bits() {
-    static const int bits = [] {
-        const char *env = getenv("LBVH_QUERY_ORDER_BITS");
-        const int want = env ? atoi(env) : 30;
-        return (want >= 3 && want <= 63 && want % 3 == 0) ? want : 30;
-    }();
-    return bits;
-}
+// order changes speed only.
+constexpr int order_bits() { return 30; }
 
 // The order in which threads take the queries: the Morton order of the query
 // centres inside the tree's bounds (encode + radix sort, the build's own
@@ -345,33 +339,23 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
         qa.order = t->perm();
         return LBVH_OK;
     }
+    // codes of at most 32 bits, packed with the query index (code << 32 | i):
+    // one 8-byte word per query each way, and the last pass writes the order alone
     const size_t unq = (size_t)qa.nq;
-    const int passes = sort_passes(order_bits());
-    const bool narrow = order_bits() <= 30;  // 32-bit keys: a third less traffic per pass
     for (int k = 0; k < 2; ++k) {
         LBVH_CUDA(t->qkeys[k].ensure(unq * 8, s));
         LBVH_CUDA(t->qvals[k].ensure(unq * 4, s));
     }
     LBVH_CUDA(t->qlookback.ensure((size_t)sort_tiles_max(qa.nq) * kRadix * 4 * 2, s));
-    LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)passes * kRadix * 4, s));
+    LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)sort_passes(order_bits()) * kRadix * 4, s));
     const int as_prims = qa.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
-    if (narrow)
-        launch_encode(qa.queries, qa.nq, as_prims, order_bits(), t->bounds.as<float>(),
-                      t->qkeys[0].as<uint32_t>(), t->hist.as<uint32_t>(), 1, s);
-    else
-        launch_encode(qa.queries, qa.nq, as_prims, order_bits(), t->bounds.as<float>(),
-                      t->qkeys[0].as<uint64_t>(), t->hist.as<uint32_t>(), 1, s);
+    launch_encode(qa.queries, qa.nq, as_prims, order_bits(), t->bounds.as<float>(), t->qkeys[0].as<uint64_t>(),
+                  t->hist.as<uint32_t>(), 1, true, s);
     LBVH_LAUNCHED();
     SortScratch scratch{t->hist.as<uint32_t>(), t->qlookback.as<uint32_t>(), sort_tiles_max(qa.nq) * kRadix};
-    const bool in_b =
-        narrow ? run_onesweep32(t->qkeys[0].as<uint32_t>(), t->qvals[0].as<uint32_t>(), true,
-                                t->qkeys[1].as<uint32_t>(), t->qvals[1].as<uint32_t>(), qa.nq, passes, scratch,
-                                t->dctl(), s)
-               : run_onesweep(t->qkeys[0].as<uint64_t>(), t->qvals[0].as<uint32_t>(), true,
-                              t->qkeys[1].as<uint64_t>(), t->qvals[1].as<uint32_t>(), qa.nq, passes, scratch,
-                              t->dctl(), s);
+    qa.order = run_index_sort(t->qkeys[0].as<uint64_t>(), t->qkeys[1].as<uint64_t>(), t->qvals[0].as<uint32_t>(),
+                              t->qvals[1].as<uint32_t>(), qa.nq, order_bits(), true, scratch, t->dctl(), s);
     LBVH_LAUNCHED();
-    qa.order = t->qvals[in_b ? 1 : 0].as<uint32_t>();
     return LBVH_OK;
 }
 
@@ -760,7 +744,7 @@ void lbvh_tree_destroy(lbvh_tree_t t) {
     else if (t->nodes.p) cudaDeviceSynchronize();  // a build that failed part-way may still run
     if (t->queried) cudaEventSynchronize(t->used);
     for (DevBuf *b : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
-                      &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
+                      &t->store, &t->pend, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                       &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                       &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots, &t->vscratch, &t->spill_head,
                       &t->spill, &t->stage_off[0], &t->stage_off[1], &t->stage_hits[0], &t->stage_hits[1]})
@@ -812,27 +796,37 @@ lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
         t->prof.end(LBVH_STAGE_BOUNDS, s);
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_ENCODE, s);
+        // codes of at most 30 bits are packed with the index from the start
+        const bool packed = morton_bits <= 30;
         launch_encode(d_prims, n, kind, morton_bits, t->bounds.as<float>(), t->keys[0].as<uint64_t>(),
-                      t->hist.as<uint32_t>(), 1, s);
+                      t->hist.as<uint32_t>(), 1, packed, s);
         t->prof.end(LBVH_STAGE_ENCODE, s);
         LBVH_LAUNCHED();
         SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles_max(n) * kRadix};
         nvtxRangePushA("sort");
-        t->sorted_in_b = run_onesweep(t->keys[0].as<uint64_t>(), t->vals[0].as<uint32_t>(), true,
-                                      t->keys[1].as<uint64_t>(), t->vals[1].as<uint32_t>(), n, passes,
-                                      scratch, c, s, t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr);
+        const uint32_t *perm = run_index_sort(t->keys[0].as<uint64_t>(), t->keys[1].as<uint64_t>(),
+                                              t->vals[0].as<uint32_t>(), t->vals[1].as<uint32_t>(), n, morton_bits,
+                                              packed, scratch, c, s,
+                                              t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr);
         nvtxRangePop();
         if (t->prof.on)
             for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
         LBVH_LAUNCHED();
+        // the sort leaves the permutation alone; the sorted codes go to keys[0]
+        t->perm_in = perm == t->vals[1].as<uint32_t>() ? 1 : 0;
+        t->codes_in = 0;
         t->prof.begin(LBVH_STAGE_CONSTRUCT, s);
-        if (algorithm == LBVH_BUILD_MODIFIED_APETREI)
-            launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(), t->leaves(),
-                             t->store.as<unsigned long long>(), &c->build_flags, s);
-        else
+        if (algorithm == LBVH_BUILD_MODIFIED_APETREI) {
+            launch_construct_encode(t->perm(), d_prims, t->bounds.as<float>(), morton_bits, n, kind,
+                                    t->keys[0].as<uint64_t>(), t->inodes(), t->leaves(),
+                                    t->store.as<unsigned long long>(), &c->build_flags, t->pend.p, s);
+        } else {
+            launch_sorted_codes(d_prims, t->perm(), n, kind, morton_bits, t->bounds.as<float>(),
+                                t->keys[0].as<uint64_t>(), s);
             launch_variant_hierarchy(algorithm, t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(),
                                      t->leaves(), t->vscratch.p, t->store.as<unsigned long long>(),
                                      &c->build_flags, s);
+        }
         t->prof.end(LBVH_STAGE_CONSTRUCT, s);
         LBVH_LAUNCHED();
         if (algorithm != LBVH_BUILD_MODIFIED_APETREI) {
@@ -875,7 +869,7 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
     t->kind = kind;
     t->bits = 0;
     t->prims_ptr = d_prims;
-    t->sorted_in_b = false;
+    t->codes_in = t->perm_in = 0;
     Control *c = t->dctl();
     LBVH_CUDA(cudaMemsetAsync(&c->build_flags, 0, sizeof(uint32_t), s));
     if (t->store_dirty && t->store.bytes) {
@@ -888,7 +882,7 @@ lbvh_status lbvh_build_from_sorted(lbvh_tree_t t, const uint64_t *d_sorted_codes
         launch_bounds(d_prims, n, kind, t->partials.as<float>(), t->bounds.as<float>(), c, s);
         LBVH_LAUNCHED();
         launch_construct(t->sorted_codes(), t->perm(), d_prims, n, kind, t->inodes(),
-                         t->leaves(), t->store.as<unsigned long long>(), &c->build_flags, s);
+                         t->leaves(), t->store.as<unsigned long long>(), &c->build_flags, t->pend.p, s);
         LBVH_LAUNCHED();
     }
     return finish_build(t, s);
@@ -918,7 +912,7 @@ lbvh_status lbvh_refit(lbvh_tree_t t, const float *d_prims, lbvh_stream_t stream
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_CONSTRUCT, s);
         launch_construct(t->sorted_codes(), t->perm(), d_prims, n, t->kind, t->inodes(), t->leaves(),
-                         t->store.as<unsigned long long>(), &c->build_flags, s);
+                         t->store.as<unsigned long long>(), &c->build_flags, t->pend.p, s);
         t->prof.end(LBVH_STAGE_CONSTRUCT, s);
         LBVH_LAUNCHED();
     }
@@ -998,7 +992,7 @@ lbvh_status lbvh_tree_load(lbvh_tree_t t, const void *h_buf, uint64_t bytes, lbv
     t->n = n;
     t->kind = kind;
     t->bits = (int)h.bits;
-    t->sorted_in_b = false;
+    t->codes_in = t->perm_in = 0;
     t->prims_ptr = nullptr;
     LBVH_CUDA(cudaMemsetAsync(&t->dctl()->build_flags, 0, sizeof(uint32_t), s));
     LBVH_CUDA(cudaMemcpyAsync(t->bounds.p, h.bounds, 24, cudaMemcpyHostToDevice, s));
@@ -1032,7 +1026,7 @@ lbvh_status lbvh_tree_bytes(lbvh_tree_t t, uint64_t *bytes) {
     if (!t || !bytes) return LBVH_ERR_INVALID;
     uint64_t b = 0;
     for (const DevBuf *d : {&t->keys[0], &t->keys[1], &t->vals[0], &t->vals[1], &t->nodes,
-                            &t->store, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
+                            &t->store, &t->pend, &t->lookback, &t->hist, &t->partials, &t->bounds, &t->ctl,
                             &t->counts, &t->tile_sums, &t->overflow, &t->qkeys[0], &t->qkeys[1],
                             &t->qvals[0], &t->qvals[1], &t->qlookback, &t->slots, &t->vscratch,
                             &t->spill_head, &t->spill})
@@ -1281,7 +1275,7 @@ lbvh_status lbvh_morton_codes(const float *d_prims, int64_t n, int kind, int mor
     if (e == cudaSuccess) e = hist.ensure((size_t)kMaxPasses * kRadix * 4, s);
     if (e == cudaSuccess) {
         launch_bounds(d_prims, n, kind, partials.as<float>(), d_bounds, ctl.as<Control>(), s);
-        launch_encode(d_prims, n, kind, morton_bits, d_bounds, d_codes, hist.as<uint32_t>(), 0, s);
+        launch_encode(d_prims, n, kind, morton_bits, d_bounds, d_codes, hist.as<uint32_t>(), 0, false, s);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctl.p, sizeof h, cudaMemcpyDeviceToHost, s);
@@ -1557,7 +1551,7 @@ lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cud
     t->n = n;
     t->kind = kind;
     t->bits = b->sig.bits;
-    t->sorted_in_b = false;
+    t->codes_in = t->perm_in = 0;
     t->prims_ptr = nullptr;
     LBVH_CUDA(cudaMemsetAsync(&t->dctl()->build_flags, 0, sizeof(uint32_t), s));
     LBVH_CUDA(cudaMemcpyAsync(t->bounds.p, b->bounds.as<float>() + 6 * instance, 24, cudaMemcpyDeviceToDevice, s));

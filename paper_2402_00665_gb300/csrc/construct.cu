@@ -42,10 +42,8 @@
 //     trees; a split only ever joins leaves of one).
 #include <cuda/atomic>
 
-#include <cstdlib>
-#include <mutex>
-
 #include "lbvh_internal.cuh"
+#include "morton.cuh"
 
 namespace lbvh {
 
@@ -88,19 +86,14 @@ __device__ __forceinline__ void load_node_box(const float4 *inodes, const float4
 }
 
 // The exchange on store[p] publishes this thread's finished node (release)
-// and, for the second thread, makes the sibling's node visible (acquire):
-// either as one acq_rel atomic, or as a relaxed atomic between two fences.
-template <bool kAcqRel>
-__device__ __forceinline__ unsigned long long publish_exchange(unsigned long long *slot,
-                                                               unsigned long long v) {
-    if (kAcqRel) {
-        cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*slot);
-        return a.exchange(v, cuda::memory_order_acq_rel);
-    }
-    __threadfence();
-    const unsigned long long old = atomicExch(slot, v);
-    __threadfence();
-    return old;
+// and, for the second thread, makes the sibling's node visible (acquire), as
+// one acq_rel atomic. Measured with every exchange at device scope at 2^25
+// points: 2.29 ms, against 2.96 ms for a relaxed exchange between two
+// __threadfence() and 2.76 ms for a release-only exchange with an acquire
+// fence taken by the second thread alone.
+__device__ __forceinline__ unsigned long long publish_exchange(unsigned long long *slot, unsigned long long v) {
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*slot);
+    return a.exchange(v, cuda::memory_order_acq_rel);
 }
 
 // A thread's finished node while it climbs: leaf range [l, r], delta*(l-1),
@@ -111,46 +104,42 @@ struct Climb {
 };
 
 // delta*(i-1), delta*(i), delta*(i+1) around leaf i (255 = +inf at -1 and n-1).
+// Codes out of order (c0 > c1) latch kFlagCorrupt: the input is not sorted.
 __device__ __forceinline__ void leaf_deltas(int i, int n, const uint64_t *__restrict__ codes, uint32_t &dl,
-                                            uint32_t &dr, uint32_t &drn) {
+                                            uint32_t &dr, uint32_t &drn, uint32_t *flags) {
     const uint64_t c0 = codes[i];
     dl = i > 0 ? delta_star(codes[i - 1], c0, (uint32_t)(i - 1)) : kInf;
     dr = kInf;
     drn = kInf;
     if (i + 1 < n) {
         const uint64_t c1 = codes[i + 1];
+        if (c0 > c1) atomicOr(flags, kFlagCorrupt);
         dr = delta_star(c0, c1, (uint32_t)i);
         if (i + 2 < n) drn = delta_star(c1, codes[i + 2], (uint32_t)(i + 1));
     }
 }
 
-// Algorithm 4's leaf step for leaf i of one tree of n leaves, given its
-// delta* values: the leaf's skip and box (written out) and the climb state.
-// perm holds primitive indices into `prims`, the tree's own indices being
-// perm - perm_base. False (and kFlagCorrupt) if perm is not a permutation of
-// this tree.
+// The primitive's box (a point's box is the point).
 template <int kKind>
-__device__ __forceinline__ bool leaf_write(int i, int n, const uint32_t *__restrict__ perm, uint32_t perm_base,
-                                           const float *__restrict__ prims, float4 *leaves, uint32_t *flags,
-                                           uint32_t dl, uint32_t dr, uint32_t drn, Climb &c) {
-    const int ni = n - 1;
-    const int leaf_skip = i == n - 1 ? kSentinel : (dr < drn ? ni + i + 1 : i + 1);
-    const uint32_t p_id = perm[i];
-    const uint32_t p_own = p_id - perm_base;
-    if (p_own >= (uint32_t)n) {  // not a permutation of this tree: the sort failed
-        atomicOr(flags, kFlagCorrupt);
-        return false;
-    }
-    float3 lo, hi;
+__device__ __forceinline__ void gather_box(const float *__restrict__ prims, uint32_t p_id, float3 &lo, float3 &hi) {
     if (kKind == LBVH_PRIM_POINTS) {
-        lo = make_float3(prims[3 * (int64_t)p_id], prims[3 * (int64_t)p_id + 1],
-                         prims[3 * (int64_t)p_id + 2]);
+        lo = make_float3(prims[3 * (int64_t)p_id], prims[3 * (int64_t)p_id + 1], prims[3 * (int64_t)p_id + 2]);
         hi = lo;
     } else {
         const float *b = prims + 6 * (int64_t)p_id;
         lo = make_float3(b[0], b[1], b[2]);
         hi = make_float3(b[3], b[4], b[5]);
     }
+}
+
+// Algorithm 4's leaf step for leaf i of one tree of n leaves, given its
+// delta* values and its primitive (own index p_own, box lo/hi): the leaf's
+// skip and box are written out and the climb state is set.
+template <int kKind>
+__device__ __forceinline__ void leaf_write(int i, int n, uint32_t p_own, float3 lo, float3 hi, float4 *leaves,
+                                           uint32_t dl, uint32_t dr, uint32_t drn, Climb &c) {
+    const int ni = n - 1;
+    const int leaf_skip = i == n - 1 ? kSentinel : (dr < drn ? ni + i + 1 : i + 1);
     // the leaf's skip is position i+1: one bit says I_{i+1} rather than L_{i+1}
     const uint32_t word = p_own | (leaf_skip >= 0 && leaf_skip < ni ? kLeafSkipInternal : 0u);
     if (kKind == LBVH_PRIM_POINTS) {
@@ -160,17 +149,28 @@ __device__ __forceinline__ bool leaf_write(int i, int n, const uint32_t *__restr
         leaves[2 * (int64_t)i + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
     }
     c = Climb{(uint32_t)i, (uint32_t)i, dl, dr, drn, lo, hi};
-    return true;
 }
 
+// The leaf step from sorted codes and a permutation. perm holds primitive
+// indices into `prims`, the tree's own indices being perm - perm_base. False
+// (and kFlagCorrupt) if perm is not a permutation of this tree.
 template <int kKind>
 __device__ __forceinline__ bool leaf_step(int i, int n, const uint64_t *__restrict__ codes,
                                           const uint32_t *__restrict__ perm, uint32_t perm_base,
                                           const float *__restrict__ prims, float4 *leaves, uint32_t *flags,
                                           Climb &c) {
     uint32_t dl, dr, drn;
-    leaf_deltas(i, n, codes, dl, dr, drn);
-    return leaf_write<kKind>(i, n, perm, perm_base, prims, leaves, flags, dl, dr, drn, c);
+    leaf_deltas(i, n, codes, dl, dr, drn, flags);
+    const uint32_t p_id = perm[i];
+    const uint32_t p_own = p_id - perm_base;
+    if (p_own >= (uint32_t)n) {  // not a permutation of this tree: the sort failed
+        atomicOr(flags, kFlagCorrupt);
+        return false;
+    }
+    float3 lo, hi;
+    gather_box<kKind>(prims, p_id, lo, hi);
+    leaf_write<kKind>(i, n, p_own, lo, hi, leaves, dl, dr, drn, c);
+    return true;
 }
 
 // The parent's split p of c's node (range_right for a left child, range_left
@@ -217,7 +217,7 @@ __device__ __forceinline__ int write_parent(Climb &c, uint32_t p, int n, float3 
 
 // Climb from c's node with device-scope exchanges on store[p] until this
 // thread is the first up at a split, or has written the root I_0.
-template <int kKind, bool kAcqRel>
+template <int kKind>
 __device__ __forceinline__ void climb_global(Climb c, int n, float4 *inodes, const float4 *leaves,
                                              unsigned long long *store, uint32_t *flags) {
     const int ni = n - 1;
@@ -231,7 +231,7 @@ __device__ __forceinline__ void climb_global(Climb c, int n, float4 *inodes, con
             atomicOr(flags, kFlagCorrupt);
             return;
         }
-        const unsigned long long other = publish_exchange<kAcqRel>(store + p, mine);
+        const unsigned long long other = publish_exchange(store + p, mine);
         if (other == 0ull) return;  // first thread up
         store[p] = 0ull;            // second thread up: leave the slot empty again
         if ((uint32_t)other >= (uint32_t)n) {
@@ -246,58 +246,54 @@ __device__ __forceinline__ void climb_global(Climb c, int n, float4 *inodes, con
     atomicOr(flags, kFlagCorrupt);
 }
 
-// Algorithm 4 for leaf i, every exchange at device scope (batched trees).
-template <int kKind, bool kAcqRel>
-__device__ __forceinline__ void construct_leaf(int i, int n, const uint64_t *__restrict__ codes,
-                                               const uint32_t *__restrict__ perm, uint32_t perm_base,
-                                               const float *__restrict__ prims, float4 *inodes,
-                                               float4 *leaves, unsigned long long *store,
-                                               uint32_t *flags) {
-    Climb c;
-    if (!leaf_step<kKind>(i, n, codes, perm, perm_base, prims, leaves, flags, c)) return;
-    if (n == 1) return;
-    climb_global<kKind, kAcqRel>(c, n, inodes, leaves, store, flags);
-}
-
 // Algorithm 4 with the climb split in two phases. The leaves are cut into
-// groups of kGroup consecutive leaves [a, a + kGroup) (a warp, or a whole
-// CTA). A node whose leaf range lies inside a group has both children there,
-// so its split p has a <= p and p + 1 < a + kGroup; such splits meet in a
-// shared-memory word with a block-scope exchange, and the sibling's box is
-// read from shared memory. A thread stops phase 1 at a split on the group's
-// edge, or as the first up at a word. After the group's barrier every node
-// inside the group is finished; a word still holding its first thread's half
-// has a sibling that spans the group's edge, and that thread, like one stopped
-// at the edge, continues with the device-scope exchanges of climb_global.
-// Each node is still written once, by the second thread up at its split, with
-// the same fields: only where the two halves meet changes.
-template <int kGroup>
-struct GroupShape {
-    static constexpr int kCta = kGroup == 32 ? 256 : kGroup;  // warp groups: eight per CTA
-};
+// groups of kGroup consecutive leaves [a, a + kGroup), one per CTA. A node
+// whose leaf range lies inside a group has both children there, so its split
+// p has a <= p and p + 1 < a + kGroup; such splits meet in a shared-memory
+// word with a block-scope exchange, and the sibling's box is read from shared
+// memory. A thread stops phase 1 at a split on the group's edge, or as the
+// first up at a word. After the group's barrier every node inside the group
+// is finished; a word still holding its first thread's half has a sibling
+// that spans the group's edge, and that thread, like one stopped at the edge,
+// continues with the device-scope exchanges of climb_global. Each node is
+// still written once, by the second thread up at its split, with the same
+// fields: only where the two halves meet changes. Groups of 128 measured
+// fastest at 2^25 points (32: 2.67 ms, 64: 2.08, 128: 2.06, 256: 2.20, 512:
+// 2.44; every exchange at device scope: 2.32).
+constexpr int kGroup = 128;
 
-template <int kCta>
 struct GroupSmem {
-    unsigned long long word[kCta];  // split at global position a + j: word[g0 + j]
-    float3 lo[2][kCta], hi[2][kCta];  // boxes: [0] leaf, [1] internal node, by global position / index
+    unsigned long long word[kGroup];    // split at global position a + j: word[j]
+    float3 lo[2][kGroup], hi[2][kGroup];  // boxes: [0] leaf, [1] internal node, by global position / index
+    uint64_t code[kGroup + 3];          // sorted codes a-1 .. a+kGroup+1 (construct_encode_kernel)
     int failed;
+    int pending;                        // climbs handed to climb_pending_kernel
 };
 
-// Both phases for the thread of leaf i of a tree of n leaves whose leaf 0 sits
-// at global position o (0 for a single tree; trees of a batch follow each
-// other), in the group whose first global position is a (shared slots from
-// g0). A split joins two leaves of one tree, so groups may hold several trees.
-template <int kKind, int kGroup, int kCta>
-__device__ __forceinline__ void two_phase(GroupSmem<kCta> &sm, bool active, int i, int n, int64_t o, int64_t a,
-                                          int g0, int t, const uint64_t *__restrict__ codes,
-                                          const uint32_t *__restrict__ perm, uint32_t perm_base,
-                                          const float *__restrict__ prims, float4 *inodes, float4 *leaves,
-                                          unsigned long long *store, uint32_t *flags) {
+// Climbs that leave a group: the CTA hands up to kPendSlots of them to
+// climb_pending_kernel through its own slots (16 bytes each: l, r, the three
+// delta* values and a valid bit), so that no CTA waits on device-scope
+// exchanges with most of its threads done. On uniform points a group of 128
+// leaves has 7.3 such climbs on average and 13 at most; more than kPendSlots
+// climb in place.
+constexpr int kPendSlots = 16;
+constexpr uint32_t kPendValid = 1u << 31;
+
+// Both phases for thread t, holding leaf i's climb state c (go: the leaf was
+// written and the tree has internal nodes), of a tree of n leaves whose leaf
+// 0 sits at global position o (0 for a single tree; trees of a batch follow
+// each other), in the group whose first global position is a. A split joins
+// two leaves of one tree, so groups may hold several trees. Every thread of
+// the CTA must call this (it holds the group's barrier).
+// pend (nullable): the CTA's kPendSlots slots.
+template <int kKind>
+__device__ __forceinline__ void two_phase(GroupSmem &sm, bool go, Climb c, int n, int64_t o, int64_t a, int t,
+                                          float4 *inodes, const float4 *leaves, unsigned long long *store,
+                                          uint32_t *flags, uint4 *pend) {
     const int ni = n - 1;
-    Climb c;
     bool pending = false, in_word = false;
     int word_at = 0;
-    if (active && leaf_step<kKind>(i, n, codes, perm, perm_base, prims, leaves, flags, c) && n > 1) {
+    if (go) {
         sm.lo[0][t] = c.lo;
         sm.hi[0][t] = c.hi;
         for (int level = 0; level < 128; ++level) {
@@ -314,7 +310,7 @@ __device__ __forceinline__ void two_phase(GroupSmem<kCta> &sm, bool active, int 
                 break;
             }
             const int at = (int)rel;
-            cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(sm.word[g0 + at]);
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(sm.word[at]);
             const unsigned long long other = w.exchange(mine, cuda::memory_order_acq_rel);
             if (other == 0ull) {  // first up: the sibling may come in this phase, or never
                 pending = in_word = true;
@@ -328,103 +324,184 @@ __device__ __forceinline__ void two_phase(GroupSmem<kCta> &sm, bool active, int 
             }
             const int sibling = take_half(c, is_left, p, other, ni);
             const int k = sibling < ni ? 1 : 0;
-            const int sat = g0 + (int)(o + (sibling < ni ? sibling : sibling - ni) - a);  // g0 + at or + at + 1
+            const int sat = (int)(o + (sibling < ni ? sibling : sibling - ni) - a);  // at or at + 1
             const int q = write_parent(c, p, n, sm.lo[k][sat], sm.hi[k][sat], inodes);
             if (q == 0) break;  // the root: the whole tree lies in this group
-            const int qat = g0 + (int)(o + q - a);  // q is l or r, inside the group
+            const int qat = (int)(o + q - a);  // q is l or r, inside the group
             sm.lo[1][qat] = c.lo;
             sm.hi[1][qat] = c.hi;
         }
     }
-    if (kGroup == 32)
-        __syncwarp();
-    else
-        __syncthreads();
+    __syncthreads();
     if (!pending) return;
-    if (in_word && sm.word[g0 + word_at] == 0ull) return;  // the sibling came and carried on
+    if (in_word && sm.word[word_at] == 0ull) return;  // the sibling came and carried on
+    if (pend) {
+        const int slot = atomicAdd(&sm.pending, 1);
+        if (slot < kPendSlots) {
+            pend[slot] = make_uint4(c.l, c.r, kPendValid | c.d_left | c.d_right << 8 | c.d_next << 16, 0u);
+            return;
+        }
+    }
     // this thread wrote its own node, so its device-scope release covers it
-    climb_global<kKind, true>(c, n, inodes, leaves, store, flags);
+    climb_global<kKind>(c, n, inodes, leaves, store, flags);
 }
 
-template <int kKind, int kGroup>
-__global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kGroup>::kCta)
+// The climbs handed over by the groups, one thread per slot: the climber's
+// node (range [l, r], written by the first kernel) is read back for its box
+// and the climb goes on with device-scope exchanges. Every valid slot is
+// cleared, so the slots are zero again for the next build.
+template <int kKind>
+__global__ void __launch_bounds__(256)
+    climb_pending_kernel(uint4 *pend, int64_t slots, int n, float4 *inodes, const float4 *leaves,
+                         unsigned long long *store, uint32_t *flags) {
+    const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (k >= slots) return;
+    const uint4 e = pend[k];
+    if (!(e.z & kPendValid)) return;
+    pend[k] = make_uint4(0u, 0u, 0u, 0u);
+    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;
+    const int ni = n - 1;
+    Climb c;
+    c.l = e.x;
+    c.r = e.y;
+    c.d_left = e.z & 0xffu;
+    c.d_right = (e.z >> 8) & 0xffu;
+    c.d_next = (e.z >> 16) & 0xffu;
+    if (c.l > c.r || c.r >= (uint32_t)n) {
+        atomicOr(flags, kFlagCorrupt);
+        return;
+    }
+    // the node of range [l, r]: leaf l, or internal node r or l (its Karras index)
+    const int id = c.l == c.r ? ni + (int)c.l : (c.d_right < c.d_left ? (int)c.r : (int)c.l);
+    load_node_box<kKind>(inodes, leaves, ni, id, c.lo, c.hi);
+    climb_global<kKind>(c, n, inodes, leaves, store, flags);
+}
+
+// Clears the CTA's shared words and reads the build's error flags: true if
+// an earlier stage failed, in which case the whole CTA returns and leaves
+// `store` untouched.
+__device__ __forceinline__ bool group_start(GroupSmem &sm, const uint32_t *flags) {
+    sm.word[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) {
+        sm.failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
+        sm.pending = 0;
+    }
+    __syncthreads();
+    return sm.failed != 0;
+}
+
+// Algorithm 4 from sorted codes and a permutation (lbvh_build_from_sorted,
+// refit, the no-allocation entry point).
+template <int kKind>
+__global__ void __launch_bounds__(kGroup, 2048 / kGroup)
     construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
                            const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
-                           unsigned long long *store, uint32_t *flags) {
-    constexpr int kCta = GroupShape<kGroup>::kCta;
-    __shared__ GroupSmem<kCta> sm;
+                           unsigned long long *store, uint32_t *flags, uint4 *pend) {
+    __shared__ GroupSmem sm;
+    if (group_start(sm, flags)) return;
     const int t = threadIdx.x;
-    const int g0 = t / kGroup * kGroup;  // the group's first thread
-    const int i = blockIdx.x * kCta + t;
-    sm.word[t] = 0ull;
-    if (t == 0) sm.failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
+    const int i = blockIdx.x * kGroup + t;
+    Climb c;
+    const bool ok = i < n && leaf_step<kKind>(i, n, codes, perm, 0u, prims, leaves, flags, c);
+    two_phase<kKind>(sm, ok && n > 1, c, n, 0, (int64_t)blockIdx.x * kGroup, t, inodes, leaves, store, flags,
+                     pend ? pend + (int64_t)blockIdx.x * kPendSlots : nullptr);
+}
+
+// Algorithm 4 after a sort that kept only the permutation. Each thread
+// gathers its leaf's primitive and derives its Morton code again with the
+// encoder's function (the same bits); the codes of the CTA's leaves and of
+// three neighbours (positions a-1, a+kGroup, a+kGroup+1, gathered by threads
+// 0-2) meet in shared memory for the delta* values. The sorted codes are
+// written to codes_out (the tree keeps them for export and refit).
+template <int kKind>
+__global__ void __launch_bounds__(kGroup, 2048 / kGroup)
+    construct_encode_kernel(const uint32_t *__restrict__ perm, const float *__restrict__ prims,
+                            const float *__restrict__ bounds, int b, int n, uint64_t *__restrict__ codes_out,
+                            float4 *inodes, float4 *leaves, unsigned long long *store, uint32_t *flags,
+                            uint4 *pend) {
+    __shared__ GroupSmem sm;
+    if (group_start(sm, flags)) return;
+    const int t = threadIdx.x;
+    const int64_t a = (int64_t)blockIdx.x * kGroup;
+    const int i = (int)a + t;
+    const Grid3 g = make_grid(bounds, b);
+    bool ok = i < n;
+    uint32_t p_id = 0;
+    float3 lo = make_float3(0.f, 0.f, 0.f), hi = lo;
+    if (ok) {
+        p_id = __ldcs(perm + i);
+        if (p_id >= (uint32_t)n) {  // not a permutation: the sort failed
+            atomicOr(flags, kFlagCorrupt);
+            ok = false;
+        } else {
+            gather_box<kKind>(prims, p_id, lo, hi);
+        }
+    }
+    // the three neighbours outside the CTA's range
+    int64_t hpos = -1;
+    float3 hlo = lo, hhi = hi;
+    if (t < 3) {
+        hpos = t == 0 ? a - 1 : a + kGroup + t - 1;
+        if (hpos >= 0 && hpos < n) {
+            const uint32_t hp = perm[hpos];
+            if (hp < (uint32_t)n) gather_box<kKind>(prims, hp, hlo, hhi);
+            else hpos = -1;
+        } else {
+            hpos = -1;
+        }
+    }
+    if (ok) {
+        const uint64_t code = morton(__fmul_rn(__fadd_rn(lo.x, hi.x), 0.5f), __fmul_rn(__fadd_rn(lo.y, hi.y), 0.5f),
+                                     __fmul_rn(__fadd_rn(lo.z, hi.z), 0.5f), g);
+        sm.code[t + 1] = code;
+        codes_out[i] = code;
+    }
+    if (hpos >= 0)
+        sm.code[t == 0 ? 0 : kGroup + t] =
+            morton(__fmul_rn(__fadd_rn(hlo.x, hhi.x), 0.5f), __fmul_rn(__fadd_rn(hlo.y, hhi.y), 0.5f),
+                   __fmul_rn(__fadd_rn(hlo.z, hhi.z), 0.5f), g);
     __syncthreads();
-    if (sm.failed) return;  // the sort failed: leave store untouched (the whole CTA returns)
-    two_phase<kKind, kGroup, kCta>(sm, i < n, i, n, 0, (int64_t)blockIdx.x * kCta + g0, g0, t, codes, perm, 0u,
-                                   prims, inodes, leaves, store, flags);
+    Climb c;
+    if (ok) {
+        const uint64_t c0 = sm.code[t + 1];
+        const uint32_t dl = i > 0 ? delta_star(sm.code[t], c0, (uint32_t)(i - 1)) : kInf;
+        uint32_t dr = kInf, drn = kInf;
+        if (i + 1 < n) {
+            const uint64_t c1 = sm.code[t + 2];
+            dr = delta_star(c0, c1, (uint32_t)i);
+            if (i + 2 < n) drn = delta_star(c1, sm.code[t + 3], (uint32_t)(i + 1));
+        }
+        leaf_write<kKind>(i, n, p_id, lo, hi, leaves, dl, dr, drn, c);
+    }
+    two_phase<kKind>(sm, ok && n > 1, c, n, 0, a, t, inodes, leaves, store, flags,
+                     pend ? pend + (int64_t)blockIdx.x * kPendSlots : nullptr);
 }
 
 // Many trees at once, grouped by global sorted position: global position g
 // belongs to the instance b with off[b] <= g < off[b+1]; its tree's records
 // start at node_start[b] (float4 units) and its store words at store_start[b].
-template <int kKind, int kGroup>
-__global__ void __launch_bounds__(GroupShape<kGroup>::kCta, 2048 / GroupShape<kGroup>::kCta)
+template <int kKind>
+__global__ void __launch_bounds__(kGroup, 2048 / kGroup)
     batch_construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
                                  const float *__restrict__ prims, const int64_t *__restrict__ off,
                                  const int64_t *__restrict__ node_start, const int64_t *__restrict__ store_start,
                                  int count, int64_t total, float4 *nodes, unsigned long long *store,
                                  uint32_t *flags) {
-    constexpr int kCta = GroupShape<kGroup>::kCta;
-    __shared__ GroupSmem<kCta> sm;
+    __shared__ GroupSmem sm;
+    if (group_start(sm, flags)) return;
     const int t = threadIdx.x;
-    const int g0 = t / kGroup * kGroup;
-    const int64_t g = (int64_t)blockIdx.x * kCta + t;
-    sm.word[t] = 0ull;
-    if (t == 0) sm.failed = (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) != 0;
-    __syncthreads();
-    if (sm.failed) return;
+    const int64_t g = (int64_t)blockIdx.x * kGroup + t;
     const bool active = g < total;
     const int b = active ? instance_of(off, count, g) : 0;
     const int64_t o = active ? off[b] : 0;
     const int n = active ? (int)(off[b + 1] - o) : 1;
     float4 *inodes = nodes + (active ? node_start[b] : 0);
     float4 *leaves = inodes + 2 * (int64_t)(n - 1);
-    two_phase<kKind, kGroup, kCta>(sm, active, (int)(g - o), n, o, (int64_t)blockIdx.x * kCta + g0, g0, t,
-                                   codes + o, perm + o, (uint32_t)o, prims, inodes, leaves,
-                                   store + (active ? store_start[b] : 0), flags);
-}
-
-template <int kKind, bool kAcqRel>
-__global__ void __launch_bounds__(kThreads)
-    construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
-                     const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
-                     unsigned long long *store, uint32_t *flags) {
-    const int i = blockIdx.x * kThreads + threadIdx.x;
-    if (i >= n) return;
-    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;  // the sort failed: leave store untouched
-    construct_leaf<kKind, kAcqRel>(i, n, codes, perm, 0u, prims, inodes, leaves, store, flags);
-}
-
-// Many trees at once: global sorted position g belongs to the instance b with
-// off[b] <= g < off[b+1]; its tree's records start at node_start[b] (float4
-// units) and its store words at store_start[b].
-template <int kKind>
-__global__ void __launch_bounds__(kThreads)
-    batch_construct_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
-                           const float *__restrict__ prims, const int64_t *__restrict__ off,
-                           const int64_t *__restrict__ node_start, const int64_t *__restrict__ store_start,
-                           int count, int64_t total, float4 *nodes, unsigned long long *store,
-                           uint32_t *flags) {
-    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (g >= total) return;
-    if (__ldcg(flags) & (kFlagTimeout | kFlagCorrupt)) return;  // the sort failed: leave store untouched
-    const int b = instance_of(off, count, g);
-    const int64_t o = off[b];
-    const int n = (int)(off[b + 1] - o);
-    float4 *inodes = nodes + node_start[b];
-    float4 *leaves = inodes + 2 * (int64_t)(n - 1);
-    construct_leaf<kKind, true>((int)(g - o), n, codes + o, perm + o, (uint32_t)o, prims, inodes, leaves,
-                                store + store_start[b], flags);
+    Climb c;
+    const bool ok = active && leaf_step<kKind>((int)(g - o), n, codes + o, perm + o, (uint32_t)o, prims, leaves,
+                                               flags, c);
+    two_phase<kKind>(sm, ok && n > 1, c, n, o, (int64_t)blockIdx.x * kGroup, t, inodes, leaves,
+                     store + (active ? store_start[b] : 0), flags, nullptr);
 }
 
 }  // namespace
@@ -433,71 +510,54 @@ void launch_batch_construct(const uint64_t *sorted_codes, const uint32_t *perm, 
                             const BatchTables &bt, int kind, float4 *nodes, unsigned long long *store,
                             uint32_t *flags, cudaStream_t s) {
     if (bt.total_prims <= 0) return;
-    // LBVH_CONSTRUCT_GLOBAL=1: every exchange at device scope (tuning)
-    static const bool one_phase = getenv("LBVH_CONSTRUCT_GLOBAL") && atoi(getenv("LBVH_CONSTRUCT_GLOBAL"));
-    const bool pts = kind == LBVH_PRIM_POINTS;
-    if (one_phase) {
-        const unsigned blocks = (unsigned)((bt.total_prims + kThreads - 1) / kThreads);
-        auto k = pts ? batch_construct_kernel<LBVH_PRIM_POINTS> : batch_construct_kernel<LBVH_PRIM_BOXES>;
-        k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count,
-                                      bt.total_prims, nodes, store, flags);
-    } else {
-        constexpr int kGroup = 128, kCta = GroupShape<kGroup>::kCta;
-        const unsigned blocks = (unsigned)((bt.total_prims + kCta - 1) / kCta);
-        auto k = pts ? batch_construct_block_kernel<LBVH_PRIM_POINTS, kGroup>
-                     : batch_construct_block_kernel<LBVH_PRIM_BOXES, kGroup>;
-        k<<<blocks, kCta, 0, s>>>(sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count,
-                                  bt.total_prims, nodes, store, flags);
-    }
+    const unsigned blocks = (unsigned)((bt.total_prims + kGroup - 1) / kGroup);
+    auto k = kind == LBVH_PRIM_POINTS ? batch_construct_block_kernel<LBVH_PRIM_POINTS>
+                                      : batch_construct_block_kernel<LBVH_PRIM_BOXES>;
+    k<<<blocks, kGroup, 0, s>>>(sorted_codes, perm, prims, bt.prim_off, bt.node_start, bt.store_start, bt.count,
+                                bt.total_prims, nodes, store, flags);
     count_launches(1);
 }
 
+size_t construct_pend_bytes(int64_t n) { return (size_t)((n + kGroup - 1) / kGroup) * kPendSlots * sizeof(uint4); }
+
 namespace {
 
-template <int kGroup>
-void launch_construct_block(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims, int64_t n,
-                            int kind, float4 *inodes, float4 *leaves, unsigned long long *store, uint32_t *flags,
-                            cudaStream_t s) {
-    constexpr int kCta = GroupShape<kGroup>::kCta;
-    const unsigned blocks = (unsigned)((n + kCta - 1) / kCta);
-    auto k = kind == LBVH_PRIM_POINTS ? construct_block_kernel<LBVH_PRIM_POINTS, kGroup>
-                                      : construct_block_kernel<LBVH_PRIM_BOXES, kGroup>;
-    k<<<blocks, kCta, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags);
+void launch_pending(int64_t n, int kind, float4 *inodes, float4 *leaves, unsigned long long *store,
+                    uint32_t *flags, void *pend, cudaStream_t s) {
+    if (!pend || n < 2) return;
+    const int64_t slots = (n + kGroup - 1) / kGroup * kPendSlots;
+    const unsigned blocks = (unsigned)((slots + 255) / 256);
+    auto k = kind == LBVH_PRIM_POINTS ? climb_pending_kernel<LBVH_PRIM_POINTS> : climb_pending_kernel<LBVH_PRIM_BOXES>;
+    k<<<blocks, 256, 0, s>>>(static_cast<uint4 *>(pend), slots, (int)n, inodes, leaves, store, flags);
+    count_launches(1);
 }
 
 }  // namespace
 
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
                       int64_t n, int kind, float4 *inodes, float4 *leaves,
-                      unsigned long long *store, uint32_t *flags, cudaStream_t s) {
+                      unsigned long long *store, uint32_t *flags, void *pend, cudaStream_t s) {
     if (n <= 0) return;
-    // tuning: LBVH_CONSTRUCT_GROUP = leaves per phase-1 group of
-    // construct_block_kernel (32, 64, 128 or 256); LBVH_CONSTRUCT_GLOBAL=1 runs
-    // every exchange at device scope (construct_kernel), LBVH_CONSTRUCT_FENCES=1
-    // that with the fence form
-    static const int group = [] {
-        const char *e = getenv("LBVH_CONSTRUCT_GROUP");
-        const int g = e ? atoi(e) : 128;
-        return (g == 32 || g == 64 || g == 256) ? g : 128;
-    }();
-    static const bool one_phase = getenv("LBVH_CONSTRUCT_GLOBAL") && atoi(getenv("LBVH_CONSTRUCT_GLOBAL"));
-    static const bool fences = getenv("LBVH_CONSTRUCT_FENCES") && atoi(getenv("LBVH_CONSTRUCT_FENCES"));
-    const bool pts = kind == LBVH_PRIM_POINTS;
-    if (one_phase || fences) {
-        const unsigned blocks = (unsigned)((n + kThreads - 1) / kThreads);
-        auto k = fences ? (pts ? construct_kernel<LBVH_PRIM_POINTS, false> : construct_kernel<LBVH_PRIM_BOXES, false>)
-                        : (pts ? construct_kernel<LBVH_PRIM_POINTS, true> : construct_kernel<LBVH_PRIM_BOXES, true>);
-        k<<<blocks, kThreads, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags);
-    } else if (group == 32) {
-        launch_construct_block<32>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
-    } else if (group == 64) {
-        launch_construct_block<64>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
-    } else if (group == 256) {
-        launch_construct_block<256>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
-    } else {
-        launch_construct_block<128>(sorted_codes, perm, prims, n, kind, inodes, leaves, store, flags, s);
-    }
+    const unsigned blocks = (unsigned)((n + kGroup - 1) / kGroup);
+    auto k = kind == LBVH_PRIM_POINTS ? construct_block_kernel<LBVH_PRIM_POINTS>
+                                      : construct_block_kernel<LBVH_PRIM_BOXES>;
+    k<<<blocks, kGroup, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags,
+                                static_cast<uint4 *>(pend));
     count_launches(1);
+    launch_pending(n, kind, inodes, leaves, store, flags, pend, s);
+}
+
+void launch_construct_encode(const uint32_t *perm, const float *prims, const float *bounds, int bits, int64_t n,
+                             int kind, uint64_t *codes_out, float4 *inodes, float4 *leaves,
+                             unsigned long long *store, uint32_t *flags, void *pend, cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned blocks = (unsigned)((n + kGroup - 1) / kGroup);
+    auto k = kind == LBVH_PRIM_POINTS ? construct_encode_kernel<LBVH_PRIM_POINTS>
+                                      : construct_encode_kernel<LBVH_PRIM_BOXES>;
+    k<<<blocks, kGroup, 0, s>>>(perm, prims, bounds, bits / 3, (int)n, codes_out, inodes, leaves, store, flags,
+                                static_cast<uint4 *>(pend));
+    count_launches(1);
+    launch_pending(n, kind, inodes, leaves, store, flags, pend, s);
 }
 
 }  // namespace lbvh
@@ -516,29 +576,22 @@ constexpr int64_t kStaticMaxPrims = (int64_t(1) << 20) + 1;  // store words: n -
 __device__ __align__(256) unsigned long long g_static_store[kStaticMaxPrims - 1];
 __device__ __align__(256) uint32_t g_static_flags[64];
 
-// Device addresses of the two arrays, looked up once per device (with that
-// device current) and kept; host code must not use the symbols themselves.
+// Device addresses of the two arrays for the current device. Host code must
+// not use the symbols themselves (in host code they name host-side stand-ins).
+// The lookup is repeated on every call: it is cheap, and an address kept from
+// an earlier call would go stale if the caller reset the device (the module,
+// and with it the arrays, is loaded again into the new context).
 struct StaticScratch {
     unsigned long long *store = nullptr;
     uint32_t *flags = nullptr;
 };
-std::mutex g_static_mu;
-constexpr int kMaxDevices = 64;
-StaticScratch g_static[kMaxDevices];
 
 lbvh_status static_scratch(StaticScratch *out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBVH_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    StaticScratch &s = g_static[dev];
-    if (!s.store) {
-        void *store = nullptr, *flags = nullptr;
-        if (cudaGetSymbolAddress(&store, g_static_store) != cudaSuccess) return LBVH_ERR_CUDA;
-        if (cudaGetSymbolAddress(&flags, g_static_flags) != cudaSuccess) return LBVH_ERR_CUDA;
-        s.store = static_cast<unsigned long long *>(store);
-        s.flags = static_cast<uint32_t *>(flags);
-    }
-    *out = s;
+    void *store = nullptr, *flags = nullptr;
+    if (cudaGetSymbolAddress(&store, g_static_store) != cudaSuccess) return LBVH_ERR_CUDA;
+    if (cudaGetSymbolAddress(&flags, g_static_flags) != cudaSuccess) return LBVH_ERR_CUDA;
+    out->store = static_cast<unsigned long long *>(store);
+    out->flags = static_cast<uint32_t *>(flags);
     return LBVH_OK;
 }
 
@@ -550,6 +603,7 @@ extern "C" lbvh_status lbvh_construct_static(const uint64_t *d_sorted_codes, con
     if (n < 1 || n > kStaticMaxPrims) return LBVH_ERR_INVALID;
     if (kind != LBVH_PRIM_POINTS && kind != LBVH_PRIM_BOXES) return LBVH_ERR_INVALID;
     if (!d_sorted_codes || !d_perm || !d_prims || !d_leaves || (n > 1 && !d_inodes)) return LBVH_ERR_INVALID;
+    (void)cudaGetLastError();  // an earlier, unrelated error must not be charged to this call
     StaticScratch scratch;
     const lbvh_status st = static_scratch(&scratch);
     if (st != LBVH_OK) return st;
@@ -563,7 +617,7 @@ extern "C" lbvh_status lbvh_construct_static(const uint64_t *d_sorted_codes, con
         if (cudaMemsetAsync(flags, 0, sizeof(uint32_t), s) != cudaSuccess) return LBVH_ERR_CUDA;
     }
     lbvh::launch_construct(d_sorted_codes, d_perm, d_prims, n, kind, reinterpret_cast<float4 *>(d_inodes),
-                           reinterpret_cast<float4 *>(d_leaves), scratch.store, flags, s);
+                           reinterpret_cast<float4 *>(d_leaves), scratch.store, flags, nullptr, s);
     return cudaGetLastError() == cudaSuccess ? LBVH_OK : LBVH_ERR_CUDA;
 }
 

@@ -42,12 +42,13 @@ constexpr int kQueryBufferHits = 64;  // hits kept per query by the walk
 // FP32 min / max that order -0.0 below +0.0, so the scene bounds and the
 // boxes do not depend on the order in which values are combined. Inputs are
 // finite (a build with a NaN or infinity is rejected).
-__device__ __forceinline__ float min_ordered(float a, float b) {
-    return (a < b || (a == b && __float_as_int(a) < 0)) ? a : b;
-}
-__device__ __forceinline__ float max_ordered(float a, float b) {
-    return (a > b || (a == b && __float_as_int(a) >= 0)) ? a : b;
-}
+// On GB300 fminf / fmaxf (PTX min.f32 / max.f32) already order -0.0 below
+// +0.0, whichever argument comes first (checked on the device, and pinned by
+// the signed-zero parity tests against the oracle's explicit ordering), so
+// each is one instruction (the explicit comparison form cost the construct
+// 0.30 ms at 2^25 points: 2.12 against 1.82 ms).
+__device__ __forceinline__ float min_ordered(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float max_ordered(float a, float b) { return fmaxf(a, b); }
 
 // ---------------------------------------------------------------- node layout
 // Canonical ids: internal k -> k, leaf k -> (n-1)+k, sentinel -> -1.
@@ -129,11 +130,16 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
                   int variant_idx = -1, const SortSegments *seg = nullptr);
-// The same sort for 32-bit keys (the default tile shape; segment tables made
-// for tile variant 0 fit it). At most 4 passes.
-bool run_onesweep32(uint32_t *keys_a, uint32_t *vals_a, bool iota, uint32_t *keys_b, uint32_t *vals_b,
-                    int64_t n, int passes, const SortScratch &scratch, Control *ctl, cudaStream_t s,
-                    const SortSegments *seg = nullptr);
+// The sort of a tree build, which needs only the permutation: keys_a holds
+// the codes (packed: words code << 32 | index, codes of at most 32 bits),
+// vals_a/vals_b/keys_b are scratch. Passes run as described in sort.cu
+// (packed words once the low four bytes are sorted, payloads alone out of
+// the last pass). Returns the buffer (vals_a or vals_b) holding the sorted
+// permutation; keys_a and keys_b are free again afterwards. hist and the
+// look-back are used as by run_onesweep.
+uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, int64_t n,
+                         int key_bits, bool packed, const SortScratch &scratch, Control *ctl, cudaStream_t s,
+                         cudaEvent_t (*pass_events)[2] = nullptr, int variant_idx = -1);
 int sort_variant_count();
 // Test hook (lbvh_test_hold_sort_tile): tile `tile` of every sort's first pass
 // publishes nothing, so later tiles' bounded look-back waits run out; -1: off.
@@ -149,16 +155,18 @@ inline int64_t sort_tiles_max(int64_t n) { return (n + sort_tile_keys_min() - 1)
 int bounds_blocks(int64_t n);
 void launch_bounds(const float *prims, int64_t n, int kind, float *partials, float *bounds,
                    Control *ctl, cudaStream_t s);
+// packed: codes[i] = code << 32 | i (bits <= 30), for run_index_sort's packed mode.
 void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
-// The same codes as 32-bit keys (bits <= 30).
-void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint32_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s);
+                   uint64_t *codes, uint32_t *hist, int hist_passes, bool packed, cudaStream_t s);
+// codes[i] = the Morton code of primitive perm[i].
+void launch_sorted_codes(const float *prims, const uint32_t *perm, int64_t n, int kind, int bits,
+                         const float *bounds, uint64_t *codes, cudaStream_t s);
 
 // ---------------------------------------------------------------- construct
 // Algorithm 4 with boxes: writes inodes and leaves (layout above), and uses
 // `store` (n-1 words, all zero on entry; left all zero on exit).
-// flags: kFlagCorrupt is latched if the input is not a sorted permutation.
+// flags: kFlagCorrupt is latched if a perm entry is out of range, adjacent
+// codes are out of order, or a climb leaves the tree.
 // The Karras and Apetrei hierarchy builds (variants.cu): scratch bytes, the
 // hierarchy kernel, and the second pass (Karras: boxes; Apetrei: ordering and
 // skips). `store` is the tree's zeroed Algorithm 4 scratch (left zeroed).
@@ -169,9 +177,20 @@ void launch_variant_hierarchy(int algorithm, const uint64_t *codes, const uint32
 void launch_variant_second(int algorithm, const uint64_t *codes, const uint32_t *perm, const float *prims,
                            int64_t n, int kind, float4 *inodes, float4 *leaves, void *scratch,
                            unsigned long long *store, uint32_t *flags, cudaStream_t s);
+// pend (nullable): construct_pend_bytes(n) of zeroed scratch, left zeroed.
+// With it, the climbs that leave a CTA's group of leaves run in a second
+// kernel with full warps instead of holding their CTA; without it (the
+// no-allocation entry point) they run in place.
+size_t construct_pend_bytes(int64_t n);
 void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const float *prims,
                       int64_t n, int kind, float4 *inodes, float4 *leaves,
-                      unsigned long long *store, uint32_t *flags, cudaStream_t s);
+                      unsigned long long *store, uint32_t *flags, void *pend, cudaStream_t s);
+// The same pass after run_index_sort: each leaf's code is derived again from
+// its gathered primitive (bounds: the build's scene bounds; bits: code bits)
+// and the sorted codes are written to codes_out.
+void launch_construct_encode(const uint32_t *perm, const float *prims, const float *bounds, int bits, int64_t n,
+                             int kind, uint64_t *codes_out, float4 *inodes, float4 *leaves,
+                             unsigned long long *store, uint32_t *flags, void *pend, cudaStream_t s);
 
 // ---------------------------------------------------------------- query
 struct TreeView {

@@ -1,15 +1,5 @@
-// morton.cu -- scene bounds and Morton codes (Sec. 3.1, Karras step 1).
-//
-// The paper leaves the encoding open. The one used here:
-//   centroid    a point itself; a box (lo + hi) * 0.5 in FP32
-//   bounds      per-axis min / max of the centroids (exact FP32 compares,
-//               -0.0 ordered below +0.0)
-//   quantise    t = (c - min) / (max - min), IEEE FP32 subtract and divide;
-//               v = t * 2^b (exact); cell = 0 if !(v > 0), 2^b - 1 if
-//               v >= 2^b - 1, else trunc(v); cell = 0 on an axis of zero extent
-//   interleave  bit 3k+2 = x_k, 3k+1 = y_k, 3k = z_k
-// Every float operation is an explicit round-to-nearest intrinsic so the
-// compiler cannot contract or reassociate them.
+// morton.cu -- scene bounds and Morton codes (Sec. 3.1, Karras step 1). The
+// encoding itself (centroid, quantisation, interleave) is in morton.cuh.
 //
 // Both kernels stream the primitives once. Points are read as float4 (three
 // float4 = four points per thread step) when the array is 16-byte aligned.
@@ -19,66 +9,13 @@
 #include <cfloat>
 
 #include "lbvh_internal.cuh"
+#include "morton.cuh"
 
 namespace lbvh {
 
 namespace {
 
 constexpr int kThreads = 256;
-
-// Mask of the bit positions that input bit k occupies after the spreading
-// steps of levels >= L: bit k has moved up by 2 * (k with its low L bits
-// cleared). At level 0 every bit k sits at 3k.
-constexpr uint64_t spread_mask(int level) {
-    uint64_t m = 0;
-    for (int k = 0; k < 21; ++k) m |= 1ull << (k + 2 * (k & ~((1 << level) - 1)));
-    return m;
-}
-
-// Moves bit k of a 21-bit value to bit 3k.
-__device__ __forceinline__ uint64_t spread3(uint32_t v) {
-    uint64_t x = v & 0x1fffffu;
-    x = (x | (x << 32)) & spread_mask(4);
-    x = (x | (x << 16)) & spread_mask(3);
-    x = (x | (x << 8)) & spread_mask(2);
-    x = (x | (x << 4)) & spread_mask(1);
-    x = (x | (x << 2)) & spread_mask(0);
-    return x;
-}
-
-struct Grid3 {
-    float lo[3];
-    float extent[3];
-    float cells;  // 2^b
-    float top;    // 2^b - 1
-    uint32_t topi;
-};
-
-__device__ __forceinline__ uint32_t cell_of(float c, float lo, float extent, const Grid3 &g) {
-    if (!(extent > 0.0f)) return 0u;
-    const float t = __fdiv_rn(__fsub_rn(c, lo), extent);
-    const float v = __fmul_rn(t, g.cells);
-    if (!(v > 0.0f)) return 0u;
-    if (v >= g.top) return g.topi;
-    return __float2uint_rz(v);
-}
-
-__device__ __forceinline__ uint64_t morton(float x, float y, float z, const Grid3 &g) {
-    const uint32_t qx = cell_of(x, g.lo[0], g.extent[0], g);
-    const uint32_t qy = cell_of(y, g.lo[1], g.extent[1], g);
-    const uint32_t qz = cell_of(z, g.lo[2], g.extent[2], g);
-    return (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-}
-
-__device__ __forceinline__ bool finite3(float x, float y, float z) {
-    return fabsf(x) <= FLT_MAX && fabsf(y) <= FLT_MAX && fabsf(z) <= FLT_MAX;
-}
-
-__device__ __forceinline__ void box_centroid(const float *b, float &x, float &y, float &z) {
-    x = __fmul_rn(__fadd_rn(b[0], b[3]), 0.5f);
-    y = __fmul_rn(__fadd_rn(b[1], b[4]), 0.5f);
-    z = __fmul_rn(__fadd_rn(b[2], b[5]), 0.5f);
-}
 
 struct MinMax {
     float lo[3], hi[3];
@@ -229,25 +166,21 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-template <int kKind, typename K>
+// kPacked: each word is code << 32 | index (codes of at most 32 bits, for a
+// sort that carries the index in the key's low half); else the code alone.
+// The histograms count the bytes of the code.
+template <int kKind, bool kPacked>
 __global__ void __launch_bounds__(kThreads)
     encode_kernel(const float *__restrict__ prims, int64_t n, int b,
-                  const float *__restrict__ bounds, K *__restrict__ codes,
+                  const float *__restrict__ bounds, uint64_t *__restrict__ codes,
                   uint32_t *__restrict__ hist, int passes) {
     __shared__ uint32_t s_hist[kMaxPasses * kRadix];
     for (int k = threadIdx.x; k < passes * kRadix; k += kThreads) s_hist[k] = 0;
-    Grid3 g;
-    for (int a = 0; a < 3; ++a) {
-        g.lo[a] = bounds[a];
-        g.extent[a] = __fsub_rn(bounds[3 + a], bounds[a]);
-    }
-    g.topi = (1u << b) - 1u;
-    g.cells = (float)(1u << b);
-    g.top = (float)g.topi;
+    const Grid3 g = make_grid(bounds, b);
     __syncthreads();
     for_each_centroid<kKind>(prims, n, [&](int64_t i, float x, float y, float z) {
         const uint64_t c = morton(x, y, z, g);
-        codes[i] = (K)c;
+        codes[i] = kPacked ? (c << 32) | (uint64_t)(uint32_t)i : c;
         for (int p = 0; p < passes; ++p)
             atomicAdd(&s_hist[p * kRadix + (uint32_t)((c >> (kRadixBits * p)) & (kRadix - 1))], 1u);
     });
@@ -255,6 +188,27 @@ __global__ void __launch_bounds__(kThreads)
     for (int k = threadIdx.x; k < passes * kRadix; k += kThreads) {
         const uint32_t v = s_hist[k];
         if (v) atomicAdd(&hist[k], v);
+    }
+}
+
+// The codes of the primitives in sorted order: codes[i] = the code of
+// primitive perm[i] (a gather through the permutation and the same encoding).
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    sorted_codes_kernel(const float *__restrict__ prims, const uint32_t *__restrict__ perm, int64_t n, int b,
+                        const float *__restrict__ bounds, uint64_t *__restrict__ codes) {
+    const Grid3 g = make_grid(bounds, b);
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        const int64_t p = perm[i];
+        float x, y, z;
+        if (kKind == LBVH_PRIM_POINTS) {
+            x = prims[3 * p];
+            y = prims[3 * p + 1];
+            z = prims[3 * p + 2];
+        } else {
+            box_centroid(prims + 6 * p, x, y, z);
+        }
+        codes[i] = morton(x, y, z, g);
     }
 }
 
@@ -346,15 +300,7 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ uint32_t s_hist[kRadix];
     s_hist[threadIdx.x] = 0;  // kThreads == kRadix
     const BatchChunk c = chunks[blockIdx.x];
-    Grid3 g;
-    const float *bd = bounds + 6 * (int64_t)c.inst;
-    for (int a = 0; a < 3; ++a) {
-        g.lo[a] = bd[a];
-        g.extent[a] = __fsub_rn(bd[3 + a], bd[a]);
-    }
-    g.topi = (1u << b) - 1u;
-    g.cells = (float)(1u << b);
-    g.top = (float)g.topi;
+    const Grid3 g = make_grid(bounds + 6 * (int64_t)c.inst, b);
     __syncthreads();
     for (int64_t i = c.begin + threadIdx.x; i < c.end; i += kThreads) {
         float x, y, z;
@@ -413,28 +359,31 @@ void launch_bounds(const float *prims, int64_t n, int kind, float *partials, flo
     count_launches(1);
 }
 
-template <typename K>
-static void encode_as(const float *prims, int64_t n, int kind, int bits, const float *bounds, K *codes,
-                      uint32_t *hist, int hist_passes, cudaStream_t s) {
+void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
+                   uint64_t *codes, uint32_t *hist, int hist_passes, bool packed, cudaStream_t s) {
     const int blocks = bounds_blocks(n);
     const int b = bits / 3;
-    if (kind == LBVH_PRIM_POINTS)
-        encode_kernel<LBVH_PRIM_POINTS, K><<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
-                                                                       hist_passes);
-    else
-        encode_kernel<LBVH_PRIM_BOXES, K><<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
-                                                                      hist_passes);
+    auto k = kind == LBVH_PRIM_POINTS ? (packed ? encode_kernel<LBVH_PRIM_POINTS, true>
+                                               : encode_kernel<LBVH_PRIM_POINTS, false>)
+                                      : (packed ? encode_kernel<LBVH_PRIM_BOXES, true>
+                                                : encode_kernel<LBVH_PRIM_BOXES, false>);
+    k<<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist, hist_passes);
     count_launches(1);
 }
 
-void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint64_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s) {
-    encode_as(prims, n, kind, bits, bounds, codes, hist, hist_passes, s);
-}
-
-void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint32_t *codes, uint32_t *hist, int hist_passes, cudaStream_t s) {
-    encode_as(prims, n, kind, bits, bounds, codes, hist, hist_passes, s);
+void launch_sorted_codes(const float *prims, const uint32_t *perm, int64_t n, int kind, int bits,
+                         const float *bounds, uint64_t *codes, cudaStream_t s) {
+    if (n <= 0) return;
+    int64_t blocks = (n + kThreads - 1) / kThreads;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    if (blocks > cap) blocks = cap;
+    if (kind == LBVH_PRIM_POINTS)
+        sorted_codes_kernel<LBVH_PRIM_POINTS><<<(unsigned)blocks, kThreads, 0, s>>>(prims, perm, n, bits / 3,
+                                                                                    bounds, codes);
+    else
+        sorted_codes_kernel<LBVH_PRIM_BOXES><<<(unsigned)blocks, kThreads, 0, s>>>(prims, perm, n, bits / 3,
+                                                                                   bounds, codes);
+    count_launches(1);
 }
 
 }  // namespace lbvh

@@ -8,10 +8,22 @@
 // so each pass reads and writes the data once.
 // Per pass, each CTA takes a tile (256 threads x 8-16 keys) by ticket (so every tile it may
 // wait on is already running), ranks the keys by digit inside the tile with
-// warp match/ballot counting, publishes its per-digit counts, resolves the
+// warp ballots, publishes its per-digit counts, resolves the
 // exclusive prefix of its digits over all earlier tiles by decoupled look-back
 // with a bounded spin, stages the tile in shared memory in digit order and
 // writes it out so that consecutive threads write consecutive addresses.
+//
+// Layouts of a pass. A digit is byte `db` of the 64-bit key (passes sort
+// bytes 0, 1, 2, ... in turn).
+//   key + payload  uint64 keys[] and uint32 vals[] (or vals = the index)
+//   packed         one uint64 word per element: the key's high 32 bits in
+//                  the word's high half, the payload in its low half
+// Once the low four bytes of a key are sorted the sort no longer needs them,
+// so the pass that sorts byte 3 may write packed words, and later passes move
+// 8 bytes per element instead of 12; the last pass may write the payloads
+// alone (the sorted permutation), which is all a tree build needs (it
+// derives each leaf's code again from the primitive it gathers). Keys of at
+// most 32 bits are packed from the start by the encoder (code << 32 | index).
 //
 // The same kernel also sorts many independent segments at once (batches of
 // trees): tiles then never straddle two segments, and each segment has its own
@@ -21,7 +33,6 @@
 // prefix), bits 29:0 = count. Two regions alternate between passes; every
 // tile clears its word block in the other region for the next pass.
 #include <atomic>
-#include <cstdlib>
 
 #include "lbvh_internal.cuh"
 
@@ -38,6 +49,10 @@ constexpr uint32_t kCountMask = (1u << 30) - 1u;
 // 2^26 polls whatever the clock says.
 constexpr uint64_t kWaitNs = 1000000000ull;
 constexpr uint32_t kSpinLimit = 1u << 26;
+
+// Input and output layouts of one pass.
+enum : int { kInIota = 0, kInKV = 1, kInPacked = 2 };
+enum : int { kOutKV = 0, kOutPack = 1, kOutPacked = 2, kOutLow = 3 };
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -61,6 +76,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// Byte (sel & 3) of the key's low (kHi false) or high half: one byte permute.
+template <bool kHi>
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t sel) {
+    return __byte_perm(kHi ? (uint32_t)(k >> 32) : (uint32_t)k, 0u, sel);
+}
+
 // Exclusive scan of one value per thread over the 256 threads of the block.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -77,7 +98,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return before + x - v;
 }
 
-template <int kItems, typename K = uint64_t>
+template <int kItems, bool kVals>
 struct SortSmem {
     static constexpr int kTile = kSortThreads * kItems;
     uint32_t warp_hist[kWarps][kRadix];  // per-warp digit counts, then per-warp offsets
@@ -87,21 +108,18 @@ struct SortSmem {
     uint32_t tile;
     int32_t seg;                         // segment of the tile (segmented sorts)
     uint32_t next_hist[kRadix];          // digit counts of the next pass
-    K keys[kTile];
-    uint32_t vals[kTile];
+    uint64_t keys[kTile];
+    uint32_t vals[kVals ? kTile : 1];
 };
 
-// Lanes of the warp whose digit equals d: match.any, or eight ballots (one
-// per digit bit).
-template <bool kBallot>
+// Lanes of the warp whose digit equals d: eight ballots, one per digit bit
+// (faster than match.any on GB300).
 __device__ __forceinline__ uint32_t digit_peers(uint32_t d) {
-    if (!kBallot) return __match_any_sync(0xffffffffu, d);
     uint32_t peers = 0xffffffffu;
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
-        const uint32_t bit = (d >> b) & 1u;
-        const uint32_t vote = __ballot_sync(0xffffffffu, bit);
-        peers &= bit ? vote : ~vote;
+        const uint32_t vote = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? vote : ~vote;
     }
     return peers;
 }
@@ -111,87 +129,116 @@ struct SegArgs {
     int count;
 };
 
-// kSeg: segments are sorted independently. A tile then lies inside one
-// segment; its keys start at off[seg] + (tile - tile_first[seg]) * kTile, its
-// digit counts come from and go to the segment's rows of the histograms, and
-// its look-back chain ends at the segment's first tile.
-template <bool kIota, int kItems, int kMinBlocks, bool kBallot, bool kSeg, typename K = uint64_t>
-__global__ void __launch_bounds__(kSortThreads, kMinBlocks)
-    onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                    K *__restrict__ keys_out, uint32_t *__restrict__ vals_out, int64_t n,
-                    int shift, const uint32_t *__restrict__ pass_hist, uint32_t *lookback,
-                    uint32_t *lookback_next, uint32_t *ticket, int64_t tiles,
-                    uint32_t *flags, uint32_t *next_hist, SegArgs seg, int64_t hold_tile,
-                    int64_t prefetch_ahead) {
-    using Smem = SortSmem<kItems, K>;
+struct PassArgs {
+    const uint64_t *keys_in;
+    const uint32_t *vals_in;
+    uint64_t *keys_out;
+    uint32_t *vals_out;
+    int64_t n;
+    int db;  // digit byte
+    const uint32_t *pass_hist;
+    uint32_t *lookback, *lookback_next, *ticket;
+    int64_t tiles;
+    uint32_t *flags, *next_hist;
+    SegArgs seg;
+    int64_t hold_tile, prefetch_ahead;
+};
+
+// kIn / kOut: the layouts above; kHi: the digit byte lies in the key's high
+// half (always for packed input). kSeg: segments are sorted independently. A
+// tile then lies inside one segment; its keys start at off[seg] + (tile -
+// tile_first[seg]) * kTile, its digit counts come from and go to the
+// segment's rows of the histograms, and its look-back chain ends at the
+// segment's first tile.
+template <int kIn, int kOut, bool kHi, int kItems, int kMinBlocks, bool kSeg>
+__global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(const PassArgs a) {
+    constexpr bool kVals = kIn != kInPacked;  // a payload travels beside the key
+    using Smem = SortSmem<kItems, kVals>;
     constexpr int kTile = Smem::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t sel = 0x4440u | (uint32_t)(a.db & 3);
+    const int nb = a.db + 1;  // the next pass's digit byte
+    const uint32_t nsel = 0x4440u | (uint32_t)(nb & 3);
+    const int64_t tiles = a.tiles;
+    uint32_t *next_hist = a.next_hist;
+    const uint32_t *pass_hist = a.pass_hist;
 
     if (threadIdx.x == 0) {
-        const uint32_t t = atomicAdd(ticket, 1u);
-        if (t == tiles - 1) *ticket = 0;  // last ticket handed out: reset for the next pass
+        const uint32_t t = atomicAdd(a.ticket, 1u);
+        if (t == tiles - 1) *a.ticket = 0;  // last ticket handed out: reset for the next pass
         sm.tile = t;
-        if (kSeg) sm.seg = instance_of(seg.tile_first, seg.count, t);
+        if (kSeg) sm.seg = instance_of(a.seg.tile_first, a.seg.count, t);
     }
     for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) (&sm.warp_hist[0][0])[k] = 0;
     sm.next_hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t tile = sm.tile;
-    int64_t first_tile = 0, seg_begin = 0, seg_end = n, tile_base = tile * kTile;
+    int64_t first_tile = 0, seg_begin = 0, seg_end = a.n, tile_base = tile * kTile;
     if (kSeg) {
         const int sg = sm.seg;
-        first_tile = seg.tile_first[sg];
-        seg_begin = seg.off[sg];
-        seg_end = seg.off[sg + 1];
+        first_tile = a.seg.tile_first[sg];
+        seg_begin = a.seg.off[sg];
+        seg_end = a.seg.off[sg + 1];
         tile_base = seg_begin + (tile - first_tile) * kTile;
         pass_hist += (int64_t)sg * kRadix;
         if (next_hist) next_hist += (int64_t)sg * kRadix;
     }
-    const int64_t valid = min((int64_t)kTile, seg_end - tile_base);
+    const int valid = (int)min((int64_t)kTile, seg_end - tile_base);
     // warm L2 with the tile a CTA will take about one wave from now (its
     // keys and payloads are contiguous: one bulk prefetch each)
-    if (!kSeg && threadIdx.x == 0 && prefetch_ahead > 0) {
-        const int64_t ft = tile + prefetch_ahead;
+    if (!kSeg && threadIdx.x == 0 && a.prefetch_ahead > 0) {
+        const int64_t ft = tile + a.prefetch_ahead;
         if (ft < tiles) {
             const int64_t fb = ft * kTile;
-            const int64_t fcnt = min((int64_t)kTile, n - fb);
-            const uint32_t kbytes = (uint32_t)((fcnt * (int64_t)sizeof(K)) & ~15ll);  // rounded down: stays inside
-            if (kbytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(keys_in + fb), "r"(kbytes) : "memory");
-            if (!kIota) {
-                const uint32_t vbytes = (uint32_t)((fcnt * 4) & ~15ll);
-                if (vbytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(vals_in + fb), "r"(vbytes)
+            const int64_t fcnt = min((int64_t)kTile, a.n - fb);
+            const uint32_t kbytes = (uint32_t)((fcnt * 8) & ~15ll);  // rounded down: stays inside
+            if (kbytes)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.keys_in + fb), "r"(kbytes)
                              : "memory");
+            if (kIn == kInKV) {
+                const uint32_t vbytes = (uint32_t)((fcnt * 4) & ~15ll);
+                if (vbytes)
+                    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.vals_in + fb), "r"(vbytes)
+                                 : "memory");
             }
         }
     }
 
     // ---- load: warp w owns keys [w*32*kItems, (w+1)*32*kItems) of the tile,
     // round j lane l holds key w*32*kItems + 32*j + l
-    K key[kItems];
-    uint32_t val[kItems];
+    uint64_t key[kItems];
+    uint32_t val[kVals ? kItems : 1];
     uint32_t rank[kItems];
+    {
+        const int wbase = warp * (kItems * 32) + lane;
+        const uint64_t *kp = a.keys_in + tile_base + wbase;
+        const uint32_t *vp = a.vals_in + tile_base + wbase;
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const int local = warp * (kItems * 32) + j * 32 + lane;
-        const int64_t g = tile_base + local;
-        if (local < valid) {
-            key[j] = keys_in[g];
-            val[j] = kIota ? (uint32_t)g : vals_in[g];
-        } else {
-            key[j] = ~K(0);  // ranks after every real key of digit 0xff
-            val[j] = 0;
+        for (int j = 0; j < kItems; ++j) {
+            const int local = wbase + j * 32;
+            if (local < valid) {
+                key[j] = kp[j * 32];
+                if (kIn == kInKV) val[j] = vp[j * 32];
+                if (kIn == kInIota) val[j] = (uint32_t)(tile_base + local);
+            } else {
+                key[j] = ~0ull;  // ranks after every real key of digit 0xff
+                if (kVals) val[j] = 0;
+            }
         }
     }
 
     // ---- digit counts for the next pass (its global histogram)
     if (next_hist) {
+        const bool nhi = nb >= 4;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
             const int local = warp * (kItems * 32) + j * 32 + lane;
-            if (local < valid)
-                atomicAdd(&sm.next_hist[(uint32_t)(key[j] >> (shift + kRadixBits)) & (kRadix - 1)], 1u);
+            if (local < valid) {
+                const uint32_t w = nhi ? (uint32_t)(key[j] >> 32) : (uint32_t)key[j];
+                atomicAdd(&sm.next_hist[__byte_perm(w, 0u, nsel)], 1u);
+            }
         }
     }
 
@@ -199,8 +246,8 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
     const uint32_t below = lanemask_lt();
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const uint32_t d = (uint32_t)(key[j] >> shift) & (kRadix - 1);
-        const uint32_t peers = digit_peers<kBallot>(d);
+        const uint32_t d = digit_of<kHi>(key[j], sel);
+        const uint32_t peers = digit_peers(d);
         const uint32_t before = __popc(peers & below);
         const uint32_t base = sm.warp_hist[warp][d];
         __syncwarp();
@@ -219,8 +266,8 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
         sm.warp_hist[w][d] = count;
         count += c;
     }
-    uint32_t *my_word = lookback + tile * kRadix + d;
-    const bool publish = tile != hold_tile;  // a test hook: this tile's successors must time out
+    uint32_t *my_word = a.lookback + tile * kRadix + d;
+    const bool publish = tile != a.hold_tile;  // a test hook: this tile's successors must time out
     if (publish) st_relaxed(my_word, (tile == first_tile ? kStatePrefix : kStateAgg) | count);
 
     const uint32_t global_base = (uint32_t)seg_begin + block_exclusive_scan(pass_hist[d], sm.scan);
@@ -232,7 +279,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
     if (tile > first_tile) {
         int64_t t = tile - 1;
         while (true) {
-            const uint32_t *w = lookback + t * kRadix + d;
+            const uint32_t *w = a.lookback + t * kRadix + d;
             uint32_t v = ld_relaxed(w);
             if ((v & kStateMask) == 0) {
                 const uint64_t t0 = global_ns();
@@ -240,7 +287,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
                 while ((v & kStateMask) == 0) {
                     ++spins;
                     if (spins > kSpinLimit || ((spins & 1023u) == 0 && global_ns() - t0 > kWaitNs)) {
-                        atomicOr(flags, kFlagTimeout);
+                        atomicOr(a.flags, kFlagTimeout);
                         v = kStatePrefix;  // give up: results are flagged invalid
                         break;
                     }
@@ -253,7 +300,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
         }
         if (publish) st_relaxed(my_word, kStatePrefix | (exclusive + count));
     }
-    lookback_next[tile * kRadix + d] = 0;  // the next pass's region
+    a.lookback_next[tile * kRadix + d] = 0;  // the next pass's region
     sm.out_base[d] = (int32_t)(global_base + exclusive) - (int32_t)start;
     __syncthreads();
 
@@ -265,76 +312,103 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks)
     // ---- stage in digit order
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const uint32_t dj = (uint32_t)(key[j] >> shift) & (kRadix - 1);
+        const uint32_t dj = digit_of<kHi>(key[j], sel);
         const uint32_t slot = sm.tile_start[dj] + sm.warp_hist[warp][dj] + rank[j];
         sm.keys[slot] = key[j];
-        sm.vals[slot] = val[j];
+        if (kVals) sm.vals[slot] = val[j];
     }
     __syncthreads();
 
     // ---- write out: slot s goes to out_base[digit] + s
+    const uint32_t lo = (uint32_t)seg_begin, span = (uint32_t)(seg_end - seg_begin);
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const int s = j * kSortThreads + threadIdx.x;
         if (s < valid) {
-            const K k = sm.keys[s];
-            const uint32_t dj = (uint32_t)(k >> shift) & (kRadix - 1);
-            const int64_t pos = (int64_t)sm.out_base[dj] + s;
-            if (pos < seg_begin || pos >= seg_end) {  // only after a timed-out look-back
-                atomicOr(flags, kFlagCorrupt);
+            const uint64_t k = sm.keys[s];
+            const int32_t pos = sm.out_base[digit_of<kHi>(k, sel)] + s;
+            if ((uint32_t)pos - lo >= span) {  // only after a timed-out look-back
+                atomicOr(a.flags, kFlagCorrupt);
                 continue;
             }
-            keys_out[pos] = k;
-            vals_out[pos] = sm.vals[s];
+            if (kOut == kOutKV) {
+                a.keys_out[pos] = k;
+                a.vals_out[pos] = sm.vals[s];
+            } else if (kOut == kOutPack) {
+                a.keys_out[pos] = (k & 0xffffffff00000000ull) | sm.vals[s];
+            } else if (kOut == kOutPacked) {
+                a.keys_out[pos] = k;
+            } else if (kIn == kInPacked) {
+                a.vals_out[pos] = (uint32_t)k;
+            } else {
+                a.vals_out[pos] = sm.vals[s];
+            }
         }
     }
 }
 
-template <typename K>
-using PassKernelT = void (*)(const K *, const uint32_t *, K *, uint32_t *, int64_t, int, const uint32_t *,
-                             uint32_t *, uint32_t *, uint32_t *, int64_t, uint32_t *, uint32_t *, SegArgs,
-                             int64_t, int64_t);
-using PassKernel = PassKernelT<uint64_t>;
+using PassKernel = void (*)(PassArgs);
 
-template <typename K = uint64_t>
-struct VariantT {
-    int items, min_blocks;
-    bool ballot;
-    PassKernelT<K> first, rest;          // payload = index / payload read
-    PassKernelT<K> seg_first, seg_rest;  // the same, segmented
-    size_t smem;
+// The (input, output, digit half) combinations the library runs.
+enum PassKind : int {
+    kIotaKV,        // pass 0 of a pair sort: payload = index
+    kKVKVLo,        // key + payload in and out, digit in the low half
+    kKVKVHi,        // the same, digit in the high half
+    kKVPack,        // byte 3: key + payload in, packed words out
+    kPackedPacked,  // packed in and out
+    kPackedLow,     // packed in, payloads out (the last pass)
+    kPassKinds
 };
-using Variant = VariantT<uint64_t>;
 
-template <int kItems, int kMinBlocks, bool kBallot, typename K = uint64_t>
-VariantT<K> make_variant() {
-    return VariantT<K>{kItems,
-                       kMinBlocks,
-                       kBallot,
-                       onesweep_kernel<true, kItems, kMinBlocks, kBallot, false, K>,
-                       onesweep_kernel<false, kItems, kMinBlocks, kBallot, false, K>,
-                       onesweep_kernel<true, kItems, kMinBlocks, kBallot, true, K>,
-                       onesweep_kernel<false, kItems, kMinBlocks, kBallot, true, K>,
-                       sizeof(SortSmem<kItems, K>)};
+struct Variant {
+    int items, min_blocks;
+    PassKernel k[2][kPassKinds];  // [segmented][kind]
+    size_t smem_kv, smem_packed;
+};
+
+template <int kItems, int kMinBlocks, bool kSeg>
+void fill_kinds(PassKernel (&k)[kPassKinds]) {
+    k[kIotaKV] = onesweep_kernel<kInIota, kOutKV, false, kItems, kMinBlocks, kSeg>;
+    k[kKVKVLo] = onesweep_kernel<kInKV, kOutKV, false, kItems, kMinBlocks, kSeg>;
+    k[kKVKVHi] = onesweep_kernel<kInKV, kOutKV, true, kItems, kMinBlocks, kSeg>;
+    k[kKVPack] = onesweep_kernel<kInKV, kOutPack, false, kItems, kMinBlocks, kSeg>;
+    k[kPackedPacked] = onesweep_kernel<kInPacked, kOutPacked, true, kItems, kMinBlocks, kSeg>;
+    k[kPackedLow] = onesweep_kernel<kInPacked, kOutLow, true, kItems, kMinBlocks, kSeg>;
 }
 
-// Tile shapes the library is compiled with. The first entry is the default;
-// LBVH_SORT_VARIANT=<index> selects another process-wide (tuning sweeps), and
-// run_onesweep can be given one explicitly (the batch autotuner).
+template <int kItems, int kMinBlocks>
+Variant make_variant() {
+    Variant v{};
+    v.items = kItems;
+    v.min_blocks = kMinBlocks;
+    fill_kinds<kItems, kMinBlocks, false>(v.k[0]);
+    fill_kinds<kItems, kMinBlocks, true>(v.k[1]);
+    v.smem_kv = sizeof(SortSmem<kItems, true>);
+    v.smem_packed = sizeof(SortSmem<kItems, false>);
+    return v;
+}
+
+size_t pass_smem(const Variant &v, int kind) {
+    return (kind == kPackedPacked || kind == kPackedLow) ? v.smem_packed : v.smem_kv;
+}
+
+// Tile shapes the library is compiled with (keys per thread, CTAs per SM).
+// The first entry is the default; the autotuner may pick another.
 const Variant *variant_table(int *count) {
     static const Variant table[] = {
-        make_variant<12, 4, true>(), make_variant<16, 3, true>(),  make_variant<8, 4, true>(),
-        make_variant<16, 2, true>(), make_variant<12, 3, true>(),  make_variant<8, 6, true>(),
-        make_variant<16, 2, false>(),
+        make_variant<12, 4>(),
+        make_variant<16, 3>(),
+        make_variant<8, 6>(),
     };
     // kernel attributes set once, thread-safely (function-local static initialisation)
     static const bool configured = [] {
-        for (const Variant &v : table) {
-            for (PassKernel k : {v.first, v.rest, v.seg_first, v.seg_rest}) {
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
-                cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-            }
-        }
+        for (const Variant &v : table)
+            for (int sg = 0; sg < 2; ++sg)
+                for (int kind = 0; kind < kPassKinds; ++kind) {
+                    cudaFuncSetAttribute(v.k[sg][kind], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)pass_smem(v, kind));
+                    cudaFuncSetAttribute(v.k[sg][kind], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+                }
         return true;
     }();
     (void)configured;
@@ -342,30 +416,10 @@ const Variant *variant_table(int *count) {
     return table;
 }
 
-// 32-bit keys (query orders of up to 30 bits): the default tile shape only;
-// its tiles hold as many keys as variant 0's, so segment tables made for
-// variant 0 serve it.
-const VariantT<uint32_t> &variant32() {
-    static const VariantT<uint32_t> v = [] {
-        const VariantT<uint32_t> w = make_variant<12, 4, true, uint32_t>();
-        for (PassKernelT<uint32_t> k : {w.first, w.rest, w.seg_first, w.seg_rest}) {
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)w.smem);
-            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        }
-        return w;
-    }();
-    return v;
-}
-
 const Variant &variant(int idx = -1) {
     int count = 0;
     const Variant *table = variant_table(&count);
-    static const int pick = [&] {
-        const char *env = getenv("LBVH_SORT_VARIANT");
-        const int want = env ? atoi(env) : 0;
-        return (want >= 0 && want < count) ? want : 0;
-    }();
-    return table[(idx >= 0 && idx < count) ? idx : pick];
+    return table[(idx >= 0 && idx < count) ? idx : 0];
 }
 
 __global__ void __launch_bounds__(256)
@@ -421,68 +475,101 @@ int64_t sort_tile_keys_min() {
 
 // Tiles between a tile and the one its CTA prefetches into L2: two per SM
 // (a sweep of 76..1216 at 2^25 keys: 0.313 ms per pass from 152 to 456,
-// 0.327 ms without prefetch). LBVH_SORT_PREFETCH=0 turns it off, any other
-// value sets the distance (tuning sweeps).
-static int64_t prefetch_tiles() {
-    static const int64_t env = [] {
-        const char *e = getenv("LBVH_SORT_PREFETCH");
-        return e ? (int64_t)atoll(e) : -1;
-    }();
-    if (env >= 0) return env;
-    return (int64_t)device_sm_count() * 2;
-}
+// 0.327 ms without prefetch).
+static int64_t prefetch_tiles() { return (int64_t)device_sm_count() * 2; }
 
-template <typename K>
-static bool run_passes(const VariantT<K> &v, K *keys_a, uint32_t *vals_a, bool iota, K *keys_b, uint32_t *vals_b,
-                       int64_t n, int passes, const SortScratch &scratch, Control *ctl, cudaStream_t s,
-                       cudaEvent_t (*pass_events)[2], const SortSegments *seg) {
-    if (n <= 0 || passes <= 0) return false;
-    const int64_t tiles = seg ? seg->tiles
-                              : (n + (int64_t)kSortThreads * v.items - 1) / ((int64_t)kSortThreads * v.items);
-    if (tiles <= 0) return false;
+namespace {
+
+// One pass: kind, digit byte, buffers.
+struct Pass {
+    int kind, db;
+    const uint64_t *kin;
+    const uint32_t *vin;
+    uint64_t *kout;
+    uint32_t *vout;
+};
+
+void run_pass_list(const Variant &v, const Pass *ps, int passes, int64_t n, const SortScratch &scratch,
+                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], const SortSegments *seg) {
+    const int64_t tiles = seg ? seg->tiles : (n + (int64_t)kSortThreads * v.items - 1) / ((int64_t)kSortThreads * v.items);
+    if (tiles <= 0) return;
     const SegArgs sa{seg ? seg->off : nullptr, seg ? seg->tile_first : nullptr, seg ? seg->count : 0};
     const int64_t hist_stride = (int64_t)kRadix * (seg ? seg->count : 1);
     cudaMemsetAsync(scratch.lookback, 0, (size_t)tiles * kRadix * sizeof(uint32_t), s);
-    K *kin = keys_a, *kout = keys_b;
-    uint32_t *vin = vals_a, *vout = vals_b;
     for (int p = 0; p < passes; ++p) {
-        uint32_t *cur = scratch.lookback + (p & 1) * scratch.lookback_words;
-        uint32_t *nxt = scratch.lookback + ((p + 1) & 1) * scratch.lookback_words;
-        const uint32_t *hist = scratch.hist + p * hist_stride;
+        const Pass &q = ps[p];
+        PassArgs a{};
+        a.keys_in = q.kin;
+        a.vals_in = q.vin;
+        a.keys_out = q.kout;
+        a.vals_out = q.vout;
+        a.n = n;
+        a.db = q.db;
+        a.pass_hist = scratch.hist + p * hist_stride;
+        a.lookback = scratch.lookback + (p & 1) * scratch.lookback_words;
+        a.lookback_next = scratch.lookback + ((p + 1) & 1) * scratch.lookback_words;
+        a.ticket = &ctl->sort_ticket[p];
+        a.tiles = tiles;
+        a.flags = &ctl->build_flags;
+        a.next_hist = p + 1 < passes ? scratch.hist + (p + 1) * hist_stride : nullptr;
+        a.seg = sa;
+        a.hold_tile = p == 0 ? g_hold_tile.load(std::memory_order_relaxed) : -1;
+        a.prefetch_ahead = prefetch_tiles();
         if (pass_events) cudaEventRecord(pass_events[p][0], s);
-        PassKernelT<K> k =
-            seg ? ((p == 0 && iota) ? v.seg_first : v.seg_rest) : ((p == 0 && iota) ? v.first : v.rest);
-        uint32_t *next_hist = p + 1 < passes ? scratch.hist + (p + 1) * hist_stride : nullptr;
-        const int64_t hold = p == 0 ? g_hold_tile.load(std::memory_order_relaxed) : -1;
-        k<<<(unsigned)tiles, kSortThreads, v.smem, s>>>(kin, vin, kout, vout, n, kRadixBits * p, hist, cur,
-                                                         nxt, &ctl->sort_ticket[p], tiles, &ctl->build_flags,
-                                                         next_hist, sa, hold, prefetch_tiles());
+        v.k[seg ? 1 : 0][q.kind]<<<(unsigned)tiles, kSortThreads, pass_smem(v, q.kind), s>>>(a);
         if (pass_events) cudaEventRecord(pass_events[p][1], s);
         count_launches(1);
-        K *tk = kin;
-        kin = kout;
-        kout = tk;
-        uint32_t *tv = vin;
-        vin = vout;
-        vout = tv;
     }
-    return (passes & 1) != 0;
 }
+
+}  // namespace
 
 bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_b,
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx,
                   const SortSegments *seg) {
-    return run_passes(variant(variant_idx), keys_a, vals_a, iota, keys_b, vals_b, n, passes, scratch, ctl, s,
-                      pass_events, seg);
+    if (n <= 0 || passes <= 0) return false;
+    Pass ps[kMaxPasses];
+    uint64_t *kb[2] = {keys_a, keys_b};
+    uint32_t *vb[2] = {vals_a, vals_b};
+    for (int p = 0; p < passes; ++p) {
+        const int in = p & 1, out = in ^ 1;
+        ps[p] = Pass{(p == 0 && iota) ? kIotaKV : (p >= 4 ? kKVKVHi : kKVKVLo), p, kb[in], vb[in], kb[out], vb[out]};
+    }
+    run_pass_list(variant(variant_idx), ps, passes, n, scratch, ctl, s, pass_events, seg);
+    return (passes & 1) != 0;
 }
 
-bool run_onesweep32(uint32_t *keys_a, uint32_t *vals_a, bool iota, uint32_t *keys_b, uint32_t *vals_b,
-                    int64_t n, int passes, const SortScratch &scratch, Control *ctl, cudaStream_t s,
-                    const SortSegments *seg) {
-    if (passes > 4) passes = 4;  // four 8-bit digits cover a 32-bit key
-    return run_passes(variant32(), keys_a, vals_a, iota, keys_b, vals_b, n, passes, scratch, ctl, s, nullptr,
-                      seg);
+uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, int64_t n,
+                         int key_bits, bool packed, const SortScratch &scratch, Control *ctl, cudaStream_t s,
+                         cudaEvent_t (*pass_events)[2], int variant_idx) {
+    if (n <= 0) return vals_a;
+    const int passes = sort_passes(key_bits);
+    Pass ps[kMaxPasses];
+    uint64_t *kb[2] = {keys_a, keys_b};
+    uint32_t *vb[2] = {vals_a, vals_b};
+    uint32_t *perm = vals_a;
+    if (packed) {
+        // bytes 4 .. 4 + passes - 1 of words code << 32 | index
+        for (int p = 0; p < passes; ++p) {
+            const int in = p & 1, out = in ^ 1;
+            const bool last = p == passes - 1;
+            ps[p] = Pass{last ? kPackedLow : kPackedPacked, 4 + p, kb[in], nullptr, kb[out], last ? vb[0] : nullptr};
+        }
+        perm = vb[0];
+    } else {
+        // bytes 0-3 with key + payload (byte 3's pass packs), then packed;
+        // more than 32 key bits means at least five passes
+        for (int p = 0; p < passes; ++p) {
+            const int in = p & 1, out = in ^ 1;
+            const bool last = p == passes - 1;
+            int kind = p == 0 ? kIotaKV : (p < 3 ? kKVKVLo : (p == 3 ? kKVPack : (last ? kPackedLow : kPackedPacked)));
+            ps[p] = Pass{kind, p, kb[in], p <= 3 ? vb[in] : nullptr, kb[out], (p < 3 || last) ? vb[out] : nullptr};
+            if (last) perm = vb[out];
+        }
+    }
+    run_pass_list(variant(variant_idx), ps, passes, n, scratch, ctl, s, pass_events, nullptr);
+    return perm;
 }
 
 }  // namespace lbvh

@@ -160,7 +160,25 @@ def test_sort_pairs_stable(n, key_bits, distinct):
 # ---------------------------------------------------------------- builds
 
 
+def signed_zero_points(n, seed):
+    """Coordinates drawn from {-0.0, +0.0, 0.25, 1.0}: box unions must order
+    -0.0 below +0.0 whichever child comes first."""
+    rng = np.random.default_rng(seed)
+    v = np.array([-0.0, 0.0, 0.25, 1.0], np.float32)
+    return v[rng.integers(0, 4, size=(n, 3))]
+
+
+def signed_zero_boxes(n, seed):
+    rng = np.random.default_rng(seed)
+    lo = np.array([-0.0, 0.0, 0.25], np.float32)[rng.integers(0, 3, size=(n, 3))]
+    zero_hi = np.array([-0.0, 0.0], np.float32)[rng.integers(0, 2, size=(n, 3))]
+    hi = np.where(lo == 0.0, zero_hi, lo + np.float32(0.5)).astype(np.float32)
+    return np.concatenate([lo, hi], axis=1)
+
+
 BUILD_CASES = {
+    "signed_zero_points": lambda: (signed_zero_points(20000, seed=11), 0, 63),
+    "signed_zero_boxes": lambda: (signed_zero_boxes(20000, seed=12), 1, 30),
     "d1_uniform_16384_30bit": lambda: (inputs.uniform_points(16384, seed=0), 0, 30),
     "uniform_ragged_63bit": lambda: (inputs.uniform_points(70001, seed=5), 0, 63),
     "boxes_mixture_30bit": lambda: (inputs.gaussian_mixture_boxes(60000, seed=6), 1, 30),
