@@ -98,10 +98,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return before + x - v;
 }
 
-template <int kItems, bool kVals>
+template <int kItems, bool kVals, bool kTable>
 struct SortSmem {
     static constexpr int kTile = kSortThreads * kItems;
     uint32_t warp_hist[kWarps][kRadix];  // per-warp digit counts, then per-warp offsets
+    uint32_t peer_mask[kTable ? kWarps : 1][kRadix];  // table ranking: lanes of the round holding each digit (zero between rounds)
     int32_t out_base[kRadix];            // global position of the digit's first staged key, minus its tile start
     uint32_t tile_start[kRadix];         // first staged slot of each digit
     uint32_t scan[kWarps];
@@ -145,15 +146,18 @@ struct PassArgs {
 };
 
 // kIn / kOut: the layouts above; kHi: the digit byte lies in the key's high
-// half (always for packed input). kSeg: segments are sorted independently. A
+// half (always for packed input). kTable: the lanes of a round that share a
+// digit are found through a per-warp table in shared memory (each lane ORs
+// its bit into its digit's word and reads the word back) instead of eight
+// ballots. kSeg: segments are sorted independently. A
 // tile then lies inside one segment; its keys start at off[seg] + (tile -
 // tile_first[seg]) * kTile, its digit counts come from and go to the
 // segment's rows of the histograms, and its look-back chain ends at the
 // segment's first tile.
-template <int kIn, int kOut, bool kHi, int kItems, int kMinBlocks, bool kSeg>
+template <int kIn, int kOut, bool kHi, int kItems, int kMinBlocks, bool kTable, bool kSeg>
 __global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(const PassArgs a) {
     constexpr bool kVals = kIn != kInPacked;  // a payload travels beside the key
-    using Smem = SortSmem<kItems, kVals>;
+    using Smem = SortSmem<kItems, kVals, kTable>;
     constexpr int kTile = Smem::kTile;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
@@ -171,7 +175,10 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(cons
         sm.tile = t;
         if (kSeg) sm.seg = instance_of(a.seg.tile_first, a.seg.count, t);
     }
-    for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) (&sm.warp_hist[0][0])[k] = 0;
+    for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) {
+        (&sm.warp_hist[0][0])[k] = 0;
+        if (kTable) (&sm.peer_mask[0][0])[k] = 0;
+    }
     sm.next_hist[threadIdx.x] = 0;
     __syncthreads();
     const int64_t tile = sm.tile;
@@ -247,11 +254,21 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(cons
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const uint32_t d = digit_of<kHi>(key[j], sel);
-        const uint32_t peers = digit_peers(d);
+        uint32_t peers;
+        if (kTable) {
+            atomicOr(&sm.peer_mask[warp][d], 1u << lane);
+            __syncwarp();
+            peers = sm.peer_mask[warp][d];
+        } else {
+            peers = digit_peers(d);
+        }
         const uint32_t before = __popc(peers & below);
         const uint32_t base = sm.warp_hist[warp][d];
         __syncwarp();
-        if (before == 0) sm.warp_hist[warp][d] = base + __popc(peers);
+        if (before == 0) {
+            sm.warp_hist[warp][d] = base + __popc(peers);
+            if (kTable) sm.peer_mask[warp][d] = 0;
+        }
         __syncwarp();
         rank[j] = base + before;
     }
@@ -362,29 +379,31 @@ enum PassKind : int {
 
 struct Variant {
     int items, min_blocks;
+    bool table;
     PassKernel k[2][kPassKinds];  // [segmented][kind]
     size_t smem_kv, smem_packed;
 };
 
-template <int kItems, int kMinBlocks, bool kSeg>
+template <int kItems, int kMinBlocks, bool kTable, bool kSeg>
 void fill_kinds(PassKernel (&k)[kPassKinds]) {
-    k[kIotaKV] = onesweep_kernel<kInIota, kOutKV, false, kItems, kMinBlocks, kSeg>;
-    k[kKVKVLo] = onesweep_kernel<kInKV, kOutKV, false, kItems, kMinBlocks, kSeg>;
-    k[kKVKVHi] = onesweep_kernel<kInKV, kOutKV, true, kItems, kMinBlocks, kSeg>;
-    k[kKVPack] = onesweep_kernel<kInKV, kOutPack, false, kItems, kMinBlocks, kSeg>;
-    k[kPackedPacked] = onesweep_kernel<kInPacked, kOutPacked, true, kItems, kMinBlocks, kSeg>;
-    k[kPackedLow] = onesweep_kernel<kInPacked, kOutLow, true, kItems, kMinBlocks, kSeg>;
+    k[kIotaKV] = onesweep_kernel<kInIota, kOutKV, false, kItems, kMinBlocks, kTable, kSeg>;
+    k[kKVKVLo] = onesweep_kernel<kInKV, kOutKV, false, kItems, kMinBlocks, kTable, kSeg>;
+    k[kKVKVHi] = onesweep_kernel<kInKV, kOutKV, true, kItems, kMinBlocks, kTable, kSeg>;
+    k[kKVPack] = onesweep_kernel<kInKV, kOutPack, false, kItems, kMinBlocks, kTable, kSeg>;
+    k[kPackedPacked] = onesweep_kernel<kInPacked, kOutPacked, true, kItems, kMinBlocks, kTable, kSeg>;
+    k[kPackedLow] = onesweep_kernel<kInPacked, kOutLow, true, kItems, kMinBlocks, kTable, kSeg>;
 }
 
-template <int kItems, int kMinBlocks>
+template <int kItems, int kMinBlocks, bool kTable>
 Variant make_variant() {
     Variant v{};
     v.items = kItems;
     v.min_blocks = kMinBlocks;
-    fill_kinds<kItems, kMinBlocks, false>(v.k[0]);
-    fill_kinds<kItems, kMinBlocks, true>(v.k[1]);
-    v.smem_kv = sizeof(SortSmem<kItems, true>);
-    v.smem_packed = sizeof(SortSmem<kItems, false>);
+    v.table = kTable;
+    fill_kinds<kItems, kMinBlocks, kTable, false>(v.k[0]);
+    fill_kinds<kItems, kMinBlocks, kTable, true>(v.k[1]);
+    v.smem_kv = sizeof(SortSmem<kItems, true, kTable>);
+    v.smem_packed = sizeof(SortSmem<kItems, false, kTable>);
     return v;
 }
 
@@ -396,9 +415,10 @@ size_t pass_smem(const Variant &v, int kind) {
 // The first entry is the default; the autotuner may pick another.
 const Variant *variant_table(int *count) {
     static const Variant table[] = {
-        make_variant<12, 4>(),
-        make_variant<16, 3>(),
-        make_variant<8, 6>(),
+        make_variant<12, 4, false>(),
+        make_variant<12, 4, true>(),
+        make_variant<16, 3, false>(),
+        make_variant<8, 6, false>(),
     };
     // kernel attributes set once, thread-safely (function-local static initialisation)
     static const bool configured = [] {
