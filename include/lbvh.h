@@ -496,6 +496,48 @@ const char *lbvh_stage_name(int stage);
 /* Number of CUDA kernels this library has launched in this process. */
 uint64_t lbvh_kernel_launches(void);
 
+/* ---------------------------------------------------------------- autotuner */
+
+/* The library's own tuning parameters, none of which changes any result (the
+ * paper has no counterpart; they choose how the kernels run):
+ *   sort variant  the radix sort's tile shape (keys per thread, CTAs per SM)
+ *                 and how a warp finds the lanes sharing a digit (eight
+ *                 ballots, or a per-warp table in shared memory), an index
+ *                 in [0, lbvh_sort_variant_count());
+ *   walk variant  how Algorithm 1's collecting walk runs: 0 one thread per
+ *                 query, 1/2/3 groups of 8/16/32 lanes walking the union of
+ *                 their queries' paths together (lbvh_walk_variant_count()).
+ * A process-wide cache holds the choice for each configuration (the GPU's
+ * name, ceil(log2 n), Morton bits, primitive kind, query kind, trees built
+ * together); builds and queries use the cached choice for their
+ * configuration, else variant 0. */
+int lbvh_sort_variant_count(void);
+int lbvh_walk_variant_count(void);
+
+/* Times every sort variant on this build (two builds each, device time of
+ * the sort passes) and, when nq > 0, every walk variant on these queries
+ * (two runs each, device time of the collecting walk), stores the fastest of
+ * each in the cache and leaves the tree built with the chosen sort variant.
+ * Arguments as lbvh_build and lbvh_query_into; sort_variant / walk_variant
+ * (nullable) receive the choices. Synchronises `stream`. */
+lbvh_status lbvh_tree_autotune(lbvh_tree_t tree, const float *d_prims, int64_t n, int kind, int morton_bits,
+                               const float *d_queries, int64_t nq, int query_kind, const float *d_radii,
+                               float radius, lbvh_stream_t stream, int *sort_variant, int *walk_variant);
+
+/* Fix this tree's variants (-1: use the cache; LBVH_ERR_INVALID if out of
+ * range). Every variant gives the same, exact results. */
+lbvh_status lbvh_tree_set_tuning(lbvh_tree_t tree, int sort_variant, int walk_variant);
+
+/* The cache as a small JSON file: save writes every entry (atomically, via a
+ * temporary file beside `path`); load merges a saved file's entries into the
+ * cache, dropping variant indices this library does not have
+ * (LBVH_ERR_INVALID if the file cannot be read or parsed; the cache is then
+ * unchanged). clear empties the cache; entries counts it. */
+lbvh_status lbvh_tune_save(const char *path);
+lbvh_status lbvh_tune_load(const char *path);
+void lbvh_tune_clear(void);
+int lbvh_tune_entries(void);
+
 /* ---------------------------------------------------------------- misc */
 
 /* Human-readable name of a status. */

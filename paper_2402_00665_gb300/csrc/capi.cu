@@ -173,6 +173,7 @@ struct lbvh_tree_s {
     int bits = 0;
     bool has_build = false;
     int codes_in = 0, perm_in = 0;  // which keys[] / vals[] buffer holds the sorted codes / permutation
+    int sort_choice = -1, walk_choice = -1;  // lbvh_tree_set_tuning (-1: the tuner's cache, else the default)
     bool store_dirty = false;  // a failed build may have left store words set
     DevBuf keys[2], vals[2];
     DevBuf nodes, store, lookback, hist, partials, bounds, ctl;
@@ -388,6 +389,7 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     t->prof.end(LBVH_STAGE_QORDER, s);
     if (ost != LBVH_OK) return ost;
     const QueryScratch qs = query_scratch(t);
+    qa.walk = t->walk_choice >= 0 ? t->walk_choice : tune_walk_choice(t->n, t->bits, t->kind, qa.qkind, 1);
     t->prof.begin(LBVH_STAGE_QCOUNT, s);
     launch_query_collect(t->view(), qa, qs, c, s);
     t->prof.end(LBVH_STAGE_QCOUNT, s);
@@ -454,15 +456,12 @@ struct BatchSignature {
     }
 };
 
-// Process-wide autotuning results: sort tile shape per (keys, passes) bucket.
-std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tuned_variant;
-
-int ceil_log2(int64_t x) {
-    int b = 0;
-    while (((int64_t)1 << b) < x) ++b;
-    return b;
+// The tuner's configuration of a batch: its primitives' size bucket, bits and
+// kind, and its instance count rounded up to a power of two.
+lbvh::TuneKey batch_tune_key(int64_t N, int bits, int kind, int64_t count) {
+    return lbvh::tune_key(N, bits, kind, -1, int64_t(1) << lbvh::ceil_log2(count < 1 ? 1 : count));
 }
+
 
 }  // namespace
 
@@ -674,16 +673,15 @@ lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {
 }
 
 // Sort tile shape for this batch: the fastest variant on the batch's own keys
-// (timed with events on `s`), remembered per (keys bucket, passes).
+// (timed with events on `s`), kept in the tuner's cache for its configuration.
 lbvh_status batch_autotune(lbvh_batch_t b, cudaStream_t s) {
     using namespace lbvh;
     if (b->sort_variant >= 0 || b->N < (1 << 20)) return LBVH_OK;
-    const std::pair<int, int> key{ceil_log2(b->N), b->passes};
+    const TuneKey key = batch_tune_key(b->N, b->sig.bits, b->sig.kind, b->count);
     {
-        std::lock_guard<std::mutex> lock(g_tune_mu);
-        auto it = g_tuned_variant.find(key);
-        if (it != g_tuned_variant.end()) {
-            b->sort_variant = it->second;
+        TuneChoice known;
+        if (tune_find(key, &known) && known.sort >= 0) {
+            b->sort_variant = known.sort;
             return LBVH_OK;
         }
     }
@@ -720,8 +718,10 @@ lbvh_status batch_autotune(lbvh_batch_t b, cudaStream_t s) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->sort_variant = pick;
-    std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tuned_variant[key] = pick;
+    TuneChoice made;
+    made.sort = pick;
+    made.sort_ms = best;
+    tune_put(key, made);
     return LBVH_OK;
 }
 
@@ -804,10 +804,11 @@ lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
         LBVH_LAUNCHED();
         SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles_max(n) * kRadix};
         nvtxRangePushA("sort");
+        const int variant = t->sort_choice >= 0 ? t->sort_choice : tune_sort_choice(n, morton_bits, kind, 1);
         const uint32_t *perm = run_index_sort(t->keys[0].as<uint64_t>(), t->keys[1].as<uint64_t>(),
                                               t->vals[0].as<uint32_t>(), t->vals[1].as<uint32_t>(), n, morton_bits,
                                               packed, scratch, c, s,
-                                              t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr);
+                                              t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr, variant);
         nvtxRangePop();
         if (t->prof.on)
             for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
@@ -1113,24 +1114,8 @@ bool page_locked(const void *h) {
 // 27.8 with 2, 29.2 with 8, 35.5 with 16, against 32.6 ms for the query and
 // the copies one after the other (each chunk adds a host round trip, and
 // its copy shares the link and L2 with the next chunk's walk).
-// LBVH_HOST_CHUNK=<queries> and LBVH_HOST_CHUNKS=<count> override both
-// (tuning sweeps).
-int64_t host_chunk_min() {
-    static const int64_t v = [] {
-        const char *e = getenv("LBVH_HOST_CHUNK");
-        const long long x = e ? atoll(e) : 0;
-        return x > 0 ? (int64_t)x : (int64_t(1) << 23);
-    }();
-    return v;
-}
-int64_t host_chunks_max() {
-    static const int64_t v = [] {
-        const char *e = getenv("LBVH_HOST_CHUNKS");
-        const long long x = e ? atoll(e) : 0;
-        return x > 0 ? (int64_t)x : 4;
-    }();
-    return v;
-}
+constexpr int64_t kHostChunkMin = int64_t(1) << 23;
+constexpr int64_t kHostChunksMax = 4;
 
 lbvh_status host_stream(lbvh_tree_t t) {
     if (t->xfer) return LBVH_OK;
@@ -1160,8 +1145,8 @@ lbvh_status lbvh_query_into_host(lbvh_tree_t t, const float *d_queries, int64_t 
     if ((st = host_stream(t)) != LBVH_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int dim = qkind == LBVH_Q_SPHERE ? 3 : (qkind == LBVH_Q_BOX ? 6 : 8);
-    const int64_t cmin = host_chunk_min();
-    const int64_t chunks = nq <= cmin ? 1 : std::min<int64_t>(host_chunks_max(), (nq + cmin - 1) / cmin);
+    const int64_t cmin = kHostChunkMin;
+    const int64_t chunks = nq <= cmin ? 1 : std::min<int64_t>(kHostChunksMax, (nq + cmin - 1) / cmin);
     const int64_t per = (nq + chunks - 1) / chunks;
     uint64_t base = 0;
     bool over = false;
@@ -1415,9 +1400,8 @@ lbvh_status lbvh_batch_build_query(lbvh_batch_t b, const float *d_prims, const i
         if (!same_tables) {
             b->ready = false;
             if ((st = batch_setup(b, s)) != LBVH_OK) return st;
-            std::lock_guard<std::mutex> lock(g_tune_mu);
-            auto it = g_tuned_variant.find({ceil_log2(b->N), b->passes});
-            b->sort_variant = it != g_tuned_variant.end() ? it->second : -1;
+            b->sort_variant = lbvh::tune_sort_choice(b->N, sig.bits, sig.kind,
+                                                     int64_t(1) << lbvh::ceil_log2(b->count < 1 ? 1 : b->count));
         } else {
             const bool same_points = qkind == LBVH_Q_SPHERE && kind == LBVH_PRIM_POINTS;
             const bool same_boxes = qkind == LBVH_Q_BOX && kind == LBVH_PRIM_BOXES;
@@ -1572,6 +1556,115 @@ void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s) {
 }  // namespace lbvh
 
 extern "C" {
+
+lbvh_status lbvh_tree_set_tuning(lbvh_tree_t t, int sort_variant, int walk_variant) {
+    if (!t || sort_variant < -1 || sort_variant >= lbvh::sort_variant_count() || walk_variant < -1 ||
+        walk_variant >= lbvh::kWalkKinds)
+        return LBVH_ERR_INVALID;
+    t->sort_choice = sort_variant;
+    t->walk_choice = walk_variant;
+    return LBVH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device milliseconds of stages [lo, hi) of the tree's last build or query
+// (the tree's profiling must be on); synchronises the recording streams.
+float stages_ms(lbvh_tree_t t, int lo, int hi) {
+    float sum = 0.0f;
+    for (int k = lo; k < hi; ++k) {
+        if (!t->prof.recorded[k]) continue;
+        if (cudaEventSynchronize(t->prof.ev[k][1]) != cudaSuccess) return -1.0f;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, t->prof.ev[k][0], t->prof.ev[k][1]) != cudaSuccess) return -1.0f;
+        sum += ms;
+    }
+    return sum;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbvh_status lbvh_tree_autotune(lbvh_tree_t t, const float *d_prims, int64_t n, int kind, int morton_bits,
+                               const float *d_queries, int64_t nq, int qkind, const float *d_radii, float radius,
+                               lbvh_stream_t stream, int *sort_variant, int *walk_variant) {
+    using namespace lbvh;
+    NvtxRange nvtx_range("lbvh_tree_autotune");
+    lbvh_status st = check_build_args(t, d_prims, n, kind);
+    if (st != LBVH_OK) return st;
+    if (!valid_bits(morton_bits) || nq < 0 || (nq > 0 && !d_queries)) return LBVH_ERR_INVALID;
+    if (nq > 0 && qkind != LBVH_Q_SPHERE && qkind != LBVH_Q_BOX && qkind != LBVH_Q_RAY) return LBVH_ERR_INVALID;
+    if (qkind == LBVH_Q_SPHERE && nq > 0 && !d_radii && !(std::isfinite(radius) && radius >= 0.0f))
+        return LBVH_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool prof_was = t->prof.on;
+    const int keep_sort = t->sort_choice, keep_walk = t->walk_choice;
+    LBVH_CUDA(t->prof.enable(true));
+    auto finish = [&](lbvh_status r) {
+        t->sort_choice = keep_sort;
+        t->walk_choice = keep_walk;
+        t->prof.on = prof_was;
+        return r;
+    };
+    // the sort: every variant on this build's own keys, the best of two runs each
+    float best_sort = 1e30f;
+    int pick_sort = 0;
+    for (int v = 0; v < sort_variant_count() && n > 0; ++v) {
+        t->sort_choice = v;
+        for (int rep = 0; rep < 2; ++rep) {
+            if ((st = lbvh_build(t, d_prims, n, kind, morton_bits, stream)) != LBVH_OK) return finish(st);
+            const float ms = stages_ms(t, LBVH_STAGE_SORT0, LBVH_STAGE_SORT0 + sort_passes(morton_bits));
+            if (ms < 0.0f) return finish(LBVH_ERR_CUDA);
+            if (ms < best_sort) {
+                best_sort = ms;
+                pick_sort = v;
+            }
+        }
+    }
+    if (n > 0) {
+        TuneChoice made;
+        made.sort = pick_sort;
+        made.sort_ms = best_sort;
+        tune_put(tune_key(n, morton_bits, kind, -1, 1), made);
+    }
+    t->sort_choice = pick_sort;
+    if ((st = lbvh_build(t, d_prims, n, kind, morton_bits, stream)) != LBVH_OK) return finish(st);
+    if ((st = lbvh_tree_status(t)) != LBVH_OK) return finish(st);
+    int pick_walk = kWalkThread;
+    if (nq > 0 && n > 0) {
+        DevBuf offsets;
+        LBVH_CUDA(offsets.ensure((size_t)(nq + 1) * 8, s));
+        float best_walk = 1e30f;
+        for (int w = 0; w < kWalkKinds; ++w) {
+            t->walk_choice = w;
+            for (int rep = 0; rep < 2; ++rep) {
+                QueryArgs qa{d_queries, nq, qkind, d_radii, radius, nullptr};
+                uint64_t total = 0;
+                st = query_count(t, qa, offsets.as<int64_t>(), s, &total);
+                if (st != LBVH_OK) {
+                    offsets.release(s);
+                    return finish(st);
+                }
+                const float ms = stages_ms(t, LBVH_STAGE_QCOUNT, LBVH_STAGE_QCOUNT + 1);
+                if (ms >= 0.0f && ms < best_walk) {
+                    best_walk = ms;
+                    pick_walk = w;
+                }
+            }
+        }
+        offsets.release(s);
+        TuneChoice made;
+        made.walk = pick_walk;
+        made.walk_ms = best_walk;
+        tune_put(tune_key(n, morton_bits, kind, qkind, 1), made);
+    }
+    if (sort_variant) *sort_variant = pick_sort;
+    if (walk_variant) *walk_variant = pick_walk;
+    return finish(LBVH_OK);
+}
 
 lbvh_status lbvh_tree_set_profiling(lbvh_tree_t t, int on) {
     if (!t) return LBVH_ERR_INVALID;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "lbvh.h"
 
@@ -206,7 +207,11 @@ struct QueryArgs {
     const float *radii;  // null: `radius` for every query
     float radius;
     const uint32_t *order;  // null: thread i walks query i; else query order[i]
+    int walk = 0;           // kWalk*: how the collecting walk runs
 };
+// The collecting walk: one thread per query, or groups of 8, 16 or 32 lanes
+// walking together (walk_group in query.cu).
+enum : int { kWalkThread = 0, kWalkGroup8 = 1, kWalkGroup16 = 2, kWalkGroup32 = 3, kWalkKinds = 4 };
 // Hits past a walk's slot go to chunks of kSpillChunkWords words taken from a
 // shared pool (word 0 links to the next chunk of the same walk, the rest
 // hold hits). When the pool runs out, the query walks a second time instead.
@@ -311,6 +316,31 @@ lbvh_status tree_from_batch(lbvh_batch_t b, int64_t instance, lbvh_tree_t t, cud
 void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s);
 
 int device_sm_count();
+
+// ---------------------------------------------------------------- autotuner (tune.cu)
+// A configuration: GPU, ceil(log2 n), Morton bits, primitive kind, query kind
+// (-1: the sort of a build), trees built together.
+struct TuneKey {
+    std::string gpu;
+    int n_log2, bits, kind, qkind;
+    int64_t instances;
+    bool operator<(const TuneKey &o) const;
+};
+// sort: variant of sort.cu's table; walk: kWalk*; -1: not measured.
+struct TuneChoice {
+    int sort = -1, walk = -1;
+    float sort_ms = 0.0f, walk_ms = 0.0f;
+};
+int ceil_log2(int64_t x);
+std::string current_gpu_name();
+TuneKey tune_key(int64_t n, int bits, int kind, int qkind, int64_t instances);
+bool tune_find(const TuneKey &k, TuneChoice *out);
+// Stores the fields of c that are set (>= 0), keeping the others.
+void tune_put(const TuneKey &k, const TuneChoice &c);
+// The cached choices for a configuration: the sort variant (-1: the default)
+// and the walk (kWalkThread when nothing is cached).
+int tune_sort_choice(int64_t n, int bits, int kind, int64_t instances);
+int tune_walk_choice(int64_t n, int bits, int kind, int qkind, int64_t instances);
 
 // Device memory of the library: one stream-ordered pool per device, owned by
 // the library, that keeps freed blocks for reuse (its release threshold is

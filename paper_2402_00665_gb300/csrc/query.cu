@@ -216,6 +216,46 @@ __device__ __forceinline__ bool walk(const TreeView &t, const Q &q, F &&on_leaf)
     return node == kSentinel || node == nodes;
 }
 
+// Algorithm 1 walked by a group of kLanes adjacent lanes together (8, 16 or
+// 32): the group stands at one node, every lane tests its own query there,
+// and at an internal node the group goes to the left child if any lane's
+// predicate holds, else to the skip. Every lane calls on_leaf for each leaf
+// its own predicate accepts. The group's walk visits every node that one of
+// its lanes' own walks visits (a leaf a lane accepts has all its ancestors
+// accepted by that lane, the predicates being monotone), in the same
+// pre-order, so each lane reports exactly its own walk's hits, in the same
+// order. A step loads one node for the whole group (a broadcast) instead of
+// one per lane, and walks the union of the lanes' paths. Lanes without a
+// query (active false) walk along and report nothing.
+template <int kP, int kLanes, typename Q, typename F>
+__device__ __forceinline__ bool walk_group(const TreeView &t, const Q &q, bool active, F &&on_leaf) {
+    const int ni = (int)t.n - 1;
+    const int nodes = 2 * (int)t.n - 1;
+    const uint32_t max_steps = 2u * (uint32_t)nodes;
+    const float4 *base = t.inodes;
+    const int lane = threadIdx.x & 31;
+    const uint32_t gmask =
+        kLanes == 32 ? 0xffffffffu : (((1u << kLanes) - 1u) << (lane & ~(kLanes - 1)));
+    int node = 0;
+    uint32_t steps = 0;
+    while ((uint32_t)node < (uint32_t)nodes) {
+        if (++steps > max_steps) return false;
+        const bool leaf = node >= ni;
+        const int unit = kP == LBVH_PRIM_BOXES ? 2 * node : (leaf ? node + ni : 2 * node);
+        float4 a, b;
+        load_node<kP>(base, unit, leaf, a, b);
+        const bool hit = active && hits(q, xyz(a), xyz(b));
+        const uint32_t word = __float_as_uint(a.w);
+        if (leaf) {
+            if (hit) on_leaf(word & kLeafIndexMask);
+            node = node + 1 - ((word & kLeafSkipInternal) ? ni : 0);
+        } else {
+            node = __float_as_int((__ballot_sync(gmask, hit) & gmask) ? a.w : b.w);
+        }
+    }
+    return node == kSentinel || node == nodes;
+}
+
 constexpr int kSlot = kQueryBufferHits;  // ids kept per walk (slot size)
 constexpr int kRegSort = 32;             // lists up to this long are sorted in one thread's registers
 
@@ -252,13 +292,17 @@ __device__ __forceinline__ void spill_put(const QueryScratch &qs, Control *ctl, 
 // hits go to the slot, later ones to spill chunks. Writes (count, i) and, for
 // a long list, its overflow-list entry (tagged when all its hits are in slot
 // + chunks).
-template <int kQ, int kP, bool kPairs>
+// kLanes = 0: the thread walks alone (walk); else with its group of kLanes
+// lanes (walk_group; every lane of the warp must call this, `has_query`
+// false for lanes past the last query).
+template <int kQ, int kP, bool kPairs, int kLanes = 0>
 __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs &qa, const QueryScratch &qs,
-                                             Control *ctl, int64_t i, int64_t qi, bool walk_ok) {
+                                             Control *ctl, int64_t i, int64_t qi, bool walk_ok,
+                                             bool has_query = true) {
     uint32_t cnt = 0;
     uint32_t cur = kNoChunk;
     if (walk_ok) {
-        const auto q = QueryOf<kQ>::load(qa, qi);
+        const auto q = has_query ? QueryOf<kQ>::load(qa, qi) : typename QueryOf<kQ>::type{};
         uint32_t *slot = qs.slots + i * kSlot;
         // kPairs: hits go to the slot two at a time (one 8-byte store; words
         // past the count are never read). Point trees, one tree: walk 16.19
@@ -266,7 +310,7 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
         // 8-byte spill; 16.00 ms at 40 registers); on box trees it cost more
         // (D3 walk 8.39 -> 8.49 ms at 40 registers).
         uint2 buf = make_uint2(0u, 0u);
-        const bool ok = walk<kP>(t, q, [&](uint32_t id) {
+        auto keep = [&](uint32_t id) {
             if (cnt < (uint32_t)kSlot) {
                 if (!kPairs) {
                     __stcs(slot + cnt, id);
@@ -280,97 +324,50 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
                 spill_put(qs, ctl, i, cnt, id, cur);
             }
             ++cnt;
-        });
+        };
+        bool ok;
+        if constexpr (kLanes == 0)
+            ok = walk<kP>(t, q, keep);
+        else
+            ok = walk_group<kP, kLanes>(t, q, has_query, keep);
+        if (!has_query) return;
         if (kPairs && cnt < (uint32_t)kSlot && (cnt & 1u)) __stcs(reinterpret_cast<uint2 *>(slot + cnt - 1), buf);
         if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
     }
+    if (!has_query) return;
     __stcs(qs.count_pos + qi, make_uint2(cnt, (uint32_t)i));  // streamed: keep L2 for the tree
     if (cnt > (uint32_t)kSlot)
         qs.overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] =
             (uint32_t)qi | (cur != kSpillFailed ? kSpilledTag : 0u);
 }
 
-// K walks per thread, advanced in lock step: each iteration first issues the
-// node loads of every live walk, then tests them, so K independent loads are
-// in flight per thread (the walk is bound by the latency of its dependent
-// loads, not by bandwidth). Thread t walks sorted positions K*t .. K*t+K-1,
-// which are neighbours in the Morton order. Each walk keeps its hit count and
-// up to kSlot primitive ids (walk order) in the slot of its walk position.
-// At most 32 registers (8 CTAs of 256 threads per SM): the walk hides its
-// load latency with occupancy.
-template <int kQ, int kP, int K>
-__global__ void __launch_bounds__(kThreads, K == 1 ? 8 : 1)
-    collect_kernel(TreeView t, QueryArgs qa, QueryScratch qs, Control *ctl) {
-    uint2 *__restrict__ count_pos = qs.count_pos;
-    uint32_t *__restrict__ slots = qs.slots;
-    const int64_t first = ((int64_t)blockIdx.x * kThreads + threadIdx.x) * K;
-    if (first >= qa.nq) return;
+// The collecting walk with groups of kLanes lanes walking together
+// (walk_group); thread i takes walk position i as in collect_kernel.
+template <int kQ, int kP, int kLanes>
+__global__ void __launch_bounds__(kThreads, 8)
+    collect_group_kernel(TreeView t, QueryArgs qa, QueryScratch qs, Control *ctl) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t warp_first = i - (threadIdx.x & 31);
+    if (warp_first >= qa.nq) return;  // whole warps leave together
+    const bool has = i < qa.nq;
     const bool walk_ok = t.n > 0 && ctl->build_flags == 0;
-    if (K == 1) {
-        collect_walk<kQ, kP, kP == LBVH_PRIM_POINTS>(t, qa, qs, ctl, first, thread_query(qa, first), walk_ok);
-        return;
-    }
-    // K > 1 (tuning): lock-step walks; lists past the slot take the second walk
-    const int ni = (int)t.n - 1;
-    const int nodes = 2 * (int)t.n - 1;
-    const uint32_t max_steps = 2u * (uint32_t)nodes;
-    const float4 *base = t.inodes;
-    using Q = typename QueryOf<kQ>::type;
-    Q q[K];
-    int node[K];
-    uint32_t cnt[K], steps[K];
-    int64_t qi[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const int64_t i = first + j;
-        cnt[j] = 0;
-        steps[j] = 0;
-        node[j] = (i < qa.nq && walk_ok) ? 0 : kSentinel;
-        qi[j] = i < qa.nq ? thread_query(qa, i) : 0;
-        if (i < qa.nq) q[j] = QueryOf<kQ>::load(qa, qi[j]);
-    }
-    while (true) {
-        float4 a[K], b[K];
-        bool live[K], any = false;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            live[j] = (uint32_t)node[j] < (uint32_t)nodes;
-            any |= live[j];
-            if (live[j]) {
-                const bool leaf = node[j] >= ni;
-                const int unit = kP == LBVH_PRIM_BOXES ? 2 * node[j] : (leaf ? node[j] + ni : 2 * node[j]);
-                load_node<kP>(base, unit, leaf, a[j], b[j]);
-            }
-        }
-        if (!any) break;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (!live[j]) continue;
-            if (++steps[j] > max_steps) {  // a corrupt tree: stop this walk
-                node[j] = nodes + 1;
-                continue;
-            }
-            const bool leaf = node[j] >= ni;
-            const bool hit = hits(q[j], xyz(a[j]), xyz(b[j]));
-            const uint32_t word = __float_as_uint(a[j].w);
-            if (hit && leaf) {
-                if (cnt[j] < (uint32_t)kSlot) __stcs(slots + (first + j) * kSlot + cnt[j], word & kLeafIndexMask);
-                ++cnt[j];
-            }
-            // internal: left child on a hit, else skip; leaf k: position k+1
-            node[j] = leaf ? node[j] + 1 - ((word & kLeafSkipInternal) ? ni : 0)
-                           : __float_as_int(hit ? a[j].w : b[j].w);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const int64_t i = first + j;
-        if (i >= qa.nq) continue;
-        if (walk_ok && !(node[j] == kSentinel || node[j] == nodes)) atomicOr(&ctl->query_flags, kFlagCorrupt);
-        __stcs(count_pos + qi[j], make_uint2(cnt[j], (uint32_t)i));  // streamed: keep L2 for the tree
-        if (cnt[j] > (uint32_t)kSlot)
-            qs.overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] = (uint32_t)qi[j];
-    }
+    collect_walk<kQ, kP, kP == LBVH_PRIM_POINTS, kLanes>(t, qa, qs, ctl, i, has ? thread_query(qa, i) : 0, walk_ok,
+                                                       has);
+}
+
+// One thread per walk position: thread i walks position i (query order[i]).
+// At most 32 registers (8 CTAs of 256 threads per SM): the walk hides its
+// load latency with occupancy. Several walks per thread in lock step (K
+// independent loads in flight per thread) measured slower on GB300: the walk
+// is bound by L1 wavefronts (distinct sectors per load), which more walks per
+// thread only increase.
+template <int kQ, int kP>
+__global__ void __launch_bounds__(kThreads, 8)
+    collect_kernel(TreeView t, QueryArgs qa, QueryScratch qs, Control *ctl) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i >= qa.nq) return;
+    const bool walk_ok = t.n > 0 && ctl->build_flags == 0;
+    collect_walk<kQ, kP, kP == LBVH_PRIM_POINTS>(t, qa, qs, ctl, i, thread_query(qa, i), walk_ok);
 }
 
 // Batcher's odd-even merge sort of v[0..kN) (kN a power of two), keeping only
@@ -841,38 +838,19 @@ void dispatch_kinds(int qkind, int pkind, F &&f) {
     }
 }
 
-// Walks per thread in the collecting kernel: LBVH_WALKS_PER_THREAD=1..4
-// overrides the default (tuning sweeps). One is fastest on GB300: the walk is
-// bound by L1 wavefronts (distinct sectors per load), which more walks per
-// thread only increase.
-static int walks_per_thread() {
-    static const int k = [] {
-        const char *env = getenv("LBVH_WALKS_PER_THREAD");
-        const int want = env ? atoi(env) : 1;
-        return want >= 1 && want <= 4 ? want : 1;
-    }();
-    return k;
-}
-
-template <int K>
-void launch_collect_k(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
-                      cudaStream_t s) {
-    const int64_t threads = (q.nq + K - 1) / K;
-    const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
-    dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
-        collect_kernel<decltype(qk)::value, decltype(pk)::value, K><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl);
-    });
-}
-
 void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
                           cudaStream_t s) {
     if (q.nq <= 0) return;
-    switch (walks_per_thread()) {
-    case 3: launch_collect_k<3>(t, q, qs, ctl, s); break;
-    case 4: launch_collect_k<4>(t, q, qs, ctl, s); break;
-    case 2: launch_collect_k<2>(t, q, qs, ctl, s); break;
-    default: launch_collect_k<1>(t, q, qs, ctl, s); break;
-    }
+    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
+    dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
+        constexpr int Q = decltype(qk)::value, P = decltype(pk)::value;
+        switch (q.walk) {
+        case kWalkGroup8: collect_group_kernel<Q, P, 8><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
+        case kWalkGroup16: collect_group_kernel<Q, P, 16><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
+        case kWalkGroup32: collect_group_kernel<Q, P, 32><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
+        default: collect_kernel<Q, P><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
+        }
+    });
     count_launches(1);
 }
 

@@ -70,6 +70,14 @@ SIGNATURES = {
     "lbvh_server_destroy": (None, [_P]),
     "lbvh_construct_static": (_I32, [_P, _P, _P, _I64, _I32, _P, _P, _P, _P]),
     "lbvh_tree_set_profiling": (_I32, [_P, _I32]),
+    "lbvh_sort_variant_count": (_I32, []),
+    "lbvh_walk_variant_count": (_I32, []),
+    "lbvh_tree_autotune": (_I32, [_P, _P, _I64, _I32, _I32, _P, _I64, _I32, _P, _F32, _P, _P, _P]),
+    "lbvh_tree_set_tuning": (_I32, [_P, _I32, _I32]),
+    "lbvh_tune_save": (_I32, [ctypes.c_char_p]),
+    "lbvh_tune_load": (_I32, [ctypes.c_char_p]),
+    "lbvh_tune_clear": (None, []),
+    "lbvh_tune_entries": (_I32, []),
     "lbvh_tree_stage_times": (_I32, [_P, _P]),
     "lbvh_stage_name": (ctypes.c_char_p, [_I32]),
     "lbvh_kernel_launches": (_U64, []),
@@ -234,6 +242,31 @@ class Tree:
         b = ctypes.c_uint64()
         _check(self._lib.lbvh_tree_bytes(self._h, ctypes.byref(b)), "lbvh_tree_bytes")
         return b.value
+
+    def autotune(self, prims, kind: int = POINTS, morton_bits: int = 30, queries=None, qkind: int = SPHERE,
+                 radius: float = 0.0, radii=None, stream=None) -> tuple:
+        """lbvh_tree_autotune: times every sort (and, with queries, every walk)
+        variant on these inputs, caches the fastest; returns (sort, walk)."""
+        torch = _torch()
+        p = _dev(prims, torch.float32, 3 if kind == POINTS else 6)
+        q, nq, r = None, 0, None
+        if queries is not None:
+            q = _dev(queries, torch.float32, _QDIM[qkind])
+            nq = q.shape[0]
+            r = _dev(radii, torch.float32) if radii is not None else None
+        sv, wv = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lbvh_tree_autotune(self._h, _ptr(p), p.shape[0], kind, morton_bits,
+                                            _ptr(q) if q is not None else None, nq, qkind,
+                                            _ptr(r) if r is not None else None, float(radius), _stream(stream),
+                                            ctypes.byref(sv), ctypes.byref(wv)), "lbvh_tree_autotune")
+        self._keep = (p, q, r)
+        self.kind = kind
+        return sv.value, wv.value
+
+    def set_tuning(self, sort_variant: int = -1, walk_variant: int = -1):
+        """lbvh_tree_set_tuning: fix this tree's variants (-1: the cache's choice)."""
+        _check(self._lib.lbvh_tree_set_tuning(self._h, int(sort_variant), int(walk_variant)),
+               "lbvh_tree_set_tuning")
 
     def set_profiling(self, on: bool = True):
         _check(self._lib.lbvh_tree_set_profiling(self._h, int(bool(on))), "lbvh_tree_set_profiling")
@@ -509,6 +542,32 @@ def sort_pairs(keys, vals=None, key_bits: int = 64, stream=None):
     _check(lib.lbvh_sort_pairs(_ptr(k), _ptr(v), n, key_bits, _ptr(ko), _ptr(vo), _stream(stream)),
            "lbvh_sort_pairs")
     return ko, vo
+
+
+def sort_variant_count() -> int:
+    return load().lbvh_sort_variant_count()
+
+
+def walk_variant_count() -> int:
+    return load().lbvh_walk_variant_count()
+
+
+def tune_save(path: str) -> None:
+    """lbvh_tune_save: the tuner's cache to a JSON file."""
+    _check(load().lbvh_tune_save(os.fsencode(path)), "lbvh_tune_save")
+
+
+def tune_load(path: str) -> None:
+    """lbvh_tune_load: merge a saved cache file into the tuner's cache."""
+    _check(load().lbvh_tune_load(os.fsencode(path)), "lbvh_tune_load")
+
+
+def tune_clear() -> None:
+    load().lbvh_tune_clear()
+
+
+def tune_entries() -> int:
+    return load().lbvh_tune_entries()
 
 
 def release_cached_memory() -> None:

@@ -101,3 +101,37 @@ def test_binding_fails_loudly_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError, match="no CUDA device"):
         lbvh.Tree().build([[0.0, 0.0, 0.0]])
+
+
+def test_tune_cache_file_round_trip_without_a_gpu(lib_path, tmp_path):
+    """The tuner's cache file is read and written on the host alone."""
+    import json
+    lib = lbvh.load(lib_path)
+    lib.lbvh_tune_clear()
+    good = tmp_path / "tune.json"
+    good.write_text(json.dumps({"lbvh_tune_cache": 1, "entries": [
+        {"gpu": "NVIDIA GB300", "n_log2": 25, "bits": 63, "kind": 0, "qkind": -1, "instances": 1,
+         "sort_variant": 1, "sort_ms": 2.27, "walk_variant": -1, "walk_ms": 0},
+        {"gpu": "NVIDIA GB300", "n_log2": 25, "bits": 63, "kind": 0, "qkind": 0, "instances": 1,
+         "sort_variant": -1, "sort_ms": 0, "walk_variant": 3, "walk_ms": 15.5},
+        {"gpu": 'other "quoted" gpu', "n_log2": 10, "bits": 30, "kind": 1, "qkind": 1, "instances": 4096,
+         "sort_variant": 99, "sort_ms": 1.0, "walk_variant": 1, "walk_ms": 0.5}]}))
+    assert lib.lbvh_tune_load(os.fsencode(str(good))) == lbvh.OK
+    assert lib.lbvh_tune_entries() == 3
+    out = tmp_path / "saved.json"
+    assert lib.lbvh_tune_save(os.fsencode(str(out))) == lbvh.OK
+    saved = json.load(open(out))["entries"]
+    by_gpu = {(e["gpu"], e["qkind"]): e for e in saved}
+    assert by_gpu[("NVIDIA GB300", -1)]["sort_variant"] == 1
+    assert by_gpu[("NVIDIA GB300", 0)]["walk_variant"] == 3
+    # a variant index the library does not have is dropped on load
+    assert by_gpu[('other "quoted" gpu', 1)]["sort_variant"] == -1
+    assert by_gpu[('other "quoted" gpu', 1)]["walk_variant"] == 1
+    bad = tmp_path / "bad.json"
+    for text in ("", "{", '{"entries": [{"gpu": 3}]}', '{"entries": [{"n_log2": 1}]}', "not json"):
+        bad.write_text(text)
+        assert lib.lbvh_tune_load(os.fsencode(str(bad))) == lbvh.ERR_INVALID
+    assert lib.lbvh_tune_load(os.fsencode(str(tmp_path / "missing.json"))) == lbvh.ERR_INVALID
+    assert lib.lbvh_tune_entries() == 3  # a failed load leaves the cache as it was
+    lib.lbvh_tune_clear()
+    assert lib.lbvh_tune_entries() == 0
