@@ -20,6 +20,9 @@ and at the top of ``lbvh_oracle.c``:
   box overlap, and ray segment (slab test: Sec. 1 names both distance and
   ray range searches)
 * refit - boxes (Sec. 3.1 step 4) recomputed on a kept topology
+* k nearest neighbours - brute force in the order (squared distance, index),
+  the distance being the ball test's d2 (the distance range search of Sec. 1
+  asked for its k closest answers)
 """
 from __future__ import annotations
 
@@ -83,6 +86,8 @@ def _load():
             "oracle_sphere_box": (i32, [P, f32, P]),
             "oracle_box_box": (i32, [P, P]),
             "oracle_ray_box": (i32, [P, P]),
+            "oracle_knn_bruteforce": (i32, [P, i64, i32, P, i64, i32, P, P]),
+            "oracle_point_box_d2": (f32, [P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -283,3 +288,27 @@ def box_box(a6, b6) -> bool:
     a = np.ascontiguousarray(a6, dtype=np.float32)
     b = np.ascontiguousarray(b6, dtype=np.float32)
     return bool(_load().oracle_box_box(_ptr(a), _ptr(b)))
+
+
+def knn(prims, kind, queries, k: int):
+    """Brute-force k nearest neighbours: (idx uint32[nq, k], d2 float32[nq, k]),
+    each row in the order (squared distance, primitive index), padded with
+    0xffffffff / +inf past min(k, n); a query with a non-finite coordinate
+    has no neighbours."""
+    lib = _load()
+    p = _prims(prims, kind)
+    q = np.ascontiguousarray(queries, np.float32).reshape(-1, 3)
+    nq = q.shape[0]
+    idx = np.empty((nq, k), np.uint32)
+    d2 = np.empty((nq, k), np.float32)
+    st = lib.oracle_knn_bruteforce(_ptr(p), p.shape[0], kind, _ptr(q), nq, int(k), _ptr(idx), _ptr(d2))
+    if st != OK:
+        raise OracleError(st)
+    return idx, d2
+
+
+def point_box_d2(point, box6) -> float:
+    lib = _load()
+    c = np.ascontiguousarray(point, np.float32)
+    b = np.ascontiguousarray(box6, np.float32)
+    return float(lib.oracle_point_box_d2(_ptr(c), _ptr(b)))

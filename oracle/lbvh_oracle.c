@@ -406,6 +406,76 @@ static int sphere_box_r2(const float *c, float r2, const float *box) {
     return d2 <= r2;
 }
 
+/* Squared distance from a point to a closed box, by the same steps as the
+ * ball test above: e = max(lo - c, c - hi, 0) per axis, d2 = ex*ex, then
+ * + ey*ey and + ez*ez each as one fused multiply-add. */
+static float point_box_d2(const float *c, const float *box) {
+    float e[3];
+    for (int a = 0; a < 3; ++a) {
+        float below = box[a] - c[a];
+        float above = c[a] - box[3 + a];
+        e[a] = fmaxf(fmaxf(below, above), 0.0f);
+    }
+    float d2 = e[0] * e[0];
+    d2 = fmaf(e[1], e[1], d2);
+    d2 = fmaf(e[2], e[2], d2);
+    return d2;
+}
+
+float oracle_point_box_d2(const float *point, const float *box6) { return point_box_d2(point, box6); }
+
+/* The k nearest primitives of each query point by brute force: every
+ * primitive's squared distance (point_box_d2) and the first k in the order
+ * (d2, primitive index). A query with a coordinate that is not finite has no
+ * neighbours. Row qi of idx / d2 (uint32 / float [nq][k]) holds them in that
+ * order; entries past min(k, n), and every entry of a query without
+ * neighbours, are 0xffffffff / +inf. */
+int oracle_knn_bruteforce(const float *prims, int64_t n, int kind, const float *queries, int64_t nq, int k,
+                          uint32_t *idx, float *d2_out) {
+    if (n < 0 || nq < 0 || k < 1 || (kind != ORACLE_POINTS && kind != ORACLE_BOXES)) return ORACLE_INVALID;
+    const int64_t m = n < k ? n : k;
+    float *bd = (float *)malloc((size_t)(k > 0 ? k : 1) * sizeof(float));
+    uint32_t *bi = (uint32_t *)malloc((size_t)(k > 0 ? k : 1) * sizeof(uint32_t));
+    if (!bd || !bi) {
+        free(bd);
+        free(bi);
+        return ORACLE_INVALID;
+    }
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        const float *c = queries + 3 * qi;
+        int64_t have = 0;
+        if (isfinite(c[0]) && isfinite(c[1]) && isfinite(c[2])) {
+            for (int64_t j = 0; j < n; ++j) {
+                float box[6];
+                for (int a = 0; a < 3; ++a) {
+                    box[a] = kind == ORACLE_POINTS ? prims[3 * j + a] : prims[6 * j + a];
+                    box[3 + a] = kind == ORACLE_POINTS ? prims[3 * j + a] : prims[6 * j + 3 + a];
+                }
+                const float d = point_box_d2(c, box);
+                /* j is larger than every index kept so far, so among equal
+                 * distances it goes last */
+                if (have == m && !(d < bd[m - 1])) continue;
+                int64_t at = have < m ? have : m - 1;
+                while (at > 0 && d < bd[at - 1]) {
+                    bd[at] = bd[at - 1];
+                    bi[at] = bi[at - 1];
+                    --at;
+                }
+                bd[at] = d;
+                bi[at] = (uint32_t)j;
+                if (have < m) ++have;
+            }
+        }
+        for (int64_t r = 0; r < k; ++r) {
+            idx[qi * k + r] = r < have ? bi[r] : 0xffffffffu;
+            if (d2_out) d2_out[qi * k + r] = r < have ? bd[r] : INFINITY;
+        }
+    }
+    free(bd);
+    free(bi);
+    return ORACLE_OK;
+}
+
 int oracle_sphere_box(const float *centre, float radius, const float *box6) {
     float r2 = radius * radius;
     return sphere_box_r2(centre, r2, box6);

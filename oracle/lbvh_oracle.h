@@ -119,6 +119,18 @@ int64_t oracle_query_bruteforce(const float *prims, int64_t n, int kind,
                                 const float *radii, float radius,
                                 int64_t *offsets, uint32_t *hits, int64_t cap);
 
+/* k nearest neighbours (the distance range search of Sec. 1 turned into its
+ * k closest answers) by brute force: for each query point the first k
+ * primitives in the order (squared point-to-box distance, primitive index).
+ * queries float[nq][3]; idx uint32[nq][k], d2 float[nq][k] (nullable); rows
+ * are padded with 0xffffffff / +inf past min(k, n), and a query with a
+ * non-finite coordinate has no neighbours. Returns ORACLE_OK or
+ * ORACLE_INVALID. */
+int oracle_knn_bruteforce(const float *prims, int64_t n, int kind, const float *queries, int64_t nq, int k,
+                          uint32_t *idx, float *d2);
+/* The squared distance used above (the ball test's d2). */
+float oracle_point_box_d2(const float *point, const float *box6);
+
 /* The predicates themselves, exported for tests. */
 int oracle_sphere_box(const float *centre, float radius, const float *box6);
 int oracle_box_box(const float *a6, const float *b6);

@@ -584,3 +584,86 @@ def test_ray_traversal_equals_bruteforce(kind):
     boff, bhits = oracle.bruteforce(prims, kind, rays, oracle.RAY)
     assert np.array_equal(off, boff) and np.array_equal(hits, bhits)
     assert len(hits) >= nr // 2
+
+
+# ---------------------------------------------------------------- k nearest neighbours
+
+
+def test_knn_hand_computed_line():
+    """Points at x = 0..4 on a line, a query at x = 2.4: distances 2.4, 1.4,
+    0.4, 0.6, 1.6, so the order is 2, 3, 1, 4, 0."""
+    pts = np.array([[x, 0.0, 0.0] for x in range(5)], np.float32)
+    q = np.array([[2.4, 0.0, 0.0]], np.float32)
+    idx, d2 = oracle.knn(pts, oracle.POINTS, q, 3)
+    assert idx.tolist() == [[2, 3, 1]]
+    assert np.allclose(d2, [[0.16, 0.36, 1.96]], rtol=1e-6)
+    idx, _ = oracle.knn(pts, oracle.POINTS, q, 5)
+    assert idx.tolist() == [[2, 3, 1, 4, 0]]
+
+
+def test_knn_ties_go_to_the_lower_index_and_padding():
+    # indices 0 and 1 are both at distance 1; 2 and 3 are the same point
+    pts = np.array([[1, 0, 0], [-1, 0, 0], [0, 3, 0], [0, 3, 0]], np.float32)
+    q = np.zeros((1, 3), np.float32)
+    idx, d2 = oracle.knn(pts, oracle.POINTS, q, 6)
+    assert idx.tolist() == [[0, 1, 2, 3, 0xFFFFFFFF, 0xFFFFFFFF]]
+    assert d2[0, :4].tolist() == [1.0, 1.0, 9.0, 9.0] and np.isinf(d2[0, 4:]).all()
+    # the reverse listing keeps the index order among equal distances
+    idx, _ = oracle.knn(pts[::-1].copy(), oracle.POINTS, q, 4)
+    assert idx.tolist() == [[2, 3, 0, 1]]
+    # no primitives: nothing but padding
+    idx, d2 = oracle.knn(np.zeros((0, 3), np.float32), oracle.POINTS, q, 2)
+    assert idx.tolist() == [[0xFFFFFFFF] * 2] and np.isinf(d2).all()
+
+
+def test_knn_non_finite_query_has_no_neighbours():
+    pts = inputs.uniform_points(50, seed=3)
+    q = np.array([[np.nan, 0.5, 0.5], [0.5, np.inf, 0.5], [0.5, 0.5, 0.5]], np.float32)
+    idx, d2 = oracle.knn(pts, oracle.POINTS, q, 4)
+    assert (idx[:2] == 0xFFFFFFFF).all() and np.isinf(d2[:2]).all()
+    assert (idx[2] != 0xFFFFFFFF).all()
+
+
+def test_knn_boxes_distance_is_the_gap_to_the_box():
+    boxes = np.array([
+        [0, 0, 0, 1, 1, 1],        # contains the query: distance 0
+        [-1, -1, -1, 2, 2, 2],     # contains it too: distance 0, higher index
+        [3, 0, 0, 4, 1, 1],        # 2.5 away along x
+        [2, 2, 0, 3, 3, 1],        # (1.5, 1.5, 0) away: 4.5
+    ], np.float32)
+    q = np.array([[0.5, 0.5, 0.5]], np.float32)
+    idx, d2 = oracle.knn(boxes, oracle.BOXES, q, 4)
+    assert idx.tolist() == [[0, 1, 3, 2]]
+    assert d2.tolist() == [[0.0, 0.0, 4.5, 6.25]]
+
+
+def test_knn_distance_is_the_ball_test_distance():
+    """d2 <= r*r exactly when the (separately pinned) ball test holds."""
+    rng = np.random.default_rng(7)
+    for _ in range(400):
+        c = rng.random(3, dtype=np.float32)
+        lo = rng.random(3, dtype=np.float32)
+        box = np.concatenate([lo, lo + rng.random(3, dtype=np.float32) * np.float32(0.3)])
+        d2 = oracle.point_box_d2(c, box)
+        r = float(np.sqrt(np.float32(d2)))
+        for rr in (np.nextafter(np.float32(r), np.float32(0)), np.float32(r), np.nextafter(np.float32(r), np.float32(9))):
+            assert oracle.sphere_box(c, float(rr), box) == (d2 <= np.float32(rr) * np.float32(rr))
+
+
+def test_knn_matches_float64_distances_away_from_ties():
+    rng = np.random.default_rng(11)
+    pts = rng.random((3000, 3), dtype=np.float32)
+    q = rng.random((200, 3), dtype=np.float32)
+    k = 16
+    idx, d2 = oracle.knn(pts, oracle.POINTS, q, k)
+    d64 = ((q[:, None, :].astype(np.float64) - pts[None, :, :].astype(np.float64)) ** 2).sum(axis=2)
+    order = np.argsort(d64, axis=1, kind="stable")
+    checked = 0
+    for i in range(len(q)):
+        s = np.sort(d64[i])
+        if s[k] - s[k - 1] < 1e-5 or np.min(np.diff(s[:k + 1])) < 1e-6:
+            continue  # a near tie FP32 may order either way
+        assert idx[i].tolist() == order[i, :k].tolist()
+        assert np.allclose(d2[i], s[:k], rtol=1e-5, atol=1e-7)
+        checked += 1
+    assert checked > 150
