@@ -242,6 +242,28 @@ lbvh_status lbvh_query(lbvh_tree_t tree, const float *d_queries, int64_t nq, int
                        const float *d_radii, float radius, int64_t **d_offsets,
                        uint32_t **d_hits, uint64_t *total, lbvh_stream_t stream);
 
+/* Largest k accepted by lbvh_knn. */
+#define LBVH_KNN_MAX_K 256
+
+/* The k nearest primitives of each query point: the distance range search of
+ * Sec. 1 asked for its k closest answers, walked stacklessly (Algorithm 1)
+ * with a ball whose radius is the current k-th best distance, which only
+ * shrinks, so the walk never skips a subtree that could hold an answer.
+ *   d_queries  query points float[nq][3].
+ *   k          1 .. LBVH_KNN_MAX_K.
+ *   d_idx      uint32[nq][k] out: row q holds the min(k, n) nearest primitive
+ *              indices in the order (squared distance, primitive index), then
+ *              0xffffffff padding. The squared distance is the one of the
+ *              sphere query (the point's gap to the primitive's box per axis,
+ *              FP32, d2 = ex*ex, + ey*ey, + ez*ez as fused multiply-adds). A
+ *              query with a non-finite coordinate has no neighbours.
+ *   d_dist2    float[nq][k] out or NULL: the squared distances, +inf padding.
+ * Buffers are the caller's. Synchronises `stream` once (for the status).
+ * LBVH_ERR_INVALID on bad arguments or an unbuilt tree; the build's error if
+ * it failed; LBVH_ERR_CORRUPT if a walk met an id outside the tree. */
+lbvh_status lbvh_knn(lbvh_tree_t tree, const float *d_queries, int64_t nq, int k, uint32_t *d_idx,
+                     float *d_dist2, lbvh_stream_t stream);
+
 /* Free device memory returned by lbvh_query. Accepts NULL. */
 void lbvh_free(void *d_ptr);
 

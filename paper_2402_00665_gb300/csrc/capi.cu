@@ -1197,6 +1197,34 @@ lbvh_status lbvh_query_into_host(lbvh_tree_t t, const float *d_queries, int64_t 
     return over ? LBVH_ERR_CAPACITY : LBVH_OK;
 }
 
+lbvh_status lbvh_knn(lbvh_tree_t t, const float *d_queries, int64_t nq, int k, uint32_t *d_idx, float *d_dist2,
+                     lbvh_stream_t stream) {
+    NvtxRange nvtx_range("lbvh_knn");
+    using namespace lbvh;
+    if (!t || !t->has_build || nq < 0 || nq > LBVH_MAX_PRIMS || k < 1 || k > LBVH_KNN_MAX_K)
+        return LBVH_ERR_INVALID;
+    if (nq > 0 && (!d_queries || !d_idx)) return LBVH_ERR_INVALID;
+    if (nq == 0) return LBVH_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LBVH_CUDA(cudaStreamWaitEvent(s, t->built, 0));
+    Control *c = t->dctl();
+    LBVH_CUDA(cudaMemsetAsync(&c->query_flags, 0, offsetof(Control, pad) - offsetof(Control, query_flags), s));
+    QueryArgs qa{d_queries, nq, LBVH_Q_SPHERE, nullptr, 0.0f, nullptr};
+    lbvh_status st = query_order(t, qa, s);  // the Morton order of the query points
+    if (st != LBVH_OK) return st;
+    // a lean (server-resident) tree keeps no sorted codes: its walks start
+    // without seeds, which is exact but slower
+    const uint64_t *codes = t->lean ? nullptr : t->sorted_codes();
+    launch_knn(t->view(), codes, t->bounds.as<float>(), t->bits, qa, k, d_idx, d_dist2, c, s);
+    LBVH_LAUNCHED();
+    if (!t->used) LBVH_CUDA(cudaEventCreateWithFlags(&t->used, cudaEventDisableTiming));
+    LBVH_CUDA(cudaEventRecord(t->used, s));
+    t->queried = true;
+    if ((st = read_control(t, s)) != LBVH_OK) return st;
+    st = flags_status(t->h_ctl->build_flags);
+    return st != LBVH_OK ? st : flags_status(t->h_ctl->query_flags);
+}
+
 lbvh_status lbvh_query(lbvh_tree_t t, const float *d_queries, int64_t nq, int qkind,
                        const float *d_radii, float radius, int64_t **d_offsets, uint32_t **d_hits,
                        uint64_t *total, lbvh_stream_t stream) {

@@ -233,6 +233,13 @@ struct QueryScratch {
 // The collecting walk (counts, short sorted lists, overflow list).
 void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScratch &qs, Control *ctl,
                           cudaStream_t s);
+// k nearest neighbours of the query points q.queries (float[nq][3], q.order
+// the walk order) into rows of out_idx / out_d2 (uint32 / float [nq][k]);
+// codes: the tree's sorted codes (null: no seeding), bounds and bits of its
+// Morton grid. k <= kKnnMaxK.
+constexpr int kKnnMaxK = 256;
+void launch_knn(const TreeView &t, const uint64_t *codes, const float *bounds, int bits, const QueryArgs &q, int k,
+                uint32_t *out_idx, float *out_d2, Control *ctl, cudaStream_t s);
 // offsets[0..nq] = exclusive scan of count_pos[.].x (offsets[nq] = total =
 // ctl->total).
 int64_t scan_tile_count(int64_t nq);

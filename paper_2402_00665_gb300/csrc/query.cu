@@ -47,6 +47,7 @@
 #include <type_traits>
 
 #include "lbvh_internal.cuh"
+#include "morton.cuh"
 
 namespace lbvh {
 
@@ -74,13 +75,16 @@ __device__ __forceinline__ float gap(float lo, float c, float hi) {
     return __fsub_rn(c, fminf(fmaxf(c, lo), hi));
 }
 
-__device__ __forceinline__ bool hits(const Sphere &s, float3 lo, float3 hi) {
-    const float ex = gap(lo.x, s.c.x, hi.x);
-    const float ey = gap(lo.y, s.c.y, hi.y);
-    const float ez = gap(lo.z, s.c.z, hi.z);
-    const float d2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
-    return d2 <= s.r2;
+// Squared distance from c to the box: ex*ex, then + ey*ey and + ez*ez each
+// as one fused multiply-add.
+__device__ __forceinline__ float box_d2(float3 c, float3 lo, float3 hi) {
+    const float ex = gap(lo.x, c.x, hi.x);
+    const float ey = gap(lo.y, c.y, hi.y);
+    const float ez = gap(lo.z, c.z, hi.z);
+    return __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
 }
+
+__device__ __forceinline__ bool hits(const Sphere &s, float3 lo, float3 hi) { return box_d2(s.c, lo, hi) <= s.r2; }
 
 // Slab test, each operation rounded once: per axis t1 = (lo - o) * inv and
 // t2 = (hi - o) * inv; tnear = max(tmin, min(t1, t2)), tfar = min(tmax,
@@ -816,6 +820,141 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ---- k nearest neighbours
+
+// Max-heap of (squared distance bits << 32 | primitive index) keys in the
+// thread's local memory: keys order like (distance, index), distances being
+// non-negative floats.
+template <int kCap>
+struct KnnHeap {
+    uint64_t h[kCap];
+    int cnt;
+
+    __device__ __forceinline__ void push(uint64_t key) {
+        int i = cnt++;
+        while (i > 0) {
+            const int p = (i - 1) >> 1;
+            if (h[p] >= key) break;
+            h[i] = h[p];
+            i = p;
+        }
+        h[i] = key;
+    }
+    // the largest key leaves and `key` (smaller than it) enters
+    __device__ __forceinline__ void sift_from_top(uint64_t key, int size) {
+        int i = 0;
+        while (true) {
+            const int l = 2 * i + 1;
+            if (l >= size) break;
+            const int r = l + 1;
+            const int c = (r < size && h[r] > h[l]) ? r : l;
+            if (h[c] <= key) break;
+            h[i] = h[c];
+            i = c;
+        }
+        h[i] = key;
+    }
+    // heap sort: ascending keys in h[0..cnt)
+    __device__ __forceinline__ void sort() {
+        for (int e = cnt - 1; e > 0; --e) {
+            const uint64_t top = h[0];
+            sift_from_top(h[e], e);
+            h[e] = top;
+        }
+    }
+};
+
+__device__ __forceinline__ uint64_t knn_key(float d2, uint32_t id) {
+    return ((uint64_t)__float_as_uint(d2) << 32) | id;
+}
+
+// The k nearest primitives of each query point: Algorithm 1 with a ball
+// whose radius is the current k-th best distance. The radius only shrinks
+// during the walk, so a subtree the walk skips (its box farther than the
+// radius then) holds no primitive that could enter the list later: the walk
+// stays exact. A node is entered when its box distance is <= the radius (a
+// primitive at exactly that distance may still win on its index). The list
+// starts from the m = min(k, n) leaves around the query's place in the
+// sorted Morton codes (a lower-bound search of the query's own code), so the
+// walk starts with a tight radius; those leaves are not considered again.
+// Queries with a non-finite coordinate get no neighbours. Row qi of out_idx
+// / out_d2 holds the neighbours in the order (d2, index), padded with
+// 0xffffffff / +inf.
+template <int kP, int kCap>
+__global__ void __launch_bounds__(128)
+    knn_kernel(TreeView t, const uint64_t *__restrict__ codes, const float *__restrict__ bounds, int bits,
+               QueryArgs qa, int k, uint32_t *__restrict__ out_idx, float *__restrict__ out_d2, Control *ctl) {
+    const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (i >= qa.nq) return;
+    const int64_t qi = thread_query(qa, i);
+    const float3 c = make_float3(__ldcs(qa.queries + 3 * qi), __ldcs(qa.queries + 3 * qi + 1),
+                                 __ldcs(qa.queries + 3 * qi + 2));
+    const int n = (int)t.n;
+    const int m = k < n ? k : n;
+    KnnHeap<kCap> hp;
+    hp.cnt = 0;
+    const bool finite = isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
+    if (finite && n > 0 && ctl->build_flags == 0) {
+        const int ni = n - 1;
+        const float4 *base = t.inodes;  // leaves follow the internal records
+        // the seed leaves [s0, s0 + m)
+        int s0 = 0;
+        if (codes && bits > 0 && m < n) {
+            const uint64_t qc = morton(c.x, c.y, c.z, make_grid(bounds, bits / 3));
+            int lo = 0, hi = n;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(codes + mid) < qc) lo = mid + 1;
+                else hi = mid;
+            }
+            s0 = min(max(lo - m / 2, 0), n - m);
+        }
+        for (int j = s0; j < s0 + m; ++j) {
+            const int unit = kP == LBVH_PRIM_BOXES ? 2 * (ni + j) : ni + j + ni;
+            float4 a, b;
+            load_node<kP>(base, unit, true, a, b);
+            hp.push(knn_key(box_d2(c, xyz(a), xyz(b)), __float_as_uint(a.w) & kLeafIndexMask));
+        }
+        if (m < n) {
+            const int nodes = 2 * n - 1;
+            const uint32_t max_steps = 2u * (uint32_t)nodes;
+            uint32_t steps = 0;
+            int node = 0;
+            while ((uint32_t)node < (uint32_t)nodes) {
+                if (++steps > max_steps) break;
+                const bool leaf = node >= ni;
+                const int unit = kP == LBVH_PRIM_BOXES ? 2 * node : (leaf ? node + ni : 2 * node);
+                float4 a, b;
+                load_node<kP>(base, unit, leaf, a, b);
+                const float d2 = box_d2(c, xyz(a), xyz(b));
+                const uint64_t worst = hp.h[0];  // the list is full (m entries) from the seeds on
+                const bool inside = d2 <= __uint_as_float((uint32_t)(worst >> 32));
+                const uint32_t word = __float_as_uint(a.w);
+                if (leaf) {
+                    const int pos = node - ni;
+                    if (inside && (pos < s0 || pos >= s0 + m)) {
+                        const uint64_t key = knn_key(d2, word & kLeafIndexMask);
+                        if (key < worst) hp.sift_from_top(key, m);
+                    }
+                    node = node + 1 - ((word & kLeafSkipInternal) ? ni : 0);
+                } else {
+                    node = __float_as_int(inside ? a.w : b.w);
+                }
+            }
+            if (!(node == kSentinel || node == nodes)) atomicOr(&ctl->query_flags, kFlagCorrupt);
+        }
+        hp.sort();
+    }
+    uint32_t *ri = out_idx + qi * k;
+    float *rd = out_d2 ? out_d2 + qi * k : nullptr;
+    for (int r = 0; r < k; ++r) {
+        const bool have = r < hp.cnt;
+        const uint64_t key = have ? hp.h[r] : ~0ull;
+        __stcs(ri + r, have ? (uint32_t)key : 0xffffffffu);
+        if (rd) __stcs(rd + r, have ? __uint_as_float((uint32_t)(key >> 32)) : __int_as_float(0x7f800000));
+    }
+}
+
 }  // namespace
 
 template <typename F>
@@ -918,6 +1057,23 @@ void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt,
     });
     count_launches(1);
     launch_sort_lists(qs, (uint64_t)q.nq, offsets, hits, capacity, ctl, s);
+}
+
+void launch_knn(const TreeView &t, const uint64_t *codes, const float *bounds, int bits, const QueryArgs &q, int k,
+                uint32_t *out_idx, float *out_d2, Control *ctl, cudaStream_t s) {
+    if (q.nq <= 0) return;
+    const unsigned blocks = (unsigned)((q.nq + 127) / 128);
+    auto go = [&](auto cap) {
+        constexpr int C = decltype(cap)::value;
+        if (t.kind == LBVH_PRIM_POINTS)
+            knn_kernel<LBVH_PRIM_POINTS, C><<<blocks, 128, 0, s>>>(t, codes, bounds, bits, q, k, out_idx, out_d2, ctl);
+        else
+            knn_kernel<LBVH_PRIM_BOXES, C><<<blocks, 128, 0, s>>>(t, codes, bounds, bits, q, k, out_idx, out_d2, ctl);
+    };
+    if (k <= 16) go(std::integral_constant<int, 16>{});
+    else if (k <= 64) go(std::integral_constant<int, 64>{});
+    else go(std::integral_constant<int, kKnnMaxK>{});
+    count_launches(1);
 }
 
 int64_t scan_tile_count(int64_t nq) { return (nq + kScanTile - 1) / kScanTile; }

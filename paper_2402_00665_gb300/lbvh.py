@@ -23,6 +23,7 @@ POINTS, BOXES = 0, 1
 SPHERE, BOX, RAY = 0, 1, 2
 MAX_PRIMS = (1 << 30) - 1
 MAX_BATCH = 1 << 20
+KNN_MAX_K = 256
 SERVER_PHASES = 4
 BUILD_MODIFIED_APETREI, BUILD_KARRAS, BUILD_APETREI = 0, 1, 2
 _QDIM = {SPHERE: 3, BOX: 6, RAY: 8}
@@ -48,6 +49,7 @@ SIGNATURES = {
     "lbvh_query_into_host": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _U64, _P, _P]),
     "lbvh_query": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _P, _P]),
     "lbvh_free": (None, [_P]),
+    "lbvh_knn": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
     "lbvh_morton_codes": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "lbvh_sort_pairs": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
     "lbvh_batch_create": (_I32, [_P]),
@@ -322,6 +324,19 @@ class Tree:
                                             _ptr(offsets), _ptr(hits), cap, ctypes.byref(total),
                                             _stream(stream))
         return st, total.value
+
+    def knn(self, queries, k: int, stream=None, distances: bool = True):
+        """lbvh_knn: the k nearest primitives of each query point; returns
+        (idx int32[nq, k] view of uint32, d2 float32[nq, k] or None), rows in
+        the order (squared distance, index), padded with 0xffffffff / +inf."""
+        torch = _torch()
+        q = _dev(queries, torch.float32, 3)
+        nq = q.shape[0]
+        idx = torch.empty((nq, k), dtype=torch.int32, device=q.device)
+        d2 = torch.empty((nq, k), dtype=torch.float32, device=q.device) if distances else None
+        _check(self._lib.lbvh_knn(self._h, _ptr(q), nq, int(k), _ptr(idx), _ptr(d2) if d2 is not None else None,
+                                  _stream(stream)), "lbvh_knn")
+        return idx, d2
 
     def query(self, queries, qkind: int = SPHERE, radius: float = 0.0, radii=None, capacity=None,
               stream=None):

@@ -86,3 +86,23 @@ def test_full_mixture_boxes_2pow25(bits):
     off, hits = t.query(torch.from_numpy(queries).cuda(), lbvh.BOX, capacity=16 * N)
     sample = np.random.default_rng(8).choice(N // 2, size=2048, replace=False)
     sampled_csr_check(off, hits, o, queries, oracle.BOX, 0.0, sample)
+
+
+def test_full_uniform_points_knn_2pow25():
+    """k = 16 nearest neighbours of all 2^25 points in the 2^25-point tree:
+    32 sampled rows against the oracle's brute force, and on every row the
+    properties that hold at any size (the point itself first at distance 0,
+    distances non-decreasing)."""
+    from paper_2402_00665_gb300 import lbvh
+    pts = inputs.uniform_points(N, seed=0)
+    dpts = torch.from_numpy(pts).cuda()
+    t = lbvh.Tree().build(dpts, lbvh.POINTS, 63)
+    idx, d2 = t.knn(dpts.clone(), 16)
+    sample = np.random.default_rng(9).choice(N, size=32, replace=False)
+    wi, wd = oracle.knn(pts, oracle.POINTS, pts[sample], 16)
+    gi = idx.cpu().numpy().view(np.uint32)
+    gd = d2.cpu().numpy()
+    assert np.array_equal(gi[sample], wi)
+    assert np.array_equal(gd[sample].view(np.uint32), wd.view(np.uint32))
+    assert (gi[:, 0] == np.arange(N, dtype=np.uint32)).all() and (gd[:, 0] == 0).all()
+    assert (np.diff(gd, axis=1) >= 0).all()
