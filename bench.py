@@ -63,7 +63,8 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
     """Algorithmic bytes of one launch of a stage (the data the method must
     move): pb = bytes of a primitive, lb = of a leaf record, qb = of a query;
     long_lists = (queries with more hits than the walk keeps, their hits)."""
-    qb = 32 if box_queries == "ray" else (24 if box_queries else 12)
+    knn = box_queries == "knn"
+    qb = 32 if box_queries == "ray" else (24 if box_queries and not knn else 12)
     pb, lb = (24, 32) if boxes else (12, 16)
     table = {
         "bounds": pb * n,
@@ -73,7 +74,8 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
         # codes, perm, primitive read; leaf + internal node write
         "construct": (8 + 4 + pb + lb + 32) * n,
         # query + count/position per query, each kept hit, the tree once
-        "query_walk": (qb + 8) * nq + 4 * hits + (32 + lb) * n,
+        # (kNN: the query, index and squared distance of each neighbour, the tree once)
+        "query_walk": (qb * nq + 8 * hits if knn else (qb + 8) * nq + 4 * hits) + (32 + lb) * n,
         "query_order": (qb + 4 + 4 * 16) * nq,  # 30-bit order codes as 32-bit keys: 4 sort passes
         "query_scan": 4 * nq + 8 * (nq + 1),
         "query_copy": 16 * nq + 8 * hits,
@@ -81,6 +83,37 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
         "query_overflow": (qb + 16) * long_lists[0] + 12 * long_lists[1],
     }
     return table.get(stage)
+
+def model_build_bytes(n: int, bits: int, boxes: bool = False) -> int:
+    """Algorithmic bytes of a whole build in the reference model of the path:
+    bounds read the primitives; encode reads them and writes 8-byte codes;
+    the sort reads 8 B for the global histogram and moves 12 B in and 12 B
+    out per pass (8-bit digits); the construct reads code, permutation and
+    primitive, writes the leaf's skip and box and the internal node, touches
+    one 8-byte store word and re-reads a sibling box (24 B). Points: 144 + 24
+    per pass = 336 B/prim at 63 bits (8 passes); boxes read and write 24-byte
+    primitives and 32-byte leaves instead."""
+    passes = (bits + 7) // 8
+    per = (200 if boxes else 144) + 24 * passes
+    return per * n
+
+
+def moved_build_bytes(n: int, bits: int, boxes: bool = False) -> int:
+    """Bytes this implementation's build kernels read and write, counted
+    from their layouts (each element once): bounds and encode stream the
+    primitives; the sort moves key + index (12 B each way) until the low four
+    bytes are sorted, then one packed 8-byte word, and the last pass writes
+    the 4-byte permutation alone (codes of at most 30 bits are packed from
+    the encoder on); the construct reads the permutation and gathers each
+    primitive, writes the sorted code, the leaf and the internal node."""
+    pb, lb = (24, 32) if boxes else (12, 16)
+    passes = (bits + 7) // 8
+    if bits <= 30:
+        sort = 16 * (passes - 1) + 12
+    else:
+        sort = 20 + 24 * 2 + 20 + 16 * (passes - 5) + 12
+    return (pb + (pb + 8) + sort + (4 + pb + 8 + lb + 32)) * n
+
 
 BATCH_WORKLOADS = {
     # name: (description, clouds, min size, max size, seed, Morton bits)
@@ -136,6 +169,9 @@ WORKLOADS = {
     "mixture_boxes_2^25_30bit": ("as mixture_boxes_2^25_63bit with 30-bit codes: most centres of a component "
                                  "share a code, so the index tie-break decides much of the tree",
                                  1 << 25, 30, "mixture_boxes"),
+    "knn_uniform_2^25_63bit": ("2^25 FP32 points uniform in [0,1)^3, 63-bit Morton codes; build + the 16 "
+                               "nearest neighbours of every point (lbvh_knn: Algorithm 1 with a shrinking ball)",
+                               1 << 25, 63, "knn"),
     "mixture_boxes_2^23_63bit": ("as mixture_boxes_2^25_63bit with 2^23 boxes and 2^22 queries (profiling case)",
                                  1 << 23, 63, "mixture_boxes"),
 }
@@ -265,6 +301,8 @@ def make_inputs(workload: str, seed: int):
         queries = inputs.gaussian_mixture_boxes(n // 2, seed=seed + 1, component_seed=seed)
         return desc, n, bits, prims, queries, True, True, 0.0
     pts = inputs.uniform_points(n, seed=seed)
+    if workload_family(workload) == "knn":
+        return desc, n, bits, pts, None, False, "knn", 0.0
     r = inputs.radius_for_neighbours(n)
     return desc, n, bits, pts, None, False, False, r
 
@@ -300,7 +338,16 @@ def traffic_for(stage: str):
 # ---------------------------------------------------------------- oracle timing
 
 
-def oracle_sample(seed: int, n_sample: int = 1 << 23, q_sample: int = 1 << 18, bits: int = 63,
+# One bounded sample of the workload for the CPU oracle, the same for the
+# reference arm (one sample per step) and the cpu_baseline leg (the median of
+# CPU_BASELINE_SAMPLES samples): a full build of 2^22 primitives and 2^17 of
+# its queries (about 2-3 s of one core), or the whole workload when it is
+# smaller.
+ORACLE_N, ORACLE_Q = 1 << 22, 1 << 17
+CPU_BASELINE_SAMPLES = 5
+
+
+def oracle_sample(seed: int, n_sample: int = ORACLE_N, q_sample: int = ORACLE_Q, bits: int = 63,
                   family: str = "uniform"):
     """The CPU oracle on a bounded sample of the same workload: a full build of
     n_sample primitives and q_sample of its queries (uniform points with radius
@@ -317,6 +364,12 @@ def oracle_sample(seed: int, n_sample: int = 1 << 23, q_sample: int = 1 << 18, b
         q = inputs.gaussian_mixture_boxes(q_sample, seed=seed + 102, component_seed=seed + 101)
         kind, qkind, r, what = oracle.BOXES, oracle.BOX, 0.0, "Gaussian-mixture boxes", 
         qwhat = "box-overlap queries from the same mixture"
+    elif family == "knn":
+        prims = inputs.uniform_points(n_sample, seed=seed + 101)
+        q_sample = min(q_sample, 64)  # brute force: every primitive per query
+        q = prims[:q_sample]
+        kind, qkind, r, what = oracle.POINTS, None, 0.0, "uniform points"
+        qwhat = "16-nearest-neighbour queries at its points (brute force)"
     else:
         prims = inputs.uniform_points(n_sample, seed=seed + 101)
         q = prims[:q_sample]
@@ -325,7 +378,10 @@ def oracle_sample(seed: int, n_sample: int = 1 << 23, q_sample: int = 1 << 18, b
     t0 = time.perf_counter()
     tree = oracle.build(prims, kind, bits)
     t1 = time.perf_counter()
-    oracle.query(tree, q, qkind, radius=r)
+    if qkind is None:
+        oracle.knn(prims, kind, q, 16)
+    else:
+        oracle.query(tree, q, qkind, radius=r)
     t2 = time.perf_counter()
     per_prim = (t1 - t0) / n_sample + (t2 - t1) / q_sample
     desc = (f"oracle (C, 1 thread) build of {n_sample} {what} at {bits} bits "
@@ -380,8 +436,8 @@ def run_reference(args, world, rank):
         sdesc = f"oracle refit (C boxes in post-order, 1 thread) of a {m}-point tree, per step"
     else:
         for step in range(args.warmup + args.steps):
-            v, sdesc, dt = oracle_sample(args.seed + step, n_sample=1 << 19, q_sample=1 << 13, bits=bits,
-                                         family=family)
+            v, sdesc, dt = oracle_sample(args.seed + step, n_sample=min(ORACLE_N, n), q_sample=min(ORACLE_Q, n),
+                                         bits=bits, family=family)
             if step >= args.warmup:
                 samples.append(v)
                 step_s.append(dt)
@@ -413,7 +469,8 @@ def run_gpu(args, world, rank, local):
     desc, n, bits, prims_host, queries_host, boxes, box_queries, radius = make_inputs(args.workload,
                                                                                        args.seed + rank)
     kind = lbvh.BOXES if boxes else lbvh.POINTS
-    qkind = lbvh.RAY if box_queries == "ray" else (lbvh.BOX if box_queries else lbvh.SPHERE)
+    knn = box_queries == "knn"
+    qkind = lbvh.RAY if box_queries == "ray" else (lbvh.BOX if box_queries and not knn else lbvh.SPHERE)
     pts = torch.from_numpy(prims_host).to(dev)
     # queries in their own buffer (the points themselves for the uniform
     # workloads): the general query path (query centres Morton-encoded and
@@ -425,16 +482,26 @@ def run_gpu(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     tree = lbvh.Tree()
+    # the autotuner picks the sort and walk variants on these very inputs
+    # (device-timed, two runs of each candidate) before anything is timed
+    tune_sort, tune_walk = tree.autotune(pts, kind, bits, queries=None if knn else qpts, qkind=qkind,
+                                         radius=float(radius))
     tree.set_profiling(True)
     offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     # size the hit buffer once (a production caller does the same)
     tree.build(pts, kind, bits)
-    st, total = tree.query_into(qpts, qkind, offsets, None, radius=float(radius))
-    assert st in (lbvh.OK, lbvh.ERR_CAPACITY), st
-    hits = torch.empty(max(int(total * 1.05) + 1024, 1), dtype=torch.int32, device=dev)
+    hits = None
+    if not knn:
+        st, total = tree.query_into(qpts, qkind, offsets, None, radius=float(radius))
+        assert st in (lbvh.OK, lbvh.ERR_CAPACITY), st
+        hits = torch.empty(max(int(total * 1.05) + 1024, 1), dtype=torch.int32, device=dev)
+    K = 16
 
     def step():
         tree.build(pts, kind, bits)
+        if knn:
+            tree.knn(qpts, K)
+            return nq * K
         s, tot = tree.query_into(qpts, qkind, offsets, hits, radius=float(radius))
         if s != lbvh.OK:
             raise lbvh.LbvhError(s, "lbvh_query_into")
@@ -482,17 +549,49 @@ def run_gpu(args, world, rank, local):
     query_ms = sum(v for k, v in stage_ms.items() if k.startswith("query"))
     dominant = max(stage_ms, key=lambda k: stage_ms[k])
     peak, peak_kind = measured_hbm_gbs()
-    lens = offsets[1:] - offsets[:-1]
-    long_mask = lens > 64  # the walk keeps 64 hits per query; longer lists walk again
-    long_lists = (int(long_mask.sum().item()), int(lens[long_mask].sum().item()))
+    long_lists = (0, 0)
+    if not knn:
+        lens = offsets[1:] - offsets[:-1]
+        long_mask = lens > 64  # the walk keeps 64 hits per query; longer lists walk again
+        long_lists = (int(long_mask.sum().item()), int(lens[long_mask].sum().item()))
     alg = {k: alg_bytes(k, n, nq, total_hits, boxes, box_queries, long_lists) for k in stage_ms
            if alg_bytes(k, n, nq, total_hits) is not None}
     achieved = alg[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
-    build_bytes = sum(v for k, v in alg.items() if not k.startswith("query"))
+    build_model = model_build_bytes(n, bits, boxes)
+    build_moved = moved_build_bytes(n, bits, boxes)
+
+    # ---- the walk's own roofline: node visits against the same walk on a
+    # tree small enough that every node load hits L1 (the ceiling of its
+    # dependent-load loop on this GPU)
+    walk = None
+    if qkind != lbvh.RAY and not knn and dominant == "query_walk":
+        lv, iv = tree.walk_visits(qpts, qkind, radius=float(radius))
+        visits_s = (lv + iv) / (stage_ms["query_walk"] * 1e-3)
+        small_n = 2048
+        sp = torch.from_numpy(inputs.uniform_points(small_n, seed=77)).to(dev)
+        sq = torch.from_numpy(inputs.uniform_points(1 << 24, seed=78)).to(dev)
+        st_ = lbvh.Tree()
+        st_.set_profiling(True)
+        st_.build(sp, lbvh.POINTS, bits)
+        soff = torch.empty((1 << 24) + 1, dtype=torch.int64, device=dev)
+        sr = float(inputs.radius_for_neighbours(small_n))
+        ms_small = []
+        for _ in range(4):
+            st_.query_into(sq, lbvh.SPHERE, soff, None, radius=sr)
+            ms_small.append(st_.stage_times()["query_walk"])
+        slv, siv = st_.walk_visits(sq, lbvh.SPHERE, radius=sr)
+        st_.close()
+        small_visits_s = (slv + siv) / (min(ms_small[1:]) * 1e-3)
+        walk = {"visits_per_query": (lv + iv) / nq, "leaf_visits_per_query": lv / nq,
+                "internal_visits_per_query": iv / nq, "visits_per_s": visits_s,
+                "node_bytes_per_s": (16 * lv + 32 * iv) / (stage_ms["query_walk"] * 1e-3),
+                "l1_resident_visits_per_s": small_visits_s, "l1_frac": visits_s / small_visits_s,
+                "l1_ceiling": f"the same walk (2^24 sphere queries, ~16 hits) on a {small_n}-point tree whose "
+                              "nodes all stay in L1"}
 
     # ---- end to end through the C ABI from host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not knn:
         host_pts = torch.from_numpy(prims_host).pin_memory()
         host_q = torch.from_numpy(queries_host).pin_memory()
         host_off = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
@@ -543,8 +642,13 @@ def run_gpu(args, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, sdesc, _ = oracle_sample(args.seed, bits=bits, family=workload_family(args.workload))
-        cpu = {"value": v / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sdesc}
+        # the reference arm's sample (same sizes and seeds), median of a few
+        got = [oracle_sample(args.seed + s, n_sample=min(ORACLE_N, n), q_sample=min(ORACLE_Q, n), bits=bits,
+                             family=workload_family(args.workload))
+               for s in range(CPU_BASELINE_SAMPLES)]
+        v = statistics.median(g[0] for g in got)
+        cpu = {"value": v / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"median of {CPU_BASELINE_SAMPLES} samples, each: " + got[0][1]}
 
     if rank == 0:
         line = {
@@ -556,14 +660,25 @@ def run_gpu(args, world, rank, local):
                        "l2": f"inputs larger than L2 (primitives {pts.numel() * 4 / 1e6:.0f} MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "long_lists": {"queries": long_lists[0], "hits": long_lists[1]},
+            "us_per_step": ms_step * 1e3,
+            "launches_per_step": launches / args.steps,
+            "tuning": {"sort_variant": tune_sort, "walk_variant": tune_walk,
+                       "how": "lbvh_tree_autotune on these inputs before the warm-up"},
             "build_mprims_s": n / (build_ms * 1e-3) / 1e6,
             "query_mqueries_s": nq / (query_ms * 1e-3) / 1e6,
-            "build_hbm_frac": build_bytes / (build_ms * 1e-3) / 1e9 / peak,
+            "build_ms": build_ms,
+            "build_hbm_frac": build_model / (build_ms * 1e-3) / 1e9 / peak,
+            "build_bytes_per_prim_model": build_model / n,
+            "build_hbm_frac_moved": build_moved / (build_ms * 1e-3) / 1e9 / peak,
+            "build_bytes_per_prim_moved": build_moved / n,
+            "walk": walk,
             "stage_ms": {k: round(v, 4) for k, v in sorted(stage_ms.items(), key=lambda kv: -kv[1])},
             "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                          "peak_source": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic_for(dominant),
-                         "algorithmic_bytes": alg[dominant]},
+                         "algorithmic_bytes": alg[dominant],
+                         **({"limiter": "L1: dependent node loads of the walk (see walk.l1_frac)",
+                             "l1_frac": walk["l1_frac"]} if walk else {})},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clock,

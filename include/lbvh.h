@@ -242,6 +242,14 @@ lbvh_status lbvh_query(lbvh_tree_t tree, const float *d_queries, int64_t nq, int
                        const float *d_radii, float radius, int64_t **d_offsets,
                        uint32_t **d_hits, uint64_t *total, lbvh_stream_t stream);
 
+/* Measurement: the number of leaves and internal nodes Algorithm 1 visits
+ * for these queries (the collecting walk's work), summed over all queries,
+ * walked in the same order as lbvh_query_into; no hits are kept. Arguments
+ * as lbvh_query_into. Synchronises `stream`. */
+lbvh_status lbvh_tree_walk_visits(lbvh_tree_t tree, const float *d_queries, int64_t nq, int qkind,
+                                  const float *d_radii, float radius, uint64_t *leaf_visits,
+                                  uint64_t *internal_visits, lbvh_stream_t stream);
+
 /* Largest k accepted by lbvh_knn. */
 #define LBVH_KNN_MAX_K 256
 

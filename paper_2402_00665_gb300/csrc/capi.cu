@@ -1197,6 +1197,30 @@ lbvh_status lbvh_query_into_host(lbvh_tree_t t, const float *d_queries, int64_t 
     return over ? LBVH_ERR_CAPACITY : LBVH_OK;
 }
 
+lbvh_status lbvh_tree_walk_visits(lbvh_tree_t t, const float *d_queries, int64_t nq, int qkind,
+                                  const float *d_radii, float radius, uint64_t *leaf_visits,
+                                  uint64_t *internal_visits, lbvh_stream_t stream) {
+    using namespace lbvh;
+    lbvh_status st = check_query_args(t, d_queries, nq, qkind, d_radii, radius);
+    if (st != LBVH_OK) return st;
+    if (!leaf_visits || !internal_visits) return LBVH_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LBVH_CUDA(cudaStreamWaitEvent(s, t->built, 0));
+    QueryArgs qa{d_queries, nq, qkind, d_radii, radius, nullptr};
+    if ((st = query_order(t, qa, s)) != LBVH_OK) return st;  // the same order as the collecting walk
+    DevBuf counts;
+    LBVH_CUDA(counts.ensure(16, s, true));
+    launch_visits(t->view(), qa, counts.as<unsigned long long>(), t->dctl(), s);
+    LBVH_LAUNCHED();
+    unsigned long long h[2] = {0, 0};
+    LBVH_CUDA(cudaMemcpyAsync(h, counts.p, 16, cudaMemcpyDeviceToHost, s));
+    LBVH_CUDA(cudaStreamSynchronize(s));
+    counts.release(s);
+    *leaf_visits = h[0];
+    *internal_visits = h[1];
+    return LBVH_OK;
+}
+
 lbvh_status lbvh_knn(lbvh_tree_t t, const float *d_queries, int64_t nq, int k, uint32_t *d_idx, float *d_dist2,
                      lbvh_stream_t stream) {
     NvtxRange nvtx_range("lbvh_knn");
@@ -1210,12 +1234,17 @@ lbvh_status lbvh_knn(lbvh_tree_t t, const float *d_queries, int64_t nq, int k, u
     Control *c = t->dctl();
     LBVH_CUDA(cudaMemsetAsync(&c->query_flags, 0, offsetof(Control, pad) - offsetof(Control, query_flags), s));
     QueryArgs qa{d_queries, nq, LBVH_Q_SPHERE, nullptr, 0.0f, nullptr};
+    t->prof.clear(LBVH_STAGE_QCOUNT, LBVH_STAGE_QORDER + 1);
+    t->prof.begin(LBVH_STAGE_QORDER, s);
     lbvh_status st = query_order(t, qa, s);  // the Morton order of the query points
+    t->prof.end(LBVH_STAGE_QORDER, s);
     if (st != LBVH_OK) return st;
     // a lean (server-resident) tree keeps no sorted codes: its walks start
     // without seeds, which is exact but slower
     const uint64_t *codes = t->lean ? nullptr : t->sorted_codes();
+    t->prof.begin(LBVH_STAGE_QCOUNT, s);  // the kNN walk is timed as the query walk
     launch_knn(t->view(), codes, t->bounds.as<float>(), t->bits, qa, k, d_idx, d_dist2, c, s);
+    t->prof.end(LBVH_STAGE_QCOUNT, s);
     LBVH_LAUNCHED();
     if (!t->used) LBVH_CUDA(cudaEventCreateWithFlags(&t->used, cudaEventDisableTiming));
     LBVH_CUDA(cudaEventRecord(t->used, s));

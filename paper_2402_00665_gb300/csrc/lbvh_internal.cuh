@@ -238,6 +238,9 @@ void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScra
 // codes: the tree's sorted codes (null: no seeding), bounds and bits of its
 // Morton grid. k <= kKnnMaxK.
 constexpr int kKnnMaxK = 256;
+// Node visits of Algorithm 1 for every query (counts[0] += leaves,
+// counts[1] += internal nodes; counts zeroed by the caller).
+void launch_visits(const TreeView &t, const QueryArgs &q, unsigned long long *counts, Control *ctl, cudaStream_t s);
 void launch_knn(const TreeView &t, const uint64_t *codes, const float *bounds, int bits, const QueryArgs &q, int k,
                 uint32_t *out_idx, float *out_d2, Control *ctl, cudaStream_t s);
 // offsets[0..nq] = exclusive scan of count_pos[.].x (offsets[nq] = total =

@@ -820,6 +820,44 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
+// ---- walk statistics
+
+// Algorithm 1 for every query, counting the leaves and internal nodes it
+// visits (no hits are kept): the walk's work per query, for measurement.
+template <int kQ, int kP>
+__global__ void __launch_bounds__(kThreads)
+    visits_kernel(TreeView t, QueryArgs qa, unsigned long long *counts, Control *ctl) {
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    uint32_t leaves = 0, internal = 0;
+    if (i < qa.nq && t.n > 0 && ctl->build_flags == 0) {
+        const auto q = QueryOf<kQ>::load(qa, thread_query(qa, i));
+        const int ni = (int)t.n - 1;
+        const int nodes = 2 * (int)t.n - 1;
+        const uint32_t max_steps = 2u * (uint32_t)nodes;
+        int node = 0;
+        while ((uint32_t)node < (uint32_t)nodes && leaves + internal < max_steps) {
+            const bool leaf = node >= ni;
+            const int unit = kP == LBVH_PRIM_BOXES ? 2 * node : (leaf ? node + ni : 2 * node);
+            float4 a, b;
+            load_node<kP>(t.inodes, unit, leaf, a, b);
+            const bool hit = hits(q, xyz(a), xyz(b));
+            const uint32_t word = __float_as_uint(a.w);
+            leaves += leaf;
+            internal += !leaf;
+            node = leaf ? node + 1 - ((word & kLeafSkipInternal) ? ni : 0) : __float_as_int(hit ? a.w : b.w);
+        }
+    }
+    // one add per warp
+    for (int off = 16; off > 0; off >>= 1) {
+        leaves += __shfl_xor_sync(0xffffffffu, leaves, off);
+        internal += __shfl_xor_sync(0xffffffffu, internal, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counts, (unsigned long long)leaves);
+        atomicAdd(counts + 1, (unsigned long long)internal);
+    }
+}
+
 // ---- k nearest neighbours
 
 // Max-heap of (squared distance bits << 32 | primitive index) keys in the
@@ -1057,6 +1095,15 @@ void launch_batch_overflow(const float4 *nodes, int kind, const BatchTables &bt,
     });
     count_launches(1);
     launch_sort_lists(qs, (uint64_t)q.nq, offsets, hits, capacity, ctl, s);
+}
+
+void launch_visits(const TreeView &t, const QueryArgs &q, unsigned long long *counts, Control *ctl, cudaStream_t s) {
+    if (q.nq <= 0) return;
+    const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
+    dispatch_kinds(q.qkind, t.kind, [&](auto qk, auto pk) {
+        visits_kernel<decltype(qk)::value, decltype(pk)::value><<<blocks, kThreads, 0, s>>>(t, q, counts, ctl);
+    });
+    count_launches(1);
 }
 
 void launch_knn(const TreeView &t, const uint64_t *codes, const float *bounds, int bits, const QueryArgs &q, int k,

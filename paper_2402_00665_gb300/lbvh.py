@@ -50,6 +50,7 @@ SIGNATURES = {
     "lbvh_query": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _P, _P]),
     "lbvh_free": (None, [_P]),
     "lbvh_knn": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
+    "lbvh_tree_walk_visits": (_I32, [_P, _P, _I64, _I32, _P, _F32, _P, _P, _P]),
     "lbvh_morton_codes": (_I32, [_P, _I64, _I32, _I32, _P, _P, _P]),
     "lbvh_sort_pairs": (_I32, [_P, _P, _I64, _I32, _P, _P, _P]),
     "lbvh_batch_create": (_I32, [_P]),
@@ -324,6 +325,17 @@ class Tree:
                                             _ptr(offsets), _ptr(hits), cap, ctypes.byref(total),
                                             _stream(stream))
         return st, total.value
+
+    def walk_visits(self, queries, qkind: int = SPHERE, radius: float = 0.0, radii=None, stream=None) -> tuple:
+        """lbvh_tree_walk_visits: (leaf visits, internal-node visits) of Algorithm 1 over these queries."""
+        torch = _torch()
+        q = _dev(queries, torch.float32, _QDIM[qkind])
+        r = None if radii is None else _dev(radii, torch.float32).reshape(-1)
+        lv, iv = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.lbvh_tree_walk_visits(self._h, _ptr(q), q.shape[0], qkind, _ptr(r), float(radius),
+                                               ctypes.byref(lv), ctypes.byref(iv), _stream(stream)),
+               "lbvh_tree_walk_visits")
+        return lv.value, iv.value
 
     def knn(self, queries, k: int, stream=None, distances: bool = True):
         """lbvh_knn: the k nearest primitives of each query point; returns

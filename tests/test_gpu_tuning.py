@@ -141,3 +141,33 @@ def test_autotune_fills_the_cache_and_the_cache_survives_a_file(tmp_path):
     assert lbvh.tune_entries() == 2
     lbvh.tune_clear()
     t.close()
+
+
+def test_walk_visits_counts_the_nodes_algorithm_1_visits():
+    """lbvh_tree_walk_visits against Algorithm 1 walked in Python over the
+    oracle's canonical arrays (leaves and internal nodes counted apart)."""
+    lbvh = L()
+    n = 3000
+    pts = inputs.uniform_points(n, seed=61)
+    q = inputs.uniform_points(400, seed=62)
+    r = 0.06
+    o = oracle.build(pts, oracle.POINTS, 30)
+    ni = n - 1
+    leaf_box, ibox = o["leaf_box"], o["internal_box"]
+    want_l = want_i = 0
+    r2 = np.float32(r) * np.float32(r)
+    for c in q:
+        node = 0
+        while node != -1:
+            leaf = node >= ni
+            box = leaf_box[node - ni] if leaf else ibox[node]
+            hit = oracle.sphere_box(c, r, box)
+            if leaf:
+                want_l += 1
+                node = o["skip_leaf"][node - ni]
+            else:
+                want_i += 1
+                node = o["left"][node] if hit else o["skip_internal"][node]
+    t = lbvh.Tree().build(pts, lbvh.POINTS, 30)
+    assert t.walk_visits(q, lbvh.SPHERE, radius=r) == (want_l, want_i)
+    t.close()
