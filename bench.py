@@ -134,6 +134,9 @@ SERVED_WORKLOADS = {
                             "60 GB HBM budget with LRU eviction; served with continuous batching vs "
                             "one-at-a-time processing of the same arrivals", 400, 2000.0, 1024, 4194304, 2, 63,
                             60 << 30),
+    "served_saturated_400": ("the 400 requests of served_poisson_2000 offered all at once (every arrival at "
+                             "t = 0): the load exceeds capacity, so both arms run at their highest sustained "
+                             "throughput", 400, float("inf"), 1024, 4194304, 2, 63, 60 << 30),
     "served_poisson_short": ("as served_poisson_2000 with 60 requests (short case)", 60, 2000.0, 1024, 4194304,
                              2, 63, 60 << 30),
     "served_poisson_2000_budget4gb": ("as served_poisson_2000 under a 4 GB HBM budget: the resident trees do not "
@@ -190,6 +193,8 @@ def parse():
                     help="e2e results into device arrays, then copied to host (instead of lbvh_query_into_host)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--server-slots", type=int, default=2,
+                    help="worker slots of the request server (served workloads): batches in flight at once")
     return ap.parse_args()
 
 
@@ -947,10 +952,25 @@ def mixture_radius(n: int, k: float = 16.0, components: int = 64, sigma: float =
     return float(np.float32((3.0 * k / (4.0 * math.pi * density)) ** (1.0 / 3.0)))
 
 
-# One worker slot with batches of up to 256 requests measured best on this
-# workload (throughput at the offered load, lowest p99); two slots of 64 were
-# within noise on throughput with a wider p99.
-SERVER_SLOTS = 1
+def span_overlap(spans):
+    """(busy s, overlap s) of device spans (rows slot, begin, end): the time
+    at least one job ran, and the time two or more ran at once."""
+    events = sorted([(float(b), 1) for _, b, _ in spans] + [(float(e), -1) for _, _, e in spans])
+    busy = overlap = 0.0
+    depth, last = 0, None
+    for t, d in events:
+        if last is not None:
+            if depth >= 1:
+                busy += t - last
+            if depth >= 2:
+                overlap += t - last
+        depth += d
+        last = t
+    return busy, overlap
+
+
+# Batches of up to 256 requests; the number of worker slots (batches in
+# flight at once) is --server-slots, 2 by default.
 SERVER_MAX_BATCH = 256
 
 
@@ -966,7 +986,11 @@ def run_served(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     desc, count, rate, lo, hi, seed, bits, budget = SERVED_WORKLOADS[args.workload]
-    arrivals, sizes, kinds = inputs.poisson_requests(count, rate, lo, hi, seed + rank)
+    saturated = math.isinf(rate)
+    # the saturated workload offers the nominal mix's requests all at once
+    arrivals, sizes, kinds = inputs.poisson_requests(count, 2000.0 if saturated else rate, lo, hi, seed + rank)
+    if saturated:
+        arrivals = np.zeros_like(arrivals)
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     host = np.empty((int(off[-1]), 3), np.float32)
     radii = np.empty(count, np.float32)
@@ -988,7 +1012,8 @@ def run_served(args, world, rank, local):
         return float(np.percentile(lat, 50) * 1e3), float(np.percentile(lat, 99) * 1e3)
 
     # ---- served: a submitter follows the arrival schedule
-    srv = lbvh.Server(budget, slots=SERVER_SLOTS, max_batch=SERVER_MAX_BATCH)
+    slots = args.server_slots
+    srv = lbvh.Server(budget, slots=slots, max_batch=SERVER_MAX_BATCH)
 
     def replay(keep: bool):
         """Submit the requests on their arrival schedule (a submitter thread)
@@ -1024,6 +1049,7 @@ def run_served(args, world, rank, local):
     # kept, so the server's buffers have the sizes of steady serving
     replay(keep=False)
     torch.cuda.synchronize()
+    spans0 = len(srv.device_spans())
     phases0 = srv.phase_seconds()
     batches0 = srv.stats()["batches"]
     launches0 = lbvh.kernel_launches()
@@ -1032,6 +1058,8 @@ def run_served(args, world, rank, local):
     launches = lbvh.kernel_launches() - launches0
     stats = srv.stats()
     phases = {k: v - phases0[k] for k, v in srv.phase_seconds().items()}
+    spans = srv.device_spans()[spans0:]
+    busy_s, overlap_s = span_overlap(spans)
     server_latency = srv.latency()  # the server's own record (includes the warm-up replay)
     srv.close()
     served_p50, served_p99 = percentiles(lat)
@@ -1071,11 +1099,18 @@ def run_served(args, world, rank, local):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "requests": count, "rate_per_s": rate,
                        "n_total": n, "morton_bits": bits, "budget_bytes": budget,
-                       "offered_mprims_s": n / float(arrivals[-1]) / 1e6,
+                       "offered_mprims_s": None if saturated else n / float(arrivals[-1]) / 1e6,
+                       "arrivals": "all at t = 0" if saturated else f"Poisson, {rate:g} per s",
                        "mean_hits": totals / n, "parallelism": "replicas" if world > 1 else "single"},
             "served": {"throughput_mprims_s": value, "p50_ms": served_p50, "p99_ms": served_p99,
                        "wall_s": served_s, "mean_batch": float(np.mean(batch_sizes)),
-                       "batches": stats["batches"] - batches0, "slots": SERVER_SLOTS,
+                       "batches": stats["batches"] - batches0, "slots": slots,
+                       "device": {"jobs": int(len(spans)), "busy_s": busy_s, "overlap_s": overlap_s,
+                                  "overlap_frac": overlap_s / busy_s if busy_s > 0 else 0.0,
+                                  "jobs_per_slot": [int((spans[:, 0] == s).sum()) for s in range(slots)],
+                                  "how": "CUDA events around each batch on its slot's stream, against one "
+                                         "reference event; overlap = device time with two or more batches "
+                                         "in flight"},
                        "max_batch": SERVER_MAX_BATCH, "resident_trees": stats["resident_trees"],
                        "resident_bytes": stats["resident_bytes"], "evictions": stats["evictions"],
                        "worker_phase_s": phases,

