@@ -175,6 +175,7 @@ WORKLOADS = {
     "knn_uniform_2^25_63bit": ("2^25 FP32 points uniform in [0,1)^3, 63-bit Morton codes; build + the 16 "
                                "nearest neighbours of every point (lbvh_knn: Algorithm 1 with a shrinking ball)",
                                1 << 25, 63, "knn"),
+    "knn_uniform_2^24_63bit": ("as knn_uniform_2^25_63bit with 2^24 points (profiling case)", 1 << 24, 63, "knn"),
     "mixture_boxes_2^23_63bit": ("as mixture_boxes_2^25_63bit with 2^23 boxes and 2^22 queries (profiling case)",
                                  1 << 23, 63, "mixture_boxes"),
 }

@@ -34,7 +34,7 @@
 //     is visible before its half of the parent is, and the second thread
 //     reads the sibling's box only after it has seen that half.
 //   - two phases (construct_block_kernel): splits whose two children both
-//     lie inside one group of consecutive leaves (128 by default) meet in
+//     lie inside one group of consecutive leaves (256) meet in
 //     shared memory (block-scope exchange, sibling box from shared memory);
 //     only the nodes spanning a group's edge meet in the device-scope
 //     `store` words (sibling box through L2, ld.global.cg). Batches group
@@ -257,10 +257,11 @@ __device__ __forceinline__ void climb_global(Climb c, int n, float4 *inodes, con
 // that spans the group's edge, and that thread, like one stopped at the edge,
 // continues with the device-scope exchanges of climb_global. Each node is
 // still written once, by the second thread up at its split, with the same
-// fields: only where the two halves meet changes. Groups of 128 measured
-// fastest at 2^25 points (32: 2.67 ms, 64: 2.08, 128: 2.06, 256: 2.20, 512:
-// 2.44; every exchange at device scope: 2.32).
-constexpr int kGroup = 128;
+// fields: only where the two halves meet changes. Group size, with the
+// climbs that leave a group handed to a second kernel (construct time at 2^25
+// points, 63-bit codes): 64 leaves 1.83 ms (8 hand-off slots 1.67), 128
+// 1.64, 256 1.56 (16 slots; 12: 1.57; 8: 1.55; 32: 1.67), 512 1.57.
+constexpr int kGroup = 256;
 
 struct GroupSmem {
     unsigned long long word[kGroup];    // split at global position a + j: word[j]
@@ -274,9 +275,9 @@ struct GroupSmem {
 // climb_pending_kernel through its own slots (16 bytes each: l, r, the three
 // delta* values and a valid bit), so that no CTA waits on device-scope
 // exchanges with most of its threads done. On uniform points a group of 128
-// leaves has 7.3 such climbs on average and 13 at most; more than kPendSlots
-// climb in place.
-constexpr int kPendSlots = 16;
+// leaves has 7.3 such climbs on average and 13 at most (one more level of
+// the tree per doubling of the group); more than kPendSlots climb in place.
+constexpr int kPendSlots = 12;
 constexpr uint32_t kPendValid = 1u << 31;
 
 // Both phases for thread t, holding leaf i's climb state c (go: the leaf was

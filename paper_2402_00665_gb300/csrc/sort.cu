@@ -82,20 +82,31 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t sel) {
     return __byte_perm(kHi ? (uint32_t)(k >> 32) : (uint32_t)k, 0u, sel);
 }
 
-// Exclusive scan of one value per thread over the 256 threads of the block.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp) {
+// Exclusive scans of two values per thread over the 256 threads of the
+// block at once (one pair of barriers for both).
+__device__ __forceinline__ void block_exclusive_scan2(uint32_t v0, uint32_t v1, uint2 *s_warp, uint32_t &e0,
+                                                      uint32_t &e1) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
+    uint32_t x0 = v0, x1 = v1;
     for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
+        const uint32_t y0 = __shfl_up_sync(0xffffffffu, x0, off);
+        const uint32_t y1 = __shfl_up_sync(0xffffffffu, x1, off);
+        if (lane >= off) {
+            x0 += y0;
+            x1 += y1;
+        }
     }
-    if (lane == 31) s_warp[warp] = x;
+    if (lane == 31) s_warp[warp] = make_uint2(x0, x1);
     __syncthreads();
-    uint32_t before = 0;
-    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    uint32_t b0 = 0, b1 = 0;
+    for (int w = 0; w < warp; ++w) {
+        const uint2 s = s_warp[w];
+        b0 += s.x;
+        b1 += s.y;
+    }
     __syncthreads();
-    return before + x - v;
+    e0 = b0 + x0 - v0;
+    e1 = b1 + x1 - v1;
 }
 
 template <int kItems, bool kVals, bool kTable>
@@ -105,7 +116,7 @@ struct SortSmem {
     uint32_t peer_mask[kTable ? kWarps : 1][kRadix];  // table ranking: lanes of the round holding each digit (zero between rounds)
     int32_t out_base[kRadix];            // global position of the digit's first staged key, minus its tile start
     uint32_t tile_start[kRadix];         // first staged slot of each digit
-    uint32_t scan[kWarps];
+    uint2 scan[kWarps];
     uint32_t tile;
     int32_t seg;                         // segment of the tile (segmented sorts)
     uint32_t next_hist[kRadix];          // digit counts of the next pass
@@ -287,8 +298,9 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(cons
     const bool publish = tile != a.hold_tile;  // a test hook: this tile's successors must time out
     if (publish) st_relaxed(my_word, (tile == first_tile ? kStatePrefix : kStateAgg) | count);
 
-    const uint32_t global_base = (uint32_t)seg_begin + block_exclusive_scan(pass_hist[d], sm.scan);
-    const uint32_t start = block_exclusive_scan(count, sm.scan);
+    uint32_t hist_before, start;
+    block_exclusive_scan2(pass_hist[d], count, sm.scan, hist_before, start);
+    const uint32_t global_base = (uint32_t)seg_begin + hist_before;
     sm.tile_start[d] = start;
 
     // ---- decoupled look-back over earlier tiles for digit d
