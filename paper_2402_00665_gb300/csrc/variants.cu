@@ -89,6 +89,18 @@ __device__ __forceinline__ void read_leaf_box(const float4 *leaves, int k, float
     }
 }
 
+// The same union with the ordered minimum and maximum written as comparisons
+// (identical results for finite values). The Karras box pass runs at 2.83 ms
+// with it against 5.17 ms with grow() (2^25 points; the climb's loads and
+// its acq_rel counter are scheduled differently), while Algorithm 3's climb
+// is faster with grow() (4.0 against 6.1 ms).
+__device__ __forceinline__ float min_cmp(float a, float b) { return (a < b || (a == b && __float_as_int(a) < 0)) ? a : b; }
+__device__ __forceinline__ float max_cmp(float a, float b) { return (a > b || (a == b && __float_as_int(a) >= 0)) ? a : b; }
+__device__ __forceinline__ void grow_cmp(float3 &lo, float3 &hi, float3 slo, float3 shi) {
+    lo = make_float3(min_cmp(lo.x, slo.x), min_cmp(lo.y, slo.y), min_cmp(lo.z, slo.z));
+    hi = make_float3(max_cmp(hi.x, shi.x), max_cmp(hi.y, shi.y), max_cmp(hi.z, shi.z));
+}
+
 __device__ __forceinline__ void grow(float3 &lo, float3 &hi, float3 slo, float3 shi) {
     lo = make_float3(min_ordered(lo.x, slo.x), min_ordered(lo.y, slo.y), min_ordered(lo.z, slo.z));
     hi = make_float3(max_ordered(hi.x, shi.x), max_ordered(hi.y, shi.y), max_ordered(hi.z, shi.z));
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(kThreads)
             slo = make_float3(a.x, a.y, a.z);
             shi = make_float3(b.x, b.y, b.z);
         }
-        grow(lo, hi, slo, shi);
+        grow_cmp(lo, hi, slo, shi);
         inodes[2 * (int64_t)p] = make_float4(lo.x, lo.y, lo.z, __int_as_float(lc));
         inodes[2 * (int64_t)p + 1] = make_float4(hi.x, hi.y, hi.z, __int_as_float(skip[p]));
         if (p == 0) return;
