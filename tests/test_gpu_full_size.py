@@ -106,3 +106,20 @@ def test_full_uniform_points_knn_2pow25():
     assert np.array_equal(gd[sample].view(np.uint32), wd.view(np.uint32))
     assert (gi[:, 0] == np.arange(N, dtype=np.uint32)).all() and (gd[:, 0] == 0).all()
     assert (np.diff(gd, axis=1) >= 0).all()
+
+
+@pytest.mark.parametrize("bits", [63, 30])
+def test_full_mixture_boxes_knn_2pow25(bits):
+    """k nearest boxes (k = 1, 16, 64) in the full 2^25-box D3 tree for 64
+    query points at D3 query-box centres, against the oracle's brute force."""
+    from paper_2402_00665_gb300 import lbvh
+    boxes = inputs.gaussian_mixture_boxes(N, seed=0)
+    qb = inputs.gaussian_mixture_boxes(64, seed=1, component_seed=0)
+    q = (qb[:, :3] + qb[:, 3:]) * np.float32(0.5)
+    t = lbvh.Tree().build(torch.from_numpy(boxes).cuda(), lbvh.BOXES, bits)
+    t.check()
+    wi, wd = oracle.knn(boxes, oracle.BOXES, q, 64)
+    for k in (1, 16, 64):
+        idx, d2 = t.knn(q, k)
+        assert np.array_equal(idx.cpu().numpy().view(np.uint32), wi[:, :k]), k
+        assert np.array_equal(d2.cpu().numpy().view(np.uint32), wd[:, :k].view(np.uint32)), k
