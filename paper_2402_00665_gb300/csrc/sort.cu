@@ -423,14 +423,27 @@ size_t pass_smem(const Variant &v, int kind) {
     return (kind == kPackedPacked || kind == kPackedLow) ? v.smem_packed : v.smem_kv;
 }
 
-// Tile shapes the library is compiled with (keys per thread, CTAs per SM).
-// The first entry is the default; the autotuner may pick another.
+// Tile shapes the library is compiled with (keys per thread, CTAs per SM,
+// digit peers by table or ballots). The first entry is the default; the
+// autotuner may pick another.
 const Variant *variant_table(int *count) {
+    // Sort passes at 2^25 (ms for the 8 passes of 63-bit uniform points /
+    // mixture boxes at 63 bits / the 4 passes at 30 bits; keys per thread x
+    // CTAs per SM, digit peers by table or ballots): 24 x 2 table 2.10 /
+    // 2.14 / 1.00; 28 x 2 table 2.11 / 2.15 / 0.98; 20 x 2 table 2.17 / 2.21
+    // / 1.05; 16 x 3 table 2.17 / 2.21 / 1.03; 12 x 4 table 2.25 / 2.28 /
+    // 1.07; 32 x 2 table 2.37 / 2.42 / 1.00; 10 x 5 table 2.38 / 2.41 /
+    // 1.09; 12 x 4 ballots 2.39 / 2.34 / 1.08; 16 x 3 ballots 2.42 / 2.37 /
+    // 1.06; 8 x 6 ballots 2.50 / 2.46 / 1.15; 8 x 6 table 2.50 / 2.53 /
+    // 1.16. Larger tiles mean fewer tiles, look-back chains and barriers per
+    // key; past 28 keys the key + payload passes spill.
     static const Variant table[] = {
-        make_variant<12, 4, false>(),
+        make_variant<24, 2, true>(),
+        make_variant<28, 2, true>(),
+        make_variant<16, 3, true>(),
         make_variant<12, 4, true>(),
+        make_variant<12, 4, false>(),
         make_variant<16, 3, false>(),
-        make_variant<8, 6, false>(),
     };
     // kernel attributes set once, thread-safely (function-local static initialisation)
     static const bool configured = [] {
