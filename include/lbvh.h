@@ -516,7 +516,9 @@ enum {
     LBVH_STAGE_QFIXUP = 14,    /* second walk + sort for lists longer than 32 */
     LBVH_STAGE_QORDER = 15,    /* Morton order of the query centres (encode + sort) */
     LBVH_STAGE_SECOND = 16,    /* second pass of lbvh_build_variant's Karras / Apetrei builds */
-    LBVH_STAGE_COUNT = 17
+    LBVH_STAGE_SORTRUNS = 17,  /* codes wider than 30 bits: the sort passes cover the codes' top bits
+                                  beside the index; this stage orders the runs of equal top bits */
+    LBVH_STAGE_COUNT = 18
 };
 
 /* Turn per-stage timing of this tree's builds and queries on or off (off by

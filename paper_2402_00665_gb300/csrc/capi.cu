@@ -351,11 +351,11 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
     LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)sort_passes(order_bits()) * kRadix * 4, s));
     const int as_prims = qa.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
     launch_encode(qa.queries, qa.nq, as_prims, order_bits(), t->bounds.as<float>(), t->qkeys[0].as<uint64_t>(),
-                  t->hist.as<uint32_t>(), 1, true, s);
+                  t->hist.as<uint32_t>(), 1, kCodeLow, 0, s);
     LBVH_LAUNCHED();
     SortScratch scratch{t->hist.as<uint32_t>(), t->qlookback.as<uint32_t>(), sort_tiles_max(qa.nq) * kRadix};
     qa.order = run_index_sort(t->qkeys[0].as<uint64_t>(), t->qkeys[1].as<uint64_t>(), t->qvals[0].as<uint32_t>(),
-                              t->qvals[1].as<uint32_t>(), qa.nq, order_bits(), true, scratch, t->dctl(), s);
+                              qa.nq, order_bits(), scratch, t->dctl(), s);
     LBVH_LAUNCHED();
     return LBVH_OK;
 }
@@ -788,30 +788,43 @@ lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
     }
     t->prof.clear(0, LBVH_STAGE_QCOUNT);
     t->prof.clear(LBVH_STAGE_SECOND, LBVH_STAGE_SECOND + 1);
+    t->prof.clear(LBVH_STAGE_SORTRUNS, LBVH_STAGE_SORTRUNS + 1);
     if (n > 0) {
         const int passes = sort_passes(morton_bits);
-        LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)passes * kRadix * 4, s));
+        LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)kMaxPasses * kRadix * 4, s));
         t->prof.begin(LBVH_STAGE_BOUNDS, s);
         launch_bounds(d_prims, n, kind, t->partials.as<float>(), t->bounds.as<float>(), c, s);
         t->prof.end(LBVH_STAGE_BOUNDS, s);
         LBVH_LAUNCHED();
         t->prof.begin(LBVH_STAGE_ENCODE, s);
         // codes of at most 30 bits are packed with the index from the start
+        // (code << 32 | index); wider codes give their top bits (top << ib |
+        // index) to run_code_sort
         const bool packed = morton_bits <= 30;
+        const int ib = top_index_bits(n);
         launch_encode(d_prims, n, kind, morton_bits, t->bounds.as<float>(), t->keys[0].as<uint64_t>(),
-                      t->hist.as<uint32_t>(), 1, packed, s);
+                      t->hist.as<uint32_t>(), 1, packed ? kCodeLow : kCodeTop, ib, s);
         t->prof.end(LBVH_STAGE_ENCODE, s);
         LBVH_LAUNCHED();
         SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles_max(n) * kRadix};
         nvtxRangePushA("sort");
         const int variant = t->sort_choice >= 0 ? t->sort_choice : tune_sort_choice(n, morton_bits, kind, 1);
-        const uint32_t *perm = run_index_sort(t->keys[0].as<uint64_t>(), t->keys[1].as<uint64_t>(),
-                                              t->vals[0].as<uint32_t>(), t->vals[1].as<uint32_t>(), n, morton_bits,
-                                              packed, scratch, c, s,
-                                              t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr, variant);
+        cudaEvent_t(*pass_events)[2] = t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr;
+        // the node records are written by the construct only: until then they
+        // hold run_code_sort's 2n scratch words
+        const uint32_t *perm =
+            packed ? run_index_sort(t->keys[0].as<uint64_t>(), t->keys[1].as<uint64_t>(), t->vals[0].as<uint32_t>(),
+                                    n, morton_bits, scratch, c, s, pass_events, variant)
+                   : run_code_sort(d_prims, kind, morton_bits, t->bounds.as<float>(), n, t->keys[0].as<uint64_t>(),
+                                   t->keys[1].as<uint64_t>(), t->vals[0].as<uint32_t>(), t->vals[1].as<uint32_t>(),
+                                   t->nodes.as<uint32_t>(), scratch, c, s, pass_events,
+                                   t->prof.on ? t->prof.ev[LBVH_STAGE_SORTRUNS] : nullptr, variant);
         nvtxRangePop();
-        if (t->prof.on)
-            for (int p = 0; p < passes; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
+        if (t->prof.on) {
+            const int sorted = packed ? passes : kMaxPasses - ib / kRadixBits;
+            for (int p = 0; p < sorted; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
+            if (!packed) t->prof.recorded[LBVH_STAGE_SORTRUNS] = true;
+        }
         LBVH_LAUNCHED();
         // the sort leaves the permutation alone; the sorted codes go to keys[0]
         t->perm_in = perm == t->vals[1].as<uint32_t>() ? 1 : 0;
@@ -1317,7 +1330,7 @@ lbvh_status lbvh_morton_codes(const float *d_prims, int64_t n, int kind, int mor
     if (e == cudaSuccess) e = hist.ensure((size_t)kMaxPasses * kRadix * 4, s);
     if (e == cudaSuccess) {
         launch_bounds(d_prims, n, kind, partials.as<float>(), d_bounds, ctl.as<Control>(), s);
-        launch_encode(d_prims, n, kind, morton_bits, d_bounds, d_codes, hist.as<uint32_t>(), 0, false, s);
+        launch_encode(d_prims, n, kind, morton_bits, d_bounds, d_codes, hist.as<uint32_t>(), 0, kCodePlain, 0, s);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, ctl.p, sizeof h, cudaMemcpyDeviceToHost, s);
@@ -1744,7 +1757,7 @@ const char *lbvh_stage_name(int stage) {
     static const char *names[LBVH_STAGE_COUNT] = {
         "bounds", "encode", "sort_pass0", "sort_pass1", "sort_pass2", "sort_pass3", "sort_pass4",
         "sort_pass5", "sort_pass6", "sort_pass7", "construct", "query_walk", "query_scan",
-        "query_copy", "query_overflow", "query_order", "build_second_pass"};
+        "query_copy", "query_overflow", "query_order", "build_second_pass", "sort_runs"};
     return (stage >= 0 && stage < LBVH_STAGE_COUNT) ? names[stage] : "";
 }
 

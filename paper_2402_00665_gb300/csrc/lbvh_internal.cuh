@@ -35,7 +35,10 @@ struct Control {
     unsigned long long total;      // total hits of the last query
     uint32_t overflow_big;         // overflow lists too long for one warp's sort
     uint32_t spill_used;           // spill chunks handed out by the walk
-    uint32_t pad[6];
+    uint32_t run_long;             // run_code_sort: runs listed for a CTA each,
+    uint32_t run_fallback;         //   a run too long for one CTA was met,
+    uint32_t run_sort_count;       //   elements of the fallback sort (in this order)
+    uint32_t pad[3];
 };
 constexpr int kQueryBufferHits = 64;  // hits kept per query by the walk
 
@@ -100,6 +103,10 @@ struct SortScratch {
 // must be zero.
 void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_t *hist,
                             cudaStream_t s);
+// The first pass's digit counts of the first *count keys (count on the
+// device, at most n_max).
+void launch_digit_histogram_counted(const uint64_t *keys, int64_t n_max, const uint32_t *count, uint32_t *hist,
+                                    cudaStream_t s);
 
 // Independent segments sorted in one pass sequence: segment b is keys
 // [off[b], off[b+1]) and is sorted on its own (tiles never straddle two
@@ -131,16 +138,47 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
                   uint32_t *vals_b, int64_t n, int passes, const SortScratch &scratch,
                   Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
                   int variant_idx = -1, const SortSegments *seg = nullptr);
-// The sort of a tree build, which needs only the permutation: keys_a holds
-// the codes (packed: words code << 32 | index, codes of at most 32 bits),
-// vals_a/vals_b/keys_b are scratch. Passes run as described in sort.cu
-// (packed words once the low four bytes are sorted, payloads alone out of
-// the last pass). Returns the buffer (vals_a or vals_b) holding the sorted
-// permutation; keys_a and keys_b are free again afterwards. hist and the
-// look-back are used as by run_onesweep.
-uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, int64_t n,
-                         int key_bits, bool packed, const SortScratch &scratch, Control *ctl, cudaStream_t s,
+// The sort of codes of at most 32 bits when only the permutation is needed
+// (a 30-bit build, the query order): keys_a holds words code << 32 | index;
+// passes sort bytes 4, 5, ... in packed 8-byte words, and the last one
+// writes the indices alone to vals_out, which is returned. keys_a and keys_b
+// are free again afterwards. hist and the look-back are used as by
+// run_onesweep.
+uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_out, int64_t n, int key_bits,
+                         const SortScratch &scratch, Control *ctl, cudaStream_t s,
                          cudaEvent_t (*pass_events)[2] = nullptr, int variant_idx = -1);
+// The sort of a build's codes of more than 32 bits, first step: keys_a
+// holds words (code >> (index_bits - 1)) << index_bits | index (the code's
+// top 64 - index_bits bits above the index, n <= 2^index_bits), sorted on
+// bytes index_bits / 8 .. 7 (the index bits inside the lowest of them only
+// follow the index order the words are already in). Returns the buffer
+// holding the sorted words; the other one is free. hist[0..256) must hold
+// the first pass's digit counts and the rest of hist must be zero.
+uint64_t *run_top_sort(uint64_t *keys_a, uint64_t *keys_b, int64_t n, int index_bits, const SortScratch &scratch,
+                       Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
+                       int variant_idx = -1);
+// The whole sort of a build's codes of more than 32 bits (runs.cu): keys_a
+// holds the encoder's kCodeTop words (index bits top_index_bits(n)); the
+// top bits are sorted by run_top_sort, then the runs of equal top bits are
+// put in code order (their codes derived again from prims with the scene
+// bounds and bits / 3 bits per axis). Returns vals_a, which then holds the
+// permutation; keys_a, keys_b, vals_b and scratch (2n words) are used on the
+// way. The hist, look-back and control words as for the other sorts.
+// scratch: code_sort_scratch_words(n) words.
+// runs_events (nullable): an event pair around the second step.
+int64_t code_sort_scratch_words(int64_t n);
+uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bounds, int64_t n, uint64_t *keys_a,
+                        uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, uint32_t *scratch,
+                        const SortScratch &sc, Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2],
+                        cudaEvent_t *runs_events, int variant_idx);
+// A key + payload sort of the first *count (device) pairs, at most n_max,
+// over the low key_bits bits: a fixed grid of CTAs per pass takes tiles by
+// ticket up to the count it reads on the device. hist and the look-back as
+// for run_onesweep (the look-back regions hold sort_tiles_max(n_max) * kRadix
+// words). Returns true if the result ended in the *_b buffers.
+bool run_counted_sort(uint64_t *keys_a, uint32_t *vals_a, uint64_t *keys_b, uint32_t *vals_b,
+                      const uint32_t *count, int64_t n_max, int key_bits, const SortScratch &scratch, Control *ctl,
+                      cudaStream_t s);
 int sort_variant_count();
 // Test hook (lbvh_test_hold_sort_tile): tile `tile` of every sort's first pass
 // publishes nothing, so later tiles' bounded look-back waits run out; -1: off.
@@ -156,9 +194,19 @@ inline int64_t sort_tiles_max(int64_t n) { return (n + sort_tile_keys_min() - 1)
 int bounds_blocks(int64_t n);
 void launch_bounds(const float *prims, int64_t n, int kind, float *partials, float *bounds,
                    Control *ctl, cudaStream_t s);
-// packed: codes[i] = code << 32 | i (bits <= 30), for run_index_sort's packed mode.
+// What the encoder writes per primitive i: the code; code << 32 | i (codes
+// of at most 32 bits, run_index_sort's packed mode); or the top bits
+// (code >> (ib - 1)) << ib | i for run_top_sort, ib = index_bits with
+// n <= 2^ib (index_bits is read for kCodeTop only).
+enum CodeLayout : int { kCodePlain = 0, kCodeLow = 1, kCodeTop = 2 };
+// Index bits of the top layout for n primitives: ceil(log2 n), at least 1.
+inline int top_index_bits(int64_t n) {
+    int ib = 1;
+    while (ib < 62 && (int64_t(1) << ib) < n) ++ib;
+    return ib;
+}
 void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint64_t *codes, uint32_t *hist, int hist_passes, bool packed, cudaStream_t s);
+                   uint64_t *codes, uint32_t *hist, int hist_passes, int layout, int index_bits, cudaStream_t s);
 // codes[i] = the Morton code of primitive perm[i].
 void launch_sorted_codes(const float *prims, const uint32_t *perm, int64_t n, int kind, int bits,
                          const float *bounds, uint64_t *codes, cudaStream_t s);

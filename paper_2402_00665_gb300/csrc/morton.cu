@@ -166,23 +166,30 @@ __global__ void __launch_bounds__(kThreads)
     }
 }
 
-// kPacked: each word is code << 32 | index (codes of at most 32 bits, for a
-// sort that carries the index in the key's low half); else the code alone.
-// The histograms count the bytes of the code.
-template <int kKind, bool kPacked>
+// kLayout (CodeLayout): kCodePlain writes the code alone; kCodeLow the word
+// code << 32 | index (codes of at most 32 bits, for a sort that carries the
+// index in the key's low half); kCodeTop the word (code >> (ib - 1)) << ib |
+// index (the code's top 64 - ib bits above the index, n <= 2^ib). The
+// histograms count the bytes of the code (plain, low) or of the word from
+// byte ib / 8 on (top): the bytes the sort's passes take in turn.
+template <int kKind, int kLayout>
 __global__ void __launch_bounds__(kThreads)
-    encode_kernel(const float *__restrict__ prims, int64_t n, int b,
-                  const float *__restrict__ bounds, uint64_t *__restrict__ codes,
-                  uint32_t *__restrict__ hist, int passes) {
+    encode_kernel(const float *__restrict__ prims, int64_t n, int b, const float *__restrict__ bounds,
+                  uint64_t *__restrict__ codes, uint32_t *__restrict__ hist, int passes, int ib) {
     __shared__ uint32_t s_hist[kMaxPasses * kRadix];
     for (int k = threadIdx.x; k < passes * kRadix; k += kThreads) s_hist[k] = 0;
     const Grid3 g = make_grid(bounds, b);
+    const int hist_shift = kLayout == kCodeTop ? kRadixBits * (ib / kRadixBits) : 0;
     __syncthreads();
     for_each_centroid<kKind>(prims, n, [&](int64_t i, float x, float y, float z) {
         const uint64_t c = morton(x, y, z, g);
-        codes[i] = kPacked ? (c << 32) | (uint64_t)(uint32_t)i : c;
+        const uint64_t w = kLayout == kCodeTop   ? ((c >> (ib - 1)) << ib) | (uint64_t)(uint32_t)i
+                           : kLayout == kCodeLow ? (c << 32) | (uint64_t)(uint32_t)i
+                                                 : c;
+        codes[i] = w;
+        const uint64_t h = kLayout == kCodeTop ? w >> hist_shift : c;
         for (int p = 0; p < passes; ++p)
-            atomicAdd(&s_hist[p * kRadix + (uint32_t)((c >> (kRadixBits * p)) & (kRadix - 1))], 1u);
+            atomicAdd(&s_hist[p * kRadix + (uint32_t)((h >> (kRadixBits * p)) & (kRadix - 1))], 1u);
     });
     __syncthreads();
     for (int k = threadIdx.x; k < passes * kRadix; k += kThreads) {
@@ -360,14 +367,17 @@ void launch_bounds(const float *prims, int64_t n, int kind, float *partials, flo
 }
 
 void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint64_t *codes, uint32_t *hist, int hist_passes, bool packed, cudaStream_t s) {
+                   uint64_t *codes, uint32_t *hist, int hist_passes, int layout, int index_bits, cudaStream_t s) {
     const int blocks = bounds_blocks(n);
     const int b = bits / 3;
-    auto k = kind == LBVH_PRIM_POINTS ? (packed ? encode_kernel<LBVH_PRIM_POINTS, true>
-                                               : encode_kernel<LBVH_PRIM_POINTS, false>)
-                                      : (packed ? encode_kernel<LBVH_PRIM_BOXES, true>
-                                                : encode_kernel<LBVH_PRIM_BOXES, false>);
-    k<<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist, hist_passes);
+    using Kernel = void (*)(const float *, int64_t, int, const float *, uint64_t *, uint32_t *, int, int);
+    static const Kernel table[2][3] = {
+        {encode_kernel<LBVH_PRIM_POINTS, kCodePlain>, encode_kernel<LBVH_PRIM_POINTS, kCodeLow>,
+         encode_kernel<LBVH_PRIM_POINTS, kCodeTop>},
+        {encode_kernel<LBVH_PRIM_BOXES, kCodePlain>, encode_kernel<LBVH_PRIM_BOXES, kCodeLow>,
+         encode_kernel<LBVH_PRIM_BOXES, kCodeTop>}};
+    table[kind == LBVH_PRIM_POINTS ? 0 : 1][layout]<<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
+                                                                               hist_passes, index_bits);
     count_launches(1);
 }
 

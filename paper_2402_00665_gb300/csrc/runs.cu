@@ -1,0 +1,310 @@
+// runs.cu -- the sort of a build's Morton codes wider than 32 bits
+// (Sec. 3.1, Karras step 2), in two steps.
+//
+// 1. run_top_sort (sort.cu) sorts words top << ib | index, where
+//    ib = ceil(log2 n) and top = code >> (ib - 1) holds all of the code but
+//    its low ib - 1 bits: 64 - ib key bits travel in one 8-byte word with the
+//    index, so every pass moves 8 bytes each way, and the passes cover the
+//    key bits only (5 passes at n = 2^25 and 63-bit codes, against 8 passes
+//    over the whole code). The words come out in (top, index) order.
+// 2. Words whose top is shared with a neighbour ("members": the runs of equal
+//    top, each over consecutive positions) are not yet in code order. Runs
+//    are disjoint, so each is put in order on its own: the full codes of its
+//    elements are derived again from their primitives, and inside a run the
+//    order by (code, index) is the order of the 64-bit keys
+//    (code's low ib - 1 bits) << ib | index, all distinct.
+//
+// Uniform points at n = 2^25 with 63-bit codes have about 2,000 members in
+// runs of 2 or 3; the Gaussian-mixture boxes 16% in runs of 2 to 7; equal
+// codes make long runs.
+//
+//   runs_kernel      one pass over the sorted words: perm[j] = the index in
+//                    word j for every position outside a run; each run
+//                    element's in-run key; the thread that holds a run's
+//                    first position sorts a run of at most kShortRun
+//                    elements in place, and lists a longer one.
+//   long_runs_kernel a CTA per listed run: up to kLongRun elements sorted in
+//                    shared memory; a longer run raises the fallback.
+//   fallback         only after a run longer than kLongRun (all kernels read
+//                    the decision on the device and leave at once otherwise):
+//                    the full codes of all elements with their indices, a
+//                    stable key + payload sort of them (run_counted_sort),
+//                    and the permutation copied out.
+#include "lbvh_internal.cuh"
+#include "morton.cuh"
+
+namespace lbvh {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPer = 8;          // consecutive positions per thread
+constexpr int kShortRun = 16;    // runs sorted by one thread
+constexpr int kLongRun = 4096;   // runs sorted by one CTA in shared memory
+
+template <int kKind>
+__device__ __forceinline__ uint64_t code_of(const float *prims, uint32_t i, const Grid3 &g) {
+    float x, y, z;
+    if (kKind == LBVH_PRIM_POINTS) {
+        x = prims[3 * (int64_t)i];
+        y = prims[3 * (int64_t)i + 1];
+        z = prims[3 * (int64_t)i + 2];
+    } else {
+        box_centroid(prims + 6 * (int64_t)i, x, y, z);
+    }
+    return morton(x, y, z, g);
+}
+
+// The in-run key of the primitive with index idx: its code's low ib - 1 bits
+// above the index.
+template <int kKind>
+__device__ __forceinline__ uint64_t run_key(const float *prims, uint32_t idx, const Grid3 &g, int ib) {
+    const uint64_t low = code_of<kKind>(prims, idx, g) & ((1ull << (ib - 1)) - 1ull);
+    return low << ib | idx;
+}
+
+// A CTA covers kThreads * kPer consecutive positions, each thread kPer of
+// them. Each thread derives the in-run keys of its own run elements (its
+// gathers independent of each other) into shared memory; then the thread
+// holding a run's first position sorts a run of at most kShortRun elements
+// (keys of elements past the CTA's last position are derived there and
+// then), or lists a longer one.
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, const float *__restrict__ prims,
+                const float *__restrict__ bounds, int b, uint32_t *__restrict__ perm, uint32_t *__restrict__ long_list,
+                uint32_t *long_count, uint32_t *flags) {
+    constexpr int kSpan = kThreads * kPer;
+    __shared__ uint64_t s_key[kSpan];
+    const int64_t cta0 = (int64_t)blockIdx.x * kSpan;
+    const int64_t p0 = cta0 + (int64_t)threadIdx.x * kPer;
+    const uint32_t imask = (uint32_t)((1ull << ib) - 1ull);
+    uint64_t w[kPer];
+    uint32_t member = 0, head = 0;  // bit k: position p0 + k is in a run / starts one
+    if (p0 < n) {
+        if (p0 + kPer <= n) {
+            const uint4 *v = reinterpret_cast<const uint4 *>(words + p0);
+#pragma unroll
+            for (int k = 0; k < kPer / 2; ++k) {
+                const uint4 q = v[k];
+                w[2 * k] = (uint64_t)q.y << 32 | q.x;
+                w[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) w[k] = p0 + k < n ? words[p0 + k] : 0ull;
+        }
+        const uint64_t left = p0 > 0 ? words[p0 - 1] : 0ull;
+        const uint64_t right = p0 + kPer < n ? words[p0 + kPer] : 0ull;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int64_t p = p0 + k;
+            const uint64_t top = w[k] >> ib;
+            const bool eq_prev = p > 0 && ((k > 0 ? w[k - 1] : left) >> ib) == top;
+            const bool eq_next = p + 1 < n && ((k + 1 < kPer ? w[k + 1] : right) >> ib) == top;
+            if (p < n && (eq_prev || eq_next)) member |= 1u << k;
+            if (p < n && !eq_prev && eq_next) head |= 1u << k;
+        }
+        // positions outside runs: the index as it stands
+        if (member == 0 && p0 + kPer <= n) {
+            uint4 *o = reinterpret_cast<uint4 *>(perm + p0);
+#pragma unroll
+            for (int k = 0; k < kPer / 4; ++k)
+                o[k] = make_uint4((uint32_t)w[4 * k] & imask, (uint32_t)w[4 * k + 1] & imask,
+                                  (uint32_t)w[4 * k + 2] & imask, (uint32_t)w[4 * k + 3] & imask);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k)
+                if (p0 + k < n && !(member & (1u << k))) perm[p0 + k] = (uint32_t)w[k] & imask;
+        }
+    }
+    if (!__syncthreads_or(member != 0)) return;  // the common case: no run here
+
+    const Grid3 g = make_grid(bounds, b);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        if (member & (1u << k)) {
+            const uint32_t idx = (uint32_t)w[k] & imask;
+            uint64_t key = 0;
+            if ((int64_t)idx < n) key = run_key<kKind>(prims, idx, g, ib);
+            else atomicOr(flags, kFlagCorrupt);  // only after a timed-out pass
+            s_key[threadIdx.x * kPer + k] = key;
+        }
+    }
+    __syncthreads();
+    if (head == 0) return;
+    for (int k = 0; k < kPer; ++k) {
+        if (!(head & (1u << k))) continue;
+        const int64_t s = p0 + k;
+        const uint64_t top = words[s] >> ib;  // (not w[k]: a variable index would put w in local memory)
+        int len = 1;
+        while (len <= kShortRun && s + len < n && (words[s + len] >> ib) == top) ++len;
+        if (len > kShortRun) {
+            const uint32_t slot = atomicAdd(long_count, 1u);
+            if ((int64_t)slot < n / (kShortRun + 1) + 1) long_list[slot] = (uint32_t)s;
+            else atomicOr(flags, kFlagCorrupt);  // more long runs than positions allow
+            continue;
+        }
+        uint64_t key[kShortRun];
+        for (int i = 0; i < len; ++i) {
+            const int64_t p = s + i;
+            if (p < cta0 + kSpan) {
+                key[i] = s_key[p - cta0];
+            } else {
+                const uint32_t idx = (uint32_t)words[p] & imask;
+                key[i] = (int64_t)idx < n ? run_key<kKind>(prims, idx, g, ib) : 0ull;
+            }
+        }
+        for (int i = 1; i < len; ++i) {  // insertion sort: runs are short
+            const uint64_t v = key[i];
+            int j = i - 1;
+            while (j >= 0 && key[j] > v) {
+                key[j + 1] = key[j];
+                --j;
+            }
+            key[j + 1] = v;
+        }
+        for (int i = 0; i < len; ++i) perm[s + i] = (uint32_t)key[i] & imask;
+    }
+}
+
+// A CTA per listed run (grid-stride over the list): the run's length, then
+// its keys sorted in shared memory by a bitonic network over the next power
+// of two (padded with all-ones keys, which sort last). A run longer than
+// kLongRun raises *fallback instead.
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    long_runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, const float *__restrict__ prims,
+                     const float *__restrict__ bounds, int b, uint32_t *__restrict__ perm,
+                     const uint32_t *__restrict__ long_list, const uint32_t *long_count, uint32_t *fallback,
+                     uint32_t *flags) {
+    __shared__ uint64_t key[kLongRun];
+    __shared__ int s_len;
+    const int64_t count = min((int64_t)*long_count, n / (kShortRun + 1) + 1);
+    const uint32_t imask = (uint32_t)((1ull << ib) - 1ull);
+    const Grid3 g = make_grid(bounds, b);
+    for (int64_t r = blockIdx.x; r < count; r += gridDim.x) {
+        const int64_t s = long_list[r];
+        if (s >= n) {  // a corrupt list entry
+            if (threadIdx.x == 0) atomicOr(flags, kFlagCorrupt);
+            continue;
+        }
+        const uint64_t top = words[s] >> ib;
+        if (threadIdx.x == 0) s_len = kLongRun + 1;
+        __syncthreads();
+        // the run's end: the first position after s whose top differs
+        for (int off = 1; off <= kLongRun; off += kThreads) {
+            const int o = off + (int)threadIdx.x;
+            const bool end = o <= kLongRun && (s + o >= n || (words[s + o] >> ib) != top);
+            if (end) atomicMin(&s_len, o);
+            if (__syncthreads_or(end)) break;
+        }
+        const int len = s_len;
+        if (len > kLongRun) {
+            if (threadIdx.x == 0) atomicOr(fallback, 1u);
+            __syncthreads();  // s_len is rewritten for the next run
+            continue;
+        }
+        int pow2 = 1;
+        while (pow2 < len) pow2 <<= 1;
+        for (int i = threadIdx.x; i < pow2; i += kThreads) {
+            uint64_t k = ~0ull;
+            if (i < len) {
+                const uint32_t idx = (uint32_t)words[s + i] & imask;
+                if ((int64_t)idx < n) k = run_key<kKind>(prims, idx, g, ib);
+                else atomicOr(flags, kFlagCorrupt);  // only after a timed-out pass
+            }
+            key[i] = k;
+        }
+        __syncthreads();
+        for (int size = 2; size <= pow2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < pow2; i += kThreads) {
+                    const int j = i ^ stride;
+                    if (j > i) {
+                        const uint64_t a = key[i], c = key[j];
+                        const bool ascending = (i & size) == 0;
+                        if ((a > c) == ascending) {
+                            key[i] = c;
+                            key[j] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < len; i += kThreads) perm[s + i] = (uint32_t)key[i] & imask;
+        __syncthreads();  // key and s_len are rewritten for the next run
+    }
+}
+
+// Fallback, first step: every element's full code and index (the words'
+// order is (top, index), so a stable sort by code leaves equal codes in
+// index order), and the count the sort reads.
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    fallback_keys_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, const float *__restrict__ prims,
+                         const float *__restrict__ bounds, int b, uint64_t *__restrict__ codes,
+                         uint32_t *__restrict__ index, const uint32_t *fallback, uint32_t *count, uint32_t *flags) {
+    if (*fallback == 0) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *count = (uint32_t)n;
+    const uint32_t imask = (uint32_t)((1ull << ib) - 1ull);
+    const Grid3 g = make_grid(bounds, b);
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kThreads) {
+        uint32_t idx = (uint32_t)words[j] & imask;
+        if ((int64_t)idx >= n) {  // only after a timed-out pass
+            atomicOr(flags, kFlagCorrupt);
+            idx = 0;
+        }
+        codes[j] = code_of<kKind>(prims, idx, g);
+        index[j] = idx;
+    }
+}
+
+// Fallback, last step: the sorted indices are the permutation.
+__global__ void __launch_bounds__(kThreads)
+    fallback_copy_kernel(const uint32_t *__restrict__ index, int64_t n, uint32_t *__restrict__ perm,
+                         const uint32_t *fallback) {
+    if (*fallback == 0) return;
+    for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kThreads)
+        perm[j] = index[j];
+}
+
+}  // namespace
+
+int64_t code_sort_scratch_words(int64_t n) { return n + n / (kShortRun + 1) + 1; }
+
+uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bounds, int64_t n, uint64_t *keys_a,
+                        uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, uint32_t *scratch,
+                        const SortScratch &sc, Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2],
+                        cudaEvent_t *runs_events, int variant_idx) {
+    if (n <= 0) return vals_a;
+    const int ib = top_index_bits(n);
+    uint64_t *words = run_top_sort(keys_a, keys_b, n, ib, sc, ctl, s, pass_events, variant_idx);
+    uint64_t *codes = words == keys_a ? keys_b : keys_a;
+    uint32_t *perm = vals_a, *index_alt = scratch, *long_list = scratch + n;
+    if (runs_events) cudaEventRecord(runs_events[0], s);
+    const bool points = kind == LBVH_PRIM_POINTS;
+    const int b = bits / 3;
+    // long-run count, fallback flag, fallback sort count
+    cudaMemsetAsync(&ctl->run_long, 0, 3 * sizeof(uint32_t), s);
+    const int64_t blocks = (n + (int64_t)kThreads * kPer - 1) / ((int64_t)kThreads * kPer);
+    (points ? runs_kernel<LBVH_PRIM_POINTS> : runs_kernel<LBVH_PRIM_BOXES>)<<<(unsigned)blocks, kThreads, 0, s>>>(
+        words, n, ib, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->build_flags);
+    const int sms = device_sm_count();
+    (points ? long_runs_kernel<LBVH_PRIM_POINTS> : long_runs_kernel<LBVH_PRIM_BOXES>)<<<sms * 2, kThreads, 0, s>>>(
+        words, n, ib, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->run_fallback, &ctl->build_flags);
+    // the fallback (each kernel leaves at once unless a run was too long)
+    (points ? fallback_keys_kernel<LBVH_PRIM_POINTS> : fallback_keys_kernel<LBVH_PRIM_BOXES>)<<<sms * 4, kThreads, 0,
+                                                                                               s>>>(
+        words, n, ib, prims, bounds, b, codes, vals_b, &ctl->run_fallback, &ctl->run_sort_count, &ctl->build_flags);
+    count_launches(3);
+    cudaMemsetAsync(sc.hist, 0, (size_t)kMaxPasses * kRadix * sizeof(uint32_t), s);
+    launch_digit_histogram_counted(codes, n, &ctl->run_sort_count, sc.hist, s);
+    const bool in_b = run_counted_sort(codes, vals_b, words, index_alt, &ctl->run_sort_count, n, bits, sc, ctl, s);
+    fallback_copy_kernel<<<sms * 4, kThreads, 0, s>>>(in_b ? index_alt : vals_b, n, perm, &ctl->run_fallback);
+    count_launches(1);
+    if (runs_events) cudaEventRecord(runs_events[1], s);
+    return perm;
+}
+
+}  // namespace lbvh

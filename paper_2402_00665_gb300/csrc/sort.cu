@@ -14,16 +14,19 @@
 // writes it out so that consecutive threads write consecutive addresses.
 //
 // Layouts of a pass. A digit is byte `db` of the 64-bit key (passes sort
-// bytes 0, 1, 2, ... in turn).
+// bytes db0, db0 + 1, ... in turn).
 //   key + payload  uint64 keys[] and uint32 vals[] (or vals = the index)
-//   packed         one uint64 word per element: the key's high 32 bits in
-//                  the word's high half, the payload in its low half
-// Once the low four bytes of a key are sorted the sort no longer needs them,
-// so the pass that sorts byte 3 may write packed words, and later passes move
-// 8 bytes per element instead of 12; the last pass may write the payloads
-// alone (the sorted permutation), which is all a tree build needs (it
-// derives each leaf's code again from the primitive it gathers). Keys of at
-// most 32 bits are packed from the start by the encoder (code << 32 | index).
+//   packed         one uint64 word per element holding key bits above the
+//                  payload: code << 32 | index for codes of at most 32 bits,
+//                  or a wider code's top bits above the index (runs.cu)
+// A packed pass moves 8 bytes per element each way instead of 12; the last
+// pass of a packed sort may write the payloads alone (the sorted
+// permutation), which is all a tree build needs (it derives each leaf's code
+// again from the primitive it gathers).
+//
+// Two ways to launch a pass: one CTA per tile (onesweep_kernel), or a fixed
+// grid of CTAs that take tiles until a count read on the device runs out
+// (onesweep_counted_kernel), for a sort whose size a kernel decided.
 //
 // The same kernel also sorts many independent segments at once (batches of
 // trees): tiles then never straddle two segments, and each segment has its own
@@ -52,7 +55,7 @@ constexpr uint32_t kSpinLimit = 1u << 26;
 
 // Input and output layouts of one pass.
 enum : int { kInIota = 0, kInKV = 1, kInPacked = 2 };
-enum : int { kOutKV = 0, kOutPack = 1, kOutPacked = 2, kOutLow = 3 };
+enum : int { kOutKV = 0, kOutPacked = 1, kOutLow = 2 };
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -154,6 +157,7 @@ struct PassArgs {
     uint32_t *flags, *next_hist;
     SegArgs seg;
     int64_t hold_tile, prefetch_ahead;
+    const uint32_t *count;  // persistent passes: the number of keys, on the device
 };
 
 // kIn / kOut: the layouts above; kHi: the digit byte lies in the key's high
@@ -166,34 +170,17 @@ struct PassArgs {
 // segment's rows of the histograms, and its look-back chain ends at the
 // segment's first tile.
 template <int kIn, int kOut, bool kHi, int kItems, int kMinBlocks, bool kTable, bool kSeg>
-__global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(const PassArgs a) {
+__device__ __forceinline__ void sweep_tile(const PassArgs &a, SortSmem<kItems, kIn != kInPacked, kTable> &sm,
+                                           const int64_t tile, const int64_t n, const int64_t tiles) {
     constexpr bool kVals = kIn != kInPacked;  // a payload travels beside the key
-    using Smem = SortSmem<kItems, kVals, kTable>;
-    constexpr int kTile = Smem::kTile;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    constexpr int kTile = SortSmem<kItems, kVals, kTable>::kTile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t sel = 0x4440u | (uint32_t)(a.db & 3);
     const int nb = a.db + 1;  // the next pass's digit byte
     const uint32_t nsel = 0x4440u | (uint32_t)(nb & 3);
-    const int64_t tiles = a.tiles;
     uint32_t *next_hist = a.next_hist;
     const uint32_t *pass_hist = a.pass_hist;
-
-    if (threadIdx.x == 0) {
-        const uint32_t t = atomicAdd(a.ticket, 1u);
-        if (t == tiles - 1) *a.ticket = 0;  // last ticket handed out: reset for the next pass
-        sm.tile = t;
-        if (kSeg) sm.seg = instance_of(a.seg.tile_first, a.seg.count, t);
-    }
-    for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) {
-        (&sm.warp_hist[0][0])[k] = 0;
-        if (kTable) (&sm.peer_mask[0][0])[k] = 0;
-    }
-    sm.next_hist[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t tile = sm.tile;
-    int64_t first_tile = 0, seg_begin = 0, seg_end = a.n, tile_base = tile * kTile;
+    int64_t first_tile = 0, seg_begin = 0, seg_end = n, tile_base = tile * kTile;
     if (kSeg) {
         const int sg = sm.seg;
         first_tile = a.seg.tile_first[sg];
@@ -210,7 +197,7 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(cons
         const int64_t ft = tile + a.prefetch_ahead;
         if (ft < tiles) {
             const int64_t fb = ft * kTile;
-            const int64_t fcnt = min((int64_t)kTile, a.n - fb);
+            const int64_t fcnt = min((int64_t)kTile, n - fb);
             const uint32_t kbytes = (uint32_t)((fcnt * 8) & ~15ll);  // rounded down: stays inside
             if (kbytes)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.keys_in + fb), "r"(kbytes)
@@ -363,8 +350,6 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(cons
             if (kOut == kOutKV) {
                 a.keys_out[pos] = k;
                 a.vals_out[pos] = sm.vals[s];
-            } else if (kOut == kOutPack) {
-                a.keys_out[pos] = (k & 0xffffffff00000000ull) | sm.vals[s];
             } else if (kOut == kOutPacked) {
                 a.keys_out[pos] = k;
             } else if (kIn == kInPacked) {
@@ -376,6 +361,61 @@ __global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(cons
     }
 }
 
+// One CTA per tile, taken by ticket (so every tile it may wait on is
+// already running).
+template <int kIn, int kOut, bool kHi, int kItems, int kMinBlocks, bool kTable, bool kSeg>
+__global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_kernel(const PassArgs a) {
+    using Smem = SortSmem<kItems, kIn != kInPacked, kTable>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    if (threadIdx.x == 0) {
+        const uint32_t t = atomicAdd(a.ticket, 1u);
+        if (t == a.tiles - 1) *a.ticket = 0;  // last ticket handed out: reset for the next pass
+        sm.tile = t;
+        if (kSeg) sm.seg = instance_of(a.seg.tile_first, a.seg.count, t);
+    }
+    for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) {
+        (&sm.warp_hist[0][0])[k] = 0;
+        if (kTable) (&sm.peer_mask[0][0])[k] = 0;
+    }
+    sm.next_hist[threadIdx.x] = 0;
+    __syncthreads();
+    sweep_tile<kIn, kOut, kHi, kItems, kMinBlocks, kTable, kSeg>(a, sm, sm.tile, a.n, a.tiles);
+}
+
+// A fixed grid of CTAs taking tiles by ticket until the keys run out; the
+// number of keys is read from the device (*a.count), so a pass can follow a
+// kernel that decided it, with no host round trip. A CTA takes its next
+// ticket only when it is ready to work on that tile, so every tile a CTA
+// waits on is being worked on. Each CTA takes exactly one ticket past the
+// last tile (and leaves), so the ticket handed out last is number
+// tiles + gridDim.x - 1, whose holder resets the counter.
+template <int kIn, int kOut, bool kHi, int kItems, int kMinBlocks, bool kTable>
+__global__ void __launch_bounds__(kSortThreads, kMinBlocks) onesweep_counted_kernel(const PassArgs a) {
+    using Smem = SortSmem<kItems, kIn != kInPacked, kTable>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem &sm = *reinterpret_cast<Smem *>(smem_raw);
+    const int64_t n = min((int64_t)*a.count, a.n);  // a.n: the most the buffers hold
+    const int64_t tiles = (n + Smem::kTile - 1) / Smem::kTile;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const uint32_t t = atomicAdd(a.ticket, 1u);
+            if ((int64_t)t == tiles + gridDim.x - 1) *a.ticket = 0;
+            sm.tile = t;
+        }
+        for (int k = threadIdx.x; k < kWarps * kRadix; k += kSortThreads) {
+            (&sm.warp_hist[0][0])[k] = 0;
+            if (kTable) (&sm.peer_mask[0][0])[k] = 0;
+        }
+        sm.next_hist[threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t tile = sm.tile;
+        if (tile >= tiles) return;
+        sweep_tile<kIn, kOut, kHi, kItems, kMinBlocks, kTable, false>(a, sm, tile, n, tiles);
+        __syncthreads();  // the tile's shared state is read before the next one clears it
+    }
+}
+
 using PassKernel = void (*)(PassArgs);
 
 // The (input, output, digit half) combinations the library runs.
@@ -383,9 +423,9 @@ enum PassKind : int {
     kIotaKV,        // pass 0 of a pair sort: payload = index
     kKVKVLo,        // key + payload in and out, digit in the low half
     kKVKVHi,        // the same, digit in the high half
-    kKVPack,        // byte 3: key + payload in, packed words out
     kPackedPacked,  // packed in and out
     kPackedLow,     // packed in, payloads out (the last pass)
+    kPackedPackedLo,  // packed in and out, digit in the low half (words key << ib | index, ib < 32)
     kPassKinds
 };
 
@@ -401,9 +441,9 @@ void fill_kinds(PassKernel (&k)[kPassKinds]) {
     k[kIotaKV] = onesweep_kernel<kInIota, kOutKV, false, kItems, kMinBlocks, kTable, kSeg>;
     k[kKVKVLo] = onesweep_kernel<kInKV, kOutKV, false, kItems, kMinBlocks, kTable, kSeg>;
     k[kKVKVHi] = onesweep_kernel<kInKV, kOutKV, true, kItems, kMinBlocks, kTable, kSeg>;
-    k[kKVPack] = onesweep_kernel<kInKV, kOutPack, false, kItems, kMinBlocks, kTable, kSeg>;
     k[kPackedPacked] = onesweep_kernel<kInPacked, kOutPacked, true, kItems, kMinBlocks, kTable, kSeg>;
     k[kPackedLow] = onesweep_kernel<kInPacked, kOutLow, true, kItems, kMinBlocks, kTable, kSeg>;
+    k[kPackedPackedLo] = kSeg ? nullptr : onesweep_kernel<kInPacked, kOutPacked, false, kItems, kMinBlocks, kTable, false>;
 }
 
 template <int kItems, int kMinBlocks, bool kTable>
@@ -420,7 +460,7 @@ Variant make_variant() {
 }
 
 size_t pass_smem(const Variant &v, int kind) {
-    return (kind == kPackedPacked || kind == kPackedLow) ? v.smem_packed : v.smem_kv;
+    return (kind == kPackedPacked || kind == kPackedLow || kind == kPackedPackedLo) ? v.smem_packed : v.smem_kv;
 }
 
 // Tile shapes the library is compiled with (keys per thread, CTAs per SM,
@@ -450,6 +490,7 @@ const Variant *variant_table(int *count) {
         for (const Variant &v : table)
             for (int sg = 0; sg < 2; ++sg)
                 for (int kind = 0; kind < kPassKinds; ++kind) {
+                    if (!v.k[sg][kind]) continue;
                     cudaFuncSetAttribute(v.k[sg][kind], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pass_smem(v, kind));
                     cudaFuncSetAttribute(v.k[sg][kind], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -467,9 +508,12 @@ const Variant &variant(int idx = -1) {
     return table[(idx >= 0 && idx < count) ? idx : 0];
 }
 
+// count (nullable): only the first *count keys (read on the device) are counted.
 __global__ void __launch_bounds__(256)
     digit_histogram_kernel(const uint64_t *__restrict__ keys, int64_t n, int passes,
-                           uint32_t *__restrict__ hist) {
+                           uint32_t *__restrict__ hist, const uint32_t *count) {
+    if (count) n = min(n, (int64_t)*count);
+    if (n == 0) return;
     __shared__ uint32_t s_hist[kMaxPasses * kRadix];
     for (int k = threadIdx.x; k < passes * kRadix; k += blockDim.x) s_hist[k] = 0;
     __syncthreads();
@@ -494,7 +538,17 @@ void launch_digit_histogram(const uint64_t *keys, int64_t n, int passes, uint32_
     int64_t blocks = (n + 255) / 256;
     const int64_t cap = (int64_t)device_sm_count() * 8;
     if (blocks > cap) blocks = cap;
-    digit_histogram_kernel<<<(int)blocks, 256, 0, s>>>(keys, n, passes, hist);
+    digit_histogram_kernel<<<(int)blocks, 256, 0, s>>>(keys, n, passes, hist, nullptr);
+    count_launches(1);
+}
+
+void launch_digit_histogram_counted(const uint64_t *keys, int64_t n_max, const uint32_t *count, uint32_t *hist,
+                                    cudaStream_t s) {
+    if (n_max <= 0) return;
+    int64_t blocks = (n_max + 255) / 256;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    digit_histogram_kernel<<<(int)blocks, 256, 0, s>>>(keys, n_max, 1, hist, count);
     count_launches(1);
 }
 
@@ -585,36 +639,103 @@ bool run_onesweep(uint64_t *keys_a, uint32_t *vals_a, bool iota, uint64_t *keys_
     return (passes & 1) != 0;
 }
 
-uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, int64_t n,
-                         int key_bits, bool packed, const SortScratch &scratch, Control *ctl, cudaStream_t s,
-                         cudaEvent_t (*pass_events)[2], int variant_idx) {
-    if (n <= 0) return vals_a;
+uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_out, int64_t n, int key_bits,
+                         const SortScratch &scratch, Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2],
+                         int variant_idx) {
+    if (n <= 0) return vals_out;
     const int passes = sort_passes(key_bits);
     Pass ps[kMaxPasses];
     uint64_t *kb[2] = {keys_a, keys_b};
-    uint32_t *vb[2] = {vals_a, vals_b};
-    uint32_t *perm = vals_a;
-    if (packed) {
-        // bytes 4 .. 4 + passes - 1 of words code << 32 | index
-        for (int p = 0; p < passes; ++p) {
-            const int in = p & 1, out = in ^ 1;
-            const bool last = p == passes - 1;
-            ps[p] = Pass{last ? kPackedLow : kPackedPacked, 4 + p, kb[in], nullptr, kb[out], last ? vb[0] : nullptr};
-        }
-        perm = vb[0];
-    } else {
-        // bytes 0-3 with key + payload (byte 3's pass packs), then packed;
-        // more than 32 key bits means at least five passes
-        for (int p = 0; p < passes; ++p) {
-            const int in = p & 1, out = in ^ 1;
-            const bool last = p == passes - 1;
-            int kind = p == 0 ? kIotaKV : (p < 3 ? kKVKVLo : (p == 3 ? kKVPack : (last ? kPackedLow : kPackedPacked)));
-            ps[p] = Pass{kind, p, kb[in], p <= 3 ? vb[in] : nullptr, kb[out], (p < 3 || last) ? vb[out] : nullptr};
-            if (last) perm = vb[out];
-        }
+    // bytes 4 .. 4 + passes - 1 of words code << 32 | index
+    for (int p = 0; p < passes; ++p) {
+        const int in = p & 1, out = in ^ 1;
+        const bool last = p == passes - 1;
+        ps[p] = Pass{last ? kPackedLow : kPackedPacked, 4 + p, kb[in], nullptr, kb[out], last ? vals_out : nullptr};
     }
     run_pass_list(variant(variant_idx), ps, passes, n, scratch, ctl, s, pass_events, nullptr);
-    return perm;
+    return vals_out;
+}
+
+uint64_t *run_top_sort(uint64_t *keys_a, uint64_t *keys_b, int64_t n, int index_bits, const SortScratch &scratch,
+                       Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx) {
+    if (n <= 0) return keys_a;
+    const int first = index_bits / kRadixBits;  // the byte holding the key's lowest bit
+    const int passes = kMaxPasses - first;
+    Pass ps[kMaxPasses];
+    uint64_t *kb[2] = {keys_a, keys_b};
+    for (int p = 0; p < passes; ++p) {
+        const int in = p & 1, out = in ^ 1;
+        const int db = first + p;
+        ps[p] = Pass{db < 4 ? kPackedPackedLo : kPackedPacked, db, kb[in], nullptr, kb[out], nullptr};
+    }
+    run_pass_list(variant(variant_idx), ps, passes, n, scratch, ctl, s, pass_events, nullptr);
+    return kb[passes & 1];
+}
+
+namespace {
+
+// The counted passes use the default tile shape (24 keys x 2 CTAs per SM,
+// shared-memory table).
+constexpr int kCountedItems = 24, kCountedBlocks = 2;
+
+struct CountedKernels {
+    PassKernel lo, hi;  // key + payload, digit in the low / high half
+    size_t smem;
+};
+
+const CountedKernels &counted_kernels() {
+    static const CountedKernels c = [] {
+        CountedKernels k{};
+        k.lo = onesweep_counted_kernel<kInKV, kOutKV, false, kCountedItems, kCountedBlocks, true>;
+        k.hi = onesweep_counted_kernel<kInKV, kOutKV, true, kCountedItems, kCountedBlocks, true>;
+        k.smem = sizeof(SortSmem<kCountedItems, true, true>);
+        for (PassKernel f : {k.lo, k.hi}) {
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+            cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
+        return k;
+    }();
+    return c;
+}
+
+}  // namespace
+
+bool run_counted_sort(uint64_t *keys_a, uint32_t *vals_a, uint64_t *keys_b, uint32_t *vals_b,
+                      const uint32_t *count, int64_t n_max, int key_bits, const SortScratch &scratch, Control *ctl,
+                      cudaStream_t s) {
+    if (n_max <= 0) return false;
+    const CountedKernels &k = counted_kernels();
+    const int passes = sort_passes(key_bits);
+    const int64_t tile = (int64_t)kSortThreads * kCountedItems;
+    const int64_t tiles_max = (n_max + tile - 1) / tile;
+    int64_t grid = (int64_t)device_sm_count() * kCountedBlocks;
+    if (grid > tiles_max) grid = tiles_max;
+    cudaMemsetAsync(scratch.lookback, 0, (size_t)tiles_max * kRadix * sizeof(uint32_t), s);
+    uint64_t *kb[2] = {keys_a, keys_b};
+    uint32_t *vb[2] = {vals_a, vals_b};
+    for (int p = 0; p < passes; ++p) {
+        const int in = p & 1, out = in ^ 1;
+        PassArgs a{};
+        a.keys_in = kb[in];
+        a.vals_in = vb[in];
+        a.keys_out = kb[out];
+        a.vals_out = vb[out];
+        a.n = n_max;
+        a.db = p;
+        a.pass_hist = scratch.hist + p * kRadix;
+        a.lookback = scratch.lookback + (p & 1) * scratch.lookback_words;
+        a.lookback_next = scratch.lookback + ((p + 1) & 1) * scratch.lookback_words;
+        a.ticket = &ctl->sort_ticket[p];
+        a.tiles = tiles_max;
+        a.flags = &ctl->build_flags;
+        a.next_hist = p + 1 < passes ? scratch.hist + (p + 1) * kRadix : nullptr;
+        a.hold_tile = -1;
+        a.prefetch_ahead = 0;
+        a.count = count;
+        (p < 4 ? k.lo : k.hi)<<<(unsigned)grid, kSortThreads, k.smem, s>>>(a);
+        count_launches(1);
+    }
+    return (passes & 1) != 0;
 }
 
 }  // namespace lbvh

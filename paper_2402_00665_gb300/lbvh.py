@@ -27,7 +27,7 @@ KNN_MAX_K = 256
 SERVER_PHASES = 4
 BUILD_MODIFIED_APETREI, BUILD_KARRAS, BUILD_APETREI = 0, 1, 2
 _QDIM = {SPHERE: 3, BOX: 6, RAY: 8}
-STAGE_COUNT = 17
+STAGE_COUNT = 18
 
 STATUS = {0: "LBVH_OK", 1: "LBVH_ERR_INVALID", 2: "LBVH_ERR_NONFINITE", 3: "LBVH_ERR_OOM",
           4: "LBVH_ERR_CUDA", 5: "LBVH_ERR_TIMEOUT", 6: "LBVH_ERR_CORRUPT", 7: "LBVH_ERR_CAPACITY"}
