@@ -52,7 +52,10 @@ UNIT = "Mprims/s"
 # method itself must move, independent of how a kernel moves it.
 #   bounds      read the points                              12
 #   encode      read the points, write the 64-bit codes      12 + 8
-#   sort pass   read key + payload, write key + payload      12 + 12 (pass 0: no payload read)
+#   sort pass   read one 8-byte word (key bits above the index), write one 8 + 8
+#               (the last pass of a 30-bit sort writes the 4-byte index alone)
+#   sort runs   read the sorted words, write the permutation 8 + 4 (codes
+#               wider than 30 bits: the runs of equal top bits put in order)
 #   construct   key 8 + perm 4 + point 12 read, leaf 16 and internal node 32
 #               written (the store words and sibling boxes of the nodes inside
 #               a CTA's leaves stay in shared memory)
@@ -69,8 +72,8 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
     table = {
         "bounds": pb * n,
         "encode": (pb + 8) * n,
-        "sort_pass0": 20 * n,
-        **{f"sort_pass{k}": 24 * n for k in range(1, 8)},
+        **{f"sort_pass{k}": 16 * n for k in range(8)},
+        "sort_runs": 12 * n,
         # codes, perm, primitive read; leaf + internal node write
         "construct": (8 + 4 + pb + lb + 32) * n,
         # query + count/position per query, each kept hit, the tree once
@@ -101,17 +104,21 @@ def model_build_bytes(n: int, bits: int, boxes: bool = False) -> int:
 def moved_build_bytes(n: int, bits: int, boxes: bool = False) -> int:
     """Bytes this implementation's build kernels read and write, counted
     from their layouts (each element once): bounds and encode stream the
-    primitives; the sort moves key + index (12 B each way) until the low four
-    bytes are sorted, then one packed 8-byte word, and the last pass writes
-    the 4-byte permutation alone (codes of at most 30 bits are packed from
-    the encoder on); the construct reads the permutation and gathers each
-    primitive, writes the sorted code, the leaf and the internal node."""
+    primitives, the encoder writes one 8-byte word; codes of at most 30 bits
+    are sorted as code << 32 | index words (the last pass writes the 4-byte
+    permutation alone); wider codes as top bits << ib | index words, ib =
+    ceil(log2 n), over bytes ib // 8 .. 7, then one pass reads the sorted
+    words and writes the permutation (the rare runs of equal top bits
+    gather their primitives again: not counted); the construct reads the
+    permutation and gathers each primitive, writes the sorted code, the leaf
+    and the internal node."""
     pb, lb = (24, 32) if boxes else (12, 16)
-    passes = (bits + 7) // 8
     if bits <= 30:
+        passes = (bits + 7) // 8
         sort = 16 * (passes - 1) + 12
     else:
-        sort = 20 + 24 * 2 + 20 + 16 * (passes - 5) + 12
+        ib = max(1, (n - 1).bit_length())
+        sort = 16 * (8 - ib // 8) + 12
     return (pb + (pb + 8) + sort + (4 + pb + 8 + lb + 32)) * n
 
 
