@@ -136,9 +136,15 @@ __global__ void __launch_bounds__(kThreads)
     for (int k = 0; k < kPer; ++k) {
         if (!(head & (1u << k))) continue;
         const int64_t s = p0 + k;
-        const uint64_t top = words[s] >> ib;  // (not w[k]: a variable index would put w in local memory)
+        // the run's length: inside this thread's positions a member that
+        // starts no run continues the one before it; a run that reaches the
+        // thread's last position is followed through the words
         int len = 1;
-        while (len <= kShortRun && s + len < n && (words[s + len] >> ib) == top) ++len;
+        while (k + len < kPer && (member >> (k + len) & 1u) && !(head >> (k + len) & 1u)) ++len;
+        if (k + len == kPer) {
+            const uint64_t top = words[s] >> ib;  // (not w[k]: a variable index would put w in local memory)
+            while (len <= kShortRun && s + len < n && (words[s + len] >> ib) == top) ++len;
+        }
         if (len > kShortRun) {
             const uint32_t slot = atomicAdd(long_count, 1u);
             if ((int64_t)slot < n / (kShortRun + 1) + 1) long_list[slot] = (uint32_t)s;
