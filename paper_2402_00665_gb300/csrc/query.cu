@@ -596,28 +596,45 @@ __global__ void __launch_bounds__(kScanThreads)
     }
 }
 
+// Loads and stores run across the block (thread t at t, t + 256, ...); each
+// thread scans kScanItems consecutive counts, which it reads from and writes
+// back to shared memory (rows padded by one element against bank conflicts).
 __global__ void __launch_bounds__(kScanThreads)
     scan_apply_kernel(const uint2 *__restrict__ counts, int64_t nq,
                       const int64_t *__restrict__ tile_sums, int64_t *__restrict__ offsets) {
+    constexpr int kRow = kScanItems + 1;
     __shared__ int64_t s_warp[kScanThreads / 32];
+    __shared__ int64_t s_o[kScanThreads * kRow];  // the offsets; first the counts (the scan's barriers
+                                                  // separate the last read of a count from the first offset)
+    uint32_t *s_c = reinterpret_cast<uint32_t *>(s_o);
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    // thread t owns kScanItems consecutive counts
-    uint32_t c[kScanItems];
-    int64_t sum = 0;
-    const int64_t first = base + (int64_t)threadIdx.x * kScanItems;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = first + j;
-        c[j] = i < nq ? counts[i].x : 0u;
+        const int p = j * kScanThreads + threadIdx.x;
+        const int64_t i = base + p;
+        s_c[(p / kScanItems) * kRow + p % kScanItems] = i < nq ? counts[i].x : 0u;
+    }
+    __syncthreads();
+    uint32_t c[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        c[j] = s_c[threadIdx.x * kRow + j];
         sum += c[j];
     }
     int64_t total;
     int64_t run = tile_sums[blockIdx.x] + block_scan_exclusive(sum, s_warp, total);
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        const int64_t i = first + j;
-        if (i < nq) offsets[i] = run;
+        s_o[threadIdx.x * kRow + j] = run;
         run += c[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        const int p = j * kScanThreads + threadIdx.x;
+        const int64_t i = base + p;
+        if (i < nq) offsets[i] = s_o[(p / kScanItems) * kRow + p % kScanItems];
     }
 }
 

@@ -75,27 +75,28 @@ __global__ void __launch_bounds__(kThreads)
                 const float *__restrict__ bounds, int b, uint32_t *__restrict__ perm, uint32_t *__restrict__ long_list,
                 uint32_t *long_count, uint32_t *flags) {
     constexpr int kSpan = kThreads * kPer;
-    __shared__ uint64_t s_key[kSpan];
+    // the CTA's words, loaded across the CTA (position p at p + p / kPer: one
+    // padding word per thread's row keeps a thread's reads of its own row
+    // free of bank conflicts); then the run keys, by position
+    __shared__ uint64_t s_key[kSpan + kThreads];
     const int64_t cta0 = (int64_t)blockIdx.x * kSpan;
     const int64_t p0 = cta0 + (int64_t)threadIdx.x * kPer;
     const uint32_t imask = (uint32_t)((1ull << ib) - 1ull);
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int p = j * kThreads + threadIdx.x;
+        s_key[p + p / kPer] = cta0 + p < n ? words[cta0 + p] : 0ull;
+    }
+    __syncthreads();
     uint64_t w[kPer];
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) w[k] = s_key[threadIdx.x * (kPer + 1) + k];
     uint32_t member = 0, head = 0;  // bit k: position p0 + k is in a run / starts one
     if (p0 < n) {
-        if (p0 + kPer <= n) {
-            const uint4 *v = reinterpret_cast<const uint4 *>(words + p0);
-#pragma unroll
-            for (int k = 0; k < kPer / 2; ++k) {
-                const uint4 q = v[k];
-                w[2 * k] = (uint64_t)q.y << 32 | q.x;
-                w[2 * k + 1] = (uint64_t)q.w << 32 | q.z;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < kPer; ++k) w[k] = p0 + k < n ? words[p0 + k] : 0ull;
-        }
-        const uint64_t left = p0 > 0 ? words[p0 - 1] : 0ull;
-        const uint64_t right = p0 + kPer < n ? words[p0 + kPer] : 0ull;
+        // the last word of the previous thread's row (its padding word follows it)
+        const uint64_t left = threadIdx.x > 0 ? s_key[threadIdx.x * (kPer + 1) - 2] : (p0 > 0 ? words[p0 - 1] : 0ull);
+        const uint64_t right = threadIdx.x + 1 < kThreads ? s_key[(threadIdx.x + 1) * (kPer + 1)]
+                                                          : (p0 + kPer < n ? words[p0 + kPer] : 0ull);
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int64_t p = p0 + k;
