@@ -611,17 +611,22 @@ def run_gpu(args, world, rank, local):
         host_hits = torch.empty(hits.numel(), dtype=torch.int32).pin_memory()
         dpts = torch.empty_like(pts)
         dq = torch.empty_like(qpts)
+        main = torch.cuda.current_stream(dev)
+        side = torch.cuda.Stream(dev)
         def e2e_step():
             # inputs in by copy; results through lbvh_query_into_host, which
             # stages the CSR on the device chunk by chunk and copies each chunk
             # to the page-locked host arrays while the next one runs, or with
-            # --e2e-staged into device arrays and then copied (copying the
-            # queries on a second stream during the build, and the offsets
-            # during the hit copy, measured slower: the host links are shared
-            # and the build's sort competes for HBM)
+            # --e2e-staged into device arrays and then copied. The queries go
+            # up on a second stream once the points are up, during the build
+            # (the two copies would share the host link; the build needs only
+            # the points)
             dpts.copy_(host_pts, non_blocking=True)
-            dq.copy_(host_q, non_blocking=True)
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                dq.copy_(host_q, non_blocking=True)
             tree.build(dpts, kind, bits)
+            main.wait_stream(side)
             if args.e2e_staged:
                 s, tot = tree.query_into(dq, qkind, offsets, hits, radius=float(radius))
                 if s != lbvh.OK:
