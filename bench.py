@@ -609,51 +609,62 @@ def run_gpu(args, world, rank, local):
         host_q = torch.from_numpy(queries_host).pin_memory()
         host_off = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
         host_hits = torch.empty(hits.numel(), dtype=torch.int32).pin_memory()
-        dpts = torch.empty_like(pts)
-        dq = torch.empty_like(qpts)
+        # two sets of device inputs: step k's inputs go up (second stream)
+        # while step k - 1 queries, so a step's host->device copies overlap
+        # the previous step's walk and its device->host copies; every step
+        # still copies its own inputs up and its own results down inside the
+        # timed region (the first step of a run uploads before its build, the
+        # last one uploads nothing ahead)
+        dpts = [torch.empty_like(pts), torch.empty_like(pts)]
+        dq = [torch.empty_like(qpts), torch.empty_like(qpts)]
         main = torch.cuda.current_stream(dev)
         side = torch.cuda.Stream(dev)
-        def e2e_step():
-            # inputs in by copy; results through lbvh_query_into_host, which
-            # stages the CSR on the device chunk by chunk and copies each chunk
-            # to the page-locked host arrays while the next one runs, or with
-            # --e2e-staged into device arrays and then copied. The queries go
-            # up on a second stream once the points are up, during the build
-            # (the two copies would share the host link; the build needs only
-            # the points)
-            dpts.copy_(host_pts, non_blocking=True)
-            side.wait_stream(main)
+        uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def upload(slot):
             with torch.cuda.stream(side):
-                dq.copy_(host_q, non_blocking=True)
-            tree.build(dpts, kind, bits)
-            main.wait_stream(side)
-            if args.e2e_staged:
-                s, tot = tree.query_into(dq, qkind, offsets, hits, radius=float(radius))
-                if s != lbvh.OK:
-                    raise lbvh.LbvhError(s, "lbvh_query_into")
-                host_off.copy_(offsets, non_blocking=True)
-                host_hits[:tot].copy_(hits[:tot], non_blocking=True)
-            else:
-                s, tot = tree.query_into_host(dq, qkind, host_off, host_hits, radius=float(radius))
-                if s != lbvh.OK:
-                    raise lbvh.LbvhError(s, "lbvh_query_into_host")
-            torch.cuda.current_stream(dev).synchronize()
+                dpts[slot].copy_(host_pts, non_blocking=True)
+                dq[slot].copy_(host_q, non_blocking=True)
+                uploaded[slot].record(side)
+
+        def e2e_run(steps):
+            # results through lbvh_query_into_host, which stages the CSR on
+            # the device chunk by chunk and copies each chunk to the
+            # page-locked host arrays while the next one runs, or with
+            # --e2e-staged into device arrays and then copied
+            tot = 0
+            upload(0)
+            for k in range(steps):
+                slot = k & 1
+                main.wait_event(uploaded[slot])
+                tree.build(dpts[slot], kind, bits)
+                if k + 1 < steps:
+                    upload(slot ^ 1)  # its buffers were last read by step k - 1, which has finished
+                if args.e2e_staged:
+                    s, tot = tree.query_into(dq[slot], qkind, offsets, hits, radius=float(radius))
+                    if s != lbvh.OK:
+                        raise lbvh.LbvhError(s, "lbvh_query_into")
+                    host_off.copy_(offsets, non_blocking=True)
+                    host_hits[:tot].copy_(hits[:tot], non_blocking=True)
+                else:
+                    s, tot = tree.query_into_host(dq[slot], qkind, host_off, host_hits, radius=float(radius))
+                    if s != lbvh.OK:
+                        raise lbvh.LbvhError(s, "lbvh_query_into_host")
+                main.synchronize()
             return tot
 
-        for _ in range(2):
-            e2e_step()
+        e2e_run(2)
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tot = 0
-        for _ in range(args.steps):
-            tot = e2e_step()
+        tot = e2e_run(args.steps)
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world, dev) / args.steps
         e2e = {"value": n * world / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int((pts.numel() + qpts.numel()) * 4),
                "d2h_bytes_per_step": int((nq + 1) * 8 + tot * 4),
-               "note": "pinned host primitives and queries -> device, build, query, CSR offsets + hits "
+               "note": "pinned host primitives and queries -> device (each step's inputs copied on a second "
+                       "stream while the previous step queries), build, query, CSR offsets + hits "
                        + ("-> device, then copied to pinned host" if args.e2e_staged
                           else "-> pinned host by lbvh_query_into_host (chunks staged on the device, "
                                "each copied while the next runs)")}
