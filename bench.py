@@ -3,7 +3,8 @@
 range query of the same size, on synthetic inputs already resident in HBM.
 
 Workload (default): 2^25 points uniform in [0,1)^3 (FP32), 63-bit Morton codes;
-a build (bounds, Morton codes, 8 radix-sort passes, Algorithm 4 construct) and
+a build (bounds, Morton codes, the radix sort of the codes' top bits beside the
+index in 4 or 5 passes plus the runs of equal top bits, Algorithm 4 construct) and
 2^25 sphere queries centred at the points with the radius that holds 16
 expected neighbours (Algorithm 1, CSR output with sorted hit lists).
 
@@ -101,24 +102,25 @@ def model_build_bytes(n: int, bits: int, boxes: bool = False) -> int:
     return per * n
 
 
-def moved_build_bytes(n: int, bits: int, boxes: bool = False) -> int:
+def moved_build_bytes(n: int, bits: int, boxes: bool = False, passes: int | None = None) -> int:
     """Bytes this implementation's build kernels read and write, counted
     from their layouts (each element once): bounds and encode stream the
     primitives, the encoder writes one 8-byte word; codes of at most 30 bits
     are sorted as code << 32 | index words (the last pass writes the 4-byte
     permutation alone); wider codes as top bits << ib | index words, ib =
-    ceil(log2 n), over bytes ib // 8 .. 7, then one pass reads the sorted
-    words and writes the permutation (the rare runs of equal top bits
-    gather their primitives again: not counted); the construct reads the
-    permutation and gathers each primitive, writes the sorted code, the leaf
-    and the internal node."""
+    ceil(log2 n), over bytes ib // 8 .. 7 (or one byte fewer, the tuner's
+    choice: `passes` is the number of passes that ran), then one pass reads
+    the sorted words and writes the permutation (the runs of equal sorted
+    bits gather their primitives again: not counted); the construct reads
+    the permutation and gathers each primitive, writes the sorted code, the
+    leaf and the internal node."""
     pb, lb = (24, 32) if boxes else (12, 16)
     if bits <= 30:
         passes = (bits + 7) // 8
         sort = 16 * (passes - 1) + 12
     else:
         ib = max(1, (n - 1).bit_length())
-        sort = 16 * (8 - ib // 8) + 12
+        sort = 16 * (passes if passes is not None else 8 - ib // 8) + 12
     return (pb + (pb + 8) + sort + (4 + pb + 8 + lb + 32)) * n
 
 
@@ -571,7 +573,7 @@ def run_gpu(args, world, rank, local):
            if alg_bytes(k, n, nq, total_hits) is not None}
     achieved = alg[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
     build_model = model_build_bytes(n, bits, boxes)
-    build_moved = moved_build_bytes(n, bits, boxes)
+    build_moved = moved_build_bytes(n, bits, boxes, sum(1 for k in stage_ms if k.startswith("sort_pass")))
 
     # ---- the walk's own roofline: node visits against the same walk on a
     # tree small enough that every node load hits L1 (the ceiling of its
@@ -692,7 +694,10 @@ def run_gpu(args, world, rank, local):
             "us_per_step": ms_step * 1e3,
             "launches_per_step": launches / args.steps,
             "tuning": {"sort_variant": tune_sort, "walk_variant": tune_walk,
-                       "how": "lbvh_tree_autotune on these inputs before the warm-up"},
+                       "sort_passes": sum(1 for k in stage_ms if k.startswith("sort_pass")),
+                       "how": "lbvh_tree_autotune on these inputs before the warm-up (sort choice: tile "
+                              "shape = choice % half the choices; the second half sorts one top byte fewer "
+                              "for codes wider than 30 bits)"},
             "build_mprims_s": n / (build_ms * 1e-3) / 1e6,
             "query_mqueries_s": nq / (query_ms * 1e-3) / 1e6,
             "build_ms": build_ms,

@@ -544,7 +544,12 @@ uint64_t lbvh_kernel_launches(void);
  *   sort variant  the radix sort's tile shape (keys per thread, CTAs per SM)
  *                 and how a warp finds the lanes sharing a digit (eight
  *                 ballots, or a per-warp table in shared memory), an index
- *                 in [0, lbvh_sort_variant_count());
+ *                 in [0, lbvh_sort_variant_count()): with V =
+ *                 lbvh_sort_variant_count() / 2, variant v takes tile shape
+ *                 v % V, and for codes wider than 30 bits v >= V sorts one
+ *                 byte (one pass) fewer of the codes' top bits, leaving more
+ *                 elements in runs of equal sorted bits for the runs stage
+ *                 (Sec. 3.1 step 2 either way: the same sorted order);
  *   walk variant  how Algorithm 1's collecting walk runs: 0 one thread per
  *                 query, 1/2/3 groups of 8/16/32 lanes walking the union of
  *                 their queries' paths together (lbvh_walk_variant_count()).
@@ -556,7 +561,7 @@ int lbvh_sort_variant_count(void);
 int lbvh_walk_variant_count(void);
 
 /* Times every sort variant on this build (two builds each, device time of
- * the sort passes) and, when nq > 0, every walk variant on these queries
+ * the sort passes and the runs stage) and, when nq > 0, every walk variant on these queries
  * (two runs each, device time of the collecting walk), stores the fastest of
  * each in the cache and leaves the tree built with the chosen sort variant.
  * Arguments as lbvh_build and lbvh_query_into; sort_variant / walk_variant

@@ -802,13 +802,17 @@ lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
         // index) to run_code_sort
         const bool packed = morton_bits <= 30;
         const int ib = top_index_bits(n);
+        // the sort choice: tile shape, and whether the top-bits sort covers
+        // one byte fewer (more elements in runs of equal sorted bits)
+        const int choice = t->sort_choice >= 0 ? t->sort_choice : tune_sort_choice(n, morton_bits, kind, 1);
+        const int variant = sort_choice_tile(choice);
+        const int skip = packed ? 0 : sort_choice_skip(choice);
         launch_encode(d_prims, n, kind, morton_bits, t->bounds.as<float>(), t->keys[0].as<uint64_t>(),
-                      t->hist.as<uint32_t>(), 1, packed ? kCodeLow : kCodeTop, ib, s);
+                      t->hist.as<uint32_t>(), 1, packed ? kCodeLow : kCodeTop, ib, s, skip);
         t->prof.end(LBVH_STAGE_ENCODE, s);
         LBVH_LAUNCHED();
         SortScratch scratch{t->hist.as<uint32_t>(), t->lookback.as<uint32_t>(), sort_tiles_max(n) * kRadix};
         nvtxRangePushA("sort");
-        const int variant = t->sort_choice >= 0 ? t->sort_choice : tune_sort_choice(n, morton_bits, kind, 1);
         cudaEvent_t(*pass_events)[2] = t->prof.on ? &t->prof.ev[LBVH_STAGE_SORT0] : nullptr;
         // the node records are written by the construct only: until then they
         // hold run_code_sort's 2n scratch words
@@ -818,10 +822,10 @@ lbvh_status build_impl(lbvh_tree_t t, const float *d_prims, int64_t n, int kind,
                    : run_code_sort(d_prims, kind, morton_bits, t->bounds.as<float>(), n, t->keys[0].as<uint64_t>(),
                                    t->keys[1].as<uint64_t>(), t->vals[0].as<uint32_t>(), t->vals[1].as<uint32_t>(),
                                    t->nodes.as<uint32_t>(), scratch, c, s, pass_events,
-                                   t->prof.on ? t->prof.ev[LBVH_STAGE_SORTRUNS] : nullptr, variant);
+                                   t->prof.on ? t->prof.ev[LBVH_STAGE_SORTRUNS] : nullptr, variant, skip);
         nvtxRangePop();
         if (t->prof.on) {
-            const int sorted = packed ? passes : kMaxPasses - ib / kRadixBits;
+            const int sorted = packed ? passes : kMaxPasses - top_first_byte(ib, skip);
             for (int p = 0; p < sorted; ++p) t->prof.recorded[LBVH_STAGE_SORT0 + p] = true;
             if (!packed) t->prof.recorded[LBVH_STAGE_SORTRUNS] = true;
         }
@@ -1628,7 +1632,7 @@ void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s) {
 extern "C" {
 
 lbvh_status lbvh_tree_set_tuning(lbvh_tree_t t, int sort_variant, int walk_variant) {
-    if (!t || sort_variant < -1 || sort_variant >= lbvh::sort_variant_count() || walk_variant < -1 ||
+    if (!t || sort_variant < -1 || sort_variant >= lbvh::build_sort_choices() || walk_variant < -1 ||
         walk_variant >= lbvh::kWalkKinds)
         return LBVH_ERR_INVALID;
     t->sort_choice = sort_variant;
@@ -1679,14 +1683,19 @@ lbvh_status lbvh_tree_autotune(lbvh_tree_t t, const float *d_prims, int64_t n, i
         t->prof.on = prof_was;
         return r;
     };
-    // the sort: every variant on this build's own keys, the best of two runs each
+    // the sort: every choice on this build's own keys (tile shapes; for codes
+    // wider than 30 bits also one top-bits pass fewer), the best of two runs
+    // each, timed over the passes and the runs stage
     float best_sort = 1e30f;
     int pick_sort = 0;
-    for (int v = 0; v < sort_variant_count() && n > 0; ++v) {
+    const int choices = morton_bits <= 30 ? sort_variant_count() : build_sort_choices();
+    for (int v = 0; v < choices && n > 0; ++v) {
         t->sort_choice = v;
         for (int rep = 0; rep < 2; ++rep) {
             if ((st = lbvh_build(t, d_prims, n, kind, morton_bits, stream)) != LBVH_OK) return finish(st);
-            const float ms = stages_ms(t, LBVH_STAGE_SORT0, LBVH_STAGE_SORT0 + sort_passes(morton_bits));
+            const float mp = stages_ms(t, LBVH_STAGE_SORT0, LBVH_STAGE_SORT0 + kMaxPasses);
+            const float mr = stages_ms(t, LBVH_STAGE_SORTRUNS, LBVH_STAGE_SORTRUNS + 1);
+            const float ms = mp < 0.0f || mr < 0.0f ? -1.0f : mp + mr;
             if (ms < 0.0f) return finish(LBVH_ERR_CUDA);
             if (ms < best_sort) {
                 best_sort = ms;

@@ -150,18 +150,22 @@ uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_out,
 // The sort of a build's codes of more than 32 bits, first step: keys_a
 // holds words (code >> (index_bits - 1)) << index_bits | index (the code's
 // top 64 - index_bits bits above the index, n <= 2^index_bits), sorted on
-// bytes index_bits / 8 .. 7 (the index bits inside the lowest of them only
-// follow the index order the words are already in). Returns the buffer
-// holding the sorted words; the other one is free. hist[0..256) must hold
-// the first pass's digit counts and the rest of hist must be zero.
-uint64_t *run_top_sort(uint64_t *keys_a, uint64_t *keys_b, int64_t n, int index_bits, const SortScratch &scratch,
-                       Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2] = nullptr,
-                       int variant_idx = -1);
+// bytes top_first_byte(index_bits, skip) .. 7: with skip 0 from the byte
+// holding the code's lowest bit in the word (the index bits inside it only
+// follow the index order the words are already in), with skip 1 one byte
+// (one pass) fewer. The words come out ordered by their bits from
+// top_run_shift(index_bits, skip) up, and in index order where those are
+// equal. Returns the buffer holding the sorted words; the other one is free.
+// hist[0..256) must hold the first pass's digit counts and the rest of hist
+// must be zero.
+uint64_t *run_top_sort(uint64_t *keys_a, uint64_t *keys_b, int64_t n, int index_bits, int skip,
+                       const SortScratch &scratch, Control *ctl, cudaStream_t s,
+                       cudaEvent_t (*pass_events)[2] = nullptr, int variant_idx = -1);
 // The whole sort of a build's codes of more than 32 bits (runs.cu): keys_a
-// holds the encoder's kCodeTop words (index bits top_index_bits(n)); the
-// top bits are sorted by run_top_sort, then the runs of equal top bits are
-// put in code order (their codes derived again from prims with the scene
-// bounds and bits / 3 bits per axis). Returns vals_a, which then holds the
+// holds the encoder's kCodeTop words (index bits top_index_bits(n)); their
+// top bits are sorted by run_top_sort (skip: as there), then the runs of
+// equal sorted bits are put in code order (their codes derived again from
+// prims with the scene bounds and bits / 3 bits per axis). Returns vals_a, which then holds the
 // permutation; keys_a, keys_b, vals_b and scratch (2n words) are used on the
 // way. The hist, look-back and control words as for the other sorts.
 // scratch: code_sort_scratch_words(n) words.
@@ -170,7 +174,7 @@ int64_t code_sort_scratch_words(int64_t n);
 uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bounds, int64_t n, uint64_t *keys_a,
                         uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, uint32_t *scratch,
                         const SortScratch &sc, Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2],
-                        cudaEvent_t *runs_events, int variant_idx);
+                        cudaEvent_t *runs_events, int variant_idx, int skip);
 // A key + payload sort of the first *count (device) pairs, at most n_max,
 // over the low key_bits bits: a fixed grid of CTAs per pass takes tiles by
 // ticket up to the count it reads on the device. hist and the look-back as
@@ -180,6 +184,12 @@ bool run_counted_sort(uint64_t *keys_a, uint32_t *vals_a, uint64_t *keys_b, uint
                       const uint32_t *count, int64_t n_max, int key_bits, const SortScratch &scratch, Control *ctl,
                       cudaStream_t s);
 int sort_variant_count();
+// A tree build's sort choice c (the tuner's index, lbvh_tree_set_tuning):
+// tile shape c % sort_variant_count() and, for codes wider than 30 bits,
+// skip = c / sort_variant_count() (run_top_sort sorts one byte fewer when 1).
+inline int build_sort_choices() { return 2 * sort_variant_count(); }
+inline int sort_choice_tile(int c) { return c < 0 ? -1 : c % sort_variant_count(); }
+inline int sort_choice_skip(int c) { return c < 0 ? 0 : c / sort_variant_count(); }
 // Test hook (lbvh_test_hold_sort_tile): tile `tile` of every sort's first pass
 // publishes nothing, so later tiles' bounded look-back waits run out; -1: off.
 void sort_set_hold_tile(int64_t tile);
@@ -205,8 +215,24 @@ inline int top_index_bits(int64_t n) {
     while (ib < 62 && (int64_t(1) << ib) < n) ++ib;
     return ib;
 }
+// The first byte run_top_sort sorts, and the run shift: the sorted words are
+// ordered by their bits from the run shift up (the code's bits from
+// shift - 1 up; below the shift, index order). skip 1 starts one byte
+// higher, which is taken only while the in-run keys (the code's low
+// shift - 1 bits above the index_bits-bit index) fit 64 bits.
+__host__ __device__ inline int top_first_byte(int index_bits, int skip) {
+    const int first = index_bits / kRadixBits;
+    const bool ok = skip > 0 && first + 1 < kMaxPasses && kRadixBits * (first + 1) - 1 + index_bits <= 64;
+    return ok ? first + 1 : first;
+}
+__host__ __device__ inline int top_run_shift(int index_bits, int skip) {
+    const int first = top_first_byte(index_bits, skip);
+    return first == index_bits / kRadixBits ? index_bits : kRadixBits * first;
+}
+// skip (kCodeTop): the histogram counts byte top_first_byte(index_bits, skip).
 void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint64_t *codes, uint32_t *hist, int hist_passes, int layout, int index_bits, cudaStream_t s);
+                   uint64_t *codes, uint32_t *hist, int hist_passes, int layout, int index_bits, cudaStream_t s,
+                   int skip = 0);
 // codes[i] = the Morton code of primitive perm[i].
 void launch_sorted_codes(const float *prims, const uint32_t *perm, int64_t n, int kind, int bits,
                          const float *bounds, uint64_t *codes, cudaStream_t s);

@@ -171,15 +171,16 @@ __global__ void __launch_bounds__(kThreads)
 // index in the key's low half); kCodeTop the word (code >> (ib - 1)) << ib |
 // index (the code's top 64 - ib bits above the index, n <= 2^ib). The
 // histograms count the bytes of the code (plain, low) or of the word from
-// byte ib / 8 on (top): the bytes the sort's passes take in turn.
+// byte top_first_byte(ib, skip) on (top): the bytes the sort's passes take
+// in turn.
 template <int kKind, int kLayout>
 __global__ void __launch_bounds__(kThreads)
     encode_kernel(const float *__restrict__ prims, int64_t n, int b, const float *__restrict__ bounds,
-                  uint64_t *__restrict__ codes, uint32_t *__restrict__ hist, int passes, int ib) {
+                  uint64_t *__restrict__ codes, uint32_t *__restrict__ hist, int passes, int ib, int skip) {
     __shared__ uint32_t s_hist[kMaxPasses * kRadix];
     for (int k = threadIdx.x; k < passes * kRadix; k += kThreads) s_hist[k] = 0;
     const Grid3 g = make_grid(bounds, b);
-    const int hist_shift = kLayout == kCodeTop ? kRadixBits * (ib / kRadixBits) : 0;
+    const int hist_shift = kLayout == kCodeTop ? kRadixBits * top_first_byte(ib, skip) : 0;
     __syncthreads();
     for_each_centroid<kKind>(prims, n, [&](int64_t i, float x, float y, float z) {
         const uint64_t c = morton(x, y, z, g);
@@ -367,17 +368,18 @@ void launch_bounds(const float *prims, int64_t n, int kind, float *partials, flo
 }
 
 void launch_encode(const float *prims, int64_t n, int kind, int bits, const float *bounds,
-                   uint64_t *codes, uint32_t *hist, int hist_passes, int layout, int index_bits, cudaStream_t s) {
+                   uint64_t *codes, uint32_t *hist, int hist_passes, int layout, int index_bits, cudaStream_t s,
+                   int skip) {
     const int blocks = bounds_blocks(n);
     const int b = bits / 3;
-    using Kernel = void (*)(const float *, int64_t, int, const float *, uint64_t *, uint32_t *, int, int);
+    using Kernel = void (*)(const float *, int64_t, int, const float *, uint64_t *, uint32_t *, int, int, int);
     static const Kernel table[2][3] = {
         {encode_kernel<LBVH_PRIM_POINTS, kCodePlain>, encode_kernel<LBVH_PRIM_POINTS, kCodeLow>,
          encode_kernel<LBVH_PRIM_POINTS, kCodeTop>},
         {encode_kernel<LBVH_PRIM_BOXES, kCodePlain>, encode_kernel<LBVH_PRIM_BOXES, kCodeLow>,
          encode_kernel<LBVH_PRIM_BOXES, kCodeTop>}};
     table[kind == LBVH_PRIM_POINTS ? 0 : 1][layout]<<<blocks, kThreads, 0, s>>>(prims, n, b, bounds, codes, hist,
-                                                                               hist_passes, index_bits);
+                                                                               hist_passes, index_bits, skip);
     count_launches(1);
 }
 

@@ -55,11 +55,11 @@ __device__ __forceinline__ uint64_t code_of(const float *prims, uint32_t i, cons
     return morton(x, y, z, g);
 }
 
-// The in-run key of the primitive with index idx: its code's low ib - 1 bits
-// above the index.
+// The in-run key of the primitive with index idx: the code bits below the
+// sorted ones (its low rs - 1 bits, rs the run shift) above the index.
 template <int kKind>
-__device__ __forceinline__ uint64_t run_key(const float *prims, uint32_t idx, const Grid3 &g, int ib) {
-    const uint64_t low = code_of<kKind>(prims, idx, g) & ((1ull << (ib - 1)) - 1ull);
+__device__ __forceinline__ uint64_t run_key(const float *prims, uint32_t idx, const Grid3 &g, int ib, int rs) {
+    const uint64_t low = code_of<kKind>(prims, idx, g) & ((1ull << (rs - 1)) - 1ull);
     return low << ib | idx;
 }
 
@@ -71,7 +71,7 @@ __device__ __forceinline__ uint64_t run_key(const float *prims, uint32_t idx, co
 // then), or lists a longer one.
 template <int kKind>
 __global__ void __launch_bounds__(kThreads)
-    runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, const float *__restrict__ prims,
+    runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, int rs, const float *__restrict__ prims,
                 const float *__restrict__ bounds, int b, uint32_t *__restrict__ perm, uint32_t *__restrict__ long_list,
                 uint32_t *long_count, uint32_t *flags) {
     constexpr int kSpan = kThreads * kPer;
@@ -100,9 +100,9 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int64_t p = p0 + k;
-            const uint64_t top = w[k] >> ib;
-            const bool eq_prev = p > 0 && ((k > 0 ? w[k - 1] : left) >> ib) == top;
-            const bool eq_next = p + 1 < n && ((k + 1 < kPer ? w[k + 1] : right) >> ib) == top;
+            const uint64_t top = w[k] >> rs;
+            const bool eq_prev = p > 0 && ((k > 0 ? w[k - 1] : left) >> rs) == top;
+            const bool eq_next = p + 1 < n && ((k + 1 < kPer ? w[k + 1] : right) >> rs) == top;
             if (p < n && (eq_prev || eq_next)) member |= 1u << k;
             if (p < n && !eq_prev && eq_next) head |= 1u << k;
         }
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kThreads)
         if (member & (1u << k)) {
             const uint32_t idx = (uint32_t)w[k] & imask;
             uint64_t key = 0;
-            if ((int64_t)idx < n) key = run_key<kKind>(prims, idx, g, ib);
+            if ((int64_t)idx < n) key = run_key<kKind>(prims, idx, g, ib, rs);
             else atomicOr(flags, kFlagCorrupt);  // only after a timed-out pass
             s_key[threadIdx.x * kPer + k] = key;
         }
@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(kThreads)
         int len = 1;
         while (k + len < kPer && (member >> (k + len) & 1u) && !(head >> (k + len) & 1u)) ++len;
         if (k + len == kPer) {
-            const uint64_t top = words[s] >> ib;  // (not w[k]: a variable index would put w in local memory)
-            while (len <= kShortRun && s + len < n && (words[s + len] >> ib) == top) ++len;
+            const uint64_t top = words[s] >> rs;  // (not w[k]: a variable index would put w in local memory)
+            while (len <= kShortRun && s + len < n && (words[s + len] >> rs) == top) ++len;
         }
         if (len > kShortRun) {
             const uint32_t slot = atomicAdd(long_count, 1u);
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads)
                 key[i] = s_key[p - cta0];
             } else {
                 const uint32_t idx = (uint32_t)words[p] & imask;
-                key[i] = (int64_t)idx < n ? run_key<kKind>(prims, idx, g, ib) : 0ull;
+                key[i] = (int64_t)idx < n ? run_key<kKind>(prims, idx, g, ib, rs) : 0ull;
             }
         }
         for (int i = 1; i < len; ++i) {  // insertion sort: runs are short
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads)
 // kLongRun raises *fallback instead.
 template <int kKind>
 __global__ void __launch_bounds__(kThreads)
-    long_runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, const float *__restrict__ prims,
+    long_runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, int rs, const float *__restrict__ prims,
                      const float *__restrict__ bounds, int b, uint32_t *__restrict__ perm,
                      const uint32_t *__restrict__ long_list, const uint32_t *long_count, uint32_t *fallback,
                      uint32_t *flags) {
@@ -196,13 +196,13 @@ __global__ void __launch_bounds__(kThreads)
             if (threadIdx.x == 0) atomicOr(flags, kFlagCorrupt);
             continue;
         }
-        const uint64_t top = words[s] >> ib;
+        const uint64_t top = words[s] >> rs;
         if (threadIdx.x == 0) s_len = kLongRun + 1;
         __syncthreads();
         // the run's end: the first position after s whose top differs
         for (int off = 1; off <= kLongRun; off += kThreads) {
             const int o = off + (int)threadIdx.x;
-            const bool end = o <= kLongRun && (s + o >= n || (words[s + o] >> ib) != top);
+            const bool end = o <= kLongRun && (s + o >= n || (words[s + o] >> rs) != top);
             if (end) atomicMin(&s_len, o);
             if (__syncthreads_or(end)) break;
         }
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kThreads)
             uint64_t k = ~0ull;
             if (i < len) {
                 const uint32_t idx = (uint32_t)words[s + i] & imask;
-                if ((int64_t)idx < n) k = run_key<kKind>(prims, idx, g, ib);
+                if ((int64_t)idx < n) k = run_key<kKind>(prims, idx, g, ib, rs);
                 else atomicOr(flags, kFlagCorrupt);  // only after a timed-out pass
             }
             key[i] = k;
@@ -283,10 +283,11 @@ int64_t code_sort_scratch_words(int64_t n) { return n + n / (kShortRun + 1) + 1;
 uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bounds, int64_t n, uint64_t *keys_a,
                         uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, uint32_t *scratch,
                         const SortScratch &sc, Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2],
-                        cudaEvent_t *runs_events, int variant_idx) {
+                        cudaEvent_t *runs_events, int variant_idx, int skip) {
     if (n <= 0) return vals_a;
     const int ib = top_index_bits(n);
-    uint64_t *words = run_top_sort(keys_a, keys_b, n, ib, sc, ctl, s, pass_events, variant_idx);
+    const int rs = top_run_shift(ib, skip);
+    uint64_t *words = run_top_sort(keys_a, keys_b, n, ib, skip, sc, ctl, s, pass_events, variant_idx);
     uint64_t *codes = words == keys_a ? keys_b : keys_a;
     uint32_t *perm = vals_a, *index_alt = scratch, *long_list = scratch + n;
     if (runs_events) cudaEventRecord(runs_events[0], s);
@@ -296,10 +297,11 @@ uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bou
     cudaMemsetAsync(&ctl->run_long, 0, 3 * sizeof(uint32_t), s);
     const int64_t blocks = (n + (int64_t)kThreads * kPer - 1) / ((int64_t)kThreads * kPer);
     (points ? runs_kernel<LBVH_PRIM_POINTS> : runs_kernel<LBVH_PRIM_BOXES>)<<<(unsigned)blocks, kThreads, 0, s>>>(
-        words, n, ib, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->build_flags);
+        words, n, ib, rs, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->build_flags);
     const int sms = device_sm_count();
     (points ? long_runs_kernel<LBVH_PRIM_POINTS> : long_runs_kernel<LBVH_PRIM_BOXES>)<<<sms * 2, kThreads, 0, s>>>(
-        words, n, ib, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->run_fallback, &ctl->build_flags);
+        words, n, ib, rs, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->run_fallback,
+        &ctl->build_flags);
     // the fallback (each kernel leaves at once unless a run was too long)
     (points ? fallback_keys_kernel<LBVH_PRIM_POINTS> : fallback_keys_kernel<LBVH_PRIM_BOXES>)<<<sms * 4, kThreads, 0,
                                                                                                s>>>(

@@ -656,10 +656,11 @@ uint32_t *run_index_sort(uint64_t *keys_a, uint64_t *keys_b, uint32_t *vals_out,
     return vals_out;
 }
 
-uint64_t *run_top_sort(uint64_t *keys_a, uint64_t *keys_b, int64_t n, int index_bits, const SortScratch &scratch,
-                       Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2], int variant_idx) {
+uint64_t *run_top_sort(uint64_t *keys_a, uint64_t *keys_b, int64_t n, int index_bits, int skip,
+                       const SortScratch &scratch, Control *ctl, cudaStream_t s, cudaEvent_t (*pass_events)[2],
+                       int variant_idx) {
     if (n <= 0) return keys_a;
-    const int first = index_bits / kRadixBits;  // the byte holding the key's lowest bit
+    const int first = top_first_byte(index_bits, skip);
     const int passes = kMaxPasses - first;
     Pass ps[kMaxPasses];
     uint64_t *kb[2] = {keys_a, keys_b};

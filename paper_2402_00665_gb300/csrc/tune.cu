@@ -4,9 +4,10 @@
 // trees (ceil(log2 n)), the Morton bits, the primitive kind, the query kind
 // (-1 for the sort of a build) and the number of trees built together (1 for
 // a single tree, the instance count of a batch). It records the sort's tile
-// shape and ranking (a variant of sort.cu's table) and how the collecting
-// walk runs (one thread per query, or groups of 8, 16 or 32 lanes), each
-// with the time it measured. lbvh_tree_autotune and the batch path fill the
+// shape and ranking (a variant of sort.cu's table; for a single tree's codes
+// wider than 30 bits, also whether the top-bits sort takes one pass fewer)
+// and how the collecting walk runs (one thread per query, or groups of 8, 16
+// or 32 lanes), each with the time it measured. lbvh_tree_autotune and the batch path fill the
 // cache by timing every candidate on the caller's own data; builds and
 // queries look their configuration up and fall back to the defaults. The
 // cache can be written to and read from a small JSON file, so a process can
@@ -230,9 +231,11 @@ lbvh_status lbvh_tune_load(const char *path) {
             return LBVH_ERR_INVALID;
         }
     }
-    int sorts = lbvh::sort_variant_count();
     for (auto &e : got_entries) {
-        // a variant index this build of the library does not have is dropped
+        // a choice this build of the library does not have is dropped (a
+        // batch's sort takes a tile shape alone, a single tree's build also
+        // the top-bits pass count)
+        const int sorts = e.first.instances > 1 ? lbvh::sort_variant_count() : lbvh::build_sort_choices();
         if (e.second.sort >= sorts) e.second.sort = -1;
         if (e.second.walk >= lbvh::kWalkKinds) e.second.walk = -1;
         lbvh::tune_put(e.first, e.second);
@@ -250,7 +253,7 @@ int lbvh_tune_entries(void) {
     return (int)lbvh::g_cache.size();
 }
 
-int lbvh_sort_variant_count(void) { return lbvh::sort_variant_count(); }
+int lbvh_sort_variant_count(void) { return lbvh::build_sort_choices(); }
 
 int lbvh_walk_variant_count(void) { return lbvh::kWalkKinds; }
 

@@ -56,9 +56,18 @@ def test_full_uniform_points_2pow25_63bit():
     r = inputs.radius_for_neighbours(N)
     dpts = torch.from_numpy(pts).cuda()
     dq = dpts.clone()
-    t = lbvh.Tree().build(dpts, lbvh.POINTS, 63)
-    t.check()
     o = oracle.build(pts, oracle.POINTS, 63)
+    # the top-bits sort over 4 bytes instead of 5 (the tuner's choice here:
+    # 0.8% of the points in runs of equal top 32 code bits), then the default
+    skip1 = lbvh.sort_variant_count() // 2
+    t = lbvh.Tree()
+    t.set_tuning(skip1, -1)
+    t.build(dpts, lbvh.POINTS, 63)
+    t.check()
+    assert_tree_equal(t.export(), o)
+    t.set_tuning(-1, -1)
+    t.build(dpts, lbvh.POINTS, 63)
+    t.check()
     assert_tree_equal(t.export(), o)
     off, hits = t.query(dq, lbvh.SPHERE, radius=float(r), capacity=20 * N)
     sample = np.random.default_rng(7).choice(N, size=4096, replace=False)
@@ -77,11 +86,18 @@ def test_full_mixture_boxes_2pow25(bits):
     from paper_2402_00665_gb300 import lbvh
     boxes = inputs.gaussian_mixture_boxes(N, seed=0)
     queries = inputs.gaussian_mixture_boxes(N // 2, seed=1, component_seed=0)
-    t = lbvh.Tree().build(boxes, lbvh.BOXES, bits)
-    t.check()
     o = oracle.build(boxes, oracle.BOXES, bits)
     if bits == 30:
         assert len(np.unique(o["sorted"])) < N // 2  # many duplicate codes: tie-break stress
+    t = lbvh.Tree()
+    if bits == 63:  # the top-bits sort one byte shorter: most boxes in runs
+        t.set_tuning(lbvh.sort_variant_count() // 2, -1)
+        t.build(boxes, lbvh.BOXES, bits)
+        t.check()
+        assert_tree_equal(t.export(), o)
+        t.set_tuning(-1, -1)
+    t.build(boxes, lbvh.BOXES, bits)
+    t.check()
     assert_tree_equal(t.export(), o)
     off, hits = t.query(torch.from_numpy(queries).cuda(), lbvh.BOX, capacity=16 * N)
     sample = np.random.default_rng(8).choice(N // 2, size=2048, replace=False)
