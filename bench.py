@@ -61,12 +61,14 @@ UNIT = "Mprims/s"
 #               written (the store words and sibling boxes of the nodes inside
 #               a CTA's leaves stay in shared memory)
 #   query walk  query 12 read, count 4 written, 4 per hit kept, tree read once (48 B/leaf)
-#   query copy  count/start/offset read per query, 4 per hit read and 4 written
+#   query copy  count 4 and offset 8 read per query, 4 per hit read and 4 written
 def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_queries: bool = False,
-              long_lists: tuple = (0, 0)):
+              long_lists: tuple = (0, 0), order_passes: int = 4):
     """Algorithmic bytes of one launch of a stage (the data the method must
     move): pb = bytes of a primitive, lb = of a leaf record, qb = of a query;
-    long_lists = (queries with more hits than the walk keeps, their hits)."""
+    long_lists = (queries with more hits than the walk keeps, their hits);
+    order_passes = sort passes of the query order (4 for 30-bit order codes,
+    3 for 24-bit ones, the tuner's choice)."""
     knn = box_queries == "knn"
     qb = 32 if box_queries == "ray" else (24 if box_queries and not knn else 12)
     pb, lb = (24, 32) if boxes else (12, 16)
@@ -77,12 +79,12 @@ def alg_bytes(stage: str, n: int, nq: int, hits: int, boxes: bool = False, box_q
         "sort_runs": 12 * n,
         # codes, perm, primitive read; leaf + internal node write
         "construct": (8 + 4 + pb + lb + 32) * n,
-        # query + count/position per query, each kept hit, the tree once
+        # query + count per query, each kept hit, the tree once
         # (kNN: the query, index and squared distance of each neighbour, the tree once)
-        "query_walk": (qb * nq + 8 * hits if knn else (qb + 8) * nq + 4 * hits) + (32 + lb) * n,
-        "query_order": (qb + 4 + 4 * 16) * nq,  # 30-bit order codes as 32-bit keys: 4 sort passes
+        "query_walk": (qb * nq + 8 * hits if knn else (qb + 4) * nq + 4 * hits) + (32 + lb) * n,
+        "query_order": (qb + 4 + order_passes * 16) * nq,  # order codes packed with the index
         "query_scan": 4 * nq + 8 * (nq + 1),
-        "query_copy": 16 * nq + 8 * hits,
+        "query_copy": 12 * nq + 8 * hits,
         # the second walk of the long lists: query + offsets, hits written, then sorted in place
         "query_overflow": (qb + 16) * long_lists[0] + 12 * long_lists[1],
     }
@@ -569,7 +571,8 @@ def run_gpu(args, world, rank, local):
         lens = offsets[1:] - offsets[:-1]
         long_mask = lens > 64  # the walk keeps 64 hits per query; longer lists walk again
         long_lists = (int(long_mask.sum().item()), int(lens[long_mask].sum().item()))
-    alg = {k: alg_bytes(k, n, nq, total_hits, boxes, box_queries, long_lists) for k in stage_ms
+    order_passes = 3 if tune_walk >= lbvh.walk_variant_count() // 2 else 4
+    alg = {k: alg_bytes(k, n, nq, total_hits, boxes, box_queries, long_lists, order_passes) for k in stage_ms
            if alg_bytes(k, n, nq, total_hits) is not None}
     achieved = alg[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
     build_model = model_build_bytes(n, bits, boxes)
@@ -695,9 +698,11 @@ def run_gpu(args, world, rank, local):
             "launches_per_step": launches / args.steps,
             "tuning": {"sort_variant": tune_sort, "walk_variant": tune_walk,
                        "sort_passes": sum(1 for k in stage_ms if k.startswith("sort_pass")),
+                       "query_order_bits": 24 if order_passes == 3 else 30,
                        "how": "lbvh_tree_autotune on these inputs before the warm-up (sort choice: tile "
                               "shape = choice % half the choices; the second half sorts one top byte fewer "
-                              "for codes wider than 30 bits)"},
+                              "for codes wider than 30 bits; walk choice: kind = choice % half, the second "
+                              "half orders the queries by 24-bit instead of 30-bit Morton codes)"},
             "build_mprims_s": n / (build_ms * 1e-3) / 1e6,
             "query_mqueries_s": nq / (query_ms * 1e-3) / 1e6,
             "build_ms": build_ms,

@@ -552,7 +552,10 @@ uint64_t lbvh_kernel_launches(void);
  *                 (Sec. 3.1 step 2 either way: the same sorted order);
  *   walk variant  how Algorithm 1's collecting walk runs: 0 one thread per
  *                 query, 1/2/3 groups of 8/16/32 lanes walking the union of
- *                 their queries' paths together (lbvh_walk_variant_count()).
+ *                 their queries' paths together; 4-7 the same with the
+ *                 queries put in the Morton order of 24-bit codes of their
+ *                 centres (one sort pass fewer) instead of 30-bit ones
+ *                 (lbvh_walk_variant_count() = 8).
  * A process-wide cache holds the choice for each configuration (the GPU's
  * name, ceil(log2 n), Morton bits, primitive kind, query kind, trees built
  * together); builds and queries use the cached choice for their
@@ -562,8 +565,9 @@ int lbvh_walk_variant_count(void);
 
 /* Times every sort variant on this build (two builds each, device time of
  * the sort passes and the runs stage) and, when nq > 0, every walk variant on these queries
- * (two runs each, device time of the collecting walk), stores the fastest of
- * each in the cache and leaves the tree built with the chosen sort variant.
+ * (two runs each, device time of the query order and the collecting walk),
+ * stores the fastest of each in the cache and leaves the tree built with the
+ * chosen sort variant.
  * Arguments as lbvh_build and lbvh_query_into; sort_variant / walk_variant
  * (nullable) receive the choices. Synchronises `stream`. */
 lbvh_status lbvh_tree_autotune(lbvh_tree_t tree, const float *d_prims, int64_t n, int kind, int morton_bits,

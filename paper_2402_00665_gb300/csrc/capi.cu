@@ -318,18 +318,18 @@ lbvh_status read_control(lbvh_tree_t t, cudaStream_t s) {
 }
 
 constexpr int64_t kOrderMinQueries = 2048;  // below this, walk in input order
-// Morton bits of the query order: 30 (4 sort passes). 24 bits saved a pass
-// on uniform queries at the same walk time, but on clustered queries (a
-// Gaussian mixture) the coarser cells cost more walk time than the pass;
-// order changes speed only.
+// Morton bits of the query order: 30 (4 sort passes) by default, or 24 (3
+// passes) as the tuner's choice. 24 bits walk uniform queries as fast as 30,
+// but on clustered queries (a Gaussian mixture) the coarser cells cost more
+// walk time than the pass saves; order changes speed only. Batches use 30.
 constexpr int order_bits() { return 30; }
 
 // The order in which threads take the queries: the Morton order of the query
-// centres inside the tree's bounds (encode + radix sort, the build's own
-// kernels). Queries that are the primitives of the last build (same pointer
-// and count) reuse the build's permutation. Order only changes speed, never
-// results.
-lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
+// centres inside the tree's bounds (encode + radix sort of `bits`-bit codes,
+// the build's own kernels). Queries that are the primitives of the last build
+// (same pointer and count) reuse the build's permutation. Order only changes
+// speed, never results.
+lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s, int bits = order_bits()) {
     using namespace lbvh;
     qa.order = nullptr;
     // rays are walked in the caller's order (a camera's rays are coherent as given)
@@ -348,20 +348,20 @@ lbvh_status query_order(lbvh_tree_t t, lbvh::QueryArgs &qa, cudaStream_t s) {
         LBVH_CUDA(t->qvals[k].ensure(unq * 4, s));
     }
     LBVH_CUDA(t->qlookback.ensure((size_t)sort_tiles_max(qa.nq) * kRadix * 4 * 2, s));
-    LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)sort_passes(order_bits()) * kRadix * 4, s));
+    LBVH_CUDA(cudaMemsetAsync(t->hist.p, 0, (size_t)sort_passes(bits) * kRadix * 4, s));
     const int as_prims = qa.qkind == LBVH_Q_SPHERE ? LBVH_PRIM_POINTS : LBVH_PRIM_BOXES;
-    launch_encode(qa.queries, qa.nq, as_prims, order_bits(), t->bounds.as<float>(), t->qkeys[0].as<uint64_t>(),
+    launch_encode(qa.queries, qa.nq, as_prims, bits, t->bounds.as<float>(), t->qkeys[0].as<uint64_t>(),
                   t->hist.as<uint32_t>(), 1, kCodeLow, 0, s);
     LBVH_LAUNCHED();
     SortScratch scratch{t->hist.as<uint32_t>(), t->qlookback.as<uint32_t>(), sort_tiles_max(qa.nq) * kRadix};
     qa.order = run_index_sort(t->qkeys[0].as<uint64_t>(), t->qkeys[1].as<uint64_t>(), t->qvals[0].as<uint32_t>(),
-                              qa.nq, order_bits(), scratch, t->dctl(), s);
+                              qa.nq, bits, scratch, t->dctl(), s);
     LBVH_LAUNCHED();
     return LBVH_OK;
 }
 
 lbvh::QueryScratch query_scratch(lbvh_tree_t t) {
-    return lbvh::QueryScratch{t->counts.as<uint2>(), t->slots.as<uint32_t>(), t->overflow.as<uint32_t>(),
+    return lbvh::QueryScratch{t->counts.as<uint32_t>(), t->slots.as<uint32_t>(), t->overflow.as<uint32_t>(),
                               t->spill_head.as<uint32_t>(), t->spill.as<uint32_t>(),
                               lbvh::spill_chunks_for(t->spill_nq)};
 }
@@ -372,7 +372,7 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     using namespace lbvh;
     LBVH_CUDA(cudaStreamWaitEvent(s, t->built, 0));
     const size_t unq = (size_t)qa.nq;
-    LBVH_CUDA(t->counts.ensure(unq * 8 + 8, s));
+    LBVH_CUDA(t->counts.ensure(unq * 4 + 4, s));
     LBVH_CUDA(t->overflow.ensure(unq * 4 + 4, s));
     LBVH_CUDA(t->spill_head.ensure(unq * 4 + 4, s));
     if (spill_chunks_for(qa.nq) > spill_chunks_for(t->spill_nq) || !t->spill.p) {
@@ -384,18 +384,19 @@ lbvh_status query_count(lbvh_tree_t t, lbvh::QueryArgs &qa, int64_t *d_offsets,
     Control *c = t->dctl();
     LBVH_CUDA(cudaMemsetAsync(&c->query_flags, 0, offsetof(Control, pad) - offsetof(Control, query_flags), s));
     t->prof.clear(LBVH_STAGE_QCOUNT, LBVH_STAGE_QORDER + 1);
+    const int choice = t->walk_choice >= 0 ? t->walk_choice : tune_walk_choice(t->n, t->bits, t->kind, qa.qkind, 1);
+    qa.walk = walk_choice_kind(choice);
     t->prof.begin(LBVH_STAGE_QORDER, s);
-    lbvh_status ost = query_order(t, qa, s);
+    lbvh_status ost = query_order(t, qa, s, walk_choice_order_bits(choice));
     t->prof.end(LBVH_STAGE_QORDER, s);
     if (ost != LBVH_OK) return ost;
     const QueryScratch qs = query_scratch(t);
-    qa.walk = t->walk_choice >= 0 ? t->walk_choice : tune_walk_choice(t->n, t->bits, t->kind, qa.qkind, 1);
     t->prof.begin(LBVH_STAGE_QCOUNT, s);
     launch_query_collect(t->view(), qa, qs, c, s);
     t->prof.end(LBVH_STAGE_QCOUNT, s);
     LBVH_LAUNCHED();
     t->prof.begin(LBVH_STAGE_QSCAN, s);
-    launch_exclusive_scan(qs.count_pos, qa.nq, d_offsets, t->tile_sums.as<int64_t>(), c, s);
+    launch_exclusive_scan(qs.counts, qa.nq, d_offsets, t->tile_sums.as<int64_t>(), c, s);
     t->prof.end(LBVH_STAGE_QSCAN, s);
     LBVH_LAUNCHED();
     lbvh_status st = read_control(t, s);
@@ -473,7 +474,7 @@ struct lbvh_batch_s {
     bool self_query = false, sorted_in_b = false;
     DevBuf prim_off, query_off, node_start, store_start, chunks, chunk_first, qchunks;
     DevBuf keys[2], vals[2], nodes, store, lookback, hist, partials, bounds, ctl;
-    DevBuf count_pos, slots, overflow, tile_sums, qkeys[2], qvals[2], qlookback, spill_head, spill;
+    DevBuf counts, slots, overflow, tile_sums, qkeys[2], qvals[2], qlookback, spill_head, spill;
     // Segmented-sort tile tables: row r (r < sort_variant_count(): that
     // variant; the last row: the default variant) holds count + 1 entries.
     DevBuf tile_first, qtile_first;
@@ -606,7 +607,7 @@ lbvh_status batch_setup(lbvh_batch_t b, cudaStream_t s) {
     LBVH_CUDA(b->hist.ensure((size_t)kMaxPasses * b->count * kRadix * 4 + 4, s));
     LBVH_CUDA(b->partials.ensure((size_t)b->nchunks * 32 + 32, s));
     LBVH_CUDA(b->bounds.ensure((size_t)b->count * 24 + 24, s));
-    LBVH_CUDA(b->count_pos.ensure(unq * 8 + 8, s));
+    LBVH_CUDA(b->counts.ensure(unq * 4 + 4, s));
     LBVH_CUDA(b->slots.ensure(unq * kQueryBufferHits * 4 + 16, s));
     LBVH_CUDA(b->overflow.ensure(unq * 4 + 4, s));
     LBVH_CUDA(b->spill_head.ensure(unq * 4 + 4, s));
@@ -662,10 +663,10 @@ lbvh_status batch_enqueue(lbvh_batch_t b, cudaStream_t s) {
                                        b->qpasses, scratch, c, s, nullptr, b->sort_variant, &seg);
         qa.order = b->qvals[in_b ? 1 : 0].as<uint32_t>();
     }
-    const QueryScratch qs{b->count_pos.as<uint2>(), b->slots.as<uint32_t>(), b->overflow.as<uint32_t>(),
+    const QueryScratch qs{b->counts.as<uint32_t>(), b->slots.as<uint32_t>(), b->overflow.as<uint32_t>(),
                           b->spill_head.as<uint32_t>(), b->spill.as<uint32_t>(), spill_chunks_for(b->NQ)};
     launch_batch_collect(b->nodes.as<float4>(), g.kind, bt, qa, qs, c, s);
-    launch_exclusive_scan(qs.count_pos, b->NQ, g.offsets, b->tile_sums.as<int64_t>(), c, s);
+    launch_exclusive_scan(qs.counts, b->NQ, g.offsets, b->tile_sums.as<int64_t>(), c, s);
     launch_query_copy_checked(qa, qs, g.offsets, g.hits, g.capacity, c, s);
     launch_batch_overflow(b->nodes.as<float4>(), g.kind, bt, qa, qs, c, g.offsets, g.hits, g.capacity, s);
     LBVH_LAUNCHED();
@@ -1408,7 +1409,7 @@ void lbvh_batch_destroy(lbvh_batch_t b) {
     b->drop_graph();
     for (DevBuf *d : {&b->prim_off, &b->query_off, &b->node_start, &b->store_start, &b->chunks, &b->chunk_first,
                       &b->qchunks, &b->keys[0], &b->keys[1], &b->vals[0], &b->vals[1], &b->nodes, &b->store,
-                      &b->lookback, &b->hist, &b->partials, &b->bounds, &b->ctl, &b->count_pos, &b->slots,
+                      &b->lookback, &b->hist, &b->partials, &b->bounds, &b->ctl, &b->counts, &b->slots,
                       &b->overflow, &b->tile_sums, &b->qkeys[0], &b->qkeys[1], &b->qvals[0], &b->qvals[1],
                       &b->qlookback, &b->tile_first, &b->qtile_first, &b->spill_head, &b->spill})
         d->release(s);
@@ -1633,7 +1634,7 @@ extern "C" {
 
 lbvh_status lbvh_tree_set_tuning(lbvh_tree_t t, int sort_variant, int walk_variant) {
     if (!t || sort_variant < -1 || sort_variant >= lbvh::build_sort_choices() || walk_variant < -1 ||
-        walk_variant >= lbvh::kWalkKinds)
+        walk_variant >= lbvh::kWalkChoices)
         return LBVH_ERR_INVALID;
     t->sort_choice = sort_variant;
     t->walk_choice = walk_variant;
@@ -1717,7 +1718,7 @@ lbvh_status lbvh_tree_autotune(lbvh_tree_t t, const float *d_prims, int64_t n, i
         DevBuf offsets;
         LBVH_CUDA(offsets.ensure((size_t)(nq + 1) * 8, s));
         float best_walk = 1e30f;
-        for (int w = 0; w < kWalkKinds; ++w) {
+        for (int w = 0; w < kWalkChoices; ++w) {
             t->walk_choice = w;
             for (int rep = 0; rep < 2; ++rep) {
                 QueryArgs qa{d_queries, nq, qkind, d_radii, radius, nullptr};
@@ -1727,7 +1728,10 @@ lbvh_status lbvh_tree_autotune(lbvh_tree_t t, const float *d_prims, int64_t n, i
                     offsets.release(s);
                     return finish(st);
                 }
-                const float ms = stages_ms(t, LBVH_STAGE_QCOUNT, LBVH_STAGE_QCOUNT + 1);
+                // the walk and the query order (whose bits are part of the choice)
+                const float mw = stages_ms(t, LBVH_STAGE_QCOUNT, LBVH_STAGE_QCOUNT + 1);
+                const float mo = stages_ms(t, LBVH_STAGE_QORDER, LBVH_STAGE_QORDER + 1);
+                const float ms = mw < 0.0f || mo < 0.0f ? -1.0f : mw + mo;
                 if (ms >= 0.0f && ms < best_walk) {
                     best_walk = ms;
                     pick_walk = w;

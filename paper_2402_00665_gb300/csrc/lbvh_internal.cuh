@@ -286,6 +286,12 @@ struct QueryArgs {
 // The collecting walk: one thread per query, or groups of 8, 16 or 32 lanes
 // walking together (walk_group in query.cu).
 enum : int { kWalkThread = 0, kWalkGroup8 = 1, kWalkGroup16 = 2, kWalkGroup32 = 3, kWalkKinds = 4 };
+// A tree's walk choice c (the tuner's index, lbvh_tree_set_tuning): walk kind
+// c % kWalkKinds, and the Morton bits of the query order: 30 (4 sort passes)
+// for c < kWalkKinds, 24 (3 passes) above.
+constexpr int kWalkChoices = 2 * kWalkKinds;
+inline int walk_choice_kind(int c) { return c < 0 ? kWalkThread : c % kWalkKinds; }
+inline int walk_choice_order_bits(int c) { return c >= kWalkKinds ? 24 : 30; }
 // Hits past a walk's slot go to chunks of kSpillChunkWords words taken from a
 // shared pool (word 0 links to the next chunk of the same walk, the rest
 // hold hits). When the pool runs out, the query walks a second time instead.
@@ -297,10 +303,10 @@ inline uint32_t spill_chunks_for(int64_t nq) {
 }
 
 struct QueryScratch {
-    uint2 *count_pos;         // nq: (hits of query q, walk position i of q)
-    uint32_t *slots;          // nq * kQueryBufferHits: first hits of walk position i, walk order
+    uint32_t *counts;         // nq: hits of query q
+    uint32_t *slots;          // nq * kQueryBufferHits: first hits of query q, in walk order
     uint32_t *overflow_list;  // nq: queries with more hits than a slot (kSpilledTag: no second walk)
-    uint32_t *spill_head;     // nq: first spill chunk of walk position i
+    uint32_t *spill_head;     // nq: first spill chunk of query q
     uint32_t *spill;          // spill_chunks * kSpillChunkWords
     uint32_t spill_chunks;
 };
@@ -317,12 +323,12 @@ constexpr int kKnnMaxK = 256;
 void launch_visits(const TreeView &t, const QueryArgs &q, unsigned long long *counts, Control *ctl, cudaStream_t s);
 void launch_knn(const TreeView &t, const uint64_t *codes, const float *bounds, int bits, const QueryArgs &q, int k,
                 uint32_t *out_idx, float *out_d2, Control *ctl, cudaStream_t s);
-// offsets[0..nq] = exclusive scan of count_pos[.].x (offsets[nq] = total =
+// offsets[0..nq] = exclusive scan of counts (offsets[nq] = total =
 // ctl->total).
 int64_t scan_tile_count(int64_t nq);
 // offsets[0..n) += base (a chunk's CSR offsets moved to its place in the whole)
 void launch_offsets_add(int64_t *offsets, int64_t n, int64_t base, cudaStream_t s);
-void launch_exclusive_scan(const uint2 *count_pos, int64_t nq, int64_t *offsets,
+void launch_exclusive_scan(const uint32_t *counts, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s);
 // Short lists from the scratch buffer to their CSR positions.
 void launch_query_copy(const QueryArgs &q, const QueryScratch &qs, const int64_t *offsets,

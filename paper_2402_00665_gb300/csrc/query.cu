@@ -25,11 +25,13 @@
 // visit the same nodes), and write results at the query's own index.
 //
 // CSR in one walk:
-//   collect   each thread walks sorted position i (query q = order[i]; K > 1
-//             adjacent positions in lock step is a tuning option) and writes
-//             up to kQueryBufferHits primitive ids, in walk order, into slot i
+//   collect   each thread walks sorted position i (query q = order[i]; groups
+//             of lanes walking together are a tuning option) and writes up
+//             to kQueryBufferHits primitive ids, in walk order, into slot q
 //             of a scratch array (no shared memory: L1 stays with the tree),
-//             and (hit count, i) at q.
+//             and the hit count at q. Slot q rather than slot i: the copy
+//             then reads the slots in order (copy 1.86 -> 1.45 ms on 2^25
+//             uniform points; the walk's stores are scattered either way).
 //   scan      exclusive scan of the counts -> offsets, total (host reads it).
 //   copy      in query order: each thread loads one slot of up to 32 hits
 //             into registers and sorts it with a bitonic network; the warp
@@ -268,7 +270,7 @@ __device__ __forceinline__ int64_t thread_query(const QueryArgs &qa, int64_t i) 
 }
 
 // Hits past a walk's slot: appended to chunks from the shared pool, the first
-// chunk recorded in spill_head[i], each chunk's word 0 linking to the next.
+// chunk recorded in spill_head[q], each chunk's word 0 linking to the next.
 // `cur` is the walk's current chunk (kNoChunk before the first); it becomes
 // kSpillFailed when the pool is exhausted, and the query then takes the
 // second walk.
@@ -307,7 +309,7 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
     uint32_t cur = kNoChunk;
     if (walk_ok) {
         const auto q = has_query ? QueryOf<kQ>::load(qa, qi) : typename QueryOf<kQ>::type{};
-        uint32_t *slot = qs.slots + i * kSlot;
+        uint32_t *slot = qs.slots + qi * kSlot;
         // kPairs: hits go to the slot two at a time (one 8-byte store; words
         // past the count are never read). Point trees, one tree: walk 16.19
         // -> 15.87 ms on 2^25 uniform points (held to 32 registers, with an
@@ -325,7 +327,7 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
                     buf.x = id;
                 }
             } else {
-                spill_put(qs, ctl, i, cnt, id, cur);
+                spill_put(qs, ctl, qi, cnt, id, cur);
             }
             ++cnt;
         };
@@ -339,7 +341,7 @@ __device__ __forceinline__ void collect_walk(const TreeView &t, const QueryArgs 
         if (!ok) atomicOr(&ctl->query_flags, kFlagCorrupt);
     }
     if (!has_query) return;
-    __stcs(qs.count_pos + qi, make_uint2(cnt, (uint32_t)i));  // streamed: keep L2 for the tree
+    __stcs(qs.counts + qi, cnt);  // streamed: keep L2 for the tree
     if (cnt > (uint32_t)kSlot)
         qs.overflow_list[atomicAdd(&ctl->overflow_filled, 1u)] =
             (uint32_t)qi | (cur != kSpillFailed ? kSpilledTag : 0u);
@@ -452,7 +454,7 @@ __device__ __forceinline__ void warp_sort64(uint32_t &v0, uint32_t &v1) {
 // step with lanes on consecutive hits. Lists of 33..64 hits are then sorted
 // and written by the whole warp, one after the other.
 __global__ void __launch_bounds__(kThreads)
-    copy_kernel(int64_t nq, const uint2 *__restrict__ count_pos, const int64_t *__restrict__ offsets,
+    copy_kernel(int64_t nq, const uint32_t *__restrict__ counts, const int64_t *__restrict__ offsets,
                 const uint32_t *__restrict__ slots, uint32_t *__restrict__ hits,
                 unsigned long long capacity, Control *ctl) {
     __shared__ uint32_t s_lists[kThreads / 32][32][kRegSort + 1];
@@ -465,10 +467,10 @@ __global__ void __launch_bounds__(kThreads)
     uint32_t c = 0, mid = 0;
     int64_t dst = 0, pos = 0;
     if (q < nq) {
-        const uint2 cp = count_pos[q];
-        c = cp.x > (uint32_t)kRegSort ? 0u : cp.x;
-        mid = cp.x > (uint32_t)kRegSort && cp.x <= (uint32_t)kSlot ? cp.x : 0u;  // longer: the overflow walk
-        pos = cp.y;
+        const uint32_t cq = counts[q];
+        c = cq > (uint32_t)kRegSort ? 0u : cq;
+        mid = cq > (uint32_t)kRegSort && cq <= (uint32_t)kSlot ? cq : 0u;  // longer: the overflow walk
+        pos = q;
         dst = offsets[q];
     }
     uint32_t mids = __ballot_sync(0xffffffffu, mid != 0);
@@ -564,13 +566,13 @@ __device__ __forceinline__ int64_t block_scan_exclusive(int64_t v, int64_t *s_wa
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-    scan_reduce_kernel(const uint2 *__restrict__ counts, int64_t nq, int64_t *tile_sums) {
+    scan_reduce_kernel(const uint32_t *__restrict__ counts, int64_t nq, int64_t *tile_sums) {
     __shared__ int64_t s_warp[kScanThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t sum = 0;
     for (int j = 0; j < kScanItems; ++j) {
         const int64_t i = base + j * kScanThreads + threadIdx.x;
-        if (i < nq) sum += counts[i].x;
+        if (i < nq) sum += counts[i];
     }
     int64_t total;
     block_scan_exclusive(sum, s_warp, total);
@@ -600,7 +602,7 @@ __global__ void __launch_bounds__(kScanThreads)
 // thread scans kScanItems consecutive counts, which it reads from and writes
 // back to shared memory (rows padded by one element against bank conflicts).
 __global__ void __launch_bounds__(kScanThreads)
-    scan_apply_kernel(const uint2 *__restrict__ counts, int64_t nq,
+    scan_apply_kernel(const uint32_t *__restrict__ counts, int64_t nq,
                       const int64_t *__restrict__ tile_sums, int64_t *__restrict__ offsets) {
     constexpr int kRow = kScanItems + 1;
     __shared__ int64_t s_warp[kScanThreads / 32];
@@ -612,7 +614,7 @@ __global__ void __launch_bounds__(kScanThreads)
     for (int j = 0; j < kScanItems; ++j) {
         const int p = j * kScanThreads + threadIdx.x;
         const int64_t i = base + p;
-        s_c[(p / kScanItems) * kRow + p % kScanItems] = i < nq ? counts[i].x : 0u;
+        s_c[(p / kScanItems) * kRow + p % kScanItems] = i < nq ? counts[i] : 0u;
     }
     __syncthreads();
     uint32_t c[kScanItems];
@@ -777,12 +779,11 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t q = e & ~kSpilledTag;
         const int64_t base = offsets[q];
         const int64_t m = offsets[q + 1] - base;
-        const uint32_t pos = qs.count_pos[q].y;
         uint32_t *dst = hits + base;
-        const uint32_t *slot = qs.slots + (int64_t)pos * kSlot;
+        const uint32_t *slot = qs.slots + (int64_t)q * kSlot;
         for (int k = lane; k < kSlot; k += 32) dst[k] = slot[k];
         int64_t done = kSlot;
-        uint32_t c = qs.spill_head[pos];
+        uint32_t c = qs.spill_head[q];
         while (done < m) {
             if (c >= qs.spill_chunks) break;  // cannot happen for a tagged list; guards the reads
             const uint32_t *chunk = qs.spill + (int64_t)c * kSpillChunkWords;
@@ -1061,7 +1062,7 @@ void launch_query_copy_checked(const QueryArgs &q, const QueryScratch &qs, const
                                uint32_t *hits, unsigned long long capacity, Control *ctl, cudaStream_t s) {
     if (q.nq <= 0) return;
     const unsigned blocks = (unsigned)((q.nq + kThreads - 1) / kThreads);
-    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, qs.count_pos, offsets, qs.slots, hits, capacity, ctl);
+    copy_kernel<<<blocks, kThreads, 0, s>>>(q.nq, qs.counts, offsets, qs.slots, hits, capacity, ctl);
     count_launches(1);
 }
 
@@ -1164,7 +1165,7 @@ void launch_offsets_add(int64_t *offsets, int64_t n, int64_t base, cudaStream_t 
     count_launches(1);
 }
 
-void launch_exclusive_scan(const uint2 *counts, int64_t nq, int64_t *offsets,
+void launch_exclusive_scan(const uint32_t *counts, int64_t nq, int64_t *offsets,
                            int64_t *tile_sums, Control *ctl, cudaStream_t s) {
     const int64_t tiles = scan_tile_count(nq);
     if (tiles > 0)

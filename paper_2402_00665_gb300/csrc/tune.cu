@@ -7,7 +7,8 @@
 // shape and ranking (a variant of sort.cu's table; for a single tree's codes
 // wider than 30 bits, also whether the top-bits sort takes one pass fewer)
 // and how the collecting walk runs (one thread per query, or groups of 8, 16
-// or 32 lanes), each with the time it measured. lbvh_tree_autotune and the batch path fill the
+// or 32 lanes, and the query order's Morton bits), each with the time it
+// measured. lbvh_tree_autotune and the batch path fill the
 // cache by timing every candidate on the caller's own data; builds and
 // queries look their configuration up and fall back to the defaults. The
 // cache can be written to and read from a small JSON file, so a process can
@@ -237,7 +238,7 @@ lbvh_status lbvh_tune_load(const char *path) {
         // the top-bits pass count)
         const int sorts = e.first.instances > 1 ? lbvh::sort_variant_count() : lbvh::build_sort_choices();
         if (e.second.sort >= sorts) e.second.sort = -1;
-        if (e.second.walk >= lbvh::kWalkKinds) e.second.walk = -1;
+        if (e.second.walk >= lbvh::kWalkChoices) e.second.walk = -1;
         lbvh::tune_put(e.first, e.second);
     }
     return LBVH_OK;
@@ -255,6 +256,6 @@ int lbvh_tune_entries(void) {
 
 int lbvh_sort_variant_count(void) { return lbvh::build_sort_choices(); }
 
-int lbvh_walk_variant_count(void) { return lbvh::kWalkKinds; }
+int lbvh_walk_variant_count(void) { return lbvh::kWalkChoices; }
 
 }  // extern "C"
