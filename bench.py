@@ -207,6 +207,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--server-slots", type=int, default=2,
                     help="worker slots of the request server (served workloads): batches in flight at once")
+    ap.add_argument("--tuning", default=None, metavar="SORT,WALK",
+                    help="fix the sort and walk variants instead of running the autotuner (profiling runs: "
+                         "no trial launches before the measured ones)")
     return ap.parse_args()
 
 
@@ -499,10 +502,19 @@ def run_gpu(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     tree = lbvh.Tree()
-    # the autotuner picks the sort and walk variants on these very inputs
-    # (device-timed, two runs of each candidate) before anything is timed
-    tune_sort, tune_walk = tree.autotune(pts, kind, bits, queries=None if knn else qpts, qkind=qkind,
-                                         radius=float(radius))
+    if args.tuning:
+        tune_sort, tune_walk = (int(x) for x in args.tuning.split(","))
+        tree.set_tuning(tune_sort, tune_walk)
+        tune_how = "fixed by --tuning"
+    else:
+        # the autotuner picks the sort and walk variants on these very inputs
+        # (device-timed, two runs of each candidate) before anything is timed
+        tune_sort, tune_walk = tree.autotune(pts, kind, bits, queries=None if knn else qpts, qkind=qkind,
+                                             radius=float(radius))
+        tune_how = "lbvh_tree_autotune on these inputs before the warm-up"
+    tune_how += (" (sort choice: tile shape = choice % half the choices; the second half sorts one top byte "
+                 "fewer for codes wider than 30 bits; walk choice: kind = choice % half, the second half orders "
+                 "the queries by 24-bit instead of 30-bit Morton codes)")
     tree.set_profiling(True)
     offsets = torch.empty(nq + 1, dtype=torch.int64, device=dev)
     # size the hit buffer once (a production caller does the same)
@@ -699,10 +711,7 @@ def run_gpu(args, world, rank, local):
             "tuning": {"sort_variant": tune_sort, "walk_variant": tune_walk,
                        "sort_passes": sum(1 for k in stage_ms if k.startswith("sort_pass")),
                        "query_order_bits": 24 if order_passes == 3 else 30,
-                       "how": "lbvh_tree_autotune on these inputs before the warm-up (sort choice: tile "
-                              "shape = choice % half the choices; the second half sorts one top byte fewer "
-                              "for codes wider than 30 bits; walk choice: kind = choice % half, the second "
-                              "half orders the queries by 24-bit instead of 30-bit Morton codes)"},
+                       "how": tune_how},
             "build_mprims_s": n / (build_ms * 1e-3) / 1e6,
             "query_mqueries_s": nq / (query_ms * 1e-3) / 1e6,
             "build_ms": build_ms,

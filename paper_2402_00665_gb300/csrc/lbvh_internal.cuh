@@ -37,8 +37,9 @@ struct Control {
     uint32_t spill_used;           // spill chunks handed out by the walk
     uint32_t run_long;             // run_code_sort: runs listed for a CTA each,
     uint32_t run_fallback;         //   a run too long for one CTA was met,
-    uint32_t run_sort_count;       //   elements of the fallback sort (in this order)
-    uint32_t pad[3];
+    uint32_t run_sort_count;       //   elements of the fallback sort,
+    uint32_t run_heads;            //   runs listed for short_runs_kernel (in this order)
+    uint32_t pad[2];
 };
 constexpr int kQueryBufferHits = 64;  // hits kept per query by the walk
 

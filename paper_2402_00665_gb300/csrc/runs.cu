@@ -6,30 +6,34 @@
 //    its low ib - 1 bits: 64 - ib key bits travel in one 8-byte word with the
 //    index, so every pass moves 8 bytes each way, and the passes cover the
 //    key bits only (5 passes at n = 2^25 and 63-bit codes, against 8 passes
-//    over the whole code). The words come out in (top, index) order.
-// 2. Words whose top is shared with a neighbour ("members": the runs of equal
-//    top, each over consecutive positions) are not yet in code order. Runs
-//    are disjoint, so each is put in order on its own: the full codes of its
-//    elements are derived again from their primitives, and inside a run the
-//    order by (code, index) is the order of the 64-bit keys
-//    (code's low ib - 1 bits) << ib | index, all distinct.
+//    over the whole code; 4 when the tuner has the passes start one byte
+//    higher). The words come out ordered by their bits from the run shift
+//    rs up (rs = ib, or the first sorted bit when a byte is skipped), and in
+//    index order where those are equal.
+// 2. Words whose sorted bits are shared with a neighbour ("members": the runs
+//    of equal word >> rs, each over consecutive positions) are not yet in
+//    code order. Runs are disjoint, so each is put in order on its own: the
+//    full codes of its elements are derived again from their primitives, and
+//    inside a run the order by (code, index) is the order of the 64-bit keys
+//    (code's low rs - 1 bits) << ib | index, all distinct.
 //
 // Uniform points at n = 2^25 with 63-bit codes have about 2,000 members in
-// runs of 2 or 3; the Gaussian-mixture boxes 16% in runs of 2 to 7; equal
-// codes make long runs.
+// runs of 2 or 3 (rs = ib = 25), or 0.8% of the points (rs = 32); the
+// Gaussian-mixture boxes 16% in runs of 2 to 7; equal codes make long runs.
 //
-//   runs_kernel      one pass over the sorted words: perm[j] = the index in
-//                    word j for every position outside a run; each run
-//                    element's in-run key; the thread that holds a run's
-//                    first position sorts a run of at most kShortRun
-//                    elements in place, and lists a longer one.
-//   long_runs_kernel a CTA per listed run: up to kLongRun elements sorted in
-//                    shared memory; a longer run raises the fallback.
-//   fallback         only after a run longer than kLongRun (all kernels read
-//                    the decision on the device and leave at once otherwise):
-//                    the full codes of all elements with their indices, a
-//                    stable key + payload sort of them (run_counted_sort),
-//                    and the permutation copied out.
+//   runs_kernel       one pass over the sorted words: perm[j] = the index in
+//                     word j for every position outside a run, and the list
+//                     of the runs' first positions.
+//   short_runs_kernel a thread per listed run: a run of at most kShortRun
+//                     elements sorted in place, a longer one listed.
+//   long_runs_kernel  a CTA per listed long run: up to kLongRun elements
+//                     sorted in shared memory; a longer run raises the
+//                     fallback.
+//   fallback          only after a run longer than kLongRun (all kernels read
+//                     the decision on the device and leave at once
+//                     otherwise): the full codes of all elements with their
+//                     indices, a stable key + payload sort of them
+//                     (run_counted_sort), and the permutation copied out.
 #include "lbvh_internal.cuh"
 #include "morton.cuh"
 
@@ -64,38 +68,36 @@ __device__ __forceinline__ uint64_t run_key(const float *prims, uint32_t idx, co
 }
 
 // A CTA covers kThreads * kPer consecutive positions, each thread kPer of
-// them. Each thread derives the in-run keys of its own run elements (its
-// gathers independent of each other) into shared memory; then the thread
-// holding a run's first position sorts a run of at most kShortRun elements
-// (keys of elements past the CTA's last position are derived there and
-// then), or lists a longer one.
-template <int kKind>
+// them: it writes the permutation at every position outside a run and lists
+// the first position of every run it holds (warp-aggregated appends). The
+// runs are ordered by short_runs_kernel, so that this pass, which every
+// element goes through, keeps no gathers or barriers waiting on them (with
+// runs in 0.8% of the positions, nearly every CTA holds one).
 __global__ void __launch_bounds__(kThreads)
-    runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, int rs, const float *__restrict__ prims,
-                const float *__restrict__ bounds, int b, uint32_t *__restrict__ perm, uint32_t *__restrict__ long_list,
-                uint32_t *long_count, uint32_t *flags) {
+    runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, int rs, uint32_t *__restrict__ perm,
+                uint32_t *__restrict__ run_list, uint32_t *run_count, int64_t run_cap, uint32_t *flags) {
     constexpr int kSpan = kThreads * kPer;
     // the CTA's words, loaded across the CTA (position p at p + p / kPer: one
     // padding word per thread's row keeps a thread's reads of its own row
-    // free of bank conflicts); then the run keys, by position
-    __shared__ uint64_t s_key[kSpan + kThreads];
+    // free of bank conflicts)
+    __shared__ uint64_t s_word[kSpan + kThreads];
     const int64_t cta0 = (int64_t)blockIdx.x * kSpan;
     const int64_t p0 = cta0 + (int64_t)threadIdx.x * kPer;
     const uint32_t imask = (uint32_t)((1ull << ib) - 1ull);
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
         const int p = j * kThreads + threadIdx.x;
-        s_key[p + p / kPer] = cta0 + p < n ? words[cta0 + p] : 0ull;
+        s_word[p + p / kPer] = cta0 + p < n ? words[cta0 + p] : 0ull;
     }
     __syncthreads();
     uint64_t w[kPer];
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) w[k] = s_key[threadIdx.x * (kPer + 1) + k];
+    for (int k = 0; k < kPer; ++k) w[k] = s_word[threadIdx.x * (kPer + 1) + k];
     uint32_t member = 0, head = 0;  // bit k: position p0 + k is in a run / starts one
     if (p0 < n) {
         // the last word of the previous thread's row (its padding word follows it)
-        const uint64_t left = threadIdx.x > 0 ? s_key[threadIdx.x * (kPer + 1) - 2] : (p0 > 0 ? words[p0 - 1] : 0ull);
-        const uint64_t right = threadIdx.x + 1 < kThreads ? s_key[(threadIdx.x + 1) * (kPer + 1)]
+        const uint64_t left = threadIdx.x > 0 ? s_word[threadIdx.x * (kPer + 1) - 2] : (p0 > 0 ? words[p0 - 1] : 0ull);
+        const uint64_t right = threadIdx.x + 1 < kThreads ? s_word[(threadIdx.x + 1) * (kPer + 1)]
                                                           : (p0 + kPer < n ? words[p0 + kPer] : 0ull);
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
@@ -119,33 +121,52 @@ __global__ void __launch_bounds__(kThreads)
                 if (p0 + k < n && !(member & (1u << k))) perm[p0 + k] = (uint32_t)w[k] & imask;
         }
     }
-    if (!__syncthreads_or(member != 0)) return;  // the common case: no run here
-
-    const Grid3 g = make_grid(bounds, b);
+    // list the run heads: one atomic per warp that holds any
+    const int lane = threadIdx.x & 31;
+    const uint32_t mine = (uint32_t)__popc(head);
+    uint32_t incl = mine;
 #pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-        if (member & (1u << k)) {
-            const uint32_t idx = (uint32_t)w[k] & imask;
-            uint64_t key = 0;
-            if ((int64_t)idx < n) key = run_key<kKind>(prims, idx, g, ib, rs);
-            else atomicOr(flags, kFlagCorrupt);  // only after a timed-out pass
-            s_key[threadIdx.x * kPer + k] = key;
-        }
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
     }
-    __syncthreads();
-    if (head == 0) return;
+    const uint32_t warp_total = __shfl_sync(0xffffffffu, incl, 31);
+    if (warp_total == 0) return;
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(run_count, warp_total);
+    base = __shfl_sync(0xffffffffu, base, 31) + incl - mine;
     for (int k = 0; k < kPer; ++k) {
         if (!(head & (1u << k))) continue;
-        const int64_t s = p0 + k;
-        // the run's length: inside this thread's positions a member that
-        // starts no run continues the one before it; a run that reaches the
-        // thread's last position is followed through the words
-        int len = 1;
-        while (k + len < kPer && (member >> (k + len) & 1u) && !(head >> (k + len) & 1u)) ++len;
-        if (k + len == kPer) {
-            const uint64_t top = words[s] >> rs;  // (not w[k]: a variable index would put w in local memory)
-            while (len <= kShortRun && s + len < n && (words[s + len] >> rs) == top) ++len;
+        if ((int64_t)base < run_cap) run_list[base] = (uint32_t)(p0 + k);
+        else atomicOr(flags, kFlagCorrupt);  // more runs than positions allow
+        ++base;
+    }
+}
+
+// One thread per listed run (a fixed grid strides over the list, whose
+// length is known on the device): the run's length from the sorted words,
+// then a run of at most kShortRun elements is put in code order in place:
+// the in-run keys of its elements (their primitives gathered, the codes
+// derived again) sorted by insertion; a longer run is listed for
+// long_runs_kernel.
+template <int kKind>
+__global__ void __launch_bounds__(kThreads)
+    short_runs_kernel(const uint64_t *__restrict__ words, int64_t n, int ib, int rs, const float *__restrict__ prims,
+                      const float *__restrict__ bounds, int b, uint32_t *__restrict__ perm,
+                      const uint32_t *__restrict__ run_list, const uint32_t *run_count, int64_t run_cap,
+                      uint32_t *__restrict__ long_list, uint32_t *long_count, uint32_t *flags) {
+    const int64_t count = min((int64_t)*run_count, run_cap);
+    const uint32_t imask = (uint32_t)((1ull << ib) - 1ull);
+    const Grid3 g = make_grid(bounds, b);
+    for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < count; r += (int64_t)gridDim.x * kThreads) {
+        const int64_t s = run_list[r];
+        if (s >= n) {  // a corrupt list entry
+            atomicOr(flags, kFlagCorrupt);
+            continue;
         }
+        const uint64_t top = words[s] >> rs;
+        int len = 1;
+        while (len <= kShortRun && s + len < n && (words[s + len] >> rs) == top) ++len;
         if (len > kShortRun) {
             const uint32_t slot = atomicAdd(long_count, 1u);
             if ((int64_t)slot < n / (kShortRun + 1) + 1) long_list[slot] = (uint32_t)s;
@@ -154,13 +175,10 @@ __global__ void __launch_bounds__(kThreads)
         }
         uint64_t key[kShortRun];
         for (int i = 0; i < len; ++i) {
-            const int64_t p = s + i;
-            if (p < cta0 + kSpan) {
-                key[i] = s_key[p - cta0];
-            } else {
-                const uint32_t idx = (uint32_t)words[p] & imask;
-                key[i] = (int64_t)idx < n ? run_key<kKind>(prims, idx, g, ib, rs) : 0ull;
-            }
+            const uint32_t idx = (uint32_t)words[s + i] & imask;
+            key[i] = 0ull;
+            if ((int64_t)idx < n) key[i] = run_key<kKind>(prims, idx, g, ib, rs);
+            else atomicOr(flags, kFlagCorrupt);  // only after a timed-out pass
         }
         for (int i = 1; i < len; ++i) {  // insertion sort: runs are short
             const uint64_t v = key[i];
@@ -278,7 +296,7 @@ __global__ void __launch_bounds__(kThreads)
 
 }  // namespace
 
-int64_t code_sort_scratch_words(int64_t n) { return n + n / (kShortRun + 1) + 1; }
+int64_t code_sort_scratch_words(int64_t n) { return n + (n / (kShortRun + 1) + 1) + (n / 2 + 1); }
 
 uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bounds, int64_t n, uint64_t *keys_a,
                         uint64_t *keys_b, uint32_t *vals_a, uint32_t *vals_b, uint32_t *scratch,
@@ -290,15 +308,20 @@ uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bou
     uint64_t *words = run_top_sort(keys_a, keys_b, n, ib, skip, sc, ctl, s, pass_events, variant_idx);
     uint64_t *codes = words == keys_a ? keys_b : keys_a;
     uint32_t *perm = vals_a, *index_alt = scratch, *long_list = scratch + n;
+    uint32_t *run_list = long_list + (n / (kShortRun + 1) + 1);  // each run has two elements or more
+    const int64_t run_cap = n / 2 + 1;
     if (runs_events) cudaEventRecord(runs_events[0], s);
     const bool points = kind == LBVH_PRIM_POINTS;
     const int b = bits / 3;
-    // long-run count, fallback flag, fallback sort count
-    cudaMemsetAsync(&ctl->run_long, 0, 3 * sizeof(uint32_t), s);
+    // long-run count, fallback flag, fallback sort count, run count
+    cudaMemsetAsync(&ctl->run_long, 0, 4 * sizeof(uint32_t), s);
     const int64_t blocks = (n + (int64_t)kThreads * kPer - 1) / ((int64_t)kThreads * kPer);
-    (points ? runs_kernel<LBVH_PRIM_POINTS> : runs_kernel<LBVH_PRIM_BOXES>)<<<(unsigned)blocks, kThreads, 0, s>>>(
-        words, n, ib, rs, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->build_flags);
+    runs_kernel<<<(unsigned)blocks, kThreads, 0, s>>>(words, n, ib, rs, perm, run_list, &ctl->run_heads, run_cap,
+                                                     &ctl->build_flags);
     const int sms = device_sm_count();
+    (points ? short_runs_kernel<LBVH_PRIM_POINTS> : short_runs_kernel<LBVH_PRIM_BOXES>)<<<sms * 8, kThreads, 0, s>>>(
+        words, n, ib, rs, prims, bounds, b, perm, run_list, &ctl->run_heads, run_cap, long_list, &ctl->run_long,
+        &ctl->build_flags);
     (points ? long_runs_kernel<LBVH_PRIM_POINTS> : long_runs_kernel<LBVH_PRIM_BOXES>)<<<sms * 2, kThreads, 0, s>>>(
         words, n, ib, rs, prims, bounds, b, perm, long_list, &ctl->run_long, &ctl->run_fallback,
         &ctl->build_flags);
@@ -306,7 +329,7 @@ uint32_t *run_code_sort(const float *prims, int kind, int bits, const float *bou
     (points ? fallback_keys_kernel<LBVH_PRIM_POINTS> : fallback_keys_kernel<LBVH_PRIM_BOXES>)<<<sms * 4, kThreads, 0,
                                                                                                s>>>(
         words, n, ib, prims, bounds, b, codes, vals_b, &ctl->run_fallback, &ctl->run_sort_count, &ctl->build_flags);
-    count_launches(3);
+    count_launches(4);
     cudaMemsetAsync(sc.hist, 0, (size_t)kMaxPasses * kRadix * sizeof(uint32_t), s);
     launch_digit_histogram_counted(codes, n, &ctl->run_sort_count, sc.hist, s);
     const bool in_b = run_counted_sort(codes, vals_b, words, index_alt, &ctl->run_sort_count, n, bits, sc, ctl, s);
