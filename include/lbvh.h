@@ -400,8 +400,9 @@ typedef struct {
 } lbvh_result;
 
 /* Start a request server: `slots` worker streams (1..16), each running one
- * batch at a time, so up to `slots` batches overlap on the device; at most
- * `max_batch` requests per batch. The scheduler admits queued requests in
+ * batch at a time, so up to `slots` batches overlap on the device (a batch
+ * of 2^23 primitives or more, which fills the GPU alone, starts only when no
+ * other batch runs); at most `max_batch` requests per batch. The scheduler admits queued requests in
  * arrival order while their estimated working bytes plus the bytes of the
  * resident trees fit `hbm_budget_bytes`, evicting the least recently used
  * resident trees (not in use) to make room; requests that arrive while others
