@@ -553,10 +553,11 @@ uint64_t lbvh_kernel_launches(void);
  *                 (Sec. 3.1 step 2 either way: the same sorted order);
  *   walk variant  how Algorithm 1's collecting walk runs: 0 one thread per
  *                 query, 1/2/3 groups of 8/16/32 lanes walking the union of
- *                 their queries' paths together; 4-7 the same with the
+ *                 their queries' paths together, 4 one thread per query in
+ *                 CTAs of 512 threads instead of 256; 5-9 the same with the
  *                 queries put in the Morton order of 24-bit codes of their
  *                 centres (one sort pass fewer) instead of 30-bit ones
- *                 (lbvh_walk_variant_count() = 8).
+ *                 (lbvh_walk_variant_count() = 10).
  * A process-wide cache holds the choice for each configuration (the GPU's
  * name, ceil(log2 n), Morton bits, primitive kind, query kind, trees built
  * together); builds and queries use the cached choice for their

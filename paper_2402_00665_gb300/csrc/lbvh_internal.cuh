@@ -284,9 +284,16 @@ struct QueryArgs {
     const uint32_t *order;  // null: thread i walks query i; else query order[i]
     int walk = 0;           // kWalk*: how the collecting walk runs
 };
-// The collecting walk: one thread per query, or groups of 8, 16 or 32 lanes
-// walking together (walk_group in query.cu).
-enum : int { kWalkThread = 0, kWalkGroup8 = 1, kWalkGroup16 = 2, kWalkGroup32 = 3, kWalkKinds = 4 };
+// The collecting walk: one thread per query (CTAs of 256 threads, or of 512),
+// or groups of 8, 16 or 32 lanes walking together (walk_group in query.cu).
+enum : int {
+    kWalkThread = 0,
+    kWalkGroup8 = 1,
+    kWalkGroup16 = 2,
+    kWalkGroup32 = 3,
+    kWalkThread512 = 4,
+    kWalkKinds = 5
+};
 // A tree's walk choice c (the tuner's index, lbvh_tree_set_tuning): walk kind
 // c % kWalkKinds, and the Morton bits of the query order: 30 (4 sort passes)
 // for c < kWalkKinds, 24 (3 passes) above.

@@ -362,15 +362,18 @@ __global__ void __launch_bounds__(kThreads, 8)
 }
 
 // One thread per walk position: thread i walks position i (query order[i]).
-// At most 32 registers (8 CTAs of 256 threads per SM): the walk hides its
-// load latency with occupancy. Several walks per thread in lock step (K
-// independent loads in flight per thread) measured slower on GB300: the walk
-// is bound by L1 wavefronts (distinct sectors per load), which more walks per
-// thread only increase.
-template <int kQ, int kP>
-__global__ void __launch_bounds__(kThreads, 8)
+// At most 32 registers (2048 threads per SM): the walk hides its load latency
+// with occupancy. Several walks per thread in lock step (K independent loads
+// in flight per thread) measured slower on GB300: the walk is bound by L1
+// wavefronts (distinct sectors per load), which more walks per thread only
+// increase. kT threads per CTA (256 or 512, a tuner choice): the CTAs that
+// share an SM's L1 walk kT adjacent queries each, so larger CTAs put more
+// neighbouring walks on one SM (D2 walk 15.93 -> 15.66 ms with 512; 1024
+// measured slower on D2 and D3).
+template <int kQ, int kP, int kT>
+__global__ void __launch_bounds__(kT, 2048 / kT)
     collect_kernel(TreeView t, QueryArgs qa, QueryScratch qs, Control *ctl) {
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x;
     if (i >= qa.nq) return;
     const bool walk_ok = t.n > 0 && ctl->build_flags == 0;
     collect_walk<kQ, kP, kP == LBVH_PRIM_POINTS>(t, qa, qs, ctl, i, thread_query(qa, i), walk_ok);
@@ -1052,7 +1055,10 @@ void launch_query_collect(const TreeView &t, const QueryArgs &q, const QueryScra
         case kWalkGroup8: collect_group_kernel<Q, P, 8><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
         case kWalkGroup16: collect_group_kernel<Q, P, 16><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
         case kWalkGroup32: collect_group_kernel<Q, P, 32><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
-        default: collect_kernel<Q, P><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
+        case kWalkThread512:
+            collect_kernel<Q, P, 512><<<(unsigned)((q.nq + 511) / 512), 512, 0, s>>>(t, q, qs, ctl);
+            break;
+        default: collect_kernel<Q, P, kThreads><<<blocks, kThreads, 0, s>>>(t, q, qs, ctl); break;
         }
     });
     count_launches(1);

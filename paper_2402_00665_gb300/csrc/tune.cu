@@ -6,9 +6,9 @@
 // a single tree, the instance count of a batch). It records the sort's tile
 // shape and ranking (a variant of sort.cu's table; for a single tree's codes
 // wider than 30 bits, also whether the top-bits sort takes one pass fewer)
-// and how the collecting walk runs (one thread per query, or groups of 8, 16
-// or 32 lanes, and the query order's Morton bits), each with the time it
-// measured. lbvh_tree_autotune and the batch path fill the
+// and how the collecting walk runs (one thread per query in CTAs of 256 or
+// 512 threads, or groups of 8, 16 or 32 lanes, and the query order's Morton
+// bits), each with the time it measured. lbvh_tree_autotune and the batch path fill the
 // cache by timing every candidate on the caller's own data; builds and
 // queries look their configuration up and fall back to the defaults. The
 // cache can be written to and read from a small JSON file, so a process can
