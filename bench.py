@@ -624,22 +624,31 @@ def run_gpu(args, world, rank, local):
     if not args.no_e2e and not knn:
         host_pts = torch.from_numpy(prims_host).pin_memory()
         host_q = torch.from_numpy(queries_host).pin_memory()
-        host_off = torch.empty(nq + 1, dtype=torch.int64).pin_memory()
-        host_hits = torch.empty(hits.numel(), dtype=torch.int32).pin_memory()
-        # two sets of device inputs: step k's inputs go up (second stream)
-        # while step k - 1 queries, so a step's host->device copies overlap
-        # the previous step's walk and its device->host copies; every step
-        # still copies its own inputs up and its own results down inside the
-        # timed region (the first step of a run uploads before its build, the
-        # last one uploads nothing ahead)
+        # two steps in flight: step k runs on lane k & 1 (its own tree,
+        # stream, device inputs and page-locked result arrays), so the copy of
+        # step k's last result chunk to the host overlaps step k + 1's build;
+        # step k's inputs go up on a side stream while step k - 1 queries.
+        # Every step still copies its own inputs up and its own CSR down
+        # inside the timed region; the region ends when both lanes are done.
+        trees = [tree, lbvh.Tree()]
+        trees[1].set_tuning(tune_sort, tune_walk)
+        for t_ in trees:
+            t_.set_profiling(False)
+        host_off = [torch.empty(nq + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
+        host_hits = [torch.empty(hits.numel(), dtype=torch.int32).pin_memory() for _ in range(2)]
         dpts = [torch.empty_like(pts), torch.empty_like(pts)]
         dq = [torch.empty_like(qpts), torch.empty_like(qpts)]
-        main = torch.cuda.current_stream(dev)
+        # --e2e-staged: each lane's device CSR
+        dev_off = [offsets, torch.empty_like(offsets) if args.e2e_staged else None]
+        dev_hits = [hits, torch.empty_like(hits) if args.e2e_staged else None]
+        lanes = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
         side = torch.cuda.Stream(dev)
         uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+        consumed = [torch.cuda.Event(), torch.cuda.Event()]  # a lane's last read of its device inputs
 
         def upload(slot):
             with torch.cuda.stream(side):
+                side.wait_event(consumed[slot])  # the lane's previous step has read them
                 dpts[slot].copy_(host_pts, non_blocking=True)
                 dq[slot].copy_(host_q, non_blocking=True)
                 uploaded[slot].record(side)
@@ -653,21 +662,30 @@ def run_gpu(args, world, rank, local):
             upload(0)
             for k in range(steps):
                 slot = k & 1
-                main.wait_event(uploaded[slot])
-                tree.build(dpts[slot], kind, bits)
+                lane = lanes[slot]
+                # the lane's previous step (k - 2) must be done before its
+                # tree, staging and host arrays are reused
+                lane.synchronize()
+                lane.wait_event(uploaded[slot])
+                trees[slot].build(dpts[slot], kind, bits, stream=lane)
                 if k + 1 < steps:
-                    upload(slot ^ 1)  # its buffers were last read by step k - 1, which has finished
+                    upload(slot ^ 1)
                 if args.e2e_staged:
-                    s, tot = tree.query_into(dq[slot], qkind, offsets, hits, radius=float(radius))
+                    s, tot = trees[slot].query_into(dq[slot], qkind, dev_off[slot], dev_hits[slot],
+                                                    radius=float(radius), stream=lane)
                     if s != lbvh.OK:
                         raise lbvh.LbvhError(s, "lbvh_query_into")
-                    host_off.copy_(offsets, non_blocking=True)
-                    host_hits[:tot].copy_(hits[:tot], non_blocking=True)
+                    with torch.cuda.stream(lane):
+                        host_off[slot].copy_(dev_off[slot], non_blocking=True)
+                        host_hits[slot][:tot].copy_(dev_hits[slot][:tot], non_blocking=True)
                 else:
-                    s, tot = tree.query_into_host(dq[slot], qkind, host_off, host_hits, radius=float(radius))
+                    s, tot = trees[slot].query_into_host(dq[slot], qkind, host_off[slot], host_hits[slot],
+                                                         radius=float(radius), stream=lane)
                     if s != lbvh.OK:
                         raise lbvh.LbvhError(s, "lbvh_query_into_host")
-                main.synchronize()
+                consumed[slot].record(lane)
+            for lane in lanes:
+                lane.synchronize()
             return tot
 
         e2e_run(2)
@@ -677,14 +695,18 @@ def run_gpu(args, world, rank, local):
         tot = e2e_run(args.steps)
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world, dev) / args.steps
+        assert int(host_off[(args.steps - 1) & 1][-1]) == tot  # the last step's CSR reached the host
+        trees[1].close()
         e2e = {"value": n * world / dt / 1e6, "unit": UNIT, "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int((pts.numel() + qpts.numel()) * 4),
                "d2h_bytes_per_step": int((nq + 1) * 8 + tot * 4),
-               "note": "pinned host primitives and queries -> device (each step's inputs copied on a second "
+               "note": "pinned host primitives and queries -> device (each step's inputs copied on a side "
                        "stream while the previous step queries), build, query, CSR offsets + hits "
                        + ("-> device, then copied to pinned host" if args.e2e_staged
                           else "-> pinned host by lbvh_query_into_host (chunks staged on the device, "
-                               "each copied while the next runs)")}
+                               "each copied while the next runs)")
+                       + "; two steps in flight on two trees and streams, so one step's last result "
+                         "copy overlaps the next step's build"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
