@@ -634,6 +634,9 @@ def run_gpu(args, world, rank, local):
         trees[1].set_tuning(tune_sort, tune_walk)
         for t_ in trees:
             t_.set_profiling(False)
+            # one chunk: the CSR's copy to the host overlaps the other lane's
+            # build and walk instead of this query's own later chunks
+            t_.set_host_chunks(1)
         host_off = [torch.empty(nq + 1, dtype=torch.int64).pin_memory() for _ in range(2)]
         host_hits = [torch.empty(hits.numel(), dtype=torch.int32).pin_memory() for _ in range(2)]
         dpts = [torch.empty_like(pts), torch.empty_like(pts)]
@@ -703,10 +706,10 @@ def run_gpu(args, world, rank, local):
                "note": "pinned host primitives and queries -> device (each step's inputs copied on a side "
                        "stream while the previous step queries), build, query, CSR offsets + hits "
                        + ("-> device, then copied to pinned host" if args.e2e_staged
-                          else "-> pinned host by lbvh_query_into_host (chunks staged on the device, "
-                               "each copied while the next runs)")
-                       + "; two steps in flight on two trees and streams, so one step's last result "
-                         "copy overlaps the next step's build"}
+                          else "-> pinned host by lbvh_query_into_host (the CSR staged on the device in one "
+                               "chunk, lbvh_tree_set_host_chunks(1), then copied)")
+                       + "; two steps in flight on two trees and streams, so one step's result copy overlaps "
+                         "the next step's build and walk"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

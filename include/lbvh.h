@@ -223,7 +223,8 @@ lbvh_status lbvh_query_into(lbvh_tree_t tree, const float *d_queries, int64_t nq
  * (cudaMallocHost, cudaHostAlloc or cudaHostRegister): h_offsets int64[nq+1],
  * h_hits uint32[capacity], owned by the caller. The queries go through the
  * device path in chunks (in index order; at least 2^23 queries each, at most
- * 4 chunks), each into one of two device staging areas that the tree owns; a
+ * 4 chunks unless lbvh_tree_set_host_chunks says otherwise), each into one of
+ * two device staging areas that the tree owns; a
  * chunk's offsets and hits are copied to the host on the tree's own copy
  * stream while the GPU works on the next chunk. Like every call here it
  * returns once the last chunk is counted; the host arrays are complete once
@@ -235,6 +236,17 @@ lbvh_status lbvh_query_into_host(lbvh_tree_t tree, const float *d_queries, int64
                                  const float *d_radii, float radius, int64_t *h_offsets,
                                  uint32_t *h_hits, uint64_t capacity, uint64_t *total,
                                  lbvh_stream_t stream);
+
+/* The most chunks lbvh_query_into_host cuts a tree's queries into (chunks
+ * of at least 2^23 queries): 1 to 16, or 0 for the default of 4 (else
+ * LBVH_ERR_INVALID). Every chunk costs a host round trip (its hit count);
+ * in return a chunk's copy to the host overlaps the next chunk's work. A
+ * caller that waits for each result does best with 3-4 (2^25 sphere queries
+ * of ~17 hits: 27.0 ms with 4 chunks, 32.6 ms with 1); a caller that keeps
+ * two queries in flight on two trees, so that one tree's copy overlaps the
+ * other tree's build and walk, does best with 1. Results do not depend on
+ * it. Not an operation of the paper: a transfer setting of this library. */
+lbvh_status lbvh_tree_set_host_chunks(lbvh_tree_t tree, int max_chunks);
 
 /* As lbvh_query_into, but the library allocates the CSR arrays
  * (*d_offsets int64[nq+1], *d_hits uint32[*total]); free them with lbvh_free. */

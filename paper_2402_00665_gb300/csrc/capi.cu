@@ -174,6 +174,7 @@ struct lbvh_tree_s {
     bool has_build = false;
     int codes_in = 0, perm_in = 0;  // which keys[] / vals[] buffer holds the sorted codes / permutation
     int sort_choice = -1, walk_choice = -1;  // lbvh_tree_set_tuning (-1: the tuner's cache, else the default)
+    int host_chunks = 0;                     // lbvh_tree_set_host_chunks (0: kHostChunksMax)
     bool store_dirty = false;  // a failed build may have left store words set
     DevBuf keys[2], vals[2];
     DevBuf nodes, store, lookback, hist, partials, bounds, ctl;
@@ -1128,12 +1129,16 @@ bool page_locked(const void *h) {
 }
 
 // Queries per chunk of lbvh_query_into_host: at least 2^23, at most 4
-// chunks. 2^25 sphere queries (17 hits each): 27.0 ms with 3 or 4 chunks,
-// 27.8 with 2, 29.2 with 8, 35.5 with 16, against 32.6 ms for the query and
-// the copies one after the other (each chunk adds a host round trip, and
-// its copy shares the link and L2 with the next chunk's walk).
+// chunks by default. 2^25 sphere queries (17 hits each): 27.0 ms with 3 or 4
+// chunks, 27.8 with 2, 29.2 with 8, 35.5 with 16, against 32.6 ms for the
+// query and the copies one after the other (each chunk adds a host round
+// trip, and its copy shares the link and L2 with the next chunk's walk).
+// With two trees in flight (one tree's copies overlapping the other's build
+// and walk), one chunk is best: 2^25 points built and queried per step at
+// 1466 Mprims/s through host memory with 1 chunk, 1392 with 2, 1271 with 4.
 constexpr int64_t kHostChunkMin = int64_t(1) << 23;
 constexpr int64_t kHostChunksMax = 4;
+constexpr int kHostChunksLimit = 16;  // lbvh_tree_set_host_chunks
 
 lbvh_status host_stream(lbvh_tree_t t) {
     if (t->xfer) return LBVH_OK;
@@ -1164,7 +1169,8 @@ lbvh_status lbvh_query_into_host(lbvh_tree_t t, const float *d_queries, int64_t 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int dim = qkind == LBVH_Q_SPHERE ? 3 : (qkind == LBVH_Q_BOX ? 6 : 8);
     const int64_t cmin = kHostChunkMin;
-    const int64_t chunks = nq <= cmin ? 1 : std::min<int64_t>(kHostChunksMax, (nq + cmin - 1) / cmin);
+    const int64_t cmax = t->host_chunks > 0 ? t->host_chunks : kHostChunksMax;
+    const int64_t chunks = nq <= cmin ? 1 : std::min<int64_t>(cmax, (nq + cmin - 1) / cmin);
     const int64_t per = (nq + chunks - 1) / chunks;
     uint64_t base = 0;
     bool over = false;
@@ -1631,6 +1637,12 @@ void tree_release_query_scratch(lbvh_tree_t t, cudaStream_t s) {
 }  // namespace lbvh
 
 extern "C" {
+
+lbvh_status lbvh_tree_set_host_chunks(lbvh_tree_t t, int max_chunks) {
+    if (!t || max_chunks < 0 || max_chunks > kHostChunksLimit) return LBVH_ERR_INVALID;
+    t->host_chunks = max_chunks;
+    return LBVH_OK;
+}
 
 lbvh_status lbvh_tree_set_tuning(lbvh_tree_t t, int sort_variant, int walk_variant) {
     if (!t || sort_variant < -1 || sort_variant >= lbvh::build_sort_choices() || walk_variant < -1 ||

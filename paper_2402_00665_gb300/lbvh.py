@@ -78,6 +78,7 @@ SIGNATURES = {
     "lbvh_walk_variant_count": (_I32, []),
     "lbvh_tree_autotune": (_I32, [_P, _P, _I64, _I32, _I32, _P, _I64, _I32, _P, _F32, _P, _P, _P]),
     "lbvh_tree_set_tuning": (_I32, [_P, _I32, _I32]),
+    "lbvh_tree_set_host_chunks": (_I32, [_P, _I32]),
     "lbvh_tune_save": (_I32, [ctypes.c_char_p]),
     "lbvh_tune_load": (_I32, [ctypes.c_char_p]),
     "lbvh_tune_clear": (None, []),
@@ -271,6 +272,10 @@ class Tree:
         """lbvh_tree_set_tuning: fix this tree's variants (-1: the cache's choice)."""
         _check(self._lib.lbvh_tree_set_tuning(self._h, int(sort_variant), int(walk_variant)),
                "lbvh_tree_set_tuning")
+
+    def set_host_chunks(self, max_chunks: int = 0):
+        """lbvh_tree_set_host_chunks: the most chunks query_into_host cuts the queries into (0: default)."""
+        _check(self._lib.lbvh_tree_set_host_chunks(self._h, int(max_chunks)), "lbvh_tree_set_host_chunks")
 
     def set_profiling(self, on: bool = True):
         _check(self._lib.lbvh_tree_set_profiling(self._h, int(bool(on))), "lbvh_tree_set_profiling")

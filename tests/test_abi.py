@@ -80,6 +80,11 @@ def test_invalid_arguments_rejected_before_any_device_work(lib_path):
         assert lib.lbvh_query_into_host(h, dummy, 1, 0, None, 1.0, off, None, 0, ctypes.byref(total),
                                         None) == lbvh.ERR_INVALID
         assert lib.lbvh_tree_status(h) == lbvh.ERR_INVALID
+        # the host-output chunk setting: 0 (default) to 16
+        for chunks, want in ((-1, lbvh.ERR_INVALID), (17, lbvh.ERR_INVALID), (0, lbvh.OK), (1, lbvh.OK),
+                             (16, lbvh.OK)):
+            assert lib.lbvh_tree_set_host_chunks(h, chunks) == want
+        assert lib.lbvh_tree_set_host_chunks(None, 1) == lbvh.ERR_INVALID
         # checkpoint images are validated before any device work
         size = ctypes.c_uint64()
         assert lib.lbvh_tree_save(h, None, 0, ctypes.byref(size)) == lbvh.ERR_INVALID  # never built

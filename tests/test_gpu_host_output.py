@@ -51,13 +51,16 @@ def test_host_csr_equals_device_csr(radius):
     assert np.array_equal(hoff.numpy(), ooff) and np.array_equal(hhits[:tot].numpy().view(np.uint32), ohits)
 
 
-def test_several_chunks():
-    # 9e6 queries: two chunks (at least 2^23 queries each), two staging areas
+@pytest.mark.parametrize("host_chunks", [0, 1, 2])
+def test_several_chunks(host_chunks):
+    # 9e6 queries: two chunks (at least 2^23 queries each), two staging areas;
+    # with lbvh_tree_set_host_chunks(1) one chunk of all the queries
     lbvh = L()
     pts = torch.from_numpy(inputs.uniform_points(1 << 20, seed=5)).cuda()
     q = torch.rand((9_000_000, 3), generator=torch.Generator().manual_seed(6)).cuda()
     r = float(inputs.radius_for_neighbours(1 << 20)) * 0.6
     t = lbvh.Tree().build(pts, lbvh.POINTS, 63)
+    t.set_host_chunks(host_chunks)
     doff, dhits = t.query(q, lbvh.SPHERE, radius=r)
     total = int(doff[-1].item())
     hoff = torch.empty(q.shape[0] + 1, dtype=torch.int64).pin_memory()
@@ -121,3 +124,64 @@ def test_no_queries_and_ray_chunks():
     torch.cuda.synchronize()
     assert st == lbvh.OK and tot == total
     assert torch.equal(hoff, doff.cpu()) and torch.equal(hhits[:tot], dhits.cpu())
+
+
+def test_two_trees_in_flight_on_two_streams():
+    # the end-to-end pattern: step k builds and queries on tree k % 2 and
+    # stream k % 2, its inputs uploaded on a side stream while step k - 1
+    # queries, so one step's last result copy overlaps the next step's build;
+    # every step's host CSR equals the same query run alone
+    lbvh = L()
+    n, nq, steps = 1 << 19, (1 << 23) + (1 << 20), 4  # two chunks per query
+    r = float(inputs.radius_for_neighbours(n))
+    host_pts = [torch.from_numpy(inputs.uniform_points(n, seed=40 + k)).pin_memory() for k in range(steps)]
+    host_q = [torch.rand((nq, 3), generator=torch.Generator().manual_seed(50 + k)).pin_memory()
+              for k in range(steps)]
+    want = []
+    alone = lbvh.Tree()
+    for k in range(steps):
+        alone.build(host_pts[k].cuda(), lbvh.POINTS, 63)
+        doff, dhits = alone.query(host_q[k].cuda(), lbvh.SPHERE, radius=r)
+        want.append((doff.cpu(), dhits.cpu()))
+    alone.close()
+    cap = max(int(w[0][-1]) for w in want) + 16
+    trees = [lbvh.Tree(), lbvh.Tree()]
+    trees[0].set_host_chunks(1)  # one tree copies its whole CSR at once, the other in two chunks
+    lanes = [torch.cuda.Stream(), torch.cuda.Stream()]
+    side = torch.cuda.Stream()
+    dpts = [torch.empty((n, 3), device="cuda"), torch.empty((n, 3), device="cuda")]
+    dq = [torch.empty((nq, 3), device="cuda"), torch.empty((nq, 3), device="cuda")]
+    uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+    consumed = [torch.cuda.Event(), torch.cuda.Event()]
+    hoff = [torch.empty(nq + 1, dtype=torch.int64).pin_memory() for _ in range(steps)]
+    hhits = [torch.empty(cap, dtype=torch.int32).pin_memory() for _ in range(steps)]
+    totals = [0] * steps
+
+    def upload(k):
+        slot = k & 1
+        with torch.cuda.stream(side):
+            side.wait_event(consumed[slot])
+            dpts[slot].copy_(host_pts[k], non_blocking=True)
+            dq[slot].copy_(host_q[k], non_blocking=True)
+            uploaded[slot].record(side)
+
+    upload(0)
+    for k in range(steps):
+        slot = k & 1
+        lanes[slot].synchronize()
+        lanes[slot].wait_event(uploaded[slot])
+        trees[slot].build(dpts[slot], lbvh.POINTS, 63, stream=lanes[slot])
+        if k + 1 < steps:
+            upload(k + 1)
+        st, totals[k] = trees[slot].query_into_host(dq[slot], lbvh.SPHERE, hoff[k], hhits[k], radius=r,
+                                                    stream=lanes[slot])
+        assert st == lbvh.OK
+        consumed[slot].record(lanes[slot])
+    for s in lanes:
+        s.synchronize()
+    for k in range(steps):
+        woff, whits = want[k]
+        assert totals[k] == int(woff[-1])
+        assert torch.equal(hoff[k], woff) and torch.equal(hhits[k][:totals[k]], whits)
+    for t in trees:
+        t.close()
