@@ -244,8 +244,12 @@ lbvh_status lbvh_query_into_host(lbvh_tree_t tree, const float *d_queries, int64
  * caller that waits for each result does best with 3-4 (2^25 sphere queries
  * of ~17 hits: 27.0 ms with 4 chunks, 32.6 ms with 1); a caller that keeps
  * two queries in flight on two trees, so that one tree's copy overlaps the
- * other tree's build and walk, does best with 1. Results do not depend on
- * it. Not an operation of the paper: a transfer setting of this library. */
+ * other tree's build and walk, does best with 1. Fewer chunks hold more at
+ * once: a chunk's query scratch (about 330 bytes per query) and its staged
+ * CSR live on the device together, so 1 chunk of 2^25 queries of ~17 hits
+ * needs about 14 GB (LBVH_ERR_OOM if it cannot be had). Results do not
+ * depend on it. Not an operation of the paper: a transfer setting of this
+ * library. */
 lbvh_status lbvh_tree_set_host_chunks(lbvh_tree_t tree, int max_chunks);
 
 /* As lbvh_query_into, but the library allocates the CSR arrays
