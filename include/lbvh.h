@@ -518,6 +518,18 @@ lbvh_status lbvh_construct_static(const uint64_t *d_sorted_codes, const uint32_t
  * after the hook is cleared is correct again. Nothing faults, traps or hangs. */
 lbvh_status lbvh_test_hold_sort_tile(int64_t tile);
 
+/* Test hook for the order of arrivals in Algorithm 4, off by default
+ * (max_ns = 0). While set, every thread of the bottom-up construct waits a
+ * pseudo-random time of up to max_ns nanoseconds (drawn from `seed`, the
+ * node and the level) before each exchange that decides which child's
+ * thread carries on, so that nodes are completed in other orders than the
+ * hardware's usual one; the tree must not change. Each wait is bounded (a
+ * clock check with an iteration cap); max_ns above 10^6 -> LBVH_ERR_INVALID.
+ * The paper has no counterpart: it tests Algorithm 4 under other
+ * interleavings. Builds without the hook run kernels that carry no trace of
+ * it. */
+lbvh_status lbvh_test_construct_jitter(unsigned long long seed, unsigned max_ns);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* Stage ids of lbvh_tree_stage_times (device time of one kernel launch, or of

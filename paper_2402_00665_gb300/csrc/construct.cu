@@ -40,6 +40,8 @@
 //     `store` words (sibling box through L2, ld.global.cg). Batches group
 //     their global sorted positions the same way (a group may hold several
 //     trees; a split only ever joins leaves of one).
+#include <atomic>
+
 #include <cuda/atomic>
 
 #include "lbvh_internal.cuh"
@@ -94,6 +96,34 @@ __device__ __forceinline__ void load_node_box(const float4 *inodes, const float4
 __device__ __forceinline__ unsigned long long publish_exchange(unsigned long long *slot, unsigned long long v) {
     cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> a(*slot);
     return a.exchange(v, cuda::memory_order_acq_rel);
+}
+
+// Test hook (lbvh_test_construct_jitter): with kJitter, a thread waits a
+// pseudo-random time of up to max_ns before each exchange (its delay drawn
+// by splitmix64 from the seed and a salt naming the thread's place and
+// level; %globaltimer, with an iteration cap as a backstop), so that the
+// two children of a node arrive in other orders than the hardware's usual
+// one. The kernels of every other build are instantiated without it.
+struct Jitter {
+    unsigned long long seed = 0;
+    unsigned max_ns = 0;
+};
+
+template <bool kJitter>
+__device__ __forceinline__ void jitter_wait(const Jitter &j, unsigned long long salt) {
+    if constexpr (kJitter) {
+        unsigned long long x = j.seed + (salt + 1ull) * 0x9e3779b97f4a7c15ull;
+        x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+        x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+        x ^= x >> 31;
+        const unsigned long long d = x % ((unsigned long long)j.max_ns + 1ull);
+        unsigned long long t0, t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (unsigned k = 0; k < (1u << 16); ++k) {
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 >= d) break;
+        }
+    }
 }
 
 // A thread's finished node while it climbs: leaf range [l, r], delta*(l-1),
@@ -217,9 +247,10 @@ __device__ __forceinline__ int write_parent(Climb &c, uint32_t p, int n, float3 
 
 // Climb from c's node with device-scope exchanges on store[p] until this
 // thread is the first up at a split, or has written the root I_0.
-template <int kKind>
+template <int kKind, bool kJitter = false>
 __device__ __forceinline__ void climb_global(Climb c, int n, float4 *inodes, const float4 *leaves,
-                                             unsigned long long *store, uint32_t *flags) {
+                                             unsigned long long *store, uint32_t *flags,
+                                             const Jitter &jt = Jitter{}) {
     const int ni = n - 1;
     // The augmented keys have at most 64 + 32 bits, so no leaf is deeper than
     // 96 levels; the bound only guards against a corrupt input order.
@@ -231,6 +262,7 @@ __device__ __forceinline__ void climb_global(Climb c, int n, float4 *inodes, con
             atomicOr(flags, kFlagCorrupt);
             return;
         }
+        jitter_wait<kJitter>(jt, (unsigned long long)p << 8 | (unsigned)level);
         const unsigned long long other = publish_exchange(store + p, mine);
         if (other == 0ull) return;  // first thread up
         store[p] = 0ull;            // second thread up: leave the slot empty again
@@ -287,10 +319,10 @@ constexpr uint32_t kPendValid = 1u << 31;
 // two leaves of one tree, so groups may hold several trees. Every thread of
 // the CTA must call this (it holds the group's barrier).
 // pend (nullable): the CTA's kPendSlots slots.
-template <int kKind>
+template <int kKind, bool kJitter = false>
 __device__ __forceinline__ void two_phase(GroupSmem &sm, bool go, Climb c, int n, int64_t o, int64_t a, int t,
                                           float4 *inodes, const float4 *leaves, unsigned long long *store,
-                                          uint32_t *flags, uint4 *pend) {
+                                          uint32_t *flags, uint4 *pend, const Jitter &jt = Jitter{}) {
     const int ni = n - 1;
     bool pending = false, in_word = false;
     int word_at = 0;
@@ -311,6 +343,7 @@ __device__ __forceinline__ void two_phase(GroupSmem &sm, bool go, Climb c, int n
                 break;
             }
             const int at = (int)rel;
+            jitter_wait<kJitter>(jt, (unsigned long long)p << 8 | (unsigned)level);
             cuda::atomic_ref<unsigned long long, cuda::thread_scope_block> w(sm.word[at]);
             const unsigned long long other = w.exchange(mine, cuda::memory_order_acq_rel);
             if (other == 0ull) {  // first up: the sibling may come in this phase, or never
@@ -344,17 +377,17 @@ __device__ __forceinline__ void two_phase(GroupSmem &sm, bool go, Climb c, int n
         }
     }
     // this thread wrote its own node, so its device-scope release covers it
-    climb_global<kKind>(c, n, inodes, leaves, store, flags);
+    climb_global<kKind, kJitter>(c, n, inodes, leaves, store, flags, jt);
 }
 
 // The climbs handed over by the groups, one thread per slot: the climber's
 // node (range [l, r], written by the first kernel) is read back for its box
 // and the climb goes on with device-scope exchanges. Every valid slot is
 // cleared, so the slots are zero again for the next build.
-template <int kKind>
+template <int kKind, bool kJitter>
 __global__ void __launch_bounds__(256)
     climb_pending_kernel(uint4 *pend, int64_t slots, int n, float4 *inodes, const float4 *leaves,
-                         unsigned long long *store, uint32_t *flags) {
+                         unsigned long long *store, uint32_t *flags, Jitter jt) {
     const int64_t k = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (k >= slots) return;
     const uint4 e = pend[k];
@@ -375,7 +408,7 @@ __global__ void __launch_bounds__(256)
     // the node of range [l, r]: leaf l, or internal node r or l (its Karras index)
     const int id = c.l == c.r ? ni + (int)c.l : (c.d_right < c.d_left ? (int)c.r : (int)c.l);
     load_node_box<kKind>(inodes, leaves, ni, id, c.lo, c.hi);
-    climb_global<kKind>(c, n, inodes, leaves, store, flags);
+    climb_global<kKind, kJitter>(c, n, inodes, leaves, store, flags, jt);
 }
 
 // Clears the CTA's shared words and reads the build's error flags: true if
@@ -393,19 +426,19 @@ __device__ __forceinline__ bool group_start(GroupSmem &sm, const uint32_t *flags
 
 // Algorithm 4 from sorted codes and a permutation (lbvh_build_from_sorted,
 // refit, the no-allocation entry point).
-template <int kKind>
+template <int kKind, bool kJitter>
 __global__ void __launch_bounds__(kGroup, 2048 / kGroup)
     construct_block_kernel(const uint64_t *__restrict__ codes, const uint32_t *__restrict__ perm,
                            const float *__restrict__ prims, int n, float4 *inodes, float4 *leaves,
-                           unsigned long long *store, uint32_t *flags, uint4 *pend) {
+                           unsigned long long *store, uint32_t *flags, uint4 *pend, Jitter jt) {
     __shared__ GroupSmem sm;
     if (group_start(sm, flags)) return;
     const int t = threadIdx.x;
     const int i = blockIdx.x * kGroup + t;
     Climb c;
     const bool ok = i < n && leaf_step<kKind>(i, n, codes, perm, 0u, prims, leaves, flags, c);
-    two_phase<kKind>(sm, ok && n > 1, c, n, 0, (int64_t)blockIdx.x * kGroup, t, inodes, leaves, store, flags,
-                     pend ? pend + (int64_t)blockIdx.x * kPendSlots : nullptr);
+    two_phase<kKind, kJitter>(sm, ok && n > 1, c, n, 0, (int64_t)blockIdx.x * kGroup, t, inodes, leaves, store,
+                              flags, pend ? pend + (int64_t)blockIdx.x * kPendSlots : nullptr, jt);
 }
 
 // Algorithm 4 after a sort that kept only the permutation. Each thread
@@ -414,12 +447,12 @@ __global__ void __launch_bounds__(kGroup, 2048 / kGroup)
 // three neighbours (positions a-1, a+kGroup, a+kGroup+1, gathered by threads
 // 0-2) meet in shared memory for the delta* values. The sorted codes are
 // written to codes_out (the tree keeps them for export and refit).
-template <int kKind>
+template <int kKind, bool kJitter>
 __global__ void __launch_bounds__(kGroup, 2048 / kGroup)
     construct_encode_kernel(const uint32_t *__restrict__ perm, const float *__restrict__ prims,
                             const float *__restrict__ bounds, int b, int n, uint64_t *__restrict__ codes_out,
                             float4 *inodes, float4 *leaves, unsigned long long *store, uint32_t *flags,
-                            uint4 *pend) {
+                            uint4 *pend, Jitter jt) {
     __shared__ GroupSmem sm;
     if (group_start(sm, flags)) return;
     const int t = threadIdx.x;
@@ -474,8 +507,8 @@ __global__ void __launch_bounds__(kGroup, 2048 / kGroup)
         }
         leaf_write<kKind>(i, n, p_id, lo, hi, leaves, dl, dr, drn, c);
     }
-    two_phase<kKind>(sm, ok && n > 1, c, n, 0, a, t, inodes, leaves, store, flags,
-                     pend ? pend + (int64_t)blockIdx.x * kPendSlots : nullptr);
+    two_phase<kKind, kJitter>(sm, ok && n > 1, c, n, 0, a, t, inodes, leaves, store, flags,
+                              pend ? pend + (int64_t)blockIdx.x * kPendSlots : nullptr, jt);
 }
 
 // Many trees at once, grouped by global sorted position: global position g
@@ -523,13 +556,27 @@ size_t construct_pend_bytes(int64_t n) { return (size_t)((n + kGroup - 1) / kGro
 
 namespace {
 
+// lbvh_test_construct_jitter's setting (max_ns 0: off)
+std::atomic<unsigned long long> g_jitter_seed{0};
+std::atomic<unsigned> g_jitter_ns{0};
+
+Jitter jitter_setting() {
+    Jitter j;
+    j.seed = g_jitter_seed.load(std::memory_order_relaxed);
+    j.max_ns = g_jitter_ns.load(std::memory_order_relaxed);
+    return j;
+}
+
 void launch_pending(int64_t n, int kind, float4 *inodes, float4 *leaves, unsigned long long *store,
-                    uint32_t *flags, void *pend, cudaStream_t s) {
+                    uint32_t *flags, void *pend, const Jitter &jt, cudaStream_t s) {
     if (!pend || n < 2) return;
     const int64_t slots = (n + kGroup - 1) / kGroup * kPendSlots;
     const unsigned blocks = (unsigned)((slots + 255) / 256);
-    auto k = kind == LBVH_PRIM_POINTS ? climb_pending_kernel<LBVH_PRIM_POINTS> : climb_pending_kernel<LBVH_PRIM_BOXES>;
-    k<<<blocks, 256, 0, s>>>(static_cast<uint4 *>(pend), slots, (int)n, inodes, leaves, store, flags);
+    const bool pts = kind == LBVH_PRIM_POINTS;
+    auto k = jt.max_ns ? (pts ? climb_pending_kernel<LBVH_PRIM_POINTS, true> : climb_pending_kernel<LBVH_PRIM_BOXES, true>)
+                       : (pts ? climb_pending_kernel<LBVH_PRIM_POINTS, false>
+                              : climb_pending_kernel<LBVH_PRIM_BOXES, false>);
+    k<<<blocks, 256, 0, s>>>(static_cast<uint4 *>(pend), slots, (int)n, inodes, leaves, store, flags, jt);
     count_launches(1);
 }
 
@@ -540,12 +587,16 @@ void launch_construct(const uint64_t *sorted_codes, const uint32_t *perm, const 
                       unsigned long long *store, uint32_t *flags, void *pend, cudaStream_t s) {
     if (n <= 0) return;
     const unsigned blocks = (unsigned)((n + kGroup - 1) / kGroup);
-    auto k = kind == LBVH_PRIM_POINTS ? construct_block_kernel<LBVH_PRIM_POINTS>
-                                      : construct_block_kernel<LBVH_PRIM_BOXES>;
+    const Jitter jt = jitter_setting();
+    const bool pts = kind == LBVH_PRIM_POINTS;
+    auto k = jt.max_ns ? (pts ? construct_block_kernel<LBVH_PRIM_POINTS, true>
+                              : construct_block_kernel<LBVH_PRIM_BOXES, true>)
+                       : (pts ? construct_block_kernel<LBVH_PRIM_POINTS, false>
+                              : construct_block_kernel<LBVH_PRIM_BOXES, false>);
     k<<<blocks, kGroup, 0, s>>>(sorted_codes, perm, prims, (int)n, inodes, leaves, store, flags,
-                                static_cast<uint4 *>(pend));
+                                static_cast<uint4 *>(pend), jt);
     count_launches(1);
-    launch_pending(n, kind, inodes, leaves, store, flags, pend, s);
+    launch_pending(n, kind, inodes, leaves, store, flags, pend, jt, s);
 }
 
 void launch_construct_encode(const uint32_t *perm, const float *prims, const float *bounds, int bits, int64_t n,
@@ -553,12 +604,16 @@ void launch_construct_encode(const uint32_t *perm, const float *prims, const flo
                              unsigned long long *store, uint32_t *flags, void *pend, cudaStream_t s) {
     if (n <= 0) return;
     const unsigned blocks = (unsigned)((n + kGroup - 1) / kGroup);
-    auto k = kind == LBVH_PRIM_POINTS ? construct_encode_kernel<LBVH_PRIM_POINTS>
-                                      : construct_encode_kernel<LBVH_PRIM_BOXES>;
+    const Jitter jt = jitter_setting();
+    const bool pts = kind == LBVH_PRIM_POINTS;
+    auto k = jt.max_ns ? (pts ? construct_encode_kernel<LBVH_PRIM_POINTS, true>
+                              : construct_encode_kernel<LBVH_PRIM_BOXES, true>)
+                       : (pts ? construct_encode_kernel<LBVH_PRIM_POINTS, false>
+                              : construct_encode_kernel<LBVH_PRIM_BOXES, false>);
     k<<<blocks, kGroup, 0, s>>>(perm, prims, bounds, bits / 3, (int)n, codes_out, inodes, leaves, store, flags,
-                                static_cast<uint4 *>(pend));
+                                static_cast<uint4 *>(pend), jt);
     count_launches(1);
-    launch_pending(n, kind, inodes, leaves, store, flags, pend, s);
+    launch_pending(n, kind, inodes, leaves, store, flags, pend, jt, s);
 }
 
 }  // namespace lbvh
@@ -597,6 +652,13 @@ lbvh_status static_scratch(StaticScratch *out) {
 }
 
 }  // namespace
+
+extern "C" lbvh_status lbvh_test_construct_jitter(unsigned long long seed, unsigned max_ns) {
+    if (max_ns > 1000000u) return LBVH_ERR_INVALID;
+    lbvh::g_jitter_seed.store(seed, std::memory_order_relaxed);
+    lbvh::g_jitter_ns.store(max_ns, std::memory_order_relaxed);
+    return LBVH_OK;
+}
 
 extern "C" lbvh_status lbvh_construct_static(const uint64_t *d_sorted_codes, const uint32_t *d_perm,
                                              const float *d_prims, int64_t n, int kind, float *d_inodes,

@@ -68,6 +68,7 @@ SIGNATURES = {
     "lbvh_release_cached_memory": (_I32, []),
     "lbvh_refit": (_I32, [_P, _P, _P]),
     "lbvh_test_hold_sort_tile": (_I32, [_I64]),
+    "lbvh_test_construct_jitter": (_I32, [ctypes.c_uint64, ctypes.c_uint32]),
     "lbvh_tree_save": (_I32, [_P, _P, _U64, _P]),
     "lbvh_tree_load": (_I32, [_P, _P, _U64, _P]),
     "lbvh_build_variant": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P]),

@@ -85,6 +85,10 @@ def test_invalid_arguments_rejected_before_any_device_work(lib_path):
                              (16, lbvh.OK)):
             assert lib.lbvh_tree_set_host_chunks(h, chunks) == want
         assert lib.lbvh_tree_set_host_chunks(None, 1) == lbvh.ERR_INVALID
+        # the construct's jitter test hook: up to 10^6 ns, then off again
+        assert lib.lbvh_test_construct_jitter(7, 1000001) == lbvh.ERR_INVALID
+        assert lib.lbvh_test_construct_jitter(7, 1000) == lbvh.OK
+        assert lib.lbvh_test_construct_jitter(0, 0) == lbvh.OK
         # checkpoint images are validated before any device work
         size = ctypes.c_uint64()
         assert lib.lbvh_tree_save(h, None, 0, ctypes.byref(size)) == lbvh.ERR_INVALID  # never built
