@@ -20,9 +20,14 @@ namespace {
 
 thread_local char g_last_error[256] = "";
 
+// Records a runtime error that a call is about to return as its status, and
+// clears the thread's last-error state: the error has been reported, and a
+// later call's launch check (or the caller's own) must not take it for its
+// own (an allocation that failed would otherwise fail the next call too).
 void note_cuda(cudaError_t e) {
     std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e),
                   cudaGetErrorString(e));
+    (void)cudaGetLastError();
 }
 
 #define LBVH_CUDA(expr)                                                    \

@@ -80,7 +80,11 @@ struct Buf {
         p = nullptr;
         bytes = 0;
         want = std::max<size_t>(want, 256);
-        if (lbvh::pool_alloc(&p, want, s) != cudaSuccess) return LBVH_ERR_OOM;
+        if (lbvh::pool_alloc(&p, want, s) != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();  // reported as LBVH_ERR_OOM: no later launch check may see it
+            return LBVH_ERR_OOM;
+        }
         bytes = want;
         return LBVH_OK;
     }

@@ -61,3 +61,31 @@ def test_look_back_wait_runs_out_and_the_next_build_recovers():
 def test_hook_argument_checked():
     from paper_2402_00665_gb300 import lbvh
     assert lbvh.load().lbvh_test_hold_sort_tile(-2) == lbvh.ERR_INVALID
+
+
+def test_allocation_failure_is_reported_and_the_tree_stays_usable():
+    # a count-only query of 2^30 - 1 queries needs about 275 GB of walk slots
+    # (256 bytes each), more than the device has: the library's allocation
+    # fails and the call reports LBVH_ERR_OOM (after ~52 GB of smaller
+    # buffers were had); the tree then answers queries exactly and the
+    # library's cached memory can be given back
+    from paper_2402_00665_gb300 import lbvh
+    lib = lbvh.load()
+    n = 1 << 16
+    pts = inputs.uniform_points(n, seed=71)
+    t = lbvh.Tree().build(pts, lbvh.POINTS, 30)
+    nq = (1 << 30) - 1
+    q = torch.zeros((nq, 3), dtype=torch.float32, device="cuda")
+    off = torch.empty(nq + 1, dtype=torch.int64, device="cuda")
+    st, _ = t.query_into(q, lbvh.SPHERE, off, None, radius=0.01)
+    assert st == lbvh.ERR_OOM
+    del q, off
+    torch.cuda.synchronize()
+    r = float(inputs.radius_for_neighbours(n))
+    o = oracle.build(pts, oracle.POINTS, 30)
+    ooff, ohits = oracle.query(o, pts[:5000], oracle.SPHERE, radius=r)
+    doff, dhits = t.query(pts[:5000], lbvh.SPHERE, radius=r)
+    assert np.array_equal(doff.cpu().numpy(), ooff)
+    assert np.array_equal(dhits.cpu().numpy().view(np.uint32), ohits)
+    t.close()
+    assert lib.lbvh_release_cached_memory() == lbvh.OK
