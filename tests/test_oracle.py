@@ -342,6 +342,77 @@ def test_sphere_predicate_against_fp64():
     assert agree > 2900
 
 
+def _rn32(x):
+    """x (a Fraction) rounded to the nearest FP32 value, ties to even: the
+    IEEE rounding of one FP32 operation, computed exactly."""
+    from fractions import Fraction
+    if x == 0:
+        return np.float32(0.0)
+    sign = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()  # 2^e <= a < 2^(e+2)
+    if Fraction(2) ** e > a:
+        e -= 1
+    if Fraction(2) ** (e + 1) <= a:
+        e += 1
+    ulp = Fraction(2) ** (max(e, -126) - 23)  # subnormals below 2^-126
+    q = a / ulp
+    n = q.numerator // q.denominator
+    rem = q - n
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    v = n * ulp
+    if v >= Fraction(2) ** 128:
+        return np.float32(sign * np.inf)
+    return np.float32(sign * float(v))  # n * ulp has at most 24 significant bits: exact
+
+
+def _sphere_d2_exact(c, box):
+    """Reading G8 computed with exact rationals: per axis the gap
+    max(lo - c, c - hi, 0) from two FP32 subtractions, then d2 = ex*ex
+    rounded once, + ey*ey and + ez*ez each as one fused multiply-add (the
+    exact product plus the sum, rounded once)."""
+    from fractions import Fraction
+    F = lambda v: Fraction(float(v))  # an FP32 value is exact as a double
+    e = []
+    for a in range(3):
+        below = _rn32(F(box[a]) - F(c[a]))
+        above = _rn32(F(c[a]) - F(box[3 + a]))
+        e.append(max(below, above, np.float32(0.0)))
+    d2 = _rn32(F(e[0]) * F(e[0]))
+    d2 = _rn32(F(e[1]) * F(e[1]) + F(d2))
+    return _rn32(F(e[2]) * F(e[2]) + F(d2))
+
+
+def test_sphere_predicate_at_the_boundary_against_exact_rounding():
+    """The ball test and the kNN squared distance, exactly as reading G8 rounds
+    them, at radii on both sides of the boundary: for each centre and box, r
+    the FP32 square root of the exact d2 and its two neighbours, so that r*r
+    falls just below, on or just above d2. The reference rounds exact
+    rationals; nothing of it comes from the oracle's C code."""
+    from fractions import Fraction
+    rng = np.random.default_rng(17)
+    cases = on_boundary = 0
+    for k in range(1500):
+        scale = np.float32(10.0 ** rng.integers(-6, 3))  # gaps from ~1e-6 to ~1e2
+        lo = (rng.random(3) * scale).astype(np.float32)
+        hi = (lo + rng.random(3).astype(np.float32) * scale).astype(np.float32)
+        c = (rng.random(3) * np.float32(3) * scale - scale).astype(np.float32)
+        if k % 3 == 0:  # one axis inside the slab, or two: fewer terms
+            c[rng.integers(0, 3)] = (lo[0] + hi[0]) * np.float32(0.5) if lo[0] <= hi[0] else c[0]
+        box = np.concatenate([lo, hi])
+        d2 = _sphere_d2_exact(c, box)
+        assert np.float32(oracle.point_box_d2(c, box)) == d2
+        r0 = np.float32(math.sqrt(float(d2)))
+        for r in (np.nextafter(r0, np.float32(0)), r0, np.nextafter(r0, np.float32(np.inf))):
+            r2 = _rn32(Fraction(float(r)) * Fraction(float(r)))
+            want = bool(d2 <= r2)
+            assert oracle.sphere_box(c, r, box) == want, (c, box, r)
+            cases += 1
+            on_boundary += int(d2 == r2)
+    assert cases == 4500 and on_boundary > 0
+
+
 def test_predicate_closed_boundaries():
     box = np.array([0, 0, 0, 1, 1, 1], np.float32)
     assert oracle.sphere_box([2.0, 0.5, 0.5], 1.0, box)  # touching: closed ball
