@@ -632,6 +632,72 @@ def test_ray_box_matches_exact_slab_test_away_from_the_boundary():
     assert agree > 2500
 
 
+def _slab_g14(ray, box):
+    """Reading G14 with every FP32 operation rounded exactly (rationals, one
+    rounding each): inv = 1/d; an axis with d = 0 or an infinite inv needs
+    lo <= o <= hi; else t1 = (lo - o) * inv and t2 = (hi - o) * inv, each
+    difference and product rounded; tnear = max(tmin, min t), tfar = min(tmax,
+    max t); hit iff tnear <= tfar. A non-finite origin or direction, or a NaN
+    tmin or tmax, hits nothing."""
+    from fractions import Fraction
+    F = lambda v: Fraction(float(v))
+    if not (np.all(np.isfinite(ray[:3])) and np.all(np.isfinite(ray[4:7]))) or np.isnan(ray[3]) or np.isnan(ray[7]):
+        return False
+    tnear, tfar = np.float32(ray[3]), np.float32(ray[7])
+    for a in range(3):
+        o, d = ray[a], ray[4 + a]
+        inv = np.float32(np.inf) if d == 0 else _rn32(Fraction(1) / F(d))
+        if d == 0 or np.isinf(inv):
+            if not (box[a] <= o <= box[3 + a]):
+                return False
+            continue
+        t1 = _rn32(F(_rn32(F(box[a]) - F(o))) * F(inv))
+        t2 = _rn32(F(_rn32(F(box[3 + a]) - F(o))) * F(inv))
+        tlo, thi = (t1, t2) if t1 < t2 else (t2, t1)
+        tnear = tlo if tlo > tnear else tnear
+        tfar = thi if thi < tfar else tfar
+    return bool(tnear <= tfar)
+
+
+def test_ray_box_at_the_boundary_against_exact_rounding():
+    """Rays aimed at points of a box's surface with the segment ending where
+    the rounded slab test puts the entry (tmax = that tnear) or one FP32 step
+    before or after it, so that tnear <= tfar is decided by the last bit: the
+    oracle against reading G14 rounded exactly (no oracle code in the
+    reference)."""
+    rng = np.random.default_rng(53)
+    cases = flips = 0
+    for _ in range(800):
+        lo = rng.random(3).astype(np.float32)
+        box = np.concatenate([lo, (lo + rng.random(3) * 0.3).astype(np.float32)]).astype(np.float32)
+        target = (box[:3] + rng.random(3).astype(np.float32) * (box[3:] - box[:3])).astype(np.float32)
+        target[rng.integers(0, 3)] = box[rng.integers(0, 2) * 3 + rng.integers(0, 3)]  # onto a face plane
+        o = (rng.random(3) * 3 - 1).astype(np.float32)
+        d = (target - o).astype(np.float32)
+        if not np.all(np.isfinite(d)) or np.all(d == 0):
+            continue
+        probe = _ray(o, d, 0.0, np.inf)
+        # the rounded entry parameter: tnear of the unbounded segment
+        tn = np.float32(0.0)
+        for a in range(3):
+            if d[a] != 0:
+                from fractions import Fraction
+                inv = _rn32(Fraction(1) / Fraction(float(d[a])))
+                t1 = _rn32(Fraction(float(_rn32(Fraction(float(box[a])) - Fraction(float(o[a]))))) * Fraction(float(inv)))
+                t2 = _rn32(Fraction(float(_rn32(Fraction(float(box[3 + a])) - Fraction(float(o[a]))))) * Fraction(float(inv)))
+                tn = max(tn, min(t1, t2))
+        results = []
+        for tmax in (np.nextafter(tn, np.float32(-np.inf)), tn, np.nextafter(tn, np.float32(np.inf))):
+            ray = _ray(o, d, 0.0, tmax)
+            want = _slab_g14(ray, box)
+            assert oracle.ray_box(ray, box) == want, (ray, box)
+            results.append(want)
+            cases += 1
+        flips += int(results[0] != results[1])
+        assert _slab_g14(probe, box) == oracle.ray_box(probe, box)
+    assert cases > 2000 and flips > 100
+
+
 @pytest.mark.parametrize("kind", [oracle.POINTS, oracle.BOXES])
 def test_ray_traversal_equals_bruteforce(kind):
     rng = np.random.default_rng(52)
