@@ -170,6 +170,34 @@ def test_quantize_matches_exact_floor():
         assert mismatches <= 2 + 2000 * 3 * 2.0 ** (b - 24)
 
 
+def test_quantize_equals_reading_g7_rounded_exactly():
+    """The cell index exactly as reading G7 computes it, each FP32 operation
+    rounded once from exact rationals (extent = hi - lo, t = (c - lo) / extent,
+    v = t * 2^b, then 0, the last cell, or trunc(v)), on centres at cell
+    boundaries and one or two FP32 steps either side, where the roundings
+    decide the cell. The reference is built from the reading alone."""
+    from fractions import Fraction
+    F = lambda v: Fraction(float(v))
+    rng = np.random.default_rng(6)
+    moved = 0
+    for lo, hi in ((np.float32(-1.25), np.float32(3.5)), (np.float32(0.0), np.float32(1.0)),
+                   (np.float32(1e-3), np.float32(7e-3)), (np.float32(-300.0), np.float32(2.5e4))):
+        for b in (1, 10, 21):
+            top = (1 << b) - 1
+            extent = _rn32(F(hi) - F(lo))
+            for k in rng.integers(0, 1 << b, 150):
+                edge = np.float32(float(F(lo) + F(extent) * Fraction(int(k), 1 << b)))
+                for c in (edge, np.nextafter(edge, np.float32(-np.inf)), np.nextafter(edge, np.float32(np.inf)),
+                          np.nextafter(np.nextafter(edge, np.float32(np.inf)), np.float32(np.inf))):
+                    t = _rn32(F(_rn32(F(c) - F(lo))) / F(extent))
+                    v = _rn32(F(t) * (1 << b))
+                    want = 0 if not v > 0 else (top if v >= top else int(math.floor(float(v))))
+                    assert oracle.quantize(float(c), float(lo), float(hi), b) == want, (c, lo, hi, b)
+                    exact = (F(c) - F(lo)) / (F(hi) - F(lo)) * (1 << b)
+                    moved += int(want != min(max(math.floor(exact), 0), top))
+    assert moved > 0  # some centres are put in the neighbouring cell by the roundings
+
+
 def test_morton_codes_and_bounds():
     pts = inputs.uniform_points(1000, seed=3)
     codes, bounds = oracle.morton_codes(pts, oracle.POINTS, 30)
